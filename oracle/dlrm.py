@@ -1,0 +1,384 @@
+"""HE-LRM: client-side digit selectors, block-diagonal packing, and the
+encrypted DLRM pipeline (test infrastructure only).
+
+Paper passages followed:
+  - Sec. 3 (private embedding lookup as y = E^T s with a one-hot selector s
+    built by the client, evaluated as a plaintext-matrix x ciphertext product
+    with the BSGS method, consuming one level);
+  - Sec. 4.1 (deterministic base-p digit decomposition, little-endian,
+    l = ceil(log_p k); the embedding is sum_j C_j[i_j]);
+  - Sec. 4.2.2 (block-diagonal packing of all tables into one matrix, the
+    client concatenating the one-hots of all tables into one vector);
+  - Sec. 2.2 and Sec. 5.3 (DLRM: bottom MLP, embeddings, interaction, top MLP,
+    encrypted logit, sigmoid at the client).
+
+The readings where the paper is silent (activation x^2 everywhere but the last
+top layer, the dot-interaction scheme, the level schedule, slot layouts) are
+stated at each function.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import ckks, linear, ring
+
+DIM = 16
+
+
+# --------------------------------------------------------------------------
+# Client side: digits and selectors (Sec. 4.1, Sec. 4.2.2)
+# --------------------------------------------------------------------------
+def num_digits(k: int, p: int) -> int:
+    """Smallest l >= 1 with p^l >= k (integer loop, no floating-point log)."""
+    ell, cap = 1, p
+    while cap < k:
+        cap *= p
+        ell += 1
+    return ell
+
+
+def digits(i: int, p: int, ell: int) -> list:
+    """Little-endian base-p digits (i_0, ..., i_{l-1}) of i: i = sum_j i_j p^j."""
+    out = []
+    for _ in range(ell):
+        out.append(i % p)
+        i //= p
+    return out
+
+
+def selector_layout(cards, p):
+    """[(table, digit, offset, width)]: table t in order, digit j ascending.
+
+    A table with k <= p keeps its plain one-hot of width k; a larger table gets
+    l_t one-hots of width p.
+    """
+    out, off = [], 0
+    for t, k in enumerate(cards):
+        if k <= p:
+            out.append((t, 0, off, k))
+            off += k
+        else:
+            for j in range(num_digits(k, p)):
+                out.append((t, j, off, p))
+                off += p
+    return out, off
+
+
+def selector_vector(cards, p, indices) -> np.ndarray:
+    """The concatenated one-hot digit selectors of one query."""
+    lay, width = selector_layout(cards, p)
+    v = np.zeros(width)
+    for (t, j, off, w) in lay:
+        i = int(indices[t])
+        if cards[t] <= p:
+            v[off + i] = 1.0
+        else:
+            v[off + digits(i, p, num_digits(cards[t], p))[j]] = 1.0
+    return v
+
+
+def replicate(v: np.ndarray, period: int, n: int) -> np.ndarray:
+    vp = np.zeros(period)
+    vp[: len(v)] = v
+    return vp[np.arange(n) % period]
+
+
+def embedding_matrix(cards, p, tables, row_offset: int, n_rows: int, dim: int = DIM) -> np.ndarray:
+    """Block-diagonal packing: table t's transposed compressed tables occupy
+    rows [row_offset + dim t, row_offset + dim (t+1)) and the selector columns
+    of its digits (torch.block_diag of the per-table [C_0^T ... C_{l-1}^T])."""
+    lay, width = selector_layout(cards, p)
+    M = np.zeros((n_rows, width))
+    for (t, j, off, w) in lay:
+        C = np.asarray(tables[t][j], dtype=np.float64)
+        M[row_offset + dim * t: row_offset + dim * (t + 1), off: off + w] = C[:w].T
+    return M
+
+
+# --------------------------------------------------------------------------
+# Cleartext FP64 DLRM: the plain definition of the result
+# --------------------------------------------------------------------------
+def embedding_cleartext(cards, p, tables, indices):
+    out = []
+    for t, k in enumerate(cards):
+        i = int(indices[t])
+        if k <= p:
+            out.append(np.asarray(tables[t][0][i], dtype=np.float64))
+        else:
+            ds = digits(i, p, num_digits(k, p))
+            out.append(sum(np.asarray(tables[t][j][ds[j]], dtype=np.float64) for j in range(len(ds))))
+    return out
+
+
+def dlrm_cleartext(spec, w, dense, indices):
+    """Bottom MLP (x^2 after every layer), embeddings, interaction
+    ([b; e_1..e_T] for concat; [b; <z_a, z_c> for a < c] for dot, pairs in
+    lexicographic order), top MLP (x^2 after all but the last layer); returns
+    (logit, sigmoid(logit), top-MLP input)."""
+    h = np.asarray(dense, dtype=np.float64)
+    for W, b in zip(w.bottom_W, w.bottom_b):
+        h = (W @ h + b) ** 2
+    embs = embedding_cleartext(spec.cards, spec.base, w.tables, indices)
+    blocks = [h] + embs
+    if spec.interaction == "dot":
+        x = [h] + [np.array([blocks[a] @ blocks[c]]) for a in range(len(blocks))
+                   for c in range(a + 1, len(blocks))]
+        x = np.concatenate(x)
+    else:
+        x = np.concatenate(blocks)
+    y = x
+    for i, (W, b) in enumerate(zip(w.top_W, w.top_b)):
+        y = W @ y + b
+        if i + 1 < len(w.top_W):
+            y = y ** 2
+    logit = float(y[0])
+    return logit, 1.0 / (1.0 + np.exp(-logit)), x
+
+
+# --------------------------------------------------------------------------
+# Model compilation (layouts, levels, plaintexts)
+# --------------------------------------------------------------------------
+@dataclass
+class Layer:
+    pm: linear.PtMatrix
+    bias: np.ndarray | None          # signed coefficients at (level - 1), scale = out_scale
+    square: bool
+
+
+@dataclass
+class Compiled:
+    spec: object
+    lvl_dense: int
+    lvl_sel: int
+    lvl_z: int
+    lvl_u: int
+    p_dense: int
+    p_sel: int
+    W_z: int
+    W2: int = 0
+    W_u: int = 0
+    Bp: int = 0                      # blocks in z (with the ones block for dot)
+    S: int = 0                       # dot: number of block shifts
+    bottom: list = field(default_factory=list)
+    emb: linear.PtMatrix | None = None
+    ones: np.ndarray | None = None
+    masks: list = field(default_factory=list)       # dot: mask_0 .. mask_S
+    mask_scale: float = 0.0
+    top: list = field(default_factory=list)
+
+    def rotation_steps(self):
+        st = set()
+        for lay in self.bottom + self.top:
+            st |= set(linear.rotation_steps(lay.pm))
+        st |= set(linear.rotation_steps(self.emb))
+        if self.spec.interaction == "dot":
+            st.add(-DIM * self.Bp)
+            st |= {DIM * s for s in range(1, self.S + 1)}
+        return sorted(st)
+
+    def plaintexts(self):
+        """Every plaintext of the model, in the canonical order: per bottom
+        layer its diagonals in (g, b) order then its bias; the embedding
+        diagonals; (dot) the ones block and the masks 0..S; per top layer its
+        diagonals then its bias."""
+        out = []
+        for lay in self.bottom:
+            out += [lay.pm.pts[k] for k in lay.pm.ordered_keys()] + [lay.bias]
+        out += [self.emb.pts[k] for k in self.emb.ordered_keys()]
+        if self.spec.interaction == "dot":
+            out += [self.ones] + list(self.masks)
+        for lay in self.top:
+            out += [lay.pm.pts[k] for k in lay.pm.ordered_keys()] + [lay.bias]
+        return out
+
+
+def pair_index(a: int, c: int, B: int) -> int:
+    """Index of the pair (a, c), a < c < B, in lexicographic order."""
+    return sum(B - 1 - x for x in range(a)) + (c - a - 1)
+
+
+def dot_top_matrix(W0: np.ndarray, B: int, Bp: int, S: int, W2: int, W_u: int) -> np.ndarray:
+    """First top layer over the interaction layout: region s-1 (width W2) holds,
+    in block a, the products z_a * z_{(a+s) mod B'}; its 16 slots all get the
+    weight of pair {a, (a+s) mod B'} (the block sum of the dot product is folded
+    into the weights), except pair {0, ones} whose slots carry b_out itself."""
+    M = np.zeros((W0.shape[0], W_u))
+    for s in range(1, S + 1):
+        n_a = Bp // 2 if (Bp % 2 == 0 and s == Bp // 2) else Bp
+        for a in range(n_a):
+            x, y = sorted((a, (a + s) % Bp))
+            cols = (s - 1) * W2 + DIM * a + np.arange(DIM)
+            if y == Bp - 1:
+                if x == 0:
+                    M[:, cols] = W0[:, :DIM]
+            else:
+                M[:, cols] = W0[:, [DIM + pair_index(x, y, B)]]
+    return M
+
+
+def compile_model(p: ckks.Params, spec, w) -> Compiled:
+    """Levels are assigned as late as possible so the logit ends at level 0:
+    each matvec and each x^2 consumes one level, the dot interaction two."""
+    T = len(spec.cards)
+    B = T + 1
+    n_bot, n_top = len(w.bottom_W), len(w.top_W)
+    lvl_u = 2 * n_top - 1
+    dot = spec.interaction == "dot"
+    lvl_z = lvl_u + 2 if dot else lvl_u
+    lvl_sel = lvl_z + 1
+    lvl_dense = lvl_z + 2 * n_bot
+    if lvl_dense > p.L:
+        raise ValueError(f"model needs {lvl_dense} levels, chain has {p.L}")
+    Bp = B + 1 if dot else B
+    W_z = linear.pow2ceil(DIM * Bp)
+    lay_sel, sel_w = selector_layout(spec.cards, spec.base)
+    c = Compiled(spec, lvl_dense, lvl_sel, lvl_z, lvl_u, linear.pow2ceil(spec.n_dense),
+                 linear.pow2ceil(sel_w), W_z, Bp=Bp)
+    if dot:
+        c.W2 = linear.pow2ceil(2 * DIM * Bp)
+        c.S = Bp // 2
+        c.W_u = linear.pow2ceil(c.S * c.W2)
+    else:
+        c.W_u = W_z
+    if max(c.W_u, c.p_sel, W_z) > p.n:
+        raise ValueError("layout wider than the slot count")
+
+    delta = p.delta
+    # Bottom MLP
+    lvl, scale, in_pad = lvl_dense, delta, c.p_dense
+    for i, (W, b) in enumerate(zip(w.bottom_W, w.bottom_b)):
+        last = i + 1 == n_bot
+        out_pad = W_z if last else linear.pow2ceil(W.shape[0])
+        pm = linear.prepare(p, W, in_pad, out_pad, lvl, scale, delta)
+        bias = ckks.encode_real(p, replicate(b, out_pad, p.n), delta)
+        c.bottom.append(Layer(pm, bias, True))
+        lvl -= 1
+        scale = (delta * delta) / p.q[lvl]
+        lvl -= 1
+        in_pad = out_pad
+    assert lvl == lvl_z
+    scale_b = scale
+    # Embedding lookup (block-diagonal, rows [16, 16 (T+1)) of the z layout)
+    M = embedding_matrix(spec.cards, spec.base, w.tables, DIM, DIM * B)
+    c.emb = linear.prepare(p, M, c.p_sel, W_z, lvl_sel, delta, scale_b)
+    if dot:
+        ones = np.zeros(W_z)
+        ones[DIM * B: DIM * B + DIM] = 1.0
+        c.ones = ckks.encode_real(p, replicate(ones, W_z, p.n), scale_b)
+        c.mask_scale = float(p.q[lvl_z]) * delta / scale_b
+        j = np.arange(p.n)
+        c.masks.append(ckks.encode_real(p, ((j % c.W2) < DIM * Bp).astype(float), c.mask_scale))
+        for s in range(1, c.S + 1):
+            n_a = Bp // 2 if (Bp % 2 == 0 and s == Bp // 2) else Bp
+            lo = (s - 1) * c.W2
+            m = (((j % c.W_u) >= lo) & ((j % c.W_u) < lo + DIM * n_a)).astype(float)
+            c.masks.append(ckks.encode_real(p, m, c.mask_scale))
+        u_scale = (delta * delta) / p.q[lvl_z - 1]
+    else:
+        u_scale = scale_b
+    # Top MLP
+    lvl, scale = lvl_u, u_scale
+    for i, (W, b) in enumerate(zip(w.top_W, w.top_b)):
+        last = i + 1 == n_top
+        if i == 0:
+            in_pad = c.W_u
+            Wm = dot_top_matrix(W, B, Bp, c.S, c.W2, c.W_u) if dot else W
+        else:
+            in_pad = linear.pow2ceil(W.shape[1])
+            Wm = W
+        out_pad = linear.pow2ceil(W.shape[0])
+        pm = linear.prepare(p, Wm, in_pad, out_pad, lvl, scale, delta)
+        bias = ckks.encode_real(p, replicate(b, out_pad, p.n), delta)
+        c.top.append(Layer(pm, bias, not last))
+        lvl -= 1
+        scale = delta
+        if not last:
+            scale = (delta * delta) / p.q[lvl]
+            lvl -= 1
+    assert lvl == 0
+    return c
+
+
+# --------------------------------------------------------------------------
+# The encrypted pipeline (Sec. 5.3)
+# --------------------------------------------------------------------------
+def query_slots(p: ckks.Params, c: Compiled, dense, indices):
+    """Client packing: dense features with period p_dense; concatenated digit
+    one-hots with period p_sel."""
+    xd = replicate(np.asarray(dense, dtype=np.float64), c.p_dense, p.n)
+    xs = replicate(selector_vector(c.spec.cards, c.spec.base, indices), c.p_sel, p.n)
+    return xd, xs
+
+
+def encrypt_query(p, keys, c: Compiled, dense, indices, seed: int):
+    """ct_dense with `seed` at lvl_dense, ct_sel with `seed + 1` at lvl_sel, both at Delta."""
+    xd, xs = query_slots(p, c, dense, indices)
+    ct_d = ckks.encrypt(p, keys, ckks.encode_real(p, xd, p.delta), c.lvl_dense, p.delta, seed)
+    ct_s = ckks.encrypt(p, keys, ckks.encode_real(p, xs, p.delta), c.lvl_sel, p.delta, seed + 1)
+    return ct_d, ct_s
+
+
+def _dense_layer(p, keys, lay: Layer, x: ckks.Ct) -> ckks.Ct:
+    y = linear.matvec(p, keys, lay.pm, x)
+    y = ckks.add_pt(p, y, lay.bias, y.scale)
+    if lay.square:
+        y = ckks.square(p, keys, y)
+    return y
+
+
+def dot_interaction(p, keys, c: Compiled, z: ckks.Ct) -> ckks.Ct:
+    """Pairwise products of the z blocks in two levels.
+
+    z1 = z masked to one period of W2 (first 16 B' slots); zz = z1 + rot(z1,
+    -16 B') repeats the blocks so block a+s reads z_{(a+s) mod B'}; A_s = z
+    masked to region s-1 of the W_u layout; u = relin(sum_s A_s (x) rot(zz, 16 s))
+    rescaled: region s-1, block a holds z_a * z_{(a+s) mod B'}.
+    """
+    z1 = ckks.rescale(p, ckks.mul_pt(p, z, c.masks[0], c.mask_scale))
+    z1.scale = p.delta
+    A = []
+    for s in range(1, c.S + 1):
+        a = ckks.rescale(p, ckks.mul_pt(p, z, c.masks[s], c.mask_scale))
+        a.scale = p.delta
+        A.append(a)
+    zz = ckks.add(p, z1, ckks.rotate(p, keys, z1, -DIM * c.Bp))
+    R = ckks.rotate_hoisted(p, keys, zz, [DIM * s for s in range(1, c.S + 1)])
+    lvl = z1.level
+    mods = p.q_mods(lvl)
+    acc = None
+    for s in range(1, c.S + 1):
+        d = ckks.tensor(p, A[s - 1], R[DIM * s])
+        acc = d if acc is None else tuple(ring.add(x, y, mods) for x, y in zip(acc, d))
+    return ckks.rescale(p, ckks.relinearize(p, keys, acc, lvl, p.delta * p.delta))
+
+
+def infer(p, keys, c: Compiled, ct_dense: ckks.Ct, ct_sel: ckks.Ct) -> ckks.Ct:
+    h = ct_dense
+    for lay in c.bottom:
+        h = _dense_layer(p, keys, lay, h)
+    e = linear.matvec(p, keys, c.emb, ct_sel)
+    z = ckks.add(p, h, e)
+    if c.spec.interaction == "dot":
+        z = ckks.add_pt(p, z, c.ones, z.scale)
+        u = dot_interaction(p, keys, c, z)
+    else:
+        u = z
+    y = u
+    for lay in c.top:
+        y = _dense_layer(p, keys, lay, y)
+    return y
+
+
+def decrypt_logit(p, sk, ct: ckks.Ct):
+    logit = float(ckks.decrypt(p, sk, ct, 1)[0])
+    return logit, 1.0 / (1.0 + np.exp(-logit))
+
+
+# --------------------------------------------------------------------------
+# The stand-alone lookup (the tiny workload): one table, digits in base p
+# --------------------------------------------------------------------------
+def lookup_matrix(tables, p_base: int, k: int) -> np.ndarray:
+    """dim x (l p) matrix [C_0^T ... C_{l-1}^T] of one compressed table."""
+    return embedding_matrix([k], p_base, [tables], 0, DIM)

@@ -1,0 +1,187 @@
+"""Plaintext-matrix x ciphertext-vector products (test infrastructure only).
+
+Halevi-Shoup diagonal method and its baby-step giant-step (BSGS) form
+(HE-LRM Sec. 2.1.4 "Neural Network Layers in FHE": the diagonals of the weight
+matrix multiply rotations of the input; BSGS pre-rotates the diagonals so only
+O(sqrt n) rotations remain), evaluated with double hoisting (Sec. 3.2.1 cites
+the double-hoisted BSGS of Bossuat et al.: one ModUp shared by the baby steps,
+products accumulated over QP, the giant-step rotations applied to QP
+ciphertexts, one final ModDown).
+
+Layout (a reading: the paper shows it only in a figure).  A vector of padded
+length v = 2^k is replicated with period v over all n slots.  For a matrix
+n_out x n_in padded to out_pad x in_pad (powers of two) there are
+D = min(in_pad, out_pad) extended diagonals
+
+    diag_i[j] = W[j mod out_pad, (j + i) mod in_pad],   j < n,  i < D,
+
+and, when in_pad > out_pad, rotate-and-add folds by in_pad/2, ..., out_pad.
+The result is W x replicated with period out_pad.  BSGS split: n1 = the
+smallest power of two with n1^2 >= D, n2 = D / n1; i = g*n1 + b and
+diag'_{g,b} = rot(diag_{g n1 + b}, -g n1).  All-zero diagonals are skipped,
+which changes no result (their products are exactly zero).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import ckks, ring
+
+
+def pow2ceil(x: int) -> int:
+    x = max(int(x), 1)
+    return 1 << (x - 1).bit_length()
+
+
+def bsgs_split(D: int):
+    n1 = 1
+    while n1 * n1 < D:
+        n1 *= 2
+    return n1, D // n1
+
+
+def extended_diagonals(W: np.ndarray, in_pad: int, out_pad: int, n: int) -> np.ndarray:
+    """[D, n] float64 array of diag_i[j] = Wpad[j mod out_pad, (j+i) mod in_pad]."""
+    Wp = np.zeros((out_pad, in_pad))
+    Wp[: W.shape[0], : W.shape[1]] = W
+    D = min(in_pad, out_pad)
+    j = np.arange(n)
+    return np.stack([Wp[j % out_pad, (j + i) % in_pad] for i in range(D)])
+
+
+def fold_shifts(in_pad: int, out_pad: int):
+    out, s = [], in_pad // 2
+    while s >= out_pad:
+        out.append(s)
+        s //= 2
+    return out
+
+
+@dataclass
+class Layout:
+    in_pad: int
+    out_pad: int
+    D: int
+    n1: int
+    n2: int
+    folds: list
+
+    @staticmethod
+    def make(in_pad: int, out_pad: int) -> "Layout":
+        D = min(in_pad, out_pad)
+        n1, n2 = bsgs_split(D)
+        return Layout(in_pad, out_pad, D, n1, n2, fold_shifts(in_pad, out_pad))
+
+
+@dataclass
+class PtMatrix:
+    """Encoded pre-rotated diagonals of one layer at input level `level`.
+
+    `pts` maps (g, b) -> signed integer coefficients (length N) for the
+    non-zero diagonals, listed in (g, b) order; `pt_scale` is their scale.
+    """
+    layout: Layout
+    level: int
+    pt_scale: float
+    out_scale: float
+    pts: dict = field(default_factory=dict)
+
+    def ordered_keys(self):
+        return sorted(self.pts)
+
+
+def prepare(p: ckks.Params, W: np.ndarray, in_pad: int, out_pad: int, level: int,
+            ct_scale: float, target_scale: float) -> PtMatrix:
+    """Encode the diagonals so the rescaled output has scale exactly target_scale:
+    pt_scale = q_l * target / ct_scale."""
+    lay = Layout.make(in_pad, out_pad)
+    diags = extended_diagonals(np.asarray(W, dtype=np.float64), in_pad, out_pad, p.n)
+    pt_scale = float(p.q[level]) * target_scale / ct_scale
+    pm = PtMatrix(lay, level, pt_scale, target_scale)
+    for g in range(lay.n2):
+        for b in range(lay.n1):
+            dg = diags[g * lay.n1 + b]
+            if not np.any(dg):
+                continue
+            rot = np.roll(dg, g * lay.n1)            # rot(x, -s)[j] = x[j - s]
+            pm.pts[(g, b)] = ckks.encode_real(p, rot, pt_scale)
+    return pm
+
+
+def rotation_steps(pm: PtMatrix):
+    """Rotations (slot steps) the matvec uses."""
+    lay = pm.layout
+    babies = {b for (_, b) in pm.pts}
+    giants = {g for (g, _) in pm.pts}
+    return sorted({b for b in babies if b} | {g * lay.n1 for g in giants if g} | set(lay.folds))
+
+
+def matvec(p: ckks.Params, keys: ckks.Keys, pm: PtMatrix, ct: ckks.Ct) -> ckks.Ct:
+    """Double-hoisted BSGS y = W x, then rescale, then the folds."""
+    lay, lvl = pm.layout, ct.level
+    if lvl != pm.level:
+        raise ValueError("ciphertext level does not match the prepared matrix")
+    qp = p.qp_mods(lvl)
+    qm = p.q_mods(lvl)
+    psis = p.psis(qp)
+
+    # Baby steps in QP, sharing one ModUp of c1 (no ModDown).
+    digits = ckks.modup(p, ct.c1, lvl)
+    baby = {}
+    for b in sorted({b for (_, b) in pm.pts}):
+        if b == 0:
+            baby[0] = (ckks.lift_times_P(p, ct.c0, lvl), ckks.lift_times_P(p, ct.c1, lvl))
+            continue
+        k = p.galois(b)
+        dr = [ckks.automorphism(p, d, k, qp) for d in digits]
+        u0, u1 = ckks.ks_inner(p, dr, ckks._key_for(keys, k), lvl)
+        u0 = ring.add(u0, ckks.lift_times_P(p, ckks.automorphism(p, ct.c0, k, qm), lvl), qp)
+        baby[b] = (u0, u1)
+    # Products are sums of ring products; evaluate them in the oracle's own
+    # NTT domain (an exact ring isomorphism) to save transforms.
+    baby_hat = {b: (ring.ntt(u0, qp, psis), ring.ntt(u1, qp, psis)) for b, (u0, u1) in baby.items()}
+
+    acc0 = np.zeros((len(qp), p.N), dtype=np.uint64)
+    acc1 = np.zeros_like(acc0)
+    for g in range(lay.n2):
+        bs = [b for (gg, b) in pm.pts if gg == g]
+        if not bs:
+            continue
+        s0 = np.zeros((len(qp), p.N), dtype=np.uint64)
+        s1 = np.zeros_like(s0)
+        for b in bs:
+            dh = ring.ntt(ring.from_signed(pm.pts[(g, b)], qp), qp, psis)
+            s0 = ring.add(s0, ring.mul(dh, baby_hat[b][0], qp), qp)
+            s1 = ring.add(s1, ring.mul(dh, baby_hat[b][1], qp), qp)
+        in0 = ring.ntt(s0, qp, psis, inverse=True)
+        in1 = ring.ntt(s1, qp, psis, inverse=True)
+        if g == 0:
+            acc0, acc1 = ring.add(acc0, in0, qp), ring.add(acc1, in1, qp)
+            continue
+        # Giant step on a QP ciphertext: ModDown the a-part, ModUp, phi, key
+        # inner product; the b-part is already in QP and only gets phi.
+        k = p.galois(g * lay.n1)
+        c1q = ckks.moddown(p, in1, lvl)
+        dr = [ckks.automorphism(p, d, k, qp) for d in ckks.modup(p, c1q, lvl)]
+        k0, k1 = ckks.ks_inner(p, dr, ckks._key_for(keys, k), lvl)
+        acc0 = ring.add(acc0, ring.add(ckks.automorphism(p, in0, k, qp), k0, qp), qp)
+        acc1 = ring.add(acc1, k1, qp)
+
+    out = ckks.Ct(ckks.moddown(p, acc0, lvl), ckks.moddown(p, acc1, lvl), lvl,
+                  ct.scale * pm.pt_scale)
+    out = ckks.rescale(p, out)
+    out.scale = pm.out_scale
+    for sh in lay.folds:
+        out = ckks.add(p, out, ckks.rotate(p, keys, out, sh))
+    return out
+
+
+def matvec_cleartext(W: np.ndarray, x: np.ndarray, in_pad: int, out_pad: int, n: int) -> np.ndarray:
+    """What the encrypted matvec must decrypt to, slot by slot (FP64)."""
+    xp = np.zeros(in_pad)
+    xp[: len(x)] = x
+    y = np.zeros(out_pad)
+    y[: W.shape[0]] = np.asarray(W, dtype=np.float64) @ xp[: W.shape[1]]
+    return y[np.arange(n) % out_pad]

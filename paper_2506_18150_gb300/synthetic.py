@@ -1,0 +1,241 @@
+"""Seeded synthetic workloads shaped like the HE-LRM experiments.
+
+The UCI Heart Disease and Criteo datasets and trained DLRM weights are not
+available, so every input is drawn here from a fixed seed with the shapes of
+the paper's workloads (Sec. 5.1, Sec. 5.4): dense features, embedding-table
+cardinalities, compressed tables, MLP weights and query indices.  FHE cost is
+data-oblivious, so only the shapes matter for time; the values matter for
+correctness checks only.
+
+This module holds no homomorphic arithmetic and imports nothing from the
+library or from the oracle; both the library's tests/bench and the oracle
+consume what it returns.  The one computation in it is the weight
+calibration: a plain FP64 forward pass used only to rescale each layer so its
+pre-activations have unit RMS over 256 seeded calibration queries (the x^2
+activation would otherwise overflow the CKKS message range).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+# --------------------------------------------------------------------------
+# CKKS parameter presets (bit sizes; the primes are derived by each side)
+# --------------------------------------------------------------------------
+PARAMS = {
+    # N = 2^13, three 50-bit primes + one 50-bit special prime, one prime per digit
+    "tiny": dict(log_n=13, q_bits=[50, 50, 50], n_p=1, p_bits=50, alpha=1, log2_scale=40.0),
+    # N = 2^16, 60-bit base prime + 20 x 40-bit, three 60-bit special primes
+    "full": dict(log_n=16, q_bits=[60] + [40] * 20, n_p=3, p_bits=60, alpha=3, log2_scale=40.0),
+}
+
+
+def reduced_params(log_n: int, n_levels: int) -> dict:
+    """The 'full' chain shape at a smaller ring degree and depth (tests)."""
+    return dict(log_n=log_n, q_bits=[60] + [40] * n_levels, n_p=3, p_bits=60, alpha=3,
+                log2_scale=40.0)
+
+
+# --------------------------------------------------------------------------
+# Model shapes
+# --------------------------------------------------------------------------
+@dataclass
+class DLRMSpec:
+    name: str
+    n_dense: int
+    bottom: list            # layer widths, [n_dense, ..., dim]
+    top: list               # layer widths, [top_in, ..., 1]
+    cards: list             # rows k_t of each embedding table
+    base: int               # digit base p
+    dim: int = 16
+    interaction: str = "dot"    # "dot" (pairwise) or "concat" (the paper's choice)
+
+
+def n_digits(k: int, p: int) -> int:
+    """Number of compressed tables for k rows in base p (k <= p keeps one plain table)."""
+    if k <= p:
+        return 1
+    ell, cap = 1, p
+    while cap < k:
+        cap *= p
+        ell += 1
+    return ell
+
+
+def table_rows(k: int, p: int) -> list:
+    return [k] if k <= p else [p] * n_digits(k, p)
+
+
+def top_input_width(spec: DLRMSpec) -> int:
+    b = len(spec.cards) + 1
+    if spec.interaction == "dot":
+        return spec.dim + b * (b - 1) // 2
+    return spec.dim * b
+
+
+def uci_spec(seed: int = 0, interaction: str = "dot") -> DLRMSpec:
+    """UCI-health-shaped: 10 dense features, 8 tables with 2..64 rows, dim 16,
+    bottom 10-32-16, top 52-32-1 (52 = 16 + C(9, 2) for the dot interaction)."""
+    rng = np.random.default_rng([seed, 101])
+    cards = [int(c) for c in rng.integers(2, 65, size=8)]
+    s = DLRMSpec("uci", 10, [10, 32, 16], [0, 32, 1], cards, 64, 16, interaction)
+    s.top[0] = top_input_width(s)
+    return s
+
+
+def uci_paper_spec() -> DLRMSpec:
+    """The paper's UCI shape: 5 dense features and tables of [2,4,2,3,2,3,4,3] rows."""
+    s = DLRMSpec("uci_paper", 5, [5, 16, 16], [0, 16, 1], [2, 4, 2, 3, 2, 3, 4, 3], 64, 16)
+    s.top[0] = top_input_width(s)
+    return s
+
+
+def criteo_cards(seed: int = 0, total: float = 33.8e6) -> list:
+    """26 log-uniform cardinalities on [3, 1e7]; every k > 1e5 is multiplied by
+    one common factor (clamped at 1e7), found by bisection, so the total is
+    33.8M rows within 0.5%.  (The real per-feature Criteo sizes are not used.)"""
+    rng = np.random.default_rng([seed, 202])
+    base = np.exp(rng.uniform(np.log(3.0), np.log(1e7), size=26))
+    big = base > 1e5
+
+    def tot(f):
+        k = np.where(big, np.minimum(base * f, 1e7), base)
+        return np.round(k).sum()
+
+    lo, hi = 1e-3, 1e3
+    for _ in range(200):
+        mid = np.sqrt(lo * hi)
+        if tot(mid) < total:
+            lo = mid
+        else:
+            hi = mid
+    k = np.where(big, np.minimum(base * hi, 1e7), base)
+    return [int(max(3, round(v))) for v in k]
+
+
+def criteo_spec(seed: int = 0, interaction: str = "dot") -> DLRMSpec:
+    """Criteo-shaped: 13 dense, 26 tables totalling ~33.8M rows, dim 16, base 64,
+    bottom 13-512-256-64-16, top 367-512-256-1 (367 = 16 + C(27, 2))."""
+    s = DLRMSpec("criteo", 13, [13, 512, 256, 64, 16], [0, 512, 256, 1], criteo_cards(seed), 64, 16,
+                 interaction)
+    s.top[0] = top_input_width(s)
+    return s
+
+
+def tiny_table(seed: int = 0):
+    """The 1024-row x dim-16 table compressed in base 32: C_0, C_1 in U[-0.05, 0.05]^(32x16)."""
+    rng = np.random.default_rng(seed)
+    return [rng.uniform(-0.05, 0.05, size=(32, 16)).astype(np.float32) for _ in range(2)]
+
+
+# --------------------------------------------------------------------------
+# Weights
+# --------------------------------------------------------------------------
+@dataclass
+class DLRMWeights:
+    bottom_W: list = field(default_factory=list)
+    bottom_b: list = field(default_factory=list)
+    top_W: list = field(default_factory=list)
+    top_b: list = field(default_factory=list)
+    tables: list = field(default_factory=list)      # tables[t][j]: rows x dim float32
+
+
+def _calib_forward_bottom(Ws, bs, x):
+    h = x
+    for W, b in zip(Ws, bs):
+        h = (h @ W.T + b) ** 2
+    return h
+
+
+def _calib_top_input(spec, h, embs):
+    blocks = [h] + embs
+    if spec.interaction == "dot":
+        cols = [h]
+        for a in range(len(blocks)):
+            for c in range(a + 1, len(blocks)):
+                cols.append(np.sum(blocks[a] * blocks[c], axis=1, keepdims=True))
+        return np.concatenate(cols, axis=1)
+    return np.concatenate(blocks, axis=1)
+
+
+def make_weights(spec: DLRMSpec, seed: int = 0) -> DLRMWeights:
+    """Weights and biases N(0, 0.1), tables U[-0.05, 0.05] (FP32), then each
+    layer's (W, b) is multiplied by one scalar so its pre-activation RMS over
+    256 calibration queries is 1."""
+    rng = np.random.default_rng([seed, 303])
+    w = DLRMWeights()
+    for a, b in zip(spec.bottom[:-1], spec.bottom[1:]):
+        w.bottom_W.append(rng.normal(0, 0.1, size=(b, a)))
+        w.bottom_b.append(rng.normal(0, 0.1, size=b))
+    for a, b in zip(spec.top[:-1], spec.top[1:]):
+        w.top_W.append(rng.normal(0, 0.1, size=(b, a)))
+        w.top_b.append(rng.normal(0, 0.1, size=b))
+    for k in spec.cards:
+        w.tables.append([rng.uniform(-0.05, 0.05, size=(r, spec.dim)).astype(np.float32)
+                         for r in table_rows(k, spec.base)])
+
+    dense, idx = make_queries(spec, 256, seed=10_000 + seed)
+    h = dense
+    for i in range(len(w.bottom_W)):
+        pre = h @ w.bottom_W[i].T + w.bottom_b[i]
+        c = 1.0 / np.sqrt(np.mean(pre ** 2))
+        w.bottom_W[i] *= c
+        w.bottom_b[i] *= c
+        h = (pre * c) ** 2
+    embs = []
+    for t, k in enumerate(spec.cards):
+        rows = table_rows(k, spec.base)
+        e = np.zeros((len(idx), spec.dim))
+        rem = idx[:, t].astype(np.int64)
+        for j, r in enumerate(rows):
+            e += w.tables[t][j][rem % r].astype(np.float64)
+            rem //= r
+        embs.append(e)
+    y = _calib_top_input(spec, h, embs)
+    for i in range(len(w.top_W)):
+        pre = y @ w.top_W[i].T + w.top_b[i]
+        c = 1.0 / np.sqrt(np.mean(pre ** 2))
+        w.top_W[i] *= c
+        w.top_b[i] *= c
+        y = pre * c
+        if i + 1 < len(w.top_W):
+            y = y ** 2
+    return w
+
+
+# --------------------------------------------------------------------------
+# Queries
+# --------------------------------------------------------------------------
+def _zipf_rank(rng, k: int, a: float = 1.1) -> int:
+    while True:
+        r = int(rng.zipf(a))
+        if r <= k:
+            return r
+
+
+def make_queries(spec: DLRMSpec, count: int, seed: int = 0):
+    """(dense [count, n_dense] float64, indices [count, T] uint64).
+
+    UCI-shaped dense features are N(0,1) with uniform indices; Criteo-shaped
+    dense features are LogNormal(0,1) with Zipf(1.1) ranks mapped to rows by a
+    seeded affine bijection r -> (a r + c) mod k, gcd(a, k) = 1."""
+    rng = np.random.default_rng([seed, 404])
+    T = len(spec.cards)
+    if spec.name.startswith("criteo"):
+        dense = rng.lognormal(0.0, 1.0, size=(count, spec.n_dense))
+        prm = np.random.default_rng([seed, 405])
+        idx = np.zeros((count, T), dtype=np.uint64)
+        for t, k in enumerate(spec.cards):
+            a = int(prm.integers(1, max(k, 2)))
+            while np.gcd(a, k) != 1:
+                a += 1
+            c = int(prm.integers(0, k))
+            for q in range(count):
+                r = _zipf_rank(rng, k) - 1
+                idx[q, t] = (a * r + c) % k
+    else:
+        dense = rng.normal(0.0, 1.0, size=(count, spec.n_dense))
+        idx = np.stack([rng.integers(0, k, size=count) for k in spec.cards], axis=1).astype(np.uint64)
+    return dense, idx

@@ -1,0 +1,166 @@
+"""Pins for the HE-LRM layer of the oracle: digit decomposition, selectors,
+block-diagonal packing, the BSGS matvec, the encrypted lookup, and the
+encrypted DLRM against the FP64 cleartext model."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import ckks, dlrm, linear
+from paper_2506_18150_gb300 import synthetic as syn
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_digit_decomposition_paper_example():
+    g = json.load(open(os.path.join(GOLDEN, "digit_example.json")))
+    assert dlrm.num_digits(g["k"], g["p"]) == g["ell"]
+    assert dlrm.digits(g["i"], g["p"], g["ell"]) == g["digits"]
+
+
+def test_digits_reconstruct_every_index():
+    for k, p in [(16, 4), (1024, 32), (10**7, 64), (65, 64), (64, 64)]:
+        ell = dlrm.num_digits(k, p)
+        assert p**ell >= k and (ell == 1 or p ** (ell - 1) < k)
+        for i in list(range(min(k, 300))) + [k - 1]:
+            d = dlrm.digits(i, p, ell)
+            assert all(0 <= x < p for x in d) and sum(x * p**j for j, x in enumerate(d)) == i
+
+
+def test_parameter_reduction_is_p_l_d():
+    """O(kd) -> O(p l d) parameters (Sec. 4.1.1)."""
+    k, p, d = 10**7, 64, 16
+    assert sum(syn.table_rows(k, p)) * d == p * dlrm.num_digits(k, p) * d == 4096
+
+
+def test_lookup_matrix_is_the_gather_for_all_1024_indices():
+    C = syn.tiny_table(0)
+    M = dlrm.lookup_matrix(C, 32, 1024)
+    assert M.shape == (16, 64)
+    for i in range(1024):
+        sel = dlrm.selector_vector([1024], 32, [i])
+        assert sel.sum() == 2 and sel[i % 32] == 1 and sel[32 + i // 32] == 1
+        want = C[0][i % 32].astype(np.float64) + C[1][i // 32].astype(np.float64)
+        assert np.allclose(M @ sel, want, atol=1e-12)
+
+
+def test_block_diagonal_packing_gives_contiguous_outputs():
+    spec = syn.uci_spec(0)
+    w = syn.make_weights(spec, 0)
+    _, idx = syn.make_queries(spec, 5, seed=1)
+    M = dlrm.embedding_matrix(spec.cards, spec.base, w.tables, 16, 16 * 9)
+    for q in range(5):
+        y = M @ dlrm.selector_vector(spec.cards, spec.base, idx[q])
+        embs = dlrm.embedding_cleartext(spec.cards, spec.base, w.tables, idx[q])
+        assert np.allclose(y[:16], 0) and np.allclose(y[16:], np.concatenate(embs))
+
+
+def test_uci_paper_packing_uses_28_slots():
+    s = syn.uci_paper_spec()
+    _, width = dlrm.selector_layout(s.cards, s.base)
+    assert s.n_dense + width == 28
+
+
+def test_selector_ciphertext_counts_and_compression_table():
+    t = json.load(open(os.path.join(GOLDEN, "compression_table.json")))
+    n = t["slots_per_ct"]
+    for row in t["rows"]:
+        if "cts" in row:
+            assert -(-row["slots"] // n) == row["cts"]
+        # CR x slots is the total row count of the uncompressed model (~33.8M)
+        assert abs(row["cr"] * row["slots"] / t["total_rows"] - 1) < 0.02
+    assert -(-int(t["total_rows"]) // n) == t["naive_cts"]
+
+
+def test_diagonal_count_for_416_outputs():
+    """26 tables x 16 = 416 outputs, padded to 512: 512 diagonals (Sec. 5.4)."""
+    lay = linear.Layout.make(in_pad=8192, out_pad=linear.pow2ceil(416))
+    assert lay.D == 512 and lay.n1 * lay.n2 == 512 and lay.folds == [4096, 2048, 1024, 512]
+    assert linear.Layout.make(in_pad=512, out_pad=512).D == 512
+
+
+def test_bsgs_split():
+    for D, n1, n2 in [(1, 1, 1), (2, 2, 1), (16, 4, 4), (32, 8, 4), (256, 16, 16), (512, 32, 16)]:
+        assert linear.bsgs_split(D) == (n1, n2)
+
+
+@pytest.mark.parametrize("shape", [(16, 64), (64, 16), (32, 32), (1, 32), (10, 3), (5, 7)])
+def test_bsgs_matvec_matches_cleartext(small_params, shape):
+    p = small_params
+    rng = np.random.default_rng(shape[0] * 100 + shape[1])
+    W = rng.normal(0, 0.3, shape)
+    x = rng.uniform(-1, 1, shape[1])
+    ip, op = linear.pow2ceil(shape[1]), linear.pow2ceil(shape[0])
+    pm = linear.prepare(p, W, ip, op, 3, p.delta, p.delta)
+    sk, keys = ckks.keygen(p, 55, rot_steps=linear.rotation_steps(pm), relin=False)
+    ct = ckks.encrypt(p, keys, ckks.encode_real(p, dlrm.replicate(x, ip, p.n), p.delta), 3, p.delta, 6)
+    out = linear.matvec(p, keys, pm, ct)
+    assert out.level == 2                                    # one level consumed
+    got = ckks.decrypt(p, sk, out)
+    assert np.max(np.abs(got - linear.matvec_cleartext(W, x, ip, op, p.n))) < 1e-5
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    pr = syn.PARAMS["tiny"]
+    p = ckks.Params(pr["log_n"], pr["q_bits"], pr["n_p"], pr["p_bits"], pr["alpha"], pr["log2_scale"])
+    C = syn.tiny_table(0)
+    M = dlrm.lookup_matrix(C, 32, 1024)
+    pm = linear.prepare(p, M, 64, 16, 1, p.delta, p.delta)
+    pm_d = [linear.prepare(p, M[:, 32 * j: 32 * j + 32], 32, 16, 1, p.delta, p.delta) for j in range(2)]
+    steps = sorted(set(linear.rotation_steps(pm)) | set(linear.rotation_steps(pm_d[0])))
+    sk, keys = ckks.keygen(p, 0, rot_steps=steps, relin=False)
+    return p, C, M, pm, pm_d, sk, keys
+
+
+def test_tiny_lookup_packed_and_separate(tiny):
+    """Config 'tiny': 1024 x 16 table in base 32; (a) both digit selectors in one
+    ciphertext (64 slots), (b) each selector its own ciphertext (sum of two
+    matvecs).  Decrypted row vs the cleartext gather, max-abs <= 1e-3."""
+    p, C, M, pm, pm_d, sk, keys = tiny
+    rng = np.random.default_rng(0)
+    for i in rng.integers(0, 1024, 3):
+        want = C[0][i % 32].astype(np.float64) + C[1][i // 32].astype(np.float64)
+        sel = dlrm.selector_vector([1024], 32, [i])
+        ct = ckks.encrypt(p, keys, ckks.encode_real(p, dlrm.replicate(sel, 64, p.n), p.delta), 1, p.delta, int(i))
+        out = linear.matvec(p, keys, pm, ct)
+        assert out.level == 0
+        got = ckks.decrypt(p, sk, out)
+        assert np.max(np.abs(got[:16] - want)) < 1e-3
+        assert np.max(np.abs(got - np.tile(want, p.n // 16))) < 1e-3
+        parts = []
+        for j in range(2):
+            s = dlrm.replicate(sel[32 * j: 32 * j + 32], 32, p.n)
+            c = ckks.encrypt(p, keys, ckks.encode_real(p, s, p.delta), 1, p.delta, int(i) + 7 * j)
+            parts.append(linear.matvec(p, keys, pm_d[j], c))
+        got2 = ckks.decrypt(p, sk, ckks.add(p, parts[0], parts[1]))
+        assert np.max(np.abs(got2[:16] - want)) < 1e-3
+
+
+@pytest.mark.parametrize("interaction", ["dot", "concat"])
+def test_encrypted_uci_dlrm_matches_cleartext(interaction):
+    spec = syn.uci_spec(0, interaction)
+    w = syn.make_weights(spec, 0)
+    pr = syn.reduced_params(13, 9)
+    p = ckks.Params(pr["log_n"], pr["q_bits"], pr["n_p"], pr["p_bits"], pr["alpha"], pr["log2_scale"])
+    c = dlrm.compile_model(p, spec, w)
+    assert (c.lvl_dense, c.lvl_sel) == ((9, 6) if interaction == "dot" else (7, 4))
+    sk, keys = ckks.keygen(p, 1, rot_steps=c.rotation_steps())
+    dense, idx = syn.make_queries(spec, 1, seed=5)
+    cd, cs = dlrm.encrypt_query(p, keys, c, dense[0], idx[0], 100)
+    out = dlrm.infer(p, keys, c, cd, cs)
+    assert out.level == 0
+    logit, prob = dlrm.decrypt_logit(p, sk, out)
+    ref, ref_prob, _ = dlrm.dlrm_cleartext(spec, w, dense[0], idx[0])
+    assert abs(logit - ref) < 1e-3 and abs(prob - ref_prob) < 1e-3
+
+
+def test_criteo_shape():
+    spec = syn.criteo_spec(0)
+    assert len(spec.cards) == 26 and abs(sum(spec.cards) / 33.8e6 - 1) < 0.005
+    assert min(spec.cards) >= 3 and max(spec.cards) <= 10**7
+    assert spec.top[0] == 16 + 27 * 26 // 2 == 367
+    _, width = dlrm.selector_layout(spec.cards, spec.base)
+    assert 2048 < width <= 8192
+    assert syn.uci_spec(0).top[0] == 52

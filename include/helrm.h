@@ -1,0 +1,309 @@
+/*
+ * helrm.h -- C ABI of the GB300 (sm_103a) encrypted-DLRM library.
+ *
+ * HE-LRM (Garimella, Ebel, De Micheli, Reagen; arXiv 2506.18150) evaluates a
+ * DLRM on CKKS-encrypted inputs: the client digit-decomposes each categorical
+ * index, one-hot encodes the digits, packs every table's selectors into one
+ * vector and encrypts it (Sec. 4.1, Sec. 4.2.2); the server runs the bottom MLP,
+ * the block-diagonally packed embedding lookup y = E^T s and the top MLP, each
+ * a plaintext-matrix x ciphertext-vector product evaluated with the
+ * double-hoisted baby-step giant-step method (Sec. 2.1.4, Sec. 3.2.1), and
+ * returns an encrypted logit (Sec. 5.3).  The CKKS operations are those of the
+ * paper's appendix "CKKS operations".
+ *
+ * Conventions for every call:
+ *  - The return value is a helrm_status.  On error the outputs are left
+ *    untouched, *out handles are set to NULL, nothing aborts, and the message
+ *    is available from helrm_last_error(ctx).
+ *  - Handles are opaque and owned by the library; release them with
+ *    helrm_free().  Host arrays passed in are read during the call (copied as
+ *    needed) and stay owned by the caller.  Pointers named d_* are device
+ *    pointers; every other pointer is a host pointer.
+ *  - All GPU work is ordered on the context's CUDA stream (the one given to
+ *    helrm_ctx_create, e.g. a PyTorch stream).  Calls that return host data
+ *    synchronise that stream before returning; the others return once the work
+ *    is enqueued.
+ *  - Polynomials are stored on the device in RNS form, limb-major
+ *    [limb][coefficient], u64 residues in [0, q), in the NTT (evaluation)
+ *    domain.  Export/import use the coefficient domain.
+ *  - One context per host thread; a context is not thread-safe.
+ *
+ * Readings of points the paper leaves open (prime choice, noise
+ * distributions, PRNG, key-switching gadget, rounding of ModDown and rescale,
+ * slot order, layouts and level schedule) are fixed so that the library and
+ * an independent CPU oracle compute bit-identical ciphertexts from the same
+ * seeds and the same integer plaintexts.  They are listed in the project's
+ * design notes.
+ */
+#ifndef HELRM_H
+#define HELRM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HELRM_OK = 0,
+    HELRM_E_INVAL = -1,   /* bad argument, size, handle or corrupted input */
+    HELRM_E_PARAM = -2,   /* unsupported parameter set */
+    HELRM_E_LEVEL = -3,   /* operand level mismatch or no level left */
+    HELRM_E_SCALE = -4,   /* operand scale mismatch */
+    HELRM_E_NOKEY = -5,   /* missing rotation / relinearisation key */
+    HELRM_E_NOMEM = -6,   /* device allocation failed or memory cap reached */
+    HELRM_E_CUDA = -7,    /* CUDA runtime error */
+    HELRM_E_TIMEOUT = -8  /* a bounded device-side wait ran out */
+} helrm_status;
+
+/*
+ * CKKS parameters (appendix "CKKS operations": R = Z[X]/(X^N+1), Q = prod q_i).
+ *   log_n      N = 2^log_n, 10 <= log_n <= 16; slots n = N/2.
+ *   n_q        L+1 ciphertext primes, 1..32;  q_bits[i] their bit sizes (30..61).
+ *   n_p        K special primes for key switching, 1..8, each of p_bits (30..61).
+ *   alpha      primes per key-switching digit (1..8); dnum = ceil((L+1)/alpha).
+ *   log2_scale default scale Delta = 2^log2_scale.
+ * Primes: q = 1 mod 2N, for each requested size the largest unused one below
+ * 2^bits, q_0..q_L in order, then the special primes.
+ */
+typedef struct {
+    uint32_t log_n;
+    uint32_t n_q;
+    const uint32_t *q_bits;
+    uint32_t n_p;
+    uint32_t p_bits;
+    uint32_t alpha;
+    double log2_scale;
+} helrm_params;
+
+typedef struct helrm_ctx helrm_ctx;
+typedef struct helrm_sk helrm_sk;       /* secret key (device) */
+typedef struct helrm_evk helrm_evk;     /* public, relinearisation and rotation keys (device) */
+typedef struct helrm_pt helrm_pt;       /* plaintext polynomial (device) */
+typedef struct helrm_ct helrm_ct;       /* ciphertext (device) */
+typedef struct helrm_ptmat helrm_ptmat; /* encoded BSGS diagonals of one matrix (device) */
+typedef struct helrm_emb helrm_emb;     /* packed embedding tables (device) */
+typedef struct helrm_model helrm_model; /* compiled DLRM (device) */
+
+/* ------------------------------------------------------------------ context */
+/* Create a context on `cuda_device`, ordering work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  Derives the primes and
+ * uploads the NTT and base-conversion tables.  Errors: HELRM_E_PARAM. */
+helrm_status helrm_ctx_create(const helrm_params *params, int cuda_device, void *cuda_stream,
+                              helrm_ctx **out);
+/* primes_out: L+1+K values, q_0..q_L then p_0..p_{K-1}.  psi_out (optional,
+ * may be NULL): the primitive 2N-th root used by the NTT for each prime
+ * (psi = g^((q-1)/2N), g the smallest quadratic non-residue). */
+helrm_status helrm_ctx_primes(const helrm_ctx *ctx, uint64_t *primes_out, uint64_t *psi_out);
+/* dims_out[0..5] = N, n (slots), L, K, alpha, dnum at level L. */
+helrm_status helrm_ctx_dims(const helrm_ctx *ctx, uint32_t *dims_out);
+/* Cap the bytes of device memory the context may hold; 0 = no cap.  An
+ * allocation past the cap fails with HELRM_E_NOMEM (admission control). */
+helrm_status helrm_ctx_set_memory_cap(helrm_ctx *ctx, uint64_t bytes);
+/* Bytes currently held by the context's handles and scratch. */
+helrm_status helrm_ctx_memory_in_use(const helrm_ctx *ctx, uint64_t *bytes);
+/* Wait for all work enqueued on the context's stream. */
+helrm_status helrm_ctx_synchronize(helrm_ctx *ctx);
+/* Number of library kernels launched so far on this context. */
+helrm_status helrm_ctx_launch_count(const helrm_ctx *ctx, uint64_t *count);
+
+/* ------------------------------------------------------------- raw NTT (a2) */
+/* In-place negacyclic NTT of n_limbs contiguous limbs of N u64 at d_data;
+ * limb l uses prime index first_prime + l (0..L+K, QP order).  Forward: input
+ * in [0,q) coefficient order, output ahat[i] = a(psi^(2 brv(i) + 1))
+ * (bit-reversed evaluation order); inverse undoes it, including the 1/N.
+ * The buffer is owned by the caller. */
+helrm_status helrm_ntt(helrm_ctx *ctx, uint64_t *d_data, uint32_t n_limbs, uint32_t first_prime,
+                       int inverse);
+
+/* ---------------------------------------------------------------- keys (a1) */
+/* Key generation from a 64-bit seed (ChaCha20 streams, as for the oracle):
+ * ternary secret s, public key (-a s + e, a), the relinearisation key (s^2)
+ * and one rotation key per step in rot_steps (slot shifts, negative = right;
+ * duplicates and 0 ignored).  Keys are generated over the full QP basis and
+ * stay resident on the device. */
+helrm_status helrm_keygen(helrm_ctx *ctx, uint64_t seed, const int32_t *rot_steps, uint32_t n_rot,
+                          helrm_sk **sk_out, helrm_evk **evk_out);
+/* Add rotation keys for more steps to an existing key set. */
+helrm_status helrm_evk_add_rotations(helrm_ctx *ctx, const helrm_sk *sk, helrm_evk *evk,
+                                     const int32_t *rot_steps, uint32_t n_rot);
+/* Total device bytes of the evaluation keys. */
+helrm_status helrm_evk_bytes(const helrm_evk *evk, uint64_t *bytes);
+
+/* --------------------------------------------------------- plaintexts (a1) */
+/* m = round(scale * sigma^-1(z)) for n_slots real slots z (rest zero), at
+ * `level` (limbs q_0..q_level).  slot j is the evaluation at zeta^(5^j). */
+helrm_status helrm_encode(helrm_ctx *ctx, const double *slots, uint32_t n_slots, int32_t level,
+                          double scale, helrm_pt **out);
+/* Plaintext from N signed integer coefficients (|c| < 2^62). */
+helrm_status helrm_pt_import(helrm_ctx *ctx, const int64_t *coeffs, int32_t level, double scale,
+                             helrm_pt **out);
+/* Signed coefficients of a plaintext (centred mod q_0; exact when |c| < q_0/2). */
+helrm_status helrm_pt_export(helrm_ctx *ctx, const helrm_pt *pt, int64_t *coeffs_out);
+
+/* ------------------------------------------------------- ciphertexts (a1, a14) */
+/* (v*pk_b + e0 + m, v*pk_a + e1) at the plaintext's level; v ternary, e0 and
+ * e1 centred binomial, all drawn from `seed`. */
+helrm_status helrm_encrypt(helrm_ctx *ctx, const helrm_evk *evk, const helrm_pt *pt, uint64_t seed,
+                           helrm_ct **out);
+/* Decrypt (m = c0 + c1 s on q_0, centred; requires |m| < q_0/2) and decode
+ * the first n_slots slots into slots_out. */
+helrm_status helrm_decrypt(helrm_ctx *ctx, const helrm_sk *sk, const helrm_ct *ct, double *slots_out,
+                           uint32_t n_slots);
+/* Coefficient-domain export: coeffs_out holds 2 x (level+1) x N u64 (c0 limbs
+ * then c1 limbs, canonical residues); level/scale optional (may be NULL). */
+helrm_status helrm_ct_export(helrm_ctx *ctx, const helrm_ct *ct, uint64_t *coeffs_out, int32_t *level,
+                             double *scale);
+/* Import the same layout.  A residue >= its prime gives HELRM_E_INVAL. */
+helrm_status helrm_ct_import(helrm_ctx *ctx, const uint64_t *coeffs, int32_t level, double scale,
+                             helrm_ct **out);
+helrm_status helrm_ct_info(const helrm_ct *ct, int32_t *level, double *scale);
+
+/* ----------------------------------------------------- ciphertext ops (a2-a10) */
+helrm_status helrm_add(helrm_ctx *ctx, const helrm_ct *a, const helrm_ct *b, helrm_ct **out);
+helrm_status helrm_sub(helrm_ctx *ctx, const helrm_ct *a, const helrm_ct *b, helrm_ct **out);
+helrm_status helrm_add_pt(helrm_ctx *ctx, const helrm_ct *a, const helrm_pt *pt, helrm_ct **out);
+/* Slot-wise product with a plaintext; the scale becomes scale_a * scale_pt
+ * (no rescale). */
+helrm_status helrm_mul_pt(helrm_ctx *ctx, const helrm_ct *a, const helrm_pt *pt, helrm_ct **out);
+/* ct x ct: tensor, relinearise with the s^2 key, rescale (appendix:
+ * "Multiplication ... followed by a rescaling procedure"). */
+helrm_status helrm_mul(helrm_ctx *ctx, const helrm_evk *evk, const helrm_ct *a, const helrm_ct *b,
+                       helrm_ct **out);
+/* Drop q_level: out = round(x / q_level) (centred remainder). */
+helrm_status helrm_rescale(helrm_ctx *ctx, const helrm_ct *a, helrm_ct **out);
+/* Keep limbs q_0..q_level (level <= current). */
+helrm_status helrm_drop_level(helrm_ctx *ctx, const helrm_ct *a, int32_t level, helrm_ct **out);
+/* Cyclic left shift of the slots by `step` (appendix "Rotation"):
+ * X -> X^(5^step mod 2N) then hybrid key switching (ModUp, key inner
+ * product, ModDown).  HELRM_E_NOKEY if the key is missing. */
+helrm_status helrm_rotate(helrm_ctx *ctx, const helrm_evk *evk, const helrm_ct *a, int32_t step,
+                          helrm_ct **out);
+/* n rotations of one ciphertext sharing one ModUp (hoisting); outs[i] for steps[i]. */
+helrm_status helrm_rotate_hoisted(helrm_ctx *ctx, const helrm_evk *evk, const helrm_ct *a,
+                                  const int32_t *steps, uint32_t n, helrm_ct **outs);
+
+/* ------------------------------------------------------------ matvec (a3-a8) */
+/* Encode the BSGS diagonals of the rows x cols row-major FP64 matrix W, padded
+ * to out_pad x in_pad (powers of two, <= n): D = min(in_pad, out_pad) extended
+ * diagonals diag_i[j] = W[j mod out_pad, (j+i) mod in_pad], split i = g n1 + b
+ * (n1 = smallest power of two with n1^2 >= D), pre-rotated by -g n1 and
+ * encoded over the QP basis at `level` with scale q_level * target_scale /
+ * ct_scale.  All-zero diagonals are skipped. */
+helrm_status helrm_ptmat_prepare(helrm_ctx *ctx, const double *W, uint32_t rows, uint32_t cols,
+                                 uint32_t in_pad, uint32_t out_pad, int32_t level, double ct_scale,
+                                 double target_scale, helrm_ptmat **out);
+/* info_out[0..5] = D, n1, n2, number of non-zero diagonals, number of folds, level. */
+helrm_status helrm_ptmat_info(const helrm_ptmat *m, uint32_t *info_out);
+/* Rotation steps the matvec needs; steps_out may be NULL to query the count. */
+helrm_status helrm_ptmat_rotations(const helrm_ptmat *m, int32_t *steps_out, uint32_t *n_out);
+/* Replace the encoded diagonals by `count` plaintexts of N signed
+ * coefficients each, in (g, b) order of the non-zero diagonals. */
+helrm_status helrm_ptmat_import(helrm_ctx *ctx, helrm_ptmat *m, const int64_t *coeffs, uint32_t count);
+/* y = W x: double-hoisted BSGS (one ModUp of c1 shared by the baby steps, the
+ * diagonal products accumulated over QP, giant steps rotated in QP, one final
+ * ModDown), rescale, then the rotate-and-add folds for wide matrices.  The
+ * output is W x replicated with period out_pad, one level lower, at
+ * target_scale.  n_in must be 1. */
+helrm_status helrm_ptct_matvec(helrm_ctx *ctx, const helrm_evk *evk, const helrm_ptmat *m,
+                               const helrm_ct *in, uint32_t n_in, helrm_ct **out);
+
+/* ------------------------------------------------------- embeddings (a11) */
+/* Pack n_tables compressed tables block-diagonally (Sec. 4.2.2): table t with
+ * card[t] rows keeps one plain table if card[t] <= base_p, else
+ * l_t = ceil(log_p card[t]) digit tables of base_p rows; tables[t] points to
+ * its digit tables stacked (sum of rows) x dim, FP32 row-major.  Output rows
+ * of table t are [out_offset + dim t, out_offset + dim (t+1)) of a vector of
+ * period out_pad; the selector vector (all digits' one-hots concatenated,
+ * table by table) has period in_pad = next power of two.  Prepared at
+ * `level` for the given scales. */
+helrm_status helrm_emb_prepare(helrm_ctx *ctx, uint32_t n_tables, const uint64_t *card, uint32_t base_p,
+                               uint32_t dim, const float *const *tables, uint32_t out_offset,
+                               uint32_t out_pad, int32_t level, double ct_scale, double target_scale,
+                               helrm_emb **out);
+/* Client packing: little-endian base-p digits of each index, one one-hot per
+ * digit, concatenated; slots_out gets n_slots values (selector replicated with
+ * its period). */
+helrm_status helrm_query_pack(const helrm_emb *emb, const uint64_t *indices, double *slots_out,
+                              uint32_t n_slots);
+/* Selector width (before padding) and its period. */
+helrm_status helrm_emb_info(const helrm_emb *emb, uint32_t *width, uint32_t *period);
+/* y = M^T sel for the packed selector ciphertext (n_sel must be 1). */
+helrm_status helrm_embedding_lookup(helrm_ctx *ctx, const helrm_evk *evk, const helrm_emb *emb,
+                                    const helrm_ct *sel, uint32_t n_sel, helrm_ct **out);
+
+/* ------------------------------------------------------------- DLRM (a12-a14) */
+typedef struct {
+    uint32_t n_dense;
+    uint32_t n_bottom;               /* bottom layers; widths[0] = n_dense, last = dim */
+    const uint32_t *bottom_widths;   /* n_bottom + 1 */
+    const double *const *bottom_W;   /* [layer] -> out x in row-major */
+    const double *const *bottom_b;   /* [layer] -> out */
+    uint32_t n_top;                  /* top layers; last width 1 */
+    const uint32_t *top_widths;      /* n_top + 1; widths[0] = dim + pairs (dot) or dim (T+1) (concat) */
+    const double *const *top_W;
+    const double *const *top_b;
+    uint32_t n_tables;
+    const uint64_t *cards;
+    uint32_t base_p;
+    uint32_t dim;                    /* must be 16 */
+    const float *const *tables;      /* as for helrm_emb_prepare */
+    int32_t interaction;             /* 0 = pairwise dot, 1 = concatenation */
+} helrm_model_desc;
+
+/* Compile the model: layouts, as-late-as-possible levels (the logit ends at
+ * level 0), all diagonals, biases and masks encoded on the device.
+ * Errors: HELRM_E_PARAM if the chain is too short or a layout exceeds n. */
+helrm_status helrm_model_create(helrm_ctx *ctx, const helrm_model_desc *desc, helrm_model **out);
+/* info_out[0..8] = level of ct_dense, level of ct_sel, level of z, level of
+ * the top input, dense period, selector period, W_z, W_u, plaintext count. */
+helrm_status helrm_model_info(const helrm_model *m, uint32_t *info_out);
+helrm_status helrm_model_rotations(const helrm_model *m, int32_t *steps_out, uint32_t *n_out);
+/* Replace / read all encoded plaintexts (count x N signed coefficients) in
+ * the canonical order: per bottom layer its diagonals then its bias; the
+ * embedding diagonals; (dot) the ones block and masks 0..S; per top layer its
+ * diagonals then its bias. */
+helrm_status helrm_model_import_plaintexts(helrm_ctx *ctx, helrm_model *m, const int64_t *coeffs,
+                                           uint32_t count);
+helrm_status helrm_model_export_plaintexts(helrm_ctx *ctx, const helrm_model *m, int64_t *coeffs,
+                                           uint32_t count);
+/* Client side (a1): pack, encode and encrypt one query: ct_dense with `seed`
+ * at its level, ct_sel with seed + 1.  dense: n_dense values; indices: one
+ * per table. */
+helrm_status helrm_encrypt_query(helrm_ctx *ctx, const helrm_evk *evk, const helrm_model *m,
+                                 const double *dense, const uint64_t *indices, uint64_t seed,
+                                 helrm_ct **ct_dense, helrm_ct **ct_sel);
+/* Server side (a2-a13): the encrypted logit (slot 0, level 0). */
+helrm_status helrm_infer(helrm_ctx *ctx, const helrm_evk *evk, const helrm_model *m,
+                         const helrm_ct *ct_dense, const helrm_ct *ct_sel, helrm_ct **logit);
+/* Client side (a14): decrypt slot 0 and apply the sigmoid. */
+helrm_status helrm_decrypt_logit(helrm_ctx *ctx, const helrm_sk *sk, const helrm_ct *logit,
+                                 double *logit_out, double *prob_out);
+/* The whole protocol for n_queries queries from host buffers: pack, encode,
+ * encrypt, infer, decrypt.  dense: n_queries x n_dense; indices: n_queries x
+ * n_tables; logits_out / probs_out: n_queries (probs_out may be NULL).
+ * Query q uses seed + 2q. */
+helrm_status helrm_infer_e2e(helrm_ctx *ctx, const helrm_sk *sk, const helrm_evk *evk,
+                             const helrm_model *m, const double *dense, const uint64_t *indices,
+                             uint32_t n_queries, uint64_t seed, double *logits_out, double *probs_out);
+
+/* The same protocol with every buffer on the device (d_dense: n_queries x
+ * n_dense FP64, d_indices: n_queries x n_tables u64, d_logits / d_probs:
+ * n_queries FP64, d_probs may be NULL).  Nothing is copied to or from the
+ * host and the call does not synchronise.  An index outside its table sets no
+ * selector slot for that table (its embedding decrypts to zero); indices are
+ * not range-checked on the host. */
+helrm_status helrm_infer_e2e_device(helrm_ctx *ctx, const helrm_sk *sk, const helrm_evk *evk,
+                                    const helrm_model *m, const double *d_dense, const uint64_t *d_indices,
+                                    uint32_t n_queries, uint64_t seed, double *d_logits, double *d_probs);
+
+/* --------------------------------------------------------------- misc */
+/* Release any handle (context last; handles must not outlive their context). */
+void helrm_free(void *handle);
+const char *helrm_last_error(const helrm_ctx *ctx);
+const char *helrm_status_string(helrm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HELRM_H */

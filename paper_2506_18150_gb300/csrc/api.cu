@@ -1,0 +1,624 @@
+// api.cu -- extern "C" entry points declared in include/helrm.h.
+//
+// Every entry point validates its handles, converts C++ errors and CUDA
+// errors into a helrm_status, records the message on the context, and leaves
+// its outputs untouched (out handles NULL) on failure.
+#include <cstring>
+#include <new>
+
+#include "core.cuh"
+
+namespace helrm {
+Ctx *ctx_create(const helrm_params *p, int device, void *stream);
+struct Emb;
+struct Model;
+Emb *emb_prepare(Ctx *c, const std::vector<u64> &cards, int base, int dim, const float *const *tables,
+                 int out_offset, int out_pad, int level, double ct_scale, double target_scale);
+void emb_pack_host(const Emb *e, const u64 *indices, std::vector<double> &sel);
+const PtMatrix *emb_matrix_of(const Emb *e);
+void emb_info(const Emb *e, u32 *width, u32 *period);
+Ctx *emb_ctx(const Emb *e);
+Model *model_create(Ctx *c, const helrm_model_desc *d);
+void model_import(Ctx *c, Model *m, const i64 *coeffs, u32 count);
+void model_export(Ctx *c, Model *m, i64 *coeffs, u32 count);
+Ciphertext *model_infer(Ctx *c, const EvalKey *evk, const Model *m, const Ciphertext *ct_dense,
+                        const Ciphertext *ct_sel);
+void model_encrypt_query(Ctx *c, const EvalKey *evk, const Model *m, const double *dense, const u64 *indices,
+                         u64 seed, Ciphertext **ct_dense, Ciphertext **ct_sel, bool on_device);
+void model_info(const Model *m, u32 *o);
+std::vector<int> model_rotations(const Model *m);
+Ctx *model_ctx(const Model *m);
+u32 model_n_dense(const Model *m);
+u32 model_n_tables(const Model *m);
+}  // namespace helrm
+
+using namespace helrm;
+
+namespace {
+
+template <class T>
+T *as(const void *h, u32 kind, const char *what)
+{
+    HCHECK(h, HELRM_E_INVAL, std::string(what) + " is NULL");
+    const Handle *hh = (const Handle *)h;
+    HCHECK(hh->kind == kind, HELRM_E_INVAL, std::string(what) + " is not a valid handle of its type");
+    return (T *)h;
+}
+Ctx *C(const helrm_ctx *c) { return as<Ctx>(c, KIND_CTX, "ctx"); }
+const SecretKey *SK(const helrm_sk *s) { return as<SecretKey>(s, KIND_SK, "secret key"); }
+EvalKey *EVK(const helrm_evk *e) { return as<EvalKey>(e, KIND_EVK, "evaluation key"); }
+Plaintext *PT(const helrm_pt *p) { return as<Plaintext>(p, KIND_PT, "plaintext"); }
+Ciphertext *CT(const helrm_ct *p) { return as<Ciphertext>(p, KIND_CT, "ciphertext"); }
+PtMatrix *PM(const helrm_ptmat *p) { return as<PtMatrix>(p, KIND_PTMAT, "ptmat"); }
+Emb *EMB(const helrm_emb *p) { return as<Emb>(p, KIND_EMB, "embedding"); }
+Model *MOD(const helrm_model *p) { return as<Model>(p, KIND_MODEL, "model"); }
+
+Ctx *ctx_or_null(const void *h)
+{
+    if (!h) return nullptr;
+    const Handle *hh = (const Handle *)h;
+    return hh->kind == KIND_CTX ? (Ctx *)h : nullptr;
+}
+
+template <class F>
+helrm_status guard(Ctx *ctx, F &&f)
+{
+    try {
+        f();
+        return HELRM_OK;
+    } catch (const Error &e) {
+        if (ctx) ctx->last_error = e.msg;
+        if (e.code == HELRM_E_CUDA || e.code == HELRM_E_NOMEM) cudaGetLastError();
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        if (ctx) ctx->last_error = "host allocation failed";
+        return HELRM_E_NOMEM;
+    } catch (const std::exception &e) {
+        if (ctx) ctx->last_error = e.what();
+        return HELRM_E_INVAL;
+    } catch (...) {
+        if (ctx) ctx->last_error = "unknown error";
+        return HELRM_E_INVAL;
+    }
+}
+
+template <class T>
+void set_out(T **out, T *v)
+{
+    *out = v;
+}
+
+}  // namespace
+
+extern "C" {
+
+// ------------------------------------------------------------------ context
+helrm_status helrm_ctx_create(const helrm_params *params, int cuda_device, void *cuda_stream, helrm_ctx **out)
+{
+    if (out) *out = nullptr;
+    return guard(nullptr, [&] {
+        HCHECK(out, HELRM_E_INVAL, "out is NULL");
+        *out = (helrm_ctx *)ctx_create(params, cuda_device, cuda_stream);
+    });
+}
+
+helrm_status helrm_ctx_primes(const helrm_ctx *ctx, uint64_t *primes_out, uint64_t *psi_out)
+{
+    Ctx *c = ctx_or_null(ctx);
+    return guard(c, [&] {
+        Ctx *cc = C(ctx);
+        HCHECK(primes_out, HELRM_E_INVAL, "primes_out is NULL");
+        std::memcpy(primes_out, cc->primes.data(), cc->primes.size() * 8);
+        if (psi_out) std::memcpy(psi_out, cc->psi.data(), cc->psi.size() * 8);
+    });
+}
+
+helrm_status helrm_ctx_dims(const helrm_ctx *ctx, uint32_t *d)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        HCHECK(d, HELRM_E_INVAL, "dims_out is NULL");
+        d[0] = c->N;
+        d[1] = c->n_slots;
+        d[2] = c->L;
+        d[3] = c->K;
+        d[4] = c->alpha;
+        d[5] = c->dnum(c->L);
+    });
+}
+
+helrm_status helrm_ctx_set_memory_cap(helrm_ctx *ctx, uint64_t bytes)
+{
+    return guard(ctx_or_null(ctx), [&] { C(ctx)->mem_cap = bytes; });
+}
+
+helrm_status helrm_ctx_memory_in_use(const helrm_ctx *ctx, uint64_t *bytes)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        HCHECK(bytes, HELRM_E_INVAL, "bytes is NULL");
+        *bytes = C(ctx)->mem_in_use;
+    });
+}
+
+helrm_status helrm_ctx_synchronize(helrm_ctx *ctx)
+{
+    return guard(ctx_or_null(ctx), [&] { CUDA_CHECK(cudaStreamSynchronize(C(ctx)->stream)); });
+}
+
+helrm_status helrm_ctx_launch_count(const helrm_ctx *ctx, uint64_t *count)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        HCHECK(count, HELRM_E_INVAL, "count is NULL");
+        *count = C(ctx)->launches;
+    });
+}
+
+helrm_status helrm_ntt(helrm_ctx *ctx, uint64_t *d_data, uint32_t n_limbs, uint32_t first_prime, int inverse)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        HCHECK(d_data || n_limbs == 0, HELRM_E_INVAL, "d_data is NULL");
+        HCHECK((int)first_prime + (int)n_limbs <= c->nP(), HELRM_E_INVAL, "prime index out of range");
+        LimbMap m{(int)first_prime, 1 << 30, c->L + 1, 0};
+        if (inverse)
+            k::ntt_inv(c, d_data, (int)n_limbs, m);
+        else
+            k::ntt_fwd(c, d_data, (int)n_limbs, m);
+    });
+}
+
+// ------------------------------------------------------------------ keys
+helrm_status helrm_keygen(helrm_ctx *ctx, uint64_t seed, const int32_t *rot_steps, uint32_t n_rot,
+                          helrm_sk **sk_out, helrm_evk **evk_out)
+{
+    if (sk_out) *sk_out = nullptr;
+    if (evk_out) *evk_out = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        HCHECK(sk_out && evk_out, HELRM_E_INVAL, "output pointers are NULL");
+        HCHECK(rot_steps || n_rot == 0, HELRM_E_INVAL, "rot_steps is NULL");
+        std::unique_ptr<SecretKey> sk(keygen_sk(c, seed));
+        std::unique_ptr<EvalKey> evk(keygen_evk(c, sk.get(), seed));
+        keygen_rot(c, sk.get(), evk.get(), std::vector<int>(rot_steps, rot_steps + n_rot));
+        CUDA_CHECK(cudaStreamSynchronize(c->stream));
+        *sk_out = (helrm_sk *)sk.release();
+        *evk_out = (helrm_evk *)evk.release();
+    });
+}
+
+helrm_status helrm_evk_add_rotations(helrm_ctx *ctx, const helrm_sk *sk, helrm_evk *evk, const int32_t *rot_steps,
+                                     uint32_t n_rot)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        HCHECK(rot_steps || n_rot == 0, HELRM_E_INVAL, "rot_steps is NULL");
+        keygen_rot(c, SK(sk), EVK(evk), std::vector<int>(rot_steps, rot_steps + n_rot));
+        CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    });
+}
+
+helrm_status helrm_evk_bytes(const helrm_evk *evk, uint64_t *bytes)
+{
+    return guard(nullptr, [&] {
+        EvalKey *e = EVK(evk);
+        HCHECK(bytes, HELRM_E_INVAL, "bytes is NULL");
+        u64 b = e->pk.bytes + (e->relin ? e->relin->data.bytes : 0);
+        for (auto &kv : e->rot) b += kv.second->data.bytes;
+        *bytes = b;
+    });
+}
+
+// ------------------------------------------------------------------ plaintexts
+helrm_status helrm_encode(helrm_ctx *ctx, const double *slots, uint32_t n_slots, int32_t level, double scale,
+                          helrm_pt **out)
+{
+    if (out) *out = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        HCHECK(out && (slots || n_slots == 0), HELRM_E_INVAL, "NULL argument");
+        HCHECK(n_slots <= (u32)c->n_slots, HELRM_E_INVAL, "more values than slots");
+        *out = (helrm_pt *)pt_encode(c, slots, (int)n_slots, c->n_slots, level, false, scale, PT_PLAIN);
+    });
+}
+
+helrm_status helrm_pt_import(helrm_ctx *ctx, const int64_t *coeffs, int32_t level, double scale, helrm_pt **out)
+{
+    if (out) *out = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        HCHECK(out && coeffs, HELRM_E_INVAL, "NULL argument");
+        *out = (helrm_pt *)pt_from_signed(c, coeffs, level, false, scale, PT_PLAIN);
+    });
+}
+
+helrm_status helrm_pt_export(helrm_ctx *ctx, const helrm_pt *pt, int64_t *coeffs_out)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        HCHECK(coeffs_out, HELRM_E_INVAL, "coeffs_out is NULL");
+        pt_export_signed(C(ctx), PT(pt), coeffs_out);
+    });
+}
+
+// ------------------------------------------------------------------ ciphertexts
+helrm_status helrm_encrypt(helrm_ctx *ctx, const helrm_evk *evk, const helrm_pt *pt, uint64_t seed, helrm_ct **out)
+{
+    if (out) *out = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        HCHECK(out, HELRM_E_INVAL, "out is NULL");
+        *out = (helrm_ct *)encrypt_pt(C(ctx), EVK(evk), PT(pt), seed);
+    });
+}
+
+helrm_status helrm_decrypt(helrm_ctx *ctx, const helrm_sk *sk, const helrm_ct *ct, double *slots_out,
+                           uint32_t n_slots)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        HCHECK(slots_out || n_slots == 0, HELRM_E_INVAL, "slots_out is NULL");
+        decrypt_slots(C(ctx), SK(sk), CT(ct), slots_out, (int)n_slots);
+    });
+}
+
+helrm_status helrm_ct_export(helrm_ctx *ctx, const helrm_ct *ct, uint64_t *coeffs_out, int32_t *level,
+                             double *scale)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        Ciphertext *a = CT(ct);
+        HCHECK(coeffs_out, HELRM_E_INVAL, "coeffs_out is NULL");
+        const int nq = a->level + 1;
+        DevMem t(c, (size_t)2 * nq * c->N * 8);
+        k::copy(c, t.u(), a->data.u(), (size_t)2 * nq * c->N);
+        k::ntt_inv(c, t.u(), 2 * nq, c->qmap(a->level, 0, nq));
+        CUDA_CHECK(cudaMemcpyAsync(coeffs_out, t.ptr, t.bytes, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_CHECK(cudaStreamSynchronize(c->stream));
+        if (level) *level = a->level;
+        if (scale) *scale = a->scale;
+    });
+}
+
+helrm_status helrm_ct_import(helrm_ctx *ctx, const uint64_t *coeffs, int32_t level, double scale, helrm_ct **out)
+{
+    if (out) *out = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        HCHECK(out && coeffs, HELRM_E_INVAL, "NULL argument");
+        HCHECK(level >= 0 && level <= c->L, HELRM_E_LEVEL, "level out of range");
+        const int nq = level + 1;
+        std::unique_ptr<Ciphertext> a(new_ct(c, level, scale));
+        CUDA_CHECK(cudaMemcpyAsync(a->data.ptr, coeffs, a->data.bytes, cudaMemcpyHostToDevice, c->stream));
+        DevMem flag(c, 8);
+        CUDA_CHECK(cudaMemsetAsync(flag.ptr, 0, 8, c->stream));
+        k::check_range(c, a->data.u(), 2 * nq, c->qmap(level, 0, nq), flag.as<int>());
+        int h = 0;
+        CUDA_CHECK(cudaMemcpyAsync(&h, flag.ptr, 4, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_CHECK(cudaStreamSynchronize(c->stream));
+        HCHECK(!h, HELRM_E_INVAL, "imported ciphertext has a residue >= its prime");
+        k::ntt_fwd(c, a->data.u(), 2 * nq, c->qmap(level, 0, nq));
+        *out = (helrm_ct *)a.release();
+    });
+}
+
+helrm_status helrm_ct_info(const helrm_ct *ct, int32_t *level, double *scale)
+{
+    return guard(nullptr, [&] {
+        Ciphertext *a = CT(ct);
+        if (level) *level = a->level;
+        if (scale) *scale = a->scale;
+    });
+}
+
+// ------------------------------------------------------------------ ops
+#define CT_OP(body)                                       \
+    if (out) *out = nullptr;                              \
+    return guard(ctx_or_null(ctx), [&] {                  \
+        HCHECK(out, HELRM_E_INVAL, "out is NULL");        \
+        Ctx *c = C(ctx);                                  \
+        *out = (helrm_ct *)(body);                        \
+    })
+
+helrm_status helrm_add(helrm_ctx *ctx, const helrm_ct *a, const helrm_ct *b, helrm_ct **out)
+{
+    CT_OP(ct_add(c, CT(a), CT(b), false));
+}
+helrm_status helrm_sub(helrm_ctx *ctx, const helrm_ct *a, const helrm_ct *b, helrm_ct **out)
+{
+    CT_OP(ct_add(c, CT(a), CT(b), true));
+}
+helrm_status helrm_add_pt(helrm_ctx *ctx, const helrm_ct *a, const helrm_pt *pt, helrm_ct **out)
+{
+    CT_OP(ct_add_pt(c, CT(a), PT(pt)));
+}
+helrm_status helrm_mul_pt(helrm_ctx *ctx, const helrm_ct *a, const helrm_pt *pt, helrm_ct **out)
+{
+    CT_OP(ct_mul_pt(c, CT(a), PT(pt)));
+}
+helrm_status helrm_mul(helrm_ctx *ctx, const helrm_evk *evk, const helrm_ct *a, const helrm_ct *b, helrm_ct **out)
+{
+    CT_OP(ct_mul(c, EVK(evk), CT(a), CT(b)));
+}
+helrm_status helrm_rescale(helrm_ctx *ctx, const helrm_ct *a, helrm_ct **out) { CT_OP(ct_rescale(c, CT(a))); }
+helrm_status helrm_drop_level(helrm_ctx *ctx, const helrm_ct *a, int32_t level, helrm_ct **out)
+{
+    CT_OP(ct_drop(c, CT(a), level));
+}
+helrm_status helrm_rotate(helrm_ctx *ctx, const helrm_evk *evk, const helrm_ct *a, int32_t step, helrm_ct **out)
+{
+    CT_OP(ct_rotate(c, EVK(evk), CT(a), step));
+}
+
+helrm_status helrm_rotate_hoisted(helrm_ctx *ctx, const helrm_evk *evk, const helrm_ct *a, const int32_t *steps,
+                                  uint32_t n, helrm_ct **outs)
+{
+    if (outs)
+        for (u32 i = 0; i < n; i++) outs[i] = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        HCHECK(outs && (steps || n == 0), HELRM_E_INVAL, "NULL argument");
+        std::vector<Ciphertext *> r;
+        ct_rotate_hoisted(c, EVK(evk), CT(a), std::vector<int>(steps, steps + n), r);
+        for (u32 i = 0; i < n; i++) outs[i] = (helrm_ct *)r[i];
+    });
+}
+
+// ------------------------------------------------------------------ matvec
+helrm_status helrm_ptmat_prepare(helrm_ctx *ctx, const double *W, uint32_t rows, uint32_t cols, uint32_t in_pad,
+                                 uint32_t out_pad, int32_t level, double ct_scale, double target_scale,
+                                 helrm_ptmat **out)
+{
+    if (out) *out = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        HCHECK(out, HELRM_E_INVAL, "out is NULL");
+        *out = (helrm_ptmat *)ptmat_prepare(C(ctx), W, (int)rows, (int)cols, (int)in_pad, (int)out_pad, level,
+                                            ct_scale, target_scale);
+    });
+}
+
+helrm_status helrm_ptmat_info(const helrm_ptmat *m, uint32_t *o)
+{
+    return guard(nullptr, [&] {
+        PtMatrix *p = PM(m);
+        HCHECK(o, HELRM_E_INVAL, "info_out is NULL");
+        o[0] = p->D;
+        o[1] = p->n1;
+        o[2] = p->n2;
+        o[3] = (u32)p->gb.size();
+        o[4] = (u32)p->folds.size();
+        o[5] = p->level;
+    });
+}
+
+static void copy_steps(const std::vector<int> &st, int32_t *steps_out, uint32_t *n_out)
+{
+    HCHECK(n_out, HELRM_E_INVAL, "n_out is NULL");
+    if (steps_out) {
+        HCHECK(*n_out >= st.size(), HELRM_E_INVAL, "steps_out too small");
+        for (size_t i = 0; i < st.size(); i++) steps_out[i] = st[i];
+    }
+    *n_out = (u32)st.size();
+}
+
+helrm_status helrm_ptmat_rotations(const helrm_ptmat *m, int32_t *steps_out, uint32_t *n_out)
+{
+    return guard(nullptr, [&] { copy_steps(PM(m)->rotations(), steps_out, n_out); });
+}
+
+helrm_status helrm_ptmat_import(helrm_ctx *ctx, helrm_ptmat *m, const int64_t *coeffs, uint32_t count)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        PtMatrix *p = PM(m);
+        HCHECK(coeffs, HELRM_E_INVAL, "coeffs is NULL");
+        HCHECK(count == p->pts.size(), HELRM_E_INVAL, "diagonal count mismatch");
+        for (u32 i = 0; i < count; i++)
+            p->pts[i].reset(pt_from_signed(c, coeffs + (size_t)i * c->N, p->level, true, p->pt_scale, PT_MONT));
+        p->upload_index();
+    });
+}
+
+helrm_status helrm_ptct_matvec(helrm_ctx *ctx, const helrm_evk *evk, const helrm_ptmat *m, const helrm_ct *in,
+                               uint32_t n_in, helrm_ct **out)
+{
+    if (out) *out = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        HCHECK(out, HELRM_E_INVAL, "out is NULL");
+        HCHECK(n_in == 1, HELRM_E_INVAL, "n_in must be 1");
+        *out = (helrm_ct *)matvec(C(ctx), EVK(evk), PM(m), CT(in));
+    });
+}
+
+// ------------------------------------------------------------------ embeddings
+helrm_status helrm_emb_prepare(helrm_ctx *ctx, uint32_t n_tables, const uint64_t *card, uint32_t base_p, uint32_t dim,
+                               const float *const *tables, uint32_t out_offset, uint32_t out_pad, int32_t level,
+                               double ct_scale, double target_scale, helrm_emb **out)
+{
+    if (out) *out = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        HCHECK(out && card && n_tables, HELRM_E_INVAL, "NULL argument");
+        *out = (helrm_emb *)emb_prepare(C(ctx), std::vector<u64>(card, card + n_tables), (int)base_p, (int)dim,
+                                        tables, (int)out_offset, (int)out_pad, level, ct_scale, target_scale);
+    });
+}
+
+helrm_status helrm_query_pack(const helrm_emb *emb, const uint64_t *indices, double *slots_out, uint32_t n_slots)
+{
+    Ctx *c = nullptr;
+    if (emb && ((const Handle *)emb)->kind == KIND_EMB) c = emb_ctx((const Emb *)emb);
+    return guard(c, [&] {
+        Emb *e = EMB(emb);
+        HCHECK(indices && (slots_out || n_slots == 0), HELRM_E_INVAL, "NULL argument");
+        std::vector<double> sel;
+        emb_pack_host(e, indices, sel);
+        u32 w, per;
+        emb_info(e, &w, &per);
+        for (u32 j = 0; j < n_slots; j++) slots_out[j] = (j % per) < w ? sel[j % per] : 0.0;
+    });
+}
+
+helrm_status helrm_emb_info(const helrm_emb *emb, uint32_t *width, uint32_t *period)
+{
+    return guard(nullptr, [&] {
+        HCHECK(width && period, HELRM_E_INVAL, "NULL argument");
+        emb_info(EMB(emb), width, period);
+    });
+}
+
+helrm_status helrm_embedding_lookup(helrm_ctx *ctx, const helrm_evk *evk, const helrm_emb *emb, const helrm_ct *sel,
+                                    uint32_t n_sel, helrm_ct **out)
+{
+    if (out) *out = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        HCHECK(out, HELRM_E_INVAL, "out is NULL");
+        HCHECK(n_sel == 1, HELRM_E_INVAL, "n_sel must be 1");
+        *out = (helrm_ct *)matvec(C(ctx), EVK(evk), emb_matrix_of(EMB(emb)), CT(sel));
+    });
+}
+
+// ------------------------------------------------------------------ model
+helrm_status helrm_model_create(helrm_ctx *ctx, const helrm_model_desc *desc, helrm_model **out)
+{
+    if (out) *out = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        HCHECK(out && desc, HELRM_E_INVAL, "NULL argument");
+        *out = (helrm_model *)model_create(C(ctx), desc);
+    });
+}
+
+helrm_status helrm_model_info(const helrm_model *m, uint32_t *info_out)
+{
+    return guard(nullptr, [&] {
+        HCHECK(info_out, HELRM_E_INVAL, "info_out is NULL");
+        model_info(MOD(m), info_out);
+    });
+}
+
+helrm_status helrm_model_rotations(const helrm_model *m, int32_t *steps_out, uint32_t *n_out)
+{
+    return guard(nullptr, [&] { copy_steps(model_rotations(MOD(m)), steps_out, n_out); });
+}
+
+helrm_status helrm_model_import_plaintexts(helrm_ctx *ctx, helrm_model *m, const int64_t *coeffs, uint32_t count)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        HCHECK(coeffs, HELRM_E_INVAL, "coeffs is NULL");
+        model_import(C(ctx), MOD(m), coeffs, count);
+    });
+}
+
+helrm_status helrm_model_export_plaintexts(helrm_ctx *ctx, const helrm_model *m, int64_t *coeffs, uint32_t count)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        HCHECK(coeffs, HELRM_E_INVAL, "coeffs is NULL");
+        model_export(C(ctx), MOD(m), coeffs, count);
+    });
+}
+
+helrm_status helrm_encrypt_query(helrm_ctx *ctx, const helrm_evk *evk, const helrm_model *m, const double *dense,
+                                 const uint64_t *indices, uint64_t seed, helrm_ct **ct_dense, helrm_ct **ct_sel)
+{
+    if (ct_dense) *ct_dense = nullptr;
+    if (ct_sel) *ct_sel = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        HCHECK(dense && indices && ct_dense && ct_sel, HELRM_E_INVAL, "NULL argument");
+        Ciphertext *a, *b;
+        model_encrypt_query(C(ctx), EVK(evk), MOD(m), dense, indices, seed, &a, &b, false);
+        *ct_dense = (helrm_ct *)a;
+        *ct_sel = (helrm_ct *)b;
+    });
+}
+
+helrm_status helrm_infer(helrm_ctx *ctx, const helrm_evk *evk, const helrm_model *m, const helrm_ct *ct_dense,
+                         const helrm_ct *ct_sel, helrm_ct **logit)
+{
+    if (logit) *logit = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        HCHECK(logit, HELRM_E_INVAL, "logit is NULL");
+        *logit = (helrm_ct *)model_infer(C(ctx), EVK(evk), MOD(m), CT(ct_dense), CT(ct_sel));
+    });
+}
+
+helrm_status helrm_decrypt_logit(helrm_ctx *ctx, const helrm_sk *sk, const helrm_ct *logit, double *logit_out,
+                                 double *prob_out)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        HCHECK(logit_out, HELRM_E_INVAL, "logit_out is NULL");
+        double v = 0;
+        decrypt_slots(C(ctx), SK(sk), CT(logit), &v, 1);
+        *logit_out = v;
+        if (prob_out) *prob_out = 1.0 / (1.0 + std::exp(-v));
+    });
+}
+
+helrm_status helrm_infer_e2e(helrm_ctx *ctx, const helrm_sk *sk, const helrm_evk *evk, const helrm_model *m,
+                             const double *dense, const uint64_t *indices, uint32_t n_queries, uint64_t seed,
+                             double *logits_out, double *probs_out)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        Model *mm = MOD(m);
+        HCHECK(dense && indices && logits_out, HELRM_E_INVAL, "NULL argument");
+        const size_t nd = model_n_dense(mm), nt = model_n_tables(mm);
+        for (u32 q = 0; q < n_queries; q++) {
+            Ciphertext *a, *b;
+            model_encrypt_query(c, EVK(evk), mm, dense + q * nd, indices + q * nt, seed + 2ull * q, &a, &b, false);
+            std::unique_ptr<Ciphertext> ca(a), cb(b);
+            std::unique_ptr<Ciphertext> y(model_infer(c, EVK(evk), mm, ca.get(), cb.get()));
+            double v = 0;
+            decrypt_slots(c, SK(sk), y.get(), &v, 1);
+            logits_out[q] = v;
+            if (probs_out) probs_out[q] = 1.0 / (1.0 + std::exp(-v));
+        }
+    });
+}
+
+helrm_status helrm_infer_e2e_device(helrm_ctx *ctx, const helrm_sk *sk, const helrm_evk *evk, const helrm_model *m,
+                                    const double *d_dense, const uint64_t *d_indices, uint32_t n_queries, uint64_t seed,
+                                    double *d_logits, double *d_probs)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        Model *mm = MOD(m);
+        HCHECK(d_dense && d_indices && d_logits, HELRM_E_INVAL, "NULL argument");
+        const size_t nd = model_n_dense(mm), nt = model_n_tables(mm);
+        for (u32 q = 0; q < n_queries; q++) {
+            Ciphertext *a, *b;
+            model_encrypt_query(c, EVK(evk), mm, d_dense + q * nd, d_indices + q * nt, seed + 2ull * q, &a, &b, true);
+            std::unique_ptr<Ciphertext> ca(a), cb(b);
+            std::unique_ptr<Ciphertext> y(model_infer(c, EVK(evk), mm, ca.get(), cb.get()));
+            decrypt_slots_device(c, SK(sk), y.get(), d_logits + q, 1);
+        }
+        if (d_probs) k::sigmoid(c, d_probs, d_logits, (int)n_queries);
+    });
+}
+
+// ------------------------------------------------------------------ misc
+void helrm_free(void *handle)
+{
+    if (!handle) return;
+    Handle *h = (Handle *)handle;
+    if (h->kind < KIND_CTX || h->kind > KIND_MODEL) return;
+    delete h;
+}
+
+const char *helrm_last_error(const helrm_ctx *ctx)
+{
+    Ctx *c = ctx_or_null(ctx);
+    return c ? c->last_error.c_str() : "invalid context";
+}
+
+const char *helrm_status_string(helrm_status s)
+{
+    switch (s) {
+    case HELRM_OK: return "ok";
+    case HELRM_E_INVAL: return "invalid argument";
+    case HELRM_E_PARAM: return "unsupported parameters";
+    case HELRM_E_LEVEL: return "level mismatch";
+    case HELRM_E_SCALE: return "scale mismatch";
+    case HELRM_E_NOKEY: return "missing key";
+    case HELRM_E_NOMEM: return "out of device memory";
+    case HELRM_E_CUDA: return "CUDA error";
+    case HELRM_E_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

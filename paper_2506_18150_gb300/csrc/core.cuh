@@ -1,0 +1,370 @@
+// core.cuh -- internal declarations of the GB300 HE-LRM library.
+//
+// Device words are u64 residues in [0, q).  Two multiplication forms are used:
+//  * Montgomery (R = 2^64): constant operands (keys, diagonals, masks, base
+//    conversion factors) are stored as b*R mod q, so REDC(a * bR) = a*b mod q
+//    in one reduction; a 128-bit sum of such products is reduced once.
+//  * Shoup: NTT twiddles carry w' = floor(w 2^64 / q), so a*w mod q costs one
+//    high and two low 64-bit products.
+// GB300 has no 64x64 multiplier: each 64-bit product is a short IMAD
+// sequence, which is why the constant-operand forms matter.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/helrm.h"
+
+namespace helrm {
+
+using u64 = uint64_t;
+using u32 = uint32_t;
+using i64 = int64_t;
+using u128 = unsigned __int128;
+
+// ----------------------------------------------------------------- errors
+struct Error {
+    helrm_status code;
+    std::string msg;
+};
+[[noreturn]] void fail(helrm_status code, const std::string &msg);
+#define HCHECK(cond, code, msg)                 \
+    do {                                        \
+        if (!(cond)) ::helrm::fail((code), (msg)); \
+    } while (0)
+#define CUDA_CHECK(x)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (x);                                                               \
+        if (e_ != cudaSuccess)                                                              \
+            ::helrm::fail(HELRM_E_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_));   \
+    } while (0)
+
+// ----------------------------------------------------------- modular math
+struct PrimeInfo {
+    u64 q;      // the prime
+    u64 qinv;   // q^-1 mod 2^64
+    u64 r2;     // 2^128 mod q (to enter Montgomery form)
+    u64 rmod;   // 2^64 mod q
+};
+
+__host__ __device__ __forceinline__ u64 mulhi64(u64 a, u64 b)
+{
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (u64)(((u128)a * b) >> 64);
+#endif
+}
+
+// (hi 2^64 + lo) 2^-64 mod q, for hi < q.  m q has low word lo, so the
+// difference is an exact multiple of 2^64: result = hi - mulhi(m, q), in (-q, q).
+__host__ __device__ __forceinline__ u64 redc(u64 hi, u64 lo, u64 q, u64 qinv)
+{
+    u64 m = lo * qinv;
+    u64 mh = mulhi64(m, q);
+    u64 r = hi - mh;
+    return hi < mh ? r + q : r;
+}
+// a * b mod q with b in Montgomery form (b R mod q, b < q); any a < 2^64.
+__host__ __device__ __forceinline__ u64 mont_mul(u64 a, u64 b_mont, u64 q, u64 qinv)
+{
+    return redc(mulhi64(a, b_mont), a * b_mont, q, qinv);
+}
+// a * b mod q for two plain residues: two reductions (a b R^-1, then * R^2 R^-1).
+__host__ __device__ __forceinline__ u64 mul_mod(u64 a, u64 b, u64 q, u64 qinv, u64 r2)
+{
+    return mont_mul(mont_mul(a, b, q, qinv), r2, q, qinv);
+}
+__host__ __device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q)
+{
+    u64 s = a + b;
+    return s >= q ? s - q : s;
+}
+__host__ __device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 q)
+{
+    return a >= b ? a - b : a + q - b;
+}
+// Shoup: a * w mod q with wp = floor(w 2^64 / q), w < q, any a < 2^64.
+__host__ __device__ __forceinline__ u64 shoup_mul(u64 a, u64 w, u64 wp, u64 q)
+{
+    u64 qh = mulhi64(a, wp);
+    u64 r = a * w - qh * q;
+    return r >= q ? r - q : r;
+}
+// 128-bit accumulator kept with hi < q (subtracting q 2^64 preserves the
+// value mod q), reduced by one REDC at the end.
+struct Acc128 {
+    u64 lo = 0, hi = 0;
+    __host__ __device__ __forceinline__ void mac(u64 a, u64 b, u64 q)
+    {
+        u64 pl = a * b;
+        u64 ph = mulhi64(a, b);
+        u64 nl = lo + pl;
+        hi += ph + (nl < pl ? 1 : 0);
+        lo = nl;
+        if (hi >= q) hi -= q;
+    }
+    __host__ __device__ __forceinline__ u64 reduce(u64 q, u64 qinv) const { return redc(hi, lo, q, qinv); }
+};
+
+// Limb l of a level-ell QP polynomial uses prime q_l for l <= ell, else p_{l-ell-1}
+// (global prime index L+1+(l-ell-1)).  `off` shifts the first limb; a non-zero
+// `period` restarts the numbering every `period` limbs (several polynomials of
+// the same basis stored back to back, e.g. both halves of a ciphertext).
+struct LimbMap {
+    int off;         // index of this array's first limb in the level's QP numbering
+    int qc;          // number of Q limbs in the level's basis (ell + 1)
+    int pbase;       // global prime index of p_0 (L + 1)
+    int period = 0;  // 0 = no repetition
+    __host__ __device__ __forceinline__ int pid(int l) const
+    {
+        int x = (period ? l % period : l) + off;
+        return x < qc ? x : pbase + (x - qc);
+    }
+};
+
+// ----------------------------------------------------------------- context
+struct Ctx;
+
+// Device buffer owned by a handle; freed stream-ordered on the context's stream.
+struct DevMem {
+    Ctx *ctx = nullptr;
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    DevMem() = default;
+    DevMem(Ctx *c, size_t b);
+    ~DevMem();
+    DevMem(const DevMem &) = delete;
+    DevMem &operator=(const DevMem &) = delete;
+    DevMem(DevMem &&o) noexcept { *this = std::move(o); }
+    DevMem &operator=(DevMem &&o) noexcept;
+    u64 *u() const { return (u64 *)ptr; }
+    template <class T>
+    T *as() const { return (T *)ptr; }
+};
+
+enum Kind : u32 {
+    KIND_CTX = 0x48E10001u,
+    KIND_SK,
+    KIND_EVK,
+    KIND_PT,
+    KIND_CT,
+    KIND_PTMAT,
+    KIND_EMB,
+    KIND_MODEL,
+};
+
+struct Handle {
+    u32 kind;
+    explicit Handle(u32 k) : kind(k) {}
+    virtual ~Handle() { kind = 0; }
+};
+
+// Device tables for one fast base conversion (src primes -> dst primes).
+struct BConvTable {
+    int n_src = 0, n_dst = 0;
+    DevMem tab;   // see kernels.cu: bconv layout
+};
+
+struct Ctx : Handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int logN = 0, N = 0, n_slots = 0, L = 0, K = 0, alpha = 1;
+    double delta = 0;
+    std::vector<u64> primes;   // q_0..q_L, p_0..p_{K-1}
+    std::vector<u64> psi;      // primitive 2N-th roots
+    std::vector<PrimeInfo> pinfo;
+    DevMem d_pinfo;            // PrimeInfo[nP]
+    DevMem d_tw_fwd;           // ulonglong2 [nP][N]: psi^brv(k), Shoup
+    DevMem d_tw_inv;           // ulonglong2 [nP][N]: psi^-brv(k), Shoup
+    DevMem d_ninv;             // ulonglong2 [nP]: N^-1, Shoup
+    DevMem d_fft_tw;           // double2 [N/2]: e^(-2 pi i t / N)
+    DevMem d_slot_of;          // int [N]: u -> slot j with 5^j = +-(2u+1) mod 2N
+    DevMem d_u_of_slot;        // int [n]: j -> (5^j mod 2N - 1)/2
+    DevMem d_pmod_mont;        // u64 [nP]: (P mod q_i) R mod q_i for i <= L, 0 for the P primes
+    DevMem d_pinv_mont;        // u64 [nP]: (P^-1 mod q_i) R mod q_i for i <= L
+    DevMem d_one_mont;         // u64 [nP]: R mod q_i (the constant 1 in Montgomery form)
+    std::map<std::pair<int, int>, BConvTable> modup_tab;   // (level, digit)
+    std::map<int, BConvTable> moddown_tab;                 // level
+    std::map<int, DevMem> rescale_tab;                     // level -> constants
+    u64 mem_in_use = 0, mem_cap = 0;
+    u64 launches = 0;
+    std::string last_error;
+    cudaMemPool_t pool = nullptr;
+
+    Ctx() : Handle(KIND_CTX) {}
+    ~Ctx() override;
+    int nP() const { return L + 1 + K; }
+    int dnum(int level) const { return (level + 1 + alpha - 1) / alpha; }
+    int digit_lo(int j) const { return j * alpha; }
+    int digit_hi(int j, int level) const { return std::min((j + 1) * alpha, level + 1); }
+    // level-ell QP numbering starting at limb `off`, repeating every `period` limbs
+    LimbMap qmap(int level, int off = 0, int period = 0) const { return LimbMap{off, level + 1, L + 1, period}; }
+    void *alloc(size_t bytes);
+    void release(void *p, size_t bytes);
+    u64 galois(int step) const;
+    const BConvTable &modup_table(int level, int digit);
+    const BConvTable &moddown_table(int level);
+    const u64 *rescale_table(int level);
+};
+
+// ---------------------------------------------------------------- objects
+struct Poly {  // (n_limbs x N) u64 in the NTT domain
+    DevMem mem;
+    int limbs = 0;
+};
+
+struct SecretKey : Handle {
+    Ctx *ctx;
+    DevMem s_ntt;    // [L+1+K][N] s in NTT form, plain residues
+    DevMem s_mont;   // same in Montgomery form
+    SecretKey(Ctx *c) : Handle(KIND_SK), ctx(c) {}
+};
+
+struct SwitchKey {          // digits j: (b_j, a_j) over the full QP basis, NTT + Montgomery form
+    DevMem data;            // [dnum][2][L+1+K][N]
+    int dnum = 0;
+};
+
+struct EvalKey : Handle {
+    Ctx *ctx;
+    u64 seed = 0;
+    DevMem pk;              // [2][L+1][N] (b, a) NTT, Montgomery form
+    std::unique_ptr<SwitchKey> relin;
+    std::map<u64, std::unique_ptr<SwitchKey>> rot;   // galois element -> key
+    EvalKey(Ctx *c) : Handle(KIND_EVK), ctx(c) {}
+};
+
+enum PtForm { PT_PLAIN = 0, PT_MONT = 1 };
+
+struct Plaintext : Handle {
+    Ctx *ctx;
+    int level = 0;
+    bool qp = false;        // limbs q_0..q_level (+ p_0..p_{K-1} if qp)
+    int form = PT_PLAIN;
+    double scale = 1;
+    DevMem data;            // [limbs][N] NTT domain
+    Plaintext(Ctx *c) : Handle(KIND_PT), ctx(c) {}
+    int limbs() const { return level + 1 + (qp ? ctx->K : 0); }
+};
+
+struct Ciphertext : Handle {
+    Ctx *ctx;
+    int level = 0;
+    double scale = 1;
+    DevMem data;            // [2][level+1][N] NTT domain
+    Ciphertext(Ctx *c) : Handle(KIND_CT), ctx(c) {}
+    u64 *c0() const { return data.u(); }
+    u64 *c1() const { return data.u() + (size_t)(level + 1) * ctx->N; }
+};
+
+// ----------------------------------------------------------- kernel API
+// (kernels.cu / ntt.cu; all launched on ctx->stream, all counted)
+namespace k {
+void ntt_fwd(Ctx *c, u64 *data, int n_limbs, LimbMap map);
+void ntt_inv(Ctx *c, u64 *data, int n_limbs, LimbMap map);
+void copy(Ctx *c, u64 *dst, const u64 *src, size_t n_words);
+void zero(Ctx *c, u64 *dst, size_t n_words);
+void add(Ctx *c, u64 *out, const u64 *a, const u64 *b, int n_limbs, LimbMap map);
+void sub(Ctx *c, u64 *out, const u64 *a, const u64 *b, int n_limbs, LimbMap map);
+void neg(Ctx *c, u64 *out, const u64 *a, int n_limbs, LimbMap map);
+// out = a * b_mont (b in Montgomery form)
+void mul_mont(Ctx *c, u64 *out, const u64 *a, const u64 *b_mont, int n_limbs, LimbMap map);
+// out = a * b (both plain)
+void mul_plain(Ctx *c, u64 *out, const u64 *a, const u64 *b, int n_limbs, LimbMap map);
+// out = a * R mod q (enter Montgomery form)
+void to_mont(Ctx *c, u64 *out, const u64 *a, int n_limbs, LimbMap map);
+// out = a R^-1 mod q (leave Montgomery form)
+void from_mont(Ctx *c, u64 *out, const u64 *a, int n_limbs, LimbMap map);
+// (d0, d1, d2) (+)= (a0 b0, a0 b1 + a1 b0, a1 b1) over n_limbs limbs
+void tensor(Ctx *c, u64 *d, const u64 *a0, const u64 *a1, const u64 *b0, const u64 *b1, int n_limbs, LimbMap map,
+            bool accumulate);
+// out_l = a_l * scal_mont[pid(l)] (one constant per limb, Montgomery form, indexed by prime)
+void mul_scalar_mont(Ctx *c, u64 *out, const u64 *a, const u64 *d_scal_by_prime, int n_limbs,
+                     LimbMap map);
+// out = (a - b) * scal[pid]
+void sub_mul_scalar(Ctx *c, u64 *out, const u64 *a, const u64 *b, const u64 *d_scal_by_prime,
+                    int n_limbs, LimbMap map);
+// centred integers (int64 N) -> residues for n_limbs limbs
+void from_signed(Ctx *c, u64 *out, const i64 *in, int n_limbs, LimbMap map);
+void bconv(Ctx *c, const BConvTable &t, const u64 *in_base, u64 *out_base);
+// d_out[l][i] = sum_j dig_j[l][perm(i)] * key_j(l)[i] for the level-ell QP basis, both
+// polys of the key; if c0 != null, out0 on Q limbs += P * c0[perm(i)]
+void ks_inner_auto(Ctx *c, u64 *out, const u64 *digits, int dnum, const u64 *key, int level,
+                   u64 galois, const u64 *c0, const u64 *d_pmod_mont);
+// inner[g][2][limbs][N] = sum_b diag[(g,b)] * baby[b]
+void bsgs_mac(Ctx *c, u64 *inner, const u64 *baby, int n_baby, const u64 *const *d_diag_ptrs,
+              const int *d_gb_index, int n2, int n1, int limbs, LimbMap map);
+void automorphism(Ctx *c, u64 *out, const u64 *in, int n_limbs, u64 galois);
+// rescale helper: coefficient-form last limb -> centred residues for ell limbs
+void rescale_spread(Ctx *c, u64 *out, const u64 *last_coef, int level);
+// random
+void chacha_words(Ctx *c, u32 *out, u64 seed, u32 purpose, u64 index, u64 first_word, u64 n_words);
+void sample_uniform(Ctx *c, u64 *out, u64 seed, u32 purpose, u64 index, int n_limbs,
+                    const int *d_limb_pid, const int *d_limb_gid);
+void sample_ternary(Ctx *c, i64 *out, u64 seed, u32 purpose, u64 index);
+void sample_cbd21(Ctx *c, i64 *out, u64 seed, u32 purpose, u64 index);
+// FFT encode / decode
+void encode_slots(Ctx *c, u64 *out_residues, const double *d_slots, int n_valid, int period,
+                  double scale, int n_limbs, LimbMap map, i64 *d_coeffs_out);
+void decode_limb0(Ctx *c, double *d_slots_out, const u64 *m_coef_limb0, double scale, int n_slots);
+void check_range(Ctx *c, const u64 *data, int n_limbs, LimbMap map, int *d_flag);
+// selector one-hots of one query: d_tab [T][3] = (rows, offset, digits)
+void pack_selector(Ctx *c, double *sel, const u64 *d_idx, const int *d_tab, int T, int base, int in_pad);
+void sigmoid(Ctx *c, double *d_p, const double *d_x, int n);
+}  // namespace k
+
+// ------------------------------------------------------ scheme (scheme.cu)
+Ciphertext *new_ct(Ctx *c, int level, double scale);
+void ks_modup(Ctx *c, const u64 *poly_ntt, int level, u64 *digits_out);
+void ks_moddown(Ctx *c, const u64 *qp_ntt, int level, u64 *out_ntt);
+Ciphertext *ct_rescale(Ctx *c, const Ciphertext *a);
+Ciphertext *ct_add(Ctx *c, const Ciphertext *a, const Ciphertext *b, bool subtract = false);
+Ciphertext *ct_add_pt(Ctx *c, const Ciphertext *a, const Plaintext *pt);
+Ciphertext *ct_mul_pt(Ctx *c, const Ciphertext *a, const Plaintext *pt);
+Ciphertext *ct_drop(Ctx *c, const Ciphertext *a, int level);
+void ct_rotate_hoisted(Ctx *c, const EvalKey *evk, const Ciphertext *a, const std::vector<int> &steps,
+                       std::vector<Ciphertext *> &outs);
+Ciphertext *ct_rotate(Ctx *c, const EvalKey *evk, const Ciphertext *a, int step);
+void ct_tensor_acc(Ctx *c, u64 *d012, const Ciphertext *a, const Ciphertext *b, bool accumulate);
+Ciphertext *ct_relin(Ctx *c, const EvalKey *evk, const u64 *d012, int level, double scale);
+Ciphertext *ct_mul(Ctx *c, const EvalKey *evk, const Ciphertext *a, const Ciphertext *b);
+Plaintext *pt_encode(Ctx *c, const double *h_slots, int n_slots, int period, int level, bool qp,
+                     double scale, int form);
+Plaintext *pt_encode_dev(Ctx *c, const double *d_slots, int n_valid, int period, int level, double scale);
+Plaintext *pt_from_signed(Ctx *c, const i64 *h_coeffs, int level, bool qp, double scale, int form);
+void pt_export_signed(Ctx *c, const Plaintext *pt, i64 *h_out);
+SecretKey *keygen_sk(Ctx *c, u64 seed);
+EvalKey *keygen_evk(Ctx *c, const SecretKey *sk, u64 seed);
+void keygen_rot(Ctx *c, const SecretKey *sk, EvalKey *evk, const std::vector<int> &steps);
+Ciphertext *encrypt_pt(Ctx *c, const EvalKey *evk, const Plaintext *pt, u64 seed);
+void decrypt_slots(Ctx *c, const SecretKey *sk, const Ciphertext *ct, double *h_out, int n_slots);
+// decrypt into a device buffer, stream-ordered, no synchronisation
+void decrypt_slots_device(Ctx *c, const SecretKey *sk, const Ciphertext *ct, double *d_out, int n_slots);
+const SwitchKey *rot_key(const EvalKey *evk, u64 galois);
+
+// ------------------------------------------------------ matvec (linear.cu)
+struct PtMatrix : Handle {
+    Ctx *ctx;
+    int in_pad = 0, out_pad = 0, D = 0, n1 = 0, n2 = 0, level = 0;
+    double pt_scale = 0, out_scale = 0;
+    std::vector<int> folds;
+    std::vector<std::pair<int, int>> gb;      // non-zero diagonals, (g, b) order
+    std::vector<std::unique_ptr<Plaintext>> pts;
+    DevMem d_ptrs;                             // device array of diagonal pointers
+    DevMem d_gb_index;                         // int [n2][n1] -> index in pts or -1
+    PtMatrix(Ctx *c) : Handle(KIND_PTMAT), ctx(c) {}
+    std::vector<int> rotations() const;
+    void upload_index();
+};
+PtMatrix *ptmat_prepare(Ctx *c, const double *W, int rows, int cols, int in_pad, int out_pad,
+                        int level, double ct_scale, double target_scale);
+Ciphertext *matvec(Ctx *c, const EvalKey *evk, const PtMatrix *m, const Ciphertext *in);
+int pow2ceil(int x);
+
+}  // namespace helrm

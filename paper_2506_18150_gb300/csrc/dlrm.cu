@@ -1,0 +1,470 @@
+// dlrm.cu -- HE-LRM on top of the CKKS layer.
+//
+//  * client: base-p digits of each index (little-endian, l = ceil(log_p k),
+//    Sec. 4.1), one one-hot per digit, all tables' selectors concatenated
+//    (Sec. 4.2.2), replicated with the selector's period, encoded, encrypted;
+//  * server: block-diagonal packing of every table's transposed compressed
+//    tables into one matrix, so the lookup of all tables is one BSGS matvec
+//    that consumes one level and leaves the embeddings contiguous (Sec. 4.2);
+//  * DLRM (Sec. 2.2, Sec. 5.3): bottom MLP, embeddings, interaction, top MLP,
+//    encrypted logit; x^2 activations after every layer but the last.
+//
+// Model layout (the reading used by library and oracle alike): z holds
+// blocks of 16 slots with period W_z = pow2ceil(16 B'): block 0 = bottom MLP
+// output, block t = embedding of table t-1, and for the dot interaction a block
+// of ones (B' = T + 2).  Dot interaction in two levels: z1 = z masked to the
+// first 16 B' slots of each period W2 = pow2ceil(32 B'); zz = z1 + rot(z1, -16 B')
+// repeats the blocks; A_s = z masked to region s-1 of the top-input layout
+// (period W_u); u = relin(sum_s A_s (x) rot(zz, 16 s)), s = 1..B'/2, so region
+// s-1, block a holds z_a * z_{(a+s) mod B'}; the first top layer sums the 16
+// slots of each pair in its weights.  Levels are assigned as late as possible so
+// the logit ends at level 0.
+#include <algorithm>
+#include <cmath>
+
+#include "core.cuh"
+
+namespace helrm {
+
+constexpr int DIM = 16;
+
+struct SelSeg {
+    int t, j, off, width;
+};
+
+static int num_digits(u64 k, u64 p)
+{
+    int ell = 1;
+    unsigned __int128 cap = p;
+    while (cap < k) {
+        cap *= p;
+        ell++;
+    }
+    return ell;
+}
+
+static std::vector<SelSeg> selector_layout(const std::vector<u64> &cards, int p, int *width)
+{
+    std::vector<SelSeg> out;
+    int off = 0;
+    for (int t = 0; t < (int)cards.size(); t++) {
+        if (cards[t] <= (u64)p) {
+            out.push_back({t, 0, off, (int)cards[t]});
+            off += (int)cards[t];
+        } else {
+            int ell = num_digits(cards[t], p);
+            for (int j = 0; j < ell; j++) {
+                out.push_back({t, j, off, p});
+                off += p;
+            }
+        }
+    }
+    *width = off;
+    return out;
+}
+
+struct Emb : Handle {
+    Ctx *ctx;
+    std::vector<u64> cards;
+    int base = 0, dim = 0, width = 0, in_pad = 0, out_pad = 0;
+    std::vector<SelSeg> layout;
+    std::unique_ptr<PtMatrix> pm;
+    DevMem d_tab;   // int [T][3]: card (clamped), offset, digits
+    Emb(Ctx *c) : Handle(KIND_EMB), ctx(c) {}
+};
+
+// Matrix of the packed lookup: rows [out_offset + dim t, out_offset + dim (t+1))
+// take table t's transposed digit tables at the selector columns of its digits.
+static std::vector<double> emb_matrix(const Emb &e, const float *const *tables, int out_offset, int rows)
+{
+    std::vector<double> M((size_t)rows * e.width, 0.0);
+    std::vector<int> row0(e.cards.size(), 0);
+    for (auto &s : e.layout) {
+        const float *C = tables[s.t] + (size_t)row0[s.t] * e.dim;
+        for (int r = 0; r < s.width; r++)
+            for (int kk = 0; kk < e.dim; kk++)
+                M[(size_t)(out_offset + e.dim * s.t + kk) * e.width + s.off + r] = (double)C[(size_t)r * e.dim + kk];
+        row0[s.t] += s.width;
+    }
+    return M;
+}
+
+Emb *emb_prepare(Ctx *c, const std::vector<u64> &cards, int base, int dim, const float *const *tables,
+                 int out_offset, int out_pad, int level, double ct_scale, double target_scale)
+{
+    HCHECK(!cards.empty() && base >= 2 && dim >= 1 && tables, HELRM_E_INVAL, "bad embedding description");
+    for (u64 k2 : cards) HCHECK(k2 >= 1, HELRM_E_INVAL, "table with no rows");
+    std::unique_ptr<Emb> e(new Emb(c));
+    e->cards = cards;
+    e->base = base;
+    e->dim = dim;
+    e->layout = selector_layout(cards, base, &e->width);
+    e->in_pad = pow2ceil(e->width);
+    e->out_pad = out_pad;
+    const int rows = out_offset + dim * (int)cards.size();
+    HCHECK(rows <= out_pad, HELRM_E_INVAL, "embedding outputs exceed out_pad");
+    HCHECK(e->in_pad <= c->n_slots, HELRM_E_PARAM, "selector wider than the slot count");
+    std::vector<double> M = emb_matrix(*e, tables, out_offset, rows);
+    e->pm.reset(ptmat_prepare(c, M.data(), rows, e->width, e->in_pad, out_pad, level, ct_scale, target_scale));
+    std::vector<int> tab;
+    for (size_t t = 0; t < cards.size(); t++) {
+        int off = -1;
+        for (auto &s : e->layout)
+            if (s.t == (int)t) {
+                off = s.off;
+                break;
+            }
+        tab.push_back((int)std::min<u64>(cards[t], (u64)1 << 30));
+        tab.push_back(off);
+        tab.push_back(cards[t] <= (u64)base ? 1 : num_digits(cards[t], base));
+    }
+    e->d_tab = DevMem(c, tab.size() * 4);
+    CUDA_CHECK(cudaMemcpyAsync(e->d_tab.ptr, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    return e.release();
+}
+
+void emb_pack_host(const Emb *e, const u64 *indices, std::vector<double> &sel)
+{
+    sel.assign(e->width, 0.0);
+    for (auto &s : e->layout) {
+        u64 i = indices[s.t];
+        HCHECK(i < e->cards[s.t], HELRM_E_INVAL, "index out of range for its table");
+        if (e->cards[s.t] <= (u64)e->base) {
+            sel[s.off + i] = 1.0;
+        } else {
+            for (int j = 0; j < s.j; j++) i /= (u64)e->base;
+            sel[s.off + (int)(i % (u64)e->base)] = 1.0;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ model
+struct Layer {
+    std::unique_ptr<PtMatrix> pm;
+    std::unique_ptr<Plaintext> bias;
+    bool square = false;
+};
+
+struct Model : Handle {
+    Ctx *ctx;
+    int n_dense = 0, interaction = 0, T = 0, B = 0, Bp = 0, S = 0;
+    int lvl_dense = 0, lvl_sel = 0, lvl_z = 0, lvl_u = 0, p_dense = 0, W_z = 0, W2 = 0, W_u = 0;
+    double mask_scale = 0;
+    std::vector<Layer> bottom, top;
+    std::unique_ptr<Emb> emb;
+    std::unique_ptr<Plaintext> ones;
+    std::vector<std::unique_ptr<Plaintext>> masks;
+    Model(Ctx *c) : Handle(KIND_MODEL), ctx(c) {}
+
+    std::vector<std::unique_ptr<Plaintext> *> plaintexts()
+    {
+        std::vector<std::unique_ptr<Plaintext> *> out;
+        for (auto &l : bottom) {
+            for (auto &p : l.pm->pts) out.push_back(&p);
+            out.push_back(&l.bias);
+        }
+        for (auto &p : emb->pm->pts) out.push_back(&p);
+        if (interaction == 0) {
+            out.push_back(&ones);
+            for (auto &m : masks) out.push_back(&m);
+        }
+        for (auto &l : top) {
+            for (auto &p : l.pm->pts) out.push_back(&p);
+            out.push_back(&l.bias);
+        }
+        return out;
+    }
+    std::vector<int> rotations() const
+    {
+        std::vector<int> st;
+        auto addv = [&](const std::vector<int> &v) { st.insert(st.end(), v.begin(), v.end()); };
+        for (auto &l : bottom) addv(l.pm->rotations());
+        addv(emb->pm->rotations());
+        if (interaction == 0) {
+            st.push_back(-DIM * Bp);
+            for (int s = 1; s <= S; s++) st.push_back(DIM * s);
+        }
+        for (auto &l : top) addv(l.pm->rotations());
+        std::sort(st.begin(), st.end());
+        st.erase(std::unique(st.begin(), st.end()), st.end());
+        return st;
+    }
+};
+
+static int pair_index(int a, int c2, int B)
+{
+    int idx = 0;
+    for (int x = 0; x < a; x++) idx += B - 1 - x;
+    return idx + (c2 - a - 1);
+}
+
+static Plaintext *encode_vec(Ctx *c, const std::vector<double> &v, int level, double scale, int form)
+{
+    return pt_encode(c, v.data(), (int)v.size(), (int)v.size(), level, false, scale, form);
+}
+
+static std::vector<double> replicate_bias(const double *b, int n, int period)
+{
+    std::vector<double> v(period, 0.0);
+    for (int i = 0; i < n; i++) v[i] = b[i];
+    return v;
+}
+
+Model *model_create(Ctx *c, const helrm_model_desc *d)
+{
+    HCHECK(d && d->dim == DIM, HELRM_E_INVAL, "model dim must be 16");
+    HCHECK(d->n_bottom >= 1 && d->n_top >= 1 && d->n_tables >= 1, HELRM_E_INVAL, "empty model");
+    HCHECK(d->bottom_widths[0] == d->n_dense && d->bottom_widths[d->n_bottom] == DIM, HELRM_E_INVAL,
+           "bottom MLP must map n_dense -> 16");
+    HCHECK(d->top_widths[d->n_top] == 1, HELRM_E_INVAL, "top MLP must end in one logit");
+    HCHECK(d->interaction == 0 || d->interaction == 1, HELRM_E_INVAL, "interaction must be 0 (dot) or 1 (concat)");
+    std::unique_ptr<Model> m(new Model(c));
+    const bool dot = d->interaction == 0;
+    m->n_dense = (int)d->n_dense;
+    m->interaction = d->interaction;
+    m->T = (int)d->n_tables;
+    m->B = m->T + 1;
+    const int nb = (int)d->n_bottom, nt = (int)d->n_top;
+    const u32 want_top = dot ? DIM + m->B * (m->B - 1) / 2 : DIM * m->B;
+    HCHECK(d->top_widths[0] == want_top, HELRM_E_INVAL, "top MLP input width does not match the interaction");
+    m->lvl_u = 2 * nt - 1;
+    m->lvl_z = dot ? m->lvl_u + 2 : m->lvl_u;
+    m->lvl_sel = m->lvl_z + 1;
+    m->lvl_dense = m->lvl_z + 2 * nb;
+    HCHECK(m->lvl_dense <= c->L, HELRM_E_PARAM,
+           "model needs " + std::to_string(m->lvl_dense) + " levels, chain has " + std::to_string(c->L));
+    m->Bp = dot ? m->B + 1 : m->B;
+    m->W_z = pow2ceil(DIM * m->Bp);
+    m->p_dense = pow2ceil(m->n_dense);
+    if (dot) {
+        m->W2 = pow2ceil(2 * DIM * m->Bp);
+        m->S = m->Bp / 2;
+        m->W_u = pow2ceil(m->S * m->W2);
+    } else {
+        m->W_u = m->W_z;
+    }
+    int width = 0;
+    std::vector<u64> cards(d->cards, d->cards + d->n_tables);
+    selector_layout(cards, (int)d->base_p, &width);
+    HCHECK(std::max({m->W_u, pow2ceil(width), m->W_z, m->p_dense}) <= c->n_slots, HELRM_E_PARAM,
+           "layout wider than the slot count");
+
+    const double delta = c->delta;
+    int lvl = m->lvl_dense, in_pad = m->p_dense;
+    double scale = delta;
+    for (int i = 0; i < nb; i++) {
+        const int rows = (int)d->bottom_widths[i + 1], cols = (int)d->bottom_widths[i];
+        const int out_pad = (i + 1 == nb) ? m->W_z : pow2ceil(rows);
+        Layer L;
+        L.pm.reset(ptmat_prepare(c, d->bottom_W[i], rows, cols, in_pad, out_pad, lvl, scale, delta));
+        L.bias.reset(encode_vec(c, replicate_bias(d->bottom_b[i], rows, out_pad), lvl - 1, delta, PT_PLAIN));
+        L.square = true;
+        m->bottom.push_back(std::move(L));
+        lvl -= 1;
+        scale = (delta * delta) / (double)c->primes[lvl];
+        lvl -= 1;
+        in_pad = out_pad;
+    }
+    const double scale_b = scale;
+    m->emb.reset(emb_prepare(c, cards, (int)d->base_p, DIM, d->tables, DIM, m->W_z, m->lvl_sel, delta, scale_b));
+    double u_scale = scale_b;
+    if (dot) {
+        std::vector<double> ones(m->W_z, 0.0);
+        for (int kk = 0; kk < DIM; kk++) ones[DIM * m->B + kk] = 1.0;
+        m->ones.reset(encode_vec(c, ones, m->lvl_z, scale_b, PT_PLAIN));
+        m->mask_scale = (double)c->primes[m->lvl_z] * delta / scale_b;
+        std::vector<double> m0(m->W2, 0.0);
+        for (int j = 0; j < DIM * m->Bp; j++) m0[j] = 1.0;
+        m->masks.emplace_back(encode_vec(c, m0, m->lvl_z, m->mask_scale, PT_MONT));
+        for (int s = 1; s <= m->S; s++) {
+            const int n_a = (m->Bp % 2 == 0 && s == m->Bp / 2) ? m->Bp / 2 : m->Bp;
+            std::vector<double> ms(m->W_u, 0.0);
+            for (int j = 0; j < DIM * n_a; j++) ms[(size_t)(s - 1) * m->W2 + j] = 1.0;
+            m->masks.emplace_back(encode_vec(c, ms, m->lvl_z, m->mask_scale, PT_MONT));
+        }
+        u_scale = (delta * delta) / (double)c->primes[m->lvl_z - 1];
+    }
+    lvl = m->lvl_u;
+    scale = u_scale;
+    for (int i = 0; i < nt; i++) {
+        const bool last = i + 1 == nt;
+        const int rows = (int)d->top_widths[i + 1], cols = (int)d->top_widths[i];
+        const int out_pad = pow2ceil(rows);
+        Layer L;
+        if (i == 0 && dot) {
+            // first top layer over the interaction layout
+            std::vector<double> Wm((size_t)rows * m->W_u, 0.0);
+            const double *W0 = d->top_W[0];
+            for (int s = 1; s <= m->S; s++) {
+                const int n_a = (m->Bp % 2 == 0 && s == m->Bp / 2) ? m->Bp / 2 : m->Bp;
+                for (int a = 0; a < n_a; a++) {
+                    int x = a, y = (a + s) % m->Bp;
+                    if (x > y) std::swap(x, y);
+                    for (int kk = 0; kk < DIM; kk++) {
+                        const size_t col = (size_t)(s - 1) * m->W2 + DIM * a + kk;
+                        for (int r = 0; r < rows; r++) {
+                            double w = 0.0;
+                            if (y == m->Bp - 1) {
+                                if (x == 0) w = W0[(size_t)r * cols + kk];
+                            } else {
+                                w = W0[(size_t)r * cols + DIM + pair_index(x, y, m->B)];
+                            }
+                            Wm[(size_t)r * m->W_u + col] = w;
+                        }
+                    }
+                }
+            }
+            L.pm.reset(ptmat_prepare(c, Wm.data(), rows, m->W_u, m->W_u, out_pad, lvl, scale, delta));
+        } else {
+            const int ip = (i == 0) ? m->W_u : pow2ceil(cols);
+            L.pm.reset(ptmat_prepare(c, d->top_W[i], rows, cols, ip, out_pad, lvl, scale, delta));
+        }
+        L.bias.reset(encode_vec(c, replicate_bias(d->top_b[i], rows, out_pad), lvl - 1, delta, PT_PLAIN));
+        L.square = !last;
+        m->top.push_back(std::move(L));
+        lvl -= 1;
+        scale = delta;
+        if (!last) {
+            scale = (delta * delta) / (double)c->primes[lvl];
+            lvl -= 1;
+        }
+    }
+    HCHECK(lvl == 0, HELRM_E_PARAM, "internal: level schedule does not end at 0");
+    return m.release();
+}
+
+void model_import(Ctx *c, Model *m, const i64 *coeffs, u32 count)
+{
+    auto pts = m->plaintexts();
+    HCHECK(count == pts.size(), HELRM_E_INVAL,
+           "plaintext count mismatch: model has " + std::to_string(pts.size()));
+    for (size_t i = 0; i < pts.size(); i++) {
+        Plaintext *o = pts[i]->get();
+        pts[i]->reset(pt_from_signed(c, coeffs + i * (size_t)c->N, o->level, o->qp, o->scale, o->form));
+    }
+    for (auto &l : m->bottom) l.pm->upload_index();
+    m->emb->pm->upload_index();
+    for (auto &l : m->top) l.pm->upload_index();
+}
+
+void model_export(Ctx *c, Model *m, i64 *coeffs, u32 count)
+{
+    auto pts = m->plaintexts();
+    HCHECK(count == pts.size(), HELRM_E_INVAL, "plaintext count mismatch");
+    for (size_t i = 0; i < pts.size(); i++) pt_export_signed(c, pts[i]->get(), coeffs + i * (size_t)c->N);
+}
+
+static Ciphertext *dense_layer(Ctx *c, const EvalKey *evk, const Layer &L, const Ciphertext *x)
+{
+    std::unique_ptr<Ciphertext> y(matvec(c, evk, L.pm.get(), x));
+    y.reset(ct_add_pt(c, y.get(), L.bias.get()));
+    if (L.square) y.reset(ct_mul(c, evk, y.get(), y.get()));
+    return y.release();
+}
+
+static Ciphertext *dot_interaction(Ctx *c, const EvalKey *evk, const Model *m, const Ciphertext *z)
+{
+    auto masked = [&](int i) {
+        std::unique_ptr<Ciphertext> t(ct_mul_pt(c, z, m->masks[i].get()));
+        Ciphertext *r = ct_rescale(c, t.get());
+        r->scale = c->delta;
+        return r;
+    };
+    std::unique_ptr<Ciphertext> z1(masked(0));
+    std::vector<std::unique_ptr<Ciphertext>> A;
+    for (int s = 1; s <= m->S; s++) A.emplace_back(masked(s));
+    std::unique_ptr<Ciphertext> r(ct_rotate(c, evk, z1.get(), -DIM * m->Bp));
+    std::unique_ptr<Ciphertext> zz(ct_add(c, z1.get(), r.get()));
+    std::vector<int> steps;
+    for (int s = 1; s <= m->S; s++) steps.push_back(DIM * s);
+    std::vector<Ciphertext *> R;
+    ct_rotate_hoisted(c, evk, zz.get(), steps, R);
+    std::vector<std::unique_ptr<Ciphertext>> Rk;
+    for (auto *p : R) Rk.emplace_back(p);
+    const int lvl = z1->level;
+    DevMem d(c, (size_t)3 * (lvl + 1) * c->N * 8);
+    for (int s = 1; s <= m->S; s++) ct_tensor_acc(c, d.u(), A[s - 1].get(), Rk[s - 1].get(), s > 1);
+    std::unique_ptr<Ciphertext> rl(ct_relin(c, evk, d.u(), lvl, c->delta * c->delta));
+    return ct_rescale(c, rl.get());
+}
+
+Ciphertext *model_infer(Ctx *c, const EvalKey *evk, const Model *m, const Ciphertext *ct_dense,
+                        const Ciphertext *ct_sel)
+{
+    HCHECK(ct_dense->level == m->lvl_dense, HELRM_E_LEVEL, "ct_dense is not at the model's dense level");
+    HCHECK(ct_sel->level == m->lvl_sel, HELRM_E_LEVEL, "ct_sel is not at the model's selector level");
+    std::unique_ptr<Ciphertext> h;
+    const Ciphertext *x = ct_dense;
+    for (auto &L : m->bottom) {
+        h.reset(dense_layer(c, evk, L, x));
+        x = h.get();
+    }
+    std::unique_ptr<Ciphertext> e(matvec(c, evk, m->emb->pm.get(), ct_sel));
+    std::unique_ptr<Ciphertext> z(ct_add(c, h.get(), e.get()));
+    h.reset();
+    e.reset();
+    std::unique_ptr<Ciphertext> y;
+    if (m->interaction == 0) {
+        z.reset(ct_add_pt(c, z.get(), m->ones.get()));
+        y.reset(dot_interaction(c, evk, m, z.get()));
+    } else {
+        y = std::move(z);
+    }
+    for (auto &L : m->top) y.reset(dense_layer(c, evk, L, y.get()));
+    return y.release();
+}
+
+// client side: pack on the device, encode, encrypt
+void model_encrypt_query(Ctx *c, const EvalKey *evk, const Model *m, const double *dense, const u64 *indices,
+                         u64 seed, Ciphertext **ct_dense, Ciphertext **ct_sel, bool on_device)
+{
+    const Emb *e = m->emb.get();
+    DevMem dd, di, sel(c, (size_t)e->in_pad * 8);
+    const double *d_dense = dense;
+    const u64 *d_idx = indices;
+    if (!on_device) {
+        for (int t = 0; t < m->T; t++)
+            HCHECK(indices[t] < e->cards[t], HELRM_E_INVAL, "index out of range for its table");
+        dd = DevMem(c, (size_t)m->n_dense * 8);
+        di = DevMem(c, (size_t)m->T * 8);
+        CUDA_CHECK(cudaMemcpyAsync(dd.ptr, dense, (size_t)m->n_dense * 8, cudaMemcpyHostToDevice, c->stream));
+        CUDA_CHECK(cudaMemcpyAsync(di.ptr, indices, (size_t)m->T * 8, cudaMemcpyHostToDevice, c->stream));
+        d_dense = dd.as<double>();
+        d_idx = di.u();
+    }
+    k::pack_selector(c, sel.as<double>(), d_idx, e->d_tab.as<int>(), m->T, e->base, e->in_pad);
+    std::unique_ptr<Plaintext> pd(pt_encode_dev(c, d_dense, m->n_dense, m->p_dense, m->lvl_dense, c->delta));
+    std::unique_ptr<Plaintext> ps(pt_encode_dev(c, sel.as<double>(), e->in_pad, e->in_pad, m->lvl_sel, c->delta));
+    std::unique_ptr<Ciphertext> a(encrypt_pt(c, evk, pd.get(), seed));
+    std::unique_ptr<Ciphertext> b(encrypt_pt(c, evk, ps.get(), seed + 1));
+    *ct_dense = a.release();
+    *ct_sel = b.release();
+}
+
+// model accessors for the C ABI
+void model_info(const Model *m, u32 *o)
+{
+    o[0] = m->lvl_dense;
+    o[1] = m->lvl_sel;
+    o[2] = m->lvl_z;
+    o[3] = m->lvl_u;
+    o[4] = m->p_dense;
+    o[5] = m->emb->in_pad;
+    o[6] = m->W_z;
+    o[7] = m->W_u;
+    o[8] = (u32)const_cast<Model *>(m)->plaintexts().size();
+}
+std::vector<int> model_rotations(const Model *m) { return m->rotations(); }
+const PtMatrix *emb_matrix_of(const Emb *e) { return e->pm.get(); }
+void emb_info(const Emb *e, u32 *width, u32 *period)
+{
+    *width = e->width;
+    *period = e->in_pad;
+}
+Ctx *emb_ctx(const Emb *e) { return e->ctx; }
+Ctx *model_ctx(const Model *m) { return m->ctx; }
+u32 model_n_dense(const Model *m) { return (u32)m->n_dense; }
+u32 model_n_tables(const Model *m) { return (u32)m->T; }
+
+}  // namespace helrm

@@ -1,0 +1,166 @@
+// linear.cu -- plaintext-matrix x ciphertext-vector products (HE-LRM Sec. 2.1.4
+// and Sec. 3.2.1: diagonal method with baby-step giant-step, double hoisting).
+//
+// Layout: a vector of padded length v is replicated with period v over the n
+// slots.  For W padded to out_pad x in_pad there are D = min(in_pad, out_pad)
+// extended diagonals diag_i[j] = W[j mod out_pad, (j + i) mod in_pad]; when the
+// matrix is wide, rotate-and-add folds by in_pad/2, ..., out_pad finish the
+// sum.  BSGS: n1 = smallest power of two with n1^2 >= D, n2 = D / n1,
+// i = g n1 + b, diag'_{g,b} = rot(diag_i, -g n1), which reads
+// W[(j - g n1) mod out_pad, (j + b) mod in_pad].
+//
+// Double hoisting: one ModUp of c1; each baby step b is phi_{5^b} applied to
+// the extended digits, the key inner product and P phi(c0), all kept over QP
+// (no ModDown); one MAC kernel forms inner_g = sum_b diag'_{g,b} baby_b for all
+// g; each giant step g > 0 ModDowns the a-part of inner_g, ModUps it, applies
+// phi_{5^{g n1}} and the key, and adds phi(b-part); one ModDown at the end,
+// then rescale, then the folds.
+#include <algorithm>
+#include <cmath>
+
+#include "core.cuh"
+
+namespace helrm {
+
+int pow2ceil(int x)
+{
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+std::vector<int> PtMatrix::rotations() const
+{
+    std::vector<int> st;
+    for (auto &gb2 : gb) {
+        if (gb2.second) st.push_back(gb2.second);
+        if (gb2.first) st.push_back(gb2.first * n1);
+    }
+    for (int f : folds) st.push_back(f);
+    std::sort(st.begin(), st.end());
+    st.erase(std::unique(st.begin(), st.end()), st.end());
+    return st;
+}
+
+void PtMatrix::upload_index()
+{
+    std::vector<const u64 *> ptrs;
+    for (auto &p : pts) ptrs.push_back(p->data.u());
+    std::vector<int> idx((size_t)n1 * n2, -1);
+    for (size_t t = 0; t < gb.size(); t++) idx[(size_t)gb[t].first * n1 + gb[t].second] = (int)t;
+    d_ptrs = DevMem(ctx, std::max<size_t>(ptrs.size(), 1) * sizeof(u64 *));
+    d_gb_index = DevMem(ctx, idx.size() * sizeof(int));
+    if (!ptrs.empty())
+        CUDA_CHECK(cudaMemcpyAsync(d_ptrs.ptr, ptrs.data(), ptrs.size() * sizeof(u64 *), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+    CUDA_CHECK(cudaMemcpyAsync(d_gb_index.ptr, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice,
+                               ctx->stream));
+    CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+}
+
+PtMatrix *ptmat_prepare(Ctx *c, const double *W, int rows, int cols, int in_pad, int out_pad, int level,
+                        double ct_scale, double target_scale)
+{
+    HCHECK(W && rows >= 1 && cols >= 1, HELRM_E_INVAL, "empty matrix");
+    HCHECK(in_pad == pow2ceil(in_pad) && out_pad == pow2ceil(out_pad), HELRM_E_INVAL, "pads must be powers of two");
+    HCHECK(rows <= out_pad && cols <= in_pad, HELRM_E_INVAL, "matrix larger than its padding");
+    HCHECK(in_pad <= c->n_slots && out_pad <= c->n_slots, HELRM_E_PARAM, "padding exceeds the slot count");
+    HCHECK(level >= 1 && level <= c->L, HELRM_E_LEVEL, "matvec level must be in [1, L]");
+    std::unique_ptr<PtMatrix> m(new PtMatrix(c));
+    m->in_pad = in_pad;
+    m->out_pad = out_pad;
+    m->D = std::min(in_pad, out_pad);
+    m->n1 = 1;
+    while (m->n1 * m->n1 < m->D) m->n1 <<= 1;
+    m->n2 = m->D / m->n1;
+    m->level = level;
+    for (int s = in_pad / 2; s >= out_pad; s /= 2) m->folds.push_back(s);
+    m->pt_scale = (double)c->primes[level] * target_scale / ct_scale;
+    m->out_scale = target_scale;
+    auto Wp = [&](int r, int col) -> double { return (r < rows && col < cols) ? W[(size_t)r * cols + col] : 0.0; };
+    const int P = std::max(in_pad, out_pad);
+    std::vector<double> v(P);
+    for (int g = 0; g < m->n2; g++)
+        for (int b = 0; b < m->n1; b++) {
+            bool nz = false;
+            for (int j = 0; j < P; j++) {
+                int r = ((j - g * m->n1) % out_pad + out_pad) % out_pad;
+                v[j] = Wp(r, (j + b) % in_pad);
+                nz |= v[j] != 0.0;
+            }
+            if (!nz) continue;
+            m->gb.push_back({g, b});
+            m->pts.emplace_back(pt_encode(c, v.data(), P, P, level, true, m->pt_scale, PT_MONT));
+        }
+    m->upload_index();
+    return m.release();
+}
+
+Ciphertext *matvec(Ctx *c, const EvalKey *evk, const PtMatrix *m, const Ciphertext *in)
+{
+    const int l = in->level, N = c->N, nq = l + 1, nl = nq + c->K, dnum = c->dnum(l);
+    HCHECK(l == m->level, HELRM_E_LEVEL, "ciphertext level does not match the prepared matrix");
+    const size_t plane = (size_t)nl * N;
+    std::vector<char> need_b(m->n1, 0), need_g(m->n2, 0);
+    for (auto &gb : m->gb) {
+        need_b[gb.second] = 1;
+        need_g[gb.first] = 1;
+    }
+    // keys first, so a missing key fails before any work
+    std::vector<const SwitchKey *> bkey(m->n1, nullptr), gkey(m->n2, nullptr);
+    for (int b = 1; b < m->n1; b++)
+        if (need_b[b]) bkey[b] = rot_key(evk, c->galois(b));
+    for (int g = 1; g < m->n2; g++)
+        if (need_g[g]) gkey[g] = rot_key(evk, c->galois(g * m->n1));
+
+    DevMem digits(c, (size_t)dnum * plane * 8);
+    DevMem baby(c, (size_t)m->n1 * 2 * plane * 8);
+    ks_modup(c, in->c1(), l, digits.u());
+    for (int b = 0; b < m->n1; b++) {
+        if (!need_b[b]) continue;
+        u64 *bb = baby.u() + (size_t)b * 2 * plane;
+        if (b == 0) {   // (P c0, P c1) over QP: P mod q_i on the Q limbs, 0 on the P limbs
+            for (int p = 0; p < 2; p++) {
+                k::mul_scalar_mont(c, bb + p * plane, p ? in->c1() : in->c0(), c->d_pmod_mont.u(), nq, c->qmap(l));
+                k::zero(c, bb + p * plane + (size_t)nq * N, (size_t)c->K * N);
+            }
+        } else {
+            k::ks_inner_auto(c, bb, digits.u(), dnum, bkey[b]->data.u(), l, c->galois(b), in->c0(),
+                             c->d_pmod_mont.u());
+        }
+    }
+    DevMem inner(c, (size_t)m->n2 * 2 * plane * 8);
+    k::bsgs_mac(c, inner.u(), baby.u(), m->n1, m->d_ptrs.as<const u64 *>(), m->d_gb_index.as<int>(), m->n2, m->n1, nl,
+                c->qmap(l));
+    baby = DevMem();
+    DevMem acc(c, 2 * plane * 8), c1q(c, (size_t)nq * N * 8), t(c, 2 * plane * 8), phi(c, plane * 8);
+    k::zero(c, acc.u(), 2 * plane);
+    const LimbMap qp2 = c->qmap(l, 0, nl), qp = c->qmap(l);
+    for (int g = 0; g < m->n2; g++) {
+        if (!need_g[g]) continue;
+        const u64 *ig = inner.u() + (size_t)g * 2 * plane;
+        if (g == 0) {
+            k::add(c, acc.u(), acc.u(), ig, 2 * nl, qp2);
+            continue;
+        }
+        const u64 gal = c->galois(g * m->n1);
+        ks_moddown(c, ig + plane, l, c1q.u());
+        ks_modup(c, c1q.u(), l, digits.u());
+        k::ks_inner_auto(c, t.u(), digits.u(), dnum, gkey[g]->data.u(), l, gal, nullptr, nullptr);
+        k::automorphism(c, phi.u(), ig, nl, gal);
+        k::add(c, acc.u(), acc.u(), phi.u(), nl, qp);
+        k::add(c, acc.u(), acc.u(), t.u(), 2 * nl, qp2);
+    }
+    std::unique_ptr<Ciphertext> o(new_ct(c, l, in->scale * m->pt_scale));
+    ks_moddown(c, acc.u(), l, o->c0());
+    ks_moddown(c, acc.u() + plane, l, o->c1());
+    std::unique_ptr<Ciphertext> y(ct_rescale(c, o.get()));
+    y->scale = m->out_scale;
+    for (int f : m->folds) {
+        std::unique_ptr<Ciphertext> r(ct_rotate(c, evk, y.get(), f));
+        y.reset(ct_add(c, y.get(), r.get()));
+    }
+    return y.release();
+}
+
+}  // namespace helrm

@@ -1,0 +1,499 @@
+"""ctypes binding of libhelrm.so (argument marshalling only).
+
+Every function mirrors the C entry point of the same name in include/helrm.h;
+all computation runs in the CUDA library.  Handles are wrapped in objects that
+release themselves (helrm_free) when garbage-collected, and keep their context
+alive.  A non-OK status raises HelrmError with the library's message.  If the
+shared library has not been built the import of any function raises: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhelrm.so")
+
+STATUS = {0: "HELRM_OK", -1: "HELRM_E_INVAL", -2: "HELRM_E_PARAM", -3: "HELRM_E_LEVEL",
+          -4: "HELRM_E_SCALE", -5: "HELRM_E_NOKEY", -6: "HELRM_E_NOMEM", -7: "HELRM_E_CUDA",
+          -8: "HELRM_E_TIMEOUT"}
+
+
+class HelrmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class Params(C.Structure):
+    _fields_ = [("log_n", C.c_uint32), ("n_q", C.c_uint32), ("q_bits", C.POINTER(C.c_uint32)),
+                ("n_p", C.c_uint32), ("p_bits", C.c_uint32), ("alpha", C.c_uint32),
+                ("log2_scale", C.c_double)]
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [("n_dense", C.c_uint32), ("n_bottom", C.c_uint32),
+                ("bottom_widths", C.POINTER(C.c_uint32)),
+                ("bottom_W", C.POINTER(C.POINTER(C.c_double))), ("bottom_b", C.POINTER(C.POINTER(C.c_double))),
+                ("n_top", C.c_uint32), ("top_widths", C.POINTER(C.c_uint32)),
+                ("top_W", C.POINTER(C.POINTER(C.c_double))), ("top_b", C.POINTER(C.POINTER(C.c_double))),
+                ("n_tables", C.c_uint32), ("cards", C.POINTER(C.c_uint64)), ("base_p", C.c_uint32),
+                ("dim", C.c_uint32), ("tables", C.POINTER(C.POINTER(C.c_float))),
+                ("interaction", C.c_int32)]
+
+
+_lib = None
+_vp = C.c_void_p
+_pp = C.POINTER(C.c_void_p)
+_u64p = C.POINTER(C.c_uint64)
+_i64p = C.POINTER(C.c_int64)
+_u32p = C.POINTER(C.c_uint32)
+_i32p = C.POINTER(C.c_int32)
+_dp = C.POINTER(C.c_double)
+
+_SIGS = {
+    "helrm_ctx_create": [C.POINTER(Params), C.c_int, _vp, _pp],
+    "helrm_ctx_primes": [_vp, _u64p, _u64p],
+    "helrm_ctx_dims": [_vp, _u32p],
+    "helrm_ctx_set_memory_cap": [_vp, C.c_uint64],
+    "helrm_ctx_memory_in_use": [_vp, _u64p],
+    "helrm_ctx_synchronize": [_vp],
+    "helrm_ctx_launch_count": [_vp, _u64p],
+    "helrm_ntt": [_vp, _vp, C.c_uint32, C.c_uint32, C.c_int],
+    "helrm_keygen": [_vp, C.c_uint64, _i32p, C.c_uint32, _pp, _pp],
+    "helrm_evk_add_rotations": [_vp, _vp, _vp, _i32p, C.c_uint32],
+    "helrm_evk_bytes": [_vp, _u64p],
+    "helrm_encode": [_vp, _dp, C.c_uint32, C.c_int32, C.c_double, _pp],
+    "helrm_pt_import": [_vp, _i64p, C.c_int32, C.c_double, _pp],
+    "helrm_pt_export": [_vp, _vp, _i64p],
+    "helrm_encrypt": [_vp, _vp, _vp, C.c_uint64, _pp],
+    "helrm_decrypt": [_vp, _vp, _vp, _dp, C.c_uint32],
+    "helrm_ct_export": [_vp, _vp, _u64p, _i32p, _dp],
+    "helrm_ct_import": [_vp, _u64p, C.c_int32, C.c_double, _pp],
+    "helrm_ct_info": [_vp, _i32p, _dp],
+    "helrm_add": [_vp, _vp, _vp, _pp],
+    "helrm_sub": [_vp, _vp, _vp, _pp],
+    "helrm_add_pt": [_vp, _vp, _vp, _pp],
+    "helrm_mul_pt": [_vp, _vp, _vp, _pp],
+    "helrm_mul": [_vp, _vp, _vp, _vp, _pp],
+    "helrm_rescale": [_vp, _vp, _pp],
+    "helrm_drop_level": [_vp, _vp, C.c_int32, _pp],
+    "helrm_rotate": [_vp, _vp, _vp, C.c_int32, _pp],
+    "helrm_rotate_hoisted": [_vp, _vp, _vp, _i32p, C.c_uint32, _pp],
+    "helrm_ptmat_prepare": [_vp, _dp, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int32,
+                            C.c_double, C.c_double, _pp],
+    "helrm_ptmat_info": [_vp, _u32p],
+    "helrm_ptmat_rotations": [_vp, _i32p, _u32p],
+    "helrm_ptmat_import": [_vp, _vp, _i64p, C.c_uint32],
+    "helrm_ptct_matvec": [_vp, _vp, _vp, _vp, C.c_uint32, _pp],
+    "helrm_emb_prepare": [_vp, C.c_uint32, _u64p, C.c_uint32, C.c_uint32, C.POINTER(C.POINTER(C.c_float)),
+                          C.c_uint32, C.c_uint32, C.c_int32, C.c_double, C.c_double, _pp],
+    "helrm_query_pack": [_vp, _u64p, _dp, C.c_uint32],
+    "helrm_emb_info": [_vp, _u32p, _u32p],
+    "helrm_embedding_lookup": [_vp, _vp, _vp, _vp, C.c_uint32, _pp],
+    "helrm_model_create": [_vp, C.POINTER(ModelDesc), _pp],
+    "helrm_model_info": [_vp, _u32p],
+    "helrm_model_rotations": [_vp, _i32p, _u32p],
+    "helrm_model_import_plaintexts": [_vp, _vp, _i64p, C.c_uint32],
+    "helrm_model_export_plaintexts": [_vp, _vp, _i64p, C.c_uint32],
+    "helrm_encrypt_query": [_vp, _vp, _vp, _dp, _u64p, C.c_uint64, _pp, _pp],
+    "helrm_infer": [_vp, _vp, _vp, _vp, _vp, _pp],
+    "helrm_decrypt_logit": [_vp, _vp, _vp, _dp, _dp],
+    "helrm_infer_e2e": [_vp, _vp, _vp, _vp, _dp, _u64p, C.c_uint32, C.c_uint64, _dp, _dp],
+}
+
+
+def lib():
+    """Load libhelrm.so; raises if it is missing (build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.helrm_free.argtypes = [_vp]
+        L.helrm_free.restype = None
+        L.helrm_last_error.argtypes = [_vp]
+        L.helrm_last_error.restype = C.c_char_p
+        L.helrm_status_string.argtypes = [C.c_int]
+        L.helrm_status_string.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def declared_symbols():
+    """Entry points this binding expects (all declared in include/helrm.h)."""
+    return sorted(list(_SIGS) + ["helrm_free", "helrm_last_error", "helrm_status_string"])
+
+
+class Handle:
+    """An owned library handle; freed on garbage collection (after its dependants)."""
+
+    def __init__(self, ptr, keep=None):
+        self.ptr = C.c_void_p(ptr)
+        self._keep = keep
+
+    def __del__(self):
+        try:
+            if self.ptr and _lib is not None:
+                _lib.helrm_free(self.ptr)
+                self.ptr = C.c_void_p()
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        return self.ptr
+
+
+class Context(Handle):
+    pass
+
+
+def _check(ctx, st):
+    if st != 0:
+        msg = lib().helrm_last_error(ctx.ptr if ctx is not None else None)
+        raise HelrmError(st, msg.decode() if msg else "")
+
+
+def _u64(a):
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    return a, a.ctypes.data_as(_u64p)
+
+
+def _i64(a):
+    a = np.ascontiguousarray(a, dtype=np.int64)
+    return a, a.ctypes.data_as(_i64p)
+
+
+def _f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+def _i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(_i32p)
+
+
+# ------------------------------------------------------------------ context
+def helrm_ctx_create(log_n, q_bits, n_p, p_bits, alpha, log2_scale, device=0, stream=0) -> Context:
+    qb = (C.c_uint32 * len(q_bits))(*q_bits)
+    p = Params(log_n, len(q_bits), qb, n_p, p_bits, alpha, log2_scale)
+    out = C.c_void_p()
+    st = lib().helrm_ctx_create(C.byref(p), device, C.c_void_p(stream), C.byref(out))
+    if st != 0:
+        raise HelrmError(st, "helrm_ctx_create failed (see parameters)")
+    return Context(out.value)
+
+
+def helrm_ctx_primes(ctx):
+    d = helrm_ctx_dims(ctx)
+    n = d[2] + 1 + d[3]
+    pr = np.zeros(n, dtype=np.uint64)
+    psi = np.zeros(n, dtype=np.uint64)
+    _check(ctx, lib().helrm_ctx_primes(ctx.ptr, pr.ctypes.data_as(_u64p), psi.ctypes.data_as(_u64p)))
+    return [int(x) for x in pr], [int(x) for x in psi]
+
+
+def helrm_ctx_dims(ctx):
+    d = (C.c_uint32 * 6)()
+    _check(ctx, lib().helrm_ctx_dims(ctx.ptr, d))
+    return list(d)
+
+
+def helrm_ctx_set_memory_cap(ctx, nbytes: int):
+    _check(ctx, lib().helrm_ctx_set_memory_cap(ctx.ptr, nbytes))
+
+
+def helrm_ctx_memory_in_use(ctx) -> int:
+    v = C.c_uint64()
+    _check(ctx, lib().helrm_ctx_memory_in_use(ctx.ptr, C.byref(v)))
+    return v.value
+
+
+def helrm_ctx_synchronize(ctx):
+    _check(ctx, lib().helrm_ctx_synchronize(ctx.ptr))
+
+
+def helrm_ctx_launch_count(ctx) -> int:
+    v = C.c_uint64()
+    _check(ctx, lib().helrm_ctx_launch_count(ctx.ptr, C.byref(v)))
+    return v.value
+
+
+def helrm_ntt(ctx, d_ptr: int, n_limbs: int, first_prime: int, inverse: bool):
+    _check(ctx, lib().helrm_ntt(ctx.ptr, C.c_void_p(d_ptr), n_limbs, first_prime, int(inverse)))
+
+
+# ------------------------------------------------------------------ keys / pts / cts
+def helrm_keygen(ctx, seed: int, rot_steps=()):
+    st_arr, st_p = _i32(list(rot_steps) or [0])
+    sk, evk = C.c_void_p(), C.c_void_p()
+    _check(ctx, lib().helrm_keygen(ctx.ptr, seed, st_p, len(rot_steps), C.byref(sk), C.byref(evk)))
+    return Handle(sk.value, ctx), Handle(evk.value, ctx)
+
+
+def helrm_evk_add_rotations(ctx, sk, evk, rot_steps):
+    a, p = _i32(list(rot_steps) or [0])
+    _check(ctx, lib().helrm_evk_add_rotations(ctx.ptr, sk.ptr, evk.ptr, p, len(rot_steps)))
+
+
+def helrm_evk_bytes(ctx, evk) -> int:
+    v = C.c_uint64()
+    _check(ctx, lib().helrm_evk_bytes(evk.ptr, C.byref(v)))
+    return v.value
+
+
+def helrm_encode(ctx, slots, level: int, scale: float):
+    a, p = _f64(slots)
+    out = C.c_void_p()
+    _check(ctx, lib().helrm_encode(ctx.ptr, p, len(a), level, scale, C.byref(out)))
+    return Handle(out.value, ctx)
+
+
+def helrm_pt_import(ctx, coeffs, level: int, scale: float):
+    a, p = _i64(coeffs)
+    out = C.c_void_p()
+    _check(ctx, lib().helrm_pt_import(ctx.ptr, p, level, scale, C.byref(out)))
+    return Handle(out.value, ctx)
+
+
+def helrm_pt_export(ctx, pt):
+    n = helrm_ctx_dims(ctx)[0]
+    out = np.zeros(n, dtype=np.int64)
+    _check(ctx, lib().helrm_pt_export(ctx.ptr, pt.ptr, out.ctypes.data_as(_i64p)))
+    return out
+
+
+def helrm_encrypt(ctx, evk, pt, seed: int):
+    out = C.c_void_p()
+    _check(ctx, lib().helrm_encrypt(ctx.ptr, evk.ptr, pt.ptr, seed, C.byref(out)))
+    return Handle(out.value, ctx)
+
+
+def helrm_decrypt(ctx, sk, ct, n_slots: int):
+    out = np.zeros(max(n_slots, 1))
+    _check(ctx, lib().helrm_decrypt(ctx.ptr, sk.ptr, ct.ptr, out.ctypes.data_as(_dp), n_slots))
+    return out[:n_slots]
+
+
+def helrm_ct_info(ctx, ct):
+    lv, sc = C.c_int32(), C.c_double()
+    _check(ctx, lib().helrm_ct_info(ct.ptr, C.byref(lv), C.byref(sc)))
+    return lv.value, sc.value
+
+
+def helrm_ct_export(ctx, ct):
+    """(coeffs [2, level+1, N] uint64 coefficient domain, level, scale)."""
+    lv, sc = helrm_ct_info(ctx, ct)
+    n = helrm_ctx_dims(ctx)[0]
+    out = np.zeros((2, lv + 1, n), dtype=np.uint64)
+    _check(ctx, lib().helrm_ct_export(ctx.ptr, ct.ptr, out.ctypes.data_as(_u64p), None, None))
+    return out, lv, sc
+
+
+def helrm_ct_import(ctx, coeffs, level: int, scale: float):
+    a, p = _u64(coeffs)
+    out = C.c_void_p()
+    _check(ctx, lib().helrm_ct_import(ctx.ptr, p, level, scale, C.byref(out)))
+    return Handle(out.value, ctx)
+
+
+def _ct_op(name, ctx, *args):
+    out = C.c_void_p()
+    _check(ctx, getattr(lib(), name)(ctx.ptr, *args, C.byref(out)))
+    return Handle(out.value, ctx)
+
+
+def helrm_add(ctx, a, b):
+    return _ct_op("helrm_add", ctx, a.ptr, b.ptr)
+
+
+def helrm_sub(ctx, a, b):
+    return _ct_op("helrm_sub", ctx, a.ptr, b.ptr)
+
+
+def helrm_add_pt(ctx, a, pt):
+    return _ct_op("helrm_add_pt", ctx, a.ptr, pt.ptr)
+
+
+def helrm_mul_pt(ctx, a, pt):
+    return _ct_op("helrm_mul_pt", ctx, a.ptr, pt.ptr)
+
+
+def helrm_mul(ctx, evk, a, b):
+    return _ct_op("helrm_mul", ctx, evk.ptr, a.ptr, b.ptr)
+
+
+def helrm_rescale(ctx, a):
+    return _ct_op("helrm_rescale", ctx, a.ptr)
+
+
+def helrm_drop_level(ctx, a, level: int):
+    return _ct_op("helrm_drop_level", ctx, a.ptr, level)
+
+
+def helrm_rotate(ctx, evk, a, step: int):
+    return _ct_op("helrm_rotate", ctx, evk.ptr, a.ptr, step)
+
+
+def helrm_rotate_hoisted(ctx, evk, a, steps):
+    arr, p = _i32(list(steps))
+    outs = (C.c_void_p * len(steps))()
+    _check(ctx, lib().helrm_rotate_hoisted(ctx.ptr, evk.ptr, a.ptr, p, len(steps), outs))
+    return [Handle(o, ctx) for o in outs]
+
+
+# ------------------------------------------------------------------ matvec / embeddings
+def helrm_ptmat_prepare(ctx, W, in_pad, out_pad, level, ct_scale, target_scale):
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    out = C.c_void_p()
+    _check(ctx, lib().helrm_ptmat_prepare(ctx.ptr, W.ctypes.data_as(_dp), W.shape[0], W.shape[1], in_pad,
+                                          out_pad, level, ct_scale, target_scale, C.byref(out)))
+    return Handle(out.value, ctx)
+
+
+def helrm_ptmat_info(ctx, m):
+    o = (C.c_uint32 * 6)()
+    _check(ctx, lib().helrm_ptmat_info(m.ptr, o))
+    return dict(zip(["D", "n1", "n2", "nonzero", "folds", "level"], list(o)))
+
+
+def _steps(fn, ctx, h):
+    n = C.c_uint32(0)
+    _check(ctx, fn(h.ptr, None, C.byref(n)))
+    arr = (C.c_int32 * max(n.value, 1))()
+    _check(ctx, fn(h.ptr, arr, C.byref(n)))
+    return list(arr)[: n.value]
+
+
+def helrm_ptmat_rotations(ctx, m):
+    return _steps(lib().helrm_ptmat_rotations, ctx, m)
+
+
+def helrm_ptmat_import(ctx, m, coeffs):
+    a, p = _i64(coeffs)
+    _check(ctx, lib().helrm_ptmat_import(ctx.ptr, m.ptr, p, a.shape[0]))
+
+
+def helrm_ptct_matvec(ctx, evk, m, ct):
+    return _ct_op("helrm_ptct_matvec", ctx, evk.ptr, m.ptr, ct.ptr, 1)
+
+
+def _float_tables(tables):
+    """tables[t] = list of digit tables (rows x dim) -> stacked float32 arrays + pointer array."""
+    arrs = [np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float32) for x in t], axis=0))
+            for t in tables]
+    ptrs = (C.POINTER(C.c_float) * len(arrs))(*[a.ctypes.data_as(C.POINTER(C.c_float)) for a in arrs])
+    return arrs, ptrs
+
+
+def helrm_emb_prepare(ctx, cards, base_p, dim, tables, out_offset, out_pad, level, ct_scale, target_scale):
+    c_arr, c_p = _u64(cards)
+    arrs, ptrs = _float_tables(tables)
+    out = C.c_void_p()
+    _check(ctx, lib().helrm_emb_prepare(ctx.ptr, len(cards), c_p, base_p, dim, ptrs, out_offset, out_pad, level,
+                                        ct_scale, target_scale, C.byref(out)))
+    return Handle(out.value, ctx)
+
+
+def helrm_emb_info(ctx, emb):
+    w, p = C.c_uint32(), C.c_uint32()
+    _check(ctx, lib().helrm_emb_info(emb.ptr, C.byref(w), C.byref(p)))
+    return w.value, p.value
+
+
+def helrm_query_pack(ctx, emb, indices, n_slots):
+    a, p = _u64(indices)
+    out = np.zeros(n_slots)
+    _check(ctx, lib().helrm_query_pack(emb.ptr, p, out.ctypes.data_as(_dp), n_slots))
+    return out
+
+
+def helrm_embedding_lookup(ctx, evk, emb, sel):
+    return _ct_op("helrm_embedding_lookup", ctx, evk.ptr, emb.ptr, sel.ptr, 1)
+
+
+# ------------------------------------------------------------------ model
+def helrm_model_create(ctx, spec, w):
+    """spec: synthetic.DLRMSpec-like object; w: synthetic.DLRMWeights-like object."""
+    keep = []
+
+    def dptrs(mats):
+        arrs = [np.ascontiguousarray(m, dtype=np.float64) for m in mats]
+        keep.extend(arrs)
+        return (C.POINTER(C.c_double) * len(arrs))(*[a.ctypes.data_as(_dp) for a in arrs])
+
+    bw = (C.c_uint32 * len(spec.bottom))(*spec.bottom)
+    tw = (C.c_uint32 * len(spec.top))(*spec.top)
+    cards = np.ascontiguousarray(spec.cards, dtype=np.uint64)
+    tarrs, tptrs = _float_tables(w.tables)
+    keep += [bw, tw, cards, tarrs, tptrs]
+    d = ModelDesc(spec.n_dense, len(w.bottom_W), bw, dptrs(w.bottom_W), dptrs(w.bottom_b),
+                  len(w.top_W), tw, dptrs(w.top_W), dptrs(w.top_b), len(spec.cards),
+                  cards.ctypes.data_as(_u64p), spec.base, spec.dim, tptrs,
+                  0 if spec.interaction == "dot" else 1)
+    out = C.c_void_p()
+    _check(ctx, lib().helrm_model_create(ctx.ptr, C.byref(d), C.byref(out)))
+    return Handle(out.value, ctx)
+
+
+def helrm_model_info(ctx, m):
+    o = (C.c_uint32 * 9)()
+    _check(ctx, lib().helrm_model_info(m.ptr, o))
+    keys = ["lvl_dense", "lvl_sel", "lvl_z", "lvl_u", "p_dense", "p_sel", "W_z", "W_u", "n_plaintexts"]
+    return dict(zip(keys, list(o)))
+
+
+def helrm_model_rotations(ctx, m):
+    return _steps(lib().helrm_model_rotations, ctx, m)
+
+
+def helrm_model_import_plaintexts(ctx, m, coeffs):
+    a, p = _i64(coeffs)
+    _check(ctx, lib().helrm_model_import_plaintexts(ctx.ptr, m.ptr, p, a.shape[0]))
+
+
+def helrm_model_export_plaintexts(ctx, m):
+    n = helrm_ctx_dims(ctx)[0]
+    cnt = helrm_model_info(ctx, m)["n_plaintexts"]
+    out = np.zeros((cnt, n), dtype=np.int64)
+    _check(ctx, lib().helrm_model_export_plaintexts(ctx.ptr, m.ptr, out.ctypes.data_as(_i64p), cnt))
+    return out
+
+
+def helrm_encrypt_query(ctx, evk, m, dense, indices, seed: int):
+    d, dp = _f64(dense)
+    i, ip = _u64(indices)
+    a, b = C.c_void_p(), C.c_void_p()
+    _check(ctx, lib().helrm_encrypt_query(ctx.ptr, evk.ptr, m.ptr, dp, ip, seed, C.byref(a), C.byref(b)))
+    return Handle(a.value, ctx), Handle(b.value, ctx)
+
+
+def helrm_infer(ctx, evk, m, ct_dense, ct_sel):
+    return _ct_op("helrm_infer", ctx, evk.ptr, m.ptr, ct_dense.ptr, ct_sel.ptr)
+
+
+def helrm_decrypt_logit(ctx, sk, ct):
+    lg, pr = C.c_double(), C.c_double()
+    _check(ctx, lib().helrm_decrypt_logit(ctx.ptr, sk.ptr, ct.ptr, C.byref(lg), C.byref(pr)))
+    return lg.value, pr.value
+
+
+def helrm_infer_e2e(ctx, sk, evk, m, dense, indices, seed: int):
+    d, dp = _f64(dense)
+    i, ip = _u64(indices)
+    nq = d.shape[0]
+    lg = np.zeros(nq)
+    pr = np.zeros(nq)
+    _check(ctx, lib().helrm_infer_e2e(ctx.ptr, sk.ptr, evk.ptr, m.ptr, dp, ip, nq, seed,
+                                      lg.ctypes.data_as(_dp), pr.ctypes.data_as(_dp)))
+    return lg, pr

@@ -106,6 +106,14 @@ helrm_status helrm_ctx_memory_in_use(const helrm_ctx *ctx, uint64_t *bytes);
 helrm_status helrm_ctx_synchronize(helrm_ctx *ctx);
 /* Number of library kernels launched so far on this context. */
 helrm_status helrm_ctx_launch_count(const helrm_ctx *ctx, uint64_t *count);
+/* Kernel timing: enable != 0 clears previous records and brackets every
+ * library kernel (each NTT counts as one, both passes) with CUDA events on
+ * the context stream; 0 stops recording.  Adds a little launch overhead. */
+helrm_status helrm_ctx_profile(helrm_ctx *ctx, int enable);
+/* Synchronise and summarise the records: one line per kernel,
+ * "name launches total_ms algorithmic_bytes\n", into buf (len bytes, always
+ * NUL-terminated); *needed (optional) receives the full length + 1. */
+helrm_status helrm_ctx_profile_report(helrm_ctx *ctx, char *buf, uint64_t len, uint64_t *needed);
 
 /* ------------------------------------------------------------- raw NTT (a2) */
 /* In-place negacyclic NTT of n_limbs contiguous limbs of N u64 at d_data;

@@ -142,7 +142,7 @@ helrm_status helrm_ctx_memory_in_use(const helrm_ctx *ctx, uint64_t *bytes)
 
 helrm_status helrm_ctx_synchronize(helrm_ctx *ctx)
 {
-    return guard(ctx_or_null(ctx), [&] { CUDA_CHECK(cudaStreamSynchronize(C(ctx)->stream)); });
+    return guard(ctx_or_null(ctx), [&] { C(ctx)->check_device_errors(); });
 }
 
 helrm_status helrm_ctx_launch_count(const helrm_ctx *ctx, uint64_t *count)
@@ -150,6 +150,56 @@ helrm_status helrm_ctx_launch_count(const helrm_ctx *ctx, uint64_t *count)
     return guard(ctx_or_null(ctx), [&] {
         HCHECK(count, HELRM_E_INVAL, "count is NULL");
         *count = C(ctx)->launches;
+    });
+}
+
+helrm_status helrm_ctx_profile(helrm_ctx *ctx, int enable)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        if (enable) {
+            CUDA_CHECK(cudaStreamSynchronize(c->stream));
+            for (auto &r : c->prof) {
+                c->event_pool.push_back(r.start);
+                c->event_pool.push_back(r.stop);
+            }
+            c->prof.clear();
+        }
+        c->prof_on = enable != 0;
+    });
+}
+
+helrm_status helrm_ctx_profile_report(helrm_ctx *ctx, char *buf, uint64_t len, uint64_t *needed)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        CUDA_CHECK(cudaStreamSynchronize(c->stream));
+        struct Agg {
+            u64 n = 0;
+            double ms = 0, bytes = 0;
+        };
+        std::map<std::string, Agg> agg;
+        for (auto &r : c->prof) {
+            float ms = 0;
+            CUDA_CHECK(cudaEventElapsedTime(&ms, r.start, r.stop));
+            Agg &a = agg[r.name];
+            a.n++;
+            a.ms += ms;
+            a.bytes += r.bytes;
+        }
+        std::string s;
+        char line[256];
+        for (auto &kv : agg) {
+            snprintf(line, sizeof line, "%s %llu %.6f %.0f\n", kv.first.c_str(), (unsigned long long)kv.second.n,
+                     kv.second.ms, kv.second.bytes);
+            s += line;
+        }
+        if (needed) *needed = s.size() + 1;
+        if (buf && len) {
+            size_t n = std::min<size_t>(len - 1, s.size());
+            std::memcpy(buf, s.data(), n);
+            buf[n] = 0;
+        }
     });
 }
 
@@ -217,7 +267,9 @@ helrm_status helrm_encode(helrm_ctx *ctx, const double *slots, uint32_t n_slots,
         Ctx *c = C(ctx);
         HCHECK(out && (slots || n_slots == 0), HELRM_E_INVAL, "NULL argument");
         HCHECK(n_slots <= (u32)c->n_slots, HELRM_E_INVAL, "more values than slots");
-        *out = (helrm_pt *)pt_encode(c, slots, (int)n_slots, c->n_slots, level, false, scale, PT_PLAIN);
+        std::unique_ptr<Plaintext> pt(pt_encode(c, slots, (int)n_slots, c->n_slots, level, false, scale, PT_PLAIN));
+        c->check_device_errors();
+        *out = (helrm_pt *)pt.release();
     });
 }
 

@@ -124,9 +124,28 @@ DevMem &DevMem::operator=(DevMem &&o) noexcept
     return *this;
 }
 
+cudaEvent_t Ctx::take_event()
+{
+    // events are recycled once their pair has been read (prof.clear()).
+    cudaEvent_t e;
+    if (!event_pool.empty()) {
+        e = event_pool.back();
+        event_pool.pop_back();
+        return e;
+    }
+    CUDA_CHECK(cudaEventCreate(&e));
+    return e;
+}
+
 Ctx::~Ctx()
 {
     cudaStreamSynchronize(stream);
+    for (auto &r : prof) {
+        cudaEventDestroy(r.start);
+        cudaEventDestroy(r.stop);
+    }
+    for (auto e : event_pool) cudaEventDestroy(e);
+    modup_ptrs.clear();
     modup_tab.clear();
     moddown_tab.clear();
     rescale_tab.clear();
@@ -140,7 +159,19 @@ Ctx::~Ctx()
     d_pmod_mont = DevMem();
     d_pinv_mont = DevMem();
     d_one_mont = DevMem();
+    d_err = DevMem();
     cudaStreamSynchronize(stream);
+}
+
+void Ctx::check_device_errors()
+{
+    int h = 0;
+    CUDA_CHECK(cudaMemcpyAsync(&h, d_err.ptr, 4, cudaMemcpyDeviceToHost, stream));
+    CUDA_CHECK(cudaStreamSynchronize(stream));
+    if (h) {
+        CUDA_CHECK(cudaMemsetAsync(d_err.ptr, 0, 8, stream));
+        fail(HELRM_E_INVAL, "an encoded coefficient exceeded 2^62 (scale or slot values too large)");
+    }
 }
 
 u64 Ctx::galois(int step) const
@@ -216,6 +247,17 @@ const BConvTable &Ctx::modup_table(int level, int digit)
         }
     }
     return modup_tab[key] = make_bconv(this, sp, sl, dp, dl);
+}
+
+const u64 *const *Ctx::modup_table_ptrs(int level)
+{
+    auto it = modup_ptrs.find(level);
+    if (it != modup_ptrs.end()) return it->second.as<const u64 *const>();
+    std::vector<const u64 *> p;
+    for (int j = 0; j < dnum(level); j++) p.push_back(modup_table(level, j).tab.u());
+    DevMem m;
+    upload(this, m, p.data(), p.size() * sizeof(u64 *));
+    return (modup_ptrs[level] = std::move(m)).as<const u64 *const>();
 }
 
 const BConvTable &Ctx::moddown_table(int level)
@@ -360,6 +402,8 @@ Ctx *ctx_create(const helrm_params *p, int device, void *stream)
     upload(c.get(), c->d_pmod_mont, pmod.data(), 8 * nP);
     upload(c.get(), c->d_pinv_mont, pinv.data(), 8 * nP);
     upload(c.get(), c->d_one_mont, one.data(), 8 * nP);
+    u64 zero = 0;
+    upload(c.get(), c->d_err, &zero, 8);
     return c.release();
 }
 

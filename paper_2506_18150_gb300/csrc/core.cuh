@@ -189,6 +189,7 @@ struct Ctx : Handle {
     DevMem d_pmod_mont;        // u64 [nP]: (P mod q_i) R mod q_i for i <= L, 0 for the P primes
     DevMem d_pinv_mont;        // u64 [nP]: (P^-1 mod q_i) R mod q_i for i <= L
     DevMem d_one_mont;         // u64 [nP]: R mod q_i (the constant 1 in Montgomery form)
+    DevMem d_err;              // int: set by kernels that detect bad data (encoder overflow)
     std::map<std::pair<int, int>, BConvTable> modup_tab;   // (level, digit)
     std::map<int, BConvTable> moddown_tab;                 // level
     std::map<int, DevMem> rescale_tab;                     // level -> constants
@@ -196,6 +197,16 @@ struct Ctx : Handle {
     u64 launches = 0;
     std::string last_error;
     cudaMemPool_t pool = nullptr;
+    // optional per-kernel timing with CUDA events on the context stream
+    struct ProfRec {
+        const char *name;
+        cudaEvent_t start, stop;
+        double bytes;
+    };
+    bool prof_on = false;
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> event_pool;
+    cudaEvent_t take_event();
 
     Ctx() : Handle(KIND_CTX) {}
     ~Ctx() override;
@@ -209,8 +220,31 @@ struct Ctx : Handle {
     void release(void *p, size_t bytes);
     u64 galois(int step) const;
     const BConvTable &modup_table(int level, int digit);
+    std::map<int, DevMem> modup_ptrs;                      // level -> device array of dnum table pointers
+    const u64 *const *modup_table_ptrs(int level);
     const BConvTable &moddown_table(int level);
     const u64 *rescale_table(int level);
+    // synchronise; if a kernel flagged bad data since the last check, clear and raise
+    void check_device_errors();
+};
+
+// Scope timer: when profiling is on, brackets the enclosed launches with a
+// pair of events and the kernel's algorithmic bytes (reads + writes once).
+struct KTimer {
+    Ctx *c;
+    size_t idx = (size_t)-1;
+    KTimer(Ctx *ctx, const char *name, double bytes) : c(ctx)
+    {
+        if (!c->prof_on) return;
+        Ctx::ProfRec r{name, c->take_event(), c->take_event(), bytes};
+        cudaEventRecord(r.start, c->stream);
+        c->prof.push_back(r);
+        idx = c->prof.size() - 1;
+    }
+    ~KTimer()
+    {
+        if (idx != (size_t)-1) cudaEventRecord(c->prof[idx].stop, c->stream);
+    }
 };
 
 // ---------------------------------------------------------------- objects
@@ -268,6 +302,8 @@ struct Ciphertext : Handle {
 namespace k {
 void ntt_fwd(Ctx *c, u64 *data, int n_limbs, LimbMap map);
 void ntt_inv(Ctx *c, u64 *data, int n_limbs, LimbMap map);
+// transform an arbitrary list of limbs (offset in limbs from base, prime id) in one launch pair
+void ntt_list(Ctx *c, u64 *base, const std::vector<std::pair<u32, int>> &limbs, bool inverse);
 void copy(Ctx *c, u64 *dst, const u64 *src, size_t n_words);
 void zero(Ctx *c, u64 *dst, size_t n_words);
 void add(Ctx *c, u64 *out, const u64 *a, const u64 *b, int n_limbs, LimbMap map);
@@ -293,6 +329,8 @@ void sub_mul_scalar(Ctx *c, u64 *out, const u64 *a, const u64 *b, const u64 *d_s
 // centred integers (int64 N) -> residues for n_limbs limbs
 void from_signed(Ctx *c, u64 *out, const i64 *in, int n_limbs, LimbMap map);
 void bconv(Ctx *c, const BConvTable &t, const u64 *in_base, u64 *out_base);
+// ModUp base conversion of every digit at `level` in one launch (digits: [dnum][level+1+K][N])
+void bconv_modup(Ctx *c, int level, const u64 *coef, u64 *digits);
 // d_out[l][i] = sum_j dig_j[l][perm(i)] * key_j(l)[i] for the level-ell QP basis, both
 // polys of the key; if c0 != null, out0 on Q limbs += P * c0[perm(i)]
 void ks_inner_auto(Ctx *c, u64 *out, const u64 *digits, int dnum, const u64 *key, int level,
@@ -323,6 +361,7 @@ void sigmoid(Ctx *c, double *d_p, const double *d_x, int n);
 Ciphertext *new_ct(Ctx *c, int level, double scale);
 void ks_modup(Ctx *c, const u64 *poly_ntt, int level, u64 *digits_out);
 void ks_moddown(Ctx *c, const u64 *qp_ntt, int level, u64 *out_ntt);
+void ks_moddown2(Ctx *c, const u64 *u, int level, u64 *out0, u64 *out1);
 Ciphertext *ct_rescale(Ctx *c, const Ciphertext *a);
 Ciphertext *ct_add(Ctx *c, const Ciphertext *a, const Ciphertext *b, bool subtract = false);
 Ciphertext *ct_add_pt(Ctx *c, const Ciphertext *a, const Plaintext *pt);

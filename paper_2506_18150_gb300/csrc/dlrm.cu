@@ -331,6 +331,7 @@ Model *model_create(Ctx *c, const helrm_model_desc *d)
         }
     }
     HCHECK(lvl == 0, HELRM_E_PARAM, "internal: level schedule does not end at 0");
+    c->check_device_errors();
     return m.release();
 }
 

@@ -136,6 +136,35 @@ __global__ void k_bconv(const u64 *__restrict__ in, u64 *__restrict__ out, const
     }
 }
 
+// All digits of a ModUp in one launch: blockIdx.y = digit j, table tabs[j],
+// output digit j at out + j * out_stride.
+__global__ void k_bconv_multi(const u64 *__restrict__ in, u64 *__restrict__ out, size_t out_stride,
+                              const u64 *const *__restrict__ tabs, int logN)
+{
+    extern __shared__ u64 st[];
+    const u64 *tab = tabs[blockIdx.y];
+    const int ns = (int)tab[0], nd = (int)tab[1];
+    const int words = 2 + 4 * ns + 3 * nd + ns * nd;
+    for (int i = threadIdx.x; i < words; i += blockDim.x) st[i] = tab[i];
+    __syncthreads();
+    const int db = 2 + 4 * ns, hb = db + 3 * nd;
+    const size_t N = (size_t)1 << logN;
+    u64 *o = out + blockIdx.y * out_stride;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+        u64 t[8];
+        for (int s = 0; s < ns; s++) {
+            const u64 *e = st + 2 + 4 * s;
+            t[s] = mont_mul(in[e[3] * N + i], e[2], e[0], e[1]);
+        }
+        for (int k2 = 0; k2 < nd; k2++) {
+            const u64 *e = st + db + 3 * k2;
+            Acc128 acc;
+            for (int s = 0; s < ns; s++) acc.mac(t[s], st[hb + s * nd + k2], e[0]);
+            o[e[2] * N + i] = acc.reduce(e[0], e[1]);
+        }
+    }
+}
+
 // ------------------------------------------------- automorphism + key inner product
 // NTT-domain Galois map for the bit-reversed order: slot i holds a(psi^(2x+1)),
 // x = brv(i); X -> X^k sends it to the slot of exponent (2x+1)k.
@@ -416,16 +445,19 @@ __global__ void k_dec_pick(double *out, const double2 *__restrict__ Y, const int
         out[j] = Y[u_of_slot[j]].x / scale;
 }
 
-// one slot directly: z_j = (1/scale) sum_k m_k cos(pi t_j k / N), t_j = 2 u_j + 1
-__global__ void k_dec_direct(double *out, const u64 *__restrict__ m0, u64 q0, const int *__restrict__ u_of_slot,
-                             double scale, int logN)
+// few slots directly: z_j = (1/scale) sum_k m_k cos(pi t_j k / N), t_j = 2 u_j + 1.
+// Pass 1: block b of slot j sums its chunk of k into part[j][b]; pass 2 adds
+// the DEC_BLOCKS partials in a fixed order (deterministic).
+constexpr int DEC_BLOCKS = 64;
+__global__ void k_dec_direct(double *part, const u64 *__restrict__ m0, u64 q0, const int *__restrict__ u_of_slot,
+                             int logN)
 {
     __shared__ double red[256];
     const int N = 1 << logN;
-    const int j = blockIdx.x;
+    const int j = blockIdx.y;
     const u64 t = 2ull * u_of_slot[j] + 1;
     double acc = 0;
-    for (int k2 = threadIdx.x; k2 < N; k2 += blockDim.x) {
+    for (int k2 = blockIdx.x * blockDim.x + threadIdx.x; k2 < N; k2 += gridDim.x * blockDim.x) {
         const u64 x = m0[k2];
         const double v = x > (q0 - 1) / 2 ? -(double)(q0 - x) : (double)x;
         const u64 e = (t * (u64)k2) & ((2ull << logN) - 1);
@@ -437,7 +469,16 @@ __global__ void k_dec_direct(double *out, const u64 *__restrict__ m0, u64 q0, co
         if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[j] = red[0] / scale;
+    if (threadIdx.x == 0) part[j * DEC_BLOCKS + blockIdx.x] = red[0];
+}
+
+__global__ void k_dec_sum(double *out, const double *__restrict__ part, double scale, int n)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double s = 0;
+    for (int b = 0; b < DEC_BLOCKS; b++) s += part[j * DEC_BLOCKS + b];
+    out[j] = s / scale;
 }
 
 __global__ void k_pack_selector(double *sel, const u64 *__restrict__ idx, const int *__restrict__ tab, int T,
@@ -494,6 +535,7 @@ static void binop(Ctx *c, u64 *out, const u64 *a, const u64 *b, int n_limbs, Lim
 {
     size_t total = (size_t)n_limbs * c->N;
     if (!total) return;
+    KTimer kt(c, "elementwise", (b ? 24.0 : 16.0) * total);
     k_binop<<<grid_for(total), TPB, 0, c->stream>>>(out, a, b, c->logN, total, c->d_pinfo.as<PrimeInfo>(), map, op);
     LAUNCHED(c);
 }
@@ -508,6 +550,7 @@ void tensor(Ctx *c, u64 *d, const u64 *a0, const u64 *a1, const u64 *b0, const u
             bool accumulate)
 {
     size_t total = (size_t)n_limbs * c->N;
+    KTimer kt(c, "tensor", (accumulate ? 10.0 : 7.0) * 8 * total);
     k_tensor<<<grid_for(total), TPB, 0, c->stream>>>(d, a0, a1, b0, b1, c->logN, total, c->d_pinfo.as<PrimeInfo>(),
                                                      map, accumulate ? 1 : 0);
     LAUNCHED(c);
@@ -517,6 +560,7 @@ void mul_scalar_mont(Ctx *c, u64 *out, const u64 *a, const u64 *scal, int n_limb
 {
     size_t total = (size_t)n_limbs * c->N;
     if (!total) return;
+    KTimer kt(c, "elementwise", 16.0 * total);
     k_scalar<<<grid_for(total), TPB, 0, c->stream>>>(out, a, nullptr, scal, c->logN, total,
                                                      c->d_pinfo.as<PrimeInfo>(), map);
     LAUNCHED(c);
@@ -525,6 +569,7 @@ void sub_mul_scalar(Ctx *c, u64 *out, const u64 *a, const u64 *b, const u64 *sca
 {
     size_t total = (size_t)n_limbs * c->N;
     if (!total) return;
+    KTimer kt(c, "elementwise", 24.0 * total);
     k_scalar<<<grid_for(total), TPB, 0, c->stream>>>(out, a, b, scal, c->logN, total,
                                                      c->d_pinfo.as<PrimeInfo>(), map);
     LAUNCHED(c);
@@ -540,13 +585,33 @@ void bconv(Ctx *c, const BConvTable &t, const u64 *in_base, u64 *out_base)
 {
     int words = 2 + 4 * t.n_src + 3 * t.n_dst + t.n_src * t.n_dst;
     HCHECK(t.n_src <= 8, HELRM_E_PARAM, "base conversion supports at most 8 source primes");
+    KTimer kt(c, "bconv", 8.0 * c->N * (t.n_src + t.n_dst));
     k_bconv<<<grid_for(c->N), TPB, words * 8, c->stream>>>(in_base, out_base, t.tab.u(), words, c->logN);
     LAUNCHED(c);
 }
+void bconv_modup(Ctx *c, int level, const u64 *coef, u64 *digits)
+{
+    const int dnum = c->dnum(level), nl = level + 1 + c->K;
+    int max_words = 0, n_src = 0, n_dst = 0;
+    for (int j = 0; j < dnum; j++) {
+        const BConvTable &t = c->modup_table(level, j);
+        max_words = std::max(max_words, 2 + 4 * t.n_src + 3 * t.n_dst + t.n_src * t.n_dst);
+        n_src += t.n_src;
+        n_dst += t.n_dst;
+    }
+    KTimer kt(c, "bconv", 8.0 * c->N * (n_src + n_dst));
+    const u64 *const *tabs = c->modup_table_ptrs(level);
+    dim3 grid(std::max(1u, grid_for(c->N) / (unsigned)dnum), dnum);
+    k_bconv_multi<<<grid, TPB, max_words * 8, c->stream>>>(coef, digits, (size_t)nl * c->N, tabs, c->logN);
+    LAUNCHED(c);
+}
+
 void ks_inner_auto(Ctx *c, u64 *out, const u64 *digits, int dnum, const u64 *key, int level, u64 galois,
                    const u64 *c0, const u64 *d_pmod_mont)
 {
     size_t total = (size_t)(level + 1 + c->K) * c->N;
+    // digits once, both key halves once, c0 once (if added), two output polys
+    KTimer kt(c, "ks_inner_auto", 8.0 * (total * (3.0 * dnum + 2) + (c0 ? (double)(level + 1) * c->N : 0.0)));
     k_ks_inner<<<grid_for(total), TPB, 0, c->stream>>>(out, digits, dnum, key, level, c->L, c->K, c->logN, galois,
                                                        c0, d_pmod_mont, c->d_pinfo.as<PrimeInfo>());
     LAUNCHED(c);
@@ -555,14 +620,17 @@ void automorphism(Ctx *c, u64 *out, const u64 *in, int n_limbs, u64 galois)
 {
     size_t total = (size_t)n_limbs * c->N;
     if (!total) return;
+    KTimer kt(c, "automorphism", 16.0 * total);
     k_automorphism<<<grid_for(total), TPB, 0, c->stream>>>(out, in, c->logN, total, galois);
     LAUNCHED(c);
 }
 void bsgs_mac(Ctx *c, u64 *inner, const u64 *baby, int n_baby, const u64 *const *d_diag_ptrs,
               const int *d_gb_index, int n2, int n1, int limbs, LimbMap map)
 {
-    (void)n_baby;
     size_t smem = (size_t)n1 * 2 * MAC_TC * 8;
+    // n_baby: number of distinct diagonals (non-zero); babies read once, diagonals once,
+    // n2 inner ciphertexts written once
+    KTimer kt(c, "bsgs_mac", 8.0 * limbs * c->N * (2.0 * n1 + (double)n_baby + 2.0 * n2));
     HCHECK(smem <= 200 * 1024, HELRM_E_PARAM, "too many baby steps for the MAC tile");
     if (smem > 48 * 1024)
         CUDA_CHECK(cudaFuncSetAttribute(k_bsgs_mac, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -575,6 +643,7 @@ void rescale_spread(Ctx *c, u64 *out, const u64 *last_coef, int level)
 {
     size_t total = (size_t)level * c->N;
     if (!total) return;
+    KTimer kt(c, "rescale_spread", 8.0 * (total + c->N));
     k_rescale_spread<<<grid_for(total), TPB, 0, c->stream>>>(out, last_coef, c->rescale_table(level), c->nP(),
                                                              c->logN, total, c->d_pinfo.as<PrimeInfo>());
     LAUNCHED(c);
@@ -626,27 +695,29 @@ static void fft(Ctx *c, double2 *buf_a, double2 *buf_b, bool inverse, double2 **
 void encode_slots(Ctx *c, u64 *out, const double *d_slots, int n_valid, int period, double scale, int n_limbs,
                   LimbMap map, i64 *d_coeffs_out)
 {
-    DevMem a(c, (size_t)c->N * sizeof(double2)), b(c, (size_t)c->N * sizeof(double2)), flag(c, 8);
-    CUDA_CHECK(cudaMemsetAsync(flag.ptr, 0, 8, c->stream));
+    DevMem a(c, (size_t)c->N * sizeof(double2)), b(c, (size_t)c->N * sizeof(double2));
+    KTimer kt(c, "encode_fft", 8.0 * c->N * n_limbs);
     k_enc_gather<<<grid_for(c->N), TPB, 0, c->stream>>>(a.as<double2>(), d_slots, c->d_slot_of.as<int>(), n_valid,
                                                         period, c->N);
     LAUNCHED(c);
     double2 *X;
     fft(c, a.as<double2>(), b.as<double2>(), false, &X);
     k_enc_round<<<grid_for(c->N), TPB, 0, c->stream>>>(out, d_coeffs_out, X, scale, c->logN, n_limbs,
-                                                       c->d_pinfo.as<PrimeInfo>(), map, flag.as<int>());
+                                                       c->d_pinfo.as<PrimeInfo>(), map, c->d_err.as<int>());
     LAUNCHED(c);
-    int h = 0;
-    CUDA_CHECK(cudaMemcpyAsync(&h, flag.ptr, 4, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_CHECK(cudaStreamSynchronize(c->stream));
-    HCHECK(!h, HELRM_E_INVAL, "encoded coefficient exceeds 2^62 (scale or values too large)");
+    // an overflow is reported by the next synchronising call (Ctx::check_device_errors)
 }
 
 void decode_limb0(Ctx *c, double *d_out, const u64 *m0, double scale, int n_slots)
 {
     const u64 q0 = c->primes[0];
+    KTimer kt(c, "decode", 8.0 * c->N);
     if (n_slots <= 16) {
-        k_dec_direct<<<n_slots, 256, 0, c->stream>>>(d_out, m0, q0, c->d_u_of_slot.as<int>(), scale, c->logN);
+        DevMem part(c, (size_t)n_slots * DEC_BLOCKS * 8);
+        k_dec_direct<<<dim3(DEC_BLOCKS, n_slots), 256, 0, c->stream>>>(part.as<double>(), m0, q0,
+                                                                       c->d_u_of_slot.as<int>(), c->logN);
+        LAUNCHED(c);
+        k_dec_sum<<<1, 32, 0, c->stream>>>(d_out, part.as<double>(), scale, n_slots);
         LAUNCHED(c);
         return;
     }

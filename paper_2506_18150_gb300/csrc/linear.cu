@@ -92,6 +92,7 @@ PtMatrix *ptmat_prepare(Ctx *c, const double *W, int rows, int cols, int in_pad,
             m->gb.push_back({g, b});
             m->pts.emplace_back(pt_encode(c, v.data(), P, P, level, true, m->pt_scale, PT_MONT));
         }
+    c->check_device_errors();
     m->upload_index();
     return m.release();
 }
@@ -130,7 +131,7 @@ Ciphertext *matvec(Ctx *c, const EvalKey *evk, const PtMatrix *m, const Cipherte
         }
     }
     DevMem inner(c, (size_t)m->n2 * 2 * plane * 8);
-    k::bsgs_mac(c, inner.u(), baby.u(), m->n1, m->d_ptrs.as<const u64 *>(), m->d_gb_index.as<int>(), m->n2, m->n1, nl,
+    k::bsgs_mac(c, inner.u(), baby.u(), (int)m->gb.size(), m->d_ptrs.as<const u64 *>(), m->d_gb_index.as<int>(), m->n2, m->n1, nl,
                 c->qmap(l));
     baby = DevMem();
     DevMem acc(c, 2 * plane * 8), c1q(c, (size_t)nq * N * 8), t(c, 2 * plane * 8), phi(c, plane * 8);
@@ -152,8 +153,7 @@ Ciphertext *matvec(Ctx *c, const EvalKey *evk, const PtMatrix *m, const Cipherte
         k::add(c, acc.u(), acc.u(), t.u(), 2 * nl, qp2);
     }
     std::unique_ptr<Ciphertext> o(new_ct(c, l, in->scale * m->pt_scale));
-    ks_moddown(c, acc.u(), l, o->c0());
-    ks_moddown(c, acc.u() + plane, l, o->c1());
+    ks_moddown2(c, acc.u(), l, o->c0(), o->c1());
     std::unique_ptr<Ciphertext> y(ct_rescale(c, o.get()));
     y->scale = m->out_scale;
     for (int f : m->folds) {

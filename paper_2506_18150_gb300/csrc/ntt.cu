@@ -3,222 +3,230 @@
 // Forward: merged Cooley-Tukey (twiddle psi^brv(m+i) at stage m, block i),
 // standard order in, bit-reversed evaluation order out:
 // ahat[i] = a(psi^(2 brv(i) + 1)).  Inverse: merged Gentleman-Sande with
-// psi^-brv(m+i), then 1/N.  Twiddles use Shoup's precomputed quotient.
+// psi^-brv(m+i), then 1/N.  Twiddles carry Shoup quotients.
 //
-// N = N1 * N2 is split into two shared-memory passes, each reading and
-// writing every limb once: the first log2(N1) stages pair elements N/2..N2
-// apart, so each of the N2 columns (stride N2) is an independent N1-point
-// problem; the remaining log2(N2) stages stay inside contiguous rows of N2.
-// A CTA holds a tile of up to 4096 words (32 KB): C columns x N1 rows for the
-// column pass (C consecutive words per row keep the loads coalesced), or R
-// whole rows for the row pass.  When a whole ciphertext is transformed, the
-// intermediate between the two passes is L2-resident (129 MB L2).
+// N = N1 * N2 runs as two passes, each reading and writing every limb once.
+// The first log2(N1) stages pair elements N/2..N2 apart, so each of the N2
+// columns (stride N2) is an independent N1-point problem.  The remaining
+// log2(N2) stages stay inside contiguous rows of N2.  Within a pass every
+// thread keeps 8 elements in registers and applies up to three stages per
+// round (a radix-8 step); shared memory is used only to regroup elements
+// between rounds, so a 256-point sub-transform costs two barriers.  Loads and
+// stores are coalesced: consecutive threads take consecutive columns (column
+// pass) or consecutive elements of a row (row pass).  A launch takes any list
+// of limbs (offset, prime), so a whole ModUp or ModDown is one transform.
 #include "core.cuh"
 
 namespace helrm {
 namespace {
 
-constexpr int TILE = 4096;
+constexpr int MAX_LIMBS = 256;
+constexpr int TILE = 4096;   // words per CTA (32 KB of data)
 
-struct Split {
-    int logN, logN1, N1, N2, C, R;
+struct LimbList {
+    int n;
+    u32 off[MAX_LIMBS];   // limb offset from the base pointer, in limbs
+    unsigned short pid[MAX_LIMBS];
 };
-Split split_of(int logN)
-{
-    Split s;
-    s.logN = logN;
-    s.logN1 = logN / 2;
-    s.N1 = 1 << s.logN1;
-    s.N2 = 1 << (logN - s.logN1);
-    s.C = std::min(TILE / s.N1, s.N2);
-    s.R = std::min(TILE / s.N2, s.N1);
-    return s;
-}
 
-__global__ void __launch_bounds__(512) k_fwd_cols(u64 *data, int logN, int logN1, int logC,
-                                                   const ulonglong2 *__restrict__ tw_all,
-                                                   const PrimeInfo *__restrict__ pinfo, LimbMap map)
-{
-    extern __shared__ u64 sm[];
-    const int N = 1 << logN, N1 = 1 << logN1, N2 = N >> logN1, C = 1 << logC;
-    const int pid = map.pid(blockIdx.y);
-    const u64 q = pinfo[pid].q;
-    const ulonglong2 *tw = tw_all + (size_t)pid * N;
-    u64 *a = data + (size_t)blockIdx.y * N;
-    const int c0 = blockIdx.x * C;
-    const int tile = N1 * C;
-    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
-        int r = idx >> logC, c = idx & (C - 1);
-        sm[idx] = a[(size_t)r * N2 + c0 + c];
-    }
-    __syncthreads();
-    for (int s = 0; s < logN1; s++) {
-        const int m = 1 << s;
-        const int logt = logN1 - s - 1;
-        for (int b = threadIdx.x; b < tile / 2; b += blockDim.x) {
-            int c = b & (C - 1), pr = b >> logC;
-            int g = pr >> logt, pos = pr & ((1 << logt) - 1);
-            int r = (g << (logt + 1)) + pos;
-            ulonglong2 w = tw[m + g];
-            int i0 = (r << logC) + c, i1 = ((r + (1 << logt)) << logC) + c;
-            u64 u = sm[i0];
-            u64 v = shoup_mul(sm[i1], w.x, w.y, q);
-            sm[i0] = add_mod(u, v, q);
-            sm[i1] = sub_mod(u, v, q);
-        }
-        __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
-        int r = idx >> logC, c = idx & (C - 1);
-        a[(size_t)r * N2 + c0 + c] = sm[idx];
-    }
-}
+__device__ __forceinline__ int pad(int e) { return e + (e >> 4); }
 
-__global__ void __launch_bounds__(512) k_fwd_rows(u64 *data, int logN, int logN1, int logR,
-                                                   const ulonglong2 *__restrict__ tw_all,
-                                                   const PrimeInfo *__restrict__ pinfo, LimbMap map)
-{
-    extern __shared__ u64 sm[];
-    const int N = 1 << logN, logN2 = logN - logN1, N2 = 1 << logN2, R = 1 << logR;
-    const int pid = map.pid(blockIdx.y);
-    const u64 q = pinfo[pid].q;
-    const ulonglong2 *tw = tw_all + (size_t)pid * N;
-    const int r0 = blockIdx.x * R;
-    u64 *a = data + (size_t)blockIdx.y * N + (size_t)r0 * N2;
-    const int tile = R * N2;
-    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) sm[idx] = a[idx];
-    __syncthreads();
-    for (int s = logN1; s < logN; s++) {
-        const int m = 1 << s;
-        const int logt = logN - s - 1;   // t = N / 2m <= N2 / 2
-        for (int b = threadIdx.x; b < tile / 2; b += blockDim.x) {
-            int row = b >> (logN2 - 1), x = b & ((N2 >> 1) - 1);
-            int g = x >> logt, pos = x & ((1 << logt) - 1);
-            int jl = (g << (logt + 1)) + pos;
-            int i = ((r0 + row) << (logN2 - 1 - logt)) + g;
-            ulonglong2 w = tw[m + i];
-            int i0 = (row << logN2) + jl, i1 = i0 + (1 << logt);
-            u64 u = sm[i0];
-            u64 v = shoup_mul(sm[i1], w.x, w.y, q);
-            sm[i0] = add_mod(u, v, q);
-            sm[i1] = sub_mod(u, v, q);
-        }
-        __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) a[idx] = sm[idx];
-}
-
-__global__ void __launch_bounds__(512) k_inv_rows(u64 *data, int logN, int logN1, int logR,
-                                                   const ulonglong2 *__restrict__ tw_all,
-                                                   const PrimeInfo *__restrict__ pinfo, LimbMap map)
-{
-    extern __shared__ u64 sm[];
-    const int N = 1 << logN, logN2 = logN - logN1, N2 = 1 << logN2, R = 1 << logR;
-    const int pid = map.pid(blockIdx.y);
-    const u64 q = pinfo[pid].q;
-    const ulonglong2 *tw = tw_all + (size_t)pid * N;
-    const int r0 = blockIdx.x * R;
-    u64 *a = data + (size_t)blockIdx.y * N + (size_t)r0 * N2;
-    const int tile = R * N2;
-    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) sm[idx] = a[idx];
-    __syncthreads();
-    for (int s = logN - 1; s >= logN1; s--) {
-        const int m = 1 << s;
-        const int logt = logN - s - 1;
-        for (int b = threadIdx.x; b < tile / 2; b += blockDim.x) {
-            int row = b >> (logN2 - 1), x = b & ((N2 >> 1) - 1);
-            int g = x >> logt, pos = x & ((1 << logt) - 1);
-            int jl = (g << (logt + 1)) + pos;
-            int i = ((r0 + row) << (logN2 - 1 - logt)) + g;
-            ulonglong2 w = tw[m + i];
-            int i0 = (row << logN2) + jl, i1 = i0 + (1 << logt);
-            u64 u = sm[i0], v = sm[i1];
-            sm[i0] = add_mod(u, v, q);
-            sm[i1] = shoup_mul(sub_mod(u, v, q), w.x, w.y, q);
-        }
-        __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) a[idx] = sm[idx];
-}
-
-__global__ void __launch_bounds__(512) k_inv_cols(u64 *data, int logN, int logN1, int logC,
+// One pass of the forward transform over sub-transforms of P = 2^LOGP points.
+// COLS: sub-transform g is column c0+g of the limb, elements r*N2 + c.
+// ROWS: sub-transform g is row r0+g, elements (r0+g)*N2 + x.
+// Twiddle of local stage s, local block lb: tw[((bm + seg) << s) + lb], with
+// bm = 1, seg = 0 for the column pass and bm = N1, seg = row for the row pass.
+template <int LOGP, bool COLS, bool INV>
+__global__ void __launch_bounds__(512) k_ntt_pass(u64 *data, int logN, int logG, LimbList list,
                                                    const ulonglong2 *__restrict__ tw_all,
                                                    const ulonglong2 *__restrict__ ninv,
-                                                   const PrimeInfo *__restrict__ pinfo, LimbMap map)
+                                                   const PrimeInfo *__restrict__ pinfo, int scale_out)
 {
+    constexpr int P = 1 << LOGP;
+    constexpr int TPS = P / 8;              // threads per sub-transform
     extern __shared__ u64 sm[];
-    const int N = 1 << logN, N1 = 1 << logN1, N2 = N >> logN1, C = 1 << logC;
-    const int pid = map.pid(blockIdx.y);
+    const int N = 1 << logN;
+    const int logN1 = logN / 2;
+    const int N2 = N >> logN1;
+    const int G = 1 << logG;                // sub-transforms per CTA
+    const int pid = list.pid[blockIdx.y];
     const u64 q = pinfo[pid].q;
     const ulonglong2 *tw = tw_all + (size_t)pid * N;
-    const ulonglong2 ni = ninv[pid];
-    u64 *a = data + (size_t)blockIdx.y * N;
-    const int c0 = blockIdx.x * C;
-    const int tile = N1 * C;
-    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
-        int r = idx >> logC, c = idx & (C - 1);
-        sm[idx] = a[(size_t)r * N2 + c0 + c];
+    u64 *a = data + (size_t)list.off[blockIdx.y] * N;
+    const int tid = threadIdx.x;
+    // thread -> (sub-transform g, lane tt); for COLS, g varies fastest so a
+    // warp reads consecutive columns of one row.
+    int g, tt;
+    if (COLS) {
+        g = tid & (G - 1);
+        tt = tid >> logG;
+    } else {
+        tt = tid & (TPS - 1);
+        g = tid / TPS;
     }
-    __syncthreads();
-    for (int s = logN1 - 1; s >= 0; s--) {
-        const int m = 1 << s;
-        const int logt = logN1 - s - 1;
-        for (int b = threadIdx.x; b < tile / 2; b += blockDim.x) {
-            int c = b & (C - 1), pr = b >> logC;
-            int g = pr >> logt, pos = pr & ((1 << logt) - 1);
-            int r = (g << (logt + 1)) + pos;
-            ulonglong2 w = tw[m + g];
-            int i0 = (r << logC) + c, i1 = ((r + (1 << logt)) << logC) + c;
-            u64 u = sm[i0], v = sm[i1];
-            sm[i0] = add_mod(u, v, q);
-            sm[i1] = shoup_mul(sub_mod(u, v, q), w.x, w.y, q);
+    const int gglob = blockIdx.x * G + g;   // column index (COLS) or row index (ROWS)
+    const int bm = COLS ? 1 : (1 << logN1);
+    const int seg = COLS ? 0 : gglob;
+    auto gaddr = [&](int e) -> size_t {
+        return COLS ? (size_t)e * N2 + gglob : (size_t)gglob * N2 + e;
+    };
+    auto saddr = [&](int e) -> int { return COLS ? pad(e * G + g) : pad(g * P + e); };
+
+    u64 v[8];
+    // rounds of up to three stages; forward goes first-to-last, inverse last-to-first
+    constexpr int NR = (LOGP + 2) / 3;
+    _Pragma("unroll") for (int rr = 0; rr < NR; rr++) {
+        const int rho = INV ? NR - 1 - rr : rr;
+        const int s0 = 3 * rho;
+        const int r = (s0 + 3 <= LOGP) ? 3 : LOGP - s0;
+        const int T = P >> (s0 + r);        // spacing of a group's members
+        const int gs = 1 << r;              // group size
+        const int ng = 8 / gs;              // groups per thread
+        // element index of member k of this thread's group qg
+        auto elem = [&](int qg, int k) {
+            const int gam = tt + qg * TPS;  // group index
+            const int blk = gam / T, boff = gam % T;
+            return blk * (T * gs) + boff + k * T;
+        };
+        if (rr == 0) {
+            _Pragma("unroll") for (int qg = 0; qg < ng; qg++)
+                _Pragma("unroll") for (int k = 0; k < gs; k++) v[qg * gs + k] = a[gaddr(elem(qg, k))];
+        } else {
+            __syncthreads();
+            _Pragma("unroll") for (int qg = 0; qg < ng; qg++)
+                _Pragma("unroll") for (int k = 0; k < gs; k++) v[qg * gs + k] = sm[saddr(elem(qg, k))];
         }
-        __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
-        int r = idx >> logC, c = idx & (C - 1);
-        a[(size_t)r * N2 + c0 + c] = shoup_mul(sm[idx], ni.x, ni.y, q);
+        _Pragma("unroll") for (int qg = 0; qg < ng; qg++) {
+            u64 *x = v + qg * gs;
+            const int e0 = elem(qg, 0);
+            if (!INV) {
+                _Pragma("unroll") for (int u = 0; u < r; u++) {
+                    const int s = s0 + u;
+                    const int half = gs >> (u + 1);
+                    _Pragma("unroll") for (int k1 = 0; k1 < gs; k1++) {
+                        if (k1 & half) continue;
+                        const int lb = (e0 + k1 * T) >> (LOGP - s);
+                        const ulonglong2 w = tw[((bm + seg) << s) + lb];
+                        const u64 x0 = x[k1];
+                        const u64 x1 = shoup_mul(x[k1 + half], w.x, w.y, q);
+                        x[k1] = add_mod(x0, x1, q);
+                        x[k1 + half] = sub_mod(x0, x1, q);
+                    }
+                }
+            } else {
+                _Pragma("unroll") for (int u = r - 1; u >= 0; u--) {
+                    const int s = s0 + u;
+                    const int half = gs >> (u + 1);
+                    _Pragma("unroll") for (int k1 = 0; k1 < gs; k1++) {
+                        if (k1 & half) continue;
+                        const int lb = (e0 + k1 * T) >> (LOGP - s);
+                        const ulonglong2 w = tw[((bm + seg) << s) + lb];
+                        const u64 x0 = x[k1], x1 = x[k1 + half];
+                        x[k1] = add_mod(x0, x1, q);
+                        x[k1 + half] = shoup_mul(sub_mod(x0, x1, q), w.x, w.y, q);
+                    }
+                }
+            }
+        }
+        if (rr + 1 < NR) {
+            if (rr > 0) __syncthreads();    // everyone has read the previous round's layout
+            _Pragma("unroll") for (int qg = 0; qg < ng; qg++)
+                _Pragma("unroll") for (int k = 0; k < gs; k++) sm[saddr(elem(qg, k))] = v[qg * gs + k];
+        } else {
+            ulonglong2 ni = make_ulonglong2(0, 0);
+            if (scale_out) ni = ninv[pid];
+            _Pragma("unroll") for (int qg = 0; qg < ng; qg++)
+                _Pragma("unroll") for (int k = 0; k < gs; k++) {
+                    u64 y = v[qg * gs + k];
+                    if (scale_out) y = shoup_mul(y, ni.x, ni.y, q);
+                    a[gaddr(elem(qg, k))] = y;
+                }
+        }
     }
 }
 
-int ilog2(int x)
+template <int LOGP, bool COLS, bool INV>
+void launch_pass(Ctx *c, u64 *data, const LimbList &ll, int n_sub, int scale_out)
 {
-    int r = 0;
-    while ((1 << r) < x) r++;
-    return r;
+    constexpr int P = 1 << LOGP;
+    // sub-transforms per CTA: as many as fit a 4096-word tile, fewer when the
+    // batch is small so the grid still covers the SMs (columns keep >= 4
+    // consecutive words per row for coalescing)
+    int G = std::min(TILE / P, n_sub);
+    const int gmin = COLS ? 4 : 1;
+    while (G > gmin && (long)(n_sub / G) * ll.n < 2 * 152) G /= 2;
+    int logG = 0;
+    while ((1 << logG) < G) logG++;
+    const int threads = G * P / 8;
+    const size_t smem = (size_t)(G * P + (G * P >> 4) + 1) * 8;
+    dim3 grid(n_sub / G, ll.n);
+    const ulonglong2 *tw = INV ? c->d_tw_inv.as<ulonglong2>() : c->d_tw_fwd.as<ulonglong2>();
+    k_ntt_pass<LOGP, COLS, INV><<<grid, threads, smem, c->stream>>>(data, c->logN, logG, ll, tw,
+                                                                   c->d_ninv.as<ulonglong2>(),
+                                                                   c->d_pinfo.as<PrimeInfo>(), scale_out);
+}
+
+template <bool COLS, bool INV>
+void dispatch(Ctx *c, int logp, u64 *data, const LimbList &ll, int n_sub, int scale_out)
+{
+    switch (logp) {
+    case 5: launch_pass<5, COLS, INV>(c, data, ll, n_sub, scale_out); break;
+    case 6: launch_pass<6, COLS, INV>(c, data, ll, n_sub, scale_out); break;
+    case 7: launch_pass<7, COLS, INV>(c, data, ll, n_sub, scale_out); break;
+    case 8: launch_pass<8, COLS, INV>(c, data, ll, n_sub, scale_out); break;
+    default: fail(HELRM_E_PARAM, "unsupported NTT size");
+    }
+}
+
+void run(Ctx *c, u64 *data, const std::vector<std::pair<u32, int>> &limbs, bool inverse)
+{
+    if (limbs.empty()) return;
+    const int logN = c->logN, logN1 = logN / 2, logN2 = logN - logN1;
+    const int N1 = 1 << logN1, N2 = 1 << logN2;
+    KTimer kt(c, "ntt", 16.0 * c->N * limbs.size());   // algorithmic: each limb read and written once
+    for (size_t b = 0; b < limbs.size(); b += MAX_LIMBS) {
+        LimbList ll;
+        ll.n = (int)std::min<size_t>(MAX_LIMBS, limbs.size() - b);
+        for (int i = 0; i < ll.n; i++) {
+            ll.off[i] = limbs[b + i].first;
+            ll.pid[i] = (unsigned short)limbs[b + i].second;
+        }
+        if (!inverse) {
+            dispatch<true, false>(c, logN1, data, ll, N2, 0);
+            dispatch<false, false>(c, logN2, data, ll, N1, 0);
+        } else {
+            dispatch<false, true>(c, logN2, data, ll, N1, 0);
+            dispatch<true, true>(c, logN1, data, ll, N2, 1);
+        }
+        c->launches += 2;
+        CUDA_CHECK(cudaGetLastError());
+    }
 }
 
 }  // namespace
 
 namespace k {
 
+void ntt_list(Ctx *c, u64 *base, const std::vector<std::pair<u32, int>> &limbs, bool inverse)
+{
+    run(c, base, limbs, inverse);
+}
+
+static std::vector<std::pair<u32, int>> from_map(int n_limbs, LimbMap map)
+{
+    std::vector<std::pair<u32, int>> v(n_limbs);
+    for (int l = 0; l < n_limbs; l++) v[l] = {(u32)l, map.pid(l)};
+    return v;
+}
+
 void ntt_fwd(Ctx *c, u64 *data, int n_limbs, LimbMap map)
 {
-    if (n_limbs <= 0) return;
-    Split s = split_of(c->logN);
-    int tc = s.N1 * s.C, tr = s.R * s.N2;
-    dim3 gc(s.N2 / s.C, n_limbs), gr(s.N1 / s.R, n_limbs);
-    k_fwd_cols<<<gc, std::min(512, tc / 2), tc * 8, c->stream>>>(
-        data, s.logN, s.logN1, ilog2(s.C), c->d_tw_fwd.as<ulonglong2>(), c->d_pinfo.as<PrimeInfo>(), map);
-    k_fwd_rows<<<gr, std::min(512, tr / 2), tr * 8, c->stream>>>(
-        data, s.logN, s.logN1, ilog2(s.R), c->d_tw_fwd.as<ulonglong2>(), c->d_pinfo.as<PrimeInfo>(), map);
-    c->launches += 2;
-    CUDA_CHECK(cudaGetLastError());
+    if (n_limbs > 0) run(c, data, from_map(n_limbs, map), false);
 }
 
 void ntt_inv(Ctx *c, u64 *data, int n_limbs, LimbMap map)
 {
-    if (n_limbs <= 0) return;
-    Split s = split_of(c->logN);
-    int tc = s.N1 * s.C, tr = s.R * s.N2;
-    dim3 gc(s.N2 / s.C, n_limbs), gr(s.N1 / s.R, n_limbs);
-    k_inv_rows<<<gr, std::min(512, tr / 2), tr * 8, c->stream>>>(
-        data, s.logN, s.logN1, ilog2(s.R), c->d_tw_inv.as<ulonglong2>(), c->d_pinfo.as<PrimeInfo>(), map);
-    k_inv_cols<<<gc, std::min(512, tc / 2), tc * 8, c->stream>>>(
-        data, s.logN, s.logN1, ilog2(s.C), c->d_tw_inv.as<ulonglong2>(), c->d_ninv.as<ulonglong2>(),
-        c->d_pinfo.as<PrimeInfo>(), map);
-    c->launches += 2;
-    CUDA_CHECK(cudaGetLastError());
+    if (n_limbs > 0) run(c, data, from_map(n_limbs, map), true);
 }
 
 }  // namespace k

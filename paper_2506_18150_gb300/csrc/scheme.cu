@@ -37,14 +37,32 @@ void ks_modup(Ctx *c, const u64 *poly, int level, u64 *digits)
     DevMem coef(c, (size_t)nq * N * 8);
     k::copy(c, coef.u(), poly, (size_t)nq * N);
     k::ntt_inv(c, coef.u(), nq, c->qmap(level));
+    k::bconv_modup(c, level, coef.u(), digits);
+    std::vector<std::pair<u32, int>> targets;   // every converted limb of every digit
+    const LimbMap m = c->qmap(level);
     for (int j = 0; j < c->dnum(level); j++) {
         u64 *d = digits + (size_t)j * nl * N;
         const int lo = c->digit_lo(j), hi = c->digit_hi(j, level);
-        k::bconv(c, c->modup_table(level, j), coef.u(), d);
-        k::ntt_fwd(c, d, lo, c->qmap(level, 0));
-        k::ntt_fwd(c, d + (size_t)hi * N, nl - hi, c->qmap(level, hi));
         k::copy(c, d + (size_t)lo * N, poly + (size_t)lo * N, (size_t)(hi - lo) * N);
+        for (int l = 0; l < nl; l++)
+            if (l < lo || l >= hi) targets.push_back({(u32)(j * nl + l), m.pid(l)});
     }
+    k::ntt_list(c, digits, targets, false);
+}
+
+// ModDown of both halves of a QP ciphertext u = [2][nl][N] into out0, out1.
+void ks_moddown2(Ctx *c, const u64 *u, int level, u64 *out0, u64 *out1)
+{
+    const int N = c->N, nq = level + 1, K = c->K, nl = nq + K;
+    DevMem pc(c, (size_t)2 * K * N * 8), y(c, (size_t)2 * nq * N * 8);
+    k::copy(c, pc.u(), u + (size_t)nq * N, (size_t)K * N);
+    k::copy(c, pc.u() + (size_t)K * N, u + (size_t)(nl + nq) * N, (size_t)K * N);
+    k::ntt_inv(c, pc.u(), 2 * K, c->qmap(level, nq, K));
+    k::bconv(c, c->moddown_table(level), pc.u(), y.u());
+    k::bconv(c, c->moddown_table(level), pc.u() + (size_t)K * N, y.u() + (size_t)nq * N);
+    k::ntt_fwd(c, y.u(), 2 * nq, c->qmap(level, 0, nq));
+    k::sub_mul_scalar(c, out0, u, y.u(), c->d_pinv_mont.u(), nq, c->qmap(level));
+    k::sub_mul_scalar(c, out1, u + (size_t)nl * N, y.u() + (size_t)nq * N, c->d_pinv_mont.u(), nq, c->qmap(level));
 }
 
 void ks_moddown(Ctx *c, const u64 *u, int level, u64 *out)
@@ -156,8 +174,7 @@ void ct_rotate_hoisted(Ctx *c, const EvalKey *evk, const Ciphertext *a, const st
             k::copy(c, o->data.u(), a->data.u(), (size_t)2 * nq * N);
         } else {
             k::ks_inner_auto(c, u.u(), digits.u(), dnum, keys[s]->data.u(), l, g, nullptr, nullptr);
-            ks_moddown(c, u.u(), l, t.u());
-            ks_moddown(c, u.u() + (size_t)nl * N, l, o->c1());
+            ks_moddown2(c, u.u(), l, t.u(), o->c1());
             k::automorphism(c, o->c0(), a->c0(), nq, g);
             k::add(c, o->c0(), o->c0(), t.u(), nq, c->qmap(l));
         }
@@ -186,14 +203,12 @@ Ciphertext *ct_relin(Ctx *c, const EvalKey *evk, const u64 *d012, int level, dou
     HCHECK(evk->relin, HELRM_E_NOKEY, "no relinearisation key");
     const int N = c->N, nq = level + 1, nl = nq + c->K, dnum = c->dnum(level);
     const size_t plane = (size_t)nq * N;
-    DevMem digits(c, (size_t)dnum * nl * N * 8), u(c, (size_t)2 * nl * N * 8), t(c, plane * 8);
+    DevMem digits(c, (size_t)dnum * nl * N * 8), u(c, (size_t)2 * nl * N * 8);
     ks_modup(c, d012 + 2 * plane, level, digits.u());
     k::ks_inner_auto(c, u.u(), digits.u(), dnum, evk->relin->data.u(), level, 1, nullptr, nullptr);
     std::unique_ptr<Ciphertext> o(new_ct(c, level, scale));
-    ks_moddown(c, u.u(), level, t.u());
-    k::add(c, o->c0(), d012, t.u(), nq, c->qmap(level));
-    ks_moddown(c, u.u() + (size_t)nl * N, level, t.u());
-    k::add(c, o->c1(), d012 + plane, t.u(), nq, c->qmap(level));
+    ks_moddown2(c, u.u(), level, o->c0(), o->c1());
+    k::add(c, o->data.u(), o->data.u(), d012, 2 * nq, c->qmap(level, 0, nq));   // (d0, d1) + ModDown(u)
     return o.release();
 }
 
@@ -272,7 +287,7 @@ void pt_export_signed(Ctx *c, const Plaintext *pt, i64 *h_out)
     k::ntt_inv(c, t.u(), 1, c->qmap(0));
     std::vector<u64> h(N);
     CUDA_CHECK(cudaMemcpyAsync(h.data(), t.ptr, (size_t)N * 8, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    c->check_device_errors();
     const u64 q0 = c->primes[0];
     for (int i = 0; i < N; i++) h_out[i] = h[i] > (q0 - 1) / 2 ? -(i64)(q0 - h[i]) : (i64)h[i];
 }
@@ -430,7 +445,7 @@ void decrypt_slots(Ctx *c, const SecretKey *sk, const Ciphertext *ct, double *h_
         k::decode_limb0(c, d.as<double>(), m.u(), ct->scale, n_slots);
         CUDA_CHECK(cudaMemcpyAsync(h_out, d.ptr, (size_t)n_slots * 8, cudaMemcpyDeviceToHost, c->stream));
     }
-    CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    c->check_device_errors();
 }
 
 }  // namespace helrm

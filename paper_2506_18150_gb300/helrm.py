@@ -104,6 +104,9 @@ _SIGS = {
     "helrm_infer": [_vp, _vp, _vp, _vp, _vp, _pp],
     "helrm_decrypt_logit": [_vp, _vp, _vp, _dp, _dp],
     "helrm_infer_e2e": [_vp, _vp, _vp, _vp, _dp, _u64p, C.c_uint32, C.c_uint64, _dp, _dp],
+    "helrm_infer_e2e_device": [_vp, _vp, _vp, _vp, _vp, _vp, C.c_uint32, C.c_uint64, _vp, _vp],
+    "helrm_ctx_profile": [_vp, C.c_int],
+    "helrm_ctx_profile_report": [_vp, C.c_char_p, C.c_uint64, _u64p],
 }
 
 
@@ -486,6 +489,31 @@ def helrm_decrypt_logit(ctx, sk, ct):
     lg, pr = C.c_double(), C.c_double()
     _check(ctx, lib().helrm_decrypt_logit(ctx.ptr, sk.ptr, ct.ptr, C.byref(lg), C.byref(pr)))
     return lg.value, pr.value
+
+
+def helrm_infer_e2e_device(ctx, sk, evk, m, d_dense: int, d_indices: int, n_queries: int, seed: int,
+                           d_logits: int, d_probs: int = 0):
+    """All buffers are device pointers (ints); stream-ordered, no synchronisation."""
+    _check(ctx, lib().helrm_infer_e2e_device(ctx.ptr, sk.ptr, evk.ptr, m.ptr, C.c_void_p(d_dense),
+                                             C.c_void_p(d_indices), n_queries, seed, C.c_void_p(d_logits),
+                                             C.c_void_p(d_probs or None)))
+
+
+def helrm_ctx_profile(ctx, enable: bool):
+    _check(ctx, lib().helrm_ctx_profile(ctx.ptr, int(enable)))
+
+
+def helrm_ctx_profile_report(ctx):
+    """{kernel name: (launches, total_ms, algorithmic_bytes)}"""
+    need = C.c_uint64(0)
+    _check(ctx, lib().helrm_ctx_profile_report(ctx.ptr, None, 0, C.byref(need)))
+    buf = C.create_string_buffer(need.value + 1)
+    _check(ctx, lib().helrm_ctx_profile_report(ctx.ptr, buf, need.value + 1, None))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, n, ms, b = line.split()
+        out[name] = (int(n), float(ms), float(b))
+    return out
 
 
 def helrm_infer_e2e(ctx, sk, evk, m, dense, indices, seed: int):

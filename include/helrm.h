@@ -305,6 +305,28 @@ helrm_status helrm_infer_e2e_device(helrm_ctx *ctx, const helrm_sk *sk, const he
                                     const helrm_model *m, const double *d_dense, const uint64_t *d_indices,
                                     uint32_t n_queries, uint64_t seed, double *d_logits, double *d_probs);
 
+/* ------------------------------------------------- allocation-free rescale */
+/* The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory: a host whose GPU memory is owned by another
+ * allocator (for example a framework's caching pool that has reserved the
+ * device), a real-time serving loop that must not take the implicit
+ * synchronisation of an allocation, or code that may only touch buffers it
+ * was handed.  It computes what helrm_rescale computes and calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *   d_in    device, n_polys x (level+1) x N u64, NTT domain (the layout of the
+ *           library's ciphertexts: c0 limbs then c1 limbs for n_polys = 2);
+ *   d_out   device, n_polys x level x N u64, NTT domain; must not overlap d_in.
+ * Its one scratch buffer is a static device array of 2 x 65536 u64 words
+ * (1 MiB) that every GPU loading the library holds until the process exits;
+ * n_polys x N above that limit is rejected with HELRM_E_INVAL.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress), so
+ * make that first call before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (different streams or contexts on the same
+ * device) race on it.  Work is ordered on the context's stream; the call does
+ * not synchronise. */
+helrm_status helrm_rescale_noalloc(helrm_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int32_t level,
+                                   uint32_t n_polys);
+
 /* --------------------------------------------------------------- misc */
 /* Release any handle (context last; handles must not outlive their context). */
 void helrm_free(void *handle);

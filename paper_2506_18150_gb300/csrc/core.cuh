@@ -302,6 +302,8 @@ struct Ciphertext : Handle {
 namespace k {
 void ntt_fwd(Ctx *c, u64 *data, int n_limbs, LimbMap map);
 void ntt_inv(Ctx *c, u64 *data, int n_limbs, LimbMap map);
+// same as ntt_fwd / ntt_inv, with the launch list built on the stack (no heap use)
+void ntt_map_noheap(Ctx *c, u64 *data, int n_limbs, LimbMap map, bool inverse);
 // transform an arbitrary list of limbs (offset in limbs from base, prime id) in one launch pair
 void ntt_list(Ctx *c, u64 *base, const std::vector<std::pair<u32, int>> &limbs, bool inverse);
 void copy(Ctx *c, u64 *dst, const u64 *src, size_t n_words);

@@ -212,6 +212,38 @@ void ntt_list(Ctx *c, u64 *base, const std::vector<std::pair<u32, int>> &limbs, 
     run(c, base, limbs, inverse);
 }
 
+// Contiguous limbs described by a LimbMap; the launch list is built on the
+// stack (no heap or device allocation on this path).
+static void run_map(Ctx *c, u64 *data, int n_limbs, LimbMap map, bool inverse)
+{
+    if (n_limbs <= 0) return;
+    const int logN = c->logN, logN1 = logN / 2, logN2 = logN - logN1;
+    const int N1 = 1 << logN1, N2 = 1 << logN2;
+    KTimer kt(c, "ntt", 16.0 * c->N * n_limbs);
+    for (int b = 0; b < n_limbs; b += MAX_LIMBS) {
+        LimbList ll;
+        ll.n = std::min(MAX_LIMBS, n_limbs - b);
+        for (int i = 0; i < ll.n; i++) {
+            ll.off[i] = (u32)(b + i);
+            ll.pid[i] = (unsigned short)map.pid(b + i);
+        }
+        if (!inverse) {
+            dispatch<true, false>(c, logN1, data, ll, N2, 0);
+            dispatch<false, false>(c, logN2, data, ll, N1, 0);
+        } else {
+            dispatch<false, true>(c, logN2, data, ll, N1, 0);
+            dispatch<true, true>(c, logN1, data, ll, N2, 1);
+        }
+        c->launches += 2;
+        CUDA_CHECK(cudaGetLastError());
+    }
+}
+
+void ntt_map_noheap(Ctx *c, u64 *data, int n_limbs, LimbMap map, bool inverse)
+{
+    run_map(c, data, n_limbs, map, inverse);
+}
+
 static std::vector<std::pair<u32, int>> from_map(int n_limbs, LimbMap map)
 {
     std::vector<std::pair<u32, int>> v(n_limbs);

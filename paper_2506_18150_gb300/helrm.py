@@ -105,6 +105,7 @@ _SIGS = {
     "helrm_decrypt_logit": [_vp, _vp, _vp, _dp, _dp],
     "helrm_infer_e2e": [_vp, _vp, _vp, _vp, _dp, _u64p, C.c_uint32, C.c_uint64, _dp, _dp],
     "helrm_infer_e2e_device": [_vp, _vp, _vp, _vp, _vp, _vp, C.c_uint32, C.c_uint64, _vp, _vp],
+    "helrm_rescale_noalloc": [_vp, _vp, _vp, C.c_int32, C.c_uint32],
     "helrm_ctx_profile": [_vp, C.c_int],
     "helrm_ctx_profile_report": [_vp, C.c_char_p, C.c_uint64, _u64p],
 }
@@ -497,6 +498,12 @@ def helrm_infer_e2e_device(ctx, sk, evk, m, d_dense: int, d_indices: int, n_quer
     _check(ctx, lib().helrm_infer_e2e_device(ctx.ptr, sk.ptr, evk.ptr, m.ptr, C.c_void_p(d_dense),
                                              C.c_void_p(d_indices), n_queries, seed, C.c_void_p(d_logits),
                                              C.c_void_p(d_probs or None)))
+
+
+def helrm_rescale_noalloc(ctx, d_in: int, d_out: int, level: int, n_polys: int):
+    """Rescale without allocating: device pointers in (n_polys x (level+1) x N) and
+    out (n_polys x level x N), NTT domain; scratch is a static 1 MiB device array."""
+    _check(ctx, lib().helrm_rescale_noalloc(ctx.ptr, C.c_void_p(d_in), C.c_void_p(d_out), level, n_polys))
 
 
 def helrm_ctx_profile(ctx, enable: bool):

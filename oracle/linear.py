@@ -16,8 +16,8 @@ D = min(in_pad, out_pad) extended diagonals
     diag_i[j] = W[j mod out_pad, (j + i) mod in_pad],   j < n,  i < D,
 
 and, when in_pad > out_pad, rotate-and-add folds by in_pad/2, ..., out_pad.
-The result is W x replicated with period out_pad.  BSGS split: n1 = the
-smallest power of two with n1^2 >= D, n2 = D / n1; i = g*n1 + b and
+The result is W x replicated with period out_pad.  BSGS split: n1 =
+min(D, 64), n2 = D / n1 (see bsgs_split); i = g*n1 + b and
 diag'_{g,b} = rot(diag_{g n1 + b}, -g n1).  All-zero diagonals are skipped,
 which changes no result (their products are exactly zero).
 """
@@ -35,10 +35,16 @@ def pow2ceil(x: int) -> int:
     return 1 << (x - 1).bit_length()
 
 
+BABY_MAX = 64
+
+
 def bsgs_split(D: int):
-    n1 = 1
-    while n1 * n1 < D:
-        n1 *= 2
+    """n1 = min(D, 64) baby steps, n2 = D / n1 giant steps.
+
+    A hoisted baby step costs one key inner product; a giant step costs a
+    ModDown and a ModUp as well, so the split favours baby steps (the paper
+    fixes only that BSGS needs O(sqrt n) rotations, not the split)."""
+    n1 = min(D, BABY_MAX)
     return n1, D // n1
 
 

@@ -254,6 +254,140 @@ __global__ void __launch_bounds__(MAC_TC) k_bsgs_mac(u64 *__restrict__ inner, co
     }
 }
 
+// Few giant steps (n2 <= 8): one thread per (limb, coefficient) keeps all n2
+// pairs of 128-bit accumulators in registers and streams every baby step and
+// every diagonal once.
+template <int N2>
+__global__ void __launch_bounds__(256) k_bsgs_mac_reg(u64 *__restrict__ inner, const u64 *__restrict__ baby,
+                                                      const u64 *const *__restrict__ diag,
+                                                      const int *__restrict__ gb, int n1, int nl, int logN,
+                                                      const PrimeInfo *__restrict__ pinfo, LimbMap map)
+{
+    __shared__ int sgb[64 * 8];
+    for (int t = threadIdx.x; t < n1 * N2; t += blockDim.x) sgb[t] = gb[t];
+    __syncthreads();
+    const size_t N = (size_t)1 << logN;
+    const size_t plane = (size_t)nl * N;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const PrimeInfo pi = pinfo[map.pid((int)(idx >> logN))];
+        Acc128 a0[N2], a1[N2];
+        for (int b = 0; b < n1; b++) {
+            bool need = false;
+#pragma unroll
+            for (int g = 0; g < N2; g++) need |= sgb[g * n1 + b] >= 0;
+            if (!need) continue;
+            const u64 *bb = baby + (size_t)b * 2 * plane + idx;
+            const u64 b0 = bb[0], b1 = bb[plane];
+#pragma unroll
+            for (int g = 0; g < N2; g++) {
+                const int di = sgb[g * n1 + b];
+                if (di < 0) continue;
+                const u64 d = diag[di][idx];
+                a0[g].mac(b0, d, pi.q);
+                a1[g].mac(b1, d, pi.q);
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < N2; g++) {
+            bool any = false;
+            for (int b = 0; b < n1; b++) any |= sgb[g * n1 + b] >= 0;
+            if (!any) continue;
+            u64 *o = inner + (size_t)g * 2 * plane + idx;
+            o[0] = a0[g].reduce(pi.q, pi.qinv);
+            o[plane] = a1[g].reduce(pi.q, pi.qinv);
+        }
+    }
+}
+
+// Baby steps fused into the MAC: for every (limb, coefficient) and every baby
+// step b, the hoisted rotation phi_{5^b} of the ModUp digits times key b (plus
+// P phi(c0) on the Q limbs) is formed in registers and multiplied at once into
+// the n2 giant-step accumulators.  Keys and diagonals stream from HBM once;
+// the digits (dnum x (l+1+K) x N words) stay in L2; no baby buffer exists.
+struct BabyKeys {
+    const u64 *key[64];   // key of baby step b (nullptr for b = 0 or unused)
+    u64 gal[64];          // its Galois element
+};
+
+template <int N2>
+__global__ void __launch_bounds__(256, 3) k_bsgs_fused(u64 *__restrict__ inner, const u64 *__restrict__ dig, int dnum,
+                                                    const u64 *__restrict__ c0, const u64 *__restrict__ c1,
+                                                    BabyKeys bk, const u64 *const *__restrict__ diag,
+                                                    const int *__restrict__ gb, int n1, int level, int L, int K,
+                                                    int logN, const u64 *__restrict__ pmod,
+                                                    const PrimeInfo *__restrict__ pinfo)
+{
+    __shared__ int sgb[64 * 8];
+    __shared__ int sneed[64], sany[8];
+    for (int t = threadIdx.x; t < n1 * N2; t += blockDim.x) sgb[t] = gb[t];
+    __syncthreads();
+    if (threadIdx.x < n1) {
+        int need = 0;
+        for (int g = 0; g < N2; g++) need |= sgb[g * n1 + threadIdx.x] >= 0;
+        sneed[threadIdx.x] = need;
+    }
+    if (threadIdx.x < N2) {
+        int any = 0;
+        for (int b = 0; b < n1; b++) any |= sgb[threadIdx.x * n1 + b] >= 0;
+        sany[threadIdx.x] = any;
+    }
+    __syncthreads();
+    const size_t N = (size_t)1 << logN;
+    const int nl = level + 1 + K, nP = L + 1 + K;
+    const size_t plane = (size_t)nl * N;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int l = (int)(idx >> logN);
+        const int i = (int)(idx & (N - 1));
+        const bool qlimb = l <= level;
+        const int pid = qlimb ? l : L + 1 + (l - level - 1);
+        const PrimeInfo pi = pinfo[pid];
+        const u64 pm = pmod[pid];
+        // 64-bit accumulators: each product reduced on the spot (REDC is linear,
+        // so this equals one reduction of the 128-bit sum) -- fewer registers,
+        // more warps in flight for the memory stream
+        u64 a0[N2], a1[N2];
+#pragma unroll
+        for (int g = 0; g < N2; g++) a0[g] = a1[g] = 0;
+        for (int b = 0; b < n1; b++) {
+            if (!sneed[b]) continue;
+            u64 v0, v1;
+            if (b == 0) {   // (P c0, P c1): P mod q on the Q limbs, 0 on the P limbs
+                v0 = qlimb ? mont_mul(c0[(size_t)l * N + i], pm, pi.q, pi.qinv) : 0;
+                v1 = qlimb ? mont_mul(c1[(size_t)l * N + i], pm, pi.q, pi.qinv) : 0;
+            } else {
+                const int src = auto_src(i, logN, bk.gal[b]);
+                const u64 *key = bk.key[b];
+                Acc128 t0, t1;
+                for (int j = 0; j < dnum; j++) {
+                    const u64 d = dig[((size_t)j * nl + l) * N + src];
+                    t0.mac(d, key[((size_t)(2 * j) * nP + pid) * N + i], pi.q);
+                    t1.mac(d, key[((size_t)(2 * j + 1) * nP + pid) * N + i], pi.q);
+                }
+                v0 = t0.reduce(pi.q, pi.qinv);
+                v1 = t1.reduce(pi.q, pi.qinv);
+                if (qlimb) v0 = add_mod(v0, mont_mul(c0[(size_t)l * N + src], pm, pi.q, pi.qinv), pi.q);
+            }
+#pragma unroll
+            for (int g = 0; g < N2; g++) {
+                const int di = sgb[g * n1 + b];
+                if (di < 0) continue;
+                const u64 d = diag[di][idx];
+                a0[g] = add_mod(a0[g], mont_mul(v0, d, pi.q, pi.qinv), pi.q);
+                a1[g] = add_mod(a1[g], mont_mul(v1, d, pi.q, pi.qinv), pi.q);
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < N2; g++) {
+            if (!sany[g]) continue;
+            u64 *o = inner + (size_t)g * 2 * plane + idx;
+            o[0] = a0[g];
+            o[plane] = a1[g];
+        }
+    }
+}
+
 // ------------------------------------------------------------------ rescale
 // tab: [nP] q_l^-1 (Montgomery, by prime id), [nP] q_l mod q_i, [2 nP] q_l.
 __global__ void k_rescale_spread(u64 *__restrict__ out, const u64 *__restrict__ last, const u64 *__restrict__ tab,
@@ -631,6 +765,19 @@ void bsgs_mac(Ctx *c, u64 *inner, const u64 *baby, int n_baby, const u64 *const 
     // n_baby: number of distinct diagonals (non-zero); babies read once, diagonals once,
     // n2 inner ciphertexts written once
     KTimer kt(c, "bsgs_mac", 8.0 * limbs * c->N * (2.0 * n1 + (double)n_baby + 2.0 * n2));
+    if (n2 <= 8 && n1 <= 64 && (n2 & (n2 - 1)) == 0) {   // n2 = D / n1 is a power of two
+        const size_t total = (size_t)limbs * c->N;
+        const unsigned grid = grid_for(total);
+        const PrimeInfo *pi = c->d_pinfo.as<PrimeInfo>();
+        switch (n2 <= 1 ? 1 : n2 <= 2 ? 2 : n2 <= 4 ? 4 : 8) {
+        case 1: k_bsgs_mac_reg<1><<<grid, 256, 0, c->stream>>>(inner, baby, d_diag_ptrs, d_gb_index, n1, limbs, c->logN, pi, map); break;
+        case 2: k_bsgs_mac_reg<2><<<grid, 256, 0, c->stream>>>(inner, baby, d_diag_ptrs, d_gb_index, n1, limbs, c->logN, pi, map); break;
+        case 4: k_bsgs_mac_reg<4><<<grid, 256, 0, c->stream>>>(inner, baby, d_diag_ptrs, d_gb_index, n1, limbs, c->logN, pi, map); break;
+        default: k_bsgs_mac_reg<8><<<grid, 256, 0, c->stream>>>(inner, baby, d_diag_ptrs, d_gb_index, n1, limbs, c->logN, pi, map); break;
+        }
+        LAUNCHED(c);
+        return;
+    }
     HCHECK(smem <= 200 * 1024, HELRM_E_PARAM, "too many baby steps for the MAC tile");
     if (smem > 48 * 1024)
         CUDA_CHECK(cudaFuncSetAttribute(k_bsgs_mac, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -639,6 +786,39 @@ void bsgs_mac(Ctx *c, u64 *inner, const u64 *baby, int n_baby, const u64 *const 
                                                   c->d_pinfo.as<PrimeInfo>(), map);
     LAUNCHED(c);
 }
+void bsgs_fused(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c1, const u64 *const *keys,
+                const u64 *gals, const u64 *const *d_diag_ptrs, const int *d_gb_index, int n_diag, int n1, int n2,
+                int level)
+{
+    HCHECK(n1 <= 64 && n2 <= 8 && (n2 & (n2 - 1)) == 0, HELRM_E_PARAM, "fused BSGS needs n1 <= 64, n2 <= 8");
+    const int nl = level + 1 + c->K, dnum = c->dnum(level);
+    const size_t plane = (size_t)nl * c->N;
+    int n_keys = 0;
+    BabyKeys bk;
+    for (int b = 0; b < 64; b++) {
+        bk.key[b] = b < n1 ? keys[b] : nullptr;
+        bk.gal[b] = b < n1 ? gals[b] : 1;
+        n_keys += (b < n1 && keys[b]) ? 1 : 0;
+    }
+    // keys (2 dnum planes each) and diagonals once, the c0/c1 gathers, inner written once
+    KTimer kt(c, "bsgs_fused", 8.0 * plane * (2.0 * dnum * n_keys + n_diag + 2.0 * n2) +
+                                   16.0 * (level + 1) * c->N);
+    const unsigned grid = grid_for(plane);
+    const PrimeInfo *pi = c->d_pinfo.as<PrimeInfo>();
+    const u64 *pm = c->d_pmod_mont.u();
+#define HELRM_FUSED(NN)                                                                                        \
+    k_bsgs_fused<NN><<<grid, 256, 0, c->stream>>>(inner, digits, dnum, c0, c1, bk, d_diag_ptrs, d_gb_index, n1, \
+                                                  level, c->L, c->K, c->logN, pm, pi)
+    switch (n2) {
+    case 1: HELRM_FUSED(1); break;
+    case 2: HELRM_FUSED(2); break;
+    case 4: HELRM_FUSED(4); break;
+    default: HELRM_FUSED(8); break;
+    }
+#undef HELRM_FUSED
+    LAUNCHED(c);
+}
+
 void rescale_spread(Ctx *c, u64 *out, const u64 *last_coef, int level)
 {
     size_t total = (size_t)level * c->N;

@@ -5,7 +5,8 @@
 // slots.  For W padded to out_pad x in_pad there are D = min(in_pad, out_pad)
 // extended diagonals diag_i[j] = W[j mod out_pad, (j + i) mod in_pad]; when the
 // matrix is wide, rotate-and-add folds by in_pad/2, ..., out_pad finish the
-// sum.  BSGS: n1 = smallest power of two with n1^2 >= D, n2 = D / n1,
+// sum.  BSGS: n1 = min(D, 64), n2 = D / n1 (a giant step costs a ModDown and a
+// ModUp, a hoisted baby step only a key inner product, so baby steps win),
 // i = g n1 + b, diag'_{g,b} = rot(diag_i, -g n1), which reads
 // W[(j - g n1) mod out_pad, (j + b) mod in_pad].
 //
@@ -70,8 +71,7 @@ PtMatrix *ptmat_prepare(Ctx *c, const double *W, int rows, int cols, int in_pad,
     m->in_pad = in_pad;
     m->out_pad = out_pad;
     m->D = std::min(in_pad, out_pad);
-    m->n1 = 1;
-    while (m->n1 * m->n1 < m->D) m->n1 <<= 1;
+    m->n1 = std::min(m->D, 64);
     m->n2 = m->D / m->n1;
     m->level = level;
     for (int s = in_pad / 2; s >= out_pad; s /= 2) m->folds.push_back(s);
@@ -115,25 +115,41 @@ Ciphertext *matvec(Ctx *c, const EvalKey *evk, const PtMatrix *m, const Cipherte
         if (need_g[g]) gkey[g] = rot_key(evk, c->galois(g * m->n1));
 
     DevMem digits(c, (size_t)dnum * plane * 8);
-    DevMem baby(c, (size_t)m->n1 * 2 * plane * 8);
-    ks_modup(c, in->c1(), l, digits.u());
-    for (int b = 0; b < m->n1; b++) {
-        if (!need_b[b]) continue;
-        u64 *bb = baby.u() + (size_t)b * 2 * plane;
-        if (b == 0) {   // (P c0, P c1) over QP: P mod q_i on the Q limbs, 0 on the P limbs
-            for (int p = 0; p < 2; p++) {
-                k::mul_scalar_mont(c, bb + p * plane, p ? in->c1() : in->c0(), c->d_pmod_mont.u(), nq, c->qmap(l));
-                k::zero(c, bb + p * plane + (size_t)nq * N, (size_t)c->K * N);
-            }
-        } else {
-            k::ks_inner_auto(c, bb, digits.u(), dnum, bkey[b]->data.u(), l, c->galois(b), in->c0(),
-                             c->d_pmod_mont.u());
-        }
-    }
+    bool any_baby = false;
+    for (int b = 1; b < m->n1; b++) any_baby |= need_b[b] != 0;
+    if (any_baby) ks_modup(c, in->c1(), l, digits.u());   // hoisted: one ModUp for all baby steps
     DevMem inner(c, (size_t)m->n2 * 2 * plane * 8);
-    k::bsgs_mac(c, inner.u(), baby.u(), (int)m->gb.size(), m->d_ptrs.as<const u64 *>(), m->d_gb_index.as<int>(), m->n2, m->n1, nl,
-                c->qmap(l));
-    baby = DevMem();
+    if (m->n1 <= 64 && m->n2 <= 8) {
+        // baby steps formed in registers inside the MAC (no baby buffer)
+        std::vector<const u64 *> keys(m->n1, nullptr);
+        std::vector<u64> gals(m->n1, 1);
+        for (int b = 1; b < m->n1; b++)
+            if (need_b[b]) {
+                keys[b] = bkey[b]->data.u();
+                gals[b] = c->galois(b);
+            }
+        k::bsgs_fused(c, inner.u(), digits.u(), in->c0(), in->c1(), keys.data(), gals.data(),
+                      m->d_ptrs.as<const u64 *>(), m->d_gb_index.as<int>(), (int)m->gb.size(), m->n1, m->n2, l);
+    } else {
+        // wide baby-step sets: baby steps materialised over QP, then the tiled MAC
+        DevMem baby(c, (size_t)m->n1 * 2 * plane * 8);
+        for (int b = 0; b < m->n1; b++) {
+            if (!need_b[b]) continue;
+            u64 *bb = baby.u() + (size_t)b * 2 * plane;
+            if (b == 0) {   // (P c0, P c1) over QP: P mod q_i on the Q limbs, 0 on the P limbs
+                for (int p = 0; p < 2; p++) {
+                    k::mul_scalar_mont(c, bb + p * plane, p ? in->c1() : in->c0(), c->d_pmod_mont.u(), nq,
+                                       c->qmap(l));
+                    k::zero(c, bb + p * plane + (size_t)nq * N, (size_t)c->K * N);
+                }
+            } else {
+                k::ks_inner_auto(c, bb, digits.u(), dnum, bkey[b]->data.u(), l, c->galois(b), in->c0(),
+                                 c->d_pmod_mont.u());
+            }
+        }
+        k::bsgs_mac(c, inner.u(), baby.u(), (int)m->gb.size(), m->d_ptrs.as<const u64 *>(), m->d_gb_index.as<int>(),
+                    m->n2, m->n1, nl, c->qmap(l));
+    }
     DevMem acc(c, 2 * plane * 8), c1q(c, (size_t)nq * N * 8), t(c, 2 * plane * 8), phi(c, plane * 8);
     k::zero(c, acc.u(), 2 * plane);
     const LimbMap qp2 = c->qmap(l, 0, nl), qp = c->qmap(l);
@@ -144,6 +160,8 @@ Ciphertext *matvec(Ctx *c, const EvalKey *evk, const PtMatrix *m, const Cipherte
             k::add(c, acc.u(), acc.u(), ig, 2 * nl, qp2);
             continue;
         }
+        // giant step on a QP ciphertext: ModDown the a-part, ModUp, phi, key inner product;
+        // the b-part is already over QP and only gets phi
         const u64 gal = c->galois(g * m->n1);
         ks_moddown(c, ig + plane, l, c1q.u());
         ks_modup(c, c1q.u(), l, digits.u());

@@ -31,6 +31,33 @@ struct LimbList {
 
 __device__ __forceinline__ int pad(int e) { return e + (e >> 4); }
 
+// Harvey's lazy butterflies (all values < 4q < 2^64 since every q < 2^62).
+// Shoup product without its final correction: a * w mod q in [0, 2q).
+__device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 wp, u64 q) { return a * w - mulhi64(a, wp) * q; }
+// forward (Cooley-Tukey): x0, x1 in [0, 4q) -> [0, 4q)
+__device__ __forceinline__ void bfly_ct(u64 &x0, u64 &x1, u64 w, u64 wp, u64 q, u64 q2)
+{
+    u64 a = x0 >= q2 ? x0 - q2 : x0;
+    u64 t = shoup_lazy(x1, w, wp, q);
+    x0 = a + t;
+    x1 = a - t + q2;
+}
+// inverse (Gentleman-Sande): x0, x1 in [0, 2q) -> [0, 2q)
+__device__ __forceinline__ void bfly_gs(u64 &x0, u64 &x1, u64 w, u64 wp, u64 q, u64 q2)
+{
+    u64 s = x0 + x1;
+    s = s >= q2 ? s - q2 : s;
+    u64 t = x0 - x1 + q2;
+    x0 = s;
+    x1 = shoup_lazy(t, w, wp, q);
+}
+// [0, 4q) -> [0, q)
+__device__ __forceinline__ u64 reduce4(u64 x, u64 q, u64 q2)
+{
+    x = x >= q2 ? x - q2 : x;
+    return x >= q ? x - q : x;
+}
+
 // One pass of the forward transform over sub-transforms of P = 2^LOGP points.
 // COLS: sub-transform g is column c0+g of the limb, elements r*N2 + c.
 // ROWS: sub-transform g is row r0+g, elements (r0+g)*N2 + x.
@@ -51,6 +78,7 @@ __global__ void __launch_bounds__(512) k_ntt_pass(u64 *data, int logN, int logG,
     const int G = 1 << logG;                // sub-transforms per CTA
     const int pid = list.pid[blockIdx.y];
     const u64 q = pinfo[pid].q;
+    const u64 q2 = 2 * q;
     const ulonglong2 *tw = tw_all + (size_t)pid * N;
     u64 *a = data + (size_t)list.off[blockIdx.y] * N;
     const int tid = threadIdx.x;
@@ -107,10 +135,7 @@ __global__ void __launch_bounds__(512) k_ntt_pass(u64 *data, int logN, int logG,
                         if (k1 & half) continue;
                         const int lb = (e0 + k1 * T) >> (LOGP - s);
                         const ulonglong2 w = tw[((bm + seg) << s) + lb];
-                        const u64 x0 = x[k1];
-                        const u64 x1 = shoup_mul(x[k1 + half], w.x, w.y, q);
-                        x[k1] = add_mod(x0, x1, q);
-                        x[k1 + half] = sub_mod(x0, x1, q);
+                        bfly_ct(x[k1], x[k1 + half], w.x, w.y, q, q2);
                     }
                 }
             } else {
@@ -121,9 +146,7 @@ __global__ void __launch_bounds__(512) k_ntt_pass(u64 *data, int logN, int logG,
                         if (k1 & half) continue;
                         const int lb = (e0 + k1 * T) >> (LOGP - s);
                         const ulonglong2 w = tw[((bm + seg) << s) + lb];
-                        const u64 x0 = x[k1], x1 = x[k1 + half];
-                        x[k1] = add_mod(x0, x1, q);
-                        x[k1 + half] = shoup_mul(sub_mod(x0, x1, q), w.x, w.y, q);
+                        bfly_gs(x[k1], x[k1 + half], w.x, w.y, q, q2);
                     }
                 }
             }
@@ -133,12 +156,18 @@ __global__ void __launch_bounds__(512) k_ntt_pass(u64 *data, int logN, int logG,
             _Pragma("unroll") for (int qg = 0; qg < ng; qg++)
                 _Pragma("unroll") for (int k = 0; k < gs; k++) sm[saddr(elem(qg, k))] = v[qg * gs + k];
         } else {
+            // the last pass of a transform leaves canonical residues: forward rows
+            // reduce [0, 4q) -> [0, q); inverse columns multiply by 1/N (full
+            // reduction).  The first pass leaves its lazy range for the second.
             ulonglong2 ni = make_ulonglong2(0, 0);
             if (scale_out) ni = ninv[pid];
             _Pragma("unroll") for (int qg = 0; qg < ng; qg++)
                 _Pragma("unroll") for (int k = 0; k < gs; k++) {
                     u64 y = v[qg * gs + k];
-                    if (scale_out) y = shoup_mul(y, ni.x, ni.y, q);
+                    if (scale_out)
+                        y = shoup_mul(y, ni.x, ni.y, q);
+                    else if (!COLS && !INV)
+                        y = reduce4(y, q, q2);
                     a[gaddr(elem(qg, k))] = y;
                 }
         }

@@ -81,7 +81,8 @@ def test_diagonal_count_for_416_outputs():
 
 
 def test_bsgs_split():
-    for D, n1, n2 in [(1, 1, 1), (2, 2, 1), (16, 4, 4), (32, 8, 4), (256, 16, 16), (512, 32, 16)]:
+    for D, n1, n2 in [(1, 1, 1), (2, 2, 1), (16, 16, 1), (32, 32, 1), (64, 64, 1), (256, 64, 4),
+                      (512, 64, 8), (1024, 64, 16)]:
         assert linear.bsgs_split(D) == (n1, n2)
 
 

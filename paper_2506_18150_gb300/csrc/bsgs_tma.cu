@@ -1,0 +1,310 @@
+// bsgs_tma.cu -- the hoisted baby steps fused into the BSGS multiply-
+// accumulate, fed by bulk asynchronous copies (cp.async.bulk + mbarrier).
+//
+// One CTA owns a tile of T = 256 consecutive coefficients of one limb l of the
+// level-ell QP basis and walks the needed baby steps b.  For baby step b it
+// needs, per coefficient i of the tile:
+//   * the ModUp digits at the Galois source position src(i) (DN words);
+//   * key b's two halves at i (2 DN words), and c0 at src(i);
+//   * the diagonal words of every giant step g at i (N2 words).
+// In the bit-reversed NTT order the automorphism maps an aligned block of 2^m
+// consecutive coefficients onto an aligned block of 2^m consecutive
+// coefficients (permuted inside), so every one of these is one contiguous
+// 2 KB row: a producer lane issues it as a bulk copy into a shared-memory
+// stage and the stage's mbarrier counts the bytes in.  With S = 3 stages the
+// copies for the next baby steps are in flight while the current one is
+// multiplied, so HBM latency is hidden without registers.  Each baby step's
+// value (key inner product + P phi(c0)) is reduced and multiplied at once into
+// the n2 giant-step accumulators, 64-bit, reduced per product (REDC is linear,
+// so the result equals the unfused kernels' bit for bit).
+//
+// Every wait on an mbarrier is bounded: if a stage does not complete within
+// the limit the CTA records HELRM_E_TIMEOUT in the context's error word, waits
+// (bounded again) for the copies it issued, and returns.
+#include "core.cuh"
+
+namespace helrm {
+namespace {
+
+constexpr int T = 256;             // coefficients per tile (= threads per CTA)
+constexpr int S = 3;               // pipeline stages
+constexpr long WAIT_LIMIT = 1L << 24;
+
+__device__ __forceinline__ u32 smem_addr(const void *p) { return (u32)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(u64 *bar, u32 count)
+{
+    asm volatile("mbarrier.init.shared.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(u64 *bar, u32 bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(u64 *bar, u32 parity)
+{
+    u32 ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// 1-D bulk copy global -> shared (16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, u32 bytes, u64 *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ int auto_src(int i, int logN, u64 galois)
+{
+    const u32 x = __brev((u32)i) >> (32 - logN);
+    const u64 e = ((2ull * x + 1) * galois) & ((2ull << logN) - 1);
+    return (int)(__brev((u32)((e - 1) >> 1)) >> (32 - logN));
+}
+
+struct TmaBabies {
+    const u64 *key[64];   // key of baby step b (b >= 1)
+    u64 gal[64];
+};
+
+// Stage layout (words): dig[DN][T] | kb[DN][T] | ka[DN][T] | c0[T] | dd[N2][T]
+template <int N2, int DN>
+struct Stage {
+    static constexpr int WORDS = (3 * DN + 1 + N2) * T;
+};
+
+template <int N2, int DN>
+__global__ void __launch_bounds__(T) k_bsgs_tma(u64 *__restrict__ inner, const u64 *__restrict__ dig,
+                                               const u64 *__restrict__ c0, const u64 *__restrict__ c1, TmaBabies bk,
+                                               const u64 *const *__restrict__ diag, const int *__restrict__ gb,
+                                               int n1, int level, int L, int K, int logN,
+                                               const u64 *__restrict__ pmod, const PrimeInfo *__restrict__ pinfo,
+                                               int *err)
+{
+    extern __shared__ __align__(128) u64 smem[];
+    constexpr int SW = Stage<N2, DN>::WORDS;
+    u64 *bars = smem + S * SW;                       // S mbarriers after the stages
+    __shared__ int sgb[64 * 8];
+    __shared__ int blist[64];                        // needed baby steps b >= 1, in order
+    __shared__ int nb, need0;
+    const int tid = threadIdx.x;
+    const size_t N = (size_t)1 << logN;
+    const int nl = level + 1 + K, nP = L + 1 + K;
+    const size_t plane = (size_t)nl * N;
+    const int l = blockIdx.y;
+    const int i0 = blockIdx.x * T;
+    const bool qlimb = l <= level;
+    const int pid = qlimb ? l : L + 1 + (l - level - 1);
+    const PrimeInfo pi = pinfo[pid];
+    const u64 pm = pmod[pid];
+
+    for (int t = tid; t < n1 * N2; t += T) sgb[t] = gb[t];
+    __syncthreads();
+    if (tid == 0) {
+        int c = 0;
+        for (int b = 1; b < n1; b++) {
+            int need = 0;
+            for (int g = 0; g < N2; g++) need |= sgb[g * n1 + b] >= 0;
+            if (need) blist[c++] = b;
+        }
+        int n0 = 0;
+        for (int g = 0; g < N2; g++) n0 |= sgb[g * n1] >= 0;
+        nb = c;
+        need0 = n0;
+        for (int s = 0; s < S; s++) mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    // warp 0 issues the copies of the k-th needed baby step into stage k % S
+    auto issue = [&](int k) {
+        const int b = blist[k];
+        u64 *st = smem + (k % S) * SW;
+        const int src_base = auto_src(i0, logN, bk.gal[b]) & ~(T - 1);
+        const u64 *key = bk.key[b];
+        const int lane = tid & 31;
+        int nd = 0;
+        for (int g = 0; g < N2; g++) nd += sgb[g * n1 + b] >= 0;
+        const u32 bytes = (u32)(3 * DN + (qlimb ? 1 : 0) + nd) * T * 8;
+        if (lane == 0) mbar_arrive_expect_tx(&bars[k % S], bytes);
+        __syncwarp();
+        // copy list: DN digit rows, 2 DN key rows, c0 row, present diagonal rows
+        const int n_copies = 3 * DN + 1 + N2;
+        for (int cidx = lane; cidx < n_copies; cidx += 32) {
+            const u64 *src = nullptr;
+            u64 *dst = nullptr;
+            if (cidx < DN) {
+                src = dig + ((size_t)cidx * nl + l) * N + src_base;
+                dst = st + cidx * T;
+            } else if (cidx < 2 * DN) {
+                const int j = cidx - DN;
+                src = key + ((size_t)(2 * j) * nP + pid) * N + i0;
+                dst = st + (DN + j) * T;
+            } else if (cidx < 3 * DN) {
+                const int j = cidx - 2 * DN;
+                src = key + ((size_t)(2 * j + 1) * nP + pid) * N + i0;
+                dst = st + (2 * DN + j) * T;
+            } else if (cidx == 3 * DN) {
+                if (qlimb) {
+                    src = c0 + (size_t)l * N + src_base;
+                    dst = st + 3 * DN * T;
+                }
+            } else {
+                const int g = cidx - 3 * DN - 1;
+                const int di = sgb[g * n1 + b];
+                if (di >= 0) {
+                    src = diag[di] + (size_t)l * N + i0;
+                    dst = st + (3 * DN + 1 + g) * T;
+                }
+            }
+            if (src) bulk_g2s(dst, src, T * 8, &bars[k % S]);
+        }
+    };
+
+    if (tid < 32)
+        for (int k = 0; k < S && k < nb; k++) issue(k);
+
+    // 128-bit accumulators (one full product per diagonal word, one REDC at the end)
+    Acc128 a0[N2], a1[N2];
+    const int i = i0 + tid;
+    const size_t idx = (size_t)l * N + i;
+    if (need0) {   // baby 0 = (P c0, P c1): P mod q on the Q limbs, 0 on the P limbs
+        const u64 v0 = qlimb ? mont_mul(c0[idx], pm, pi.q, pi.qinv) : 0;
+        const u64 v1 = qlimb ? mont_mul(c1[idx], pm, pi.q, pi.qinv) : 0;
+#pragma unroll
+        for (int g = 0; g < N2; g++) {
+            const int di = sgb[g * n1];
+            if (di < 0) continue;
+            const u64 d = diag[di][idx];
+            a0[g].mac(v0, d, pi.q);
+            a1[g].mac(v1, d, pi.q);
+        }
+    }
+
+    bool aborted = false;
+    int k = 0;
+    for (; k < nb; k++) {
+        const int s = k % S;
+        const u32 parity = (u32)((k / S) & 1);
+        bool ok = false;
+        for (long it = 0; it < WAIT_LIMIT; it++)
+            if (mbar_try_wait(&bars[s], parity)) {
+                ok = true;
+                break;
+            }
+        if (ok) {
+            const int b = blist[k];
+            const u64 *st = smem + s * SW;
+            const int src_loc = auto_src(i, logN, bk.gal[b]) - (auto_src(i0, logN, bk.gal[b]) & ~(T - 1));
+            Acc128 t0, t1;
+#pragma unroll
+            for (int j = 0; j < DN; j++) {
+                const u64 d = st[j * T + src_loc];
+                t0.mac(d, st[(DN + j) * T + tid], pi.q);
+                t1.mac(d, st[(2 * DN + j) * T + tid], pi.q);
+            }
+            u64 v0 = t0.reduce(pi.q, pi.qinv);
+            const u64 v1 = t1.reduce(pi.q, pi.qinv);
+            if (qlimb) v0 = add_mod(v0, mont_mul(st[3 * DN * T + src_loc], pm, pi.q, pi.qinv), pi.q);
+#pragma unroll
+            for (int g = 0; g < N2; g++) {
+                if (sgb[g * n1 + b] < 0) continue;
+                const u64 d = st[(3 * DN + 1 + g) * T + tid];
+                a0[g].mac(v0, d, pi.q);
+                a1[g].mac(v1, d, pi.q);
+            }
+        }
+        // one barrier per baby step: stage s is fully read before it is refilled,
+        // and a timeout anywhere in the CTA is seen by every thread
+        if (__syncthreads_or(!ok)) {
+            aborted = true;
+            break;
+        }
+        if (tid < 32 && k + S < nb) issue(k + S);
+    }
+    if (aborted) {
+        if (tid == 0) {
+            atomicExch(err, (int)HELRM_E_TIMEOUT);
+            // let the copies already issued land before the CTA's shared memory goes away
+            for (int kk = k; kk < nb && kk < k + S; kk++)
+                for (long it = 0; it < WAIT_LIMIT; it++)
+                    if (mbar_try_wait(&bars[kk % S], (u32)((kk / S) & 1))) break;
+        }
+        __syncthreads();
+        return;
+    }
+#pragma unroll
+    for (int g = 0; g < N2; g++) {
+        bool any = false;
+        for (int b = 0; b < n1; b++) any |= sgb[g * n1 + b] >= 0;
+        if (!any) continue;
+        u64 *o = inner + (size_t)g * 2 * plane + idx;
+        o[0] = a0[g].reduce(pi.q, pi.qinv);
+        o[plane] = a1[g].reduce(pi.q, pi.qinv);
+    }
+}
+
+template <int N2, int DN>
+void launch(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c1, const TmaBabies &bk,
+            const u64 *const *diag, const int *gb, int n1, int level)
+{
+    const size_t smem = (size_t)S * Stage<N2, DN>::WORDS * 8 + S * 8;
+    CUDA_CHECK(cudaFuncSetAttribute(k_bsgs_tma<N2, DN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid(c->N / T, level + 1 + c->K);
+    k_bsgs_tma<N2, DN><<<grid, T, smem, c->stream>>>(inner, digits, c0, c1, bk, diag, gb, n1, level, c->L, c->K,
+                                                     c->logN, c->d_pmod_mont.u(), c->d_pinfo.as<PrimeInfo>(),
+                                                     c->d_err.as<int>());
+}
+
+}  // namespace
+
+namespace k {
+
+void bsgs_tma(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c1, const u64 *const *keys,
+              const u64 *gals, const u64 *const *d_diag_ptrs, const int *d_gb_index, int n_diag, int n1, int n2,
+              int level)
+{
+    const int dnum = c->dnum(level);
+    HCHECK(n1 <= 64 && (n2 == 1 || n2 == 2 || n2 == 4 || n2 == 8), HELRM_E_PARAM, "BSGS tile supports n1 <= 64, n2 <= 8");
+    HCHECK(dnum >= 1 && dnum <= 7 && c->N >= T, HELRM_E_PARAM, "BSGS tile supports 1..7 digits");
+    TmaBabies bk;
+    int n_keys = 0;
+    for (int b = 0; b < 64; b++) {
+        bk.key[b] = b < n1 ? keys[b] : nullptr;
+        bk.gal[b] = b < n1 ? gals[b] : 1;
+        n_keys += (b > 0 && b < n1 && keys[b]) ? 1 : 0;
+    }
+    const size_t plane = (size_t)(level + 1 + c->K) * c->N;
+    KTimer kt(c, "bsgs_fused", 8.0 * plane * (2.0 * dnum * n_keys + n_diag + 2.0 * n2) +
+                                   16.0 * (level + 1) * c->N);
+#define HELRM_TMA(NN, DD) launch<NN, DD>(c, inner, digits, c0, c1, bk, d_diag_ptrs, d_gb_index, n1, level)
+#define HELRM_TMA_D(NN)              \
+    switch (dnum) {                  \
+    case 1: HELRM_TMA(NN, 1); break; \
+    case 2: HELRM_TMA(NN, 2); break; \
+    case 3: HELRM_TMA(NN, 3); break; \
+    case 4: HELRM_TMA(NN, 4); break; \
+    case 5: HELRM_TMA(NN, 5); break; \
+    case 6: HELRM_TMA(NN, 6); break; \
+    default: HELRM_TMA(NN, 7); break; \
+    }
+    switch (n2) {
+    case 1: HELRM_TMA_D(1); break;
+    case 2: HELRM_TMA_D(2); break;
+    case 4: HELRM_TMA_D(4); break;
+    default: HELRM_TMA_D(8); break;
+    }
+#undef HELRM_TMA_D
+#undef HELRM_TMA
+    c->launches++;
+    CUDA_CHECK(cudaGetLastError());
+}
+
+}  // namespace k
+}  // namespace helrm

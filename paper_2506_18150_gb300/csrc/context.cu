@@ -170,6 +170,8 @@ void Ctx::check_device_errors()
     CUDA_CHECK(cudaStreamSynchronize(stream));
     if (h) {
         CUDA_CHECK(cudaMemsetAsync(d_err.ptr, 0, 8, stream));
+        if (h == (int)HELRM_E_TIMEOUT)
+            fail(HELRM_E_TIMEOUT, "a bounded device-side wait ran out (the kernel returned early)");
         fail(HELRM_E_INVAL, "an encoded coefficient exceeded 2^62 (scale or slot values too large)");
     }
 }

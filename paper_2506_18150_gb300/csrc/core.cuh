@@ -341,6 +341,10 @@ void ks_inner_auto(Ctx *c, u64 *out, const u64 *digits, int dnum, const u64 *key
 void bsgs_mac(Ctx *c, u64 *inner, const u64 *baby, int n_baby, const u64 *const *d_diag_ptrs,
               const int *d_gb_index, int n2, int n1, int limbs, LimbMap map);
 void automorphism(Ctx *c, u64 *out, const u64 *in, int n_limbs, u64 galois);
+// the same, fed by a 3-stage pipeline of bulk asynchronous copies (bsgs_tma.cu)
+void bsgs_tma(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c1, const u64 *const *keys,
+              const u64 *gals, const u64 *const *d_diag_ptrs, const int *d_gb_index, int n_diag, int n1, int n2,
+              int level);
 // fused hoisted baby steps + BSGS MAC (n1 <= 64, n2 in {1,2,4,8}); keys[b] / gals[b]
 // for b < n1 (keys[0] unused), writes inner[g][2][level+1+K][N] for giant steps with diagonals
 void bsgs_fused(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c1, const u64 *const *keys,

@@ -310,8 +310,12 @@ struct BabyKeys {
     u64 gal[64];          // its Galois element
 };
 
-template <int N2>
-__global__ void __launch_bounds__(256, 3) k_bsgs_fused(u64 *__restrict__ inner, const u64 *__restrict__ dig, int dnum,
+// DN = number of key-switching digits at this level (a template parameter so
+// that a baby step's loads -- DN digit words, 2 DN key words, the gathered c0
+// word and its N2 diagonal words -- all land in registers and are issued
+// together before any arithmetic, one memory round trip per baby step).
+template <int N2, int DN>
+__global__ void __launch_bounds__(256, 3) k_bsgs_fused(u64 *__restrict__ inner, const u64 *__restrict__ dig,
                                                     const u64 *__restrict__ c0, const u64 *__restrict__ c1,
                                                     BabyKeys bk, const u64 *const *__restrict__ diag,
                                                     const int *__restrict__ gb, int n1, int level, int L, int K,
@@ -350,32 +354,53 @@ __global__ void __launch_bounds__(256, 3) k_bsgs_fused(u64 *__restrict__ inner, 
         u64 a0[N2], a1[N2];
 #pragma unroll
         for (int g = 0; g < N2; g++) a0[g] = a1[g] = 0;
-        for (int b = 0; b < n1; b++) {
-            if (!sneed[b]) continue;
-            u64 v0, v1;
-            if (b == 0) {   // (P c0, P c1): P mod q on the Q limbs, 0 on the P limbs
-                v0 = qlimb ? mont_mul(c0[(size_t)l * N + i], pm, pi.q, pi.qinv) : 0;
-                v1 = qlimb ? mont_mul(c1[(size_t)l * N + i], pm, pi.q, pi.qinv) : 0;
-            } else {
-                const int src = auto_src(i, logN, bk.gal[b]);
-                const u64 *key = bk.key[b];
-                Acc128 t0, t1;
-                for (int j = 0; j < dnum; j++) {
-                    const u64 d = dig[((size_t)j * nl + l) * N + src];
-                    t0.mac(d, key[((size_t)(2 * j) * nP + pid) * N + i], pi.q);
-                    t1.mac(d, key[((size_t)(2 * j + 1) * nP + pid) * N + i], pi.q);
-                }
-                v0 = t0.reduce(pi.q, pi.qinv);
-                v1 = t1.reduce(pi.q, pi.qinv);
-                if (qlimb) v0 = add_mod(v0, mont_mul(c0[(size_t)l * N + src], pm, pi.q, pi.qinv), pi.q);
+        // a missing diagonal contributes mont_mul(v, 0) = 0, so absent (g, b)
+        // pairs need no branch: their diagonal word is loaded as 0
+        if (sneed[0]) {   // baby 0 = (P c0, P c1): P mod q on the Q limbs, 0 on the P limbs
+            u64 dd[N2];
+#pragma unroll
+            for (int g = 0; g < N2; g++) {
+                const int di = sgb[g * n1];
+                dd[g] = di >= 0 ? diag[di][idx] : 0;
             }
+            const u64 v0 = qlimb ? mont_mul(c0[(size_t)l * N + i], pm, pi.q, pi.qinv) : 0;
+            const u64 v1 = qlimb ? mont_mul(c1[(size_t)l * N + i], pm, pi.q, pi.qinv) : 0;
+#pragma unroll
+            for (int g = 0; g < N2; g++) {
+                a0[g] = add_mod(a0[g], mont_mul(v0, dd[g], pi.q, pi.qinv), pi.q);
+                a1[g] = add_mod(a1[g], mont_mul(v1, dd[g], pi.q, pi.qinv), pi.q);
+            }
+        }
+        for (int b = 1; b < n1; b++) {
+            if (!sneed[b]) continue;
+            const int src = auto_src(i, logN, bk.gal[b]);
+            const u64 *key = bk.key[b];
+            u64 dg[DN], kb[DN], ka[DN], dd[N2];
+#pragma unroll
+            for (int j = 0; j < DN; j++) {
+                dg[j] = dig[((size_t)j * nl + l) * N + src];
+                kb[j] = key[((size_t)(2 * j) * nP + pid) * N + i];
+                ka[j] = key[((size_t)(2 * j + 1) * nP + pid) * N + i];
+            }
+            const u64 cs = qlimb ? c0[(size_t)l * N + src] : 0;
 #pragma unroll
             for (int g = 0; g < N2; g++) {
                 const int di = sgb[g * n1 + b];
-                if (di < 0) continue;
-                const u64 d = diag[di][idx];
-                a0[g] = add_mod(a0[g], mont_mul(v0, d, pi.q, pi.qinv), pi.q);
-                a1[g] = add_mod(a1[g], mont_mul(v1, d, pi.q, pi.qinv), pi.q);
+                dd[g] = di >= 0 ? diag[di][idx] : 0;
+            }
+            Acc128 t0, t1;
+#pragma unroll
+            for (int j = 0; j < DN; j++) {
+                t0.mac(dg[j], kb[j], pi.q);
+                t1.mac(dg[j], ka[j], pi.q);
+            }
+            u64 v0 = t0.reduce(pi.q, pi.qinv);
+            const u64 v1 = t1.reduce(pi.q, pi.qinv);
+            if (qlimb) v0 = add_mod(v0, mont_mul(cs, pm, pi.q, pi.qinv), pi.q);
+#pragma unroll
+            for (int g = 0; g < N2; g++) {
+                a0[g] = add_mod(a0[g], mont_mul(v0, dd[g], pi.q, pi.qinv), pi.q);
+                a1[g] = add_mod(a1[g], mont_mul(v1, dd[g], pi.q, pi.qinv), pi.q);
             }
         }
 #pragma unroll
@@ -806,15 +831,27 @@ void bsgs_fused(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 
     const unsigned grid = grid_for(plane);
     const PrimeInfo *pi = c->d_pinfo.as<PrimeInfo>();
     const u64 *pm = c->d_pmod_mont.u();
-#define HELRM_FUSED(NN)                                                                                        \
-    k_bsgs_fused<NN><<<grid, 256, 0, c->stream>>>(inner, digits, dnum, c0, c1, bk, d_diag_ptrs, d_gb_index, n1, \
-                                                  level, c->L, c->K, c->logN, pm, pi)
-    switch (n2) {
-    case 1: HELRM_FUSED(1); break;
-    case 2: HELRM_FUSED(2); break;
-    case 4: HELRM_FUSED(4); break;
-    default: HELRM_FUSED(8); break;
+    HCHECK(dnum >= 1 && dnum <= 7, HELRM_E_PARAM, "fused BSGS supports 1..7 key-switching digits");
+#define HELRM_FUSED(NN, DD)                                                                                    \
+    k_bsgs_fused<NN, DD><<<grid, 256, 0, c->stream>>>(inner, digits, c0, c1, bk, d_diag_ptrs, d_gb_index, n1, \
+                                                      level, c->L, c->K, c->logN, pm, pi)
+#define HELRM_FUSED_D(NN)              \
+    switch (dnum) {                    \
+    case 1: HELRM_FUSED(NN, 1); break; \
+    case 2: HELRM_FUSED(NN, 2); break; \
+    case 3: HELRM_FUSED(NN, 3); break; \
+    case 4: HELRM_FUSED(NN, 4); break; \
+    case 5: HELRM_FUSED(NN, 5); break; \
+    case 6: HELRM_FUSED(NN, 6); break; \
+    default: HELRM_FUSED(NN, 7); break; \
     }
+    switch (n2) {
+    case 1: HELRM_FUSED_D(1); break;
+    case 2: HELRM_FUSED_D(2); break;
+    case 4: HELRM_FUSED_D(4); break;
+    default: HELRM_FUSED_D(8); break;
+    }
+#undef HELRM_FUSED_D
 #undef HELRM_FUSED
     LAUNCHED(c);
 }

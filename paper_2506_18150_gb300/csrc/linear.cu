@@ -128,8 +128,8 @@ Ciphertext *matvec(Ctx *c, const EvalKey *evk, const PtMatrix *m, const Cipherte
                 keys[b] = bkey[b]->data.u();
                 gals[b] = c->galois(b);
             }
-        k::bsgs_fused(c, inner.u(), digits.u(), in->c0(), in->c1(), keys.data(), gals.data(),
-                      m->d_ptrs.as<const u64 *>(), m->d_gb_index.as<int>(), (int)m->gb.size(), m->n1, m->n2, l);
+        k::bsgs_tma(c, inner.u(), digits.u(), in->c0(), in->c1(), keys.data(), gals.data(),
+                    m->d_ptrs.as<const u64 *>(), m->d_gb_index.as<int>(), (int)m->gb.size(), m->n1, m->n2, l);
     } else {
         // wide baby-step sets: baby steps materialised over QP, then the tiled MAC
         DevMem baby(c, (size_t)m->n1 * 2 * plane * 8);

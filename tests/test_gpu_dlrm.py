@@ -113,6 +113,27 @@ def test_full_uci_configuration():
     _check_e2e(e, 4, 33)
 
 
+def test_full_criteo_configuration():
+    """Criteo-shaped DLRM at the full parameter set: 13 log-normal dense
+    features, 26 tables (33.8M rows, base 64, Zipf indices), bottom
+    13-512-256-64-16, dot interaction (27 blocks), top 367-512-256-1."""
+    from oracle import dlrm
+    from paper_2506_18150_gb300 import helrm as H
+    from paper_2506_18150_gb300 import synthetic as syn
+    spec = syn.criteo_spec(0)
+    w = syn.make_weights(spec, 0)
+    ctx = gpu_ctx(syn.PARAMS["full"])
+    model = H.helrm_model_create(ctx, spec, w)
+    info = H.helrm_model_info(ctx, model)
+    assert (info["lvl_dense"], info["lvl_sel"], info["p_sel"], info["W_u"]) == (15, 8, 8192, 16384)
+    sk, evk = H.helrm_keygen(ctx, 3, H.helrm_model_rotations(ctx, model))
+    dense, idx = syn.make_queries(spec, 2, seed=9)
+    lg, pr = H.helrm_infer_e2e(ctx, sk, evk, model, dense, idx, 11)
+    for q in range(2):
+        ref, ref_p, _ = dlrm.dlrm_cleartext(spec, w, dense[q], idx[q])
+        assert abs(lg[q] - ref) < 1e-3 and abs(pr[q] - ref_p) < 1e-3, (q, lg[q], ref)
+
+
 def test_wrong_query_level_is_rejected():
     from paper_2506_18150_gb300 import helrm as H
     from paper_2506_18150_gb300 import synthetic as syn

@@ -79,19 +79,37 @@ struct Stage {
     static constexpr int WORDS = (3 * DN + 1 + N2) * T;
 };
 
+__device__ __forceinline__ void mbar_arrive(u64 *bar)
+{
+    asm volatile("mbarrier.arrive.shared.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_bounded(u64 *bar, u32 parity)
+{
+    for (long it = 0; it < WAIT_LIMIT; it++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Warp-specialised pipeline: warps 0..7 consume (one coefficient per thread),
+// warp 8 produces.  full[s] completes when stage s's bytes have landed
+// (producer arrive + expect_tx, copies complete_tx); empty[s] completes when
+// all 8 consumer warps have read stage s, letting the producer refill it.
+constexpr int CONSUMER_WARPS = T / 32;
+
 template <int N2, int DN>
-__global__ void __launch_bounds__(T) k_bsgs_tma(u64 *__restrict__ inner, const u64 *__restrict__ dig,
-                                               const u64 *__restrict__ c0, const u64 *__restrict__ c1, TmaBabies bk,
-                                               const u64 *const *__restrict__ diag, const int *__restrict__ gb,
-                                               int n1, int level, int L, int K, int logN,
-                                               const u64 *__restrict__ pmod, const PrimeInfo *__restrict__ pinfo,
-                                               int *err)
+__global__ void __launch_bounds__(T + 32) k_bsgs_tma(u64 *__restrict__ inner, const u64 *__restrict__ dig,
+                                                    const u64 *__restrict__ c0, const u64 *__restrict__ c1,
+                                                    TmaBabies bk, const u64 *const *__restrict__ diag,
+                                                    const int *__restrict__ gb, int n1, int level, int L, int K,
+                                                    int logN, const u64 *__restrict__ pmod,
+                                                    const PrimeInfo *__restrict__ pinfo, int *err)
 {
     extern __shared__ __align__(128) u64 smem[];
     constexpr int SW = Stage<N2, DN>::WORDS;
-    u64 *bars = smem + S * SW;                       // S mbarriers after the stages
+    u64 *full = smem + S * SW;        // S mbarriers
+    u64 *empty = full + S;            // S mbarriers
     __shared__ int sgb[64 * 8];
-    __shared__ int blist[64];                        // needed baby steps b >= 1, in order
+    __shared__ int blist[64];         // needed baby steps b >= 1, in order
     __shared__ int nb, need0;
     const int tid = threadIdx.x;
     const size_t N = (size_t)1 << logN;
@@ -101,10 +119,8 @@ __global__ void __launch_bounds__(T) k_bsgs_tma(u64 *__restrict__ inner, const u
     const int i0 = blockIdx.x * T;
     const bool qlimb = l <= level;
     const int pid = qlimb ? l : L + 1 + (l - level - 1);
-    const PrimeInfo pi = pinfo[pid];
-    const u64 pm = pmod[pid];
 
-    for (int t = tid; t < n1 * N2; t += T) sgb[t] = gb[t];
+    for (int t = tid; t < n1 * N2; t += blockDim.x) sgb[t] = gb[t];
     __syncthreads();
     if (tid == 0) {
         int c = 0;
@@ -117,64 +133,81 @@ __global__ void __launch_bounds__(T) k_bsgs_tma(u64 *__restrict__ inner, const u
         for (int g = 0; g < N2; g++) n0 |= sgb[g * n1] >= 0;
         nb = c;
         need0 = n0;
-        for (int s = 0; s < S; s++) mbar_init(&bars[s], 1);
+        for (int s = 0; s < S; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], CONSUMER_WARPS);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncthreads();
+    __syncthreads();   // the last CTA-wide barrier: from here on warps run independently
 
-    // warp 0 issues the copies of the k-th needed baby step into stage k % S
-    auto issue = [&](int k) {
-        const int b = blist[k];
-        u64 *st = smem + (k % S) * SW;
-        const int src_base = auto_src(i0, logN, bk.gal[b]) & ~(T - 1);
-        const u64 *key = bk.key[b];
+    if (tid >= T) {
+        // ---------------- producer warp
         const int lane = tid & 31;
-        int nd = 0;
-        for (int g = 0; g < N2; g++) nd += sgb[g * n1 + b] >= 0;
-        const u32 bytes = (u32)(3 * DN + (qlimb ? 1 : 0) + nd) * T * 8;
-        if (lane == 0) mbar_arrive_expect_tx(&bars[k % S], bytes);
-        __syncwarp();
-        // copy list: DN digit rows, 2 DN key rows, c0 row, present diagonal rows
-        const int n_copies = 3 * DN + 1 + N2;
-        for (int cidx = lane; cidx < n_copies; cidx += 32) {
-            const u64 *src = nullptr;
-            u64 *dst = nullptr;
-            if (cidx < DN) {
-                src = dig + ((size_t)cidx * nl + l) * N + src_base;
-                dst = st + cidx * T;
-            } else if (cidx < 2 * DN) {
-                const int j = cidx - DN;
-                src = key + ((size_t)(2 * j) * nP + pid) * N + i0;
-                dst = st + (DN + j) * T;
-            } else if (cidx < 3 * DN) {
-                const int j = cidx - 2 * DN;
-                src = key + ((size_t)(2 * j + 1) * nP + pid) * N + i0;
-                dst = st + (2 * DN + j) * T;
-            } else if (cidx == 3 * DN) {
-                if (qlimb) {
-                    src = c0 + (size_t)l * N + src_base;
-                    dst = st + 3 * DN * T;
-                }
-            } else {
-                const int g = cidx - 3 * DN - 1;
-                const int di = sgb[g * n1 + b];
-                if (di >= 0) {
-                    src = diag[di] + (size_t)l * N + i0;
-                    dst = st + (3 * DN + 1 + g) * T;
-                }
+        int k = 0;
+        bool ok = true;
+        for (; k < nb; k++) {
+            const int s = k % S;
+            if (k >= S && !mbar_wait_bounded(&empty[s], (u32)(((k / S) - 1) & 1))) {
+                ok = false;
+                break;
             }
-            if (src) bulk_g2s(dst, src, T * 8, &bars[k % S]);
+            const int b = blist[k];
+            u64 *st = smem + s * SW;
+            const int src_base = auto_src(i0, logN, bk.gal[b]) & ~(T - 1);
+            const u64 *key = bk.key[b];
+            int nd = 0;
+            for (int g = 0; g < N2; g++) nd += sgb[g * n1 + b] >= 0;
+            if (lane == 0) mbar_arrive_expect_tx(&full[s], (u32)(3 * DN + (qlimb ? 1 : 0) + nd) * T * 8);
+            __syncwarp();
+            // rows: DN digit rows, 2 DN key rows, the c0 row, the present diagonal rows
+            for (int cidx = lane; cidx < 3 * DN + 1 + N2; cidx += 32) {
+                const u64 *src = nullptr;
+                u64 *dst = nullptr;
+                if (cidx < DN) {
+                    src = dig + ((size_t)cidx * nl + l) * N + src_base;
+                    dst = st + cidx * T;
+                } else if (cidx < 2 * DN) {
+                    const int j = cidx - DN;
+                    src = key + ((size_t)(2 * j) * nP + pid) * N + i0;
+                    dst = st + (DN + j) * T;
+                } else if (cidx < 3 * DN) {
+                    const int j = cidx - 2 * DN;
+                    src = key + ((size_t)(2 * j + 1) * nP + pid) * N + i0;
+                    dst = st + (2 * DN + j) * T;
+                } else if (cidx == 3 * DN) {
+                    if (qlimb) {
+                        src = c0 + (size_t)l * N + src_base;
+                        dst = st + 3 * DN * T;
+                    }
+                } else {
+                    const int g = cidx - 3 * DN - 1;
+                    const int di = sgb[g * n1 + b];
+                    if (di >= 0) {
+                        src = diag[di] + (size_t)l * N + i0;
+                        dst = st + (3 * DN + 1 + g) * T;
+                    }
+                }
+                if (src) bulk_g2s(dst, src, T * 8, &full[s]);
+            }
+            __syncwarp();
         }
-    };
+        if (!ok && lane == 0) {
+            atomicExch(err, (int)HELRM_E_TIMEOUT);
+            // let the copies already issued land before the CTA's shared memory goes away
+            for (int kk = (k >= S ? k - S : 0); kk < k; kk++) mbar_wait_bounded(&full[kk % S], (u32)((kk / S) & 1));
+        }
+        return;
+    }
 
-    if (tid < 32)
-        for (int k = 0; k < S && k < nb; k++) issue(k);
-
-    // 128-bit accumulators (one full product per diagonal word, one REDC at the end)
-    Acc128 a0[N2], a1[N2];
+    // ---------------- consumer warps: thread tid owns coefficient i0 + tid
+    const PrimeInfo pi = pinfo[pid];
+    const u64 pm = pmod[pid];
     const int i = i0 + tid;
     const size_t idx = (size_t)l * N + i;
-    if (need0) {   // baby 0 = (P c0, P c1): P mod q on the Q limbs, 0 on the P limbs
+    const int lane = tid & 31;
+    Acc128 a0[N2], a1[N2];   // one full product per diagonal word, one REDC at the end
+    if (need0) {             // baby 0 = (P c0, P c1): P mod q on the Q limbs, 0 on the P limbs
         const u64 v0 = qlimb ? mont_mul(c0[idx], pm, pi.q, pi.qinv) : 0;
         const u64 v1 = qlimb ? mont_mul(c1[idx], pm, pi.q, pi.qinv) : 0;
 #pragma unroll
@@ -186,58 +219,35 @@ __global__ void __launch_bounds__(T) k_bsgs_tma(u64 *__restrict__ inner, const u
             a1[g].mac(v1, d, pi.q);
         }
     }
-
-    bool aborted = false;
-    int k = 0;
-    for (; k < nb; k++) {
+    for (int k = 0; k < nb; k++) {
         const int s = k % S;
-        const u32 parity = (u32)((k / S) & 1);
-        bool ok = false;
-        for (long it = 0; it < WAIT_LIMIT; it++)
-            if (mbar_try_wait(&bars[s], parity)) {
-                ok = true;
-                break;
-            }
-        if (ok) {
-            const int b = blist[k];
-            const u64 *st = smem + s * SW;
-            const int src_loc = auto_src(i, logN, bk.gal[b]) - (auto_src(i0, logN, bk.gal[b]) & ~(T - 1));
-            Acc128 t0, t1;
+        if (!mbar_wait_bounded(&full[s], (u32)((k / S) & 1))) {
+            if (lane == 0) atomicExch(err, (int)HELRM_E_TIMEOUT);
+            return;   // no CTA barrier follows, so leaving early cannot deadlock
+        }
+        const int b = blist[k];
+        const u64 *st = smem + s * SW;
+        const int src_loc = auto_src(i, logN, bk.gal[b]) - (auto_src(i0, logN, bk.gal[b]) & ~(T - 1));
+        Acc128 t0, t1;
 #pragma unroll
-            for (int j = 0; j < DN; j++) {
-                const u64 d = st[j * T + src_loc];
-                t0.mac(d, st[(DN + j) * T + tid], pi.q);
-                t1.mac(d, st[(2 * DN + j) * T + tid], pi.q);
-            }
-            u64 v0 = t0.reduce(pi.q, pi.qinv);
-            const u64 v1 = t1.reduce(pi.q, pi.qinv);
-            if (qlimb) v0 = add_mod(v0, mont_mul(st[3 * DN * T + src_loc], pm, pi.q, pi.qinv), pi.q);
+        for (int j = 0; j < DN; j++) {
+            const u64 d = st[j * T + src_loc];
+            t0.mac(d, st[(DN + j) * T + tid], pi.q);
+            t1.mac(d, st[(2 * DN + j) * T + tid], pi.q);
+        }
+        u64 v0 = t0.reduce(pi.q, pi.qinv);
+        const u64 v1 = t1.reduce(pi.q, pi.qinv);
+        if (qlimb) v0 = add_mod(v0, mont_mul(st[3 * DN * T + src_loc], pm, pi.q, pi.qinv), pi.q);
+        u64 dd[N2];
 #pragma unroll
-            for (int g = 0; g < N2; g++) {
-                if (sgb[g * n1 + b] < 0) continue;
-                const u64 d = st[(3 * DN + 1 + g) * T + tid];
-                a0[g].mac(v0, d, pi.q);
-                a1[g].mac(v1, d, pi.q);
-            }
+        for (int g = 0; g < N2; g++) dd[g] = sgb[g * n1 + b] >= 0 ? st[(3 * DN + 1 + g) * T + tid] : 0;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);   // this warp is done with stage s
+#pragma unroll
+        for (int g = 0; g < N2; g++) {
+            a0[g].mac(v0, dd[g], pi.q);
+            a1[g].mac(v1, dd[g], pi.q);
         }
-        // one barrier per baby step: stage s is fully read before it is refilled,
-        // and a timeout anywhere in the CTA is seen by every thread
-        if (__syncthreads_or(!ok)) {
-            aborted = true;
-            break;
-        }
-        if (tid < 32 && k + S < nb) issue(k + S);
-    }
-    if (aborted) {
-        if (tid == 0) {
-            atomicExch(err, (int)HELRM_E_TIMEOUT);
-            // let the copies already issued land before the CTA's shared memory goes away
-            for (int kk = k; kk < nb && kk < k + S; kk++)
-                for (long it = 0; it < WAIT_LIMIT; it++)
-                    if (mbar_try_wait(&bars[kk % S], (u32)((kk / S) & 1))) break;
-        }
-        __syncthreads();
-        return;
     }
 #pragma unroll
     for (int g = 0; g < N2; g++) {
@@ -254,10 +264,10 @@ template <int N2, int DN>
 void launch(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c1, const TmaBabies &bk,
             const u64 *const *diag, const int *gb, int n1, int level)
 {
-    const size_t smem = (size_t)S * Stage<N2, DN>::WORDS * 8 + S * 8;
+    const size_t smem = (size_t)S * Stage<N2, DN>::WORDS * 8 + 2 * S * 8;
     CUDA_CHECK(cudaFuncSetAttribute(k_bsgs_tma<N2, DN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(c->N / T, level + 1 + c->K);
-    k_bsgs_tma<N2, DN><<<grid, T, smem, c->stream>>>(inner, digits, c0, c1, bk, diag, gb, n1, level, c->L, c->K,
+    k_bsgs_tma<N2, DN><<<grid, T + 32, smem, c->stream>>>(inner, digits, c0, c1, bk, diag, gb, n1, level, c->L, c->K,
                                                      c->logN, c->d_pmod_mont.u(), c->d_pinfo.as<PrimeInfo>(),
                                                      c->d_err.as<int>());
 }

@@ -302,6 +302,19 @@ struct Ciphertext : Handle {
 namespace k {
 void ntt_fwd(Ctx *c, u64 *data, int n_limbs, LimbMap map);
 void ntt_inv(Ctx *c, u64 *data, int n_limbs, LimbMap map);
+// One limb of a batched transform: the first pass reads src and writes dst,
+// the second works on dst.  With a forward transform and ea != nullptr, the
+// result is not stored in dst but as eo[i] = (ea[i] - NTT(y)[i]) * ep_scal[pid]
+// (+ eb[i] when eb != nullptr; eb may equal eo).
+struct NttLimb {
+    const u64 *src;
+    u64 *dst;
+    int pid;
+    const u64 *ea;
+    u64 *eo;
+    const u64 *eb;
+};
+void ntt_run(Ctx *c, const std::vector<NttLimb> &limbs, bool inverse, const u64 *ep_scal);
 // same as ntt_fwd / ntt_inv, with the launch list built on the stack (no heap use)
 void ntt_map_noheap(Ctx *c, u64 *data, int n_limbs, LimbMap map, bool inverse);
 // transform an arbitrary list of limbs (offset in limbs from base, prime id) in one launch pair
@@ -335,8 +348,11 @@ void bconv(Ctx *c, const BConvTable &t, const u64 *in_base, u64 *out_base);
 void bconv_modup(Ctx *c, int level, const u64 *coef, u64 *digits);
 // d_out[l][i] = sum_j dig_j[l][perm(i)] * key_j(l)[i] for the level-ell QP basis, both
 // polys of the key; if c0 != null, out0 on Q limbs += P * c0[perm(i)]
+// bq (optional): a QP polynomial whose image phi(bq) is added to the first
+// output; accumulate: add the result to what out already holds.
 void ks_inner_auto(Ctx *c, u64 *out, const u64 *digits, int dnum, const u64 *key, int level,
-                   u64 galois, const u64 *c0, const u64 *d_pmod_mont);
+                   u64 galois, const u64 *c0, const u64 *d_pmod_mont, const u64 *bq = nullptr,
+                   bool accumulate = false);
 // inner[g][2][limbs][N] = sum_b diag[(g,b)] * baby[b]
 void bsgs_mac(Ctx *c, u64 *inner, const u64 *baby, int n_baby, const u64 *const *d_diag_ptrs,
               const int *d_gb_index, int n2, int n1, int limbs, LimbMap map);
@@ -351,7 +367,7 @@ void bsgs_fused(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 
                 const u64 *gals, const u64 *const *d_diag_ptrs, const int *d_gb_index, int n_diag, int n1, int n2,
                 int level);
 // rescale helper: coefficient-form last limb -> centred residues for ell limbs
-void rescale_spread(Ctx *c, u64 *out, const u64 *last_coef, int level);
+void rescale_spread(Ctx *c, u64 *out, const u64 *last_coef, int level, int n_polys = 1);
 // random
 void chacha_words(Ctx *c, u32 *out, u64 seed, u32 purpose, u64 index, u64 first_word, u64 n_words);
 void sample_uniform(Ctx *c, u64 *out, u64 seed, u32 purpose, u64 index, int n_limbs,
@@ -372,7 +388,9 @@ void sigmoid(Ctx *c, double *d_p, const double *d_x, int n);
 Ciphertext *new_ct(Ctx *c, int level, double scale);
 void ks_modup(Ctx *c, const u64 *poly_ntt, int level, u64 *digits_out);
 void ks_moddown(Ctx *c, const u64 *qp_ntt, int level, u64 *out_ntt);
-void ks_moddown2(Ctx *c, const u64 *u, int level, u64 *out0, u64 *out1);
+// out_h = ModDown(u_h) (+ add_h when add_h != nullptr; add_h may equal out_h)
+void ks_moddown2(Ctx *c, const u64 *u, int level, u64 *out0, u64 *out1, const u64 *add0 = nullptr,
+                 const u64 *add1 = nullptr);
 Ciphertext *ct_rescale(Ctx *c, const Ciphertext *a);
 Ciphertext *ct_add(Ctx *c, const Ciphertext *a, const Ciphertext *b, bool subtract = false);
 Ciphertext *ct_add_pt(Ctx *c, const Ciphertext *a, const Plaintext *pt);

@@ -178,7 +178,7 @@ __device__ __forceinline__ int auto_src(int i, int logN, u64 galois)
 __global__ void k_ks_inner(u64 *__restrict__ out, const u64 *__restrict__ dig, int dnum,
                            const u64 *__restrict__ key, int level, int L, int K, int logN, u64 galois,
                            const u64 *__restrict__ c0, const u64 *__restrict__ pmod,
-                           const PrimeInfo *__restrict__ pinfo)
+                           const u64 *__restrict__ bq, int accumulate, const PrimeInfo *__restrict__ pinfo)
 {
     const size_t N = (size_t)1 << logN;
     const int nl = level + 1 + K, nP = L + 1 + K;
@@ -197,9 +197,15 @@ __global__ void k_ks_inner(u64 *__restrict__ out, const u64 *__restrict__ dig, i
             a1.mac(d, key[((size_t)(2 * j + 1) * nP + pid) * N + i], pi.q);
         }
         u64 r0 = a0.reduce(pi.q, pi.qinv);
+        u64 r1 = a1.reduce(pi.q, pi.qinv);
         if (c0 && l <= level) r0 = add_mod(r0, mont_mul(c0[(size_t)l * N + src], pmod[pid], pi.q, pi.qinv), pi.q);
+        if (bq) r0 = add_mod(r0, bq[(size_t)l * N + src], pi.q);
+        if (accumulate) {
+            r0 = add_mod(r0, out[idx], pi.q);
+            r1 = add_mod(r1, out[total + idx], pi.q);
+        }
         out[idx] = r0;
-        out[total + idx] = a1.reduce(pi.q, pi.qinv);
+        out[total + idx] = r1;
     }
 }
 
@@ -421,6 +427,8 @@ __global__ void k_rescale_spread(u64 *__restrict__ out, const u64 *__restrict__ 
     const size_t N = (size_t)1 << logN;
     const u64 ql = tab[2 * nP];
     const u64 half = (ql - 1) >> 1;
+    out += blockIdx.y * total;   // poly blockIdx.y: [level][N] from its own last limb
+    last += blockIdx.y * N;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
         const int l = (int)(idx >> logN);
@@ -766,13 +774,16 @@ void bconv_modup(Ctx *c, int level, const u64 *coef, u64 *digits)
 }
 
 void ks_inner_auto(Ctx *c, u64 *out, const u64 *digits, int dnum, const u64 *key, int level, u64 galois,
-                   const u64 *c0, const u64 *d_pmod_mont)
+                   const u64 *c0, const u64 *d_pmod_mont, const u64 *bq, bool accumulate)
 {
     size_t total = (size_t)(level + 1 + c->K) * c->N;
-    // digits once, both key halves once, c0 once (if added), two output polys
-    KTimer kt(c, "ks_inner_auto", 8.0 * (total * (3.0 * dnum + 2) + (c0 ? (double)(level + 1) * c->N : 0.0)));
+    // digits once, both key halves once, c0 / bq once (if added), two output polys
+    // written (and read, when accumulating)
+    KTimer kt(c, "ks_inner_auto", 8.0 * (total * (3.0 * dnum + (accumulate ? 4 : 2) + (bq ? 1 : 0)) +
+                                         (c0 ? (double)(level + 1) * c->N : 0.0)));
     k_ks_inner<<<grid_for(total), TPB, 0, c->stream>>>(out, digits, dnum, key, level, c->L, c->K, c->logN, galois,
-                                                       c0, d_pmod_mont, c->d_pinfo.as<PrimeInfo>());
+                                                       c0, d_pmod_mont, bq, accumulate ? 1 : 0,
+                                                       c->d_pinfo.as<PrimeInfo>());
     LAUNCHED(c);
 }
 void automorphism(Ctx *c, u64 *out, const u64 *in, int n_limbs, u64 galois)
@@ -856,12 +867,12 @@ void bsgs_fused(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 
     LAUNCHED(c);
 }
 
-void rescale_spread(Ctx *c, u64 *out, const u64 *last_coef, int level)
+void rescale_spread(Ctx *c, u64 *out, const u64 *last_coef, int level, int n_polys)
 {
     size_t total = (size_t)level * c->N;
     if (!total) return;
-    KTimer kt(c, "rescale_spread", 8.0 * (total + c->N));
-    k_rescale_spread<<<grid_for(total), TPB, 0, c->stream>>>(out, last_coef, c->rescale_table(level), c->nP(),
+    KTimer kt(c, "rescale_spread", 8.0 * n_polys * (total + c->N));
+    k_rescale_spread<<<dim3(grid_for(total), n_polys), TPB, 0, c->stream>>>(out, last_coef, c->rescale_table(level), c->nP(),
                                                              c->logN, total, c->d_pinfo.as<PrimeInfo>());
     LAUNCHED(c);
 }

@@ -150,28 +150,22 @@ Ciphertext *matvec(Ctx *c, const EvalKey *evk, const PtMatrix *m, const Cipherte
         k::bsgs_mac(c, inner.u(), baby.u(), (int)m->gb.size(), m->d_ptrs.as<const u64 *>(), m->d_gb_index.as<int>(),
                     m->n2, m->n1, nl, c->qmap(l));
     }
-    DevMem acc(c, 2 * plane * 8), c1q(c, (size_t)nq * N * 8), t(c, 2 * plane * 8), phi(c, plane * 8);
-    k::zero(c, acc.u(), 2 * plane);
-    const LimbMap qp2 = c->qmap(l, 0, nl), qp = c->qmap(l);
-    for (int g = 0; g < m->n2; g++) {
+    // the giant steps accumulate into inner_0
+    u64 *acc = inner.u();
+    DevMem c1q(c, (size_t)nq * N * 8);
+    if (!need_g[0]) k::zero(c, acc, 2 * plane);
+    for (int g = 1; g < m->n2; g++) {
         if (!need_g[g]) continue;
         const u64 *ig = inner.u() + (size_t)g * 2 * plane;
-        if (g == 0) {
-            k::add(c, acc.u(), acc.u(), ig, 2 * nl, qp2);
-            continue;
-        }
-        // giant step on a QP ciphertext: ModDown the a-part, ModUp, phi, key inner product;
-        // the b-part is already over QP and only gets phi
+        // giant step on a QP ciphertext: ModDown the a-part, ModUp, then one kernel
+        // adds the key inner product and phi of the b-part (already over QP) to acc
         const u64 gal = c->galois(g * m->n1);
         ks_moddown(c, ig + plane, l, c1q.u());
         ks_modup(c, c1q.u(), l, digits.u());
-        k::ks_inner_auto(c, t.u(), digits.u(), dnum, gkey[g]->data.u(), l, gal, nullptr, nullptr);
-        k::automorphism(c, phi.u(), ig, nl, gal);
-        k::add(c, acc.u(), acc.u(), phi.u(), nl, qp);
-        k::add(c, acc.u(), acc.u(), t.u(), 2 * nl, qp2);
+        k::ks_inner_auto(c, acc, digits.u(), dnum, gkey[g]->data.u(), l, gal, nullptr, nullptr, ig, true);
     }
     std::unique_ptr<Ciphertext> o(new_ct(c, l, in->scale * m->pt_scale));
-    ks_moddown2(c, acc.u(), l, o->c0(), o->c1());
+    ks_moddown2(c, acc, l, o->c0(), o->c1());
     std::unique_ptr<Ciphertext> y(ct_rescale(c, o.get()));
     y->scale = m->out_scale;
     for (int f : m->folds) {

@@ -3,7 +3,9 @@
 // Forward: merged Cooley-Tukey (twiddle psi^brv(m+i) at stage m, block i),
 // standard order in, bit-reversed evaluation order out:
 // ahat[i] = a(psi^(2 brv(i) + 1)).  Inverse: merged Gentleman-Sande with
-// psi^-brv(m+i), then 1/N.  Twiddles carry Shoup quotients.
+// psi^-brv(m+i), then 1/N.  Twiddles carry Shoup quotients; butterflies are
+// Harvey's lazy ones (values in [0, 4q) forward, [0, 2q) inverse, q < 2^62),
+// corrected once at the end.
 //
 // N = N1 * N2 runs as two passes, each reading and writing every limb once.
 // The first log2(N1) stages pair elements N/2..N2 apart, so each of the N2
@@ -13,61 +15,74 @@
 // round (a radix-8 step); shared memory is used only to regroup elements
 // between rounds, so a 256-point sub-transform costs two barriers.  Loads and
 // stores are coalesced: consecutive threads take consecutive columns (column
-// pass) or consecutive elements of a row (row pass).  A launch takes any list
-// of limbs (offset, prime), so a whole ModUp or ModDown is one transform.
+// pass) or consecutive elements of a row (row pass).
+//
+// A launch takes a list of limbs, each with its own source, destination and
+// prime: the first pass reads the source and writes the destination (so no
+// copy is needed before a transform), the second works in place.  A forward
+// transform may end with a fused epilogue out = (a - NTT(y)) * c[prime] (+ b)
+// (c a Montgomery constant), which is how ModDown and rescale finish.
 #include "core.cuh"
 
 namespace helrm {
 namespace {
 
-constexpr int MAX_LIMBS = 256;
+constexpr int MAX_LIMBS = 128;
 constexpr int TILE = 4096;   // words per CTA (32 KB of data)
 
 struct LimbList {
     int n;
-    u32 off[MAX_LIMBS];   // limb offset from the base pointer, in limbs
+    const u64 *src[MAX_LIMBS];
+    u64 *dst[MAX_LIMBS];
+    const u64 *ea[MAX_LIMBS];   // epilogue a operand (nullptr: no epilogue)
+    const u64 *eb[MAX_LIMBS];   // epilogue addend (nullptr: none)
+    u64 *eo[MAX_LIMBS];         // epilogue output
     unsigned short pid[MAX_LIMBS];
 };
 
 __device__ __forceinline__ int pad(int e) { return e + (e >> 4); }
 
-// Harvey's lazy butterflies (all values < 4q < 2^64 since every q < 2^62).
 // Shoup product without its final correction: a * w mod q in [0, 2q).
 __device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 wp, u64 q) { return a * w - mulhi64(a, wp) * q; }
+// x >= m ? x - m : x, as one 64-bit min (x - m wraps above x when x < m)
+__device__ __forceinline__ u64 csub(u64 x, u64 m)
+{
+    const u64 y = x - m;
+    return y < x ? y : x;
+}
 // forward (Cooley-Tukey): x0, x1 in [0, 4q) -> [0, 4q)
 __device__ __forceinline__ void bfly_ct(u64 &x0, u64 &x1, u64 w, u64 wp, u64 q, u64 q2)
 {
-    u64 a = x0 >= q2 ? x0 - q2 : x0;
-    u64 t = shoup_lazy(x1, w, wp, q);
+    const u64 a = csub(x0, q2);
+    const u64 t = shoup_lazy(x1, w, wp, q);
     x0 = a + t;
     x1 = a - t + q2;
 }
 // inverse (Gentleman-Sande): x0, x1 in [0, 2q) -> [0, 2q)
 __device__ __forceinline__ void bfly_gs(u64 &x0, u64 &x1, u64 w, u64 wp, u64 q, u64 q2)
 {
-    u64 s = x0 + x1;
-    s = s >= q2 ? s - q2 : s;
-    u64 t = x0 - x1 + q2;
+    const u64 s = csub(x0 + x1, q2);
+    const u64 t = x0 - x1 + q2;
     x0 = s;
     x1 = shoup_lazy(t, w, wp, q);
 }
-// [0, 4q) -> [0, q)
-__device__ __forceinline__ u64 reduce4(u64 x, u64 q, u64 q2)
-{
-    x = x >= q2 ? x - q2 : x;
-    return x >= q ? x - q : x;
-}
 
-// One pass of the forward transform over sub-transforms of P = 2^LOGP points.
-// COLS: sub-transform g is column c0+g of the limb, elements r*N2 + c.
-// ROWS: sub-transform g is row r0+g, elements (r0+g)*N2 + x.
+enum Mode { M_LAZY = 0, M_SCALE = 1, M_REDUCE = 2 };
+
+// One pass over sub-transforms of P = 2^LOGP points.
+// COLS: sub-transform g is column g of the limb, elements r*N2 + g.
+// ROWS: sub-transform g is row g, elements g*N2 + x.
 // Twiddle of local stage s, local block lb: tw[((bm + seg) << s) + lb], with
 // bm = 1, seg = 0 for the column pass and bm = N1, seg = row for the row pass.
+// mode: M_LAZY leaves the lazy range (first pass), M_SCALE multiplies by 1/N
+// (last inverse pass), M_REDUCE reduces to [0, q) (last forward pass) and
+// applies the epilogue where the limb has one.
 template <int LOGP, bool COLS, bool INV>
-__global__ void __launch_bounds__(512) k_ntt_pass(u64 *data, int logN, int logG, LimbList list,
+__global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN, int logG, LimbList list,
                                                    const ulonglong2 *__restrict__ tw_all,
                                                    const ulonglong2 *__restrict__ ninv,
-                                                   const PrimeInfo *__restrict__ pinfo, int scale_out)
+                                                   const PrimeInfo *__restrict__ pinfo, int mode,
+                                                   const u64 *__restrict__ ep_scal)
 {
     constexpr int P = 1 << LOGP;
     constexpr int TPS = P / 8;              // threads per sub-transform
@@ -76,11 +91,17 @@ __global__ void __launch_bounds__(512) k_ntt_pass(u64 *data, int logN, int logG,
     const int logN1 = logN / 2;
     const int N2 = N >> logN1;
     const int G = 1 << logG;                // sub-transforms per CTA
-    const int pid = list.pid[blockIdx.y];
-    const u64 q = pinfo[pid].q;
+    const int y = blockIdx.y;
+    const int pid = list.pid[y];
+    const PrimeInfo pi = pinfo[pid];
+    const u64 q = pi.q;
     const u64 q2 = 2 * q;
     const ulonglong2 *tw = tw_all + (size_t)pid * N;
-    u64 *a = data + (size_t)list.off[blockIdx.y] * N;
+    const u64 *in = first ? list.src[y] : list.dst[y];
+    u64 *out = list.dst[y];
+    const u64 *ea = list.ea[y];
+    const u64 *eb = list.eb[y];
+    u64 *eo = list.eo[y];
     const int tid = threadIdx.x;
     // thread -> (sub-transform g, lane tt); for COLS, g varies fastest so a
     // warp reads consecutive columns of one row.
@@ -103,7 +124,8 @@ __global__ void __launch_bounds__(512) k_ntt_pass(u64 *data, int logN, int logG,
     u64 v[8];
     // rounds of up to three stages; forward goes first-to-last, inverse last-to-first
     constexpr int NR = (LOGP + 2) / 3;
-    _Pragma("unroll") for (int rr = 0; rr < NR; rr++) {
+#pragma unroll
+    for (int rr = 0; rr < NR; rr++) {
         const int rho = INV ? NR - 1 - rr : rr;
         const int s0 = 3 * rho;
         const int r = (s0 + 3 <= LOGP) ? 3 : LOGP - s0;
@@ -117,21 +139,28 @@ __global__ void __launch_bounds__(512) k_ntt_pass(u64 *data, int logN, int logG,
             return blk * (T * gs) + boff + k * T;
         };
         if (rr == 0) {
-            _Pragma("unroll") for (int qg = 0; qg < ng; qg++)
-                _Pragma("unroll") for (int k = 0; k < gs; k++) v[qg * gs + k] = a[gaddr(elem(qg, k))];
+#pragma unroll
+            for (int qg = 0; qg < ng; qg++)
+#pragma unroll
+                for (int k = 0; k < gs; k++) v[qg * gs + k] = in[gaddr(elem(qg, k))];
         } else {
             __syncthreads();
-            _Pragma("unroll") for (int qg = 0; qg < ng; qg++)
-                _Pragma("unroll") for (int k = 0; k < gs; k++) v[qg * gs + k] = sm[saddr(elem(qg, k))];
+#pragma unroll
+            for (int qg = 0; qg < ng; qg++)
+#pragma unroll
+                for (int k = 0; k < gs; k++) v[qg * gs + k] = sm[saddr(elem(qg, k))];
         }
-        _Pragma("unroll") for (int qg = 0; qg < ng; qg++) {
+#pragma unroll
+        for (int qg = 0; qg < ng; qg++) {
             u64 *x = v + qg * gs;
             const int e0 = elem(qg, 0);
             if (!INV) {
-                _Pragma("unroll") for (int u = 0; u < r; u++) {
+#pragma unroll
+                for (int u = 0; u < r; u++) {
                     const int s = s0 + u;
                     const int half = gs >> (u + 1);
-                    _Pragma("unroll") for (int k1 = 0; k1 < gs; k1++) {
+#pragma unroll
+                    for (int k1 = 0; k1 < gs; k1++) {
                         if (k1 & half) continue;
                         const int lb = (e0 + k1 * T) >> (LOGP - s);
                         const ulonglong2 w = tw[((bm + seg) << s) + lb];
@@ -139,10 +168,12 @@ __global__ void __launch_bounds__(512) k_ntt_pass(u64 *data, int logN, int logG,
                     }
                 }
             } else {
-                _Pragma("unroll") for (int u = r - 1; u >= 0; u--) {
+#pragma unroll
+                for (int u = r - 1; u >= 0; u--) {
                     const int s = s0 + u;
                     const int half = gs >> (u + 1);
-                    _Pragma("unroll") for (int k1 = 0; k1 < gs; k1++) {
+#pragma unroll
+                    for (int k1 = 0; k1 < gs; k1++) {
                         if (k1 & half) continue;
                         const int lb = (e0 + k1 * T) >> (LOGP - s);
                         const ulonglong2 w = tw[((bm + seg) << s) + lb];
@@ -153,29 +184,41 @@ __global__ void __launch_bounds__(512) k_ntt_pass(u64 *data, int logN, int logG,
         }
         if (rr + 1 < NR) {
             if (rr > 0) __syncthreads();    // everyone has read the previous round's layout
-            _Pragma("unroll") for (int qg = 0; qg < ng; qg++)
-                _Pragma("unroll") for (int k = 0; k < gs; k++) sm[saddr(elem(qg, k))] = v[qg * gs + k];
+#pragma unroll
+            for (int qg = 0; qg < ng; qg++)
+#pragma unroll
+                for (int k = 0; k < gs; k++) sm[saddr(elem(qg, k))] = v[qg * gs + k];
         } else {
-            // the last pass of a transform leaves canonical residues: forward rows
-            // reduce [0, 4q) -> [0, q); inverse columns multiply by 1/N (full
-            // reduction).  The first pass leaves its lazy range for the second.
             ulonglong2 ni = make_ulonglong2(0, 0);
-            if (scale_out) ni = ninv[pid];
-            _Pragma("unroll") for (int qg = 0; qg < ng; qg++)
-                _Pragma("unroll") for (int k = 0; k < gs; k++) {
-                    u64 y = v[qg * gs + k];
-                    if (scale_out)
-                        y = shoup_mul(y, ni.x, ni.y, q);
-                    else if (!COLS && !INV)
-                        y = reduce4(y, q, q2);
-                    a[gaddr(elem(qg, k))] = y;
+            u64 ec = 0;
+            if (mode == M_SCALE) ni = ninv[pid];
+            if (mode == M_REDUCE && ea) ec = ep_scal[pid];
+#pragma unroll
+            for (int qg = 0; qg < ng; qg++)
+#pragma unroll
+                for (int k = 0; k < gs; k++) {
+                    u64 z = v[qg * gs + k];
+                    const size_t a = gaddr(elem(qg, k));
+                    if (mode == M_SCALE) {
+                        out[a] = shoup_mul(z, ni.x, ni.y, q);
+                    } else if (mode == M_REDUCE) {
+                        z = csub(csub(z, q2), q);
+                        if (ea) {
+                            u64 w = mont_mul(sub_mod(ea[a], z, q), ec, q, pi.qinv);
+                            if (eb) w = add_mod(w, eb[a], q);
+                            eo[a] = w;
+                        } else
+                            out[a] = z;
+                    } else {
+                        out[a] = z;
+                    }
                 }
         }
     }
 }
 
 template <int LOGP, bool COLS, bool INV>
-void launch_pass(Ctx *c, u64 *data, const LimbList &ll, int n_sub, int scale_out)
+void launch_pass(Ctx *c, const LimbList &ll, int n_sub, int first, int mode, const u64 *ep_scal)
 {
     constexpr int P = 1 << LOGP;
     // sub-transforms per CTA: as many as fit a 4096-word tile, fewer when the
@@ -190,104 +233,112 @@ void launch_pass(Ctx *c, u64 *data, const LimbList &ll, int n_sub, int scale_out
     const size_t smem = (size_t)(G * P + (G * P >> 4) + 1) * 8;
     dim3 grid(n_sub / G, ll.n);
     const ulonglong2 *tw = INV ? c->d_tw_inv.as<ulonglong2>() : c->d_tw_fwd.as<ulonglong2>();
-    k_ntt_pass<LOGP, COLS, INV><<<grid, threads, smem, c->stream>>>(data, c->logN, logG, ll, tw,
-                                                                   c->d_ninv.as<ulonglong2>(),
-                                                                   c->d_pinfo.as<PrimeInfo>(), scale_out);
+    k_ntt_pass<LOGP, COLS, INV><<<grid, threads, smem, c->stream>>>(
+        first, c->logN, logG, ll, tw, c->d_ninv.as<ulonglong2>(), c->d_pinfo.as<PrimeInfo>(), mode, ep_scal);
 }
 
 template <bool COLS, bool INV>
-void dispatch(Ctx *c, int logp, u64 *data, const LimbList &ll, int n_sub, int scale_out)
+void dispatch(Ctx *c, int logp, const LimbList &ll, int n_sub, int first, int mode, const u64 *ep_scal)
 {
     switch (logp) {
-    case 5: launch_pass<5, COLS, INV>(c, data, ll, n_sub, scale_out); break;
-    case 6: launch_pass<6, COLS, INV>(c, data, ll, n_sub, scale_out); break;
-    case 7: launch_pass<7, COLS, INV>(c, data, ll, n_sub, scale_out); break;
-    case 8: launch_pass<8, COLS, INV>(c, data, ll, n_sub, scale_out); break;
+    case 5: launch_pass<5, COLS, INV>(c, ll, n_sub, first, mode, ep_scal); break;
+    case 6: launch_pass<6, COLS, INV>(c, ll, n_sub, first, mode, ep_scal); break;
+    case 7: launch_pass<7, COLS, INV>(c, ll, n_sub, first, mode, ep_scal); break;
+    case 8: launch_pass<8, COLS, INV>(c, ll, n_sub, first, mode, ep_scal); break;
     default: fail(HELRM_E_PARAM, "unsupported NTT size");
     }
 }
 
-void run(Ctx *c, u64 *data, const std::vector<std::pair<u32, int>> &limbs, bool inverse)
+// both passes of one launch list
+void run_list(Ctx *c, const LimbList &ll, bool inverse, const u64 *ep_scal)
 {
-    if (limbs.empty()) return;
     const int logN = c->logN, logN1 = logN / 2, logN2 = logN - logN1;
     const int N1 = 1 << logN1, N2 = 1 << logN2;
-    KTimer kt(c, "ntt", 16.0 * c->N * limbs.size());   // algorithmic: each limb read and written once
-    for (size_t b = 0; b < limbs.size(); b += MAX_LIMBS) {
-        LimbList ll;
-        ll.n = (int)std::min<size_t>(MAX_LIMBS, limbs.size() - b);
-        for (int i = 0; i < ll.n; i++) {
-            ll.off[i] = limbs[b + i].first;
-            ll.pid[i] = (unsigned short)limbs[b + i].second;
-        }
-        if (!inverse) {
-            dispatch<true, false>(c, logN1, data, ll, N2, 0);
-            dispatch<false, false>(c, logN2, data, ll, N1, 0);
-        } else {
-            dispatch<false, true>(c, logN2, data, ll, N1, 0);
-            dispatch<true, true>(c, logN1, data, ll, N2, 1);
-        }
-        c->launches += 2;
-        CUDA_CHECK(cudaGetLastError());
+    if (!inverse) {
+        dispatch<true, false>(c, logN1, ll, N2, 1, M_LAZY, nullptr);
+        dispatch<false, false>(c, logN2, ll, N1, 0, M_REDUCE, ep_scal);
+    } else {
+        dispatch<false, true>(c, logN2, ll, N1, 1, M_LAZY, nullptr);
+        dispatch<true, true>(c, logN1, ll, N2, 0, M_SCALE, nullptr);
     }
+    c->launches += 2;
+    CUDA_CHECK(cudaGetLastError());
 }
 
 }  // namespace
 
 namespace k {
 
-void ntt_list(Ctx *c, u64 *base, const std::vector<std::pair<u32, int>> &limbs, bool inverse)
+void ntt_run(Ctx *c, const std::vector<NttLimb> &limbs, bool inverse, const u64 *ep_scal)
 {
-    run(c, base, limbs, inverse);
+    if (limbs.empty()) return;
+    KTimer kt(c, "ntt", 16.0 * c->N * limbs.size());   // algorithmic: each limb read and written once
+    for (size_t b = 0; b < limbs.size(); b += MAX_LIMBS) {
+        LimbList ll;
+        ll.n = (int)std::min<size_t>(MAX_LIMBS, limbs.size() - b);
+        for (int i = 0; i < ll.n; i++) {
+            const NttLimb &x = limbs[b + i];
+            ll.src[i] = x.src;
+            ll.dst[i] = x.dst;
+            ll.ea[i] = x.ea;
+            ll.eb[i] = x.eb;
+            ll.eo[i] = x.eo;
+            ll.pid[i] = (unsigned short)x.pid;
+        }
+        run_list(c, ll, inverse, ep_scal);
+    }
 }
 
-// Contiguous limbs described by a LimbMap; the launch list is built on the
-// stack (no heap or device allocation on this path).
-static void run_map(Ctx *c, u64 *data, int n_limbs, LimbMap map, bool inverse)
+// Contiguous limbs described by a LimbMap, in place; the launch list is built
+// on the stack (no heap or device allocation on this path).
+void ntt_map_noheap(Ctx *c, u64 *data, int n_limbs, LimbMap map, bool inverse)
 {
     if (n_limbs <= 0) return;
-    const int logN = c->logN, logN1 = logN / 2, logN2 = logN - logN1;
-    const int N1 = 1 << logN1, N2 = 1 << logN2;
     KTimer kt(c, "ntt", 16.0 * c->N * n_limbs);
+    const size_t N = (size_t)c->N;
     for (int b = 0; b < n_limbs; b += MAX_LIMBS) {
         LimbList ll;
         ll.n = std::min(MAX_LIMBS, n_limbs - b);
         for (int i = 0; i < ll.n; i++) {
-            ll.off[i] = (u32)(b + i);
+            ll.src[i] = ll.dst[i] = data + (size_t)(b + i) * N;
+            ll.ea[i] = nullptr;
+            ll.eb[i] = nullptr;
+            ll.eo[i] = nullptr;
             ll.pid[i] = (unsigned short)map.pid(b + i);
         }
-        if (!inverse) {
-            dispatch<true, false>(c, logN1, data, ll, N2, 0);
-            dispatch<false, false>(c, logN2, data, ll, N1, 0);
-        } else {
-            dispatch<false, true>(c, logN2, data, ll, N1, 0);
-            dispatch<true, true>(c, logN1, data, ll, N2, 1);
-        }
-        c->launches += 2;
-        CUDA_CHECK(cudaGetLastError());
+        run_list(c, ll, inverse, nullptr);
     }
 }
 
-void ntt_map_noheap(Ctx *c, u64 *data, int n_limbs, LimbMap map, bool inverse)
+void ntt_list(Ctx *c, u64 *base, const std::vector<std::pair<u32, int>> &limbs, bool inverse)
 {
-    run_map(c, data, n_limbs, map, inverse);
-}
-
-static std::vector<std::pair<u32, int>> from_map(int n_limbs, LimbMap map)
-{
-    std::vector<std::pair<u32, int>> v(n_limbs);
-    for (int l = 0; l < n_limbs; l++) v[l] = {(u32)l, map.pid(l)};
-    return v;
+    std::vector<NttLimb> v;
+    v.reserve(limbs.size());
+    for (auto &x : limbs) {
+        u64 *p = base + (size_t)x.first * c->N;
+        v.push_back({p, p, x.second, nullptr, nullptr, nullptr});
+    }
+    ntt_run(c, v, inverse, nullptr);
 }
 
 void ntt_fwd(Ctx *c, u64 *data, int n_limbs, LimbMap map)
 {
-    if (n_limbs > 0) run(c, data, from_map(n_limbs, map), false);
+    std::vector<NttLimb> v;
+    for (int l = 0; l < n_limbs; l++) {
+        u64 *p = data + (size_t)l * c->N;
+        v.push_back({p, p, map.pid(l), nullptr, nullptr, nullptr});
+    }
+    ntt_run(c, v, false, nullptr);
 }
 
 void ntt_inv(Ctx *c, u64 *data, int n_limbs, LimbMap map)
 {
-    if (n_limbs > 0) run(c, data, from_map(n_limbs, map), true);
+    std::vector<NttLimb> v;
+    for (int l = 0; l < n_limbs; l++) {
+        u64 *p = data + (size_t)l * c->N;
+        v.push_back({p, p, map.pid(l), nullptr, nullptr, nullptr});
+    }
+    ntt_run(c, v, true, nullptr);
 }
 
 }  // namespace k

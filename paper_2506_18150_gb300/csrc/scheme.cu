@@ -34,12 +34,13 @@ Ciphertext *new_ct(Ctx *c, int level, double scale)
 void ks_modup(Ctx *c, const u64 *poly, int level, u64 *digits)
 {
     const int N = c->N, nq = level + 1, nl = nq + c->K;
+    const LimbMap m = c->qmap(level);
     DevMem coef(c, (size_t)nq * N * 8);
-    k::copy(c, coef.u(), poly, (size_t)nq * N);
-    k::ntt_inv(c, coef.u(), nq, c->qmap(level));
+    std::vector<k::NttLimb> v;   // iNTT straight from the input into coef
+    for (int l = 0; l < nq; l++) v.push_back({poly + (size_t)l * N, coef.u() + (size_t)l * N, m.pid(l), nullptr, nullptr});
+    k::ntt_run(c, v, true, nullptr);
     k::bconv_modup(c, level, coef.u(), digits);
     std::vector<std::pair<u32, int>> targets;   // every converted limb of every digit
-    const LimbMap m = c->qmap(level);
     for (int j = 0; j < c->dnum(level); j++) {
         u64 *d = digits + (size_t)j * nl * N;
         const int lo = c->digit_lo(j), hi = c->digit_hi(j, level);
@@ -51,29 +52,47 @@ void ks_modup(Ctx *c, const u64 *poly, int level, u64 *digits)
 }
 
 // ModDown of both halves of a QP ciphertext u = [2][nl][N] into out0, out1.
-void ks_moddown2(Ctx *c, const u64 *u, int level, u64 *out0, u64 *out1)
+// The iNTT reads the P limbs of u in place of a copy; the forward NTT of the
+// converted limbs ends with out = (u - y) * P^-1 (+ add) fused into its last pass.
+void ks_moddown2(Ctx *c, const u64 *u, int level, u64 *out0, u64 *out1, const u64 *add0, const u64 *add1)
 {
     const int N = c->N, nq = level + 1, K = c->K, nl = nq + K;
+    const LimbMap m = c->qmap(level);
     DevMem pc(c, (size_t)2 * K * N * 8), y(c, (size_t)2 * nq * N * 8);
-    k::copy(c, pc.u(), u + (size_t)nq * N, (size_t)K * N);
-    k::copy(c, pc.u() + (size_t)K * N, u + (size_t)(nl + nq) * N, (size_t)K * N);
-    k::ntt_inv(c, pc.u(), 2 * K, c->qmap(level, nq, K));
+    std::vector<k::NttLimb> v;
+    for (int h = 0; h < 2; h++)
+        for (int i = 0; i < K; i++)
+            v.push_back({u + (size_t)(h * nl + nq + i) * N, pc.u() + (size_t)(h * K + i) * N, m.pid(nq + i), nullptr, nullptr});
+    k::ntt_run(c, v, true, nullptr);
     k::bconv(c, c->moddown_table(level), pc.u(), y.u());
     k::bconv(c, c->moddown_table(level), pc.u() + (size_t)K * N, y.u() + (size_t)nq * N);
-    k::ntt_fwd(c, y.u(), 2 * nq, c->qmap(level, 0, nq));
-    k::sub_mul_scalar(c, out0, u, y.u(), c->d_pinv_mont.u(), nq, c->qmap(level));
-    k::sub_mul_scalar(c, out1, u + (size_t)nl * N, y.u() + (size_t)nq * N, c->d_pinv_mont.u(), nq, c->qmap(level));
+    v.clear();
+    for (int h = 0; h < 2; h++)
+        for (int l = 0; l < nq; l++) {
+            u64 *yl = y.u() + (size_t)(h * nq + l) * N;
+            const u64 *ad = h ? add1 : add0;
+            v.push_back({yl, yl, m.pid(l), u + (size_t)(h * nl + l) * N, (h ? out1 : out0) + (size_t)l * N,
+                         ad ? ad + (size_t)l * N : nullptr});
+        }
+    k::ntt_run(c, v, false, c->d_pinv_mont.u());
 }
 
 void ks_moddown(Ctx *c, const u64 *u, int level, u64 *out)
 {
     const int N = c->N, nq = level + 1, K = c->K;
+    const LimbMap m = c->qmap(level);
     DevMem pc(c, (size_t)K * N * 8), y(c, (size_t)nq * N * 8);
-    k::copy(c, pc.u(), u + (size_t)nq * N, (size_t)K * N);
-    k::ntt_inv(c, pc.u(), K, c->qmap(level, nq));
+    std::vector<k::NttLimb> v;
+    for (int i = 0; i < K; i++)
+        v.push_back({u + (size_t)(nq + i) * N, pc.u() + (size_t)i * N, m.pid(nq + i), nullptr, nullptr});
+    k::ntt_run(c, v, true, nullptr);
     k::bconv(c, c->moddown_table(level), pc.u(), y.u());
-    k::ntt_fwd(c, y.u(), nq, c->qmap(level));
-    k::sub_mul_scalar(c, out, u, y.u(), c->d_pinv_mont.u(), nq, c->qmap(level));
+    v.clear();
+    for (int l = 0; l < nq; l++) {
+        u64 *yl = y.u() + (size_t)l * N;
+        v.push_back({yl, yl, m.pid(l), u + (size_t)l * N, out + (size_t)l * N});
+    }
+    k::ntt_run(c, v, false, c->d_pinv_mont.u());
 }
 
 const SwitchKey *rot_key(const EvalKey *evk, u64 galois)
@@ -145,15 +164,18 @@ Ciphertext *ct_rescale(Ctx *c, const Ciphertext *a)
     HCHECK(l >= 1, HELRM_E_LEVEL, "no level left to rescale");
     std::unique_ptr<Ciphertext> o(new_ct(c, l - 1, a->scale / (double)c->primes[l]));
     DevMem last(c, (size_t)2 * N * 8), r(c, (size_t)2 * l * N * 8);
-    k::copy(c, last.u(), a->c0() + (size_t)l * N, N);
-    k::copy(c, last.u() + N, a->c1() + (size_t)l * N, N);
-    k::ntt_inv(c, last.u(), 2, c->qmap(l, l, 1));
-    k::rescale_spread(c, r.u(), last.u(), l);
-    k::rescale_spread(c, r.u() + (size_t)l * N, last.u() + N, l);
-    k::ntt_fwd(c, r.u(), 2 * l, c->qmap(l - 1, 0, l));
-    const u64 *qinv = c->rescale_table(l);
-    k::sub_mul_scalar(c, o->c0(), a->c0(), r.u(), qinv, l, c->qmap(l - 1));
-    k::sub_mul_scalar(c, o->c1(), a->c1(), r.u() + (size_t)l * N, qinv, l, c->qmap(l - 1));
+    std::vector<k::NttLimb> v = {{a->c0() + (size_t)l * N, last.u(), l, nullptr, nullptr},
+                                 {a->c1() + (size_t)l * N, last.u() + N, l, nullptr, nullptr}};
+    k::ntt_run(c, v, true, nullptr);
+    k::rescale_spread(c, r.u(), last.u(), l, 2);
+    // out = (a - r) * q_l^-1, fused into the last pass of the forward NTT of r
+    v.clear();
+    for (int h = 0; h < 2; h++)
+        for (int i = 0; i < l; i++) {
+            u64 *ri = r.u() + (size_t)(h * l + i) * N;
+            v.push_back({ri, ri, i, (h ? a->c1() : a->c0()) + (size_t)i * N, (h ? o->c1() : o->c0()) + (size_t)i * N});
+        }
+    k::ntt_run(c, v, false, c->rescale_table(l));
     return o.release();
 }
 
@@ -165,7 +187,7 @@ void ct_rotate_hoisted(Ctx *c, const EvalKey *evk, const Ciphertext *a, const st
     std::vector<std::unique_ptr<Ciphertext>> res;
     std::vector<const SwitchKey *> keys;
     for (int st : steps) keys.push_back(c->galois(st) == 1 ? nullptr : rot_key(evk, c->galois(st)));
-    DevMem digits(c, (size_t)dnum * nl * N * 8), u(c, (size_t)2 * nl * N * 8), t(c, (size_t)nq * N * 8);
+    DevMem digits(c, (size_t)dnum * nl * N * 8), u(c, (size_t)2 * nl * N * 8);
     ks_modup(c, a->c1(), l, digits.u());
     for (size_t s = 0; s < steps.size(); s++) {
         u64 g = c->galois(steps[s]);
@@ -174,9 +196,8 @@ void ct_rotate_hoisted(Ctx *c, const EvalKey *evk, const Ciphertext *a, const st
             k::copy(c, o->data.u(), a->data.u(), (size_t)2 * nq * N);
         } else {
             k::ks_inner_auto(c, u.u(), digits.u(), dnum, keys[s]->data.u(), l, g, nullptr, nullptr);
-            ks_moddown2(c, u.u(), l, t.u(), o->c1());
             k::automorphism(c, o->c0(), a->c0(), nq, g);
-            k::add(c, o->c0(), o->c0(), t.u(), nq, c->qmap(l));
+            ks_moddown2(c, u.u(), l, o->c0(), o->c1(), o->c0());   // phi(c0) + ModDown(u_0)
         }
         res.push_back(std::move(o));
     }
@@ -207,8 +228,7 @@ Ciphertext *ct_relin(Ctx *c, const EvalKey *evk, const u64 *d012, int level, dou
     ks_modup(c, d012 + 2 * plane, level, digits.u());
     k::ks_inner_auto(c, u.u(), digits.u(), dnum, evk->relin->data.u(), level, 1, nullptr, nullptr);
     std::unique_ptr<Ciphertext> o(new_ct(c, level, scale));
-    ks_moddown2(c, u.u(), level, o->c0(), o->c1());
-    k::add(c, o->data.u(), o->data.u(), d012, 2 * nq, c->qmap(level, 0, nq));   // (d0, d1) + ModDown(u)
+    ks_moddown2(c, u.u(), level, o->c0(), o->c1(), d012, d012 + plane);   // (d0, d1) + ModDown(u)
     return o.release();
 }
 

@@ -145,7 +145,6 @@ Ctx::~Ctx()
         cudaEventDestroy(r.stop);
     }
     for (auto e : event_pool) cudaEventDestroy(e);
-    modup_ptrs.clear();
     modup_tab.clear();
     moddown_tab.clear();
     rescale_tab.clear();
@@ -249,17 +248,6 @@ const BConvTable &Ctx::modup_table(int level, int digit)
         }
     }
     return modup_tab[key] = make_bconv(this, sp, sl, dp, dl);
-}
-
-const u64 *const *Ctx::modup_table_ptrs(int level)
-{
-    auto it = modup_ptrs.find(level);
-    if (it != modup_ptrs.end()) return it->second.as<const u64 *const>();
-    std::vector<const u64 *> p;
-    for (int j = 0; j < dnum(level); j++) p.push_back(modup_table(level, j).tab.u());
-    DevMem m;
-    upload(this, m, p.data(), p.size() * sizeof(u64 *));
-    return (modup_ptrs[level] = std::move(m)).as<const u64 *const>();
 }
 
 const BConvTable &Ctx::moddown_table(int level)

@@ -220,8 +220,6 @@ struct Ctx : Handle {
     void release(void *p, size_t bytes);
     u64 galois(int step) const;
     const BConvTable &modup_table(int level, int digit);
-    std::map<int, DevMem> modup_ptrs;                      // level -> device array of dnum table pointers
-    const u64 *const *modup_table_ptrs(int level);
     const BConvTable &moddown_table(int level);
     const u64 *rescale_table(int level);
     // synchronise; if a kernel flagged bad data since the last check, clear and raise
@@ -344,6 +342,13 @@ void sub_mul_scalar(Ctx *c, u64 *out, const u64 *a, const u64 *b, const u64 *d_s
 // centred integers (int64 N) -> residues for n_limbs limbs
 void from_signed(Ctx *c, u64 *out, const i64 *in, int n_limbs, LimbMap map);
 void bconv(Ctx *c, const BConvTable &t, const u64 *in_base, u64 *out_base);
+// several conversions in one launch
+struct BConvCall {
+    const BConvTable *t;
+    const u64 *in;
+    u64 *out;
+};
+void bconv_multi(Ctx *c, const std::vector<BConvCall> &calls);
 // ModUp base conversion of every digit at `level` in one launch (digits: [dnum][level+1+K][N])
 void bconv_modup(Ctx *c, int level, const u64 *coef, u64 *digits);
 // d_out[l][i] = sum_j dig_j[l][perm(i)] * key_j(l)[i] for the level-ell QP basis, both

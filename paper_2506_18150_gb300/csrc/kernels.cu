@@ -112,56 +112,53 @@ __global__ void k_from_signed(u64 *__restrict__ out, const i64 *__restrict__ in,
 }
 
 // ------------------------------------------------------------ base conversion
-__global__ void k_bconv(const u64 *__restrict__ in, u64 *__restrict__ out, const u64 *__restrict__ tab,
-                        int tab_words, int logN)
-{
-    extern __shared__ u64 st[];
-    for (int i = threadIdx.x; i < tab_words; i += blockDim.x) st[i] = tab[i];
-    __syncthreads();
-    const int ns = (int)st[0], nd = (int)st[1];
-    const int db = 2 + 4 * ns, hb = db + 3 * nd;
-    const size_t N = (size_t)1 << logN;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
-        u64 t[8];
-        for (int s = 0; s < ns; s++) {
-            const u64 *e = st + 2 + 4 * s;
-            t[s] = mont_mul(in[e[3] * N + i], e[2], e[0], e[1]);
-        }
-        for (int k2 = 0; k2 < nd; k2++) {
-            const u64 *e = st + db + 3 * k2;
-            Acc128 acc;
-            for (int s = 0; s < ns; s++) acc.mac(t[s], st[hb + s * nd + k2], e[0]);
-            out[e[2] * N + i] = acc.reduce(e[0], e[1]);
-        }
-    }
-}
+// Table layout (context.cu, make_bconv): [0] n_src, [1] n_dst; per source s
+// (q_s, q_s^-1 mod 2^64, [(Q/q_s)^-1]_{q_s} in Montgomery form, source limb);
+// per destination d (q_d, q_d^-1 mod 2^64, output limb); then the matrix
+// [Q/q_s]_{q_d} (Montgomery form), row s.
+//
+// One launch runs a list of jobs (a table, an input and an output base, a
+// range of destinations); blockIdx.y is the job and each thread one
+// coefficient, so every (coefficient, destination chunk) pair is its own
+// thread.  Table reads are warp-uniform (broadcast from L1).
+constexpr int BCONV_CHUNK = 4;
+constexpr int BCONV_MAX_JOBS = 96;
+struct BConvJob {
+    const u64 *in;
+    u64 *out;
+    const u64 *tab;
+    int d0, d1;
+};
+struct BConvJobs {
+    int n;
+    BConvJob j[BCONV_MAX_JOBS];
+};
 
-// All digits of a ModUp in one launch: blockIdx.y = digit j, table tabs[j],
-// output digit j at out + j * out_stride.
-__global__ void k_bconv_multi(const u64 *__restrict__ in, u64 *__restrict__ out, size_t out_stride,
-                              const u64 *const *__restrict__ tabs, int logN)
+__global__ void __launch_bounds__(256) k_bconv_jobs(BConvJobs jobs, int logN)
 {
-    extern __shared__ u64 st[];
-    const u64 *tab = tabs[blockIdx.y];
-    const int ns = (int)tab[0], nd = (int)tab[1];
-    const int words = 2 + 4 * ns + 3 * nd + ns * nd;
-    for (int i = threadIdx.x; i < words; i += blockDim.x) st[i] = tab[i];
-    __syncthreads();
-    const int db = 2 + 4 * ns, hb = db + 3 * nd;
+    const BConvJob jb = jobs.j[blockIdx.y];
+    const u64 *__restrict__ tab = jb.tab;
     const size_t N = (size_t)1 << logN;
-    u64 *o = out + blockIdx.y * out_stride;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
-        u64 t[8];
-        for (int s = 0; s < ns; s++) {
-            const u64 *e = st + 2 + 4 * s;
-            t[s] = mont_mul(in[e[3] * N + i], e[2], e[0], e[1]);
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int ns = (int)tab[0], nd = (int)tab[1];
+    const int db = 2 + 4 * ns, hb = db + 3 * nd;
+    u64 t[8];
+#pragma unroll
+    for (int s = 0; s < 8; s++) {
+        if (s >= ns) break;
+        const u64 *e = tab + 2 + 4 * s;
+        t[s] = mont_mul(jb.in[e[3] * N + i], e[2], e[0], e[1]);
+    }
+    for (int k2 = jb.d0; k2 < jb.d1; k2++) {
+        const u64 *e = tab + db + 3 * k2;
+        Acc128 acc;
+#pragma unroll
+        for (int s = 0; s < 8; s++) {
+            if (s >= ns) break;
+            acc.mac(t[s], tab[hb + s * nd + k2], e[0]);
         }
-        for (int k2 = 0; k2 < nd; k2++) {
-            const u64 *e = st + db + 3 * k2;
-            Acc128 acc;
-            for (int s = 0; s < ns; s++) acc.mac(t[s], st[hb + s * nd + k2], e[0]);
-            o[e[2] * N + i] = acc.reduce(e[0], e[1]);
-        }
+        jb.out[e[2] * N + i] = acc.reduce(e[0], e[1]);
     }
 }
 
@@ -748,29 +745,41 @@ void from_signed(Ctx *c, u64 *out, const i64 *in, int n_limbs, LimbMap map)
     k_from_signed<<<grid_for(total), TPB, 0, c->stream>>>(out, in, c->logN, total, c->d_pinfo.as<PrimeInfo>(), map);
     LAUNCHED(c);
 }
+void bconv_multi(Ctx *c, const std::vector<BConvCall> &calls)
+{
+    BConvJobs jobs;
+    jobs.n = 0;
+    double bytes = 0;
+    auto flush = [&] {
+        if (!jobs.n) return;
+        k_bconv_jobs<<<dim3((c->N + 255) / 256, jobs.n), 256, 0, c->stream>>>(jobs, c->logN);
+        LAUNCHED(c);
+        jobs.n = 0;
+    };
+    {
+        KTimer kt(c, "bconv", 0.0);
+        for (const BConvCall &x : calls) {
+            HCHECK(x.t->n_src <= 8, HELRM_E_PARAM, "base conversion supports at most 8 source primes");
+            bytes += 8.0 * c->N * (x.t->n_src + x.t->n_dst);   // sources read, destinations written, once
+            for (int d0 = 0; d0 < x.t->n_dst; d0 += BCONV_CHUNK) {
+                if (jobs.n == BCONV_MAX_JOBS) flush();
+                jobs.j[jobs.n++] = {x.in, x.out, x.t->tab.u(), d0, std::min(x.t->n_dst, d0 + BCONV_CHUNK)};
+            }
+        }
+        flush();
+        if (kt.idx != (size_t)-1) c->prof[kt.idx].bytes = bytes;
+    }
+}
 void bconv(Ctx *c, const BConvTable &t, const u64 *in_base, u64 *out_base)
 {
-    int words = 2 + 4 * t.n_src + 3 * t.n_dst + t.n_src * t.n_dst;
-    HCHECK(t.n_src <= 8, HELRM_E_PARAM, "base conversion supports at most 8 source primes");
-    KTimer kt(c, "bconv", 8.0 * c->N * (t.n_src + t.n_dst));
-    k_bconv<<<grid_for(c->N), TPB, words * 8, c->stream>>>(in_base, out_base, t.tab.u(), words, c->logN);
-    LAUNCHED(c);
+    bconv_multi(c, {{&t, in_base, out_base}});
 }
 void bconv_modup(Ctx *c, int level, const u64 *coef, u64 *digits)
 {
     const int dnum = c->dnum(level), nl = level + 1 + c->K;
-    int max_words = 0, n_src = 0, n_dst = 0;
-    for (int j = 0; j < dnum; j++) {
-        const BConvTable &t = c->modup_table(level, j);
-        max_words = std::max(max_words, 2 + 4 * t.n_src + 3 * t.n_dst + t.n_src * t.n_dst);
-        n_src += t.n_src;
-        n_dst += t.n_dst;
-    }
-    KTimer kt(c, "bconv", 8.0 * c->N * (n_src + n_dst));
-    const u64 *const *tabs = c->modup_table_ptrs(level);
-    dim3 grid(std::max(1u, grid_for(c->N) / (unsigned)dnum), dnum);
-    k_bconv_multi<<<grid, TPB, max_words * 8, c->stream>>>(coef, digits, (size_t)nl * c->N, tabs, c->logN);
-    LAUNCHED(c);
+    std::vector<BConvCall> v;
+    for (int j = 0; j < dnum; j++) v.push_back({&c->modup_table(level, j), coef, digits + (size_t)j * nl * c->N});
+    bconv_multi(c, v);
 }
 
 void ks_inner_auto(Ctx *c, u64 *out, const u64 *digits, int dnum, const u64 *key, int level, u64 galois,
@@ -781,9 +790,8 @@ void ks_inner_auto(Ctx *c, u64 *out, const u64 *digits, int dnum, const u64 *key
     // written (and read, when accumulating)
     KTimer kt(c, "ks_inner_auto", 8.0 * (total * (3.0 * dnum + (accumulate ? 4 : 2) + (bq ? 1 : 0)) +
                                          (c0 ? (double)(level + 1) * c->N : 0.0)));
-    k_ks_inner<<<grid_for(total), TPB, 0, c->stream>>>(out, digits, dnum, key, level, c->L, c->K, c->logN, galois,
-                                                       c0, d_pmod_mont, bq, accumulate ? 1 : 0,
-                                                       c->d_pinfo.as<PrimeInfo>());
+    k_ks_inner<<<grid_for(total), TPB, 0, c->stream>>>(out, digits, dnum, key, level, c->L, c->K, c->logN, galois, c0,
+                                                 d_pmod_mont, bq, accumulate ? 1 : 0, c->d_pinfo.as<PrimeInfo>());
     LAUNCHED(c);
 }
 void automorphism(Ctx *c, u64 *out, const u64 *in, int n_limbs, u64 galois)

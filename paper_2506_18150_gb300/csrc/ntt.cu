@@ -28,7 +28,7 @@ namespace helrm {
 namespace {
 
 constexpr int MAX_LIMBS = 128;
-constexpr int TILE = 4096;   // words per CTA (32 KB of data)
+constexpr int TILE = 1024;   // words per CTA (8 KB of data)
 
 struct LimbList {
     int n;
@@ -150,35 +150,30 @@ __global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN, int logG,
 #pragma unroll
                 for (int k = 0; k < gs; k++) v[qg * gs + k] = sm[saddr(elem(qg, k))];
         }
+        // The group's members all lie in block blk of stage s0, so at stage
+        // s0 + u the butterfly of member k1 uses local block
+        // (blk << u) + (k1 >> (r - u)): 2^u distinct twiddles, loaded once.
 #pragma unroll
         for (int qg = 0; qg < ng; qg++) {
             u64 *x = v + qg * gs;
-            const int e0 = elem(qg, 0);
-            if (!INV) {
+            const int blk = (tt + qg * TPS) / T;
 #pragma unroll
-                for (int u = 0; u < r; u++) {
-                    const int s = s0 + u;
-                    const int half = gs >> (u + 1);
+            for (int uu = 0; uu < r; uu++) {
+                const int u = INV ? r - 1 - uu : uu;
+                const int s = s0 + u;
+                const int half = gs >> (u + 1);
+                const ulonglong2 *twb = tw + (((bm + seg) << s) + (blk << u));
+                ulonglong2 wv[4];
 #pragma unroll
-                    for (int k1 = 0; k1 < gs; k1++) {
-                        if (k1 & half) continue;
-                        const int lb = (e0 + k1 * T) >> (LOGP - s);
-                        const ulonglong2 w = tw[((bm + seg) << s) + lb];
+                for (int j = 0; j < (1 << u); j++) wv[j] = twb[j];
+#pragma unroll
+                for (int k1 = 0; k1 < gs; k1++) {
+                    if (k1 & half) continue;
+                    const ulonglong2 w = wv[k1 >> (r - u)];
+                    if (!INV)
                         bfly_ct(x[k1], x[k1 + half], w.x, w.y, q, q2);
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int u = r - 1; u >= 0; u--) {
-                    const int s = s0 + u;
-                    const int half = gs >> (u + 1);
-#pragma unroll
-                    for (int k1 = 0; k1 < gs; k1++) {
-                        if (k1 & half) continue;
-                        const int lb = (e0 + k1 * T) >> (LOGP - s);
-                        const ulonglong2 w = tw[((bm + seg) << s) + lb];
+                    else
                         bfly_gs(x[k1], x[k1 + half], w.x, w.y, q, q2);
-                    }
                 }
             }
         }

@@ -64,8 +64,8 @@ void ks_moddown2(Ctx *c, const u64 *u, int level, u64 *out0, u64 *out1, const u6
         for (int i = 0; i < K; i++)
             v.push_back({u + (size_t)(h * nl + nq + i) * N, pc.u() + (size_t)(h * K + i) * N, m.pid(nq + i), nullptr, nullptr});
     k::ntt_run(c, v, true, nullptr);
-    k::bconv(c, c->moddown_table(level), pc.u(), y.u());
-    k::bconv(c, c->moddown_table(level), pc.u() + (size_t)K * N, y.u() + (size_t)nq * N);
+    const BConvTable &md = c->moddown_table(level);
+    k::bconv_multi(c, {{&md, pc.u(), y.u()}, {&md, pc.u() + (size_t)K * N, y.u() + (size_t)nq * N}});
     v.clear();
     for (int h = 0; h < 2; h++)
         for (int l = 0; l < nq; l++) {

@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(T + 32) k_bsgs_tma(u64 *__restrict__ inner, co
                                                     int logN, const u64 *__restrict__ pmod,
                                                     const PrimeInfo *__restrict__ pinfo, int *err)
 {
+    pdl_begin();
     extern __shared__ __align__(128) u64 smem[];
     constexpr int SW = Stage<N2, DN>::WORDS;
     u64 *full = smem + S * SW;        // S mbarriers
@@ -261,13 +262,13 @@ __global__ void __launch_bounds__(T + 32) k_bsgs_tma(u64 *__restrict__ inner, co
 }
 
 template <int N2, int DN>
-void launch(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c1, const TmaBabies &bk,
+void launch_tma(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c1, const TmaBabies &bk,
             const u64 *const *diag, const int *gb, int n1, int level)
 {
     const size_t smem = (size_t)S * Stage<N2, DN>::WORDS * 8 + 2 * S * 8;
     CUDA_CHECK(cudaFuncSetAttribute(k_bsgs_tma<N2, DN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(c->N / T, level + 1 + c->K);
-    k_bsgs_tma<N2, DN><<<grid, T + 32, smem, c->stream>>>(inner, digits, c0, c1, bk, diag, gb, n1, level, c->L, c->K,
+    launch(c, k_bsgs_tma<N2, DN>, grid, T + 32, smem, inner, digits, c0, c1, bk, diag, gb, n1, level, c->L, c->K,
                                                      c->logN, c->d_pmod_mont.u(), c->d_pinfo.as<PrimeInfo>(),
                                                      c->d_err.as<int>());
 }
@@ -293,7 +294,7 @@ void bsgs_tma(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c
     const size_t plane = (size_t)(level + 1 + c->K) * c->N;
     KTimer kt(c, "bsgs_fused", 8.0 * plane * (2.0 * dnum * n_keys + n_diag + 2.0 * n2) +
                                    16.0 * (level + 1) * c->N);
-#define HELRM_TMA(NN, DD) launch<NN, DD>(c, inner, digits, c0, c1, bk, d_diag_ptrs, d_gb_index, n1, level)
+#define HELRM_TMA(NN, DD) launch_tma<NN, DD>(c, inner, digits, c0, c1, bk, d_diag_ptrs, d_gb_index, n1, level)
 #define HELRM_TMA_D(NN)              \
     switch (dnum) {                  \
     case 1: HELRM_TMA(NN, 1); break; \

@@ -228,6 +228,37 @@ struct Ctx : Handle {
 
 // Scope timer: when profiling is on, brackets the enclosed launches with a
 // pair of events and the kernel's algorithmic bytes (reads + writes once).
+// Programmatic dependent launch.  Every kernel of the library starts with
+// pdl_begin(): griddepcontrol.wait blocks until the grids it depends on have
+// completed and their writes are visible, then launch_dependents lets the next
+// grid in the stream be scheduled while this one runs, so consecutive kernels
+// no longer pay a full launch latency each.  Both instructions are no-ops in
+// a grid launched without the attribute.  No kernel touches global memory
+// before pdl_begin(), which is what makes the early launch safe.
+__device__ __forceinline__ void pdl_begin()
+{
+#ifdef __CUDA_ARCH__
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+// Launch on the context's stream with programmatic stream serialisation.
+template <typename... KArgs, typename... Args>
+void launch(Ctx *c, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
+}
+
 struct KTimer {
     Ctx *c;
     size_t idx = (size_t)-1;
@@ -362,15 +393,12 @@ void ks_inner_auto(Ctx *c, u64 *out, const u64 *digits, int dnum, const u64 *key
 void bsgs_mac(Ctx *c, u64 *inner, const u64 *baby, int n_baby, const u64 *const *d_diag_ptrs,
               const int *d_gb_index, int n2, int n1, int limbs, LimbMap map);
 void automorphism(Ctx *c, u64 *out, const u64 *in, int n_limbs, u64 galois);
-// the same, fed by a 3-stage pipeline of bulk asynchronous copies (bsgs_tma.cu)
+// hoisted baby steps fused into the BSGS MAC (n1 <= 64, n2 in {1,2,4,8}), fed by a
+// 3-stage pipeline of bulk asynchronous copies (bsgs_tma.cu); keys[b] / gals[b] for
+// b < n1 (keys[0] unused); writes inner[g][2][level+1+K][N] for giant steps with diagonals
 void bsgs_tma(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c1, const u64 *const *keys,
               const u64 *gals, const u64 *const *d_diag_ptrs, const int *d_gb_index, int n_diag, int n1, int n2,
               int level);
-// fused hoisted baby steps + BSGS MAC (n1 <= 64, n2 in {1,2,4,8}); keys[b] / gals[b]
-// for b < n1 (keys[0] unused), writes inner[g][2][level+1+K][N] for giant steps with diagonals
-void bsgs_fused(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c1, const u64 *const *keys,
-                const u64 *gals, const u64 *const *d_diag_ptrs, const int *d_gb_index, int n_diag, int n1, int n2,
-                int level);
 // rescale helper: coefficient-form last limb -> centred residues for ell limbs
 void rescale_spread(Ctx *c, u64 *out, const u64 *last_coef, int level, int n_polys = 1);
 // random

@@ -38,6 +38,7 @@ enum Op { OP_ADD, OP_SUB, OP_NEG, OP_MULM, OP_MULP, OP_TOMONT, OP_FROMMONT };
 __global__ void k_binop(u64 *__restrict__ out, const u64 *__restrict__ a, const u64 *__restrict__ b,
                         int logN, size_t total, const PrimeInfo *__restrict__ pinfo, LimbMap map, int op)
 {
+    pdl_begin();
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
         const PrimeInfo pi = pinfo[map.pid((int)(idx >> logN))];
@@ -59,6 +60,7 @@ __global__ void k_tensor(u64 *__restrict__ d, const u64 *__restrict__ a0, const 
                          const u64 *__restrict__ b0, const u64 *__restrict__ b1, int logN, size_t total,
                          const PrimeInfo *__restrict__ pinfo, LimbMap map, int accumulate)
 {
+    pdl_begin();
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
         const PrimeInfo pi = pinfo[map.pid((int)(idx >> logN))];
@@ -88,6 +90,7 @@ __global__ void k_scalar(u64 *__restrict__ out, const u64 *__restrict__ a, const
                          const u64 *__restrict__ scal, int logN, size_t total,
                          const PrimeInfo *__restrict__ pinfo, LimbMap map)
 {
+    pdl_begin();
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
         const int pid = map.pid((int)(idx >> logN));
@@ -101,6 +104,7 @@ __global__ void k_scalar(u64 *__restrict__ out, const u64 *__restrict__ a, const
 __global__ void k_from_signed(u64 *__restrict__ out, const i64 *__restrict__ in, int logN, size_t total,
                               const PrimeInfo *__restrict__ pinfo, LimbMap map)
 {
+    pdl_begin();
     const size_t N = (size_t)1 << logN;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
@@ -136,6 +140,7 @@ struct BConvJobs {
 
 __global__ void __launch_bounds__(256) k_bconv_jobs(BConvJobs jobs, int logN)
 {
+    pdl_begin();
     const BConvJob jb = jobs.j[blockIdx.y];
     const u64 *__restrict__ tab = jb.tab;
     const size_t N = (size_t)1 << logN;
@@ -177,6 +182,7 @@ __global__ void k_ks_inner(u64 *__restrict__ out, const u64 *__restrict__ dig, i
                            const u64 *__restrict__ c0, const u64 *__restrict__ pmod,
                            const u64 *__restrict__ bq, int accumulate, const PrimeInfo *__restrict__ pinfo)
 {
+    pdl_begin();
     const size_t N = (size_t)1 << logN;
     const int nl = level + 1 + K, nP = L + 1 + K;
     const size_t total = (size_t)nl * N;
@@ -209,6 +215,7 @@ __global__ void k_ks_inner(u64 *__restrict__ out, const u64 *__restrict__ dig, i
 __global__ void k_automorphism(u64 *__restrict__ out, const u64 *__restrict__ in, int logN, size_t total,
                                u64 galois)
 {
+    pdl_begin();
     const size_t N = (size_t)1 << logN;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
@@ -227,6 +234,7 @@ __global__ void __launch_bounds__(MAC_TC) k_bsgs_mac(u64 *__restrict__ inner, co
                                                      const int *__restrict__ gb, int n1, int n2, int nl,
                                                      int logN, const PrimeInfo *__restrict__ pinfo, LimbMap map)
 {
+    pdl_begin();
     extern __shared__ u64 sb[];   // [n1][2][MAC_TC]
     const size_t N = (size_t)1 << logN;
     const int l = blockIdx.y;
@@ -257,170 +265,12 @@ __global__ void __launch_bounds__(MAC_TC) k_bsgs_mac(u64 *__restrict__ inner, co
     }
 }
 
-// Few giant steps (n2 <= 8): one thread per (limb, coefficient) keeps all n2
-// pairs of 128-bit accumulators in registers and streams every baby step and
-// every diagonal once.
-template <int N2>
-__global__ void __launch_bounds__(256) k_bsgs_mac_reg(u64 *__restrict__ inner, const u64 *__restrict__ baby,
-                                                      const u64 *const *__restrict__ diag,
-                                                      const int *__restrict__ gb, int n1, int nl, int logN,
-                                                      const PrimeInfo *__restrict__ pinfo, LimbMap map)
-{
-    __shared__ int sgb[64 * 8];
-    for (int t = threadIdx.x; t < n1 * N2; t += blockDim.x) sgb[t] = gb[t];
-    __syncthreads();
-    const size_t N = (size_t)1 << logN;
-    const size_t plane = (size_t)nl * N;
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        const PrimeInfo pi = pinfo[map.pid((int)(idx >> logN))];
-        Acc128 a0[N2], a1[N2];
-        for (int b = 0; b < n1; b++) {
-            bool need = false;
-#pragma unroll
-            for (int g = 0; g < N2; g++) need |= sgb[g * n1 + b] >= 0;
-            if (!need) continue;
-            const u64 *bb = baby + (size_t)b * 2 * plane + idx;
-            const u64 b0 = bb[0], b1 = bb[plane];
-#pragma unroll
-            for (int g = 0; g < N2; g++) {
-                const int di = sgb[g * n1 + b];
-                if (di < 0) continue;
-                const u64 d = diag[di][idx];
-                a0[g].mac(b0, d, pi.q);
-                a1[g].mac(b1, d, pi.q);
-            }
-        }
-#pragma unroll
-        for (int g = 0; g < N2; g++) {
-            bool any = false;
-            for (int b = 0; b < n1; b++) any |= sgb[g * n1 + b] >= 0;
-            if (!any) continue;
-            u64 *o = inner + (size_t)g * 2 * plane + idx;
-            o[0] = a0[g].reduce(pi.q, pi.qinv);
-            o[plane] = a1[g].reduce(pi.q, pi.qinv);
-        }
-    }
-}
-
-// Baby steps fused into the MAC: for every (limb, coefficient) and every baby
-// step b, the hoisted rotation phi_{5^b} of the ModUp digits times key b (plus
-// P phi(c0) on the Q limbs) is formed in registers and multiplied at once into
-// the n2 giant-step accumulators.  Keys and diagonals stream from HBM once;
-// the digits (dnum x (l+1+K) x N words) stay in L2; no baby buffer exists.
-struct BabyKeys {
-    const u64 *key[64];   // key of baby step b (nullptr for b = 0 or unused)
-    u64 gal[64];          // its Galois element
-};
-
-// DN = number of key-switching digits at this level (a template parameter so
-// that a baby step's loads -- DN digit words, 2 DN key words, the gathered c0
-// word and its N2 diagonal words -- all land in registers and are issued
-// together before any arithmetic, one memory round trip per baby step).
-template <int N2, int DN>
-__global__ void __launch_bounds__(256, 3) k_bsgs_fused(u64 *__restrict__ inner, const u64 *__restrict__ dig,
-                                                    const u64 *__restrict__ c0, const u64 *__restrict__ c1,
-                                                    BabyKeys bk, const u64 *const *__restrict__ diag,
-                                                    const int *__restrict__ gb, int n1, int level, int L, int K,
-                                                    int logN, const u64 *__restrict__ pmod,
-                                                    const PrimeInfo *__restrict__ pinfo)
-{
-    __shared__ int sgb[64 * 8];
-    __shared__ int sneed[64], sany[8];
-    for (int t = threadIdx.x; t < n1 * N2; t += blockDim.x) sgb[t] = gb[t];
-    __syncthreads();
-    if (threadIdx.x < n1) {
-        int need = 0;
-        for (int g = 0; g < N2; g++) need |= sgb[g * n1 + threadIdx.x] >= 0;
-        sneed[threadIdx.x] = need;
-    }
-    if (threadIdx.x < N2) {
-        int any = 0;
-        for (int b = 0; b < n1; b++) any |= sgb[threadIdx.x * n1 + b] >= 0;
-        sany[threadIdx.x] = any;
-    }
-    __syncthreads();
-    const size_t N = (size_t)1 << logN;
-    const int nl = level + 1 + K, nP = L + 1 + K;
-    const size_t plane = (size_t)nl * N;
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        const int l = (int)(idx >> logN);
-        const int i = (int)(idx & (N - 1));
-        const bool qlimb = l <= level;
-        const int pid = qlimb ? l : L + 1 + (l - level - 1);
-        const PrimeInfo pi = pinfo[pid];
-        const u64 pm = pmod[pid];
-        // 64-bit accumulators: each product reduced on the spot (REDC is linear,
-        // so this equals one reduction of the 128-bit sum) -- fewer registers,
-        // more warps in flight for the memory stream
-        u64 a0[N2], a1[N2];
-#pragma unroll
-        for (int g = 0; g < N2; g++) a0[g] = a1[g] = 0;
-        // a missing diagonal contributes mont_mul(v, 0) = 0, so absent (g, b)
-        // pairs need no branch: their diagonal word is loaded as 0
-        if (sneed[0]) {   // baby 0 = (P c0, P c1): P mod q on the Q limbs, 0 on the P limbs
-            u64 dd[N2];
-#pragma unroll
-            for (int g = 0; g < N2; g++) {
-                const int di = sgb[g * n1];
-                dd[g] = di >= 0 ? diag[di][idx] : 0;
-            }
-            const u64 v0 = qlimb ? mont_mul(c0[(size_t)l * N + i], pm, pi.q, pi.qinv) : 0;
-            const u64 v1 = qlimb ? mont_mul(c1[(size_t)l * N + i], pm, pi.q, pi.qinv) : 0;
-#pragma unroll
-            for (int g = 0; g < N2; g++) {
-                a0[g] = add_mod(a0[g], mont_mul(v0, dd[g], pi.q, pi.qinv), pi.q);
-                a1[g] = add_mod(a1[g], mont_mul(v1, dd[g], pi.q, pi.qinv), pi.q);
-            }
-        }
-        for (int b = 1; b < n1; b++) {
-            if (!sneed[b]) continue;
-            const int src = auto_src(i, logN, bk.gal[b]);
-            const u64 *key = bk.key[b];
-            u64 dg[DN], kb[DN], ka[DN], dd[N2];
-#pragma unroll
-            for (int j = 0; j < DN; j++) {
-                dg[j] = dig[((size_t)j * nl + l) * N + src];
-                kb[j] = key[((size_t)(2 * j) * nP + pid) * N + i];
-                ka[j] = key[((size_t)(2 * j + 1) * nP + pid) * N + i];
-            }
-            const u64 cs = qlimb ? c0[(size_t)l * N + src] : 0;
-#pragma unroll
-            for (int g = 0; g < N2; g++) {
-                const int di = sgb[g * n1 + b];
-                dd[g] = di >= 0 ? diag[di][idx] : 0;
-            }
-            Acc128 t0, t1;
-#pragma unroll
-            for (int j = 0; j < DN; j++) {
-                t0.mac(dg[j], kb[j], pi.q);
-                t1.mac(dg[j], ka[j], pi.q);
-            }
-            u64 v0 = t0.reduce(pi.q, pi.qinv);
-            const u64 v1 = t1.reduce(pi.q, pi.qinv);
-            if (qlimb) v0 = add_mod(v0, mont_mul(cs, pm, pi.q, pi.qinv), pi.q);
-#pragma unroll
-            for (int g = 0; g < N2; g++) {
-                a0[g] = add_mod(a0[g], mont_mul(v0, dd[g], pi.q, pi.qinv), pi.q);
-                a1[g] = add_mod(a1[g], mont_mul(v1, dd[g], pi.q, pi.qinv), pi.q);
-            }
-        }
-#pragma unroll
-        for (int g = 0; g < N2; g++) {
-            if (!sany[g]) continue;
-            u64 *o = inner + (size_t)g * 2 * plane + idx;
-            o[0] = a0[g];
-            o[plane] = a1[g];
-        }
-    }
-}
-
 // ------------------------------------------------------------------ rescale
 // tab: [nP] q_l^-1 (Montgomery, by prime id), [nP] q_l mod q_i, [2 nP] q_l.
 __global__ void k_rescale_spread(u64 *__restrict__ out, const u64 *__restrict__ last, const u64 *__restrict__ tab,
                                  int nP, int logN, size_t total, const PrimeInfo *__restrict__ pinfo)
 {
+    pdl_begin();
     const size_t N = (size_t)1 << logN;
     const u64 ql = tab[2 * nP];
     const u64 half = (ql - 1) >> 1;
@@ -440,6 +290,7 @@ __global__ void k_rescale_spread(u64 *__restrict__ out, const u64 *__restrict__ 
 __global__ void k_check_range(const u64 *__restrict__ d, int logN, size_t total, const PrimeInfo *__restrict__ pinfo,
                               LimbMap map, int *flag)
 {
+    pdl_begin();
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x)
         if (d[idx] >= pinfo[map.pid((int)(idx >> logN))].q) *flag = 1;
@@ -479,6 +330,7 @@ __device__ void chacha_block(u64 seed, u32 purpose, u64 index, u32 counter, u32 
 
 __global__ void k_chacha_words(u32 *out, u64 seed, u32 purpose, u64 index, u64 first_word, u64 n_words)
 {
+    pdl_begin();
     const u64 b0 = first_word / 16, b1 = (first_word + n_words + 15) / 16;
     for (u64 b = b0 + blockIdx.x * (u64)blockDim.x + threadIdx.x; b < b1; b += (u64)gridDim.x * blockDim.x) {
         u32 w[16];
@@ -495,6 +347,7 @@ __global__ void k_uniform(u64 *out, u64 seed, u32 purpose, u64 index, int logN, 
                           const int *__restrict__ limb_pid, const int *__restrict__ limb_gid,
                           const PrimeInfo *__restrict__ pinfo)
 {
+    pdl_begin();
     const u64 N = 1ull << logN;
     const u64 per = N / 4;
     const u64 total = per * n_limbs;
@@ -516,6 +369,7 @@ __global__ void k_uniform(u64 *out, u64 seed, u32 purpose, u64 index, int logN, 
 
 __global__ void k_ternary(i64 *out, u64 seed, u32 purpose, u64 index, int N)
 {
+    pdl_begin();
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < N / 16; b += gridDim.x * blockDim.x) {
         u32 w[16];
         chacha_block(seed, purpose, index, (u32)b, w);
@@ -525,6 +379,7 @@ __global__ void k_ternary(i64 *out, u64 seed, u32 purpose, u64 index, int N)
 
 __global__ void k_cbd21(i64 *out, u64 seed, u32 purpose, u64 index, int N)
 {
+    pdl_begin();
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < N / 8; b += gridDim.x * blockDim.x) {
         u32 w[16];
         chacha_block(seed, purpose, index, (u32)b, w);
@@ -541,6 +396,7 @@ __global__ void k_cbd21(i64 *out, u64 seed, u32 purpose, u64 index, int N)
 __global__ void k_fft_pass(const double2 *__restrict__ x, double2 *__restrict__ y, int logN, int s,
                            const double2 *__restrict__ tw, int inverse)
 {
+    pdl_begin();
     const int N = 1 << logN, m = 1 << s, l = N >> (s + 1);
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N / 2; idx += gridDim.x * blockDim.x) {
         const int j = idx >> s, kk = idx & (m - 1);
@@ -557,6 +413,7 @@ __global__ void k_fft_pass(const double2 *__restrict__ x, double2 *__restrict__ 
 __global__ void k_enc_gather(double2 *x, const double *__restrict__ slots, const int *__restrict__ slot_of,
                              int n_valid, int period, int N)
 {
+    pdl_begin();
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < N; u += gridDim.x * blockDim.x) {
         const int j = slot_of[u] % period;
         x[u] = make_double2(j < n_valid ? slots[j] : 0.0, 0.0);
@@ -567,6 +424,7 @@ __global__ void k_enc_gather(double2 *x, const double *__restrict__ slots, const
 __global__ void k_enc_round(u64 *out, i64 *coeffs, const double2 *__restrict__ X, double scale, int logN,
                             int n_limbs, const PrimeInfo *__restrict__ pinfo, LimbMap map, int *overflow)
 {
+    pdl_begin();
     const int N = 1 << logN;
     for (int k2 = blockIdx.x * blockDim.x + threadIdx.x; k2 < N; k2 += gridDim.x * blockDim.x) {
         double sn, cs;
@@ -592,6 +450,7 @@ __global__ void k_enc_round(u64 *out, i64 *coeffs, const double2 *__restrict__ X
 // centred limb-0 coefficients -> y_k = m_k e^(i pi k / N)
 __global__ void k_dec_twist(double2 *y, const u64 *__restrict__ m0, u64 q0, int logN)
 {
+    pdl_begin();
     const int N = 1 << logN;
     for (int k2 = blockIdx.x * blockDim.x + threadIdx.x; k2 < N; k2 += gridDim.x * blockDim.x) {
         const u64 x = m0[k2];
@@ -605,6 +464,7 @@ __global__ void k_dec_twist(double2 *y, const u64 *__restrict__ m0, u64 q0, int 
 __global__ void k_dec_pick(double *out, const double2 *__restrict__ Y, const int *__restrict__ u_of_slot,
                            double scale, int n)
 {
+    pdl_begin();
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
         out[j] = Y[u_of_slot[j]].x / scale;
 }
@@ -616,6 +476,7 @@ constexpr int DEC_BLOCKS = 64;
 __global__ void k_dec_direct(double *part, const u64 *__restrict__ m0, u64 q0, const int *__restrict__ u_of_slot,
                              int logN)
 {
+    pdl_begin();
     __shared__ double red[256];
     const int N = 1 << logN;
     const int j = blockIdx.y;
@@ -638,6 +499,7 @@ __global__ void k_dec_direct(double *part, const u64 *__restrict__ m0, u64 q0, c
 
 __global__ void k_dec_sum(double *out, const double *__restrict__ part, double scale, int n)
 {
+    pdl_begin();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     double s = 0;
@@ -648,6 +510,7 @@ __global__ void k_dec_sum(double *out, const double *__restrict__ part, double s
 __global__ void k_pack_selector(double *sel, const u64 *__restrict__ idx, const int *__restrict__ tab, int T,
                                 int base)
 {
+    pdl_begin();
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
         u64 i = idx[t];
         const int rows = tab[3 * t], off = tab[3 * t + 1], nd = tab[3 * t + 2];
@@ -669,19 +532,20 @@ namespace k {
 
 __global__ void k_sigmoid(double *p, const double *__restrict__ x, int n)
 {
+    pdl_begin();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = 1.0 / (1.0 + exp(-x[i]));
 }
 
 void sigmoid(Ctx *c, double *d_p, const double *d_x, int n)
 {
-    k_sigmoid<<<(n + 127) / 128, 128, 0, c->stream>>>(d_p, d_x, n);
+    launch(c, k_sigmoid, (n + 127) / 128, 128, 0, d_p, d_x, n);
     LAUNCHED(c);
 }
 
 void pack_selector(Ctx *c, double *sel, const u64 *d_idx, const int *d_tab, int T, int base, int in_pad)
 {
     CUDA_CHECK(cudaMemsetAsync(sel, 0, (size_t)in_pad * 8, c->stream));
-    k_pack_selector<<<(T + 127) / 128, 128, 0, c->stream>>>(sel, d_idx, d_tab, T, base);
+    launch(c, k_pack_selector, (T + 127) / 128, 128, 0, sel, d_idx, d_tab, T, base);
     LAUNCHED(c);
 }
 
@@ -700,7 +564,7 @@ static void binop(Ctx *c, u64 *out, const u64 *a, const u64 *b, int n_limbs, Lim
     size_t total = (size_t)n_limbs * c->N;
     if (!total) return;
     KTimer kt(c, "elementwise", (b ? 24.0 : 16.0) * total);
-    k_binop<<<grid_for(total), TPB, 0, c->stream>>>(out, a, b, c->logN, total, c->d_pinfo.as<PrimeInfo>(), map, op);
+    launch(c, k_binop, grid_for(total), TPB, 0, out, a, b, c->logN, total, c->d_pinfo.as<PrimeInfo>(), map, op);
     LAUNCHED(c);
 }
 void add(Ctx *c, u64 *o, const u64 *a, const u64 *b, int n, LimbMap m) { binop(c, o, a, b, n, m, OP_ADD); }
@@ -715,7 +579,7 @@ void tensor(Ctx *c, u64 *d, const u64 *a0, const u64 *a1, const u64 *b0, const u
 {
     size_t total = (size_t)n_limbs * c->N;
     KTimer kt(c, "tensor", (accumulate ? 10.0 : 7.0) * 8 * total);
-    k_tensor<<<grid_for(total), TPB, 0, c->stream>>>(d, a0, a1, b0, b1, c->logN, total, c->d_pinfo.as<PrimeInfo>(),
+    launch(c, k_tensor, grid_for(total), TPB, 0, d, a0, a1, b0, b1, c->logN, total, c->d_pinfo.as<PrimeInfo>(),
                                                      map, accumulate ? 1 : 0);
     LAUNCHED(c);
 }
@@ -725,7 +589,7 @@ void mul_scalar_mont(Ctx *c, u64 *out, const u64 *a, const u64 *scal, int n_limb
     size_t total = (size_t)n_limbs * c->N;
     if (!total) return;
     KTimer kt(c, "elementwise", 16.0 * total);
-    k_scalar<<<grid_for(total), TPB, 0, c->stream>>>(out, a, nullptr, scal, c->logN, total,
+    launch(c, k_scalar, grid_for(total), TPB, 0, out, a, nullptr, scal, c->logN, total,
                                                      c->d_pinfo.as<PrimeInfo>(), map);
     LAUNCHED(c);
 }
@@ -734,7 +598,7 @@ void sub_mul_scalar(Ctx *c, u64 *out, const u64 *a, const u64 *b, const u64 *sca
     size_t total = (size_t)n_limbs * c->N;
     if (!total) return;
     KTimer kt(c, "elementwise", 24.0 * total);
-    k_scalar<<<grid_for(total), TPB, 0, c->stream>>>(out, a, b, scal, c->logN, total,
+    launch(c, k_scalar, grid_for(total), TPB, 0, out, a, b, scal, c->logN, total,
                                                      c->d_pinfo.as<PrimeInfo>(), map);
     LAUNCHED(c);
 }
@@ -742,7 +606,7 @@ void from_signed(Ctx *c, u64 *out, const i64 *in, int n_limbs, LimbMap map)
 {
     size_t total = (size_t)n_limbs * c->N;
     if (!total) return;
-    k_from_signed<<<grid_for(total), TPB, 0, c->stream>>>(out, in, c->logN, total, c->d_pinfo.as<PrimeInfo>(), map);
+    launch(c, k_from_signed, grid_for(total), TPB, 0, out, in, c->logN, total, c->d_pinfo.as<PrimeInfo>(), map);
     LAUNCHED(c);
 }
 void bconv_multi(Ctx *c, const std::vector<BConvCall> &calls)
@@ -752,7 +616,7 @@ void bconv_multi(Ctx *c, const std::vector<BConvCall> &calls)
     double bytes = 0;
     auto flush = [&] {
         if (!jobs.n) return;
-        k_bconv_jobs<<<dim3((c->N + 255) / 256, jobs.n), 256, 0, c->stream>>>(jobs, c->logN);
+        launch(c, k_bconv_jobs, dim3((c->N + 255) / 256, jobs.n), 256, 0, jobs, c->logN);
         LAUNCHED(c);
         jobs.n = 0;
     };
@@ -790,7 +654,7 @@ void ks_inner_auto(Ctx *c, u64 *out, const u64 *digits, int dnum, const u64 *key
     // written (and read, when accumulating)
     KTimer kt(c, "ks_inner_auto", 8.0 * (total * (3.0 * dnum + (accumulate ? 4 : 2) + (bq ? 1 : 0)) +
                                          (c0 ? (double)(level + 1) * c->N : 0.0)));
-    k_ks_inner<<<grid_for(total), TPB, 0, c->stream>>>(out, digits, dnum, key, level, c->L, c->K, c->logN, galois, c0,
+    launch(c, k_ks_inner, grid_for(total), TPB, 0, out, digits, dnum, key, level, c->L, c->K, c->logN, galois, c0,
                                                  d_pmod_mont, bq, accumulate ? 1 : 0, c->d_pinfo.as<PrimeInfo>());
     LAUNCHED(c);
 }
@@ -799,7 +663,7 @@ void automorphism(Ctx *c, u64 *out, const u64 *in, int n_limbs, u64 galois)
     size_t total = (size_t)n_limbs * c->N;
     if (!total) return;
     KTimer kt(c, "automorphism", 16.0 * total);
-    k_automorphism<<<grid_for(total), TPB, 0, c->stream>>>(out, in, c->logN, total, galois);
+    launch(c, k_automorphism, grid_for(total), TPB, 0, out, in, c->logN, total, galois);
     LAUNCHED(c);
 }
 void bsgs_mac(Ctx *c, u64 *inner, const u64 *baby, int n_baby, const u64 *const *d_diag_ptrs,
@@ -809,110 +673,52 @@ void bsgs_mac(Ctx *c, u64 *inner, const u64 *baby, int n_baby, const u64 *const 
     // n_baby: number of distinct diagonals (non-zero); babies read once, diagonals once,
     // n2 inner ciphertexts written once
     KTimer kt(c, "bsgs_mac", 8.0 * limbs * c->N * (2.0 * n1 + (double)n_baby + 2.0 * n2));
-    if (n2 <= 8 && n1 <= 64 && (n2 & (n2 - 1)) == 0) {   // n2 = D / n1 is a power of two
-        const size_t total = (size_t)limbs * c->N;
-        const unsigned grid = grid_for(total);
-        const PrimeInfo *pi = c->d_pinfo.as<PrimeInfo>();
-        switch (n2 <= 1 ? 1 : n2 <= 2 ? 2 : n2 <= 4 ? 4 : 8) {
-        case 1: k_bsgs_mac_reg<1><<<grid, 256, 0, c->stream>>>(inner, baby, d_diag_ptrs, d_gb_index, n1, limbs, c->logN, pi, map); break;
-        case 2: k_bsgs_mac_reg<2><<<grid, 256, 0, c->stream>>>(inner, baby, d_diag_ptrs, d_gb_index, n1, limbs, c->logN, pi, map); break;
-        case 4: k_bsgs_mac_reg<4><<<grid, 256, 0, c->stream>>>(inner, baby, d_diag_ptrs, d_gb_index, n1, limbs, c->logN, pi, map); break;
-        default: k_bsgs_mac_reg<8><<<grid, 256, 0, c->stream>>>(inner, baby, d_diag_ptrs, d_gb_index, n1, limbs, c->logN, pi, map); break;
-        }
-        LAUNCHED(c);
-        return;
-    }
     HCHECK(smem <= 200 * 1024, HELRM_E_PARAM, "too many baby steps for the MAC tile");
     if (smem > 48 * 1024)
         CUDA_CHECK(cudaFuncSetAttribute(k_bsgs_mac, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(c->N / MAC_TC, limbs);
-    k_bsgs_mac<<<grid, MAC_TC, smem, c->stream>>>(inner, baby, d_diag_ptrs, d_gb_index, n1, n2, limbs, c->logN,
+    launch(c, k_bsgs_mac, grid, MAC_TC, smem, inner, baby, d_diag_ptrs, d_gb_index, n1, n2, limbs, c->logN,
                                                   c->d_pinfo.as<PrimeInfo>(), map);
     LAUNCHED(c);
 }
-void bsgs_fused(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c1, const u64 *const *keys,
-                const u64 *gals, const u64 *const *d_diag_ptrs, const int *d_gb_index, int n_diag, int n1, int n2,
-                int level)
-{
-    HCHECK(n1 <= 64 && n2 <= 8 && (n2 & (n2 - 1)) == 0, HELRM_E_PARAM, "fused BSGS needs n1 <= 64, n2 <= 8");
-    const int nl = level + 1 + c->K, dnum = c->dnum(level);
-    const size_t plane = (size_t)nl * c->N;
-    int n_keys = 0;
-    BabyKeys bk;
-    for (int b = 0; b < 64; b++) {
-        bk.key[b] = b < n1 ? keys[b] : nullptr;
-        bk.gal[b] = b < n1 ? gals[b] : 1;
-        n_keys += (b < n1 && keys[b]) ? 1 : 0;
-    }
-    // keys (2 dnum planes each) and diagonals once, the c0/c1 gathers, inner written once
-    KTimer kt(c, "bsgs_fused", 8.0 * plane * (2.0 * dnum * n_keys + n_diag + 2.0 * n2) +
-                                   16.0 * (level + 1) * c->N);
-    const unsigned grid = grid_for(plane);
-    const PrimeInfo *pi = c->d_pinfo.as<PrimeInfo>();
-    const u64 *pm = c->d_pmod_mont.u();
-    HCHECK(dnum >= 1 && dnum <= 7, HELRM_E_PARAM, "fused BSGS supports 1..7 key-switching digits");
-#define HELRM_FUSED(NN, DD)                                                                                    \
-    k_bsgs_fused<NN, DD><<<grid, 256, 0, c->stream>>>(inner, digits, c0, c1, bk, d_diag_ptrs, d_gb_index, n1, \
-                                                      level, c->L, c->K, c->logN, pm, pi)
-#define HELRM_FUSED_D(NN)              \
-    switch (dnum) {                    \
-    case 1: HELRM_FUSED(NN, 1); break; \
-    case 2: HELRM_FUSED(NN, 2); break; \
-    case 3: HELRM_FUSED(NN, 3); break; \
-    case 4: HELRM_FUSED(NN, 4); break; \
-    case 5: HELRM_FUSED(NN, 5); break; \
-    case 6: HELRM_FUSED(NN, 6); break; \
-    default: HELRM_FUSED(NN, 7); break; \
-    }
-    switch (n2) {
-    case 1: HELRM_FUSED_D(1); break;
-    case 2: HELRM_FUSED_D(2); break;
-    case 4: HELRM_FUSED_D(4); break;
-    default: HELRM_FUSED_D(8); break;
-    }
-#undef HELRM_FUSED_D
-#undef HELRM_FUSED
-    LAUNCHED(c);
-}
-
 void rescale_spread(Ctx *c, u64 *out, const u64 *last_coef, int level, int n_polys)
 {
     size_t total = (size_t)level * c->N;
     if (!total) return;
     KTimer kt(c, "rescale_spread", 8.0 * n_polys * (total + c->N));
-    k_rescale_spread<<<dim3(grid_for(total), n_polys), TPB, 0, c->stream>>>(out, last_coef, c->rescale_table(level), c->nP(),
+    launch(c, k_rescale_spread, dim3(grid_for(total), n_polys), TPB, 0, out, last_coef, c->rescale_table(level), c->nP(),
                                                              c->logN, total, c->d_pinfo.as<PrimeInfo>());
     LAUNCHED(c);
 }
 void check_range(Ctx *c, const u64 *data, int n_limbs, LimbMap map, int *d_flag)
 {
     size_t total = (size_t)n_limbs * c->N;
-    k_check_range<<<grid_for(total), TPB, 0, c->stream>>>(data, c->logN, total, c->d_pinfo.as<PrimeInfo>(), map,
+    launch(c, k_check_range, grid_for(total), TPB, 0, data, c->logN, total, c->d_pinfo.as<PrimeInfo>(), map,
                                                           d_flag);
     LAUNCHED(c);
 }
 void chacha_words(Ctx *c, u32 *out, u64 seed, u32 purpose, u64 index, u64 first_word, u64 n_words)
 {
     u64 blocks = (first_word + n_words + 15) / 16 - first_word / 16;
-    k_chacha_words<<<grid_for(blocks), TPB, 0, c->stream>>>(out, seed, purpose, index, first_word, n_words);
+    launch(c, k_chacha_words, grid_for(blocks), TPB, 0, out, seed, purpose, index, first_word, n_words);
     LAUNCHED(c);
 }
 void sample_uniform(Ctx *c, u64 *out, u64 seed, u32 purpose, u64 index, int n_limbs, const int *d_limb_pid,
                     const int *d_limb_gid)
 {
     size_t total = (size_t)n_limbs * c->N / 4;
-    k_uniform<<<grid_for(total), TPB, 0, c->stream>>>(out, seed, purpose, index, c->logN, n_limbs, d_limb_pid,
+    launch(c, k_uniform, grid_for(total), TPB, 0, out, seed, purpose, index, c->logN, n_limbs, d_limb_pid,
                                                       d_limb_gid, c->d_pinfo.as<PrimeInfo>());
     LAUNCHED(c);
 }
 void sample_ternary(Ctx *c, i64 *out, u64 seed, u32 purpose, u64 index)
 {
-    k_ternary<<<grid_for(c->N / 16), TPB, 0, c->stream>>>(out, seed, purpose, index, c->N);
+    launch(c, k_ternary, grid_for(c->N / 16), TPB, 0, out, seed, purpose, index, c->N);
     LAUNCHED(c);
 }
 void sample_cbd21(Ctx *c, i64 *out, u64 seed, u32 purpose, u64 index)
 {
-    k_cbd21<<<grid_for(c->N / 8), TPB, 0, c->stream>>>(out, seed, purpose, index, c->N);
+    launch(c, k_cbd21, grid_for(c->N / 8), TPB, 0, out, seed, purpose, index, c->N);
     LAUNCHED(c);
 }
 
@@ -920,7 +726,7 @@ static void fft(Ctx *c, double2 *buf_a, double2 *buf_b, bool inverse, double2 **
 {
     double2 *x = buf_a, *y = buf_b;
     for (int s = 0; s < c->logN; s++) {
-        k_fft_pass<<<grid_for(c->N / 2), TPB, 0, c->stream>>>(x, y, c->logN, s, c->d_fft_tw.as<double2>(),
+        launch(c, k_fft_pass, grid_for(c->N / 2), TPB, 0, x, y, c->logN, s, c->d_fft_tw.as<double2>(),
                                                               inverse ? 1 : 0);
         LAUNCHED(c);
         std::swap(x, y);
@@ -933,12 +739,12 @@ void encode_slots(Ctx *c, u64 *out, const double *d_slots, int n_valid, int peri
 {
     DevMem a(c, (size_t)c->N * sizeof(double2)), b(c, (size_t)c->N * sizeof(double2));
     KTimer kt(c, "encode_fft", 8.0 * c->N * n_limbs);
-    k_enc_gather<<<grid_for(c->N), TPB, 0, c->stream>>>(a.as<double2>(), d_slots, c->d_slot_of.as<int>(), n_valid,
+    launch(c, k_enc_gather, grid_for(c->N), TPB, 0, a.as<double2>(), d_slots, c->d_slot_of.as<int>(), n_valid,
                                                         period, c->N);
     LAUNCHED(c);
     double2 *X;
     fft(c, a.as<double2>(), b.as<double2>(), false, &X);
-    k_enc_round<<<grid_for(c->N), TPB, 0, c->stream>>>(out, d_coeffs_out, X, scale, c->logN, n_limbs,
+    launch(c, k_enc_round, grid_for(c->N), TPB, 0, out, d_coeffs_out, X, scale, c->logN, n_limbs,
                                                        c->d_pinfo.as<PrimeInfo>(), map, c->d_err.as<int>());
     LAUNCHED(c);
     // an overflow is reported by the next synchronising call (Ctx::check_device_errors)
@@ -950,19 +756,19 @@ void decode_limb0(Ctx *c, double *d_out, const u64 *m0, double scale, int n_slot
     KTimer kt(c, "decode", 8.0 * c->N);
     if (n_slots <= 16) {
         DevMem part(c, (size_t)n_slots * DEC_BLOCKS * 8);
-        k_dec_direct<<<dim3(DEC_BLOCKS, n_slots), 256, 0, c->stream>>>(part.as<double>(), m0, q0,
+        launch(c, k_dec_direct, dim3(DEC_BLOCKS, n_slots), 256, 0, part.as<double>(), m0, q0,
                                                                        c->d_u_of_slot.as<int>(), c->logN);
         LAUNCHED(c);
-        k_dec_sum<<<1, 32, 0, c->stream>>>(d_out, part.as<double>(), scale, n_slots);
+        launch(c, k_dec_sum, 1, 32, 0, d_out, part.as<double>(), scale, n_slots);
         LAUNCHED(c);
         return;
     }
     DevMem a(c, (size_t)c->N * sizeof(double2)), b(c, (size_t)c->N * sizeof(double2));
-    k_dec_twist<<<grid_for(c->N), TPB, 0, c->stream>>>(a.as<double2>(), m0, q0, c->logN);
+    launch(c, k_dec_twist, grid_for(c->N), TPB, 0, a.as<double2>(), m0, q0, c->logN);
     LAUNCHED(c);
     double2 *Y;
     fft(c, a.as<double2>(), b.as<double2>(), true, &Y);
-    k_dec_pick<<<grid_for(n_slots), TPB, 0, c->stream>>>(d_out, Y, c->d_u_of_slot.as<int>(), scale, n_slots);
+    launch(c, k_dec_pick, grid_for(n_slots), TPB, 0, d_out, Y, c->d_u_of_slot.as<int>(), scale, n_slots);
     LAUNCHED(c);
 }
 

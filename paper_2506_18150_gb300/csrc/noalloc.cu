@@ -36,6 +36,7 @@ struct RescaleConsts {
 __global__ void k_na_spread(u64 *__restrict__ out, const u64 *__restrict__ last, int level, int logN, int n_polys,
                             RescaleConsts rc)
 {
+    pdl_begin();
     const size_t N = (size_t)1 << logN;
     const size_t total = (size_t)n_polys * level * N;
     const u64 half = (rc.ql - 1) >> 1;
@@ -54,6 +55,7 @@ __global__ void k_na_spread(u64 *__restrict__ out, const u64 *__restrict__ last,
 __global__ void k_na_finish(u64 *__restrict__ out, const u64 *__restrict__ in, int level, int logN, int n_polys,
                             RescaleConsts rc)
 {
+    pdl_begin();
     const size_t N = (size_t)1 << logN;
     const size_t total = (size_t)n_polys * level * N;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
@@ -138,10 +140,10 @@ extern "C" helrm_status helrm_rescale_noalloc(helrm_ctx *ctx, const uint64_t *d_
         k::ntt_map_noheap(c, scratch, (int)n_polys, c->qmap(l, l, 1), true);
         const size_t total = (size_t)n_polys * l * N;
         const unsigned grid = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 64);
-        k_na_spread<<<grid, 256, 0, c->stream>>>(d_out, scratch, l, c->logN, (int)n_polys, rc);
+        launch(c, k_na_spread, grid, 256, 0, d_out, scratch, l, c->logN, (int)n_polys, rc);
         CUDA_CHECK(cudaGetLastError());
         k::ntt_map_noheap(c, d_out, (int)n_polys * l, c->qmap(l - 1, 0, l), false);
-        k_na_finish<<<grid, 256, 0, c->stream>>>(d_out, d_in, l, c->logN, (int)n_polys, rc);
+        launch(c, k_na_finish, grid, 256, 0, d_out, d_in, l, c->logN, (int)n_polys, rc);
         CUDA_CHECK(cudaGetLastError());
         c->launches += 2;
     } catch (const Error &e) {

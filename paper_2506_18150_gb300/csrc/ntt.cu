@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN, int logG,
                                                    const PrimeInfo *__restrict__ pinfo, int mode,
                                                    const u64 *__restrict__ ep_scal)
 {
+    pdl_begin();
     constexpr int P = 1 << LOGP;
     constexpr int TPS = P / 8;              // threads per sub-transform
     extern __shared__ u64 sm[];
@@ -228,7 +229,7 @@ void launch_pass(Ctx *c, const LimbList &ll, int n_sub, int first, int mode, con
     const size_t smem = (size_t)(G * P + (G * P >> 4) + 1) * 8;
     dim3 grid(n_sub / G, ll.n);
     const ulonglong2 *tw = INV ? c->d_tw_inv.as<ulonglong2>() : c->d_tw_fwd.as<ulonglong2>();
-    k_ntt_pass<LOGP, COLS, INV><<<grid, threads, smem, c->stream>>>(
+    launch(c, k_ntt_pass<LOGP, COLS, INV>, grid, threads, smem, 
         first, c->logN, logG, ll, tw, c->d_ninv.as<ulonglong2>(), c->d_pinfo.as<PrimeInfo>(), mode, ep_scal);
 }
 

@@ -84,6 +84,7 @@ typedef struct helrm_ct helrm_ct;       /* ciphertext (device) */
 typedef struct helrm_ptmat helrm_ptmat; /* encoded BSGS diagonals of one matrix (device) */
 typedef struct helrm_emb helrm_emb;     /* packed embedding tables (device) */
 typedef struct helrm_model helrm_model; /* compiled DLRM (device) */
+typedef struct helrm_batch helrm_batch; /* a batch of clients for lockstep inference */
 
 /* ------------------------------------------------------------------ context */
 /* Create a context on `cuda_device`, ordering work on `cuda_stream`
@@ -304,6 +305,37 @@ helrm_status helrm_infer_e2e(helrm_ctx *ctx, const helrm_sk *sk, const helrm_evk
 helrm_status helrm_infer_e2e_device(helrm_ctx *ctx, const helrm_sk *sk, const helrm_evk *evk,
                                     const helrm_model *m, const double *d_dense, const uint64_t *d_indices,
                                     uint32_t n_queries, uint64_t seed, double *d_logits, double *d_probs);
+
+/* ------------------------------------------------ batched inference (a2-a13) */
+/* Lockstep batching of many clients' queries of one model.  Each query goes
+ * through exactly the integer operations of helrm_infer, so every logit
+ * ciphertext is bit-identical to the one helrm_infer returns for that query
+ * alone; the batch only changes the launch shape: every NTT, base
+ * conversion, key inner product and elementwise step is one launch for all
+ * queries, and the fused baby-step + BSGS kernel reads each weight diagonal
+ * once per batch (the diagonals are shared by all clients, Sec. 3.2.1), while
+ * each query streams its own client's keys.
+ *
+ * helrm_batch_create fixes the model and the clients: evks[q] is the
+ * evaluation key set of the client of query q (entries may repeat; each needs
+ * the model's rotations).  It builds the per-client key tables on the device.
+ * The model and the key sets must outlive the batch.  Errors: HELRM_E_NOKEY
+ * if a key set lacks a rotation the model needs. */
+helrm_status helrm_batch_create(helrm_ctx *ctx, const helrm_model *m, uint32_t n, const helrm_evk *const *evks,
+                                helrm_batch **out);
+/* Server side for the n queries of the batch: ct_dense[q], ct_sel[q] at the
+ * model's levels (helrm_encrypt_query with evks[q]); logits[q] receives the
+ * encrypted logit of query q (level 0), as helrm_infer.  Stream ordered, no
+ * synchronisation. */
+helrm_status helrm_infer_batch(helrm_ctx *ctx, const helrm_batch *b, const helrm_ct *const *ct_dense,
+                               const helrm_ct *const *ct_sel, helrm_ct **logits);
+/* The whole protocol for the batch from device buffers: query q (d_dense row
+ * q, d_indices row q) is packed and encrypted under evks[q] with seed + 2q,
+ * the batch is inferred in lockstep, and logit q is decrypted with sks[q]
+ * into d_logits[q].  Nothing is copied to the host; no synchronisation. */
+helrm_status helrm_infer_batch_e2e_device(helrm_ctx *ctx, const helrm_batch *b, const helrm_sk *const *sks,
+                                         const double *d_dense, const uint64_t *d_indices, uint64_t seed,
+                                         double *d_logits);
 
 /* ------------------------------------------------- allocation-free rescale */
 /* The paper has no counterpart to this call; it exists for callers that

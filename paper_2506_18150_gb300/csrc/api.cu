@@ -30,6 +30,13 @@ std::vector<int> model_rotations(const Model *m);
 Ctx *model_ctx(const Model *m);
 u32 model_n_dense(const Model *m);
 u32 model_n_tables(const Model *m);
+struct Batch;
+Batch *batch_create(Ctx *c, const Model *m, const std::vector<const EvalKey *> &evk);
+std::vector<Ciphertext *> model_infer_batch(Ctx *c, const Batch *bt, const std::vector<const Ciphertext *> &ct_dense,
+                                            const std::vector<const Ciphertext *> &ct_sel);
+size_t batch_size(const Batch *b);
+const Model *batch_model(const Batch *b);
+const EvalKey *batch_evk(const Batch *b, size_t q);
 }  // namespace helrm
 
 using namespace helrm;
@@ -52,6 +59,7 @@ Ciphertext *CT(const helrm_ct *p) { return as<Ciphertext>(p, KIND_CT, "ciphertex
 PtMatrix *PM(const helrm_ptmat *p) { return as<PtMatrix>(p, KIND_PTMAT, "ptmat"); }
 Emb *EMB(const helrm_emb *p) { return as<Emb>(p, KIND_EMB, "embedding"); }
 Model *MOD(const helrm_model *p) { return as<Model>(p, KIND_MODEL, "model"); }
+Batch *BAT(const helrm_batch *p) { return as<Batch>(p, KIND_BATCH, "batch"); }
 
 Ctx *ctx_or_null(const void *h)
 {
@@ -642,12 +650,74 @@ helrm_status helrm_infer_e2e_device(helrm_ctx *ctx, const helrm_sk *sk, const he
     });
 }
 
+// ------------------------------------------------------ batched inference
+helrm_status helrm_batch_create(helrm_ctx *ctx, const helrm_model *m, uint32_t n, const helrm_evk *const *evks,
+                                helrm_batch **out)
+{
+    if (out) *out = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        HCHECK(out && evks && n >= 1, HELRM_E_INVAL, "NULL argument or empty batch");
+        std::vector<const EvalKey *> ev;
+        for (u32 q = 0; q < n; q++) ev.push_back(EVK(evks[q]));
+        *out = (helrm_batch *)batch_create(C(ctx), MOD(m), ev);
+    });
+}
+
+helrm_status helrm_infer_batch(helrm_ctx *ctx, const helrm_batch *b, const helrm_ct *const *ct_dense,
+                               const helrm_ct *const *ct_sel, helrm_ct **logits)
+{
+    const size_t n = (b && ((const Handle *)b)->kind == KIND_BATCH) ? batch_size((const Batch *)b) : 0;
+    if (logits)
+        for (size_t q = 0; q < n; q++) logits[q] = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        Batch *bt = BAT(b);
+        HCHECK(ct_dense && ct_sel && logits, HELRM_E_INVAL, "NULL argument");
+        std::vector<const Ciphertext *> d, s;
+        for (size_t q = 0; q < n; q++) {
+            d.push_back(CT(ct_dense[q]));
+            s.push_back(CT(ct_sel[q]));
+        }
+        std::vector<Ciphertext *> y = model_infer_batch(C(ctx), bt, d, s);
+        for (size_t q = 0; q < n; q++) logits[q] = (helrm_ct *)y[q];
+    });
+}
+
+helrm_status helrm_infer_batch_e2e_device(helrm_ctx *ctx, const helrm_batch *b, const helrm_sk *const *sks,
+                                         const double *d_dense, const uint64_t *d_indices, uint64_t seed,
+                                         double *d_logits)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        Batch *bt = BAT(b);
+        HCHECK(sks && d_dense && d_indices && d_logits, HELRM_E_INVAL, "NULL argument");
+        const Model *mm = batch_model(bt);
+        const size_t n = batch_size(bt), nd = model_n_dense((Model *)mm), nt = model_n_tables((Model *)mm);
+        std::vector<const SecretKey *> sk;
+        for (size_t q = 0; q < n; q++) sk.push_back(SK(sks[q]));
+        std::vector<std::unique_ptr<Ciphertext>> a, s;
+        std::vector<const Ciphertext *> ad, sd;
+        for (size_t q = 0; q < n; q++) {   // client side: each client packs and encrypts its own query
+            Ciphertext *x, *y;
+            model_encrypt_query(c, batch_evk(bt, q), mm, d_dense + q * nd, d_indices + q * nt, seed + 2ull * q, &x, &y,
+                                true);
+            a.emplace_back(x);
+            s.emplace_back(y);
+            ad.push_back(x);
+            sd.push_back(y);
+        }
+        std::vector<Ciphertext *> y = model_infer_batch(c, bt, ad, sd);
+        std::vector<std::unique_ptr<Ciphertext>> yo;
+        for (auto *p : y) yo.emplace_back(p);
+        for (size_t q = 0; q < n; q++) decrypt_slots_device(c, sk[q], yo[q].get(), d_logits + q, 1);
+    });
+}
+
 // ------------------------------------------------------------------ misc
 void helrm_free(void *handle)
 {
     if (!handle) return;
     Handle *h = (Handle *)handle;
-    if (h->kind < KIND_CTX || h->kind > KIND_MODEL) return;
+    if (h->kind < KIND_CTX || h->kind > KIND_SERVER) return;
     delete h;
 }
 

@@ -1,0 +1,897 @@
+// batch.cu -- lockstep batched inference: B queries of one model, each with
+// its own client's evaluation keys, advance through the layers together, and
+// every step of the path is one launch for the whole batch.
+//
+// Nothing in the arithmetic changes: each query goes through exactly the
+// integer operations of the one-query path (dlrm.cu, linear.cu, scheme.cu),
+// so its logit ciphertext is bit-identical to the one it would get alone.
+// What changes is the launch shape:
+//  * NTTs, base conversions, key inner products, automorphisms and
+//    elementwise ops take job lists covering every query (and, where the
+//    steps are independent, every giant step or rotation as well);
+//  * the fused baby-step + BSGS kernel runs all queries in one grid whose
+//    fastest index is the query, so the CTAs that share a diagonal tile run
+//    together and the diagonal rows are fetched from HBM once per batch
+//    instead of once per query (the weight diagonals are the same for every
+//    client; the keys are not);
+//  * the per-query key tables of every matrix are built once, when the batch
+//    is created, so a batch can be replayed as a CUDA graph (graph.cu).
+#include <cmath>
+
+#include "model.cuh"
+
+namespace helrm {
+namespace {
+
+constexpr int BJ = 256;   // jobs per batched launch (kernel-parameter arrays)
+constexpr int TPB = 256;
+
+inline unsigned gx_for(size_t total, int n_jobs)
+{
+    size_t g = (total + TPB - 1) / TPB;
+    size_t cap = std::max<size_t>(4, (size_t)152 * 32 / std::max(1, n_jobs));
+    return (unsigned)std::min(g, cap);
+}
+
+enum BOp { B_ADD, B_SUB, B_MULM, B_MULP };
+
+struct EwJobs {
+    int n;
+    u64 *o[BJ];
+    const u64 *a[BJ];
+    const u64 *b[BJ];
+};
+
+__global__ void k_ew_b(const EwJobs J, int logN, size_t total, const PrimeInfo *__restrict__ pinfo, LimbMap map,
+                       int op)
+{
+    pdl_begin();
+    u64 *__restrict__ o = J.o[blockIdx.y];
+    const u64 *__restrict__ a = J.a[blockIdx.y];
+    const u64 *__restrict__ b = J.b[blockIdx.y];
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const PrimeInfo pi = pinfo[map.pid((int)(idx >> logN))];
+        const u64 x = a[idx];
+        u64 r;
+        switch (op) {
+        case B_ADD: r = add_mod(x, b[idx], pi.q); break;
+        case B_SUB: r = sub_mod(x, b[idx], pi.q); break;
+        case B_MULM: r = mont_mul(x, b[idx], pi.q, pi.qinv); break;
+        default: r = mul_mod(x, b[idx], pi.q, pi.qinv, pi.r2); break;
+        }
+        o[idx] = r;
+    }
+}
+
+struct CopyJobs {
+    int n;
+    u64 *o[BJ];
+    const u64 *a[BJ];
+    u64 words[BJ];
+};
+
+__global__ void k_copy_b(const CopyJobs J)
+{
+    pdl_begin();
+    const uint2 *__restrict__ a = (const uint2 *)J.a[blockIdx.y];
+    uint2 *__restrict__ o = (uint2 *)J.o[blockIdx.y];
+    const u64 n = J.words[blockIdx.y];
+    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) o[i] = a[i];
+}
+
+struct TensorJobs {
+    int n;
+    u64 *d[BJ];
+    const u64 *a0[BJ];
+    const u64 *a1[BJ];
+    const u64 *b0[BJ];
+    const u64 *b1[BJ];
+};
+
+// (d0, d1, d2) (+)= (a0 b0, a0 b1 + a1 b0, a1 b1), as k_tensor
+__global__ void k_tensor_b(const TensorJobs J, int logN, size_t total, const PrimeInfo *__restrict__ pinfo,
+                           LimbMap map, int accumulate)
+{
+    pdl_begin();
+    const int j = blockIdx.y;
+    u64 *__restrict__ d = J.d[j];
+    const u64 *__restrict__ a0 = J.a0[j];
+    const u64 *__restrict__ a1 = J.a1[j];
+    const u64 *__restrict__ b0 = J.b0[j];
+    const u64 *__restrict__ b1 = J.b1[j];
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const PrimeInfo pi = pinfo[map.pid((int)(idx >> logN))];
+        const u64 x0 = a0[idx], x1 = a1[idx], y0 = b0[idx], y1 = b1[idx];
+        Acc128 s0, s1, s2;
+        s0.mac(x0, y0, pi.q);
+        s1.mac(x0, y1, pi.q);
+        s1.mac(x1, y0, pi.q);
+        s2.mac(x1, y1, pi.q);
+        u64 r0 = mont_mul(s0.reduce(pi.q, pi.qinv), pi.r2, pi.q, pi.qinv);
+        u64 r1 = mont_mul(s1.reduce(pi.q, pi.qinv), pi.r2, pi.q, pi.qinv);
+        u64 r2 = mont_mul(s2.reduce(pi.q, pi.qinv), pi.r2, pi.q, pi.qinv);
+        if (accumulate) {
+            r0 = add_mod(r0, d[idx], pi.q);
+            r1 = add_mod(r1, d[total + idx], pi.q);
+            r2 = add_mod(r2, d[2 * total + idx], pi.q);
+        }
+        d[idx] = r0;
+        d[total + idx] = r1;
+        d[2 * total + idx] = r2;
+    }
+}
+
+__device__ __forceinline__ int auto_src_b(int i, int logN, u64 galois)
+{
+    const u32 x = __brev((u32)i) >> (32 - logN);
+    const u64 e = ((2ull * x + 1) * galois) & ((2ull << logN) - 1);
+    return (int)(__brev((u32)((e - 1) >> 1)) >> (32 - logN));
+}
+
+struct KsJobs {
+    int n;
+    u64 *out[BJ];
+    const u64 *dig[BJ];
+    const u64 *key[BJ];
+    const u64 *c0[BJ];
+    const u64 *bq[BJ];
+    u64 gal[BJ];
+};
+
+// Fused automorphism + key inner product of k_ks_inner, one job per
+// (query, key): out_h[l][i] = sum_j dig_j[l][src(i)] key_j,h[pid(l)][i]
+// (+ P c0[l][src(i)] on the Q limbs, + bq[l][src(i)], + out when accumulating).
+__global__ void k_ks_inner_b(const KsJobs J, int dnum, int level, int L, int K, int logN, const u64 *__restrict__ pmod,
+                             int accumulate, const PrimeInfo *__restrict__ pinfo)
+{
+    pdl_begin();
+    const int jb = blockIdx.y;
+    u64 *__restrict__ out = J.out[jb];
+    const u64 *__restrict__ dig = J.dig[jb];
+    const u64 *__restrict__ key = J.key[jb];
+    const u64 *__restrict__ c0 = J.c0[jb];
+    const u64 *__restrict__ bq = J.bq[jb];
+    const u64 galois = J.gal[jb];
+    const size_t N = (size_t)1 << logN;
+    const int nl = level + 1 + K, nP = L + 1 + K;
+    const size_t total = (size_t)nl * N;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int l = (int)(idx >> logN);
+        const int i = (int)(idx & (N - 1));
+        const int pid = l <= level ? l : L + 1 + (l - level - 1);
+        const PrimeInfo pi = pinfo[pid];
+        const int src = galois == 1 ? i : auto_src_b(i, logN, galois);
+        Acc128 a0, a1;
+        for (int j = 0; j < dnum; j++) {
+            const u64 d = dig[((size_t)j * nl + l) * N + src];
+            a0.mac(d, key[((size_t)(2 * j) * nP + pid) * N + i], pi.q);
+            a1.mac(d, key[((size_t)(2 * j + 1) * nP + pid) * N + i], pi.q);
+        }
+        u64 r0 = a0.reduce(pi.q, pi.qinv);
+        u64 r1 = a1.reduce(pi.q, pi.qinv);
+        if (c0 && l <= level) r0 = add_mod(r0, mont_mul(c0[(size_t)l * N + src], pmod[pid], pi.q, pi.qinv), pi.q);
+        if (bq) r0 = add_mod(r0, bq[(size_t)l * N + src], pi.q);
+        if (accumulate) {
+            r0 = add_mod(r0, out[idx], pi.q);
+            r1 = add_mod(r1, out[total + idx], pi.q);
+        }
+        out[idx] = r0;
+        out[total + idx] = r1;
+    }
+}
+
+struct AutoJobs {
+    int n;
+    u64 *o[BJ];
+    const u64 *a[BJ];
+    u64 gal[BJ];
+};
+
+__global__ void k_auto_b(const AutoJobs J, int logN, size_t total)
+{
+    pdl_begin();
+    u64 *__restrict__ o = J.o[blockIdx.y];
+    const u64 *__restrict__ a = J.a[blockIdx.y];
+    const u64 g = J.gal[blockIdx.y];
+    const size_t N = (size_t)1 << logN;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t base = idx & ~(N - 1);
+        o[idx] = a[base + auto_src_b((int)(idx & (N - 1)), logN, g)];
+    }
+}
+
+// rescale helper of k_rescale_spread, one job per polynomial: the dropped
+// limb (coefficient form) -> its centred remainder on limbs 0..level-1
+struct SpreadJobs {
+    int n;
+    u64 *o[BJ];
+    const u64 *last[BJ];
+};
+__global__ void k_spread_b(const SpreadJobs J, const u64 *__restrict__ tab, int nP, int logN, size_t total,
+                           const PrimeInfo *__restrict__ pinfo)
+{
+    pdl_begin();
+    u64 *__restrict__ out = J.o[blockIdx.y];
+    const u64 *__restrict__ last = J.last[blockIdx.y];
+    const size_t N = (size_t)1 << logN;
+    const u64 ql = tab[2 * nP];
+    const u64 half = (ql - 1) >> 1;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int l = (int)(idx >> logN);
+        const u64 q = pinfo[l].q;
+        const u64 x = last[idx & (N - 1)];
+        const u64 xm = x < q ? x : x % q;
+        out[idx] = x <= half ? xm : sub_mod(xm, tab[nP + l], q);
+    }
+}
+
+// ------------------------------------------------------------ launch helpers
+void ew_b(Ctx *c, int op, const std::vector<u64 *> &o, const std::vector<const u64 *> &a,
+          const std::vector<const u64 *> &b, int n_limbs, LimbMap map)
+{
+    const size_t total = (size_t)n_limbs * c->N;
+    if (!total || o.empty()) return;
+    KTimer kt(c, "elementwise", 24.0 * total * o.size());
+    for (size_t s = 0; s < o.size(); s += BJ) {
+        EwJobs J;
+        J.n = (int)std::min<size_t>(BJ, o.size() - s);
+        for (int j = 0; j < J.n; j++) {
+            J.o[j] = o[s + j];
+            J.a[j] = a[s + j];
+            J.b[j] = b[s + j];
+        }
+        launch(c, k_ew_b, dim3(gx_for(total, J.n), J.n), TPB, 0, J, c->logN, total, c->d_pinfo.as<PrimeInfo>(), map,
+               op);
+        c->launches++;
+    }
+    CUDA_CHECK(cudaGetLastError());
+}
+
+void copy_b(Ctx *c, const std::vector<u64 *> &o, const std::vector<const u64 *> &a, const std::vector<u64> &words)
+{
+    if (o.empty()) return;
+    double bytes = 0;
+    u64 mx = 0;
+    for (u64 w : words) {
+        bytes += 16.0 * w;
+        mx = std::max(mx, w);
+    }
+    KTimer kt(c, "elementwise", bytes);
+    for (size_t s = 0; s < o.size(); s += BJ) {
+        CopyJobs J;
+        J.n = (int)std::min<size_t>(BJ, o.size() - s);
+        for (int j = 0; j < J.n; j++) {
+            J.o[j] = o[s + j];
+            J.a[j] = a[s + j];
+            J.words[j] = words[s + j];
+        }
+        launch(c, k_copy_b, dim3(gx_for(mx, J.n), J.n), TPB, 0, J);
+        c->launches++;
+    }
+    CUDA_CHECK(cudaGetLastError());
+}
+
+struct KsJob {
+    u64 *out;
+    const u64 *dig;
+    const u64 *key;
+    u64 gal;
+    const u64 *c0;
+    const u64 *bq;
+};
+
+void ks_inner_b(Ctx *c, const std::vector<KsJob> &jobs, int level, bool accumulate)
+{
+    if (jobs.empty()) return;
+    const int dnum = c->dnum(level);
+    const size_t total = (size_t)(level + 1 + c->K) * c->N;
+    double bytes = 0;
+    for (auto &j : jobs)
+        bytes += 8.0 * (total * (3.0 * dnum + (accumulate ? 4 : 2) + (j.bq ? 1 : 0)) +
+                        (j.c0 ? (double)(level + 1) * c->N : 0.0));
+    KTimer kt(c, "ks_inner_auto", bytes);
+    for (size_t s = 0; s < jobs.size(); s += BJ) {
+        KsJobs J;
+        J.n = (int)std::min<size_t>(BJ, jobs.size() - s);
+        for (int j = 0; j < J.n; j++) {
+            const KsJob &x = jobs[s + j];
+            J.out[j] = x.out;
+            J.dig[j] = x.dig;
+            J.key[j] = x.key;
+            J.c0[j] = x.c0;
+            J.bq[j] = x.bq;
+            J.gal[j] = x.gal;
+        }
+        launch(c, k_ks_inner_b, dim3(gx_for(total, J.n), J.n), TPB, 0, J, dnum, level, c->L, c->K, c->logN,
+               c->d_pmod_mont.u(), accumulate ? 1 : 0, c->d_pinfo.as<PrimeInfo>());
+        c->launches++;
+    }
+    CUDA_CHECK(cudaGetLastError());
+}
+
+void auto_b(Ctx *c, const std::vector<u64 *> &o, const std::vector<const u64 *> &a, const std::vector<u64> &gal,
+            int n_limbs)
+{
+    const size_t total = (size_t)n_limbs * c->N;
+    if (!total || o.empty()) return;
+    KTimer kt(c, "automorphism", 16.0 * total * o.size());
+    for (size_t s = 0; s < o.size(); s += BJ) {
+        AutoJobs J;
+        J.n = (int)std::min<size_t>(BJ, o.size() - s);
+        for (int j = 0; j < J.n; j++) {
+            J.o[j] = o[s + j];
+            J.a[j] = a[s + j];
+            J.gal[j] = gal[s + j];
+        }
+        launch(c, k_auto_b, dim3(gx_for(total, J.n), J.n), TPB, 0, J, c->logN, total);
+        c->launches++;
+    }
+    CUDA_CHECK(cudaGetLastError());
+}
+
+// ------------------------------------------------------------ batched CKKS steps
+using CtVec = std::vector<Ciphertext *>;
+using CCtVec = std::vector<const Ciphertext *>;
+
+struct Owned {   // owns the ciphertexts of one batched value
+    std::vector<std::unique_ptr<Ciphertext>> v;
+    CtVec raw() const
+    {
+        CtVec r;
+        for (auto &p : v) r.push_back(p.get());
+        return r;
+    }
+    CCtVec craw() const
+    {
+        CCtVec r;
+        for (auto &p : v) r.push_back(p.get());
+        return r;
+    }
+};
+
+// ModUp (iNTT, fast base conversion of every digit, NTT of the converted
+// limbs) of several polynomials at `level`, as ks_modup.
+void modup_b(Ctx *c, const std::vector<const u64 *> &polys, int level, const std::vector<u64 *> &digits)
+{
+    const int N = c->N, nq = level + 1, nl = nq + c->K, dnum = c->dnum(level);
+    const size_t B = polys.size();
+    const LimbMap m = c->qmap(level);
+    DevMem coef(c, B * nq * N * 8);
+    std::vector<k::NttLimb> v;
+    for (size_t q = 0; q < B; q++)
+        for (int l = 0; l < nq; l++)
+            v.push_back({polys[q] + (size_t)l * N, coef.u() + (q * nq + l) * N, m.pid(l), nullptr, nullptr, nullptr});
+    k::ntt_run(c, v, true, nullptr);
+    std::vector<k::BConvCall> bc;
+    for (size_t q = 0; q < B; q++)
+        for (int j = 0; j < dnum; j++)
+            bc.push_back({&c->modup_table(level, j), coef.u() + q * nq * N, digits[q] + (size_t)j * nl * N});
+    k::bconv_multi(c, bc);
+    std::vector<u64 *> co;
+    std::vector<const u64 *> ca;
+    std::vector<u64> cw;
+    v.clear();
+    for (size_t q = 0; q < B; q++)
+        for (int j = 0; j < dnum; j++) {
+            u64 *d = digits[q] + (size_t)j * nl * N;
+            const int lo = c->digit_lo(j), hi = c->digit_hi(j, level);
+            co.push_back(d + (size_t)lo * N);
+            ca.push_back(polys[q] + (size_t)lo * N);
+            cw.push_back((u64)(hi - lo) * N);
+            for (int l = 0; l < nl; l++)
+                if (l < lo || l >= hi) {
+                    u64 *p = d + (size_t)l * N;
+                    v.push_back({p, p, m.pid(l), nullptr, nullptr, nullptr});
+                }
+        }
+    copy_b(c, co, ca, cw);
+    k::ntt_run(c, v, false, nullptr);
+}
+
+// ModDown of `halves` QP polynomials per entry (u[q] = [halves][nl][N]), as
+// ks_moddown2 / ks_moddown: out_h = (u_h - FBC_{P->Q}([u_h]_P)) P^-1 (+ add_h).
+void moddown_b(Ctx *c, const std::vector<const u64 *> &u, int level, int halves, const std::vector<u64 *> &out0,
+               const std::vector<u64 *> &out1, const std::vector<const u64 *> &add0,
+               const std::vector<const u64 *> &add1)
+{
+    const int N = c->N, nq = level + 1, K = c->K, nl = nq + K;
+    const size_t B = u.size();
+    const LimbMap m = c->qmap(level);
+    DevMem pc(c, B * halves * K * N * 8), y(c, B * halves * nq * N * 8);
+    std::vector<k::NttLimb> v;
+    for (size_t q = 0; q < B; q++)
+        for (int h = 0; h < halves; h++)
+            for (int i = 0; i < K; i++)
+                v.push_back({u[q] + (size_t)(h * nl + nq + i) * N, pc.u() + ((q * halves + h) * K + i) * N,
+                             m.pid(nq + i), nullptr, nullptr, nullptr});
+    k::ntt_run(c, v, true, nullptr);
+    const BConvTable &md = c->moddown_table(level);
+    std::vector<k::BConvCall> bc;
+    for (size_t q = 0; q < B; q++)
+        for (int h = 0; h < halves; h++)
+            bc.push_back({&md, pc.u() + (q * halves + h) * K * N, y.u() + (q * halves + h) * nq * N});
+    k::bconv_multi(c, bc);
+    v.clear();
+    for (size_t q = 0; q < B; q++)
+        for (int h = 0; h < halves; h++)
+            for (int l = 0; l < nq; l++) {
+                u64 *yl = y.u() + ((q * halves + h) * nq + l) * N;
+                const u64 *ad = h ? add1[q] : add0[q];
+                v.push_back({yl, yl, m.pid(l), u[q] + (size_t)(h * nl + l) * N, (h ? out1[q] : out0[q]) + (size_t)l * N,
+                             ad ? ad + (size_t)l * N : nullptr});
+            }
+    k::ntt_run(c, v, false, c->d_pinv_mont.u());
+}
+
+// rescale of every ciphertext (all at the same level), as ct_rescale
+Owned rescale_b(Ctx *c, const CCtVec &a)
+{
+    Owned o;
+    if (a.empty()) return o;
+    const int l = a[0]->level, N = c->N;
+    const size_t B = a.size();
+    HCHECK(l >= 1, HELRM_E_LEVEL, "no level left to rescale");
+    for (auto *x : a) {
+        HCHECK(x->level == l, HELRM_E_LEVEL, "batched rescale needs one level");
+        o.v.emplace_back(new_ct(c, l - 1, x->scale / (double)c->primes[l]));
+    }
+    DevMem last(c, B * 2 * N * 8), r(c, B * 2 * l * N * 8);
+    std::vector<k::NttLimb> v;
+    for (size_t q = 0; q < B; q++)
+        for (int h = 0; h < 2; h++)
+            v.push_back({(h ? a[q]->c1() : a[q]->c0()) + (size_t)l * N, last.u() + (q * 2 + h) * N, l, nullptr,
+                         nullptr, nullptr});
+    k::ntt_run(c, v, true, nullptr);
+    const size_t total = (size_t)l * N;
+    {
+        KTimer kt(c, "rescale_spread", 8.0 * 2 * B * (total + N));
+        for (size_t s = 0; s < 2 * B; s += BJ) {
+            SpreadJobs J;
+            J.n = (int)std::min<size_t>(BJ, 2 * B - s);
+            for (int j = 0; j < J.n; j++) {
+                J.o[j] = r.u() + (s + j) * l * N;
+                J.last[j] = last.u() + (s + j) * N;
+            }
+            launch(c, k_spread_b, dim3(gx_for(total, J.n), J.n), TPB, 0, J, c->rescale_table(l), c->nP(), c->logN,
+                   total, c->d_pinfo.as<PrimeInfo>());
+            c->launches++;
+        }
+        CUDA_CHECK(cudaGetLastError());
+    }
+    v.clear();
+    for (size_t q = 0; q < B; q++)
+        for (int h = 0; h < 2; h++)
+            for (int i = 0; i < l; i++) {
+                u64 *ri = r.u() + ((q * 2 + h) * l + i) * N;
+                v.push_back({ri, ri, i, (h ? a[q]->c1() : a[q]->c0()) + (size_t)i * N,
+                             (h ? o.v[q]->c1() : o.v[q]->c0()) + (size_t)i * N, nullptr});
+            }
+    k::ntt_run(c, v, false, c->rescale_table(l));
+    return o;
+}
+
+Owned add_b(Ctx *c, const CCtVec &a, const CCtVec &b)
+{
+    Owned o;
+    std::vector<u64 *> oo;
+    std::vector<const u64 *> aa, bb;
+    for (size_t q = 0; q < a.size(); q++) {
+        HCHECK(a[q]->level == b[q]->level && a[q]->level == a[0]->level, HELRM_E_LEVEL, "ciphertext levels differ");
+        HCHECK(std::fabs(a[q]->scale - b[q]->scale) <= 1e-9 * a[q]->scale, HELRM_E_SCALE, "ciphertext scales differ");
+        o.v.emplace_back(new_ct(c, a[q]->level, a[q]->scale));
+        oo.push_back(o.v[q]->data.u());
+        aa.push_back(a[q]->data.u());
+        bb.push_back(b[q]->data.u());
+    }
+    if (a.empty()) return o;
+    const int l = a[0]->level;
+    ew_b(c, B_ADD, oo, aa, bb, 2 * (l + 1), c->qmap(l, 0, l + 1));
+    return o;
+}
+
+Owned add_pt_b(Ctx *c, const CCtVec &a, const Plaintext *pt)
+{
+    HCHECK(pt->form == PT_PLAIN, HELRM_E_INVAL, "plaintext is in multiplier form");
+    Owned o;
+    if (a.empty()) return o;
+    const int l = a[0]->level, nq = l + 1;
+    HCHECK(pt->level >= l, HELRM_E_LEVEL, "plaintext level below ciphertext level");
+    std::vector<u64 *> oo, co;
+    std::vector<const u64 *> aa, bb, ca;
+    std::vector<u64> cw;
+    for (size_t q = 0; q < a.size(); q++) {
+        HCHECK(a[q]->level == l, HELRM_E_LEVEL, "batched op needs one level");
+        HCHECK(std::fabs(a[q]->scale - pt->scale) <= 1e-9 * a[q]->scale, HELRM_E_SCALE, "plaintext scale differs");
+        o.v.emplace_back(new_ct(c, l, a[q]->scale));
+        oo.push_back(o.v[q]->c0());
+        aa.push_back(a[q]->c0());
+        bb.push_back(pt->data.u());
+        co.push_back(o.v[q]->c1());
+        ca.push_back(a[q]->c1());
+        cw.push_back((u64)nq * c->N);
+    }
+    ew_b(c, B_ADD, oo, aa, bb, nq, c->qmap(l));
+    copy_b(c, co, ca, cw);
+    return o;
+}
+
+// products of every ciphertext a[q] with every plaintext pts[i]: out[q * n_pt + i]
+Owned mul_pt_b(Ctx *c, const CCtVec &a, const std::vector<const Plaintext *> &pts)
+{
+    Owned o;
+    if (a.empty() || pts.empty()) return o;
+    const int l = a[0]->level, nq = l + 1;
+    const int form = pts[0]->form;
+    std::vector<u64 *> oo;
+    std::vector<const u64 *> aa, bb;
+    for (size_t q = 0; q < a.size(); q++) {
+        HCHECK(a[q]->level == l, HELRM_E_LEVEL, "batched op needs one level");
+        for (const Plaintext *pt : pts) {
+            HCHECK(pt->level >= l && !pt->qp && pt->form == form, HELRM_E_LEVEL, "plaintext level below ciphertext level");
+            std::unique_ptr<Ciphertext> x(new_ct(c, l, a[q]->scale * pt->scale));
+            for (int h = 0; h < 2; h++) {
+                oo.push_back(h ? x->c1() : x->c0());
+                aa.push_back(h ? a[q]->c1() : a[q]->c0());
+                bb.push_back(pt->data.u());
+            }
+            o.v.push_back(std::move(x));
+        }
+    }
+    ew_b(c, form == PT_MONT ? B_MULM : B_MULP, oo, aa, bb, nq, c->qmap(l));
+    return o;
+}
+
+// rotations of every a[q] by every step (one ModUp per query, shared by its
+// steps): out[q * S + s], as ct_rotate_hoisted
+Owned rotate_b(Ctx *c, const std::vector<const EvalKey *> &evk, const CCtVec &a, const std::vector<int> &steps)
+{
+    Owned o;
+    if (a.empty()) return o;
+    const int l = a[0]->level, N = c->N, nq = l + 1, nl = nq + c->K, dnum = c->dnum(l);
+    const size_t B = a.size(), S = steps.size();
+    const size_t dplane = (size_t)dnum * nl * N, uplane = (size_t)2 * nl * N;
+    for (auto *x : a) HCHECK(x->level == l, HELRM_E_LEVEL, "batched rotation needs one level");
+    std::vector<const SwitchKey *> keys(B * S, nullptr);
+    for (size_t q = 0; q < B; q++)
+        for (size_t s = 0; s < S; s++)
+            if (c->galois(steps[s]) != 1) keys[q * S + s] = rot_key(evk[q], c->galois(steps[s]));
+    DevMem digits(c, B * dplane * 8), u(c, B * S * uplane * 8);
+    std::vector<const u64 *> c1s;
+    std::vector<u64 *> dg;
+    for (size_t q = 0; q < B; q++) {
+        c1s.push_back(a[q]->c1());
+        dg.push_back(digits.u() + q * dplane);
+    }
+    modup_b(c, c1s, l, dg);
+    std::vector<KsJob> jobs;
+    std::vector<u64 *> ao, co;
+    std::vector<const u64 *> aa, ca, uu, add0;
+    std::vector<u64> ag, cw;
+    std::vector<u64 *> o0, o1;
+    for (size_t q = 0; q < B; q++)
+        for (size_t s = 0; s < S; s++) {
+            const u64 g = c->galois(steps[s]);
+            std::unique_ptr<Ciphertext> x(new_ct(c, l, a[q]->scale));
+            if (g == 1) {
+                co.push_back(x->data.u());
+                ca.push_back(a[q]->data.u());
+                cw.push_back((u64)2 * nq * N);
+            } else {
+                u64 *uq = u.u() + (q * S + s) * uplane;
+                jobs.push_back({uq, dg[q], keys[q * S + s]->data.u(), g, nullptr, nullptr});
+                ao.push_back(x->c0());
+                aa.push_back(a[q]->c0());
+                ag.push_back(g);
+                uu.push_back(uq);
+                o0.push_back(x->c0());
+                o1.push_back(x->c1());
+                add0.push_back(x->c0());
+            }
+            o.v.push_back(std::move(x));
+        }
+    copy_b(c, co, ca, cw);
+    ks_inner_b(c, jobs, l, false);
+    auto_b(c, ao, aa, ag, nq);
+    moddown_b(c, uu, l, 2, o0, o1, add0, std::vector<const u64 *>(uu.size(), nullptr));   // phi(c0) + ModDown(u)
+    return o;
+}
+
+// relinearisation of (d0, d1, d2) per query, as ct_relin
+Owned relin_b(Ctx *c, const std::vector<const EvalKey *> &evk, const std::vector<const u64 *> &d012, int level,
+              double scale)
+{
+    Owned o;
+    const int N = c->N, nq = level + 1, nl = nq + c->K, dnum = c->dnum(level);
+    const size_t B = d012.size(), plane = (size_t)nq * N, dplane = (size_t)dnum * nl * N, uplane = (size_t)2 * nl * N;
+    for (auto *e : evk) HCHECK(e->relin, HELRM_E_NOKEY, "no relinearisation key");
+    DevMem digits(c, B * dplane * 8), u(c, B * uplane * 8);
+    std::vector<const u64 *> d2, uu, a0, a1;
+    std::vector<u64 *> dg, o0, o1;
+    for (size_t q = 0; q < B; q++) {
+        d2.push_back(d012[q] + 2 * plane);
+        dg.push_back(digits.u() + q * dplane);
+    }
+    modup_b(c, d2, level, dg);
+    std::vector<KsJob> jobs;
+    for (size_t q = 0; q < B; q++) {
+        u64 *uq = u.u() + q * uplane;
+        jobs.push_back({uq, dg[q], evk[q]->relin->data.u(), 1, nullptr, nullptr});
+        o.v.emplace_back(new_ct(c, level, scale));
+        uu.push_back(uq);
+        o0.push_back(o.v[q]->c0());
+        o1.push_back(o.v[q]->c1());
+        a0.push_back(d012[q]);
+        a1.push_back(d012[q] + plane);
+    }
+    ks_inner_b(c, jobs, level, false);
+    moddown_b(c, uu, level, 2, o0, o1, a0, a1);   // (d0, d1) + ModDown(u)
+    return o;
+}
+
+void tensor_b(Ctx *c, const std::vector<u64 *> &d, const CCtVec &a, const CCtVec &b, bool accumulate)
+{
+    if (a.empty()) return;
+    const int l = a[0]->level;
+    const size_t total = (size_t)(l + 1) * c->N;
+    KTimer kt(c, "tensor", (accumulate ? 10.0 : 7.0) * 8 * total * a.size());
+    for (size_t s = 0; s < a.size(); s += BJ) {
+        TensorJobs J;
+        J.n = (int)std::min<size_t>(BJ, a.size() - s);
+        for (int j = 0; j < J.n; j++) {
+            HCHECK(a[s + j]->level == l && b[s + j]->level == l, HELRM_E_LEVEL, "ciphertext levels differ");
+            J.d[j] = d[s + j];
+            J.a0[j] = a[s + j]->c0();
+            J.a1[j] = a[s + j]->c1();
+            J.b0[j] = b[s + j]->c0();
+            J.b1[j] = b[s + j]->c1();
+        }
+        launch(c, k_tensor_b, dim3(gx_for(total, J.n), J.n), TPB, 0, J, c->logN, total, c->d_pinfo.as<PrimeInfo>(),
+               c->qmap(l), accumulate ? 1 : 0);
+        c->launches++;
+    }
+    CUDA_CHECK(cudaGetLastError());
+}
+
+// a * a, relinearised and rescaled (the x^2 activation), as ct_mul(a, a)
+Owned square_b(Ctx *c, const std::vector<const EvalKey *> &evk, const CCtVec &a)
+{
+    const int l = a[0]->level;
+    HCHECK(l >= 1, HELRM_E_LEVEL, "no level left for a multiplication");
+    const size_t B = a.size(), per = (size_t)3 * (l + 1) * c->N;
+    DevMem d(c, B * per * 8);
+    std::vector<u64 *> dd;
+    std::vector<const u64 *> cd;
+    for (size_t q = 0; q < B; q++) {
+        dd.push_back(d.u() + q * per);
+        cd.push_back(d.u() + q * per);
+    }
+    tensor_b(c, dd, a, a, false);
+    Owned r = relin_b(c, evk, cd, l, a[0]->scale * a[0]->scale);
+    return rescale_b(c, r.craw());
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ the batch
+struct Batch : Handle {
+    Ctx *ctx;
+    const Model *model;
+    std::vector<const EvalKey *> evk;
+    std::map<const PtMatrix *, DevMem> keytab;   // [B][64] baby-step keys of each fused-kernel matrix
+    Batch(Ctx *c) : Handle(KIND_BATCH), ctx(c) {}
+};
+
+static void batch_keytab(Batch *bt, const PtMatrix *m)
+{
+    Ctx *c = bt->ctx;
+    if (!(m->n1 <= 64 && m->n2 <= 8)) return;
+    std::vector<char> need(m->n1, 0);
+    for (auto &gb : m->gb) need[gb.second] = 1;
+    std::vector<const u64 *> tab(bt->evk.size() * 64, nullptr);
+    for (size_t q = 0; q < bt->evk.size(); q++)
+        for (int b = 1; b < m->n1; b++)
+            if (need[b]) tab[q * 64 + b] = rot_key(bt->evk[q], c->galois(b))->data.u();
+    DevMem d(c, tab.size() * sizeof(u64 *));
+    CUDA_CHECK(cudaMemcpyAsync(d.ptr, tab.data(), tab.size() * sizeof(u64 *), cudaMemcpyHostToDevice, c->stream));
+    bt->keytab[m] = std::move(d);
+}
+
+Batch *batch_create(Ctx *c, const Model *m, const std::vector<const EvalKey *> &evk)
+{
+    HCHECK(!evk.empty(), HELRM_E_INVAL, "empty batch");
+    std::unique_ptr<Batch> b(new Batch(c));
+    b->model = m;
+    b->evk = evk;
+    for (auto &L : m->bottom) batch_keytab(b.get(), L.pm.get());
+    batch_keytab(b.get(), m->emb->pm.get());
+    for (auto &L : m->top) batch_keytab(b.get(), L.pm.get());
+    CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    return b.release();
+}
+
+// y = W x for every query (double-hoisted BSGS, rescale, folds), as matvec
+static Owned matvec_b(Ctx *c, const Batch *bt, const PtMatrix *m, const CCtVec &in)
+{
+    const size_t B = in.size();
+    const int l = in[0]->level, N = c->N, nq = l + 1, nl = nq + c->K, dnum = c->dnum(l);
+    for (auto *x : in) HCHECK(x->level == m->level, HELRM_E_LEVEL, "ciphertext level does not match the prepared matrix");
+    auto kt = bt->keytab.find(m);
+    if (kt == bt->keytab.end()) {   // shapes outside the fused kernel: the one-query path, query by query
+        Owned o;
+        for (size_t q = 0; q < B; q++) o.v.emplace_back(matvec(c, bt->evk[q], m, in[q]));
+        return o;
+    }
+    const size_t plane = (size_t)nl * N, dplane = (size_t)dnum * plane;
+    std::vector<char> need_b(m->n1, 0), need_g(m->n2, 0);
+    for (auto &gb : m->gb) {
+        need_b[gb.second] = 1;
+        need_g[gb.first] = 1;
+    }
+    std::vector<const u64 *> gkey(B * m->n2, nullptr);
+    for (size_t q = 0; q < B; q++)
+        for (int g = 1; g < m->n2; g++)
+            if (need_g[g]) gkey[q * m->n2 + g] = rot_key(bt->evk[q], c->galois(g * m->n1))->data.u();
+    bool any_baby = false;
+    int n_keys = 0;
+    for (int b = 1; b < m->n1; b++) {
+        any_baby |= need_b[b] != 0;
+        n_keys += need_b[b] ? 1 : 0;
+    }
+    DevMem digits(c, B * dplane * 8);
+    std::vector<u64 *> dg;
+    std::vector<const u64 *> c1s;
+    for (size_t q = 0; q < B; q++) {
+        dg.push_back(digits.u() + q * dplane);
+        c1s.push_back(in[q]->c1());
+    }
+    if (any_baby) modup_b(c, c1s, l, dg);
+    const size_t iq = (size_t)m->n2 * 2 * plane;   // inner products of one query
+    DevMem inner(c, B * iq * 8);
+    std::vector<u64> gals(m->n1, 1);
+    for (int b = 1; b < m->n1; b++)
+        if (need_b[b]) gals[b] = c->galois(b);
+    std::vector<k::BsgsQuery> qs;
+    for (size_t q = 0; q < B; q++) qs.push_back({inner.u() + q * iq, dg[q], in[q]->c0(), in[q]->c1()});
+    k::bsgs_tma_batch(c, qs, kt->second.as<const u64 *const>(), gals.data(), m->d_ptrs.as<const u64 *const>(),
+                      m->d_gb_index.as<int>(), (int)m->gb.size(), n_keys, m->n1, m->n2, l);
+    // giant steps: ModDown the a-part of every (query, g > 0), ModUp them all,
+    // then one key product per g adds phi(inner_g) into inner_0 of each query
+    std::vector<int> gs;
+    for (int g = 1; g < m->n2; g++)
+        if (need_g[g]) gs.push_back(g);
+    if (!need_g[0])
+        for (size_t q = 0; q < B; q++) k::zero(c, inner.u() + q * iq, 2 * plane);
+    if (!gs.empty()) {
+        const size_t G = gs.size();
+        DevMem c1q(c, B * G * (size_t)nq * N * 8), gdig(c, B * G * dplane * 8);
+        std::vector<const u64 *> ua, c1v;
+        std::vector<u64 *> o0, gd;
+        for (size_t q = 0; q < B; q++)
+            for (size_t t = 0; t < G; t++) {
+                ua.push_back(inner.u() + q * iq + (size_t)gs[t] * 2 * plane + plane);
+                o0.push_back(c1q.u() + (q * G + t) * nq * N);
+                c1v.push_back(o0.back());
+                gd.push_back(gdig.u() + (q * G + t) * dplane);
+            }
+        std::vector<const u64 *> none(ua.size(), nullptr);
+        moddown_b(c, ua, l, 1, o0, o0, none, none);
+        modup_b(c, c1v, l, gd);
+        for (size_t t = 0; t < G; t++) {
+            std::vector<KsJob> jobs;
+            const u64 gal = c->galois(gs[t] * m->n1);
+            for (size_t q = 0; q < B; q++)
+                jobs.push_back({inner.u() + q * iq, gd[q * G + t], gkey[q * m->n2 + gs[t]], gal, nullptr,
+                                inner.u() + q * iq + (size_t)gs[t] * 2 * plane});
+            ks_inner_b(c, jobs, l, true);
+        }
+    }
+    Owned o;
+    std::vector<const u64 *> acc, none(B, nullptr);
+    std::vector<u64 *> o0, o1;
+    for (size_t q = 0; q < B; q++) {
+        o.v.emplace_back(new_ct(c, l, in[q]->scale * m->pt_scale));
+        acc.push_back(inner.u() + q * iq);
+        o0.push_back(o.v[q]->c0());
+        o1.push_back(o.v[q]->c1());
+    }
+    moddown_b(c, acc, l, 2, o0, o1, none, none);
+    Owned y = rescale_b(c, o.craw());
+    for (auto &p : y.v) p->scale = m->out_scale;
+    for (int f : m->folds) {
+        Owned r = rotate_b(c, bt->evk, y.craw(), {f});
+        y = add_b(c, y.craw(), r.craw());
+    }
+    return y;
+}
+
+static Owned dense_layer_b(Ctx *c, const Batch *bt, const Layer &L, const CCtVec &x)
+{
+    Owned y = matvec_b(c, bt, L.pm.get(), x);
+    y = add_pt_b(c, y.craw(), L.bias.get());
+    if (L.square) y = square_b(c, bt->evk, y.craw());
+    return y;
+}
+
+static Owned dot_interaction_b(Ctx *c, const Batch *bt, const Model *m, const CCtVec &z)
+{
+    const size_t B = z.size();
+    const int S = m->S;
+    std::vector<const Plaintext *> masks;
+    for (auto &p : m->masks) masks.push_back(p.get());
+    Owned zm = mul_pt_b(c, z, masks);                 // [q][i], i = 0..S
+    Owned zr = rescale_b(c, zm.craw());
+    for (auto &p : zr.v) p->scale = c->delta;
+    CCtVec z1, A;                                      // A[q * S + s - 1] = z_q masked by mask s
+    for (size_t q = 0; q < B; q++) {
+        z1.push_back(zr.v[q * (S + 1)].get());
+        for (int s = 1; s <= S; s++) A.push_back(zr.v[q * (S + 1) + s].get());
+    }
+    Owned r = rotate_b(c, bt->evk, z1, {-DIM * m->Bp});
+    Owned zz = add_b(c, z1, r.craw());
+    std::vector<int> steps;
+    for (int s = 1; s <= S; s++) steps.push_back(DIM * s);
+    Owned R = rotate_b(c, bt->evk, zz.craw(), steps);   // [q][s - 1]
+    const int lvl = z1[0]->level;
+    const size_t per = (size_t)3 * (lvl + 1) * c->N;
+    DevMem d(c, B * per * 8);
+    std::vector<u64 *> dd;
+    std::vector<const u64 *> cd;
+    for (size_t q = 0; q < B; q++) {
+        dd.push_back(d.u() + q * per);
+        cd.push_back(d.u() + q * per);
+    }
+    for (int s = 1; s <= S; s++) {
+        CCtVec as, rs;
+        for (size_t q = 0; q < B; q++) {
+            as.push_back(A[q * S + s - 1]);
+            rs.push_back(R.v[q * S + s - 1].get());
+        }
+        tensor_b(c, dd, as, rs, s > 1);
+    }
+    Owned rl = relin_b(c, bt->evk, cd, lvl, c->delta * c->delta);
+    return rescale_b(c, rl.craw());
+}
+
+std::vector<Ciphertext *> model_infer_batch(Ctx *c, const Batch *bt, const CCtVec &ct_dense, const CCtVec &ct_sel)
+{
+    const Model *m = bt->model;
+    const size_t B = bt->evk.size();
+    HCHECK(ct_dense.size() == B && ct_sel.size() == B, HELRM_E_INVAL, "batch size mismatch");
+    for (size_t q = 0; q < B; q++) {
+        HCHECK(ct_dense[q]->level == m->lvl_dense, HELRM_E_LEVEL, "ct_dense is not at the model's dense level");
+        HCHECK(ct_sel[q]->level == m->lvl_sel, HELRM_E_LEVEL, "ct_sel is not at the model's selector level");
+    }
+    Owned h;
+    CCtVec x = ct_dense;
+    for (auto &L : m->bottom) {
+        h = dense_layer_b(c, bt, L, x);
+        x = h.craw();
+    }
+    Owned e = matvec_b(c, bt, m->emb->pm.get(), ct_sel);
+    Owned z = add_b(c, h.craw(), e.craw());
+    h = Owned();
+    e = Owned();
+    Owned y;
+    if (m->interaction == 0) {
+        z = add_pt_b(c, z.craw(), m->ones.get());
+        y = dot_interaction_b(c, bt, m, z.craw());
+    } else {
+        y = std::move(z);
+    }
+    for (auto &L : m->top) y = dense_layer_b(c, bt, L, y.craw());
+    std::vector<Ciphertext *> out;
+    for (auto &p : y.v) out.push_back(p.release());
+    return out;
+}
+
+size_t batch_size(const Batch *b) { return b->evk.size(); }
+const EvalKey *batch_evk(const Batch *b, size_t q) { return b->evk[q]; }
+const Model *batch_model(const Batch *b) { return b->model; }
+Ctx *batch_ctx(const Batch *b) { return b->ctx; }
+
+}  // namespace helrm

@@ -68,9 +68,19 @@ __device__ __forceinline__ int auto_src(int i, int logN, u64 galois)
     return (int)(__brev((u32)((e - 1) >> 1)) >> (32 - logN));
 }
 
-struct TmaBabies {
-    const u64 *key[64];   // key of baby step b (b >= 1)
-    u64 gal[64];
+// Per-query operands of one batched launch (kernel parameters).  The batch
+// index is the fastest grid dimension, so the CTAs of all queries that work
+// on the same tile run together and the diagonal rows they share are read
+// from HBM once and served to the others from L2.
+constexpr int BQ = 64;
+struct TmaQueries {
+    u64 *inner[BQ];
+    const u64 *dig[BQ];
+    const u64 *c0[BQ];
+    const u64 *c1[BQ];
+};
+struct TmaGals {
+    u64 gal[64];          // Galois element of baby step b
 };
 
 // Stage layout (words): dig[DN][T] | kb[DN][T] | ka[DN][T] | c0[T] | dd[N2][T]
@@ -97,9 +107,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(u64 *bar, u32 parity)
 constexpr int CONSUMER_WARPS = T / 32;
 
 template <int N2, int DN>
-__global__ void __launch_bounds__(T + 32) k_bsgs_tma(u64 *__restrict__ inner, const u64 *__restrict__ dig,
-                                                    const u64 *__restrict__ c0, const u64 *__restrict__ c1,
-                                                    TmaBabies bk, const u64 *const *__restrict__ diag,
+__global__ void __launch_bounds__(T + 32) k_bsgs_tma(
+                                                    const TmaQueries qs, const TmaGals bk,
+                                                    const u64 *const *__restrict__ keytab,
+                                                    const u64 *const *__restrict__ diag,
                                                     const int *__restrict__ gb, int n1, int level, int L, int K,
                                                     int logN, const u64 *__restrict__ pmod,
                                                     const PrimeInfo *__restrict__ pinfo, int *err)
@@ -116,8 +127,13 @@ __global__ void __launch_bounds__(T + 32) k_bsgs_tma(u64 *__restrict__ inner, co
     const size_t N = (size_t)1 << logN;
     const int nl = level + 1 + K, nP = L + 1 + K;
     const size_t plane = (size_t)nl * N;
-    const int l = blockIdx.y;
-    const int i0 = blockIdx.x * T;
+    const int qi = blockIdx.x;
+    const int l = blockIdx.z;
+    const int i0 = blockIdx.y * T;
+    u64 *const inner = qs.inner[qi];
+    const u64 *const dig = qs.dig[qi];
+    const u64 *const c0 = qs.c0[qi];
+    const u64 *const c1 = qs.c1[qi];
     const bool qlimb = l <= level;
     const int pid = qlimb ? l : L + 1 + (l - level - 1);
 
@@ -156,7 +172,7 @@ __global__ void __launch_bounds__(T + 32) k_bsgs_tma(u64 *__restrict__ inner, co
             const int b = blist[k];
             u64 *st = smem + s * SW;
             const int src_base = auto_src(i0, logN, bk.gal[b]) & ~(T - 1);
-            const u64 *key = bk.key[b];
+            const u64 *key = keytab[(size_t)qi * 64 + b];
             int nd = 0;
             for (int g = 0; g < N2; g++) nd += sgb[g * n1 + b] >= 0;
             if (lane == 0) mbar_arrive_expect_tx(&full[s], (u32)(3 * DN + (qlimb ? 1 : 0) + nd) * T * 8);
@@ -262,39 +278,44 @@ __global__ void __launch_bounds__(T + 32) k_bsgs_tma(u64 *__restrict__ inner, co
 }
 
 template <int N2, int DN>
-void launch_tma(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c1, const TmaBabies &bk,
-            const u64 *const *diag, const int *gb, int n1, int level)
+void launch_tma(Ctx *c, const TmaQueries &qs, int nq, const TmaGals &bk, const u64 *const *keytab,
+                const u64 *const *diag, const int *gb, int n1, int level)
 {
     const size_t smem = (size_t)S * Stage<N2, DN>::WORDS * 8 + 2 * S * 8;
     CUDA_CHECK(cudaFuncSetAttribute(k_bsgs_tma<N2, DN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid(c->N / T, level + 1 + c->K);
-    launch(c, k_bsgs_tma<N2, DN>, grid, T + 32, smem, inner, digits, c0, c1, bk, diag, gb, n1, level, c->L, c->K,
-                                                     c->logN, c->d_pmod_mont.u(), c->d_pinfo.as<PrimeInfo>(),
-                                                     c->d_err.as<int>());
+    dim3 grid(nq, c->N / T, level + 1 + c->K);
+    launch(c, k_bsgs_tma<N2, DN>, grid, T + 32, smem, qs, bk, keytab, diag, gb, n1, level, c->L, c->K, c->logN,
+           c->d_pmod_mont.u(), c->d_pinfo.as<PrimeInfo>(), c->d_err.as<int>());
 }
 
 }  // namespace
 
 namespace k {
 
-void bsgs_tma(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c1, const u64 *const *keys,
-              const u64 *gals, const u64 *const *d_diag_ptrs, const int *d_gb_index, int n_diag, int n1, int n2,
-              int level)
+void bsgs_tma_batch(Ctx *c, const std::vector<BsgsQuery> &qv, const u64 *const *d_keytab, const u64 *gals,
+                    const u64 *const *d_diag_ptrs, const int *d_gb_index, int n_diag, int n_keys, int n1, int n2,
+                    int level)
 {
     const int dnum = c->dnum(level);
     HCHECK(n1 <= 64 && (n2 == 1 || n2 == 2 || n2 == 4 || n2 == 8), HELRM_E_PARAM, "BSGS tile supports n1 <= 64, n2 <= 8");
     HCHECK(dnum >= 1 && dnum <= 7 && c->N >= T, HELRM_E_PARAM, "BSGS tile supports 1..7 digits");
-    TmaBabies bk;
-    int n_keys = 0;
-    for (int b = 0; b < 64; b++) {
-        bk.key[b] = b < n1 ? keys[b] : nullptr;
-        bk.gal[b] = b < n1 ? gals[b] : 1;
-        n_keys += (b > 0 && b < n1 && keys[b]) ? 1 : 0;
-    }
+    TmaGals bk;
+    for (int b = 0; b < 64; b++) bk.gal[b] = b < n1 ? gals[b] : 1;
     const size_t plane = (size_t)(level + 1 + c->K) * c->N;
-    KTimer kt(c, "bsgs_fused", 8.0 * plane * (2.0 * dnum * n_keys + n_diag + 2.0 * n2) +
-                                   16.0 * (level + 1) * c->N);
-#define HELRM_TMA(NN, DD) launch_tma<NN, DD>(c, inner, digits, c0, c1, bk, d_diag_ptrs, d_gb_index, n1, level)
+    for (size_t q0 = 0; q0 < qv.size(); q0 += BQ) {
+        const int nq = (int)std::min<size_t>(BQ, qv.size() - q0);
+        TmaQueries qs = {};
+        for (int q = 0; q < nq; q++) {
+            qs.inner[q] = qv[q0 + q].inner;
+            qs.dig[q] = qv[q0 + q].dig;
+            qs.c0[q] = qv[q0 + q].c0;
+            qs.c1[q] = qv[q0 + q].c1;
+        }
+        // per query: its keys and ciphertext once; the diagonals once per launch
+        KTimer kt(c, "bsgs_fused", 8.0 * plane * nq * (2.0 * dnum * n_keys + 2.0 * n2) + 8.0 * plane * n_diag +
+                                       16.0 * nq * (level + 1) * c->N);
+        const u64 *const *kt_q = d_keytab + q0 * 64;
+#define HELRM_TMA(NN, DD) launch_tma<NN, DD>(c, qs, nq, bk, kt_q, d_diag_ptrs, d_gb_index, n1, level)
 #define HELRM_TMA_D(NN)              \
     switch (dnum) {                  \
     case 1: HELRM_TMA(NN, 1); break; \
@@ -305,16 +326,34 @@ void bsgs_tma(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c
     case 6: HELRM_TMA(NN, 6); break; \
     default: HELRM_TMA(NN, 7); break; \
     }
-    switch (n2) {
-    case 1: HELRM_TMA_D(1); break;
-    case 2: HELRM_TMA_D(2); break;
-    case 4: HELRM_TMA_D(4); break;
-    default: HELRM_TMA_D(8); break;
-    }
+        switch (n2) {
+        case 1: HELRM_TMA_D(1); break;
+        case 2: HELRM_TMA_D(2); break;
+        case 4: HELRM_TMA_D(4); break;
+        default: HELRM_TMA_D(8); break;
+        }
 #undef HELRM_TMA_D
 #undef HELRM_TMA
-    c->launches++;
-    CUDA_CHECK(cudaGetLastError());
+        c->launches++;
+        CUDA_CHECK(cudaGetLastError());
+    }
+}
+
+void bsgs_tma(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c1, const u64 *const *keys,
+              const u64 *gals, const u64 *const *d_diag_ptrs, const int *d_gb_index, int n_diag, int n1, int n2,
+              int level)
+{
+    // the key table of this one query, staged to the device (stream ordered)
+    std::vector<const u64 *> tab(64, nullptr);
+    int n_keys = 0;
+    for (int b = 1; b < n1; b++) {
+        tab[b] = keys[b];
+        n_keys += keys[b] ? 1 : 0;
+    }
+    DevMem d_tab(c, 64 * sizeof(u64 *));
+    CUDA_CHECK(cudaMemcpyAsync(d_tab.ptr, tab.data(), 64 * sizeof(u64 *), cudaMemcpyHostToDevice, c->stream));
+    bsgs_tma_batch(c, {{inner, digits, c0, c1}}, d_tab.as<const u64 *const>(), gals, d_diag_ptrs, d_gb_index, n_diag,
+                   n_keys, n1, n2, level);
 }
 
 }  // namespace k

@@ -301,6 +301,7 @@ Ctx *ctx_create(const helrm_params *p, int device, void *stream)
     std::unique_ptr<Ctx> c(new Ctx());
     c->device = device;
     CUDA_CHECK(cudaSetDevice(device));
+    CUDA_CHECK(cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device));
     c->stream = (cudaStream_t)stream;
     c->logN = (int)p->log_n;
     c->N = 1 << c->logN;

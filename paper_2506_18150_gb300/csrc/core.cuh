@@ -157,6 +157,8 @@ enum Kind : u32 {
     KIND_PTMAT,
     KIND_EMB,
     KIND_MODEL,
+    KIND_BATCH,
+    KIND_SERVER,
 };
 
 struct Handle {
@@ -173,6 +175,7 @@ struct BConvTable {
 
 struct Ctx : Handle {
     int device = 0;
+    int n_sms = 152;           // streaming multiprocessors of the device
     cudaStream_t stream = nullptr;
     int logN = 0, N = 0, n_slots = 0, L = 0, K = 0, alpha = 1;
     double delta = 0;
@@ -399,6 +402,17 @@ void automorphism(Ctx *c, u64 *out, const u64 *in, int n_limbs, u64 galois);
 void bsgs_tma(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c1, const u64 *const *keys,
               const u64 *gals, const u64 *const *d_diag_ptrs, const int *d_gb_index, int n_diag, int n1, int n2,
               int level);
+// the same for a batch of queries of one matrix (one launch per 64 queries):
+// query q reads its keys from d_keytab[q][0..63] (device, baby step b >= 1)
+struct BsgsQuery {
+    u64 *inner;
+    const u64 *dig;
+    const u64 *c0;
+    const u64 *c1;
+};
+void bsgs_tma_batch(Ctx *c, const std::vector<BsgsQuery> &qs, const u64 *const *d_keytab, const u64 *gals,
+                    const u64 *const *d_diag_ptrs, const int *d_gb_index, int n_diag, int n_keys, int n1, int n2,
+                    int level);
 // rescale helper: coefficient-form last limb -> centred residues for ell limbs
 void rescale_spread(Ctx *c, u64 *out, const u64 *last_coef, int level, int n_polys = 1);
 // random

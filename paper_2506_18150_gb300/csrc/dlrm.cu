@@ -22,15 +22,11 @@
 #include <algorithm>
 #include <cmath>
 
-#include "core.cuh"
+#include "model.cuh"
 
 namespace helrm {
 
-constexpr int DIM = 16;
 
-struct SelSeg {
-    int t, j, off, width;
-};
 
 static int num_digits(u64 k, u64 p)
 {
@@ -63,15 +59,6 @@ static std::vector<SelSeg> selector_layout(const std::vector<u64> &cards, int p,
     return out;
 }
 
-struct Emb : Handle {
-    Ctx *ctx;
-    std::vector<u64> cards;
-    int base = 0, dim = 0, width = 0, in_pad = 0, out_pad = 0;
-    std::vector<SelSeg> layout;
-    std::unique_ptr<PtMatrix> pm;
-    DevMem d_tab;   // int [T][3]: card (clamped), offset, digits
-    Emb(Ctx *c) : Handle(KIND_EMB), ctx(c) {}
-};
 
 // Matrix of the packed lookup: rows [out_offset + dim t, out_offset + dim (t+1))
 // take table t's transposed digit tables at the selector columns of its digits.
@@ -140,57 +127,7 @@ void emb_pack_host(const Emb *e, const u64 *indices, std::vector<double> &sel)
 }
 
 // ------------------------------------------------------------------ model
-struct Layer {
-    std::unique_ptr<PtMatrix> pm;
-    std::unique_ptr<Plaintext> bias;
-    bool square = false;
-};
 
-struct Model : Handle {
-    Ctx *ctx;
-    int n_dense = 0, interaction = 0, T = 0, B = 0, Bp = 0, S = 0;
-    int lvl_dense = 0, lvl_sel = 0, lvl_z = 0, lvl_u = 0, p_dense = 0, W_z = 0, W2 = 0, W_u = 0;
-    double mask_scale = 0;
-    std::vector<Layer> bottom, top;
-    std::unique_ptr<Emb> emb;
-    std::unique_ptr<Plaintext> ones;
-    std::vector<std::unique_ptr<Plaintext>> masks;
-    Model(Ctx *c) : Handle(KIND_MODEL), ctx(c) {}
-
-    std::vector<std::unique_ptr<Plaintext> *> plaintexts()
-    {
-        std::vector<std::unique_ptr<Plaintext> *> out;
-        for (auto &l : bottom) {
-            for (auto &p : l.pm->pts) out.push_back(&p);
-            out.push_back(&l.bias);
-        }
-        for (auto &p : emb->pm->pts) out.push_back(&p);
-        if (interaction == 0) {
-            out.push_back(&ones);
-            for (auto &m : masks) out.push_back(&m);
-        }
-        for (auto &l : top) {
-            for (auto &p : l.pm->pts) out.push_back(&p);
-            out.push_back(&l.bias);
-        }
-        return out;
-    }
-    std::vector<int> rotations() const
-    {
-        std::vector<int> st;
-        auto addv = [&](const std::vector<int> &v) { st.insert(st.end(), v.begin(), v.end()); };
-        for (auto &l : bottom) addv(l.pm->rotations());
-        addv(emb->pm->rotations());
-        if (interaction == 0) {
-            st.push_back(-DIM * Bp);
-            for (int s = 1; s <= S; s++) st.push_back(DIM * s);
-        }
-        for (auto &l : top) addv(l.pm->rotations());
-        std::sort(st.begin(), st.end());
-        st.erase(std::unique(st.begin(), st.end()), st.end());
-        return st;
-    }
-};
 
 static int pair_index(int a, int c2, int B)
 {

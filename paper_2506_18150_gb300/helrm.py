@@ -106,6 +106,9 @@ _SIGS = {
     "helrm_infer_e2e": [_vp, _vp, _vp, _vp, _dp, _u64p, C.c_uint32, C.c_uint64, _dp, _dp],
     "helrm_infer_e2e_device": [_vp, _vp, _vp, _vp, _vp, _vp, C.c_uint32, C.c_uint64, _vp, _vp],
     "helrm_rescale_noalloc": [_vp, _vp, _vp, C.c_int32, C.c_uint32],
+    "helrm_batch_create": [_vp, _vp, C.c_uint32, _pp, _pp],
+    "helrm_infer_batch": [_vp, _vp, _pp, _pp, _pp],
+    "helrm_infer_batch_e2e_device": [_vp, _vp, _pp, _vp, _vp, C.c_uint64, _vp],
     "helrm_ctx_profile": [_vp, C.c_int],
     "helrm_ctx_profile_report": [_vp, C.c_char_p, C.c_uint64, _u64p],
 }
@@ -498,6 +501,31 @@ def helrm_infer_e2e_device(ctx, sk, evk, m, d_dense: int, d_indices: int, n_quer
     _check(ctx, lib().helrm_infer_e2e_device(ctx.ptr, sk.ptr, evk.ptr, m.ptr, C.c_void_p(d_dense),
                                              C.c_void_p(d_indices), n_queries, seed, C.c_void_p(d_logits),
                                              C.c_void_p(d_probs or None)))
+
+
+def _ptrs(handles):
+    return (C.c_void_p * len(handles))(*[h.ptr.value for h in handles])
+
+
+def helrm_batch_create(ctx, m, evks):
+    """A lockstep batch of len(evks) queries of model m; evks[q] = the key set of query q's client."""
+    arr = _ptrs(evks)
+    out = C.c_void_p()
+    _check(ctx, lib().helrm_batch_create(ctx.ptr, m.ptr, len(evks), arr, C.byref(out)))
+    return Handle(out.value, (ctx, m, list(evks)))
+
+
+def helrm_infer_batch(ctx, batch, cts_dense, cts_sel):
+    n = len(cts_dense)
+    outs = (C.c_void_p * n)()
+    _check(ctx, lib().helrm_infer_batch(ctx.ptr, batch.ptr, _ptrs(cts_dense), _ptrs(cts_sel), outs))
+    return [Handle(outs[q], ctx) for q in range(n)]
+
+
+def helrm_infer_batch_e2e_device(ctx, batch, sks, d_dense: int, d_indices: int, seed: int, d_logits: int):
+    """Device pointers (ints): d_dense n x n_dense f64, d_indices n x n_tables u64, d_logits n f64."""
+    _check(ctx, lib().helrm_infer_batch_e2e_device(ctx.ptr, batch.ptr, _ptrs(sks), C.c_void_p(d_dense),
+                                                   C.c_void_p(d_indices), seed, C.c_void_p(d_logits)))
 
 
 def helrm_rescale_noalloc(ctx, d_in: int, d_out: int, level: int, n_polys: int):

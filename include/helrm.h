@@ -59,8 +59,8 @@ typedef enum {
 /*
  * CKKS parameters (appendix "CKKS operations": R = Z[X]/(X^N+1), Q = prod q_i).
  *   log_n      N = 2^log_n, 10 <= log_n <= 16; slots n = N/2.
- *   n_q        L+1 ciphertext primes, 1..32;  q_bits[i] their bit sizes (30..61).
- *   n_p        K special primes for key switching, 1..8, each of p_bits (30..61).
+ *   n_q        L+1 ciphertext primes, 1..32;  q_bits[i] their bit sizes (30..60).
+ *   n_p        K special primes for key switching, 1..8, each of p_bits (30..60).
  *   alpha      primes per key-switching digit (1..8); dnum = ceil((L+1)/alpha).
  *   log2_scale default scale Delta = 2^log2_scale.
  * Primes: q = 1 mod 2N, for each requested size the largest unused one below
@@ -85,6 +85,7 @@ typedef struct helrm_ptmat helrm_ptmat; /* encoded BSGS diagonals of one matrix 
 typedef struct helrm_emb helrm_emb;     /* packed embedding tables (device) */
 typedef struct helrm_model helrm_model; /* compiled DLRM (device) */
 typedef struct helrm_batch helrm_batch; /* a batch of clients for lockstep inference */
+typedef struct helrm_server helrm_server; /* request loop with continuous batching */
 
 /* ------------------------------------------------------------------ context */
 /* Create a context on `cuda_device`, ordering work on `cuda_stream`
@@ -133,6 +134,17 @@ helrm_status helrm_ntt(helrm_ctx *ctx, uint64_t *d_data, uint32_t n_limbs, uint3
  * stay resident on the device. */
 helrm_status helrm_keygen(helrm_ctx *ctx, uint64_t seed, const int32_t *rot_steps, uint32_t n_rot,
                           helrm_sk **sk_out, helrm_evk **evk_out);
+/* Key generation for one model: the same secret key, public key and key
+ * values as helrm_keygen(seed) with the model's rotations, but each rotation
+ * key is generated only up to the highest level at which the model uses it,
+ * and the relinearisation key up to the highest level of a ciphertext
+ * product (a key of level l holds dnum(l) digits over q_0..q_l and the special
+ * primes; every value equals the full key's, so ciphertexts are unchanged).
+ * Using such a key above its level fails with HELRM_E_NOKEY.  Serving many
+ * clients this way needs a fraction of the memory of full keys (the paper
+ * reports about 200 MiB per full key, Sec. 2.1.3). */
+helrm_status helrm_model_keygen(helrm_ctx *ctx, const helrm_model *m, uint64_t seed, helrm_sk **sk_out,
+                                helrm_evk **evk_out);
 /* Add rotation keys for more steps to an existing key set. */
 helrm_status helrm_evk_add_rotations(helrm_ctx *ctx, const helrm_sk *sk, helrm_evk *evk,
                                      const int32_t *rot_steps, uint32_t n_rot);
@@ -336,6 +348,45 @@ helrm_status helrm_infer_batch(helrm_ctx *ctx, const helrm_batch *b, const helrm
 helrm_status helrm_infer_batch_e2e_device(helrm_ctx *ctx, const helrm_batch *b, const helrm_sk *const *sks,
                                          const double *d_dense, const uint64_t *d_indices, uint64_t seed,
                                          double *d_logits);
+
+/* --------------------------------------------------- serving (a2-a13, batched) */
+/* A request loop over lockstep batches.  Clients register their model and
+ * evaluation keys once; the keys stay resident on the device.  The server
+ * has n_slots batch slots, each its own CUDA stream: batches on different
+ * slots run concurrently on the GPU.  A batch holds up to max_batch requests
+ * of one model (a batch of one runs helrm_infer itself, so n_slots = 1,
+ * max_batch = 1 is the plain one-request-at-a-time path).  mem_budget bounds
+ * the device bytes that in-flight batches may hold (0 = unbounded); a
+ * context memory cap (helrm_ctx_set_memory_cap), when set, takes precedence.
+ * Errors: HELRM_E_INVAL for sizes outside 1..16 slots, 1..256 per batch. */
+helrm_status helrm_server_create(helrm_ctx *ctx, uint32_t n_slots, uint32_t max_batch, uint64_t mem_budget,
+                                 helrm_server **out);
+/* Register a client: the model its queries use and its evaluation keys
+ * (both must outlive the server).  *client_id receives its index. */
+helrm_status helrm_server_add_client(helrm_ctx *ctx, helrm_server *s, const helrm_model *m, const helrm_evk *evk,
+                                     uint32_t *client_id);
+typedef struct {
+    double p50_ms, p99_ms, mean_ms, max_ms;  /* request latency: completion - arrival */
+    double makespan_s;                        /* first arrival to last completion */
+    double throughput;                        /* requests / makespan_s */
+    uint32_t n_batches, max_batch, max_inflight;
+    double mean_batch;
+} helrm_serve_stats;
+/* Replay n timed requests through the loop.  Request r arrives at
+ * arrival_s[r] seconds (sorted ascending) from client[r] with its two query
+ * ciphertexts (helrm_encrypt_query, already on the device).  Each pass of
+ * the loop admits the requests that have arrived, launches a batch on every
+ * free slot that the memory budget allows (oldest pending request first,
+ * with more pending requests of the same model), and polls the slots for
+ * completion.  Requests arriving while others run start as soon as a slot
+ * and memory free up, overlapping on the device.  When nothing is pending or
+ * running, the loop skips ahead to the next arrival.  logits_out[r] receives
+ * request r's encrypted logit (bit-identical to helrm_infer's);
+ * latency_ms_out[r] its latency; stats (optional) the summary.  On error all
+ * logits handed out are released and set to NULL. */
+helrm_status helrm_server_run(helrm_ctx *ctx, helrm_server *s, uint32_t n, const double *arrival_s,
+                              const uint32_t *client, const helrm_ct *const *ct_dense, const helrm_ct *const *ct_sel,
+                              helrm_ct **logits_out, double *latency_ms_out, helrm_serve_stats *stats);
 
 /* ------------------------------------------------- allocation-free rescale */
 /* The paper has no counterpart to this call; it exists for callers that

@@ -27,6 +27,7 @@ void model_encrypt_query(Ctx *c, const EvalKey *evk, const Model *m, const doubl
                          u64 seed, Ciphertext **ct_dense, Ciphertext **ct_sel, bool on_device);
 void model_info(const Model *m, u32 *o);
 std::vector<int> model_rotations(const Model *m);
+std::vector<std::pair<int, int>> model_key_levels(const Model *m, int *relin_level);
 Ctx *model_ctx(const Model *m);
 u32 model_n_dense(const Model *m);
 u32 model_n_tables(const Model *m);
@@ -37,6 +38,11 @@ std::vector<Ciphertext *> model_infer_batch(Ctx *c, const Batch *bt, const std::
 size_t batch_size(const Batch *b);
 const Model *batch_model(const Batch *b);
 const EvalKey *batch_evk(const Batch *b, size_t q);
+struct Server;
+Server *server_create(Ctx *c, int n_slots, int max_batch, u64 budget);
+u32 server_add_client(Server *s, const Model *m, const EvalKey *evk);
+void server_run(Server *s, u32 n, const double *arrival, const u32 *client, const Ciphertext *const *ct_dense,
+                const Ciphertext *const *ct_sel, Ciphertext **out, double *latency_ms, helrm_serve_stats *st);
 }  // namespace helrm
 
 using namespace helrm;
@@ -60,6 +66,7 @@ PtMatrix *PM(const helrm_ptmat *p) { return as<PtMatrix>(p, KIND_PTMAT, "ptmat")
 Emb *EMB(const helrm_emb *p) { return as<Emb>(p, KIND_EMB, "embedding"); }
 Model *MOD(const helrm_model *p) { return as<Model>(p, KIND_MODEL, "model"); }
 Batch *BAT(const helrm_batch *p) { return as<Batch>(p, KIND_BATCH, "batch"); }
+Server *SRV(const helrm_server *p) { return as<Server>(p, KIND_SERVER, "server"); }
 
 Ctx *ctx_or_null(const void *h)
 {
@@ -238,6 +245,30 @@ helrm_status helrm_keygen(helrm_ctx *ctx, uint64_t seed, const int32_t *rot_step
         std::unique_ptr<SecretKey> sk(keygen_sk(c, seed));
         std::unique_ptr<EvalKey> evk(keygen_evk(c, sk.get(), seed));
         keygen_rot(c, sk.get(), evk.get(), std::vector<int>(rot_steps, rot_steps + n_rot));
+        CUDA_CHECK(cudaStreamSynchronize(c->stream));
+        *sk_out = (helrm_sk *)sk.release();
+        *evk_out = (helrm_evk *)evk.release();
+    });
+}
+
+helrm_status helrm_model_keygen(helrm_ctx *ctx, const helrm_model *m, uint64_t seed, helrm_sk **sk_out,
+                                helrm_evk **evk_out)
+{
+    if (sk_out) *sk_out = nullptr;
+    if (evk_out) *evk_out = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        HCHECK(sk_out && evk_out, HELRM_E_INVAL, "output pointers are NULL");
+        int rl = 0;
+        std::vector<std::pair<int, int>> kl = model_key_levels(MOD(m), &rl);
+        std::vector<int> steps, levels;
+        for (auto &x : kl) {
+            steps.push_back(x.first);
+            levels.push_back(x.second);
+        }
+        std::unique_ptr<SecretKey> sk(keygen_sk(c, seed));
+        std::unique_ptr<EvalKey> evk(keygen_evk(c, sk.get(), seed, rl));
+        keygen_rot(c, sk.get(), evk.get(), steps, levels);
         CUDA_CHECK(cudaStreamSynchronize(c->stream));
         *sk_out = (helrm_sk *)sk.release();
         *evk_out = (helrm_evk *)evk.release();
@@ -709,6 +740,47 @@ helrm_status helrm_infer_batch_e2e_device(helrm_ctx *ctx, const helrm_batch *b, 
         std::vector<std::unique_ptr<Ciphertext>> yo;
         for (auto *p : y) yo.emplace_back(p);
         for (size_t q = 0; q < n; q++) decrypt_slots_device(c, sk[q], yo[q].get(), d_logits + q, 1);
+    });
+}
+
+// ------------------------------------------------------------------ serving
+helrm_status helrm_server_create(helrm_ctx *ctx, uint32_t n_slots, uint32_t max_batch, uint64_t mem_budget,
+                                 helrm_server **out)
+{
+    if (out) *out = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        HCHECK(out, HELRM_E_INVAL, "out is NULL");
+        *out = (helrm_server *)server_create(C(ctx), (int)n_slots, (int)max_batch, mem_budget);
+    });
+}
+
+helrm_status helrm_server_add_client(helrm_ctx *ctx, helrm_server *s, const helrm_model *m, const helrm_evk *evk,
+                                     uint32_t *client_id)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        C(ctx);
+        const u32 id = server_add_client(SRV(s), MOD(m), EVK(evk));
+        if (client_id) *client_id = id;
+    });
+}
+
+helrm_status helrm_server_run(helrm_ctx *ctx, helrm_server *s, uint32_t n, const double *arrival_s,
+                              const uint32_t *client, const helrm_ct *const *ct_dense, const helrm_ct *const *ct_sel,
+                              helrm_ct **logits_out, double *latency_ms_out, helrm_serve_stats *stats)
+{
+    if (logits_out)
+        for (u32 r = 0; r < n; r++) logits_out[r] = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        C(ctx);
+        HCHECK(arrival_s && client && ct_dense && ct_sel && logits_out && latency_ms_out, HELRM_E_INVAL,
+               "NULL argument");
+        std::vector<const Ciphertext *> d(n), sl(n);
+        for (u32 r = 0; r < n; r++) {
+            d[r] = CT(ct_dense[r]);
+            sl[r] = CT(ct_sel[r]);
+        }
+        server_run(SRV(s), n, arrival_s, client, d.data(), sl.data(), (Ciphertext **)logits_out, latency_ms_out,
+                   stats);
     });
 }
 

@@ -138,6 +138,7 @@ struct KsJobs {
     const u64 *c0[BJ];
     const u64 *bq[BJ];
     u64 gal[BJ];
+    int kl[BJ];           // level the job's key was generated up to
 };
 
 // Fused automorphism + key inner product of k_ks_inner, one job per
@@ -154,21 +155,23 @@ __global__ void k_ks_inner_b(const KsJobs J, int dnum, int level, int L, int K, 
     const u64 *__restrict__ c0 = J.c0[jb];
     const u64 *__restrict__ bq = J.bq[jb];
     const u64 galois = J.gal[jb];
+    const int kl = J.kl[jb];
     const size_t N = (size_t)1 << logN;
-    const int nl = level + 1 + K, nP = L + 1 + K;
+    const int nl = level + 1 + K, nK = kl + 1 + K;
     const size_t total = (size_t)nl * N;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
         const int l = (int)(idx >> logN);
         const int i = (int)(idx & (N - 1));
         const int pid = l <= level ? l : L + 1 + (l - level - 1);
+        const int kx = key_limb(pid, kl, L);
         const PrimeInfo pi = pinfo[pid];
         const int src = galois == 1 ? i : auto_src_b(i, logN, galois);
         Acc128 a0, a1;
         for (int j = 0; j < dnum; j++) {
             const u64 d = dig[((size_t)j * nl + l) * N + src];
-            a0.mac(d, key[((size_t)(2 * j) * nP + pid) * N + i], pi.q);
-            a1.mac(d, key[((size_t)(2 * j + 1) * nP + pid) * N + i], pi.q);
+            a0.mac(d, key[((size_t)(2 * j) * nK + kx) * N + i], pi.q);
+            a1.mac(d, key[((size_t)(2 * j + 1) * nK + kx) * N + i], pi.q);
         }
         u64 r0 = a0.reduce(pi.q, pi.qinv);
         u64 r1 = a1.reduce(pi.q, pi.qinv);
@@ -279,7 +282,7 @@ void copy_b(Ctx *c, const std::vector<u64 *> &o, const std::vector<const u64 *> 
 struct KsJob {
     u64 *out;
     const u64 *dig;
-    const u64 *key;
+    const SwitchKey *key;
     u64 gal;
     const u64 *c0;
     const u64 *bq;
@@ -302,7 +305,9 @@ void ks_inner_b(Ctx *c, const std::vector<KsJob> &jobs, int level, bool accumula
             const KsJob &x = jobs[s + j];
             J.out[j] = x.out;
             J.dig[j] = x.dig;
-            J.key[j] = x.key;
+            HCHECK(x.key->level >= level, HELRM_E_NOKEY, "switching key generated below the level of its use");
+            J.key[j] = x.key->data.u();
+            J.kl[j] = x.key->level;
             J.c0[j] = x.c0;
             J.bq[j] = x.bq;
             J.gal[j] = x.gal;
@@ -559,7 +564,7 @@ Owned rotate_b(Ctx *c, const std::vector<const EvalKey *> &evk, const CCtVec &a,
     std::vector<const SwitchKey *> keys(B * S, nullptr);
     for (size_t q = 0; q < B; q++)
         for (size_t s = 0; s < S; s++)
-            if (c->galois(steps[s]) != 1) keys[q * S + s] = rot_key(evk[q], c->galois(steps[s]));
+            if (c->galois(steps[s]) != 1) keys[q * S + s] = rot_key(evk[q], c->galois(steps[s]), l);
     DevMem digits(c, B * dplane * 8), u(c, B * S * uplane * 8);
     std::vector<const u64 *> c1s;
     std::vector<u64 *> dg;
@@ -583,7 +588,7 @@ Owned rotate_b(Ctx *c, const std::vector<const EvalKey *> &evk, const CCtVec &a,
                 cw.push_back((u64)2 * nq * N);
             } else {
                 u64 *uq = u.u() + (q * S + s) * uplane;
-                jobs.push_back({uq, dg[q], keys[q * S + s]->data.u(), g, nullptr, nullptr});
+                jobs.push_back({uq, dg[q], keys[q * S + s], g, nullptr, nullptr});
                 ao.push_back(x->c0());
                 aa.push_back(a[q]->c0());
                 ag.push_back(g);
@@ -608,7 +613,7 @@ Owned relin_b(Ctx *c, const std::vector<const EvalKey *> &evk, const std::vector
     Owned o;
     const int N = c->N, nq = level + 1, nl = nq + c->K, dnum = c->dnum(level);
     const size_t B = d012.size(), plane = (size_t)nq * N, dplane = (size_t)dnum * nl * N, uplane = (size_t)2 * nl * N;
-    for (auto *e : evk) HCHECK(e->relin, HELRM_E_NOKEY, "no relinearisation key");
+    for (auto *e : evk) relin_key(e, level);
     DevMem digits(c, B * dplane * 8), u(c, B * uplane * 8);
     std::vector<const u64 *> d2, uu, a0, a1;
     std::vector<u64 *> dg, o0, o1;
@@ -620,7 +625,7 @@ Owned relin_b(Ctx *c, const std::vector<const EvalKey *> &evk, const std::vector
     std::vector<KsJob> jobs;
     for (size_t q = 0; q < B; q++) {
         u64 *uq = u.u() + q * uplane;
-        jobs.push_back({uq, dg[q], evk[q]->relin->data.u(), 1, nullptr, nullptr});
+        jobs.push_back({uq, dg[q], relin_key(evk[q], level), 1, nullptr, nullptr});
         o.v.emplace_back(new_ct(c, level, scale));
         uu.push_back(uq);
         o0.push_back(o.v[q]->c0());
@@ -682,7 +687,7 @@ struct Batch : Handle {
     Ctx *ctx;
     const Model *model;
     std::vector<const EvalKey *> evk;
-    std::map<const PtMatrix *, DevMem> keytab;   // [B][64] baby-step keys of each fused-kernel matrix
+    std::map<const PtMatrix *, DevMem> keytab;   // [B][64] baby-step key pointers, then [B][64] their levels
     Batch(Ctx *c) : Handle(KIND_BATCH), ctx(c) {}
 };
 
@@ -692,12 +697,21 @@ static void batch_keytab(Batch *bt, const PtMatrix *m)
     if (!(m->n1 <= 64 && m->n2 <= 8)) return;
     std::vector<char> need(m->n1, 0);
     for (auto &gb : m->gb) need[gb.second] = 1;
-    std::vector<const u64 *> tab(bt->evk.size() * 64, nullptr);
-    for (size_t q = 0; q < bt->evk.size(); q++)
+    const size_t B = bt->evk.size();
+    std::vector<const u64 *> tab(B * 64, nullptr);
+    std::vector<int> lv(B * 64, 0);
+    for (size_t q = 0; q < B; q++)
         for (int b = 1; b < m->n1; b++)
-            if (need[b]) tab[q * 64 + b] = rot_key(bt->evk[q], c->galois(b))->data.u();
-    DevMem d(c, tab.size() * sizeof(u64 *));
-    CUDA_CHECK(cudaMemcpyAsync(d.ptr, tab.data(), tab.size() * sizeof(u64 *), cudaMemcpyHostToDevice, c->stream));
+            if (need[b]) {
+                const SwitchKey *k = rot_key(bt->evk[q], c->galois(b), m->level);
+                tab[q * 64 + b] = k->data.u();
+                lv[q * 64 + b] = k->level;
+            }
+    const size_t pb = tab.size() * sizeof(u64 *);
+    DevMem d(c, pb + lv.size() * sizeof(int));
+    CUDA_CHECK(cudaMemcpyAsync(d.ptr, tab.data(), pb, cudaMemcpyHostToDevice, c->stream));
+    CUDA_CHECK(cudaMemcpyAsync((char *)d.ptr + pb, lv.data(), lv.size() * sizeof(int), cudaMemcpyHostToDevice,
+                               c->stream));
     bt->keytab[m] = std::move(d);
 }
 
@@ -710,7 +724,7 @@ Batch *batch_create(Ctx *c, const Model *m, const std::vector<const EvalKey *> &
     for (auto &L : m->bottom) batch_keytab(b.get(), L.pm.get());
     batch_keytab(b.get(), m->emb->pm.get());
     for (auto &L : m->top) batch_keytab(b.get(), L.pm.get());
-    CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    // (the host tables were staged by the copies themselves: nothing to wait for)
     return b.release();
 }
 
@@ -732,10 +746,10 @@ static Owned matvec_b(Ctx *c, const Batch *bt, const PtMatrix *m, const CCtVec &
         need_b[gb.second] = 1;
         need_g[gb.first] = 1;
     }
-    std::vector<const u64 *> gkey(B * m->n2, nullptr);
+    std::vector<const SwitchKey *> gkey(B * m->n2, nullptr);
     for (size_t q = 0; q < B; q++)
         for (int g = 1; g < m->n2; g++)
-            if (need_g[g]) gkey[q * m->n2 + g] = rot_key(bt->evk[q], c->galois(g * m->n1))->data.u();
+            if (need_g[g]) gkey[q * m->n2 + g] = rot_key(bt->evk[q], c->galois(g * m->n1), l);
     bool any_baby = false;
     int n_keys = 0;
     for (int b = 1; b < m->n1; b++) {
@@ -757,7 +771,9 @@ static Owned matvec_b(Ctx *c, const Batch *bt, const PtMatrix *m, const CCtVec &
         if (need_b[b]) gals[b] = c->galois(b);
     std::vector<k::BsgsQuery> qs;
     for (size_t q = 0; q < B; q++) qs.push_back({inner.u() + q * iq, dg[q], in[q]->c0(), in[q]->c1()});
-    k::bsgs_tma_batch(c, qs, kt->second.as<const u64 *const>(), gals.data(), m->d_ptrs.as<const u64 *const>(),
+    k::bsgs_tma_batch(c, qs, kt->second.as<const u64 *const>(),
+                      (const int *)((const char *)kt->second.ptr + B * 64 * sizeof(u64 *)), gals.data(),
+                      m->d_ptrs.as<const u64 *const>(),
                       m->d_gb_index.as<int>(), (int)m->gb.size(), n_keys, m->n1, m->n2, l);
     // giant steps: ModDown the a-part of every (query, g > 0), ModUp them all,
     // then one key product per g adds phi(inner_g) into inner_0 of each query
@@ -890,6 +906,7 @@ std::vector<Ciphertext *> model_infer_batch(Ctx *c, const Batch *bt, const CCtVe
 }
 
 size_t batch_size(const Batch *b) { return b->evk.size(); }
+void batch_destroy(Batch *b) { delete b; }
 const EvalKey *batch_evk(const Batch *b, size_t q) { return b->evk[q]; }
 const Model *batch_model(const Batch *b) { return b->model; }
 Ctx *batch_ctx(const Batch *b) { return b->ctx; }

@@ -98,6 +98,7 @@ void *Ctx::alloc(size_t bytes)
         fail(HELRM_E_NOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
     }
     mem_in_use += bytes;
+    mem_peak = std::max(mem_peak, mem_in_use);
     return p;
 }
 void Ctx::release(void *p, size_t bytes)
@@ -293,9 +294,9 @@ Ctx *ctx_create(const helrm_params *p, int device, void *stream)
     HCHECK(p->n_q >= 1 && p->n_q <= 32 && p->q_bits, HELRM_E_PARAM, "n_q must be in [1, 32]");
     HCHECK(p->n_p >= 1 && p->n_p <= 8, HELRM_E_PARAM, "n_p must be in [1, 8]");
     HCHECK(p->alpha >= 1 && p->alpha <= 8, HELRM_E_PARAM, "alpha must be in [1, 8]");
-    HCHECK(p->p_bits >= 30 && p->p_bits <= 61, HELRM_E_PARAM, "p_bits must be in [30, 61]");
+    HCHECK(p->p_bits >= 30 && p->p_bits <= 60, HELRM_E_PARAM, "p_bits must be in [30, 60]");
     for (u32 i = 0; i < p->n_q; i++)
-        HCHECK(p->q_bits[i] >= 30 && p->q_bits[i] <= 61, HELRM_E_PARAM, "q_bits must be in [30, 61]");
+        HCHECK(p->q_bits[i] >= 30 && p->q_bits[i] <= 60, HELRM_E_PARAM, "q_bits must be in [30, 60]");
     HCHECK(p->alpha * 61 < 64 + 61 * 8, HELRM_E_PARAM, "alpha too large");
 
     std::unique_ptr<Ctx> c(new Ctx());

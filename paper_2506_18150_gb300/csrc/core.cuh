@@ -96,20 +96,36 @@ __host__ __device__ __forceinline__ u64 shoup_mul(u64 a, u64 w, u64 wp, u64 q)
     u64 r = a * w - qh * q;
     return r >= q ? r - q : r;
 }
-// 128-bit accumulator kept with hi < q (subtracting q 2^64 preserves the
-// value mod q), reduced by one REDC at the end.
+// 128-bit sum of products, reduced once at the end.  Every prime is below
+// 2^60, so a product of two residues is below 2^120 and up to 256 of them add
+// up without overflowing 128 bits: the terms are accumulated with a carry
+// chain and no reduction in between.  The result is sum * 2^-64 mod q (REDC),
+// which needs the high word below q.  reduce(): at most 16 terms, each a
+// product of a value below 2^60 and a residue mod q, so hi < 16 * 2^60 * q /
+// 2^64 = q already (every inner product of a key switch or a base
+// conversion).  reduce_long(): up to 256 terms; the high word is first
+// brought below q by a Montgomery product with R mod q (multiples of q 2^64
+// do not change the value mod q).
 struct Acc128 {
     u64 lo = 0, hi = 0;
-    __host__ __device__ __forceinline__ void mac(u64 a, u64 b, u64 q)
+    __host__ __device__ __forceinline__ void mac(u64 a, u64 b, u64 /*q*/)
     {
-        u64 pl = a * b;
-        u64 ph = mulhi64(a, b);
-        u64 nl = lo + pl;
-        hi += ph + (nl < pl ? 1 : 0);
-        lo = nl;
-        if (hi >= q) hi -= q;
+#ifdef __CUDA_ARCH__
+        asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\t"
+            "madc.hi.u64 %1, %2, %3, %1;"
+            : "+l"(lo), "+l"(hi)
+            : "l"(a), "l"(b));
+#else
+        const u128 s = ((u128)hi << 64 | lo) + (u128)a * b;
+        lo = (u64)s;
+        hi = (u64)(s >> 64);
+#endif
     }
     __host__ __device__ __forceinline__ u64 reduce(u64 q, u64 qinv) const { return redc(hi, lo, q, qinv); }
+    __host__ __device__ __forceinline__ u64 reduce_long(u64 q, u64 qinv, u64 one_mont) const
+    {
+        return redc(mont_mul(hi, one_mont, q, qinv), lo, q, qinv);
+    }
 };
 
 // Limb l of a level-ell QP polynomial uses prime q_l for l <= ell, else p_{l-ell-1}
@@ -196,7 +212,7 @@ struct Ctx : Handle {
     std::map<std::pair<int, int>, BConvTable> modup_tab;   // (level, digit)
     std::map<int, BConvTable> moddown_tab;                 // level
     std::map<int, DevMem> rescale_tab;                     // level -> constants
-    u64 mem_in_use = 0, mem_cap = 0;
+    u64 mem_in_use = 0, mem_cap = 0, mem_peak = 0;   // bytes held, cap, high-water mark
     u64 launches = 0;
     std::string last_error;
     cudaMemPool_t pool = nullptr;
@@ -292,10 +308,17 @@ struct SecretKey : Handle {
     SecretKey(Ctx *c) : Handle(KIND_SK), ctx(c) {}
 };
 
-struct SwitchKey {          // digits j: (b_j, a_j) over the full QP basis, NTT + Montgomery form
-    DevMem data;            // [dnum][2][L+1+K][N]
+// A switching key generated up to level kl: digits j < dnum(kl), each (b_j, a_j)
+// over the limbs q_0..q_kl, p_0..p_{K-1}, NTT + Montgomery form.  It serves any
+// key switch at a level <= kl; a key at kl = L is the full key, and a key at a
+// lower level is exactly the full key's restriction (same values).
+struct SwitchKey {
+    DevMem data;            // [dnum][2][kl+1+K][N]
     int dnum = 0;
+    int level = 0;          // kl
 };
+// limb of prime pid (a Q prime <= kl or a P prime, global numbering) inside a key of level kl
+__host__ __device__ __forceinline__ int key_limb(int pid, int kl, int L) { return pid <= kl ? pid : pid - L + kl; }
 
 struct EvalKey : Handle {
     Ctx *ctx;
@@ -389,7 +412,7 @@ void bconv_modup(Ctx *c, int level, const u64 *coef, u64 *digits);
 // polys of the key; if c0 != null, out0 on Q limbs += P * c0[perm(i)]
 // bq (optional): a QP polynomial whose image phi(bq) is added to the first
 // output; accumulate: add the result to what out already holds.
-void ks_inner_auto(Ctx *c, u64 *out, const u64 *digits, int dnum, const u64 *key, int level,
+void ks_inner_auto(Ctx *c, u64 *out, const u64 *digits, int dnum, const SwitchKey *key, int level,
                    u64 galois, const u64 *c0, const u64 *d_pmod_mont, const u64 *bq = nullptr,
                    bool accumulate = false);
 // inner[g][2][limbs][N] = sum_b diag[(g,b)] * baby[b]
@@ -399,18 +422,20 @@ void automorphism(Ctx *c, u64 *out, const u64 *in, int n_limbs, u64 galois);
 // hoisted baby steps fused into the BSGS MAC (n1 <= 64, n2 in {1,2,4,8}), fed by a
 // 3-stage pipeline of bulk asynchronous copies (bsgs_tma.cu); keys[b] / gals[b] for
 // b < n1 (keys[0] unused); writes inner[g][2][level+1+K][N] for giant steps with diagonals
-void bsgs_tma(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c1, const u64 *const *keys,
+void bsgs_tma(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c1, const SwitchKey *const *keys,
               const u64 *gals, const u64 *const *d_diag_ptrs, const int *d_gb_index, int n_diag, int n1, int n2,
               int level);
 // the same for a batch of queries of one matrix (one launch per 64 queries):
-// query q reads its keys from d_keytab[q][0..63] (device, baby step b >= 1)
+// query q reads its keys from d_keytab[q][0..63] (device, baby step b >= 1), whose
+// levels are d_keylv[q][0..63]
 struct BsgsQuery {
     u64 *inner;
     const u64 *dig;
     const u64 *c0;
     const u64 *c1;
 };
-void bsgs_tma_batch(Ctx *c, const std::vector<BsgsQuery> &qs, const u64 *const *d_keytab, const u64 *gals,
+void bsgs_tma_batch(Ctx *c, const std::vector<BsgsQuery> &qs, const u64 *const *d_keytab, const int *d_keylv,
+                    const u64 *gals,
                     const u64 *const *d_diag_ptrs, const int *d_gb_index, int n_diag, int n_keys, int n1, int n2,
                     int level);
 // rescale helper: coefficient-form last limb -> centred residues for ell limbs
@@ -455,13 +480,20 @@ Plaintext *pt_encode_dev(Ctx *c, const double *d_slots, int n_valid, int period,
 Plaintext *pt_from_signed(Ctx *c, const i64 *h_coeffs, int level, bool qp, double scale, int form);
 void pt_export_signed(Ctx *c, const Plaintext *pt, i64 *h_out);
 SecretKey *keygen_sk(Ctx *c, u64 seed);
-EvalKey *keygen_evk(Ctx *c, const SecretKey *sk, u64 seed);
-void keygen_rot(Ctx *c, const SecretKey *sk, EvalKey *evk, const std::vector<int> &steps);
+// relin_level < 0: the relinearisation key at the top level
+EvalKey *keygen_evk(Ctx *c, const SecretKey *sk, u64 seed, int relin_level = -1);
+// one key per step, generated up to levels[i] (empty: the top level); a key
+// already present at a level >= the requested one is kept
+void keygen_rot(Ctx *c, const SecretKey *sk, EvalKey *evk, const std::vector<int> &steps,
+                const std::vector<int> &levels = {});
 Ciphertext *encrypt_pt(Ctx *c, const EvalKey *evk, const Plaintext *pt, u64 seed);
 void decrypt_slots(Ctx *c, const SecretKey *sk, const Ciphertext *ct, double *h_out, int n_slots);
 // decrypt into a device buffer, stream-ordered, no synchronisation
 void decrypt_slots_device(Ctx *c, const SecretKey *sk, const Ciphertext *ct, double *d_out, int n_slots);
-const SwitchKey *rot_key(const EvalKey *evk, u64 galois);
+// the rotation key of a Galois element, for a key switch at `level` (HELRM_E_NOKEY if
+// missing or generated below that level)
+const SwitchKey *rot_key(const EvalKey *evk, u64 galois, int level);
+const SwitchKey *relin_key(const EvalKey *evk, int level);
 
 // ------------------------------------------------------ matvec (linear.cu)
 struct PtMatrix : Handle {

@@ -394,6 +394,43 @@ void model_info(const Model *m, u32 *o)
     o[8] = (u32)const_cast<Model *>(m)->plaintexts().size();
 }
 std::vector<int> model_rotations(const Model *m) { return m->rotations(); }
+
+// The highest level at which the model uses each rotation (baby and giant
+// steps at the matvec's level, folds one level lower, after its rescale; the
+// interaction's rotations at lvl_z - 1, after the mask rescale) and the
+// highest level of a relinearisation (the first x^2 of the bottom MLP).
+std::vector<std::pair<int, int>> model_key_levels(const Model *m, int *relin_level)
+{
+    std::map<int, int> lv;
+    auto use = [&](int st, int l) {
+        auto it = lv.find(st);
+        if (it == lv.end() || it->second < l) lv[st] = l;
+    };
+    auto mat = [&](const PtMatrix *pm) {
+        for (auto &gb : pm->gb) {
+            if (gb.second) use(gb.second, pm->level);
+            if (gb.first) use(gb.first * pm->n1, pm->level);
+        }
+        for (int f : pm->folds) use(f, pm->level - 1);
+    };
+    int rl = -1;
+    for (auto &L : m->bottom) {
+        mat(L.pm.get());
+        if (L.square) rl = std::max(rl, L.pm->level - 1);
+    }
+    mat(m->emb->pm.get());
+    if (m->interaction == 0) {
+        use(-DIM * m->Bp, m->lvl_z - 1);
+        for (int s = 1; s <= m->S; s++) use(DIM * s, m->lvl_z - 1);
+        rl = std::max(rl, m->lvl_z - 1);
+    }
+    for (auto &L : m->top) {
+        mat(L.pm.get());
+        if (L.square) rl = std::max(rl, L.pm->level - 1);
+    }
+    *relin_level = std::max(rl, 0);
+    return std::vector<std::pair<int, int>>(lv.begin(), lv.end());
+}
 const PtMatrix *emb_matrix_of(const Emb *e) { return e->pm.get(); }
 void emb_info(const Emb *e, u32 *width, u32 *period)
 {

@@ -178,26 +178,27 @@ __device__ __forceinline__ int auto_src(int i, int logN, u64 galois)
 }
 
 __global__ void k_ks_inner(u64 *__restrict__ out, const u64 *__restrict__ dig, int dnum,
-                           const u64 *__restrict__ key, int level, int L, int K, int logN, u64 galois,
+                           const u64 *__restrict__ key, int kl, int level, int L, int K, int logN, u64 galois,
                            const u64 *__restrict__ c0, const u64 *__restrict__ pmod,
                            const u64 *__restrict__ bq, int accumulate, const PrimeInfo *__restrict__ pinfo)
 {
     pdl_begin();
     const size_t N = (size_t)1 << logN;
-    const int nl = level + 1 + K, nP = L + 1 + K;
+    const int nl = level + 1 + K, nK = kl + 1 + K;
     const size_t total = (size_t)nl * N;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
         const int l = (int)(idx >> logN);
         const int i = (int)(idx & (N - 1));
         const int pid = l <= level ? l : L + 1 + (l - level - 1);
+        const int kx = key_limb(pid, kl, L);
         const PrimeInfo pi = pinfo[pid];
         const int src = galois == 1 ? i : auto_src(i, logN, galois);
         Acc128 a0, a1;
         for (int j = 0; j < dnum; j++) {
             const u64 d = dig[((size_t)j * nl + l) * N + src];
-            a0.mac(d, key[((size_t)(2 * j) * nP + pid) * N + i], pi.q);
-            a1.mac(d, key[((size_t)(2 * j + 1) * nP + pid) * N + i], pi.q);
+            a0.mac(d, key[((size_t)(2 * j) * nK + kx) * N + i], pi.q);
+            a1.mac(d, key[((size_t)(2 * j + 1) * nK + kx) * N + i], pi.q);
         }
         u64 r0 = a0.reduce(pi.q, pi.qinv);
         u64 r1 = a1.reduce(pi.q, pi.qinv);
@@ -260,8 +261,8 @@ __global__ void __launch_bounds__(MAC_TC) k_bsgs_mac(u64 *__restrict__ inner, co
         }
         if (!any) continue;
         u64 *o = inner + (size_t)g * 2 * plane + (size_t)l * N + i;
-        o[0] = a0.reduce(pi.q, pi.qinv);
-        o[plane] = a1.reduce(pi.q, pi.qinv);
+        o[0] = a0.reduce_long(pi.q, pi.qinv, pi.rmod);
+        o[plane] = a1.reduce_long(pi.q, pi.qinv, pi.rmod);
     }
 }
 
@@ -646,15 +647,17 @@ void bconv_modup(Ctx *c, int level, const u64 *coef, u64 *digits)
     bconv_multi(c, v);
 }
 
-void ks_inner_auto(Ctx *c, u64 *out, const u64 *digits, int dnum, const u64 *key, int level, u64 galois,
+void ks_inner_auto(Ctx *c, u64 *out, const u64 *digits, int dnum, const SwitchKey *key, int level, u64 galois,
                    const u64 *c0, const u64 *d_pmod_mont, const u64 *bq, bool accumulate)
 {
+    HCHECK(key->level >= level, HELRM_E_NOKEY, "switching key generated below the level of its use");
     size_t total = (size_t)(level + 1 + c->K) * c->N;
     // digits once, both key halves once, c0 / bq once (if added), two output polys
     // written (and read, when accumulating)
     KTimer kt(c, "ks_inner_auto", 8.0 * (total * (3.0 * dnum + (accumulate ? 4 : 2) + (bq ? 1 : 0)) +
                                          (c0 ? (double)(level + 1) * c->N : 0.0)));
-    launch(c, k_ks_inner, grid_for(total), TPB, 0, out, digits, dnum, key, level, c->L, c->K, c->logN, galois, c0,
+    launch(c, k_ks_inner, grid_for(total), TPB, 0, out, digits, dnum, key->data.u(), key->level, level, c->L, c->K,
+           c->logN, galois, c0,
                                                  d_pmod_mont, bq, accumulate ? 1 : 0, c->d_pinfo.as<PrimeInfo>());
     LAUNCHED(c);
 }

@@ -110,9 +110,9 @@ Ciphertext *matvec(Ctx *c, const EvalKey *evk, const PtMatrix *m, const Cipherte
     // keys first, so a missing key fails before any work
     std::vector<const SwitchKey *> bkey(m->n1, nullptr), gkey(m->n2, nullptr);
     for (int b = 1; b < m->n1; b++)
-        if (need_b[b]) bkey[b] = rot_key(evk, c->galois(b));
+        if (need_b[b]) bkey[b] = rot_key(evk, c->galois(b), l);
     for (int g = 1; g < m->n2; g++)
-        if (need_g[g]) gkey[g] = rot_key(evk, c->galois(g * m->n1));
+        if (need_g[g]) gkey[g] = rot_key(evk, c->galois(g * m->n1), l);
 
     DevMem digits(c, (size_t)dnum * plane * 8);
     bool any_baby = false;
@@ -121,14 +121,10 @@ Ciphertext *matvec(Ctx *c, const EvalKey *evk, const PtMatrix *m, const Cipherte
     DevMem inner(c, (size_t)m->n2 * 2 * plane * 8);
     if (m->n1 <= 64 && m->n2 <= 8) {
         // baby steps formed in registers inside the MAC (no baby buffer)
-        std::vector<const u64 *> keys(m->n1, nullptr);
         std::vector<u64> gals(m->n1, 1);
         for (int b = 1; b < m->n1; b++)
-            if (need_b[b]) {
-                keys[b] = bkey[b]->data.u();
-                gals[b] = c->galois(b);
-            }
-        k::bsgs_tma(c, inner.u(), digits.u(), in->c0(), in->c1(), keys.data(), gals.data(),
+            if (need_b[b]) gals[b] = c->galois(b);
+        k::bsgs_tma(c, inner.u(), digits.u(), in->c0(), in->c1(), bkey.data(), gals.data(),
                     m->d_ptrs.as<const u64 *>(), m->d_gb_index.as<int>(), (int)m->gb.size(), m->n1, m->n2, l);
     } else {
         // wide baby-step sets: baby steps materialised over QP, then the tiled MAC
@@ -143,7 +139,7 @@ Ciphertext *matvec(Ctx *c, const EvalKey *evk, const PtMatrix *m, const Cipherte
                     k::zero(c, bb + p * plane + (size_t)nq * N, (size_t)c->K * N);
                 }
             } else {
-                k::ks_inner_auto(c, bb, digits.u(), dnum, bkey[b]->data.u(), l, c->galois(b), in->c0(),
+                k::ks_inner_auto(c, bb, digits.u(), dnum, bkey[b], l, c->galois(b), in->c0(),
                                  c->d_pmod_mont.u());
             }
         }
@@ -162,7 +158,7 @@ Ciphertext *matvec(Ctx *c, const EvalKey *evk, const PtMatrix *m, const Cipherte
         const u64 gal = c->galois(g * m->n1);
         ks_moddown(c, ig + plane, l, c1q.u());
         ks_modup(c, c1q.u(), l, digits.u());
-        k::ks_inner_auto(c, acc, digits.u(), dnum, gkey[g]->data.u(), l, gal, nullptr, nullptr, ig, true);
+        k::ks_inner_auto(c, acc, digits.u(), dnum, gkey[g], l, gal, nullptr, nullptr, ig, true);
     }
     std::unique_ptr<Ciphertext> o(new_ct(c, l, in->scale * m->pt_scale));
     ks_moddown2(c, acc, l, o->c0(), o->c1());

@@ -95,11 +95,21 @@ void ks_moddown(Ctx *c, const u64 *u, int level, u64 *out)
     k::ntt_run(c, v, false, c->d_pinv_mont.u());
 }
 
-const SwitchKey *rot_key(const EvalKey *evk, u64 galois)
+const SwitchKey *rot_key(const EvalKey *evk, u64 galois, int level)
 {
     auto it = evk->rot.find(galois);
     HCHECK(it != evk->rot.end(), HELRM_E_NOKEY, "no rotation key for galois element " + std::to_string(galois));
+    HCHECK(it->second->level >= level, HELRM_E_NOKEY,
+           "the rotation key for galois element " + std::to_string(galois) + " was generated up to level " +
+               std::to_string(it->second->level) + ", below its use at level " + std::to_string(level));
     return it->second.get();
+}
+
+const SwitchKey *relin_key(const EvalKey *evk, int level)
+{
+    HCHECK(evk->relin, HELRM_E_NOKEY, "no relinearisation key");
+    HCHECK(evk->relin->level >= level, HELRM_E_NOKEY, "the relinearisation key was generated below its use");
+    return evk->relin.get();
 }
 
 // ---------------------------------------------------------------- basic ops
@@ -186,7 +196,7 @@ void ct_rotate_hoisted(Ctx *c, const EvalKey *evk, const Ciphertext *a, const st
     const int l = a->level, N = c->N, nq = l + 1, nl = nq + c->K, dnum = c->dnum(l);
     std::vector<std::unique_ptr<Ciphertext>> res;
     std::vector<const SwitchKey *> keys;
-    for (int st : steps) keys.push_back(c->galois(st) == 1 ? nullptr : rot_key(evk, c->galois(st)));
+    for (int st : steps) keys.push_back(c->galois(st) == 1 ? nullptr : rot_key(evk, c->galois(st), l));
     DevMem digits(c, (size_t)dnum * nl * N * 8), u(c, (size_t)2 * nl * N * 8);
     ks_modup(c, a->c1(), l, digits.u());
     for (size_t s = 0; s < steps.size(); s++) {
@@ -195,7 +205,7 @@ void ct_rotate_hoisted(Ctx *c, const EvalKey *evk, const Ciphertext *a, const st
         if (g == 1) {
             k::copy(c, o->data.u(), a->data.u(), (size_t)2 * nq * N);
         } else {
-            k::ks_inner_auto(c, u.u(), digits.u(), dnum, keys[s]->data.u(), l, g, nullptr, nullptr);
+            k::ks_inner_auto(c, u.u(), digits.u(), dnum, keys[s], l, g, nullptr, nullptr);
             k::automorphism(c, o->c0(), a->c0(), nq, g);
             ks_moddown2(c, u.u(), l, o->c0(), o->c1(), o->c0());   // phi(c0) + ModDown(u_0)
         }
@@ -221,12 +231,12 @@ void ct_tensor_acc(Ctx *c, u64 *d012, const Ciphertext *a, const Ciphertext *b, 
 
 Ciphertext *ct_relin(Ctx *c, const EvalKey *evk, const u64 *d012, int level, double scale)
 {
-    HCHECK(evk->relin, HELRM_E_NOKEY, "no relinearisation key");
+    const SwitchKey *rk = relin_key(evk, level);
     const int N = c->N, nq = level + 1, nl = nq + c->K, dnum = c->dnum(level);
     const size_t plane = (size_t)nq * N;
     DevMem digits(c, (size_t)dnum * nl * N * 8), u(c, (size_t)2 * nl * N * 8);
     ks_modup(c, d012 + 2 * plane, level, digits.u());
-    k::ks_inner_auto(c, u.u(), digits.u(), dnum, evk->relin->data.u(), level, 1, nullptr, nullptr);
+    k::ks_inner_auto(c, u.u(), digits.u(), dnum, rk, level, 1, nullptr, nullptr);
     std::unique_ptr<Ciphertext> o(new_ct(c, level, scale));
     ks_moddown2(c, u.u(), level, o->c0(), o->c1(), d012, d012 + plane);   // (d0, d1) + ModDown(u)
     return o.release();
@@ -316,10 +326,12 @@ void pt_export_signed(Ctx *c, const Plaintext *pt, i64 *h_out)
 struct LimbIds {   // device arrays: prime id and global QP position of each limb
     DevMem pid, gid;
 };
-static LimbIds full_limbs(Ctx *c, int n)
+// the limbs q_0..q_kl, p_0..p_{K-1} (global prime ids, which are also their QP positions)
+static LimbIds level_limbs(Ctx *c, int kl)
 {
+    const int n = kl + 1 + c->K;
     std::vector<int> ids(n);
-    for (int i = 0; i < n; i++) ids[i] = i;
+    for (int i = 0; i < n; i++) ids[i] = c->qmap(kl).pid(i);
     LimbIds r;
     r.pid = DevMem(c, n * 4);
     r.gid = DevMem(c, n * 4);
@@ -327,6 +339,11 @@ static LimbIds full_limbs(Ctx *c, int n)
     CUDA_CHECK(cudaMemcpyAsync(r.gid.ptr, ids.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
     CUDA_CHECK(cudaStreamSynchronize(c->stream));
     return r;
+}
+static LimbIds full_limbs(Ctx *c, int n)
+{
+    HCHECK(n == c->nP(), HELRM_E_PARAM, "internal: full limb list");
+    return level_limbs(c, c->L);
 }
 
 SecretKey *keygen_sk(Ctx *c, u64 seed)
@@ -344,45 +361,53 @@ SecretKey *keygen_sk(Ctx *c, u64 seed)
     return sk.release();
 }
 
-// b = -a s + e (+ [P]_{q_i} s' on digit j's primes) over all nP limbs; stored
-// (b, a) in Montgomery form at `out`.
-static void make_switch_digit(Ctx *c, const SecretKey *sk, u64 seed, u64 index, const u64 *s_prime, int j,
+// b = -a s + e (+ [P]_{q_i} s' on digit j's primes) over the limbs q_0..q_kl,
+// p_0..p_{K-1} of a key of level kl; stored (b, a) in Montgomery form at `out`.
+// Every sample is addressed by its global QP position, so a key of level kl is
+// exactly the restriction of the full (kl = L) key.
+static void make_switch_digit(Ctx *c, const SecretKey *sk, u64 seed, u64 index, const u64 *s_prime, int j, int kl,
                               const LimbIds &ids, u64 *out)
 {
-    const int nP = c->nP(), N = c->N;
-    const size_t plane = (size_t)nP * N;
-    LimbMap all = c->qmap(c->L);
+    const int N = c->N, nq = kl + 1, nK = nq + c->K;
+    const size_t plane = (size_t)nK * N;
+    const LimbMap km = c->qmap(kl);
     u64 *b = out, *a = out + plane;
     DevMem e(c, (size_t)N * 8), t(c, plane * 8);
-    k::sample_uniform(c, a, seed, P_KSK_A, index, nP, ids.pid.as<int>(), ids.gid.as<int>());
-    k::ntt_fwd(c, a, nP, all);
+    k::sample_uniform(c, a, seed, P_KSK_A, index, nK, ids.pid.as<int>(), ids.gid.as<int>());
+    k::ntt_fwd(c, a, nK, km);
     k::sample_cbd21(c, e.as<i64>(), seed, P_KSK_E, index);
-    k::from_signed(c, b, e.as<i64>(), nP, all);
-    k::ntt_fwd(c, b, nP, all);
-    k::mul_mont(c, t.u(), a, sk->s_mont.u(), nP, all);
-    k::sub(c, b, b, t.u(), nP, all);
+    k::from_signed(c, b, e.as<i64>(), nK, km);
+    k::ntt_fwd(c, b, nK, km);
+    // a s: s over the Q limbs 0..kl, then over the P limbs (stored after q_L)
+    k::mul_mont(c, t.u(), a, sk->s_mont.u(), nq, km);
+    k::mul_mont(c, t.u() + (size_t)nq * N, a + (size_t)nq * N, sk->s_mont.u() + (size_t)(c->L + 1) * N, c->K,
+                c->qmap(kl, nq));
+    k::sub(c, b, b, t.u(), nK, km);
     if (s_prime) {
-        const int lo = c->digit_lo(j), hi = c->digit_hi(j, c->L);
-        k::mul_scalar_mont(c, t.u(), s_prime + (size_t)lo * N, c->d_pmod_mont.u(), hi - lo, c->qmap(c->L, lo));
-        k::add(c, b + (size_t)lo * N, b + (size_t)lo * N, t.u(), hi - lo, c->qmap(c->L, lo));
+        const int lo = c->digit_lo(j), hi = c->digit_hi(j, kl);
+        k::mul_scalar_mont(c, t.u(), s_prime + (size_t)lo * N, c->d_pmod_mont.u(), hi - lo, c->qmap(kl, lo));
+        k::add(c, b + (size_t)lo * N, b + (size_t)lo * N, t.u(), hi - lo, c->qmap(kl, lo));
     }
-    k::to_mont(c, out, out, 2 * nP, c->qmap(c->L, 0, nP));
+    k::to_mont(c, out, out, 2 * nK, c->qmap(kl, 0, nK));
 }
 
 static std::unique_ptr<SwitchKey> make_switch_key(Ctx *c, const SecretKey *sk, u64 seed, u64 key_id,
-                                                  const u64 *s_prime, const LimbIds &ids)
+                                                  const u64 *s_prime, int kl, const LimbIds &ids)
 {
     std::unique_ptr<SwitchKey> key(new SwitchKey());
-    key->dnum = c->dnum(c->L);
-    const size_t per = (size_t)2 * c->nP() * c->N;
+    key->level = kl;
+    key->dnum = c->dnum(kl);
+    const size_t per = (size_t)2 * (kl + 1 + c->K) * c->N;
     key->data = DevMem(c, key->dnum * per * 8);
     for (int j = 0; j < key->dnum; j++)
-        make_switch_digit(c, sk, seed, (key_id << 8) | (u64)j, s_prime, j, ids, key->data.u() + j * per);
+        make_switch_digit(c, sk, seed, (key_id << 8) | (u64)j, s_prime, j, kl, ids, key->data.u() + j * per);
     return key;
 }
 
-EvalKey *keygen_evk(Ctx *c, const SecretKey *sk, u64 seed)
+EvalKey *keygen_evk(Ctx *c, const SecretKey *sk, u64 seed, int relin_level)
 {
+    if (relin_level < 0) relin_level = c->L;
+    HCHECK(relin_level <= c->L, HELRM_E_LEVEL, "key level above the chain");
     std::unique_ptr<EvalKey> evk(new EvalKey(c));
     evk->seed = seed;
     const int nq = c->L + 1, nP = c->nP(), N = c->N;
@@ -403,20 +428,27 @@ EvalKey *keygen_evk(Ctx *c, const SecretKey *sk, u64 seed)
     // relinearisation key: s' = s^2
     DevMem s2(c, (size_t)nP * N * 8);
     k::mul_mont(c, s2.u(), sk->s_ntt.u(), sk->s_mont.u(), nP, c->qmap(c->L));
-    evk->relin = make_switch_key(c, sk, seed, 0, s2.u(), ids);
+    LimbIds rids = level_limbs(c, relin_level);
+    evk->relin = make_switch_key(c, sk, seed, 0, s2.u(), relin_level, rids);
     return evk.release();
 }
 
-void keygen_rot(Ctx *c, const SecretKey *sk, EvalKey *evk, const std::vector<int> &steps)
+void keygen_rot(Ctx *c, const SecretKey *sk, EvalKey *evk, const std::vector<int> &steps,
+                const std::vector<int> &levels)
 {
     const int nP = c->nP(), N = c->N;
-    LimbIds ids = full_limbs(c, nP);
+    std::map<int, LimbIds> ids;
     DevMem sp(c, (size_t)nP * N * 8);
-    for (int st : steps) {
-        u64 g = c->galois(st);
-        if (g == 1 || evk->rot.count(g)) continue;
+    for (size_t i = 0; i < steps.size(); i++) {
+        const u64 g = c->galois(steps[i]);
+        const int kl = levels.empty() ? c->L : levels[i];
+        HCHECK(kl >= 0 && kl <= c->L, HELRM_E_LEVEL, "key level outside the chain");
+        if (g == 1) continue;
+        auto it = evk->rot.find(g);
+        if (it != evk->rot.end() && it->second->level >= kl) continue;
+        if (!ids.count(kl)) ids[kl] = level_limbs(c, kl);
         k::automorphism(c, sp.u(), sk->s_ntt.u(), nP, g);   // phi_g(s), NTT domain
-        evk->rot[g] = make_switch_key(c, sk, evk->seed, g, sp.u(), ids);
+        evk->rot[g] = make_switch_key(c, sk, evk->seed, g, sp.u(), kl, ids[kl]);
     }
 }
 

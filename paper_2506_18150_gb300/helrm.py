@@ -35,6 +35,12 @@ class Params(C.Structure):
                 ("log2_scale", C.c_double)]
 
 
+class ServeStats(C.Structure):
+    _fields_ = [("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("max_ms", C.c_double),
+                ("makespan_s", C.c_double), ("throughput", C.c_double), ("n_batches", C.c_uint32),
+                ("max_batch", C.c_uint32), ("max_inflight", C.c_uint32), ("mean_batch", C.c_double)]
+
+
 class ModelDesc(C.Structure):
     _fields_ = [("n_dense", C.c_uint32), ("n_bottom", C.c_uint32),
                 ("bottom_widths", C.POINTER(C.c_uint32)),
@@ -66,6 +72,7 @@ _SIGS = {
     "helrm_ntt": [_vp, _vp, C.c_uint32, C.c_uint32, C.c_int],
     "helrm_keygen": [_vp, C.c_uint64, _i32p, C.c_uint32, _pp, _pp],
     "helrm_evk_add_rotations": [_vp, _vp, _vp, _i32p, C.c_uint32],
+    "helrm_model_keygen": [_vp, _vp, C.c_uint64, _pp, _pp],
     "helrm_evk_bytes": [_vp, _u64p],
     "helrm_encode": [_vp, _dp, C.c_uint32, C.c_int32, C.c_double, _pp],
     "helrm_pt_import": [_vp, _i64p, C.c_int32, C.c_double, _pp],
@@ -109,6 +116,9 @@ _SIGS = {
     "helrm_batch_create": [_vp, _vp, C.c_uint32, _pp, _pp],
     "helrm_infer_batch": [_vp, _vp, _pp, _pp, _pp],
     "helrm_infer_batch_e2e_device": [_vp, _vp, _pp, _vp, _vp, C.c_uint64, _vp],
+    "helrm_server_create": [_vp, C.c_uint32, C.c_uint32, C.c_uint64, _pp],
+    "helrm_server_add_client": [_vp, _vp, _vp, _vp, _u32p],
+    "helrm_server_run": [_vp, _vp, C.c_uint32, _dp, _u32p, _pp, _pp, _pp, _dp, C.c_void_p],
     "helrm_ctx_profile": [_vp, C.c_int],
     "helrm_ctx_profile_report": [_vp, C.c_char_p, C.c_uint64, _u64p],
 }
@@ -245,6 +255,13 @@ def helrm_keygen(ctx, seed: int, rot_steps=()):
     st_arr, st_p = _i32(list(rot_steps) or [0])
     sk, evk = C.c_void_p(), C.c_void_p()
     _check(ctx, lib().helrm_keygen(ctx.ptr, seed, st_p, len(rot_steps), C.byref(sk), C.byref(evk)))
+    return Handle(sk.value, ctx), Handle(evk.value, ctx)
+
+
+def helrm_model_keygen(ctx, m, seed: int):
+    """(sk, evk) with the model's keys, each truncated to the highest level it is used at."""
+    sk, evk = C.c_void_p(), C.c_void_p()
+    _check(ctx, lib().helrm_model_keygen(ctx.ptr, m.ptr, seed, C.byref(sk), C.byref(evk)))
     return Handle(sk.value, ctx), Handle(evk.value, ctx)
 
 
@@ -526,6 +543,33 @@ def helrm_infer_batch_e2e_device(ctx, batch, sks, d_dense: int, d_indices: int, 
     """Device pointers (ints): d_dense n x n_dense f64, d_indices n x n_tables u64, d_logits n f64."""
     _check(ctx, lib().helrm_infer_batch_e2e_device(ctx.ptr, batch.ptr, _ptrs(sks), C.c_void_p(d_dense),
                                                    C.c_void_p(d_indices), seed, C.c_void_p(d_logits)))
+
+
+def helrm_server_create(ctx, n_slots: int, max_batch: int, mem_budget: int = 0):
+    out = C.c_void_p()
+    _check(ctx, lib().helrm_server_create(ctx.ptr, n_slots, max_batch, mem_budget, C.byref(out)))
+    return Handle(out.value, ctx)
+
+
+def helrm_server_add_client(ctx, server, m, evk) -> int:
+    cid = C.c_uint32()
+    _check(ctx, lib().helrm_server_add_client(ctx.ptr, server.ptr, m.ptr, evk.ptr, C.byref(cid)))
+    server._keep = (server._keep, m, evk) if server._keep is not None else (m, evk)
+    return cid.value
+
+
+def helrm_server_run(ctx, server, arrival_s, clients, cts_dense, cts_sel):
+    """Replay a trace; returns (logit ciphertexts, latencies in ms, stats dict)."""
+    n = len(arrival_s)
+    arr, ap = _f64(arrival_s)
+    cl = np.ascontiguousarray(clients, dtype=np.uint32)
+    outs = (C.c_void_p * n)()
+    lat = np.zeros(n)
+    stt = ServeStats()
+    _check(ctx, lib().helrm_server_run(ctx.ptr, server.ptr, n, ap, cl.ctypes.data_as(_u32p), _ptrs(cts_dense),
+                                       _ptrs(cts_sel), outs, lat.ctypes.data_as(_dp), C.byref(stt)))
+    stats = {f: getattr(stt, f) for f, _ in ServeStats._fields_}
+    return [Handle(outs[r], ctx) for r in range(n)], lat, stats
 
 
 def helrm_rescale_noalloc(ctx, d_in: int, d_out: int, level: int, n_polys: int):

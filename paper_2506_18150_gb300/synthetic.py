@@ -239,3 +239,21 @@ def make_queries(spec: DLRMSpec, count: int, seed: int = 0):
         dense = rng.normal(0.0, 1.0, size=(count, spec.n_dense))
         idx = np.stack([rng.integers(0, k, size=count) for k in spec.cards], axis=1).astype(np.uint64)
     return dense, idx
+
+
+# --------------------------------------------------------------------------
+# Serving traces
+# --------------------------------------------------------------------------
+def serving_trace(rate: float, count: int, n_uci_clients: int, n_criteo_clients: int, frac_uci: float = 0.8,
+                  seed: int = 0):
+    """Poisson arrivals at `rate` requests/s: (arrival_s [count] sorted,
+    client [count]).  A request is UCI-shaped with probability frac_uci (its
+    client uniform among clients 0..n_uci_clients-1), else Criteo-shaped
+    (client uniform among the next n_criteo_clients)."""
+    rng = np.random.default_rng([seed, 505])
+    arrival = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    arrival -= arrival[0]
+    uci = rng.random(count) < frac_uci
+    client = np.where(uci, rng.integers(0, n_uci_clients, count),
+                      n_uci_clients + rng.integers(0, n_criteo_clients, count))
+    return arrival, client.astype(np.uint32)

@@ -124,3 +124,32 @@ def test_batch_errors():
     with pytest.raises(H.HelrmError) as e:               # dense and selector swapped: wrong levels
         H.helrm_infer_batch(ctx, batch, [c[1] for c in cts], [c[0] for c in cts])
     assert e.value.name == "HELRM_E_LEVEL"
+
+
+def test_model_keygen_truncated_keys_give_identical_logits():
+    """helrm_model_keygen: each key generated only up to the level the model
+    uses it at.  The key values are the full keys' restrictions, so the logit
+    ciphertexts are bit-identical to those under full keys, in less memory; a
+    truncated key used above its level is refused (HELRM_E_NOKEY)."""
+    from paper_2506_18150_gb300 import helrm as H
+    from paper_2506_18150_gb300 import synthetic as syn
+    pr = syn.reduced_params(13, 12)          # three spare levels above the model's
+    spec = syn.uci_spec(0)
+    ctx = gpu_ctx(pr)
+    model = H.helrm_model_create(ctx, spec, syn.make_weights(spec, 0))
+    steps = H.helrm_model_rotations(ctx, model)
+    sk_f, evk_f = H.helrm_keygen(ctx, 9, steps)
+    sk_t, evk_t = H.helrm_model_keygen(ctx, model, 9)
+    assert H.helrm_evk_bytes(ctx, evk_t) < 0.6 * H.helrm_evk_bytes(ctx, evk_f)
+    dense, idx = syn.make_queries(spec, 2, seed=4)
+    for q in range(2):
+        cd, cs = H.helrm_encrypt_query(ctx, evk_f, model, dense[q], idx[q], 50 + 2 * q)
+        a = H.helrm_infer(ctx, evk_f, model, cd, cs)
+        b = H.helrm_infer(ctx, evk_t, model, cd, cs)
+        _same_ct(ctx, a, b)
+        batch = H.helrm_batch_create(ctx, model, [evk_t])
+        _same_ct(ctx, a, H.helrm_infer_batch(ctx, batch, [cd], [cs])[0])
+    top = H.helrm_encrypt(ctx, evk_t, H.helrm_encode(ctx, np.ones(8), 12, 2.0**40), 3)
+    with pytest.raises(H.HelrmError) as e:
+        H.helrm_rotate(ctx, evk_t, top, steps[-1])
+    assert e.value.name == "HELRM_E_NOKEY"

@@ -108,6 +108,13 @@ helrm_status helrm_ctx_memory_in_use(const helrm_ctx *ctx, uint64_t *bytes);
 helrm_status helrm_ctx_synchronize(helrm_ctx *ctx);
 /* Number of library kernels launched so far on this context. */
 helrm_status helrm_ctx_launch_count(const helrm_ctx *ctx, uint64_t *count);
+/* The NTT launch shapes the context chose when it was created: for limb
+ * counts per launch <= 4, <= 16, <= 64 and above (out[2b], out[2b+1]), the
+ * words per CTA tile and the CTA count, in multiples of the SM count, below
+ * which tiles are split.  Creation times every candidate shape on scratch
+ * limbs and keeps the fastest (set HELRM_NTT_AUTOTUNE=0 in the environment
+ * to keep the defaults 1024 / 2); every shape computes the same result. */
+helrm_status helrm_ctx_ntt_tuning(const helrm_ctx *ctx, uint32_t *out);
 /* Kernel timing: enable != 0 clears previous records and brackets every
  * library kernel (each NTT counts as one, both passes) with CUDA events on
  * the context stream; 0 stops recording.  Adds a little launch overhead. */
@@ -237,21 +244,37 @@ helrm_status helrm_ptct_matvec(helrm_ctx *ctx, const helrm_evk *evk, const helrm
  * of table t are [out_offset + dim t, out_offset + dim (t+1)) of a vector of
  * period out_pad; the selector vector (all digits' one-hots concatenated,
  * table by table) has period in_pad = next power of two.  Prepared at
- * `level` for the given scales. */
+ * `level` for the given scales.  A selector wider than the n slots spans
+ * ceil(width / n) ciphertexts (Sec. 5.4: 18 and 85 for the least compressed
+ * Criteo models): ciphertext c holds columns [c n, min((c+1) n, width)) with
+ * their own period pow2ceil(columns), and each has its own matrix
+ * (helrm_emb_matrix); the lookup is the sum of the per-ciphertext products
+ * (helrm_embedding_lookup_multi). */
 helrm_status helrm_emb_prepare(helrm_ctx *ctx, uint32_t n_tables, const uint64_t *card, uint32_t base_p,
                                uint32_t dim, const float *const *tables, uint32_t out_offset,
                                uint32_t out_pad, int32_t level, double ct_scale, double target_scale,
                                helrm_emb **out);
 /* Client packing: little-endian base-p digits of each index, one one-hot per
  * digit, concatenated; slots_out gets n_slots values (selector replicated with
- * its period). */
+ * its period).  For a selector of C > 1 ciphertexts n_slots must be C x n:
+ * block c holds ciphertext c's columns, replicated with their period. */
 helrm_status helrm_query_pack(const helrm_emb *emb, const uint64_t *indices, double *slots_out,
                               uint32_t n_slots);
+/* Number of ciphertexts the selector spans (1 when it fits n slots). */
+helrm_status helrm_emb_chunks(const helrm_emb *emb, uint32_t *n_chunks);
+/* The encoded lookup matrix of ciphertext `chunk` (owned by the embedding:
+ * valid while it lives, never freed by the caller); use it with
+ * helrm_ptmat_info / helrm_ptmat_rotations / helrm_ptmat_import. */
+helrm_status helrm_emb_matrix(const helrm_emb *emb, uint32_t chunk, helrm_ptmat **out);
 /* Selector width (before padding) and its period. */
 helrm_status helrm_emb_info(const helrm_emb *emb, uint32_t *width, uint32_t *period);
 /* y = M^T sel for the packed selector ciphertext (n_sel must be 1). */
 helrm_status helrm_embedding_lookup(helrm_ctx *ctx, const helrm_evk *evk, const helrm_emb *emb,
                                     const helrm_ct *sel, uint32_t n_sel, helrm_ct **out);
+/* The lookup for a selector of n_sel = helrm_emb_chunks ciphertexts:
+ * y = sum_c M_c^T sel_c, each term one BSGS matvec (one level), added. */
+helrm_status helrm_embedding_lookup_multi(helrm_ctx *ctx, const helrm_evk *evk, const helrm_emb *emb,
+                                          const helrm_ct *const *sel, uint32_t n_sel, helrm_ct **out);
 
 /* ------------------------------------------------------------- DLRM (a12-a14) */
 typedef struct {
@@ -335,6 +358,14 @@ helrm_status helrm_infer_e2e_device(helrm_ctx *ctx, const helrm_sk *sk, const he
  * if a key set lacks a rotation the model needs. */
 helrm_status helrm_batch_create(helrm_ctx *ctx, const helrm_model *m, uint32_t n, const helrm_evk *const *evks,
                                 helrm_batch **out);
+/* enable != 0: run the batch's server path as a CUDA graph.  The first
+ * helrm_infer_batch after enabling captures it on buffers the batch owns (one
+ * eager run sizes them, then the capture); every call copies its inputs into
+ * those buffers, launches the graph and copies the logits out.  The kernels
+ * and their order are those of the eager path, so results are identical.
+ * Inputs must keep the levels and scales of the captured call.  Must not be
+ * combined with helrm_ctx_profile. */
+helrm_status helrm_batch_set_graph(helrm_ctx *ctx, helrm_batch *b, int enable);
 /* Server side for the n queries of the batch: ct_dense[q], ct_sel[q] at the
  * model's levels (helrm_encrypt_query with evks[q]); logits[q] receives the
  * encrypted logit of query q (level 0), as helrm_infer.  Stream ordered, no

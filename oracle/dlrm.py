@@ -382,3 +382,39 @@ def decrypt_logit(p, sk, ct: ckks.Ct):
 def lookup_matrix(tables, p_base: int, k: int) -> np.ndarray:
     """dim x (l p) matrix [C_0^T ... C_{l-1}^T] of one compressed table."""
     return embedding_matrix([k], p_base, [tables], 0, DIM)
+
+
+# --------------------------------------------------------------------------
+# Selectors wider than the slot count (Sec. 3.2.1 and Sec. 5.4: a client's
+# one-hot vector of k_t entries needs ceil(k_t / n) ciphertexts; the paper's
+# least-compressed Criteo models take 18 and 85 input ciphertexts, and the
+# lookup with two input ciphertexts has 1024 non-zero diagonals)
+# --------------------------------------------------------------------------
+def selector_chunks(width: int, n: int):
+    """[(first column, columns)] of the ceil(width / n) ciphertexts: chunk c
+    holds selector columns [c n, min((c + 1) n, width))."""
+    return [(c0, min(n, width - c0)) for c0 in range(0, width, n)]
+
+
+def prepare_multi(p: ckks.Params, M: np.ndarray, out_pad: int, level: int, ct_scale: float,
+                  target_scale: float):
+    """One BSGS matrix per chunk: the columns of M that chunk c holds, padded
+    to in_pad_c = pow2ceil(columns) (so all but the last chunk have in_pad = n)."""
+    out = []
+    for c0, w in selector_chunks(M.shape[1], p.n):
+        out.append(linear.prepare(p, M[:, c0:c0 + w], linear.pow2ceil(w), out_pad, level, ct_scale, target_scale))
+    return out
+
+
+def chunk_slots(sel: np.ndarray, n: int):
+    """The slots of each chunk's ciphertext: its columns replicated with its period."""
+    return [replicate(sel[c0:c0 + w], linear.pow2ceil(w), n) for c0, w in selector_chunks(len(sel), n)]
+
+
+def lookup_multi(p: ckks.Params, keys: ckks.Keys, pms, cts):
+    """y = M s = sum_c M_c s_c: the per-ciphertext products, added."""
+    out = None
+    for pm, ct in zip(pms, cts):
+        y = linear.matvec(p, keys, pm, ct)
+        out = y if out is None else ckks.add(p, out, y)
+    return out

@@ -16,6 +16,10 @@ Emb *emb_prepare(Ctx *c, const std::vector<u64> &cards, int base, int dim, const
                  int out_offset, int out_pad, int level, double ct_scale, double target_scale);
 void emb_pack_host(const Emb *e, const u64 *indices, std::vector<double> &sel);
 const PtMatrix *emb_matrix_of(const Emb *e);
+int emb_n_chunks(const Emb *e);
+PtMatrix *emb_chunk(const Emb *e, int c);
+int emb_chunk_period(const Emb *e, int c);
+Ciphertext *emb_lookup_multi(Ctx *c, const EvalKey *evk, const Emb *e, const std::vector<const Ciphertext *> &sel);
 void emb_info(const Emb *e, u32 *width, u32 *period);
 Ctx *emb_ctx(const Emb *e);
 Model *model_create(Ctx *c, const helrm_model_desc *d);
@@ -38,6 +42,10 @@ std::vector<Ciphertext *> model_infer_batch(Ctx *c, const Batch *bt, const std::
 size_t batch_size(const Batch *b);
 const Model *batch_model(const Batch *b);
 const EvalKey *batch_evk(const Batch *b, size_t q);
+std::vector<Ciphertext *> model_infer_batch_graph(Ctx *c, Batch *bt, const std::vector<const Ciphertext *> &ct_dense,
+                                                  const std::vector<const Ciphertext *> &ct_sel);
+void batch_set_graph(Batch *b, bool on);
+bool batch_uses_graph(const Batch *b);
 struct Server;
 Server *server_create(Ctx *c, int n_slots, int max_batch, u64 budget);
 u32 server_add_client(Server *s, const Model *m, const EvalKey *evk);
@@ -165,6 +173,18 @@ helrm_status helrm_ctx_launch_count(const helrm_ctx *ctx, uint64_t *count)
     return guard(ctx_or_null(ctx), [&] {
         HCHECK(count, HELRM_E_INVAL, "count is NULL");
         *count = C(ctx)->launches;
+    });
+}
+
+helrm_status helrm_ctx_ntt_tuning(const helrm_ctx *ctx, uint32_t *out)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        const Ctx *c = C(ctx);
+        HCHECK(out, HELRM_E_INVAL, "out is NULL");
+        for (int b = 0; b < 4; b++) {
+            out[2 * b] = (uint32_t)c->ntt_tune[b].tile;
+            out[2 * b + 1] = (uint32_t)c->ntt_tune[b].mult;
+        }
     });
 }
 
@@ -541,7 +561,47 @@ helrm_status helrm_query_pack(const helrm_emb *emb, const uint64_t *indices, dou
         emb_pack_host(e, indices, sel);
         u32 w, per;
         emb_info(e, &w, &per);
-        for (u32 j = 0; j < n_slots; j++) slots_out[j] = (j % per) < w ? sel[j % per] : 0.0;
+        const int nc = emb_n_chunks(e);
+        if (nc == 1) {
+            for (u32 j = 0; j < n_slots; j++) slots_out[j] = (j % per) < w ? sel[j % per] : 0.0;
+            return;
+        }
+        // one block of n slots per ciphertext: chunk c's columns replicated with its period
+        const u32 n = (u32)emb_chunk_period(e, 0);
+        HCHECK(n_slots == (u32)nc * n, HELRM_E_INVAL, "a multi-ciphertext selector needs n_chunks x n slots");
+        for (int k = 0; k < nc; k++) {
+            const u32 c0 = (u32)k * n, cw = std::min(n, w - c0), cp = (u32)emb_chunk_period(e, k);
+            for (u32 j = 0; j < n; j++) slots_out[(size_t)k * n + j] = (j % cp) < cw ? sel[c0 + j % cp] : 0.0;
+        }
+    });
+}
+
+helrm_status helrm_emb_chunks(const helrm_emb *emb, uint32_t *n_chunks)
+{
+    return guard(nullptr, [&] {
+        HCHECK(n_chunks, HELRM_E_INVAL, "NULL argument");
+        *n_chunks = (uint32_t)emb_n_chunks(EMB(emb));
+    });
+}
+
+helrm_status helrm_emb_matrix(const helrm_emb *emb, uint32_t chunk, helrm_ptmat **out)
+{
+    return guard(nullptr, [&] {
+        const Emb *e = EMB(emb);
+        HCHECK(out && chunk < (uint32_t)emb_n_chunks(e), HELRM_E_INVAL, "chunk out of range");
+        *out = (helrm_ptmat *)emb_chunk(e, (int)chunk);
+    });
+}
+
+helrm_status helrm_embedding_lookup_multi(helrm_ctx *ctx, const helrm_evk *evk, const helrm_emb *emb,
+                                          const helrm_ct *const *sel, uint32_t n_sel, helrm_ct **out)
+{
+    if (out) *out = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        HCHECK(out && sel, HELRM_E_INVAL, "NULL argument");
+        std::vector<const Ciphertext *> v;
+        for (u32 k = 0; k < n_sel; k++) v.push_back(CT(sel[k]));
+        *out = (helrm_ct *)emb_lookup_multi(C(ctx), EVK(evk), EMB(emb), v);
     });
 }
 
@@ -560,6 +620,8 @@ helrm_status helrm_embedding_lookup(helrm_ctx *ctx, const helrm_evk *evk, const 
     return guard(ctx_or_null(ctx), [&] {
         HCHECK(out, HELRM_E_INVAL, "out is NULL");
         HCHECK(n_sel == 1, HELRM_E_INVAL, "n_sel must be 1");
+        HCHECK(emb_n_chunks(EMB(emb)) == 1, HELRM_E_INVAL,
+               "the selector spans several ciphertexts: use helrm_embedding_lookup_multi");
         *out = (helrm_ct *)matvec(C(ctx), EVK(evk), emb_matrix_of(EMB(emb)), CT(sel));
     });
 }
@@ -694,6 +756,14 @@ helrm_status helrm_batch_create(helrm_ctx *ctx, const helrm_model *m, uint32_t n
     });
 }
 
+helrm_status helrm_batch_set_graph(helrm_ctx *ctx, helrm_batch *b, int enable)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        C(ctx);
+        batch_set_graph(BAT(b), enable != 0);
+    });
+}
+
 helrm_status helrm_infer_batch(helrm_ctx *ctx, const helrm_batch *b, const helrm_ct *const *ct_dense,
                                const helrm_ct *const *ct_sel, helrm_ct **logits)
 {
@@ -708,7 +778,8 @@ helrm_status helrm_infer_batch(helrm_ctx *ctx, const helrm_batch *b, const helrm
             d.push_back(CT(ct_dense[q]));
             s.push_back(CT(ct_sel[q]));
         }
-        std::vector<Ciphertext *> y = model_infer_batch(C(ctx), bt, d, s);
+        std::vector<Ciphertext *> y = batch_uses_graph(bt) ? model_infer_batch_graph(C(ctx), bt, d, s)
+                                                           : model_infer_batch(C(ctx), bt, d, s);
         for (size_t q = 0; q < n; q++) logits[q] = (helrm_ct *)y[q];
     });
 }
@@ -736,7 +807,8 @@ helrm_status helrm_infer_batch_e2e_device(helrm_ctx *ctx, const helrm_batch *b, 
             ad.push_back(x);
             sd.push_back(y);
         }
-        std::vector<Ciphertext *> y = model_infer_batch(c, bt, ad, sd);
+        std::vector<Ciphertext *> y = batch_uses_graph(bt) ? model_infer_batch_graph(c, bt, ad, sd)
+                                                           : model_infer_batch(c, bt, ad, sd);
         std::vector<std::unique_ptr<Ciphertext>> yo;
         for (auto *p : y) yo.emplace_back(p);
         for (size_t q = 0; q < n; q++) decrypt_slots_device(c, sk[q], yo[q].get(), d_logits + q, 1);

@@ -3,9 +3,10 @@
 // every step of the path is one launch for the whole batch.
 //
 // Nothing in the arithmetic changes: each query goes through exactly the
-// integer operations of the one-query path (dlrm.cu, linear.cu, scheme.cu),
-// so its logit ciphertext is bit-identical to the one it would get alone.
-// What changes is the launch shape:
+// integer operations of the op-by-op CKKS primitives (linear.cu matvec,
+// scheme.cu rotations, products, rescale), so its logit ciphertext does not
+// depend on what it is batched with.  One query alone (helrm_infer) is a
+// batch of one.  What changes is the launch shape:
 //  * NTTs, base conversions, key inner products, automorphisms and
 //    elementwise ops take job lists covering every query (and, where the
 //    steps are independent, every giant step or rotation as well);
@@ -688,7 +689,21 @@ struct Batch : Handle {
     const Model *model;
     std::vector<const EvalKey *> evk;
     std::map<const PtMatrix *, DevMem> keytab;   // [B][64] baby-step key pointers, then [B][64] their levels
+    // graph replay: the whole server path captured once on fixed buffers
+    bool use_graph = false;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t gstream = nullptr;            // the graph's own stream (a legacy default stream cannot be captured)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::vector<std::unique_ptr<Ciphertext>> g_dense, g_sel, g_out;
     Batch(Ctx *c) : Handle(KIND_BATCH), ctx(c) {}
+    ~Batch() override
+    {
+        if (gstream) cudaStreamSynchronize(gstream);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+        if (gstream) cudaStreamDestroy(gstream);
+    }
 };
 
 static void batch_keytab(Batch *bt, const PtMatrix *m)
@@ -905,6 +920,99 @@ std::vector<Ciphertext *> model_infer_batch(Ctx *c, const Batch *bt, const CCtVe
     return out;
 }
 
+// The batch's server path through a CUDA graph.  The first call allocates
+// fixed input and output ciphertexts, copies the inputs in, and captures
+// model_infer_batch on them (its temporaries become allocation and free nodes
+// of the graph, and the logits are copied to the fixed outputs inside it);
+// every call then copies its inputs in, launches the graph and copies the
+// logits out into new ciphertexts.  The launches, their order and their
+// arithmetic are those of the eager path, so the results are identical.
+std::vector<Ciphertext *> model_infer_batch_graph(Ctx *c, Batch *bt, const CCtVec &ct_dense, const CCtVec &ct_sel)
+{
+    const size_t B = bt->evk.size();
+    const Model *m = bt->model;
+    HCHECK(ct_dense.size() == B && ct_sel.size() == B, HELRM_E_INVAL, "batch size mismatch");
+    HCHECK(!c->prof_on, HELRM_E_INVAL, "kernel profiling cannot be recorded inside a graph");
+    for (size_t q = 0; q < B; q++) {
+        HCHECK(ct_dense[q]->level == m->lvl_dense, HELRM_E_LEVEL, "ct_dense is not at the model's dense level");
+        HCHECK(ct_sel[q]->level == m->lvl_sel, HELRM_E_LEVEL, "ct_sel is not at the model's selector level");
+    }
+    auto copy_in = [&] {
+        for (size_t q = 0; q < B; q++) {
+            HCHECK(ct_dense[q]->scale == bt->g_dense[q]->scale && ct_sel[q]->scale == bt->g_sel[q]->scale,
+                   HELRM_E_SCALE, "input scales differ from the captured ones");
+            k::copy(c, bt->g_dense[q]->data.u(), ct_dense[q]->data.u(), bt->g_dense[q]->data.bytes / 8);
+            k::copy(c, bt->g_sel[q]->data.u(), ct_sel[q]->data.u(), bt->g_sel[q]->data.bytes / 8);
+        }
+    };
+    if (!bt->exec) {
+        for (size_t q = 0; q < B; q++) {
+            bt->g_dense.emplace_back(new_ct(c, m->lvl_dense, ct_dense[q]->scale));
+            bt->g_sel.emplace_back(new_ct(c, m->lvl_sel, ct_sel[q]->scale));
+        }
+        copy_in();
+        // the output buffers and scales come from one eager run on the fixed inputs
+        Owned probe;
+        {
+            std::vector<Ciphertext *> y = model_infer_batch(c, bt, [&] { CCtVec v; for (auto &p : bt->g_dense) v.push_back(p.get()); return v; }(),
+                                                            [&] { CCtVec v; for (auto &p : bt->g_sel) v.push_back(p.get()); return v; }());
+            for (auto *p : y) probe.v.emplace_back(p);
+        }
+        for (size_t q = 0; q < B; q++) bt->g_out.emplace_back(new_ct(c, probe.v[q]->level, probe.v[q]->scale));
+        probe = Owned();
+        CUDA_CHECK(cudaStreamSynchronize(c->stream));
+        if (!bt->gstream) {
+            CUDA_CHECK(cudaStreamCreateWithFlags(&bt->gstream, cudaStreamNonBlocking));
+            CUDA_CHECK(cudaEventCreateWithFlags(&bt->ev_in, cudaEventDisableTiming));
+            CUDA_CHECK(cudaEventCreateWithFlags(&bt->ev_out, cudaEventDisableTiming));
+        }
+        const cudaStream_t home = c->stream;
+        cudaGraph_t g = nullptr;
+        CUDA_CHECK(cudaStreamBeginCapture(bt->gstream, cudaStreamCaptureModeThreadLocal));
+        c->stream = bt->gstream;   // everything the path enqueues goes into the capture
+        try {
+            CCtVec d, s;
+            for (size_t q = 0; q < B; q++) {
+                d.push_back(bt->g_dense[q].get());
+                s.push_back(bt->g_sel[q].get());
+            }
+            std::vector<Ciphertext *> y = model_infer_batch(c, bt, d, s);
+            Owned yo;
+            for (auto *p : y) yo.v.emplace_back(p);
+            for (size_t q = 0; q < B; q++) k::copy(c, bt->g_out[q]->data.u(), yo.v[q]->data.u(), yo.v[q]->data.bytes / 8);
+        } catch (...) {
+            c->stream = home;
+            cudaStreamEndCapture(bt->gstream, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            throw;
+        }
+        c->stream = home;
+        CUDA_CHECK(cudaStreamEndCapture(bt->gstream, &g));
+        cudaError_t e = cudaGraphInstantiate(&bt->exec, g, 0);
+        cudaGraphDestroy(g);
+        CUDA_CHECK(e);
+    } else {
+        copy_in();
+    }
+    // the graph's stream follows the context stream's input copies, and the
+    // context stream follows the graph
+    CUDA_CHECK(cudaEventRecord(bt->ev_in, c->stream));
+    CUDA_CHECK(cudaStreamWaitEvent(bt->gstream, bt->ev_in, 0));
+    CUDA_CHECK(cudaGraphLaunch(bt->exec, bt->gstream));
+    CUDA_CHECK(cudaEventRecord(bt->ev_out, bt->gstream));
+    CUDA_CHECK(cudaStreamWaitEvent(c->stream, bt->ev_out, 0));
+    std::vector<Ciphertext *> out;
+    for (size_t q = 0; q < B; q++) {
+        Ciphertext *o = new_ct(c, bt->g_out[q]->level, bt->g_out[q]->scale);
+        k::copy(c, o->data.u(), bt->g_out[q]->data.u(), o->data.bytes / 8);
+        out.push_back(o);
+    }
+    return out;
+}
+
+void batch_set_graph(Batch *b, bool on) { b->use_graph = on; }
+bool batch_uses_graph(const Batch *b) { return b->use_graph; }
 size_t batch_size(const Batch *b) { return b->evk.size(); }
 void batch_destroy(Batch *b) { delete b; }
 const EvalKey *batch_evk(const Batch *b, size_t q) { return b->evk[q]; }

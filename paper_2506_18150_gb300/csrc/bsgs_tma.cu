@@ -27,7 +27,6 @@ namespace helrm {
 namespace {
 
 constexpr int T = 256;             // coefficients per tile (= threads per CTA)
-constexpr int S = 3;               // pipeline stages
 constexpr long WAIT_LIMIT = 1L << 24;
 
 __device__ __forceinline__ u32 smem_addr(const void *p) { return (u32)__cvta_generic_to_shared(p); }
@@ -61,12 +60,15 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, u32 bytes, 
                  : "memory");
 }
 
-__device__ __forceinline__ int auto_src(int i, int logN, u64 galois)
+// Source index of slot i under X -> X^galois in the bit-reversed NTT order,
+// from xi = 2 brv(i) + 1: only (xi galois) mod 2N matters and 2N <= 2^17, so
+// 32-bit arithmetic is exact.
+__device__ __forceinline__ int auto_src_x(u32 xi, int logN, u32 galois)
 {
-    const u32 x = __brev((u32)i) >> (32 - logN);
-    const u64 e = ((2ull * x + 1) * galois) & ((2ull << logN) - 1);
-    return (int)(__brev((u32)((e - 1) >> 1)) >> (32 - logN));
+    const u32 e = (xi * galois) & ((2u << logN) - 1u);
+    return (int)(__brev((e - 1u) >> 1) >> (32 - logN));
 }
+__device__ __forceinline__ u32 odd_of(int i, int logN) { return 2u * (__brev((u32)i) >> (32 - logN)) + 1u; }
 
 // Per-query operands of one batched launch (kernel parameters).  The batch
 // index is the fastest grid dimension, so the CTAs of all queries that work
@@ -84,9 +86,13 @@ struct TmaGals {
 };
 
 // Stage layout (words): dig[DN][T] | kb[DN][T] | ka[DN][T] | c0[T] | dd[N2][T]
+// Pipeline depth: three stages when they fit two CTAs per SM (<= 108 KB of
+// stages each), else two (many digits: e.g. 5 digits and 4 giant steps make
+// 40 KB stages, and three of them would leave one CTA per SM).
 template <int N2, int DN>
 struct Stage {
     static constexpr int WORDS = (3 * DN + 1 + N2) * T;
+    static constexpr int S = (3 * WORDS * 8 <= 108 * 1024) ? 3 : 2;
 };
 
 __device__ __forceinline__ void mbar_arrive(u64 *bar)
@@ -107,9 +113,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(u64 *bar, u32 parity)
 constexpr int CONSUMER_WARPS = T / 32;
 
 template <int N2, int DN>
-__global__ void __launch_bounds__(T + 32) k_bsgs_tma(
+// Two CTAs per SM (2 x 9 warps): an SM partition holds 16K registers and gets
+// five of the 18 warps, so a thread may use at most 96 registers.
+__global__ void __launch_bounds__(T + 32, 2) k_bsgs_tma(
                                                     const TmaQueries qs, const TmaGals bk,
                                                     const u64 *const *__restrict__ keytab,
+                                                    const int *__restrict__ keylv,
                                                     const u64 *const *__restrict__ diag,
                                                     const int *__restrict__ gb, int n1, int level, int L, int K,
                                                     int logN, const u64 *__restrict__ pmod,
@@ -118,14 +127,22 @@ __global__ void __launch_bounds__(T + 32) k_bsgs_tma(
     pdl_begin();
     extern __shared__ __align__(128) u64 smem[];
     constexpr int SW = Stage<N2, DN>::WORDS;
+    constexpr int S = Stage<N2, DN>::S;
     u64 *full = smem + S * SW;        // S mbarriers
     u64 *empty = full + S;            // S mbarriers
     __shared__ int sgb[64 * 8];
     __shared__ int blist[64];         // needed baby steps b >= 1, in order
     __shared__ int nb, need0;
+    // per stage, written by the producer before the stage's arrive (so visible
+    // to the consumers once the stage completes): the Galois element, the
+    // aligned block the gathered rows start at, and which diagonals are present
+    __shared__ u32 st_gal[S], st_mask[S];
+    __shared__ int st_base[S];
+    __shared__ const u64 *s_key[64];   // this query's key of each baby step, and its level
+    __shared__ int s_kl[64];
     const int tid = threadIdx.x;
     const size_t N = (size_t)1 << logN;
-    const int nl = level + 1 + K, nP = L + 1 + K;
+    const int nl = level + 1 + K;
     const size_t plane = (size_t)nl * N;
     const int qi = blockIdx.x;
     const int l = blockIdx.z;
@@ -138,6 +155,10 @@ __global__ void __launch_bounds__(T + 32) k_bsgs_tma(
     const int pid = qlimb ? l : L + 1 + (l - level - 1);
 
     for (int t = tid; t < n1 * N2; t += blockDim.x) sgb[t] = gb[t];
+    for (int t = tid; t < n1; t += blockDim.x) {
+        s_key[t] = keytab[(size_t)qi * 64 + t];
+        s_kl[t] = keylv[(size_t)qi * 64 + t];
+    }
     __syncthreads();
     if (tid == 0) {
         int c = 0;
@@ -161,21 +182,33 @@ __global__ void __launch_bounds__(T + 32) k_bsgs_tma(
     if (tid >= T) {
         // ---------------- producer warp
         const int lane = tid & 31;
-        int k = 0;
+        int k = 0, s = 0;
+        u32 phase = 0;
         bool ok = true;
+        const u32 x0 = odd_of(i0, logN);
         for (; k < nb; k++) {
-            const int s = k % S;
-            if (k >= S && !mbar_wait_bounded(&empty[s], (u32)(((k / S) - 1) & 1))) {
+            if (k >= S && !mbar_wait_bounded(&empty[s], phase ^ 1u)) {
                 ok = false;
                 break;
             }
             const int b = blist[k];
             u64 *st = smem + s * SW;
-            const int src_base = auto_src(i0, logN, bk.gal[b]) & ~(T - 1);
-            const u64 *key = keytab[(size_t)qi * 64 + b];
+            const int src_base = auto_src_x(x0, logN, (u32)bk.gal[b]) & ~(T - 1);
+            const u64 *key = s_key[b];
+            const int kl = s_kl[b], nK = kl + 1 + K, kx = key_limb(pid, kl, L);
             int nd = 0;
-            for (int g = 0; g < N2; g++) nd += sgb[g * n1 + b] >= 0;
-            if (lane == 0) mbar_arrive_expect_tx(&full[s], (u32)(3 * DN + (qlimb ? 1 : 0) + nd) * T * 8);
+            u32 mask = 0;
+            for (int g = 0; g < N2; g++)
+                if (sgb[g * n1 + b] >= 0) {
+                    nd++;
+                    mask |= 1u << g;
+                }
+            if (lane == 0) {
+                st_gal[s] = (u32)bk.gal[b];
+                st_base[s] = src_base;
+                st_mask[s] = mask;
+                mbar_arrive_expect_tx(&full[s], (u32)(3 * DN + (qlimb ? 1 : 0) + nd) * T * 8);
+            }
             __syncwarp();
             // rows: DN digit rows, 2 DN key rows, the c0 row, the present diagonal rows
             for (int cidx = lane; cidx < 3 * DN + 1 + N2; cidx += 32) {
@@ -186,11 +219,11 @@ __global__ void __launch_bounds__(T + 32) k_bsgs_tma(
                     dst = st + cidx * T;
                 } else if (cidx < 2 * DN) {
                     const int j = cidx - DN;
-                    src = key + ((size_t)(2 * j) * nP + pid) * N + i0;
+                    src = key + ((size_t)(2 * j) * nK + kx) * N + i0;
                     dst = st + (DN + j) * T;
                 } else if (cidx < 3 * DN) {
                     const int j = cidx - 2 * DN;
-                    src = key + ((size_t)(2 * j + 1) * nP + pid) * N + i0;
+                    src = key + ((size_t)(2 * j + 1) * nK + kx) * N + i0;
                     dst = st + (2 * DN + j) * T;
                 } else if (cidx == 3 * DN) {
                     if (qlimb) {
@@ -208,6 +241,10 @@ __global__ void __launch_bounds__(T + 32) k_bsgs_tma(
                 if (src) bulk_g2s(dst, src, T * 8, &full[s]);
             }
             __syncwarp();
+            if (++s == S) {
+                s = 0;
+                phase ^= 1u;
+            }
         }
         if (!ok && lane == 0) {
             atomicExch(err, (int)HELRM_E_TIMEOUT);
@@ -236,15 +273,16 @@ __global__ void __launch_bounds__(T + 32) k_bsgs_tma(
             a1[g].mac(v1, d, pi.q);
         }
     }
-    for (int k = 0; k < nb; k++) {
-        const int s = k % S;
-        if (!mbar_wait_bounded(&full[s], (u32)((k / S) & 1))) {
+    const u32 xi = odd_of(i, logN);
+    u32 phase = 0;
+    for (int k = 0, s = 0; k < nb; k++) {
+        if (!mbar_wait_bounded(&full[s], phase)) {
             if (lane == 0) atomicExch(err, (int)HELRM_E_TIMEOUT);
             return;   // no CTA barrier follows, so leaving early cannot deadlock
         }
-        const int b = blist[k];
         const u64 *st = smem + s * SW;
-        const int src_loc = auto_src(i, logN, bk.gal[b]) - (auto_src(i0, logN, bk.gal[b]) & ~(T - 1));
+        const u32 mask = st_mask[s];
+        const int src_loc = auto_src_x(xi, logN, st_gal[s]) - st_base[s];
         Acc128 t0, t1;
 #pragma unroll
         for (int j = 0; j < DN; j++) {
@@ -252,18 +290,34 @@ __global__ void __launch_bounds__(T + 32) k_bsgs_tma(
             t0.mac(d, st[(DN + j) * T + tid], pi.q);
             t1.mac(d, st[(2 * DN + j) * T + tid], pi.q);
         }
-        u64 v0 = t0.reduce(pi.q, pi.qinv);
+        // + P phi(c0) on the Q limbs: pm = P R mod q, so the same REDC yields it
+        if (qlimb) t0.mac(st[3 * DN * T + src_loc], pm, pi.q);
+        const u64 v0 = t0.reduce(pi.q, pi.qinv);
         const u64 v1 = t1.reduce(pi.q, pi.qinv);
-        if (qlimb) v0 = add_mod(v0, mont_mul(st[3 * DN * T + src_loc], pm, pi.q, pi.qinv), pi.q);
-        u64 dd[N2];
+        if (N2 <= 4) {   // few diagonals: take them into registers and release the stage first
+            u64 dd[N2];
 #pragma unroll
-        for (int g = 0; g < N2; g++) dd[g] = sgb[g * n1 + b] >= 0 ? st[(3 * DN + 1 + g) * T + tid] : 0;
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);   // this warp is done with stage s
+            for (int g = 0; g < N2; g++) dd[g] = (mask >> g) & 1u ? st[(3 * DN + 1 + g) * T + tid] : 0;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);   // this warp is done with stage s
 #pragma unroll
-        for (int g = 0; g < N2; g++) {
-            a0[g].mac(v0, dd[g], pi.q);
-            a1[g].mac(v1, dd[g], pi.q);
+            for (int g = 0; g < N2; g++) {
+                a0[g].mac(v0, dd[g], pi.q);
+                a1[g].mac(v1, dd[g], pi.q);
+            }
+        } else {         // many: read each as it is used (fewer live registers), then release
+#pragma unroll
+            for (int g = 0; g < N2; g++) {
+                const u64 d = (mask >> g) & 1u ? st[(3 * DN + 1 + g) * T + tid] : 0;
+                a0[g].mac(v0, d, pi.q);
+                a1[g].mac(v1, d, pi.q);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+        }
+        if (++s == S) {
+            s = 0;
+            phase ^= 1u;
         }
     }
 #pragma unroll
@@ -272,19 +326,24 @@ __global__ void __launch_bounds__(T + 32) k_bsgs_tma(
         for (int b = 0; b < n1; b++) any |= sgb[g * n1 + b] >= 0;
         if (!any) continue;
         u64 *o = inner + (size_t)g * 2 * plane + idx;
-        o[0] = a0[g].reduce(pi.q, pi.qinv);
-        o[plane] = a1[g].reduce(pi.q, pi.qinv);
+        o[0] = a0[g].reduce_long(pi.q, pi.qinv, pi.rmod);   // up to 65 terms
+        o[plane] = a1[g].reduce_long(pi.q, pi.qinv, pi.rmod);
     }
 }
 
 template <int N2, int DN>
 void launch_tma(Ctx *c, const TmaQueries &qs, int nq, const TmaGals &bk, const u64 *const *keytab,
-                const u64 *const *diag, const int *gb, int n1, int level)
+                const int *keylv, const u64 *const *diag, const int *gb, int n1, int level)
 {
+    constexpr int S = Stage<N2, DN>::S;
     const size_t smem = (size_t)S * Stage<N2, DN>::WORDS * 8 + 2 * S * 8;
-    CUDA_CHECK(cudaFuncSetAttribute(k_bsgs_tma<N2, DN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    static bool attr_set = false;   // once per instance (also keeps it out of graph captures)
+    if (!attr_set) {
+        CUDA_CHECK(cudaFuncSetAttribute(k_bsgs_tma<N2, DN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
     dim3 grid(nq, c->N / T, level + 1 + c->K);
-    launch(c, k_bsgs_tma<N2, DN>, grid, T + 32, smem, qs, bk, keytab, diag, gb, n1, level, c->L, c->K, c->logN,
+    launch(c, k_bsgs_tma<N2, DN>, grid, T + 32, smem, qs, bk, keytab, keylv, diag, gb, n1, level, c->L, c->K, c->logN,
            c->d_pmod_mont.u(), c->d_pinfo.as<PrimeInfo>(), c->d_err.as<int>());
 }
 
@@ -292,7 +351,8 @@ void launch_tma(Ctx *c, const TmaQueries &qs, int nq, const TmaGals &bk, const u
 
 namespace k {
 
-void bsgs_tma_batch(Ctx *c, const std::vector<BsgsQuery> &qv, const u64 *const *d_keytab, const u64 *gals,
+void bsgs_tma_batch(Ctx *c, const std::vector<BsgsQuery> &qv, const u64 *const *d_keytab, const int *d_keylv,
+                    const u64 *gals,
                     const u64 *const *d_diag_ptrs, const int *d_gb_index, int n_diag, int n_keys, int n1, int n2,
                     int level)
 {
@@ -315,7 +375,8 @@ void bsgs_tma_batch(Ctx *c, const std::vector<BsgsQuery> &qv, const u64 *const *
         KTimer kt(c, "bsgs_fused", 8.0 * plane * nq * (2.0 * dnum * n_keys + 2.0 * n2) + 8.0 * plane * n_diag +
                                        16.0 * nq * (level + 1) * c->N);
         const u64 *const *kt_q = d_keytab + q0 * 64;
-#define HELRM_TMA(NN, DD) launch_tma<NN, DD>(c, qs, nq, bk, kt_q, d_diag_ptrs, d_gb_index, n1, level)
+        const int *kl_q = d_keylv + q0 * 64;
+#define HELRM_TMA(NN, DD) launch_tma<NN, DD>(c, qs, nq, bk, kt_q, kl_q, d_diag_ptrs, d_gb_index, n1, level)
 #define HELRM_TMA_D(NN)              \
     switch (dnum) {                  \
     case 1: HELRM_TMA(NN, 1); break; \
@@ -339,20 +400,26 @@ void bsgs_tma_batch(Ctx *c, const std::vector<BsgsQuery> &qv, const u64 *const *
     }
 }
 
-void bsgs_tma(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c1, const u64 *const *keys,
+void bsgs_tma(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c1, const SwitchKey *const *keys,
               const u64 *gals, const u64 *const *d_diag_ptrs, const int *d_gb_index, int n_diag, int n1, int n2,
               int level)
 {
-    // the key table of this one query, staged to the device (stream ordered)
-    std::vector<const u64 *> tab(64, nullptr);
+    // the key table of this one query (pointers, then levels), staged to the device (stream ordered)
+    struct {
+        const u64 *ptr[64];
+        int lv[64];
+    } tab = {};
     int n_keys = 0;
-    for (int b = 1; b < n1; b++) {
-        tab[b] = keys[b];
-        n_keys += keys[b] ? 1 : 0;
-    }
-    DevMem d_tab(c, 64 * sizeof(u64 *));
-    CUDA_CHECK(cudaMemcpyAsync(d_tab.ptr, tab.data(), 64 * sizeof(u64 *), cudaMemcpyHostToDevice, c->stream));
-    bsgs_tma_batch(c, {{inner, digits, c0, c1}}, d_tab.as<const u64 *const>(), gals, d_diag_ptrs, d_gb_index, n_diag,
+    for (int b = 1; b < n1; b++)
+        if (keys[b]) {
+            tab.ptr[b] = keys[b]->data.u();
+            tab.lv[b] = keys[b]->level;
+            n_keys++;
+        }
+    DevMem d_tab(c, sizeof(tab));
+    CUDA_CHECK(cudaMemcpyAsync(d_tab.ptr, &tab, sizeof(tab), cudaMemcpyHostToDevice, c->stream));
+    bsgs_tma_batch(c, {{inner, digits, c0, c1}}, d_tab.as<const u64 *const>(),
+                   (const int *)((const char *)d_tab.ptr + sizeof(tab.ptr)), gals, d_diag_ptrs, d_gb_index, n_diag,
                    n_keys, n1, n2, level);
 }
 

@@ -396,6 +396,7 @@ Ctx *ctx_create(const helrm_params *p, int device, void *stream)
     upload(c.get(), c->d_one_mont, one.data(), 8 * nP);
     u64 zero = 0;
     upload(c.get(), c->d_err, &zero, 8);
+    k::ntt_autotune(c.get());   // launch shapes for this ring degree and GPU
     return c.release();
 }
 

@@ -213,6 +213,14 @@ struct Ctx : Handle {
     std::map<int, BConvTable> moddown_tab;                 // level
     std::map<int, DevMem> rescale_tab;                     // level -> constants
     u64 mem_in_use = 0, mem_cap = 0, mem_peak = 0;   // bytes held, cap, high-water mark
+    // NTT launch shape per limb-count bucket (<= 4, <= 16, <= 64, more limbs per
+    // launch): words per CTA tile and the CTA count (in multiples of the SM count)
+    // below which tiles are split; chosen by ntt_autotune at creation
+    struct NttTune {
+        int tile = 1024;
+        int mult = 2;
+    };
+    NttTune ntt_tune[4];
     u64 launches = 0;
     std::string last_error;
     cudaMemPool_t pool = nullptr;
@@ -372,6 +380,9 @@ struct NttLimb {
 void ntt_run(Ctx *c, const std::vector<NttLimb> &limbs, bool inverse, const u64 *ep_scal);
 // same as ntt_fwd / ntt_inv, with the launch list built on the stack (no heap use)
 void ntt_map_noheap(Ctx *c, u64 *data, int n_limbs, LimbMap map, bool inverse);
+// time every candidate NTT launch shape per limb-count bucket on scratch limbs
+// and keep the fastest (ntt.cu); the arithmetic is the same for every shape
+void ntt_autotune(Ctx *c);
 // transform an arbitrary list of limbs (offset in limbs from base, prime id) in one launch pair
 void ntt_list(Ctx *c, u64 *base, const std::vector<std::pair<u32, int>> &limbs, bool inverse);
 void copy(Ctx *c, u64 *dst, const u64 *src, size_t n_words);

@@ -18,7 +18,8 @@
 // (period W_u); u = relin(sum_s A_s (x) rot(zz, 16 s)), s = 1..B'/2, so region
 // s-1, block a holds z_a * z_{(a+s) mod B'}; the first top layer sums the 16
 // slots of each pair in its weights.  Levels are assigned as late as possible so
-// the logit ends at level 0.
+// the logit ends at level 0.  The layers are evaluated by batch.cu (one query
+// is a batch of one).
 #include <algorithm>
 #include <cmath>
 
@@ -60,17 +61,22 @@ static std::vector<SelSeg> selector_layout(const std::vector<u64> &cards, int p,
 }
 
 
-// Matrix of the packed lookup: rows [out_offset + dim t, out_offset + dim (t+1))
-// take table t's transposed digit tables at the selector columns of its digits.
-static std::vector<double> emb_matrix(const Emb &e, const float *const *tables, int out_offset, int rows)
+// Columns [c0, c0 + w) of the packed lookup matrix: rows [out_offset + dim t,
+// out_offset + dim (t+1)) take table t's transposed digit tables at the
+// selector columns of its digits.
+static std::vector<double> emb_matrix(const Emb &e, const float *const *tables, int out_offset, int rows, int c0,
+                                      int w)
 {
-    std::vector<double> M((size_t)rows * e.width, 0.0);
+    std::vector<double> M((size_t)rows * w, 0.0);
     std::vector<int> row0(e.cards.size(), 0);
     for (auto &s : e.layout) {
         const float *C = tables[s.t] + (size_t)row0[s.t] * e.dim;
-        for (int r = 0; r < s.width; r++)
+        for (int r = 0; r < s.width; r++) {
+            const int col = s.off + r - c0;
+            if (col < 0 || col >= w) continue;
             for (int kk = 0; kk < e.dim; kk++)
-                M[(size_t)(out_offset + e.dim * s.t + kk) * e.width + s.off + r] = (double)C[(size_t)r * e.dim + kk];
+                M[(size_t)(out_offset + e.dim * s.t + kk) * w + col] = (double)C[(size_t)r * e.dim + kk];
+        }
         row0[s.t] += s.width;
     }
     return M;
@@ -90,9 +96,18 @@ Emb *emb_prepare(Ctx *c, const std::vector<u64> &cards, int base, int dim, const
     e->out_pad = out_pad;
     const int rows = out_offset + dim * (int)cards.size();
     HCHECK(rows <= out_pad, HELRM_E_INVAL, "embedding outputs exceed out_pad");
-    HCHECK(e->in_pad <= c->n_slots, HELRM_E_PARAM, "selector wider than the slot count");
-    std::vector<double> M = emb_matrix(*e, tables, out_offset, rows);
-    e->pm.reset(ptmat_prepare(c, M.data(), rows, e->width, e->in_pad, out_pad, level, ct_scale, target_scale));
+    if (e->in_pad <= c->n_slots) {
+        std::vector<double> M = emb_matrix(*e, tables, out_offset, rows, 0, e->width);
+        e->pm.reset(ptmat_prepare(c, M.data(), rows, e->width, e->in_pad, out_pad, level, ct_scale, target_scale));
+    } else {   // one matrix per ciphertext of the selector
+        e->in_pad = c->n_slots;
+        for (int c0 = 0; c0 < e->width; c0 += c->n_slots) {
+            const int w = std::min(c->n_slots, e->width - c0);
+            std::vector<double> M = emb_matrix(*e, tables, out_offset, rows, c0, w);
+            e->chunks.emplace_back(
+                ptmat_prepare(c, M.data(), rows, w, pow2ceil(w), out_pad, level, ct_scale, target_scale));
+        }
+    }
     std::vector<int> tab;
     for (size_t t = 0; t < cards.size(); t++) {
         int off = -1;
@@ -205,6 +220,7 @@ Model *model_create(Ctx *c, const helrm_model_desc *d)
     }
     const double scale_b = scale;
     m->emb.reset(emb_prepare(c, cards, (int)d->base_p, DIM, d->tables, DIM, m->W_z, m->lvl_sel, delta, scale_b));
+    HCHECK(m->emb->pm, HELRM_E_PARAM, "the model's selector must fit one ciphertext");
     double u_scale = scale_b;
     if (dot) {
         std::vector<double> ones(m->W_z, 0.0);
@@ -293,64 +309,23 @@ void model_export(Ctx *c, Model *m, i64 *coeffs, u32 count)
     for (size_t i = 0; i < pts.size(); i++) pt_export_signed(c, pts[i]->get(), coeffs + i * (size_t)c->N);
 }
 
-static Ciphertext *dense_layer(Ctx *c, const EvalKey *evk, const Layer &L, const Ciphertext *x)
-{
-    std::unique_ptr<Ciphertext> y(matvec(c, evk, L.pm.get(), x));
-    y.reset(ct_add_pt(c, y.get(), L.bias.get()));
-    if (L.square) y.reset(ct_mul(c, evk, y.get(), y.get()));
-    return y.release();
-}
+struct Batch;
+Batch *batch_create(Ctx *c, const Model *m, const std::vector<const EvalKey *> &evk);
+void batch_destroy(Batch *b);
+std::vector<Ciphertext *> model_infer_batch(Ctx *c, const Batch *bt, const std::vector<const Ciphertext *> &ct_dense,
+                                            const std::vector<const Ciphertext *> &ct_sel);
 
-static Ciphertext *dot_interaction(Ctx *c, const EvalKey *evk, const Model *m, const Ciphertext *z)
-{
-    auto masked = [&](int i) {
-        std::unique_ptr<Ciphertext> t(ct_mul_pt(c, z, m->masks[i].get()));
-        Ciphertext *r = ct_rescale(c, t.get());
-        r->scale = c->delta;
-        return r;
-    };
-    std::unique_ptr<Ciphertext> z1(masked(0));
-    std::vector<std::unique_ptr<Ciphertext>> A;
-    for (int s = 1; s <= m->S; s++) A.emplace_back(masked(s));
-    std::unique_ptr<Ciphertext> r(ct_rotate(c, evk, z1.get(), -DIM * m->Bp));
-    std::unique_ptr<Ciphertext> zz(ct_add(c, z1.get(), r.get()));
-    std::vector<int> steps;
-    for (int s = 1; s <= m->S; s++) steps.push_back(DIM * s);
-    std::vector<Ciphertext *> R;
-    ct_rotate_hoisted(c, evk, zz.get(), steps, R);
-    std::vector<std::unique_ptr<Ciphertext>> Rk;
-    for (auto *p : R) Rk.emplace_back(p);
-    const int lvl = z1->level;
-    DevMem d(c, (size_t)3 * (lvl + 1) * c->N * 8);
-    for (int s = 1; s <= m->S; s++) ct_tensor_acc(c, d.u(), A[s - 1].get(), Rk[s - 1].get(), s > 1);
-    std::unique_ptr<Ciphertext> rl(ct_relin(c, evk, d.u(), lvl, c->delta * c->delta));
-    return ct_rescale(c, rl.get());
-}
-
+// One query runs as a batch of one (batch.cu): the same integer operations
+// as the op-by-op path below, with the independent steps of each layer (all
+// giant steps, all masks, all rotations of the interaction) merged into one
+// launch each.
 Ciphertext *model_infer(Ctx *c, const EvalKey *evk, const Model *m, const Ciphertext *ct_dense,
                         const Ciphertext *ct_sel)
 {
     HCHECK(ct_dense->level == m->lvl_dense, HELRM_E_LEVEL, "ct_dense is not at the model's dense level");
     HCHECK(ct_sel->level == m->lvl_sel, HELRM_E_LEVEL, "ct_sel is not at the model's selector level");
-    std::unique_ptr<Ciphertext> h;
-    const Ciphertext *x = ct_dense;
-    for (auto &L : m->bottom) {
-        h.reset(dense_layer(c, evk, L, x));
-        x = h.get();
-    }
-    std::unique_ptr<Ciphertext> e(matvec(c, evk, m->emb->pm.get(), ct_sel));
-    std::unique_ptr<Ciphertext> z(ct_add(c, h.get(), e.get()));
-    h.reset();
-    e.reset();
-    std::unique_ptr<Ciphertext> y;
-    if (m->interaction == 0) {
-        z.reset(ct_add_pt(c, z.get(), m->ones.get()));
-        y.reset(dot_interaction(c, evk, m, z.get()));
-    } else {
-        y = std::move(z);
-    }
-    for (auto &L : m->top) y.reset(dense_layer(c, evk, L, y.get()));
-    return y.release();
+    std::unique_ptr<Batch, void (*)(Batch *)> b(batch_create(c, m, {evk}), batch_destroy);
+    return model_infer_batch(c, b.get(), {ct_dense}, {ct_sel})[0];
 }
 
 // client side: pack on the device, encode, encrypt
@@ -432,6 +407,23 @@ std::vector<std::pair<int, int>> model_key_levels(const Model *m, int *relin_lev
     return std::vector<std::pair<int, int>>(lv.begin(), lv.end());
 }
 const PtMatrix *emb_matrix_of(const Emb *e) { return e->pm.get(); }
+int emb_n_chunks(const Emb *e) { return e->pm ? 1 : (int)e->chunks.size(); }
+PtMatrix *emb_chunk(const Emb *e, int c) { return e->pm ? e->pm.get() : e->chunks[c].get(); }
+int emb_chunk_period(const Emb *e, int c) { return e->pm ? e->in_pad : e->chunks[c]->in_pad; }
+
+// y = M s = sum_c M_c s_c for a selector spread over several ciphertexts
+Ciphertext *emb_lookup_multi(Ctx *c, const EvalKey *evk, const Emb *e, const std::vector<const Ciphertext *> &sel)
+{
+    const int n = emb_n_chunks(e);
+    HCHECK((int)sel.size() == n, HELRM_E_INVAL,
+           "the selector spans " + std::to_string(n) + " ciphertexts, got " + std::to_string(sel.size()));
+    std::unique_ptr<Ciphertext> y;
+    for (int k = 0; k < n; k++) {
+        std::unique_ptr<Ciphertext> t(matvec(c, evk, emb_chunk(e, k), sel[k]));
+        y.reset(y ? ct_add(c, y.get(), t.get()) : t.release());
+    }
+    return y.release();
+}
 void emb_info(const Emb *e, u32 *width, u32 *period)
 {
     *width = e->width;

@@ -19,7 +19,10 @@ struct Emb : Handle {
     std::vector<u64> cards;
     int base = 0, dim = 0, width = 0, in_pad = 0, out_pad = 0;
     std::vector<SelSeg> layout;
-    std::unique_ptr<PtMatrix> pm;
+    std::unique_ptr<PtMatrix> pm;                    // the lookup matrix (selector within one ciphertext)
+    // a selector wider than the slot count spans ceil(width / n) ciphertexts:
+    // chunk c holds columns [c n, min((c + 1) n, width)) and has its own matrix
+    std::vector<std::unique_ptr<PtMatrix>> chunks;   // (pm is then null)
     DevMem d_tab;   // int [T][3]: card (clamped), offset, digits
     Emb(Ctx *c) : Handle(KIND_EMB), ctx(c) {}
 };

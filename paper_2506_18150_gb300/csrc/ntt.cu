@@ -22,13 +22,15 @@
 // copy is needed before a transform), the second works in place.  A forward
 // transform may end with a fused epilogue out = (a - NTT(y)) * c[prime] (+ b)
 // (c a Montgomery constant), which is how ModDown and rescale finish.
+#include <cstdlib>
+
 #include "core.cuh"
 
 namespace helrm {
 namespace {
 
 constexpr int MAX_LIMBS = 128;
-constexpr int TILE = 1024;   // words per CTA (8 KB of data)
+inline int tune_bucket(int n_limbs) { return n_limbs <= 4 ? 0 : n_limbs <= 16 ? 1 : n_limbs <= 64 ? 2 : 3; }
 
 struct LimbList {
     int n;
@@ -217,12 +219,13 @@ template <int LOGP, bool COLS, bool INV>
 void launch_pass(Ctx *c, const LimbList &ll, int n_sub, int first, int mode, const u64 *ep_scal)
 {
     constexpr int P = 1 << LOGP;
-    // sub-transforms per CTA: as many as fit a 4096-word tile, fewer when the
+    // sub-transforms per CTA: as many as fit the tuned tile, fewer when the
     // batch is small so the grid still covers the SMs (columns keep >= 4
     // consecutive words per row for coalescing)
-    int G = std::min(TILE / P, n_sub);
+    const Ctx::NttTune &tu = c->ntt_tune[tune_bucket(ll.n)];
+    int G = std::max(1, std::min(tu.tile / P, n_sub));
     const int gmin = COLS ? 4 : 1;
-    while (G > gmin && (long)(n_sub / G) * ll.n < 2 * 152) G /= 2;
+    while (G > gmin && (long)(n_sub / G) * ll.n < (long)tu.mult * c->n_sms) G /= 2;
     int logG = 0;
     while ((1 << logG) < G) logG++;
     const int threads = G * P / 8;
@@ -304,6 +307,57 @@ void ntt_map_noheap(Ctx *c, u64 *data, int n_limbs, LimbMap map, bool inverse)
         }
         run_list(c, ll, inverse, nullptr);
     }
+}
+
+void ntt_autotune(Ctx *c)
+{
+    const char *env = getenv("HELRM_NTT_AUTOTUNE");
+    if (env && env[0] == '0') return;   // keep the default shapes
+    const int N = c->N, n_max = 128;
+    const int tiles[] = {512, 1024, 2048, 4096};
+    const int mults[] = {1, 2, 4, 8};
+    const int sizes[4] = {2, 8, 32, 128};   // a representative launch of each bucket
+    DevMem buf(c, (size_t)n_max * N * 8);
+    CUDA_CHECK(cudaMemsetAsync(buf.ptr, 0, (size_t)n_max * N * 8, c->stream));
+    cudaEvent_t e0, e1;
+    CUDA_CHECK(cudaEventCreate(&e0));
+    CUDA_CHECK(cudaEventCreate(&e1));
+    const bool prof = c->prof_on;
+    c->prof_on = false;
+    for (int bk = 0; bk < 4; bk++) {
+        const int n = sizes[bk];
+        std::vector<NttLimb> v;
+        for (int l = 0; l < n; l++) {
+            u64 *p = buf.u() + (size_t)l * N;
+            v.push_back({p, p, 1 + l % std::max(c->L, 1), nullptr, nullptr, nullptr});
+        }
+        float best = 1e30f;
+        Ctx::NttTune win = c->ntt_tune[bk];
+        for (int t : tiles)
+            for (int m : mults) {
+                c->ntt_tune[bk] = {t, m};
+                ntt_run(c, v, false, nullptr);   // warm-up
+                ntt_run(c, v, true, nullptr);
+                CUDA_CHECK(cudaEventRecord(e0, c->stream));
+                for (int r = 0; r < 3; r++) {
+                    ntt_run(c, v, false, nullptr);
+                    ntt_run(c, v, true, nullptr);
+                }
+                CUDA_CHECK(cudaEventRecord(e1, c->stream));
+                CUDA_CHECK(cudaEventSynchronize(e1));
+                float ms = 0;
+                CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best * 0.98f) {   // prefer the earlier (smaller) shape unless clearly faster
+                    best = ms;
+                    win = {t, m};
+                }
+            }
+        c->ntt_tune[bk] = win;
+    }
+    c->prof_on = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CUDA_CHECK(cudaStreamSynchronize(c->stream));
 }
 
 void ntt_list(Ctx *c, u64 *base, const std::vector<std::pair<u32, int>> &limbs, bool inverse)

@@ -102,6 +102,9 @@ _SIGS = {
     "helrm_query_pack": [_vp, _u64p, _dp, C.c_uint32],
     "helrm_emb_info": [_vp, _u32p, _u32p],
     "helrm_embedding_lookup": [_vp, _vp, _vp, _vp, C.c_uint32, _pp],
+    "helrm_emb_chunks": [_vp, _u32p],
+    "helrm_emb_matrix": [_vp, C.c_uint32, _pp],
+    "helrm_embedding_lookup_multi": [_vp, _vp, _vp, _pp, C.c_uint32, _pp],
     "helrm_model_create": [_vp, C.POINTER(ModelDesc), _pp],
     "helrm_model_info": [_vp, _u32p],
     "helrm_model_rotations": [_vp, _i32p, _u32p],
@@ -115,11 +118,13 @@ _SIGS = {
     "helrm_rescale_noalloc": [_vp, _vp, _vp, C.c_int32, C.c_uint32],
     "helrm_batch_create": [_vp, _vp, C.c_uint32, _pp, _pp],
     "helrm_infer_batch": [_vp, _vp, _pp, _pp, _pp],
+    "helrm_batch_set_graph": [_vp, _vp, C.c_int],
     "helrm_infer_batch_e2e_device": [_vp, _vp, _pp, _vp, _vp, C.c_uint64, _vp],
     "helrm_server_create": [_vp, C.c_uint32, C.c_uint32, C.c_uint64, _pp],
     "helrm_server_add_client": [_vp, _vp, _vp, _vp, _u32p],
     "helrm_server_run": [_vp, _vp, C.c_uint32, _dp, _u32p, _pp, _pp, _pp, _dp, C.c_void_p],
     "helrm_ctx_profile": [_vp, C.c_int],
+    "helrm_ctx_ntt_tuning": [_vp, _u32p],
     "helrm_ctx_profile_report": [_vp, C.c_char_p, C.c_uint64, _u64p],
 }
 
@@ -172,6 +177,13 @@ class Handle:
 
 class Context(Handle):
     pass
+
+
+class Borrowed(Handle):
+    """A handle owned by another object (kept alive by it); never freed here."""
+
+    def __del__(self):
+        pass
 
 
 def _check(ctx, st):
@@ -442,6 +454,25 @@ def helrm_query_pack(ctx, emb, indices, n_slots):
     return out
 
 
+def helrm_emb_chunks(ctx, emb) -> int:
+    n = C.c_uint32()
+    _check(ctx, lib().helrm_emb_chunks(emb.ptr, C.byref(n)))
+    return n.value
+
+
+def helrm_emb_matrix(ctx, emb, chunk: int):
+    """The embedding's own matrix of ciphertext `chunk` (not freed by this handle)."""
+    out = C.c_void_p()
+    _check(ctx, lib().helrm_emb_matrix(emb.ptr, chunk, C.byref(out)))
+    return Borrowed(out.value, emb)
+
+
+def helrm_embedding_lookup_multi(ctx, evk, emb, sels):
+    out = C.c_void_p()
+    _check(ctx, lib().helrm_embedding_lookup_multi(ctx.ptr, evk.ptr, emb.ptr, _ptrs(sels), len(sels), C.byref(out)))
+    return Handle(out.value, ctx)
+
+
 def helrm_embedding_lookup(ctx, evk, emb, sel):
     return _ct_op("helrm_embedding_lookup", ctx, evk.ptr, emb.ptr, sel.ptr, 1)
 
@@ -532,6 +563,10 @@ def helrm_batch_create(ctx, m, evks):
     return Handle(out.value, (ctx, m, list(evks)))
 
 
+def helrm_batch_set_graph(ctx, batch, enable: bool):
+    _check(ctx, lib().helrm_batch_set_graph(ctx.ptr, batch.ptr, int(enable)))
+
+
 def helrm_infer_batch(ctx, batch, cts_dense, cts_sel):
     n = len(cts_dense)
     outs = (C.c_void_p * n)()
@@ -576,6 +611,13 @@ def helrm_rescale_noalloc(ctx, d_in: int, d_out: int, level: int, n_polys: int):
     """Rescale without allocating: device pointers in (n_polys x (level+1) x N) and
     out (n_polys x level x N), NTT domain; scratch is a static 1 MiB device array."""
     _check(ctx, lib().helrm_rescale_noalloc(ctx.ptr, C.c_void_p(d_in), C.c_void_p(d_out), level, n_polys))
+
+
+def helrm_ctx_ntt_tuning(ctx):
+    """{limb bucket: (tile words, CTA multiple of the SM count)} chosen at context creation."""
+    out = (C.c_uint32 * 8)()
+    _check(ctx, lib().helrm_ctx_ntt_tuning(ctx.ptr, out))
+    return {b: (out[2 * i], out[2 * i + 1]) for i, b in enumerate(["<=4", "<=16", "<=64", ">64"])}
 
 
 def helrm_ctx_profile(ctx, enable: bool):

@@ -153,3 +153,28 @@ def test_model_keygen_truncated_keys_give_identical_logits():
     with pytest.raises(H.HelrmError) as e:
         H.helrm_rotate(ctx, evk_t, top, steps[-1])
     assert e.value.name == "HELRM_E_NOKEY"
+
+
+def test_batch_graph_replay_matches_eager():
+    """helrm_batch_set_graph: the batch's server path captured as a CUDA graph
+    and replayed on new inputs gives the eager path's ciphertexts bit for bit
+    (first call: capture; second and third: replays with other queries)."""
+    from paper_2506_18150_gb300 import helrm as H
+    from paper_2506_18150_gb300 import synthetic as syn
+    pr = syn.reduced_params(13, 9)
+    spec = syn.uci_spec(0)
+    ctx = gpu_ctx(pr)
+    model = H.helrm_model_create(ctx, spec, syn.make_weights(spec, 0))
+    keys = [H.helrm_model_keygen(ctx, model, 70 + c) for c in range(2)]
+    owner = [0, 1, 1]
+    eager = H.helrm_batch_create(ctx, model, [keys[o][1] for o in owner])
+    graph = H.helrm_batch_create(ctx, model, [keys[o][1] for o in owner])
+    H.helrm_batch_set_graph(ctx, graph, True)
+    for call in range(3):
+        dense, idx = syn.make_queries(spec, 3, seed=80 + call)
+        cts = [H.helrm_encrypt_query(ctx, keys[owner[q]][1], model, dense[q], idx[q], 500 + 10 * call + 2 * q)
+               for q in range(3)]
+        a = H.helrm_infer_batch(ctx, eager, [c[0] for c in cts], [c[1] for c in cts])
+        b = H.helrm_infer_batch(ctx, graph, [c[0] for c in cts], [c[1] for c in cts])
+        for q in range(3):
+            _same_ct(ctx, a[q], b[q])

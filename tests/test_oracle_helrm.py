@@ -165,3 +165,49 @@ def test_criteo_shape():
     _, width = dlrm.selector_layout(spec.cards, spec.base)
     assert 2048 < width <= 8192
     assert syn.uci_spec(0).top[0] == 52
+
+
+def test_selector_chunks_cover_the_width_once():
+    """Selectors wider than n slots split into ceil(width / n) ciphertexts."""
+    for width, n in [(560, 512), (512, 512), (1, 512), (33_000, 32_768), (2_772_109, 32_768)]:
+        ch = dlrm.selector_chunks(width, n)
+        assert len(ch) == -(-width // n)
+        assert [c0 for c0, _ in ch] == list(range(0, width, n))
+        assert sum(w for _, w in ch) == width and all(0 < w <= n for _, w in ch)
+    assert len(dlrm.selector_chunks(2_772_109, 32_768)) == 85        # Sec. 5.4: the 12.18x model
+
+
+def test_two_ciphertext_lookup_has_1024_diagonals():
+    """416 outputs (padded to 512) over a selector spanning two ciphertexts of
+    n = 2^15 slots: 512 diagonals per ciphertext, 1024 in all (Sec. 5.4)."""
+    n = 1 << 15
+    chunks = dlrm.selector_chunks(n + 5000, n)
+    lays = [linear.Layout.make(linear.pow2ceil(w), linear.pow2ceil(416)) for _, w in chunks]
+    assert len(lays) == 2 and sum(l.D for l in lays) == 1024
+
+
+def test_multi_ciphertext_lookup_matches_gather(small_params):
+    """N = 2^10 (n = 512 slots): two plain tables of 300 and 260 rows give a
+    560-slot selector, i.e. two ciphertexts (512 + 48 columns).  The sum of the
+    two per-ciphertext BSGS products decrypts to the gathered embeddings."""
+    p = small_params
+    cards, base = [300, 260], 512
+    rng = np.random.default_rng(12)
+    tables = [[rng.uniform(-0.05, 0.05, (k, dlrm.DIM)).astype(np.float32)] for k in cards]
+    M = dlrm.embedding_matrix(cards, base, tables, 0, 2 * dlrm.DIM)
+    pms = dlrm.prepare_multi(p, M, 2 * dlrm.DIM, 3, p.delta, p.delta)
+    assert [pm.layout.in_pad for pm in pms] == [512, 64]
+    steps = sorted(set().union(*[linear.rotation_steps(pm) for pm in pms]))
+    sk, keys = ckks.keygen(p, 21, rot_steps=steps, relin=False)
+    for idx in [(0, 0), (299, 259), (17, 200)]:
+        sel = dlrm.selector_vector(cards, base, idx)
+        x = dlrm.chunk_slots(sel, p.n)
+        # the block decomposition in the clear: M s = sum_c M_c s_c
+        parts = [M[:, c0:c0 + w] @ sel[c0:c0 + w] for c0, w in dlrm.selector_chunks(len(sel), p.n)]
+        assert np.allclose(sum(parts), M @ sel)
+        cts = [ckks.encrypt(p, keys, ckks.encode_real(p, xi, p.delta), 3, p.delta, 40 + c) for c, xi in enumerate(x)]
+        y = dlrm.lookup_multi(p, keys, pms, cts)
+        assert y.level == 2
+        got = ckks.decrypt(p, sk, y)[: 2 * dlrm.DIM]
+        want = np.concatenate(dlrm.embedding_cleartext(cards, base, tables, idx))
+        assert np.max(np.abs(got - want)) < 1e-4, idx

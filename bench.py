@@ -227,6 +227,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def job_throughput(units_per_rank, ms, world, device="cuda"):
+    """Whole-job throughput over replicas: the units all ranks processed over
+    the slowest rank's time (an all-reduce MAX of the per-rank times when
+    world > 1).  Returns (units/s, slowest ms)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * units_per_rank / (ms / 1000.0), ms
+
+
 def _timed(fn, reps=1):
     """CUDA-event time of reps calls of fn on the current stream, in ms per call."""
     import torch
@@ -336,13 +349,7 @@ def run_batched(args):
     barrier()
     launches = H.helrm_ctx_launch_count(ctx) - l0
     per = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(K))
-    total_ms = ev[0].elapsed_time(ev[K])
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * n_step * K / (total_ms / 1000.0)
+    value, total_ms = job_throughput(n_step * K, ev[0].elapsed_time(ev[K]), world)
 
     # e2e: each step's inputs copied from pinned host memory, logits read back
     host = [(torch.from_numpy(np.ascontiguousarray(g["dense"])).pin_memory(),
@@ -359,8 +366,7 @@ def run_batched(args):
             o = s * g["n_q"]
             hl[o:o + g["n_q"]].copy_(g["d_lg"][o:o + g["n_q"]], non_blocking=True)
     barrier()
-    e2e_ms = _timed(lambda: [step_e2e(W + s) for s in range(K)]) / K
-    e2e_value = world * n_step / (e2e_ms / 1000.0)
+    e2e_value, e2e_ms = job_throughput(n_step, _timed(lambda: [step_e2e(W + s) for s in range(K)]) / K, world)
     same = all(torch.equal(hl[W * g["n_q"]:], g["d_lg"][W * g["n_q"]:].cpu()) for g, (_, _, hl) in zip(groups, host))
 
     # the plain one-request-at-a-time path on the same 64 queries
@@ -550,13 +556,7 @@ def run_ours(args):
     barrier()
     launches = H.helrm_ctx_launch_count(ctx) - l0
     per = [ev[i].elapsed_time(ev[i + 1]) for i in range(K)]
-    total_ms = ev[0].elapsed_time(ev[K])
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * K / (total_ms / 1000.0)
+    value, total_ms = job_throughput(K, ev[0].elapsed_time(ev[K]), world)
     logits = d_logit.cpu().numpy()
 
     # ---- e2e: pinned host buffers through helrm_infer_e2e
@@ -584,13 +584,7 @@ def run_ours(args):
         step_host(W + s)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * K / (e2e_ms / 1000.0)
+    e2e_value, e2e_ms = job_throughput(K, e0.elapsed_time(e1), world)
     same = bool(np.allclose(h_out.numpy()[W:], logits[W:], atol=1e-9))
 
     # ---- kernel roofline: per-kernel CUDA events on the launch stream

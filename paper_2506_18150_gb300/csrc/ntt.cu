@@ -79,8 +79,12 @@ enum Mode { M_LAZY = 0, M_SCALE = 1, M_REDUCE = 2 };
 // mode: M_LAZY leaves the lazy range (first pass), M_SCALE multiplies by 1/N
 // (last inverse pass), M_REDUCE reduces to [0, q) (last forward pass) and
 // applies the epilogue where the limb has one.
-template <int LOGP, bool COLS, bool INV>
-__global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN, int logG, LimbList list,
+// FIXN > 0: the ring degree is 2^FIXN and the tile holds 2^FIXG sub-transforms,
+// both compile-time constants (the production sizes), so every shared- and
+// global-memory address is a per-thread base plus an immediate offset; 0: the
+// arguments logN / logG are used (every other size).
+template <int LOGP, bool COLS, bool INV, int FIXN = 0, int FIXG = 0>
+__global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN_arg, int logG_arg, LimbList list,
                                                    const ulonglong2 *__restrict__ tw_all,
                                                    const ulonglong2 *__restrict__ ninv,
                                                    const PrimeInfo *__restrict__ pinfo, int mode,
@@ -90,6 +94,8 @@ __global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN, int logG,
     constexpr int P = 1 << LOGP;
     constexpr int TPS = P / 8;              // threads per sub-transform
     extern __shared__ u64 sm[];
+    const int logN = FIXN ? FIXN : logN_arg;
+    const int logG = FIXN ? FIXG : logG_arg;
     const int N = 1 << logN;
     const int logN1 = logN / 2;
     const int N2 = N >> logN1;
@@ -122,7 +128,13 @@ __global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN, int logG,
     auto gaddr = [&](int e) -> size_t {
         return COLS ? (size_t)e * N2 + gglob : (size_t)gglob * N2 + e;
     };
-    auto saddr = [&](int e) -> int { return COLS ? pad(e * G + g) : pad(g * P + e); };
+    // padded shared-memory index pad(x) = x + x/16 of element e, split into a
+    // per-thread part and a part that depends on e only (a constant once the
+    // rounds are unrolled and G is fixed): for COLS, x = e G + g with g < G, so
+    // x/16 = (e G)/16 + (G > 16 ? g/16 : 0); for ROWS, x = g P + e with P a
+    // multiple of 16, so x/16 = (g P)/16 + e/16
+    const int sbase = COLS ? (G <= 16 ? g : g + (g >> 4)) : (g * P + ((g * P) >> 4));
+    auto saddr = [&](int e) -> int { return COLS ? e * G + ((e * G) >> 4) + sbase : e + (e >> 4) + sbase; };
 
     u64 v[8];
     // rounds of up to three stages; forward goes first-to-last, inverse last-to-first
@@ -215,6 +227,15 @@ __global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN, int logG,
     }
 }
 
+template <int LOGP, bool COLS, bool INV, int FIXN, int FIXG>
+void launch_kernel(Ctx *c, dim3 grid, int threads, size_t smem, const LimbList &ll, int first, int logG, int mode,
+                   const u64 *ep_scal)
+{
+    const ulonglong2 *tw = INV ? c->d_tw_inv.as<ulonglong2>() : c->d_tw_fwd.as<ulonglong2>();
+    launch(c, k_ntt_pass<LOGP, COLS, INV, FIXN, FIXG>, grid, threads, smem, first, c->logN, logG, ll, tw,
+           c->d_ninv.as<ulonglong2>(), c->d_pinfo.as<PrimeInfo>(), mode, ep_scal);
+}
+
 template <int LOGP, bool COLS, bool INV>
 void launch_pass(Ctx *c, const LimbList &ll, int n_sub, int first, int mode, const u64 *ep_scal)
 {
@@ -231,9 +252,19 @@ void launch_pass(Ctx *c, const LimbList &ll, int n_sub, int first, int mode, con
     const int threads = G * P / 8;
     const size_t smem = (size_t)(G * P + (G * P >> 4) + 1) * 8;
     dim3 grid(n_sub / G, ll.n);
-    const ulonglong2 *tw = INV ? c->d_tw_inv.as<ulonglong2>() : c->d_tw_fwd.as<ulonglong2>();
-    launch(c, k_ntt_pass<LOGP, COLS, INV>, grid, threads, smem, 
-        first, c->logN, logG, ll, tw, c->d_ninv.as<ulonglong2>(), c->d_pinfo.as<PrimeInfo>(), mode, ep_scal);
+    // N = 2^16 (both passes 256-point): instances with the tile width fixed
+    if constexpr (LOGP == 8) {
+        if (c->logN == 16) {
+            switch (logG) {
+            case 0: launch_kernel<8, COLS, INV, 16, 0>(c, grid, threads, smem, ll, first, logG, mode, ep_scal); return;
+            case 1: launch_kernel<8, COLS, INV, 16, 1>(c, grid, threads, smem, ll, first, logG, mode, ep_scal); return;
+            case 2: launch_kernel<8, COLS, INV, 16, 2>(c, grid, threads, smem, ll, first, logG, mode, ep_scal); return;
+            case 3: launch_kernel<8, COLS, INV, 16, 3>(c, grid, threads, smem, ll, first, logG, mode, ep_scal); return;
+            default: break;
+            }
+        }
+    }
+    launch_kernel<LOGP, COLS, INV, 0, 0>(c, grid, threads, smem, ll, first, logG, mode, ep_scal);
 }
 
 template <bool COLS, bool INV>
@@ -314,7 +345,7 @@ void ntt_autotune(Ctx *c)
     const char *env = getenv("HELRM_NTT_AUTOTUNE");
     if (env && env[0] == '0') return;   // keep the default shapes
     const int N = c->N, n_max = 128;
-    const int tiles[] = {512, 1024, 2048, 4096};
+    const int tiles[] = {512, 1024, 2048};
     const int mults[] = {1, 2, 4, 8};
     const int sizes[4] = {2, 8, 32, 128};   // a representative launch of each bucket
     DevMem buf(c, (size_t)n_max * N * 8);

@@ -3,6 +3,7 @@
   python -m paper_2506_18150_gb300.microbench ntt --limbs 192 --reps 20
   python -m paper_2506_18150_gb300.microbench rotate --level 8 --reps 20
 
+`multi` times the embedding lookup with a selector of --cts ciphertexts.
 `ntt` transforms `limbs` limbs of N = 2^16 words (forward then inverse) and
 reports the time per limb and the algorithmic bandwidth (16 N bytes per limb
 and direction).  `rotate` times one rotation (ModUp, fused automorphism + key
@@ -110,9 +111,48 @@ def bench_matvec(D: int, level: int, reps: int):
             "ms_per_matvec": sum(v[1] for v in rep.values()) / reps}
 
 
+def bench_multi(n_cts: int, level: int, reps: int):
+    """The embedding lookup with a selector of n_cts ciphertexts (HE-LRM Sec.
+    5.4: 18 and 85 for the least compressed Criteo models): 26 plain tables
+    of n_cts * 2^15 / 26 rows each, 416 outputs (padded to 512), prepared at
+    `level` on a chain of level+1 primes (N = 2^16).  Reports ms per lookup."""
+    import torch
+
+    from . import helrm as H
+    ctx = H.helrm_ctx_create(16, [60] + [40] * level, 3, 60, 3, 40.0, device=torch.cuda.current_device(),
+                             stream=torch.cuda.current_stream().cuda_stream)
+    n = 1 << 15
+    rows = (n_cts * n) // 26
+    cards = [rows] * 26
+    rng = np.random.default_rng(5)
+    tables = [[rng.uniform(-0.05, 0.05, (rows, 16)).astype(np.float32)] for _ in cards]
+    emb = H.helrm_emb_prepare(ctx, cards, rows, 16, tables, 0, 512, level, 2.0**40, 2.0**40)
+    chunks = H.helrm_emb_chunks(ctx, emb)
+    mats = [H.helrm_emb_matrix(ctx, emb, c) for c in range(chunks)]
+    steps = sorted(set().union(*[set(H.helrm_ptmat_rotations(ctx, m)) for m in mats]))
+    sk, evk = H.helrm_keygen(ctx, 1, steps)
+    idx = [int(v) for v in rng.integers(0, rows, 26)]
+    slots = H.helrm_query_pack(ctx, emb, idx, chunks * n)
+    cts = [H.helrm_encrypt(ctx, evk, H.helrm_encode(ctx, slots[c * n:(c + 1) * n], level, 2.0**40), 10 + c)
+           for c in range(chunks)]
+    y = H.helrm_embedding_lookup_multi(ctx, evk, emb, cts)
+    got = H.helrm_decrypt(ctx, sk, y, 416)
+    want = np.concatenate([tables[t][0][idx[t]].astype(np.float64) for t in range(26)])
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record()
+    for _ in range(reps):
+        H.helrm_embedding_lookup_multi(ctx, evk, emb, cts)
+    s1.record()
+    torch.cuda.synchronize()
+    return {"ciphertexts": chunks, "selector_slots": 26 * rows, "outputs": 416, "level": level,
+            "ms_per_lookup": s0.elapsed_time(s1) / reps, "max_abs_err": float(np.max(np.abs(got - want)))}
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["ntt", "rotate", "matvec"])
+    ap.add_argument("what", choices=["ntt", "rotate", "matvec", "multi"])
+    ap.add_argument("--cts", type=int, default=18)
     ap.add_argument("--D", type=int, default=256)
     ap.add_argument("--limbs", type=int, default=192)
     ap.add_argument("--level", type=int, default=8)
@@ -122,6 +162,8 @@ def main():
         r = bench_ntt(a.limbs, a.reps)
     elif a.what == "rotate":
         r = bench_rotate(a.level, a.reps)
+    elif a.what == "multi":
+        r = bench_multi(a.cts, a.level, a.reps)
     else:
         r = bench_matvec(a.D, a.level, a.reps)
     print(json.dumps(r))

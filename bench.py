@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=1000, help="served: requests per arrival rate")
     ap.add_argument("--rates", default="1,5,10,20,50,100,200", help="served: arrival rates (requests/s)")
+    ap.add_argument("--slots", type=int, default=2, help="served: batch slots (CUDA streams) of the batching server")
+    ap.add_argument("--max-batch", type=int, default=8, help="served: requests per batch of the batching server")
     return ap.parse_args()
 
 
@@ -436,7 +438,8 @@ def run_served(args):
     cmodel = [0] * n_uci + [1] * n_crit
     keys = [H.helrm_model_keygen(ctx, models[m], 20_000 * (rank + 1) + c) for c, m in enumerate(cmodel)]
     key_bytes = sum(H.helrm_evk_bytes(ctx, k[1]) for k in keys)
-    servers = {"batched": H.helrm_server_create(ctx, 2, 16, 0), "one_at_a_time": H.helrm_server_create(ctx, 1, 1, 0)}
+    servers = {"batched": H.helrm_server_create(ctx, args.slots, args.max_batch, 0),
+               "one_at_a_time": H.helrm_server_create(ctx, 1, 1, 0)}
     for srv in servers.values():
         for c, m in enumerate(cmodel):
             H.helrm_server_add_client(ctx, srv, models[m], keys[c][1])
@@ -482,7 +485,8 @@ def run_served(args):
                 "data": "synthetic (seeded Poisson traces; shapes of the paper's UCI/Criteo workloads)",
                 "config": {"workload": f"served: Poisson arrivals at {args.rates} requests/s, {args.requests} "
                                        "requests per rate, 80% UCI-shaped / 20% Criteo-shaped, 32 + 8 clients",
-                           "server": "2 batch slots (CUDA streams), up to 16 requests of one model per batch",
+                           "server": f"{args.slots} batch slots (CUDA streams), up to {args.max_batch} requests "
+                                     "of one model per batch",
                            "baseline_server": "1 slot, 1 request per batch (the plain path)",
                            "resident_key_bytes": key_bytes, "parallelism": f"replicas x{world}"},
                 "value_note": "inferences/s of the batching server at the highest arrival rate",

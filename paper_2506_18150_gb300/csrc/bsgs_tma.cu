@@ -85,14 +85,17 @@ struct TmaGals {
     u64 gal[64];          // Galois element of baby step b
 };
 
-// Stage layout (words): dig[DN][T] | kb[DN][T] | ka[DN][T] | c0[T] | dd[N2][T]
-// Pipeline depth: three stages when they fit two CTAs per SM (<= 108 KB of
-// stages each), else two (many digits: e.g. 5 digits and 4 giant steps make
-// 40 KB stages, and three of them would leave one CTA per SM).
+// Stage layout (words): dig[DN][T] | kb[DN][T] | ka[DN][T] | dd[N2][T].  The
+// gathered c0 word (L2-resident, one per thread) is not staged: each consumer
+// loads it itself one baby step ahead, which keeps the stage smaller.
+// Pipeline depth: as many stages (up to 4) as leave two CTAs per SM (at most
+// 108 KB of stages per CTA): the consumers stall on stages still in flight
+// (the copies' latency under load exceeds two steps of arithmetic), so every
+// extra stage the shared memory holds is time the copies get to land.
 template <int N2, int DN>
 struct Stage {
-    static constexpr int WORDS = (3 * DN + 1 + N2) * T;
-    static constexpr int S = (3 * WORDS * 8 <= 108 * 1024) ? 3 : 2;
+    static constexpr int WORDS = (3 * DN + N2) * T;
+    static constexpr int S = (4 * WORDS * 8 <= 108 * 1024) ? 4 : (3 * WORDS * 8 <= 108 * 1024) ? 3 : 2;
 };
 
 __device__ __forceinline__ void mbar_arrive(u64 *bar)
@@ -207,11 +210,11 @@ __global__ void __launch_bounds__(T + 32, 2) k_bsgs_tma(
                 st_gal[s] = (u32)bk.gal[b];
                 st_base[s] = src_base;
                 st_mask[s] = mask;
-                mbar_arrive_expect_tx(&full[s], (u32)(3 * DN + (qlimb ? 1 : 0) + nd) * T * 8);
+                mbar_arrive_expect_tx(&full[s], (u32)(3 * DN + nd) * T * 8);
             }
             __syncwarp();
-            // rows: DN digit rows, 2 DN key rows, the c0 row, the present diagonal rows
-            for (int cidx = lane; cidx < 3 * DN + 1 + N2; cidx += 32) {
+            // rows: DN digit rows, 2 DN key rows, the present diagonal rows
+            for (int cidx = lane; cidx < 3 * DN + N2; cidx += 32) {
                 const u64 *src = nullptr;
                 u64 *dst = nullptr;
                 if (cidx < DN) {
@@ -225,17 +228,12 @@ __global__ void __launch_bounds__(T + 32, 2) k_bsgs_tma(
                     const int j = cidx - 2 * DN;
                     src = key + ((size_t)(2 * j + 1) * nK + kx) * N + i0;
                     dst = st + (2 * DN + j) * T;
-                } else if (cidx == 3 * DN) {
-                    if (qlimb) {
-                        src = c0 + (size_t)l * N + src_base;
-                        dst = st + 3 * DN * T;
-                    }
                 } else {
-                    const int g = cidx - 3 * DN - 1;
+                    const int g = cidx - 3 * DN;
                     const int di = sgb[g * n1 + b];
                     if (di >= 0) {
                         src = diag[di] + (size_t)l * N + i0;
-                        dst = st + (3 * DN + 1 + g) * T;
+                        dst = st + (3 * DN + g) * T;
                     }
                 }
                 if (src) bulk_g2s(dst, src, T * 8, &full[s]);
@@ -274,8 +272,13 @@ __global__ void __launch_bounds__(T + 32, 2) k_bsgs_tma(
         }
     }
     const u32 xi = odd_of(i, logN);
+    const u64 *c0l = c0 + (size_t)l * N;
+    // phi(c0) word of the next baby step, loaded one step ahead (Q limbs only)
+    u64 c0_next = (qlimb && nb > 0) ? __ldg(c0l + auto_src_x(xi, logN, (u32)bk.gal[blist[0]])) : 0;
     u32 phase = 0;
     for (int k = 0, s = 0; k < nb; k++) {
+        const u64 c0v = c0_next;
+        if (qlimb && k + 1 < nb) c0_next = __ldg(c0l + auto_src_x(xi, logN, (u32)bk.gal[blist[k + 1]]));
         if (!mbar_wait_bounded(&full[s], phase)) {
             if (lane == 0) atomicExch(err, (int)HELRM_E_TIMEOUT);
             return;   // no CTA barrier follows, so leaving early cannot deadlock
@@ -291,13 +294,13 @@ __global__ void __launch_bounds__(T + 32, 2) k_bsgs_tma(
             t1.mac(d, st[(2 * DN + j) * T + tid], pi.q);
         }
         // + P phi(c0) on the Q limbs: pm = P R mod q, so the same REDC yields it
-        if (qlimb) t0.mac(st[3 * DN * T + src_loc], pm, pi.q);
+        if (qlimb) t0.mac(c0v, pm, pi.q);
         const u64 v0 = t0.reduce(pi.q, pi.qinv);
         const u64 v1 = t1.reduce(pi.q, pi.qinv);
         if (N2 <= 4) {   // few diagonals: take them into registers and release the stage first
             u64 dd[N2];
 #pragma unroll
-            for (int g = 0; g < N2; g++) dd[g] = (mask >> g) & 1u ? st[(3 * DN + 1 + g) * T + tid] : 0;
+            for (int g = 0; g < N2; g++) dd[g] = (mask >> g) & 1u ? st[(3 * DN + g) * T + tid] : 0;
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);   // this warp is done with stage s
 #pragma unroll
@@ -308,7 +311,7 @@ __global__ void __launch_bounds__(T + 32, 2) k_bsgs_tma(
         } else {         // many: read each as it is used (fewer live registers), then release
 #pragma unroll
             for (int g = 0; g < N2; g++) {
-                const u64 d = (mask >> g) & 1u ? st[(3 * DN + 1 + g) * T + tid] : 0;
+                const u64 d = (mask >> g) & 1u ? st[(3 * DN + g) * T + tid] : 0;
                 a0[g].mac(v0, d, pi.q);
                 a1[g].mac(v1, d, pi.q);
             }

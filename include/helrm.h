@@ -108,6 +108,14 @@ helrm_status helrm_ctx_memory_in_use(const helrm_ctx *ctx, uint64_t *bytes);
 helrm_status helrm_ctx_synchronize(helrm_ctx *ctx);
 /* Number of library kernels launched so far on this context. */
 helrm_status helrm_ctx_launch_count(const helrm_ctx *ctx, uint64_t *count);
+/* Self-test of the device-side timeout path (the paper has no counterpart).
+ * Every wait of the library's pipelined kernels on a shared-memory barrier is
+ * bounded: when it runs out, the kernel records HELRM_E_TIMEOUT in the
+ * context's error word and returns, and the next synchronising call reports
+ * it.  This call launches one CTA that waits, for at most `polls` polls
+ * (1..2^20), on a barrier that nothing arrives at, and so returns
+ * HELRM_E_TIMEOUT with the context still usable afterwards. */
+helrm_status helrm_ctx_wait_selftest(helrm_ctx *ctx, uint32_t polls);
 /* The NTT launch shapes the context chose when it was created: for limb
  * counts per launch <= 4, <= 16, <= 64 and above (out[2b], out[2b+1]), the
  * words per CTA tile and the CTA count, in multiples of the SM count, below

@@ -176,6 +176,16 @@ helrm_status helrm_ctx_launch_count(const helrm_ctx *ctx, uint64_t *count)
     });
 }
 
+helrm_status helrm_ctx_wait_selftest(helrm_ctx *ctx, uint32_t polls)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        HCHECK(polls >= 1 && polls <= (1u << 20), HELRM_E_INVAL, "polls must be in [1, 2^20]");
+        k::wait_probe(c, (long)polls);
+        c->check_device_errors();   // raises HELRM_E_TIMEOUT and clears the word
+    });
+}
+
 helrm_status helrm_ctx_ntt_tuning(const helrm_ctx *ctx, uint32_t *out)
 {
     return guard(ctx_or_null(ctx), [&] {

@@ -350,6 +350,23 @@ void launch_tma(Ctx *c, const TmaQueries &qs, int nq, const TmaGals &bk, const u
            c->d_pmod_mont.u(), c->d_pinfo.as<PrimeInfo>(), c->d_err.as<int>());
 }
 
+// The bounded wait of the pipeline on a barrier that no thread ever arrives
+// at: after `limit` polls it records HELRM_E_TIMEOUT in the error word and
+// returns, exactly as a stalled stage would (self-test of the timeout path).
+__global__ void k_wait_probe(long limit, int *err)
+{
+    pdl_begin();
+    __shared__ __align__(8) u64 bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    bool ok = false;
+    for (long it = 0; it < limit && !ok; it++) ok = mbar_try_wait(&bar, 0);
+    if (!ok && threadIdx.x == 0) atomicExch(err, (int)HELRM_E_TIMEOUT);
+}
+
 }  // namespace
 
 namespace k {
@@ -401,6 +418,13 @@ void bsgs_tma_batch(Ctx *c, const std::vector<BsgsQuery> &qv, const u64 *const *
         c->launches++;
         CUDA_CHECK(cudaGetLastError());
     }
+}
+
+void wait_probe(Ctx *c, long limit)
+{
+    launch(c, k_wait_probe, 1, 32, 0, limit, c->d_err.as<int>());
+    c->launches++;
+    CUDA_CHECK(cudaGetLastError());
 }
 
 void bsgs_tma(Ctx *c, u64 *inner, const u64 *digits, const u64 *c0, const u64 *c1, const SwitchKey *const *keys,

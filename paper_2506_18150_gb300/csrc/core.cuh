@@ -449,6 +449,9 @@ void bsgs_tma_batch(Ctx *c, const std::vector<BsgsQuery> &qs, const u64 *const *
                     const u64 *gals,
                     const u64 *const *d_diag_ptrs, const int *d_gb_index, int n_diag, int n_keys, int n1, int n2,
                     int level);
+// one CTA waits (at most `limit` polls) on an mbarrier nothing arrives at, then
+// records HELRM_E_TIMEOUT in the context's error word
+void wait_probe(Ctx *c, long limit);
 // rescale helper: coefficient-form last limb -> centred residues for ell limbs
 void rescale_spread(Ctx *c, u64 *out, const u64 *last_coef, int level, int n_polys = 1);
 // random

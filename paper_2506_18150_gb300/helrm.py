@@ -125,6 +125,7 @@ _SIGS = {
     "helrm_server_run": [_vp, _vp, C.c_uint32, _dp, _u32p, _pp, _pp, _pp, _dp, C.c_void_p],
     "helrm_ctx_profile": [_vp, C.c_int],
     "helrm_ctx_ntt_tuning": [_vp, _u32p],
+    "helrm_ctx_wait_selftest": [_vp, C.c_uint32],
     "helrm_ctx_profile_report": [_vp, C.c_char_p, C.c_uint64, _u64p],
 }
 
@@ -611,6 +612,11 @@ def helrm_rescale_noalloc(ctx, d_in: int, d_out: int, level: int, n_polys: int):
     """Rescale without allocating: device pointers in (n_polys x (level+1) x N) and
     out (n_polys x level x N), NTT domain; scratch is a static 1 MiB device array."""
     _check(ctx, lib().helrm_rescale_noalloc(ctx.ptr, C.c_void_p(d_in), C.c_void_p(d_out), level, n_polys))
+
+
+def helrm_ctx_wait_selftest(ctx, polls: int):
+    """Raises HelrmError(HELRM_E_TIMEOUT): a bounded device wait that ran out."""
+    _check(ctx, lib().helrm_ctx_wait_selftest(ctx.ptr, polls))
 
 
 def helrm_ctx_ntt_tuning(ctx):

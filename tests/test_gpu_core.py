@@ -214,3 +214,20 @@ def test_memory_cap_gives_nomem(env):
     finally:
         H.helrm_ctx_set_memory_cap(ctx, 0)
     H.helrm_add(ctx, a, a)                                 # usable again
+
+
+def test_bounded_device_wait_reports_timeout_and_context_survives(env):
+    """A device-side wait that never completes ends after its poll limit with
+    HELRM_E_TIMEOUT (no hang, no trap), and the context keeps working."""
+    from paper_2506_18150_gb300 import helrm as H
+    ctx, p, sk, evk = env[0], env[1], env[2], env[3]
+    for polls in (1, 1000):
+        with pytest.raises(H.HelrmError) as e:
+            H.helrm_ctx_wait_selftest(ctx, polls)
+        assert e.value.name == "HELRM_E_TIMEOUT"
+    with pytest.raises(H.HelrmError) as e:
+        H.helrm_ctx_wait_selftest(ctx, 0)
+    assert e.value.name == "HELRM_E_INVAL"
+    a, _, _ = fresh(env, 3, 71)                   # the context still encrypts and rescales
+    H.helrm_rescale(ctx, a)
+    H.helrm_ctx_synchronize(ctx)

@@ -246,8 +246,9 @@ helrm_status helrm_ptct_matvec(helrm_ctx *ctx, const helrm_evk *evk, const helrm
 
 /* ------------------------------------------------------- embeddings (a11) */
 /* Pack n_tables compressed tables block-diagonally (Sec. 4.2.2): table t with
- * card[t] rows keeps one plain table if card[t] <= base_p, else
- * l_t = ceil(log_p card[t]) digit tables of base_p rows; tables[t] points to
+ * card[t] rows keeps one plain table if card[t] <= threshold (threshold 0
+ * means base_p: Sec. 5.2 compresses only the tables above a size threshold),
+ * else l_t = ceil(log_p card[t]) digit tables of base_p rows; tables[t] points to
  * its digit tables stacked (sum of rows) x dim, FP32 row-major.  Output rows
  * of table t are [out_offset + dim t, out_offset + dim (t+1)) of a vector of
  * period out_pad; the selector vector (all digits' one-hots concatenated,
@@ -259,9 +260,9 @@ helrm_status helrm_ptct_matvec(helrm_ctx *ctx, const helrm_evk *evk, const helrm
  * (helrm_emb_matrix); the lookup is the sum of the per-ciphertext products
  * (helrm_embedding_lookup_multi). */
 helrm_status helrm_emb_prepare(helrm_ctx *ctx, uint32_t n_tables, const uint64_t *card, uint32_t base_p,
-                               uint32_t dim, const float *const *tables, uint32_t out_offset,
-                               uint32_t out_pad, int32_t level, double ct_scale, double target_scale,
-                               helrm_emb **out);
+                               uint64_t threshold, uint32_t dim, const float *const *tables,
+                               uint32_t out_offset, uint32_t out_pad, int32_t level, double ct_scale,
+                               double target_scale, helrm_emb **out);
 /* Client packing: little-endian base-p digits of each index, one one-hot per
  * digit, concatenated; slots_out gets n_slots values (selector replicated with
  * its period).  For a selector of C > 1 ciphertexts n_slots must be C x n:
@@ -301,40 +302,53 @@ typedef struct {
     uint32_t dim;                    /* must be 16 */
     const float *const *tables;      /* as for helrm_emb_prepare */
     int32_t interaction;             /* 0 = pairwise dot, 1 = concatenation */
+    uint64_t threshold;              /* tables with more rows are digit-decomposed (0 = base_p) */
 } helrm_model_desc;
 
 /* Compile the model: layouts, as-late-as-possible levels (the logit ends at
  * level 0), all diagonals, biases and masks encoded on the device.
  * Errors: HELRM_E_PARAM if the chain is too short or a layout exceeds n. */
 helrm_status helrm_model_create(helrm_ctx *ctx, const helrm_model_desc *desc, helrm_model **out);
-/* info_out[0..8] = level of ct_dense, level of ct_sel, level of z, level of
- * the top input, dense period, selector period, W_z, W_u, plaintext count. */
+/* info_out[0..9] = level of ct_dense, level of ct_sel, level of z, level of
+ * the top input, dense period, selector period, W_z, W_u, plaintext count,
+ * n_sel (the number of selector ciphertexts a query carries; 1 unless the
+ * selector is wider than n slots).  The selector period is that of the
+ * first selector ciphertext. */
 helrm_status helrm_model_info(const helrm_model *m, uint32_t *info_out);
 helrm_status helrm_model_rotations(const helrm_model *m, int32_t *steps_out, uint32_t *n_out);
 /* Replace / read all encoded plaintexts (count x N signed coefficients) in
  * the canonical order: per bottom layer its diagonals then its bias; the
- * embedding diagonals; (dot) the ones block and masks 0..S; per top layer its
+ * embedding diagonals (selector ciphertext by selector ciphertext); (dot) the
+ * ones block and masks 0..S; per top layer its
  * diagonals then its bias. */
 helrm_status helrm_model_import_plaintexts(helrm_ctx *ctx, helrm_model *m, const int64_t *coeffs,
                                            uint32_t count);
 helrm_status helrm_model_export_plaintexts(helrm_ctx *ctx, const helrm_model *m, int64_t *coeffs,
                                            uint32_t count);
 /* Client side (a1): pack, encode and encrypt one query: ct_dense with `seed`
- * at its level, ct_sel with seed + 1.  dense: n_dense values; indices: one
- * per table. */
+ * at its level; ct_sel must hold n_sel (helrm_model_info [9]) handles and
+ * receives the selector ciphertexts, ciphertext k encrypted with
+ * seed + 1 + k.  dense: n_dense values; indices: one per table. */
 helrm_status helrm_encrypt_query(helrm_ctx *ctx, const helrm_evk *evk, const helrm_model *m,
                                  const double *dense, const uint64_t *indices, uint64_t seed,
                                  helrm_ct **ct_dense, helrm_ct **ct_sel);
-/* Server side (a2-a13): the encrypted logit (slot 0, level 0). */
+/* Server side (a2-a13): the encrypted logit (slot 0, level 0).  For a model
+ * with n_sel = 1; helrm_infer_multi takes the general case. */
 helrm_status helrm_infer(helrm_ctx *ctx, const helrm_evk *evk, const helrm_model *m,
                          const helrm_ct *ct_dense, const helrm_ct *ct_sel, helrm_ct **logit);
+/* Server side for a query whose selector spans n_sel ciphertexts (the
+ * model's n_sel, else HELRM_E_INVAL): the embedding lookup is the sum of the
+ * n_sel per-ciphertext products; the rest is helrm_infer. */
+helrm_status helrm_infer_multi(helrm_ctx *ctx, const helrm_evk *evk, const helrm_model *m,
+                               const helrm_ct *ct_dense, const helrm_ct *const *ct_sel, uint32_t n_sel,
+                               helrm_ct **logit);
 /* Client side (a14): decrypt slot 0 and apply the sigmoid. */
 helrm_status helrm_decrypt_logit(helrm_ctx *ctx, const helrm_sk *sk, const helrm_ct *logit,
                                  double *logit_out, double *prob_out);
 /* The whole protocol for n_queries queries from host buffers: pack, encode,
  * encrypt, infer, decrypt.  dense: n_queries x n_dense; indices: n_queries x
  * n_tables; logits_out / probs_out: n_queries (probs_out may be NULL).
- * Query q uses seed + 2q. */
+ * Query q is encrypted with seed + (1 + n_sel) q (seed + 2q for n_sel = 1). */
 helrm_status helrm_infer_e2e(helrm_ctx *ctx, const helrm_sk *sk, const helrm_evk *evk,
                              const helrm_model *m, const double *dense, const uint64_t *indices,
                              uint32_t n_queries, uint64_t seed, double *logits_out, double *probs_out);
@@ -374,14 +388,16 @@ helrm_status helrm_batch_create(helrm_ctx *ctx, const helrm_model *m, uint32_t n
  * Inputs must keep the levels and scales of the captured call.  Must not be
  * combined with helrm_ctx_profile. */
 helrm_status helrm_batch_set_graph(helrm_ctx *ctx, helrm_batch *b, int enable);
-/* Server side for the n queries of the batch: ct_dense[q], ct_sel[q] at the
- * model's levels (helrm_encrypt_query with evks[q]); logits[q] receives the
+/* Server side for the n queries of the batch: ct_dense[q] and the n_sel
+ * selector ciphertexts ct_sel[q n_sel + k] at the model's levels
+ * (helrm_encrypt_query with evks[q]); logits[q] receives the
  * encrypted logit of query q (level 0), as helrm_infer.  Stream ordered, no
  * synchronisation. */
 helrm_status helrm_infer_batch(helrm_ctx *ctx, const helrm_batch *b, const helrm_ct *const *ct_dense,
                                const helrm_ct *const *ct_sel, helrm_ct **logits);
 /* The whole protocol for the batch from device buffers: query q (d_dense row
- * q, d_indices row q) is packed and encrypted under evks[q] with seed + 2q,
+ * q, d_indices row q) is packed and encrypted under evks[q] with
+ * seed + (1 + n_sel) q,
  * the batch is inferred in lockstep, and logit q is decrypted with sks[q]
  * into d_logits[q].  Nothing is copied to the host; no synchronisation. */
 helrm_status helrm_infer_batch_e2e_device(helrm_ctx *ctx, const helrm_batch *b, const helrm_sk *const *sks,
@@ -401,7 +417,8 @@ helrm_status helrm_infer_batch_e2e_device(helrm_ctx *ctx, const helrm_batch *b, 
 helrm_status helrm_server_create(helrm_ctx *ctx, uint32_t n_slots, uint32_t max_batch, uint64_t mem_budget,
                                  helrm_server **out);
 /* Register a client: the model its queries use and its evaluation keys
- * (both must outlive the server).  *client_id receives its index. */
+ * (both must outlive the server).  *client_id receives its index.  The
+ * model's selector must fit one ciphertext (n_sel = 1), else HELRM_E_INVAL. */
 helrm_status helrm_server_add_client(helrm_ctx *ctx, helrm_server *s, const helrm_model *m, const helrm_evk *evk,
                                      uint32_t *client_id);
 typedef struct {

@@ -48,15 +48,22 @@ def digits(i: int, p: int, ell: int) -> list:
     return out
 
 
-def selector_layout(cards, p):
+def compressed(k: int, p: int, threshold=None) -> bool:
+    """Whether a table of k rows is digit-decomposed: k > threshold (Sec. 5.2:
+    tables with more rows than a threshold are compressed, base p = 4 there);
+    threshold None means p, so a table that fits one digit stays plain."""
+    return k > (p if threshold is None else threshold)
+
+
+def selector_layout(cards, p, threshold=None):
     """[(table, digit, offset, width)]: table t in order, digit j ascending.
 
-    A table with k <= p keeps its plain one-hot of width k; a larger table gets
-    l_t one-hots of width p.
+    An uncompressed table keeps its plain one-hot of width k; a compressed one
+    gets l_t one-hots of width p.
     """
     out, off = [], 0
     for t, k in enumerate(cards):
-        if k <= p:
+        if not compressed(k, p, threshold):
             out.append((t, 0, off, k))
             off += k
         else:
@@ -66,13 +73,13 @@ def selector_layout(cards, p):
     return out, off
 
 
-def selector_vector(cards, p, indices) -> np.ndarray:
+def selector_vector(cards, p, indices, threshold=None) -> np.ndarray:
     """The concatenated one-hot digit selectors of one query."""
-    lay, width = selector_layout(cards, p)
+    lay, width = selector_layout(cards, p, threshold)
     v = np.zeros(width)
     for (t, j, off, w) in lay:
         i = int(indices[t])
-        if cards[t] <= p:
+        if not compressed(cards[t], p, threshold):
             v[off + i] = 1.0
         else:
             v[off + digits(i, p, num_digits(cards[t], p))[j]] = 1.0
@@ -85,11 +92,11 @@ def replicate(v: np.ndarray, period: int, n: int) -> np.ndarray:
     return vp[np.arange(n) % period]
 
 
-def embedding_matrix(cards, p, tables, row_offset: int, n_rows: int, dim: int = DIM) -> np.ndarray:
+def embedding_matrix(cards, p, tables, row_offset: int, n_rows: int, dim: int = DIM, threshold=None) -> np.ndarray:
     """Block-diagonal packing: table t's transposed compressed tables occupy
     rows [row_offset + dim t, row_offset + dim (t+1)) and the selector columns
     of its digits (torch.block_diag of the per-table [C_0^T ... C_{l-1}^T])."""
-    lay, width = selector_layout(cards, p)
+    lay, width = selector_layout(cards, p, threshold)
     M = np.zeros((n_rows, width))
     for (t, j, off, w) in lay:
         C = np.asarray(tables[t][j], dtype=np.float64)
@@ -100,11 +107,11 @@ def embedding_matrix(cards, p, tables, row_offset: int, n_rows: int, dim: int = 
 # --------------------------------------------------------------------------
 # Cleartext FP64 DLRM: the plain definition of the result
 # --------------------------------------------------------------------------
-def embedding_cleartext(cards, p, tables, indices):
+def embedding_cleartext(cards, p, tables, indices, threshold=None):
     out = []
     for t, k in enumerate(cards):
         i = int(indices[t])
-        if k <= p:
+        if not compressed(k, p, threshold):
             out.append(np.asarray(tables[t][0][i], dtype=np.float64))
         else:
             ds = digits(i, p, num_digits(k, p))
@@ -120,7 +127,7 @@ def dlrm_cleartext(spec, w, dense, indices):
     h = np.asarray(dense, dtype=np.float64)
     for W, b in zip(w.bottom_W, w.bottom_b):
         h = (W @ h + b) ** 2
-    embs = embedding_cleartext(spec.cards, spec.base, w.tables, indices)
+    embs = embedding_cleartext(spec.cards, spec.base, w.tables, indices, spec.threshold)
     blocks = [h] + embs
     if spec.interaction == "dot":
         x = [h] + [np.array([blocks[a] @ blocks[c]]) for a in range(len(blocks))
@@ -163,6 +170,8 @@ class Compiled:
     S: int = 0                       # dot: number of block shifts
     bottom: list = field(default_factory=list)
     emb: linear.PtMatrix | None = None
+    # a selector wider than n slots: one matrix per ciphertext (emb is None)
+    emb_chunks: list = field(default_factory=list)
     ones: np.ndarray | None = None
     masks: list = field(default_factory=list)       # dot: mask_0 .. mask_S
     mask_scale: float = 0.0
@@ -172,11 +181,19 @@ class Compiled:
         st = set()
         for lay in self.bottom + self.top:
             st |= set(linear.rotation_steps(lay.pm))
-        st |= set(linear.rotation_steps(self.emb))
+        for pm in self.emb_pms():
+            st |= set(linear.rotation_steps(pm))
         if self.spec.interaction == "dot":
             st.add(-DIM * self.Bp)
             st |= {DIM * s for s in range(1, self.S + 1)}
         return sorted(st)
+
+    def emb_pms(self):
+        return [self.emb] if self.emb is not None else list(self.emb_chunks)
+
+    def n_sel(self) -> int:
+        """Ciphertexts of the selector (1 unless it is wider than n slots)."""
+        return 1 if self.emb is not None else len(self.emb_chunks)
 
     def plaintexts(self):
         """Every plaintext of the model, in the canonical order: per bottom
@@ -186,7 +203,8 @@ class Compiled:
         out = []
         for lay in self.bottom:
             out += [lay.pm.pts[k] for k in lay.pm.ordered_keys()] + [lay.bias]
-        out += [self.emb.pts[k] for k in self.emb.ordered_keys()]
+        for pm in self.emb_pms():
+            out += [pm.pts[k] for k in pm.ordered_keys()]
         if self.spec.interaction == "dot":
             out += [self.ones] + list(self.masks)
         for lay in self.top:
@@ -233,9 +251,9 @@ def compile_model(p: ckks.Params, spec, w) -> Compiled:
         raise ValueError(f"model needs {lvl_dense} levels, chain has {p.L}")
     Bp = B + 1 if dot else B
     W_z = linear.pow2ceil(DIM * Bp)
-    lay_sel, sel_w = selector_layout(spec.cards, spec.base)
+    lay_sel, sel_w = selector_layout(spec.cards, spec.base, spec.threshold)
     c = Compiled(spec, lvl_dense, lvl_sel, lvl_z, lvl_u, linear.pow2ceil(spec.n_dense),
-                 linear.pow2ceil(sel_w), W_z, Bp=Bp)
+                 min(linear.pow2ceil(sel_w), p.n), W_z, Bp=Bp)
     if dot:
         c.W2 = linear.pow2ceil(2 * DIM * Bp)
         c.S = Bp // 2
@@ -261,8 +279,11 @@ def compile_model(p: ckks.Params, spec, w) -> Compiled:
     assert lvl == lvl_z
     scale_b = scale
     # Embedding lookup (block-diagonal, rows [16, 16 (T+1)) of the z layout)
-    M = embedding_matrix(spec.cards, spec.base, w.tables, DIM, DIM * B)
-    c.emb = linear.prepare(p, M, c.p_sel, W_z, lvl_sel, delta, scale_b)
+    M = embedding_matrix(spec.cards, spec.base, w.tables, DIM, DIM * B, threshold=spec.threshold)
+    if sel_w <= p.n:
+        c.emb = linear.prepare(p, M, c.p_sel, W_z, lvl_sel, delta, scale_b)
+    else:
+        c.emb_chunks = prepare_multi(p, M, W_z, lvl_sel, delta, scale_b)
     if dot:
         ones = np.zeros(W_z)
         ones[DIM * B: DIM * B + DIM] = 1.0
@@ -306,16 +327,23 @@ def compile_model(p: ckks.Params, spec, w) -> Compiled:
 # --------------------------------------------------------------------------
 def query_slots(p: ckks.Params, c: Compiled, dense, indices):
     """Client packing: dense features with period p_dense; concatenated digit
-    one-hots with period p_sel."""
+    one-hots with period p_sel (a list of per-ciphertext slot vectors when the
+    selector is wider than n slots)."""
     xd = replicate(np.asarray(dense, dtype=np.float64), c.p_dense, p.n)
-    xs = replicate(selector_vector(c.spec.cards, c.spec.base, indices), c.p_sel, p.n)
-    return xd, xs
+    sel = selector_vector(c.spec.cards, c.spec.base, indices, c.spec.threshold)
+    if c.emb is None:
+        return xd, chunk_slots(sel, p.n)
+    return xd, replicate(sel, c.p_sel, p.n)
 
 
 def encrypt_query(p, keys, c: Compiled, dense, indices, seed: int):
-    """ct_dense with `seed` at lvl_dense, ct_sel with `seed + 1` at lvl_sel, both at Delta."""
+    """ct_dense with `seed` at lvl_dense, ct_sel with `seed + 1` at lvl_sel, both at
+    Delta; a selector of several ciphertexts uses seeds seed + 1, seed + 2, ..."""
     xd, xs = query_slots(p, c, dense, indices)
     ct_d = ckks.encrypt(p, keys, ckks.encode_real(p, xd, p.delta), c.lvl_dense, p.delta, seed)
+    if c.emb is None:
+        return ct_d, [ckks.encrypt(p, keys, ckks.encode_real(p, x, p.delta), c.lvl_sel, p.delta, seed + 1 + k)
+                      for k, x in enumerate(xs)]
     ct_s = ckks.encrypt(p, keys, ckks.encode_real(p, xs, p.delta), c.lvl_sel, p.delta, seed + 1)
     return ct_d, ct_s
 
@@ -354,11 +382,15 @@ def dot_interaction(p, keys, c: Compiled, z: ckks.Ct) -> ckks.Ct:
     return ckks.rescale(p, ckks.relinearize(p, keys, acc, lvl, p.delta * p.delta))
 
 
-def infer(p, keys, c: Compiled, ct_dense: ckks.Ct, ct_sel: ckks.Ct) -> ckks.Ct:
+def infer(p, keys, c: Compiled, ct_dense: ckks.Ct, ct_sel) -> ckks.Ct:
+    """ct_sel: one ciphertext, or the list of them for a selector wider than n slots."""
     h = ct_dense
     for lay in c.bottom:
         h = _dense_layer(p, keys, lay, h)
-    e = linear.matvec(p, keys, c.emb, ct_sel)
+    if c.emb is None:
+        e = lookup_multi(p, keys, c.emb_chunks, ct_sel)
+    else:
+        e = linear.matvec(p, keys, c.emb, ct_sel)
     z = ckks.add(p, h, e)
     if c.spec.interaction == "dot":
         z = ckks.add_pt(p, z, c.ones, z.scale)

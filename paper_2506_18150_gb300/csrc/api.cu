@@ -12,7 +12,7 @@ namespace helrm {
 Ctx *ctx_create(const helrm_params *p, int device, void *stream);
 struct Emb;
 struct Model;
-Emb *emb_prepare(Ctx *c, const std::vector<u64> &cards, int base, int dim, const float *const *tables,
+Emb *emb_prepare(Ctx *c, const std::vector<u64> &cards, int base, u64 threshold, int dim, const float *const *tables,
                  int out_offset, int out_pad, int level, double ct_scale, double target_scale);
 void emb_pack_host(const Emb *e, const u64 *indices, std::vector<double> &sel);
 const PtMatrix *emb_matrix_of(const Emb *e);
@@ -26,9 +26,10 @@ Model *model_create(Ctx *c, const helrm_model_desc *d);
 void model_import(Ctx *c, Model *m, const i64 *coeffs, u32 count);
 void model_export(Ctx *c, Model *m, i64 *coeffs, u32 count);
 Ciphertext *model_infer(Ctx *c, const EvalKey *evk, const Model *m, const Ciphertext *ct_dense,
-                        const Ciphertext *ct_sel);
+                        const std::vector<const Ciphertext *> &ct_sel);
 void model_encrypt_query(Ctx *c, const EvalKey *evk, const Model *m, const double *dense, const u64 *indices,
-                         u64 seed, Ciphertext **ct_dense, Ciphertext **ct_sel, bool on_device);
+                         u64 seed, Ciphertext **ct_dense, std::vector<Ciphertext *> &ct_sel, bool on_device);
+int model_n_sel(const Model *m);
 void model_info(const Model *m, u32 *o);
 std::vector<int> model_rotations(const Model *m);
 std::vector<std::pair<int, int>> model_key_levels(const Model *m, int *relin_level);
@@ -548,14 +549,15 @@ helrm_status helrm_ptct_matvec(helrm_ctx *ctx, const helrm_evk *evk, const helrm
 }
 
 // ------------------------------------------------------------------ embeddings
-helrm_status helrm_emb_prepare(helrm_ctx *ctx, uint32_t n_tables, const uint64_t *card, uint32_t base_p, uint32_t dim,
-                               const float *const *tables, uint32_t out_offset, uint32_t out_pad, int32_t level,
-                               double ct_scale, double target_scale, helrm_emb **out)
+helrm_status helrm_emb_prepare(helrm_ctx *ctx, uint32_t n_tables, const uint64_t *card, uint32_t base_p,
+                               uint64_t threshold, uint32_t dim, const float *const *tables, uint32_t out_offset,
+                               uint32_t out_pad, int32_t level, double ct_scale, double target_scale, helrm_emb **out)
 {
     if (out) *out = nullptr;
     return guard(ctx_or_null(ctx), [&] {
         HCHECK(out && card && n_tables, HELRM_E_INVAL, "NULL argument");
-        *out = (helrm_emb *)emb_prepare(C(ctx), std::vector<u64>(card, card + n_tables), (int)base_p, (int)dim,
+        *out = (helrm_emb *)emb_prepare(C(ctx), std::vector<u64>(card, card + n_tables), (int)base_p, threshold,
+                                        (int)dim,
                                         tables, (int)out_offset, (int)out_pad, level, ct_scale, target_scale);
     });
 }
@@ -678,26 +680,63 @@ helrm_status helrm_model_export_plaintexts(helrm_ctx *ctx, const helrm_model *m,
 helrm_status helrm_encrypt_query(helrm_ctx *ctx, const helrm_evk *evk, const helrm_model *m, const double *dense,
                                  const uint64_t *indices, uint64_t seed, helrm_ct **ct_dense, helrm_ct **ct_sel)
 {
+    const int ns = (m && ((const Handle *)m)->kind == KIND_MODEL) ? model_n_sel((const Model *)m) : 1;
     if (ct_dense) *ct_dense = nullptr;
-    if (ct_sel) *ct_sel = nullptr;
+    if (ct_sel)
+        for (int k2 = 0; k2 < ns; k2++) ct_sel[k2] = nullptr;
     return guard(ctx_or_null(ctx), [&] {
         HCHECK(dense && indices && ct_dense && ct_sel, HELRM_E_INVAL, "NULL argument");
-        Ciphertext *a, *b;
-        model_encrypt_query(C(ctx), EVK(evk), MOD(m), dense, indices, seed, &a, &b, false);
+        Ciphertext *a;
+        std::vector<Ciphertext *> b;
+        model_encrypt_query(C(ctx), EVK(evk), MOD(m), dense, indices, seed, &a, b, false);
         *ct_dense = (helrm_ct *)a;
-        *ct_sel = (helrm_ct *)b;
+        for (size_t k2 = 0; k2 < b.size(); k2++) ct_sel[k2] = (helrm_ct *)b[k2];
     });
 }
 
 helrm_status helrm_infer(helrm_ctx *ctx, const helrm_evk *evk, const helrm_model *m, const helrm_ct *ct_dense,
                          const helrm_ct *ct_sel, helrm_ct **logit)
 {
+    return helrm_infer_multi(ctx, evk, m, ct_dense, &ct_sel, 1, logit);
+}
+
+helrm_status helrm_infer_multi(helrm_ctx *ctx, const helrm_evk *evk, const helrm_model *m, const helrm_ct *ct_dense,
+                               const helrm_ct *const *ct_sel, uint32_t n_sel, helrm_ct **logit)
+{
     if (logit) *logit = nullptr;
     return guard(ctx_or_null(ctx), [&] {
-        HCHECK(logit, HELRM_E_INVAL, "logit is NULL");
-        *logit = (helrm_ct *)model_infer(C(ctx), EVK(evk), MOD(m), CT(ct_dense), CT(ct_sel));
+        HCHECK(logit && ct_sel, HELRM_E_INVAL, "NULL argument");
+        std::vector<const Ciphertext *> s;
+        for (u32 k2 = 0; k2 < n_sel; k2++) s.push_back(CT(ct_sel[k2]));
+        *logit = (helrm_ct *)model_infer(C(ctx), EVK(evk), MOD(m), CT(ct_dense), s);
     });
 }
+
+namespace {
+// one query's client side + server side + decryption; query q of a run uses
+// the seeds seed + (1 + n_sel) q ... (a fresh seed per ciphertext)
+struct QueryCts {
+    std::unique_ptr<Ciphertext> dense;
+    std::vector<std::unique_ptr<Ciphertext>> sel;
+    std::vector<const Ciphertext *> sel_ptrs() const
+    {
+        std::vector<const Ciphertext *> v;
+        for (auto &p : sel) v.push_back(p.get());
+        return v;
+    }
+};
+QueryCts encrypt_one(Ctx *c, const EvalKey *evk, const Model *m, const double *dense, const u64 *indices, u64 seed,
+                     bool on_device)
+{
+    Ciphertext *a;
+    std::vector<Ciphertext *> b;
+    model_encrypt_query(c, evk, m, dense, indices, seed, &a, b, on_device);
+    QueryCts r;
+    r.dense.reset(a);
+    for (auto *p : b) r.sel.emplace_back(p);
+    return r;
+}
+}  // namespace
 
 helrm_status helrm_decrypt_logit(helrm_ctx *ctx, const helrm_sk *sk, const helrm_ct *logit, double *logit_out,
                                  double *prob_out)
@@ -720,11 +759,10 @@ helrm_status helrm_infer_e2e(helrm_ctx *ctx, const helrm_sk *sk, const helrm_evk
         Model *mm = MOD(m);
         HCHECK(dense && indices && logits_out, HELRM_E_INVAL, "NULL argument");
         const size_t nd = model_n_dense(mm), nt = model_n_tables(mm);
+        const u64 stride = 1 + (u64)model_n_sel(mm);
         for (u32 q = 0; q < n_queries; q++) {
-            Ciphertext *a, *b;
-            model_encrypt_query(c, EVK(evk), mm, dense + q * nd, indices + q * nt, seed + 2ull * q, &a, &b, false);
-            std::unique_ptr<Ciphertext> ca(a), cb(b);
-            std::unique_ptr<Ciphertext> y(model_infer(c, EVK(evk), mm, ca.get(), cb.get()));
+            QueryCts x = encrypt_one(c, EVK(evk), mm, dense + q * nd, indices + q * nt, seed + stride * q, false);
+            std::unique_ptr<Ciphertext> y(model_infer(c, EVK(evk), mm, x.dense.get(), x.sel_ptrs()));
             double v = 0;
             decrypt_slots(c, SK(sk), y.get(), &v, 1);
             logits_out[q] = v;
@@ -742,11 +780,10 @@ helrm_status helrm_infer_e2e_device(helrm_ctx *ctx, const helrm_sk *sk, const he
         Model *mm = MOD(m);
         HCHECK(d_dense && d_indices && d_logits, HELRM_E_INVAL, "NULL argument");
         const size_t nd = model_n_dense(mm), nt = model_n_tables(mm);
+        const u64 stride = 1 + (u64)model_n_sel(mm);
         for (u32 q = 0; q < n_queries; q++) {
-            Ciphertext *a, *b;
-            model_encrypt_query(c, EVK(evk), mm, d_dense + q * nd, d_indices + q * nt, seed + 2ull * q, &a, &b, true);
-            std::unique_ptr<Ciphertext> ca(a), cb(b);
-            std::unique_ptr<Ciphertext> y(model_infer(c, EVK(evk), mm, ca.get(), cb.get()));
+            QueryCts x = encrypt_one(c, EVK(evk), mm, d_dense + q * nd, d_indices + q * nt, seed + stride * q, true);
+            std::unique_ptr<Ciphertext> y(model_infer(c, EVK(evk), mm, x.dense.get(), x.sel_ptrs()));
             decrypt_slots_device(c, SK(sk), y.get(), d_logits + q, 1);
         }
         if (d_probs) k::sigmoid(c, d_probs, d_logits, (int)n_queries);
@@ -783,11 +820,10 @@ helrm_status helrm_infer_batch(helrm_ctx *ctx, const helrm_batch *b, const helrm
     return guard(ctx_or_null(ctx), [&] {
         Batch *bt = BAT(b);
         HCHECK(ct_dense && ct_sel && logits, HELRM_E_INVAL, "NULL argument");
+        const size_t ns = (size_t)model_n_sel(batch_model(bt));
         std::vector<const Ciphertext *> d, s;
-        for (size_t q = 0; q < n; q++) {
-            d.push_back(CT(ct_dense[q]));
-            s.push_back(CT(ct_sel[q]));
-        }
+        for (size_t q = 0; q < n; q++) d.push_back(CT(ct_dense[q]));
+        for (size_t r = 0; r < n * ns; r++) s.push_back(CT(ct_sel[r]));
         std::vector<Ciphertext *> y = batch_uses_graph(bt) ? model_infer_batch_graph(C(ctx), bt, d, s)
                                                            : model_infer_batch(C(ctx), bt, d, s);
         for (size_t q = 0; q < n; q++) logits[q] = (helrm_ct *)y[q];
@@ -806,16 +842,14 @@ helrm_status helrm_infer_batch_e2e_device(helrm_ctx *ctx, const helrm_batch *b, 
         const size_t n = batch_size(bt), nd = model_n_dense((Model *)mm), nt = model_n_tables((Model *)mm);
         std::vector<const SecretKey *> sk;
         for (size_t q = 0; q < n; q++) sk.push_back(SK(sks[q]));
-        std::vector<std::unique_ptr<Ciphertext>> a, s;
+        const u64 stride = 1 + (u64)model_n_sel(mm);
+        std::vector<QueryCts> qc;
         std::vector<const Ciphertext *> ad, sd;
         for (size_t q = 0; q < n; q++) {   // client side: each client packs and encrypts its own query
-            Ciphertext *x, *y;
-            model_encrypt_query(c, batch_evk(bt, q), mm, d_dense + q * nd, d_indices + q * nt, seed + 2ull * q, &x, &y,
-                                true);
-            a.emplace_back(x);
-            s.emplace_back(y);
-            ad.push_back(x);
-            sd.push_back(y);
+            qc.push_back(encrypt_one(c, batch_evk(bt, q), mm, d_dense + q * nd, d_indices + q * nt, seed + stride * q,
+                                     true));
+            ad.push_back(qc.back().dense.get());
+            for (auto *p : qc.back().sel_ptrs()) sd.push_back(p);
         }
         std::vector<Ciphertext *> y = batch_uses_graph(bt) ? model_infer_batch_graph(c, bt, ad, sd)
                                                            : model_infer_batch(c, bt, ad, sd);

@@ -737,7 +737,7 @@ Batch *batch_create(Ctx *c, const Model *m, const std::vector<const EvalKey *> &
     b->model = m;
     b->evk = evk;
     for (auto &L : m->bottom) batch_keytab(b.get(), L.pm.get());
-    batch_keytab(b.get(), m->emb->pm.get());
+    for (PtMatrix *pm : m->emb_mats()) batch_keytab(b.get(), pm);
     for (auto &L : m->top) batch_keytab(b.get(), L.pm.get());
     // (the host tables were staged by the copies themselves: nothing to wait for)
     return b.release();
@@ -891,11 +891,12 @@ static Owned dot_interaction_b(Ctx *c, const Batch *bt, const Model *m, const CC
 std::vector<Ciphertext *> model_infer_batch(Ctx *c, const Batch *bt, const CCtVec &ct_dense, const CCtVec &ct_sel)
 {
     const Model *m = bt->model;
-    const size_t B = bt->evk.size();
-    HCHECK(ct_dense.size() == B && ct_sel.size() == B, HELRM_E_INVAL, "batch size mismatch");
+    const size_t B = bt->evk.size(), ns = (size_t)m->n_sel();
+    HCHECK(ct_dense.size() == B && ct_sel.size() == B * ns, HELRM_E_INVAL, "batch size mismatch");
     for (size_t q = 0; q < B; q++) {
         HCHECK(ct_dense[q]->level == m->lvl_dense, HELRM_E_LEVEL, "ct_dense is not at the model's dense level");
-        HCHECK(ct_sel[q]->level == m->lvl_sel, HELRM_E_LEVEL, "ct_sel is not at the model's selector level");
+        for (size_t k2 = 0; k2 < ns; k2++)
+            HCHECK(ct_sel[q * ns + k2]->level == m->lvl_sel, HELRM_E_LEVEL, "ct_sel is not at the model's selector level");
     }
     Owned h;
     CCtVec x = ct_dense;
@@ -903,7 +904,15 @@ std::vector<Ciphertext *> model_infer_batch(Ctx *c, const Batch *bt, const CCtVe
         h = dense_layer_b(c, bt, L, x);
         x = h.craw();
     }
-    Owned e = matvec_b(c, bt, m->emb->pm.get(), ct_sel);
+    // the lookup: one product per selector ciphertext, added (ct_sel is query-major)
+    const std::vector<PtMatrix *> mats = m->emb_mats();
+    Owned e;
+    for (size_t k2 = 0; k2 < ns; k2++) {
+        CCtVec sk2;
+        for (size_t q = 0; q < B; q++) sk2.push_back(ct_sel[q * ns + k2]);
+        Owned t = matvec_b(c, bt, mats[k2], sk2);
+        e = k2 == 0 ? std::move(t) : add_b(c, e.craw(), t.craw());
+    }
     Owned z = add_b(c, h.craw(), e.craw());
     h = Owned();
     e = Owned();
@@ -931,25 +940,26 @@ std::vector<Ciphertext *> model_infer_batch_graph(Ctx *c, Batch *bt, const CCtVe
 {
     const size_t B = bt->evk.size();
     const Model *m = bt->model;
-    HCHECK(ct_dense.size() == B && ct_sel.size() == B, HELRM_E_INVAL, "batch size mismatch");
+    const size_t S = B * (size_t)m->n_sel();   // ct_sel is query-major, n_sel per query
+    HCHECK(ct_dense.size() == B && ct_sel.size() == S, HELRM_E_INVAL, "batch size mismatch");
     HCHECK(!c->prof_on, HELRM_E_INVAL, "kernel profiling cannot be recorded inside a graph");
-    for (size_t q = 0; q < B; q++) {
+    for (size_t q = 0; q < B; q++)
         HCHECK(ct_dense[q]->level == m->lvl_dense, HELRM_E_LEVEL, "ct_dense is not at the model's dense level");
-        HCHECK(ct_sel[q]->level == m->lvl_sel, HELRM_E_LEVEL, "ct_sel is not at the model's selector level");
-    }
+    for (size_t r = 0; r < S; r++)
+        HCHECK(ct_sel[r]->level == m->lvl_sel, HELRM_E_LEVEL, "ct_sel is not at the model's selector level");
     auto copy_in = [&] {
         for (size_t q = 0; q < B; q++) {
-            HCHECK(ct_dense[q]->scale == bt->g_dense[q]->scale && ct_sel[q]->scale == bt->g_sel[q]->scale,
-                   HELRM_E_SCALE, "input scales differ from the captured ones");
+            HCHECK(ct_dense[q]->scale == bt->g_dense[q]->scale, HELRM_E_SCALE, "input scales differ from the captured ones");
             k::copy(c, bt->g_dense[q]->data.u(), ct_dense[q]->data.u(), bt->g_dense[q]->data.bytes / 8);
-            k::copy(c, bt->g_sel[q]->data.u(), ct_sel[q]->data.u(), bt->g_sel[q]->data.bytes / 8);
+        }
+        for (size_t r = 0; r < S; r++) {
+            HCHECK(ct_sel[r]->scale == bt->g_sel[r]->scale, HELRM_E_SCALE, "input scales differ from the captured ones");
+            k::copy(c, bt->g_sel[r]->data.u(), ct_sel[r]->data.u(), bt->g_sel[r]->data.bytes / 8);
         }
     };
     if (!bt->exec) {
-        for (size_t q = 0; q < B; q++) {
-            bt->g_dense.emplace_back(new_ct(c, m->lvl_dense, ct_dense[q]->scale));
-            bt->g_sel.emplace_back(new_ct(c, m->lvl_sel, ct_sel[q]->scale));
-        }
+        for (size_t q = 0; q < B; q++) bt->g_dense.emplace_back(new_ct(c, m->lvl_dense, ct_dense[q]->scale));
+        for (size_t r = 0; r < S; r++) bt->g_sel.emplace_back(new_ct(c, m->lvl_sel, ct_sel[r]->scale));
         copy_in();
         // the output buffers and scales come from one eager run on the fixed inputs
         Owned probe;
@@ -972,10 +982,8 @@ std::vector<Ciphertext *> model_infer_batch_graph(Ctx *c, Batch *bt, const CCtVe
         c->stream = bt->gstream;   // everything the path enqueues goes into the capture
         try {
             CCtVec d, s;
-            for (size_t q = 0; q < B; q++) {
-                d.push_back(bt->g_dense[q].get());
-                s.push_back(bt->g_sel[q].get());
-            }
+            for (auto &p : bt->g_dense) d.push_back(p.get());
+            for (auto &p : bt->g_sel) s.push_back(p.get());
             std::vector<Ciphertext *> y = model_infer_batch(c, bt, d, s);
             Owned yo;
             for (auto *p : y) yo.v.emplace_back(p);

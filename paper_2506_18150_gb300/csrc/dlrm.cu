@@ -40,23 +40,31 @@ static int num_digits(u64 k, u64 p)
     return ell;
 }
 
-static std::vector<SelSeg> selector_layout(const std::vector<u64> &cards, int p, int *width)
+// Sec. 5.2: a table is digit-decomposed (base p) only if it has more rows than
+// the threshold; otherwise it keeps its plain one-hot (threshold p: a table
+// that fits one digit).
+static bool compressed(u64 k, int p, u64 threshold) { return k > threshold; }
+
+static std::vector<SelSeg> selector_layout(const std::vector<u64> &cards, int p, u64 threshold, int *width)
 {
     std::vector<SelSeg> out;
-    int off = 0;
+    long off = 0;
     for (int t = 0; t < (int)cards.size(); t++) {
-        if (cards[t] <= (u64)p) {
-            out.push_back({t, 0, off, (int)cards[t]});
-            off += (int)cards[t];
+        HCHECK(compressed(cards[t], p, threshold) || cards[t] <= (u64)1 << 30, HELRM_E_PARAM,
+               "uncompressed table too large for one selector");
+        if (!compressed(cards[t], p, threshold)) {
+            out.push_back({t, 0, (int)off, (int)cards[t]});
+            off += (long)cards[t];
         } else {
             int ell = num_digits(cards[t], p);
             for (int j = 0; j < ell; j++) {
-                out.push_back({t, j, off, p});
+                out.push_back({t, j, (int)off, p});
                 off += p;
             }
         }
+        HCHECK(off < (1L << 30), HELRM_E_PARAM, "selector wider than 2^30 slots");
     }
-    *width = off;
+    *width = (int)off;
     return out;
 }
 
@@ -82,7 +90,7 @@ static std::vector<double> emb_matrix(const Emb &e, const float *const *tables, 
     return M;
 }
 
-Emb *emb_prepare(Ctx *c, const std::vector<u64> &cards, int base, int dim, const float *const *tables,
+Emb *emb_prepare(Ctx *c, const std::vector<u64> &cards, int base, u64 threshold, int dim, const float *const *tables,
                  int out_offset, int out_pad, int level, double ct_scale, double target_scale)
 {
     HCHECK(!cards.empty() && base >= 2 && dim >= 1 && tables, HELRM_E_INVAL, "bad embedding description");
@@ -90,8 +98,9 @@ Emb *emb_prepare(Ctx *c, const std::vector<u64> &cards, int base, int dim, const
     std::unique_ptr<Emb> e(new Emb(c));
     e->cards = cards;
     e->base = base;
+    e->threshold = threshold ? threshold : (u64)base;
     e->dim = dim;
-    e->layout = selector_layout(cards, base, &e->width);
+    e->layout = selector_layout(cards, base, e->threshold, &e->width);
     e->in_pad = pow2ceil(e->width);
     e->out_pad = out_pad;
     const int rows = out_offset + dim * (int)cards.size();
@@ -118,7 +127,8 @@ Emb *emb_prepare(Ctx *c, const std::vector<u64> &cards, int base, int dim, const
             }
         tab.push_back((int)std::min<u64>(cards[t], (u64)1 << 30));
         tab.push_back(off);
-        tab.push_back(cards[t] <= (u64)base ? 1 : num_digits(cards[t], base));
+        // digits of a compressed table; 0 = a plain one-hot of `rows` slots
+        tab.push_back(compressed(cards[t], base, e->threshold) ? num_digits(cards[t], base) : 0);
     }
     e->d_tab = DevMem(c, tab.size() * 4);
     CUDA_CHECK(cudaMemcpyAsync(e->d_tab.ptr, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, c->stream));
@@ -132,7 +142,7 @@ void emb_pack_host(const Emb *e, const u64 *indices, std::vector<double> &sel)
     for (auto &s : e->layout) {
         u64 i = indices[s.t];
         HCHECK(i < e->cards[s.t], HELRM_E_INVAL, "index out of range for its table");
-        if (e->cards[s.t] <= (u64)e->base) {
+        if (!compressed(e->cards[s.t], e->base, e->threshold)) {
             sel[s.off + i] = 1.0;
         } else {
             for (int j = 0; j < s.j; j++) i /= (u64)e->base;
@@ -198,9 +208,10 @@ Model *model_create(Ctx *c, const helrm_model_desc *d)
     }
     int width = 0;
     std::vector<u64> cards(d->cards, d->cards + d->n_tables);
-    selector_layout(cards, (int)d->base_p, &width);
-    HCHECK(std::max({m->W_u, pow2ceil(width), m->W_z, m->p_dense}) <= c->n_slots, HELRM_E_PARAM,
-           "layout wider than the slot count");
+    const u64 thr = d->threshold ? d->threshold : (u64)d->base_p;
+    selector_layout(cards, (int)d->base_p, thr, &width);
+    // (a selector wider than n slots spans several ciphertexts)
+    HCHECK(std::max({m->W_u, m->W_z, m->p_dense}) <= c->n_slots, HELRM_E_PARAM, "layout wider than the slot count");
 
     const double delta = c->delta;
     int lvl = m->lvl_dense, in_pad = m->p_dense;
@@ -219,8 +230,7 @@ Model *model_create(Ctx *c, const helrm_model_desc *d)
         in_pad = out_pad;
     }
     const double scale_b = scale;
-    m->emb.reset(emb_prepare(c, cards, (int)d->base_p, DIM, d->tables, DIM, m->W_z, m->lvl_sel, delta, scale_b));
-    HCHECK(m->emb->pm, HELRM_E_PARAM, "the model's selector must fit one ciphertext");
+    m->emb.reset(emb_prepare(c, cards, (int)d->base_p, thr, DIM, d->tables, DIM, m->W_z, m->lvl_sel, delta, scale_b));
     double u_scale = scale_b;
     if (dot) {
         std::vector<double> ones(m->W_z, 0.0);
@@ -298,7 +308,8 @@ void model_import(Ctx *c, Model *m, const i64 *coeffs, u32 count)
         pts[i]->reset(pt_from_signed(c, coeffs + i * (size_t)c->N, o->level, o->qp, o->scale, o->form));
     }
     for (auto &l : m->bottom) l.pm->upload_index();
-    m->emb->pm->upload_index();
+    if (m->emb->pm) m->emb->pm->upload_index();
+    for (auto &ch : m->emb->chunks) ch->upload_index();
     for (auto &l : m->top) l.pm->upload_index();
 }
 
@@ -320,20 +331,25 @@ std::vector<Ciphertext *> model_infer_batch(Ctx *c, const Batch *bt, const std::
 // giant steps, all masks, all rotations of the interaction) merged into one
 // launch each.
 Ciphertext *model_infer(Ctx *c, const EvalKey *evk, const Model *m, const Ciphertext *ct_dense,
-                        const Ciphertext *ct_sel)
+                        const std::vector<const Ciphertext *> &ct_sel)
 {
     HCHECK(ct_dense->level == m->lvl_dense, HELRM_E_LEVEL, "ct_dense is not at the model's dense level");
-    HCHECK(ct_sel->level == m->lvl_sel, HELRM_E_LEVEL, "ct_sel is not at the model's selector level");
+    HCHECK((int)ct_sel.size() == m->n_sel(), HELRM_E_INVAL,
+           "the model's selector spans " + std::to_string(m->n_sel()) + " ciphertexts");
+    for (auto *s : ct_sel) HCHECK(s->level == m->lvl_sel, HELRM_E_LEVEL, "ct_sel is not at the model's selector level");
     std::unique_ptr<Batch, void (*)(Batch *)> b(batch_create(c, m, {evk}), batch_destroy);
-    return model_infer_batch(c, b.get(), {ct_dense}, {ct_sel})[0];
+    return model_infer_batch(c, b.get(), {ct_dense}, ct_sel)[0];
 }
 
 // client side: pack on the device, encode, encrypt
+// ct_dense with `seed`; selector ciphertext k (of n_sel) with seed + 1 + k
 void model_encrypt_query(Ctx *c, const EvalKey *evk, const Model *m, const double *dense, const u64 *indices,
-                         u64 seed, Ciphertext **ct_dense, Ciphertext **ct_sel, bool on_device)
+                         u64 seed, Ciphertext **ct_dense, std::vector<Ciphertext *> &ct_sel, bool on_device)
 {
     const Emb *e = m->emb.get();
-    DevMem dd, di, sel(c, (size_t)e->in_pad * 8);
+    const int ns = m->n_sel();
+    const size_t sel_words = ns == 1 ? (size_t)e->in_pad : (size_t)ns * c->n_slots;
+    DevMem dd, di, sel(c, sel_words * 8);
     const double *d_dense = dense;
     const u64 *d_idx = indices;
     if (!on_device) {
@@ -346,13 +362,21 @@ void model_encrypt_query(Ctx *c, const EvalKey *evk, const Model *m, const doubl
         d_dense = dd.as<double>();
         d_idx = di.u();
     }
-    k::pack_selector(c, sel.as<double>(), d_idx, e->d_tab.as<int>(), m->T, e->base, e->in_pad);
+    k::pack_selector(c, sel.as<double>(), d_idx, e->d_tab.as<int>(), m->T, e->base, (int)sel_words);
     std::unique_ptr<Plaintext> pd(pt_encode_dev(c, d_dense, m->n_dense, m->p_dense, m->lvl_dense, c->delta));
-    std::unique_ptr<Plaintext> ps(pt_encode_dev(c, sel.as<double>(), e->in_pad, e->in_pad, m->lvl_sel, c->delta));
     std::unique_ptr<Ciphertext> a(encrypt_pt(c, evk, pd.get(), seed));
-    std::unique_ptr<Ciphertext> b(encrypt_pt(c, evk, ps.get(), seed + 1));
+    std::vector<std::unique_ptr<Ciphertext>> b;
+    for (int k2 = 0; k2 < ns; k2++) {
+        // ciphertext k2 holds selector columns [k2 n, k2 n + w) with period pow2ceil(w)
+        const int w = ns == 1 ? e->in_pad : std::min(c->n_slots, e->width - k2 * c->n_slots);
+        const int per = ns == 1 ? e->in_pad : pow2ceil(w);
+        std::unique_ptr<Plaintext> ps(
+            pt_encode_dev(c, sel.as<double>() + (size_t)k2 * c->n_slots, w, per, m->lvl_sel, c->delta));
+        b.emplace_back(encrypt_pt(c, evk, ps.get(), seed + 1 + k2));
+    }
     *ct_dense = a.release();
-    *ct_sel = b.release();
+    ct_sel.clear();
+    for (auto &x : b) ct_sel.push_back(x.release());
 }
 
 // model accessors for the C ABI
@@ -367,6 +391,7 @@ void model_info(const Model *m, u32 *o)
     o[6] = m->W_z;
     o[7] = m->W_u;
     o[8] = (u32)const_cast<Model *>(m)->plaintexts().size();
+    o[9] = (u32)m->n_sel();
 }
 std::vector<int> model_rotations(const Model *m) { return m->rotations(); }
 
@@ -382,6 +407,7 @@ std::vector<std::pair<int, int>> model_key_levels(const Model *m, int *relin_lev
         if (it == lv.end() || it->second < l) lv[st] = l;
     };
     auto mat = [&](const PtMatrix *pm) {
+        if (!pm) return;
         for (auto &gb : pm->gb) {
             if (gb.second) use(gb.second, pm->level);
             if (gb.first) use(gb.first * pm->n1, pm->level);
@@ -394,6 +420,7 @@ std::vector<std::pair<int, int>> model_key_levels(const Model *m, int *relin_lev
         if (L.square) rl = std::max(rl, L.pm->level - 1);
     }
     mat(m->emb->pm.get());
+    for (auto &ch : m->emb->chunks) mat(ch.get());
     if (m->interaction == 0) {
         use(-DIM * m->Bp, m->lvl_z - 1);
         for (int s = 1; s <= m->S; s++) use(DIM * s, m->lvl_z - 1);
@@ -433,5 +460,6 @@ Ctx *emb_ctx(const Emb *e) { return e->ctx; }
 Ctx *model_ctx(const Model *m) { return m->ctx; }
 u32 model_n_dense(const Model *m) { return (u32)m->n_dense; }
 u32 model_n_tables(const Model *m) { return (u32)m->T; }
+int model_n_sel(const Model *m) { return m->n_sel(); }
 
 }  // namespace helrm

@@ -516,7 +516,7 @@ __global__ void k_pack_selector(double *sel, const u64 *__restrict__ idx, const 
         u64 i = idx[t];
         const int rows = tab[3 * t], off = tab[3 * t + 1], nd = tab[3 * t + 2];
         if (i >= (u64)rows) continue;   // out-of-range index: no slot set for this table
-        if (rows <= base) {
+        if (nd == 0) {   // a plain one-hot
             sel[off + i] = 1.0;
         } else {
             for (int j = 0; j < nd; j++) {   // little-endian base-p digits, one one-hot each

@@ -18,6 +18,7 @@ struct Emb : Handle {
     Ctx *ctx;
     std::vector<u64> cards;
     int base = 0, dim = 0, width = 0, in_pad = 0, out_pad = 0;
+    u64 threshold = 0;   // tables with more rows are digit-decomposed
     std::vector<SelSeg> layout;
     std::unique_ptr<PtMatrix> pm;                    // the lookup matrix (selector within one ciphertext)
     // a selector wider than the slot count spans ceil(width / n) ciphertexts:
@@ -44,6 +45,15 @@ struct Model : Handle {
     std::vector<std::unique_ptr<Plaintext>> masks;
     Model(Ctx *c) : Handle(KIND_MODEL), ctx(c) {}
 
+    // the lookup's matrices: one, or one per ciphertext of a wide selector
+    std::vector<PtMatrix *> emb_mats() const
+    {
+        std::vector<PtMatrix *> v;
+        if (emb->pm) v.push_back(emb->pm.get());
+        for (auto &ch : emb->chunks) v.push_back(ch.get());
+        return v;
+    }
+    int n_sel() const { return (int)emb_mats().size(); }
     std::vector<std::unique_ptr<Plaintext> *> plaintexts()
     {
         std::vector<std::unique_ptr<Plaintext> *> out;
@@ -51,7 +61,8 @@ struct Model : Handle {
             for (auto &p : l.pm->pts) out.push_back(&p);
             out.push_back(&l.bias);
         }
-        for (auto &p : emb->pm->pts) out.push_back(&p);
+        for (PtMatrix *pm : emb_mats())
+            for (auto &p : pm->pts) out.push_back(&p);
         if (interaction == 0) {
             out.push_back(&ones);
             for (auto &m : masks) out.push_back(&m);
@@ -67,7 +78,7 @@ struct Model : Handle {
         std::vector<int> st;
         auto addv = [&](const std::vector<int> &v) { st.insert(st.end(), v.begin(), v.end()); };
         for (auto &l : bottom) addv(l.pm->rotations());
-        addv(emb->pm->rotations());
+        for (PtMatrix *pm : emb_mats()) addv(pm->rotations());
         if (interaction == 0) {
             st.push_back(-DIM * Bp);
             for (int s = 1; s <= S; s++) st.push_back(DIM * s);
@@ -79,7 +90,8 @@ struct Model : Handle {
     }
 };
 
+// ct_sel: the model's n_sel() selector ciphertexts
 Ciphertext *model_infer(Ctx *c, const EvalKey *evk, const Model *m, const Ciphertext *ct_dense,
-                        const Ciphertext *ct_sel);
+                        const std::vector<const Ciphertext *> &ct_sel);
 
 }  // namespace helrm

@@ -81,6 +81,7 @@ Server *server_create(Ctx *c, int n_slots, int max_batch, u64 budget)
 
 u32 server_add_client(Server *s, const Model *m, const EvalKey *evk)
 {
+    HCHECK(m->n_sel() == 1, HELRM_E_INVAL, "the server takes models whose selector fits one ciphertext");
     s->clients.push_back({m, evk});
     return (u32)s->clients.size() - 1;
 }
@@ -188,7 +189,7 @@ void server_run(Server *s, u32 n, const double *arrival, const u32 *client, cons
                 busy[k] = 1;   // from here on the slot owns whatever was launched
                 if (take.size() == 1) {
                     const Server::Client &cl = s->clients[client[take[0]]];
-                    f.out.push_back(model_infer(c, cl.evk, m, ct_dense[take[0]], ct_sel[take[0]]));
+                    f.out.push_back(model_infer(c, cl.evk, m, ct_dense[take[0]], {ct_sel[take[0]]}));
                 } else {
                     std::vector<const EvalKey *> ev;
                     std::vector<const Ciphertext *> d, sl;

@@ -49,7 +49,7 @@ class ModelDesc(C.Structure):
                 ("top_W", C.POINTER(C.POINTER(C.c_double))), ("top_b", C.POINTER(C.POINTER(C.c_double))),
                 ("n_tables", C.c_uint32), ("cards", C.POINTER(C.c_uint64)), ("base_p", C.c_uint32),
                 ("dim", C.c_uint32), ("tables", C.POINTER(C.POINTER(C.c_float))),
-                ("interaction", C.c_int32)]
+                ("interaction", C.c_int32), ("threshold", C.c_uint64)]
 
 
 _lib = None
@@ -97,7 +97,7 @@ _SIGS = {
     "helrm_ptmat_rotations": [_vp, _i32p, _u32p],
     "helrm_ptmat_import": [_vp, _vp, _i64p, C.c_uint32],
     "helrm_ptct_matvec": [_vp, _vp, _vp, _vp, C.c_uint32, _pp],
-    "helrm_emb_prepare": [_vp, C.c_uint32, _u64p, C.c_uint32, C.c_uint32, C.POINTER(C.POINTER(C.c_float)),
+    "helrm_emb_prepare": [_vp, C.c_uint32, _u64p, C.c_uint32, C.c_uint64, C.c_uint32, C.POINTER(C.POINTER(C.c_float)),
                           C.c_uint32, C.c_uint32, C.c_int32, C.c_double, C.c_double, _pp],
     "helrm_query_pack": [_vp, _u64p, _dp, C.c_uint32],
     "helrm_emb_info": [_vp, _u32p, _u32p],
@@ -112,6 +112,7 @@ _SIGS = {
     "helrm_model_export_plaintexts": [_vp, _vp, _i64p, C.c_uint32],
     "helrm_encrypt_query": [_vp, _vp, _vp, _dp, _u64p, C.c_uint64, _pp, _pp],
     "helrm_infer": [_vp, _vp, _vp, _vp, _vp, _pp],
+    "helrm_infer_multi": [_vp, _vp, _vp, _vp, _pp, C.c_uint32, _pp],
     "helrm_decrypt_logit": [_vp, _vp, _vp, _dp, _dp],
     "helrm_infer_e2e": [_vp, _vp, _vp, _vp, _dp, _u64p, C.c_uint32, C.c_uint64, _dp, _dp],
     "helrm_infer_e2e_device": [_vp, _vp, _vp, _vp, _vp, _vp, C.c_uint32, C.c_uint64, _vp, _vp],
@@ -433,12 +434,14 @@ def _float_tables(tables):
     return arrs, ptrs
 
 
-def helrm_emb_prepare(ctx, cards, base_p, dim, tables, out_offset, out_pad, level, ct_scale, target_scale):
+def helrm_emb_prepare(ctx, cards, base_p, threshold, dim, tables, out_offset, out_pad, level, ct_scale,
+                      target_scale):
+    """threshold: tables with more rows are digit-decomposed (0 = base_p)."""
     c_arr, c_p = _u64(cards)
     arrs, ptrs = _float_tables(tables)
     out = C.c_void_p()
-    _check(ctx, lib().helrm_emb_prepare(ctx.ptr, len(cards), c_p, base_p, dim, ptrs, out_offset, out_pad, level,
-                                        ct_scale, target_scale, C.byref(out)))
+    _check(ctx, lib().helrm_emb_prepare(ctx.ptr, len(cards), c_p, base_p, threshold, dim, ptrs, out_offset, out_pad,
+                                        level, ct_scale, target_scale, C.byref(out)))
     return Handle(out.value, ctx)
 
 
@@ -496,16 +499,16 @@ def helrm_model_create(ctx, spec, w):
     d = ModelDesc(spec.n_dense, len(w.bottom_W), bw, dptrs(w.bottom_W), dptrs(w.bottom_b),
                   len(w.top_W), tw, dptrs(w.top_W), dptrs(w.top_b), len(spec.cards),
                   cards.ctypes.data_as(_u64p), spec.base, spec.dim, tptrs,
-                  0 if spec.interaction == "dot" else 1)
+                  0 if spec.interaction == "dot" else 1, getattr(spec, "threshold", 0) or 0)
     out = C.c_void_p()
     _check(ctx, lib().helrm_model_create(ctx.ptr, C.byref(d), C.byref(out)))
     return Handle(out.value, ctx)
 
 
 def helrm_model_info(ctx, m):
-    o = (C.c_uint32 * 9)()
+    o = (C.c_uint32 * 10)()
     _check(ctx, lib().helrm_model_info(m.ptr, o))
-    keys = ["lvl_dense", "lvl_sel", "lvl_z", "lvl_u", "p_dense", "p_sel", "W_z", "W_u", "n_plaintexts"]
+    keys = ["lvl_dense", "lvl_sel", "lvl_z", "lvl_u", "p_dense", "p_sel", "W_z", "W_u", "n_plaintexts", "n_sel"]
     return dict(zip(keys, list(o)))
 
 
@@ -527,15 +530,25 @@ def helrm_model_export_plaintexts(ctx, m):
 
 
 def helrm_encrypt_query(ctx, evk, m, dense, indices, seed: int):
+    """(ct_dense, ct_sel): ct_sel is one handle when the model's n_sel is 1, else a list of n_sel."""
     d, dp = _f64(dense)
     i, ip = _u64(indices)
-    a, b = C.c_void_p(), C.c_void_p()
-    _check(ctx, lib().helrm_encrypt_query(ctx.ptr, evk.ptr, m.ptr, dp, ip, seed, C.byref(a), C.byref(b)))
-    return Handle(a.value, ctx), Handle(b.value, ctx)
+    ns = helrm_model_info(ctx, m)["n_sel"]
+    a, b = C.c_void_p(), (C.c_void_p * ns)()
+    _check(ctx, lib().helrm_encrypt_query(ctx.ptr, evk.ptr, m.ptr, dp, ip, seed, C.byref(a), b))
+    sel = [Handle(b[k], ctx) for k in range(ns)]
+    return Handle(a.value, ctx), (sel[0] if ns == 1 else sel)
 
 
 def helrm_infer(ctx, evk, m, ct_dense, ct_sel):
     return _ct_op("helrm_infer", ctx, evk.ptr, m.ptr, ct_dense.ptr, ct_sel.ptr)
+
+
+def helrm_infer_multi(ctx, evk, m, ct_dense, cts_sel):
+    out = C.c_void_p()
+    _check(ctx, lib().helrm_infer_multi(ctx.ptr, evk.ptr, m.ptr, ct_dense.ptr, _ptrs(cts_sel), len(cts_sel),
+                                        C.byref(out)))
+    return Handle(out.value, ctx)
 
 
 def helrm_decrypt_logit(ctx, sk, ct):
@@ -569,7 +582,9 @@ def helrm_batch_set_graph(ctx, batch, enable: bool):
 
 
 def helrm_infer_batch(ctx, batch, cts_dense, cts_sel):
+    """cts_sel: n x n_sel handles, query-major (a flat list, or one list per query)."""
     n = len(cts_dense)
+    cts_sel = [x for s in cts_sel for x in (s if isinstance(s, (list, tuple)) else [s])]
     outs = (C.c_void_p * n)()
     _check(ctx, lib().helrm_infer_batch(ctx.ptr, batch.ptr, _ptrs(cts_dense), _ptrs(cts_sel), outs))
     return [Handle(outs[q], ctx) for q in range(n)]

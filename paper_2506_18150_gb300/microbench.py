@@ -126,7 +126,7 @@ def bench_multi(n_cts: int, level: int, reps: int):
     cards = [rows] * 26
     rng = np.random.default_rng(5)
     tables = [[rng.uniform(-0.05, 0.05, (rows, 16)).astype(np.float32)] for _ in cards]
-    emb = H.helrm_emb_prepare(ctx, cards, rows, 16, tables, 0, 512, level, 2.0**40, 2.0**40)
+    emb = H.helrm_emb_prepare(ctx, cards, rows, 0, 16, tables, 0, 512, level, 2.0**40, 2.0**40)
     chunks = H.helrm_emb_chunks(ctx, emb)
     mats = [H.helrm_emb_matrix(ctx, emb, c) for c in range(chunks)]
     steps = sorted(set().union(*[set(H.helrm_ptmat_rotations(ctx, m)) for m in mats]))

@@ -51,6 +51,7 @@ class DLRMSpec:
     base: int               # digit base p
     dim: int = 16
     interaction: str = "dot"    # "dot" (pairwise) or "concat" (the paper's choice)
+    threshold: int | None = None    # tables with more rows are digit-decomposed (None: base)
 
 
 def n_digits(k: int, p: int) -> int:
@@ -64,8 +65,10 @@ def n_digits(k: int, p: int) -> int:
     return ell
 
 
-def table_rows(k: int, p: int) -> list:
-    return [k] if k <= p else [p] * n_digits(k, p)
+def table_rows(k: int, p: int, threshold=None) -> list:
+    """Rows of the tables that replace one of k rows: itself if it is not
+    compressed (k <= threshold, which defaults to p), else l digit tables of p rows."""
+    return [k] if k <= (p if threshold is None else threshold) else [p] * n_digits(k, p)
 
 
 def top_input_width(spec: DLRMSpec) -> int:
@@ -88,6 +91,18 @@ def uci_spec(seed: int = 0, interaction: str = "dot") -> DLRMSpec:
 def uci_paper_spec() -> DLRMSpec:
     """The paper's UCI shape: 5 dense features and tables of [2,4,2,3,2,3,4,3] rows."""
     s = DLRMSpec("uci_paper", 5, [5, 16, 16], [0, 16, 1], [2, 4, 2, 3, 2, 3, 4, 3], 64, 16)
+    s.top[0] = top_input_width(s)
+    return s
+
+
+def wide_spec(interaction: str = "dot") -> DLRMSpec:
+    """A small DLRM whose packed selector is wider than 512 slots, under the
+    paper's compression policy (Sec. 5.2: base 4, tables with more rows than a
+    threshold compressed): tables of 700, 2000 and 3 rows with threshold 1000
+    give plain one-hots of 700 and 3 slots and 6 base-4 digits (24 slots) for
+    the 2000-row table, 727 slots in all; 4 dense features, bottom 4-16, top
+    22-1 (22 = 16 + C(4, 2))."""
+    s = DLRMSpec("wide", 4, [4, 16], [0, 1], [700, 2000, 3], 4, 16, interaction, threshold=1000)
     s.top[0] = top_input_width(s)
     return s
 
@@ -174,7 +189,7 @@ def make_weights(spec: DLRMSpec, seed: int = 0) -> DLRMWeights:
         w.top_b.append(rng.normal(0, 0.1, size=b))
     for k in spec.cards:
         w.tables.append([rng.uniform(-0.05, 0.05, size=(r, spec.dim)).astype(np.float32)
-                         for r in table_rows(k, spec.base)])
+                         for r in table_rows(k, spec.base, spec.threshold)])
 
     dense, idx = make_queries(spec, 256, seed=10_000 + seed)
     h = dense
@@ -186,7 +201,7 @@ def make_weights(spec: DLRMSpec, seed: int = 0) -> DLRMWeights:
         h = (pre * c) ** 2
     embs = []
     for t, k in enumerate(spec.cards):
-        rows = table_rows(k, spec.base)
+        rows = table_rows(k, spec.base, spec.threshold)
         e = np.zeros((len(idx), spec.dim))
         rem = idx[:, t].astype(np.int64)
         for j, r in enumerate(rows):

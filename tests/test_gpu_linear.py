@@ -92,7 +92,7 @@ def tiny():
     steps = sorted(set(linear.rotation_steps(pm_o)) | set(linear.rotation_steps(pm_d[0])))
     sk, evk = H.helrm_keygen(ctx, 0, steps)
     sk_o, keys_o = ckks.keygen(p, 0, rot_steps=steps, relin=False)
-    emb = H.helrm_emb_prepare(ctx, [1024], 32, 16, [C], 0, 16, 1, p.delta, p.delta)
+    emb = H.helrm_emb_prepare(ctx, [1024], 32, 0, 16, [C], 0, 16, 1, p.delta, p.delta)
     return ctx, p, C, M, pm_o, pm_d, sk, evk, sk_o, keys_o, emb
 
 
@@ -139,7 +139,7 @@ def test_uncompressed_1024_row_lookup(tiny):
     from paper_2506_18150_gb300 import helrm as H
     ctx, p, C = tiny[0], tiny[1], tiny[2]
     E = np.stack([C[0][i % 32].astype(np.float64) + C[1][i // 32].astype(np.float64) for i in range(1024)])
-    emb = H.helrm_emb_prepare(ctx, [1024], 1024, 16, [[E.astype(np.float32)]], 0, 16, 1, p.delta, p.delta)
+    emb = H.helrm_emb_prepare(ctx, [1024], 1024, 0, 16, [[E.astype(np.float32)]], 0, 16, 1, p.delta, p.delta)
     assert H.helrm_emb_info(ctx, emb) == (1024, 1024)
     sk, evk = H.helrm_keygen(ctx, 4, [])
     pm = H.helrm_ptmat_prepare(ctx, E.T, 1024, 16, 1, p.delta, p.delta)     # same layout as the lookup

@@ -211,3 +211,50 @@ def test_multi_ciphertext_lookup_matches_gather(small_params):
         got = ckks.decrypt(p, sk, y)[: 2 * dlrm.DIM]
         want = np.concatenate(dlrm.embedding_cleartext(cards, base, tables, idx))
         assert np.max(np.abs(got - want)) < 1e-4, idx
+
+
+def test_threshold_policy_layout():
+    """Sec. 5.2's policy: a table is digit-decomposed (base p) only if it has
+    more rows than the threshold; with the threshold at p this is the plain
+    rule (a table that fits one digit stays a plain one-hot)."""
+    cards = [700, 2000, 3]
+    lay, w = dlrm.selector_layout(cards, 4, 1000)
+    assert [(t, j, ww) for (t, j, _, ww) in lay] == [(0, 0, 700)] + [(1, j, 4) for j in range(6)] + [(2, 0, 3)]
+    assert w == 700 + 6 * 4 + 3 == 727
+    assert dlrm.selector_layout(cards, 4, None) == dlrm.selector_layout(cards, 4, 4)
+    # uncompressed everything: one slot per row, CR = 1
+    assert dlrm.selector_layout(cards, 4, 10**9)[1] == sum(cards)
+    # slots as a function of the threshold (the paper's CR = rows / slots)
+    for thr in [3, 700, 1000, 2000]:
+        want = sum(k if k <= thr else 4 * dlrm.num_digits(k, 4) for k in cards)
+        assert dlrm.selector_layout(cards, 4, thr)[1] == want
+    s = syn.wide_spec()
+    assert [sum(syn.table_rows(k, s.base, s.threshold)) for k in s.cards] == [700, 24, 3]
+    rng = np.random.default_rng(4)
+    w_ = syn.make_weights(s, 0)
+    for _ in range(20):
+        idx = [int(rng.integers(0, k)) for k in cards]
+        M = dlrm.embedding_matrix(cards, 4, w_.tables, 0, 48, threshold=1000)
+        y = M @ dlrm.selector_vector(cards, 4, idx, 1000)
+        assert np.allclose(y, np.concatenate(dlrm.embedding_cleartext(cards, 4, w_.tables, idx, 1000)))
+
+
+def test_encrypted_dlrm_with_two_selector_ciphertexts(small_params):
+    """N = 2^10 (512 slots): the wide model's 727-slot selector spans two
+    ciphertexts; the encrypted logit (lookup = sum of the two per-ciphertext
+    products) matches the FP64 cleartext DLRM."""
+    p = small_params
+    spec = syn.wide_spec()
+    w = syn.make_weights(spec, 0)
+    c = dlrm.compile_model(p, spec, w)
+    assert c.emb is None and c.n_sel() == 2
+    assert [pm.layout.in_pad for pm in c.emb_chunks] == [512, 256]
+    sk, keys = ckks.keygen(p, 8, rot_steps=c.rotation_steps())
+    dense, idx = syn.make_queries(spec, 2, seed=6)
+    for q in range(2):
+        cd, cs = dlrm.encrypt_query(p, keys, c, dense[q], idx[q], 200 + 3 * q)
+        assert len(cs) == 2
+        out = dlrm.infer(p, keys, c, cd, cs)
+        logit, _ = dlrm.decrypt_logit(p, sk, out)
+        ref = dlrm.dlrm_cleartext(spec, w, dense[q], idx[q])[0]
+        assert abs(logit - ref) < 1e-3, (q, logit, ref)

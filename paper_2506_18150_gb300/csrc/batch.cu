@@ -898,21 +898,27 @@ std::vector<Ciphertext *> model_infer_batch(Ctx *c, const Batch *bt, const CCtVe
         for (size_t k2 = 0; k2 < ns; k2++)
             HCHECK(ct_sel[q * ns + k2]->level == m->lvl_sel, HELRM_E_LEVEL, "ct_sel is not at the model's selector level");
     }
-    Owned h;
+    // The lookup (selector path) and the bottom MLP (dense path) are
+    // independent until z = h + e: the lookup is enqueued on a second stream
+    // and overlaps the bottom MLP, then the context's stream joins it.
+    const std::vector<PtMatrix *> mats = m->emb_mats();
+    Owned e, h;
+    Fork branch(c);
+    branch.run([&] {
+        // one product per selector ciphertext, added (ct_sel is query-major)
+        for (size_t k2 = 0; k2 < ns; k2++) {
+            CCtVec sk2;
+            for (size_t q = 0; q < B; q++) sk2.push_back(ct_sel[q * ns + k2]);
+            Owned t = matvec_b(c, bt, mats[k2], sk2);
+            e = k2 == 0 ? std::move(t) : add_b(c, e.craw(), t.craw());
+        }
+    });
     CCtVec x = ct_dense;
     for (auto &L : m->bottom) {
         h = dense_layer_b(c, bt, L, x);
         x = h.craw();
     }
-    // the lookup: one product per selector ciphertext, added (ct_sel is query-major)
-    const std::vector<PtMatrix *> mats = m->emb_mats();
-    Owned e;
-    for (size_t k2 = 0; k2 < ns; k2++) {
-        CCtVec sk2;
-        for (size_t q = 0; q < B; q++) sk2.push_back(ct_sel[q * ns + k2]);
-        Owned t = matvec_b(c, bt, mats[k2], sk2);
-        e = k2 == 0 ? std::move(t) : add_b(c, e.craw(), t.craw());
-    }
+    branch.join();
     Owned z = add_b(c, h.craw(), e.craw());
     h = Owned();
     e = Owned();
@@ -976,10 +982,12 @@ std::vector<Ciphertext *> model_infer_batch_graph(Ctx *c, Batch *bt, const CCtVe
             CUDA_CHECK(cudaEventCreateWithFlags(&bt->ev_in, cudaEventDisableTiming));
             CUDA_CHECK(cudaEventCreateWithFlags(&bt->ev_out, cudaEventDisableTiming));
         }
+        c->side_of(bt->gstream);   // the branch stream of the capture exists before it opens
         const cudaStream_t home = c->stream;
         cudaGraph_t g = nullptr;
         CUDA_CHECK(cudaStreamBeginCapture(bt->gstream, cudaStreamCaptureModeThreadLocal));
         c->stream = bt->gstream;   // everything the path enqueues goes into the capture
+        c->capturing = true;       // allocations become graph nodes (no side pool)
         try {
             CCtVec d, s;
             for (auto &p : bt->g_dense) d.push_back(p.get());
@@ -990,12 +998,14 @@ std::vector<Ciphertext *> model_infer_batch_graph(Ctx *c, Batch *bt, const CCtVe
             for (size_t q = 0; q < B; q++) k::copy(c, bt->g_out[q]->data.u(), yo.v[q]->data.u(), yo.v[q]->data.bytes / 8);
         } catch (...) {
             c->stream = home;
+            c->capturing = false;
             cudaStreamEndCapture(bt->gstream, &g);
             if (g) cudaGraphDestroy(g);
             cudaGetLastError();
             throw;
         }
         c->stream = home;
+        c->capturing = false;
         CUDA_CHECK(cudaStreamEndCapture(bt->gstream, &g));
         cudaError_t e = cudaGraphInstantiate(&bt->exec, g, 0);
         cudaGraphDestroy(g);

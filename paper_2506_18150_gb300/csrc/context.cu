@@ -92,7 +92,8 @@ void *Ctx::alloc(size_t bytes)
         fail(HELRM_E_NOMEM, "memory cap reached (" + std::to_string(mem_in_use + bytes) + " > " +
                                 std::to_string(mem_cap) + " bytes)");
     void *p = nullptr;
-    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+    cudaError_t e = (alloc_pool && !capturing) ? cudaMallocFromPoolAsync(&p, bytes, alloc_pool, stream)
+                                               : cudaMallocAsync(&p, bytes, stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         fail(HELRM_E_NOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
@@ -123,6 +124,59 @@ DevMem &DevMem::operator=(DevMem &&o) noexcept
         o.bytes = 0;
     }
     return *this;
+}
+
+Ctx::Side &Ctx::side_of(cudaStream_t home)
+{
+    auto it = sides.find(home);
+    if (it != sides.end()) return it->second;
+    Side s;
+    CUDA_CHECK(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    CUDA_CHECK(cudaMemPoolCreate(&s.pool, &props));
+    u64 thr = ~0ull;   // keep freed blocks for reuse, like the default pool
+    CUDA_CHECK(cudaMemPoolSetAttribute(s.pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    CUDA_CHECK(cudaEventCreateWithFlags(&s.fork, cudaEventDisableTiming));
+    CUDA_CHECK(cudaEventCreateWithFlags(&s.join, cudaEventDisableTiming));
+    return sides.emplace(home, s).first->second;
+}
+
+// With per-kernel timing on, a branch runs inline on the context's stream,
+// so that every kernel's pair of events brackets that kernel alone.
+Fork::Fork(Ctx *ctx) : c(ctx), home(ctx->stream), side(ctx->prof_on ? nullptr : &ctx->side_of(ctx->stream))
+{
+    if (!side) return;
+    CUDA_CHECK(cudaEventRecord(side->fork, home));
+    CUDA_CHECK(cudaStreamWaitEvent(side->stream, side->fork, 0));
+}
+void Fork::enter()
+{
+    if (!side) return;
+    c->stream = side->stream;
+    c->alloc_pool = side->pool;
+}
+void Fork::leave()
+{
+    if (!side) return;
+    c->stream = home;
+    c->alloc_pool = nullptr;
+}
+void Fork::join()
+{
+    if (joined || !side) return;
+    joined = true;
+    CUDA_CHECK(cudaEventRecord(side->join, side->stream));
+    CUDA_CHECK(cudaStreamWaitEvent(home, side->join, 0));
+}
+Fork::~Fork()
+{
+    if (joined || !side) return;
+    // an error unwinds through here: still order the home stream after the branch
+    if (cudaEventRecord(side->join, side->stream) == cudaSuccess) cudaStreamWaitEvent(home, side->join, 0);
+    cudaGetLastError();
 }
 
 cudaEvent_t Ctx::take_event()
@@ -161,6 +215,13 @@ Ctx::~Ctx()
     d_one_mont = DevMem();
     d_err = DevMem();
     cudaStreamSynchronize(stream);
+    for (auto &kv : sides) {
+        cudaStreamSynchronize(kv.second.stream);
+        cudaStreamDestroy(kv.second.stream);
+        cudaEventDestroy(kv.second.fork);
+        cudaEventDestroy(kv.second.join);
+        cudaMemPoolDestroy(kv.second.pool);   // released once its last block is freed
+    }
 }
 
 void Ctx::check_device_errors()

@@ -224,6 +224,19 @@ struct Ctx : Handle {
     u64 launches = 0;
     std::string last_error;
     cudaMemPool_t pool = nullptr;
+    // Second streams for independent branches of one inference (Fork below):
+    // one per home stream (a serving slot is a home stream), each with its own
+    // memory pool, so that a block freed on the home stream is never handed
+    // to the branch with a wait on the home stream inserted by the allocator.
+    struct Side {
+        cudaStream_t stream = nullptr;
+        cudaMemPool_t pool = nullptr;
+        cudaEvent_t fork = nullptr, join = nullptr;
+    };
+    std::map<cudaStream_t, Side> sides;
+    cudaMemPool_t alloc_pool = nullptr;   // set inside a branch: Ctx::alloc draws from it
+    bool capturing = false;               // a graph capture is open on `stream`
+    Side &side_of(cudaStream_t home);
     // optional per-kernel timing with CUDA events on the context stream
     struct ProfRec {
         const char *name;
@@ -253,6 +266,43 @@ struct Ctx : Handle {
     void check_device_errors();
 };
 
+// Fork / join of an independent branch of work.  The constructor records a
+// fork point on the context's stream; run(f) enqueues f's work on the side
+// stream of that stream (after the fork point, allocating from the side
+// pool), then restores the context's stream; join() (or the destructor)
+// makes the context's stream wait for everything the branch enqueued.  Work
+// enqueued on the context's stream between run() and join() overlaps the
+// branch.  Inside a graph capture the same calls record a forked graph.  With
+// per-kernel timing on (Ctx::prof_on) the branch runs inline instead.
+class Fork {
+  public:
+    explicit Fork(Ctx *c);
+    template <class F>
+    void run(F &&f)
+    {
+        enter();
+        try {
+            f();
+        } catch (...) {
+            leave();
+            throw;
+        }
+        leave();
+    }
+    void join();
+    ~Fork();
+    Fork(const Fork &) = delete;
+    Fork &operator=(const Fork &) = delete;
+
+  private:
+    void enter();
+    void leave();
+    Ctx *c;
+    cudaStream_t home;
+    Ctx::Side *side;   // null: inline
+    bool joined = false;
+};
+
 // Scope timer: when profiling is on, brackets the enclosed launches with a
 // pair of events and the kernel's algorithmic bytes (reads + writes once).
 // Programmatic dependent launch.  Every kernel of the library starts with
@@ -260,8 +310,9 @@ struct Ctx : Handle {
 // completed and their writes are visible, then launch_dependents lets the next
 // grid in the stream be scheduled while this one runs, so consecutive kernels
 // no longer pay a full launch latency each.  Both instructions are no-ops in
-// a grid launched without the attribute.  No kernel touches global memory
-// before pdl_begin(), which is what makes the early launch safe.
+// a grid launched without the attribute.  Before pdl_begin() a kernel reads
+// only tables that no kernel writes (the NTT reads its twiddles and prime
+// constants there), which is what makes the early launch safe.
 __device__ __forceinline__ void pdl_begin()
 {
 #ifdef __CUDA_ARCH__

@@ -362,18 +362,23 @@ void model_encrypt_query(Ctx *c, const EvalKey *evk, const Model *m, const doubl
         d_dense = dd.as<double>();
         d_idx = di.u();
     }
-    k::pack_selector(c, sel.as<double>(), d_idx, e->d_tab.as<int>(), m->T, e->base, (int)sel_words);
+    // the selector ciphertexts on a second stream, the dense one on the context's
+    std::vector<std::unique_ptr<Ciphertext>> b;
+    Fork branch(c);
+    branch.run([&] {
+        k::pack_selector(c, sel.as<double>(), d_idx, e->d_tab.as<int>(), m->T, e->base, (int)sel_words);
+        for (int k2 = 0; k2 < ns; k2++) {
+            // ciphertext k2 holds selector columns [k2 n, k2 n + w) with period pow2ceil(w)
+            const int w = ns == 1 ? e->in_pad : std::min(c->n_slots, e->width - k2 * c->n_slots);
+            const int per = ns == 1 ? e->in_pad : pow2ceil(w);
+            std::unique_ptr<Plaintext> ps(
+                pt_encode_dev(c, sel.as<double>() + (size_t)k2 * c->n_slots, w, per, m->lvl_sel, c->delta));
+            b.emplace_back(encrypt_pt(c, evk, ps.get(), seed + 1 + k2));
+        }
+    });
     std::unique_ptr<Plaintext> pd(pt_encode_dev(c, d_dense, m->n_dense, m->p_dense, m->lvl_dense, c->delta));
     std::unique_ptr<Ciphertext> a(encrypt_pt(c, evk, pd.get(), seed));
-    std::vector<std::unique_ptr<Ciphertext>> b;
-    for (int k2 = 0; k2 < ns; k2++) {
-        // ciphertext k2 holds selector columns [k2 n, k2 n + w) with period pow2ceil(w)
-        const int w = ns == 1 ? e->in_pad : std::min(c->n_slots, e->width - k2 * c->n_slots);
-        const int per = ns == 1 ? e->in_pad : pow2ceil(w);
-        std::unique_ptr<Plaintext> ps(
-            pt_encode_dev(c, sel.as<double>() + (size_t)k2 * c->n_slots, w, per, m->lvl_sel, c->delta));
-        b.emplace_back(encrypt_pt(c, evk, ps.get(), seed + 1 + k2));
-    }
+    branch.join();   // before sel, dd and di (read by the branch) are freed
     *ct_dense = a.release();
     ct_sel.clear();
     for (auto &x : b) ct_sel.push_back(x.release());

@@ -90,7 +90,6 @@ __global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN_arg, int l
                                                    const PrimeInfo *__restrict__ pinfo, int mode,
                                                    const u64 *__restrict__ ep_scal)
 {
-    pdl_begin();
     constexpr int P = 1 << LOGP;
     constexpr int TPS = P / 8;              // threads per sub-transform
     extern __shared__ u64 sm[];
@@ -102,9 +101,6 @@ __global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN_arg, int l
     const int G = 1 << logG;                // sub-transforms per CTA
     const int y = blockIdx.y;
     const int pid = list.pid[y];
-    const PrimeInfo pi = pinfo[pid];
-    const u64 q = pi.q;
-    const u64 q2 = 2 * q;
     const ulonglong2 *tw = tw_all + (size_t)pid * N;
     const u64 *in = first ? list.src[y] : list.dst[y];
     u64 *out = list.dst[y];
@@ -125,6 +121,26 @@ __global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN_arg, int l
     const int gglob = blockIdx.x * G + g;   // column index (COLS) or row index (ROWS)
     const int bm = COLS ? 1 : (1 << logN1);
     const int seg = COLS ? 0 : gglob;
+
+    // The prime and the twiddles do not depend on earlier kernels, so they are
+    // fetched before the grid-dependency wait, overlapping the previous
+    // kernel: the prime constants into registers, and the 128-byte lines of
+    // this sub-transform's twiddles (the run of 2^s entries at (bm + seg) << s
+    // for each local stage s; lane tt takes entries [8 tt, 8 tt + 8) of each
+    // run) into L2.  The column pass's set is shared, so only its g = 0 lanes
+    // fetch it.
+    const PrimeInfo pi = pinfo[pid];
+    if (!COLS || g == 0) {
+#pragma unroll
+        for (int s = 0; s < LOGP; s++)
+            if (tt * 8 < (1 << s)) {
+                const ulonglong2 *line = tw + ((size_t)(bm + seg) << s) + tt * 8;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(line));
+            }
+    }
+    pdl_begin();
+    const u64 q = pi.q;
+    const u64 q2 = 2 * q;
     auto gaddr = [&](int e) -> size_t {
         return COLS ? (size_t)e * N2 + gglob : (size_t)gglob * N2 + e;
     };

@@ -157,18 +157,44 @@ def declared_symbols():
     return sorted(list(_SIGS) + ["helrm_free", "helrm_last_error", "helrm_status_string"])
 
 
+def _owning_context(keep):
+    if isinstance(keep, Context):
+        return keep
+    if isinstance(keep, (tuple, list)):
+        for k in keep:
+            c = _owning_context(k)
+            if c is not None:
+                return c
+    return None
+
+
 class Handle:
-    """An owned library handle; freed on garbage collection (after its dependants)."""
+    """An owned library handle; freed on garbage collection.
+
+    A handle that depends on a context is counted on it, and the context is
+    released only after the last of them: the library requires that order,
+    and the cyclic garbage collector finalises the members of a cycle (a
+    context and its handles held by a traceback, say) in no particular order.
+    """
 
     def __init__(self, ptr, keep=None):
         self.ptr = C.c_void_p(ptr)
         self._keep = keep
+        self._ctx = _owning_context(keep)
+        if self._ctx is not None and self.ptr:
+            self._ctx._live += 1
+        else:
+            self._ctx = None
 
     def __del__(self):
         try:
             if self.ptr and _lib is not None:
                 _lib.helrm_free(self.ptr)
                 self.ptr = C.c_void_p()
+            ctx, self._ctx = self._ctx, None
+            if ctx is not None:
+                ctx._live -= 1
+                ctx._release_if_done()
         except Exception:
             pass
 
@@ -178,7 +204,24 @@ class Handle:
 
 
 class Context(Handle):
-    pass
+    """The context: freed when it is collected and no handle of it is left."""
+
+    def __init__(self, ptr):
+        self._live = 0
+        self._closing = False
+        super().__init__(ptr)
+
+    def _release_if_done(self):
+        if self._closing and self._live == 0 and self.ptr and _lib is not None:
+            _lib.helrm_free(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self._closing = True
+            self._release_if_done()
+        except Exception:
+            pass
 
 
 class Borrowed(Handle):

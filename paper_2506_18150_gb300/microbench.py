@@ -1,6 +1,6 @@
 """Kernel micro-benchmarks on caller-owned device buffers.
 
-  python -m paper_2506_18150_gb300.microbench ntt --limbs 192 --reps 20
+  python -m paper_2506_18150_gb300.microbench ntt --limbs 192 --reps 20 [--per 20]
   python -m paper_2506_18150_gb300.microbench rotate --level 8 --reps 20
 
 `multi` times the embedding lookup with a selector of --cts ciphertexts.
@@ -27,7 +27,7 @@ def _ctx(torch):
                               stream=torch.cuda.current_stream().cuda_stream), pr
 
 
-def bench_ntt(limbs: int, reps: int):
+def bench_ntt(limbs: int, reps: int, per: int = 20):
     import torch
 
     from . import helrm as H
@@ -36,8 +36,7 @@ def bench_ntt(limbs: int, reps: int):
     primes, _ = H.helrm_ctx_primes(ctx)
     q = primes[1]
     buf = torch.randint(0, q, (limbs * n,), dtype=torch.int64, device="cuda")
-    # limbs cycle over the 40-bit primes 1..20 (one launch per block of 20 limbs)
-    per = 20
+    # limbs cycle over the 40-bit primes 1..20 (one launch per block of `per` limbs)
     groups = [(i, min(per, limbs - i)) for i in range(0, limbs, per)]
 
     def run(inverse):
@@ -157,9 +156,10 @@ def main():
     ap.add_argument("--limbs", type=int, default=192)
     ap.add_argument("--level", type=int, default=8)
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--per", type=int, default=20, help="ntt: limbs per launch")
     a = ap.parse_args()
     if a.what == "ntt":
-        r = bench_ntt(a.limbs, a.reps)
+        r = bench_ntt(a.limbs, a.reps, a.per)
     elif a.what == "rotate":
         r = bench_rotate(a.level, a.reps)
     elif a.what == "multi":

@@ -366,37 +366,22 @@ void modup_b(Ctx *c, const std::vector<const u64 *> &polys, int level, const std
 {
     const int N = c->N, nq = level + 1, nl = nq + c->K, dnum = c->dnum(level);
     const size_t B = polys.size();
-    const LimbMap m = c->qmap(level);
     DevMem coef(c, B * nq * N * 8);
-    std::vector<k::NttLimb> v;
-    for (size_t q = 0; q < B; q++)
-        for (int l = 0; l < nq; l++)
-            v.push_back({polys[q] + (size_t)l * N, coef.u() + (q * nq + l) * N, m.pid(l), nullptr, nullptr, nullptr});
-    k::ntt_run(c, v, true, nullptr);
-    std::vector<k::BConvCall> bc;
-    for (size_t q = 0; q < B; q++)
-        for (int j = 0; j < dnum; j++)
-            bc.push_back({&c->modup_table(level, j), coef.u() + q * nq * N, digits[q] + (size_t)j * nl * N});
-    k::bconv_multi(c, bc);
+    std::vector<k::NttLimb> inv, fwd;   // the base conversion runs inside the two transforms
+    for (size_t q = 0; q < B; q++) modup_limbs(c, level, polys[q], coef.u() + q * nq * N, digits[q], inv, fwd);
+    k::ntt_run(c, inv, true, nullptr);
     std::vector<u64 *> co;
     std::vector<const u64 *> ca;
     std::vector<u64> cw;
-    v.clear();
     for (size_t q = 0; q < B; q++)
-        for (int j = 0; j < dnum; j++) {
-            u64 *d = digits[q] + (size_t)j * nl * N;
+        for (int j = 0; j < dnum; j++) {   // each digit keeps its own limbs as they are
             const int lo = c->digit_lo(j), hi = c->digit_hi(j, level);
-            co.push_back(d + (size_t)lo * N);
+            co.push_back(digits[q] + ((size_t)j * nl + lo) * N);
             ca.push_back(polys[q] + (size_t)lo * N);
             cw.push_back((u64)(hi - lo) * N);
-            for (int l = 0; l < nl; l++)
-                if (l < lo || l >= hi) {
-                    u64 *p = d + (size_t)l * N;
-                    v.push_back({p, p, m.pid(l), nullptr, nullptr, nullptr});
-                }
         }
     copy_b(c, co, ca, cw);
-    k::ntt_run(c, v, false, nullptr);
+    k::ntt_run(c, fwd, false, nullptr);
 }
 
 // ModDown of `halves` QP polynomials per entry (u[q] = [halves][nl][N]), as
@@ -407,31 +392,14 @@ void moddown_b(Ctx *c, const std::vector<const u64 *> &u, int level, int halves,
 {
     const int N = c->N, nq = level + 1, K = c->K, nl = nq + K;
     const size_t B = u.size();
-    const LimbMap m = c->qmap(level);
     DevMem pc(c, B * halves * K * N * 8), y(c, B * halves * nq * N * 8);
-    std::vector<k::NttLimb> v;
+    std::vector<k::NttLimb> inv, fwd;   // the base conversion runs inside the two transforms
     for (size_t q = 0; q < B; q++)
         for (int h = 0; h < halves; h++)
-            for (int i = 0; i < K; i++)
-                v.push_back({u[q] + (size_t)(h * nl + nq + i) * N, pc.u() + ((q * halves + h) * K + i) * N,
-                             m.pid(nq + i), nullptr, nullptr, nullptr});
-    k::ntt_run(c, v, true, nullptr);
-    const BConvTable &md = c->moddown_table(level);
-    std::vector<k::BConvCall> bc;
-    for (size_t q = 0; q < B; q++)
-        for (int h = 0; h < halves; h++)
-            bc.push_back({&md, pc.u() + (q * halves + h) * K * N, y.u() + (q * halves + h) * nq * N});
-    k::bconv_multi(c, bc);
-    v.clear();
-    for (size_t q = 0; q < B; q++)
-        for (int h = 0; h < halves; h++)
-            for (int l = 0; l < nq; l++) {
-                u64 *yl = y.u() + ((q * halves + h) * nq + l) * N;
-                const u64 *ad = h ? add1[q] : add0[q];
-                v.push_back({yl, yl, m.pid(l), u[q] + (size_t)(h * nl + l) * N, (h ? out1[q] : out0[q]) + (size_t)l * N,
-                             ad ? ad + (size_t)l * N : nullptr});
-            }
-    k::ntt_run(c, v, false, c->d_pinv_mont.u());
+            moddown_limbs(c, level, u[q] + (size_t)h * nl * N, pc.u() + (q * halves + h) * K * N,
+                          y.u() + (q * halves + h) * nq * N, h ? out1[q] : out0[q], h ? add1[q] : add0[q], inv, fwd);
+    k::ntt_run(c, inv, true, nullptr);
+    k::ntt_run(c, fwd, false, c->d_pinv_mont.u());
 }
 
 // rescale of every ciphertext (all at the same level), as ct_rescale

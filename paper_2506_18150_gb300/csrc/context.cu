@@ -252,12 +252,16 @@ static void upload(Ctx *c, DevMem &m, const void *h, size_t bytes)
 
 // ----------------------------------------------------- base conversion tables
 // Layout (u64): [0] n_src, [1] n_dst, then per src s: q, qinv, hinv_mont, limb;
-// per dst k: p, pinv, limb; then hmod[s][k] = (Qs/q_s mod p_k) R mod p_k.
+// per dst k: p, pinv, limb; then hmod[s][k] = (Qs/q_s mod p_k) R mod p_k (the
+// conversion constants the fused forward NTT reads, BConvTable::hcol).  The
+// factors [(Qs/q_s)^-1]_{q_s} reach the inverse NTT's final scale through
+// iscale.
 static BConvTable make_bconv(Ctx *c, const std::vector<int> &src_pid, const std::vector<int> &src_limb,
                              const std::vector<int> &dst_pid, const std::vector<int> &dst_limb)
 {
     int ns = (int)src_pid.size(), nd = (int)dst_pid.size();
     std::vector<u64> t;
+    std::vector<ulonglong2> isc(ns);
     t.push_back(ns);
     t.push_back(nd);
     for (int s = 0; s < ns; s++) {
@@ -267,6 +271,9 @@ static BConvTable make_bconv(Ctx *c, const std::vector<int> &src_pid, const std:
         for (int r = 0; r < ns; r++)
             if (r != s) qh = h_mulmod(qh, c->primes[src_pid[r]] % q, q);
         u64 hinv = h_inv_mod(qh, q);
+        // the same factor folded into an inverse NTT's final scale
+        const u64 w = h_mulmod(h_inv_mod((u64)c->N % q, q), hinv, q);
+        isc[s] = make_ulonglong2(w, (u64)(((u128)w << 64) / q));
         t.push_back(q);
         t.push_back(c->pinfo[src_pid[s]].qinv);
         t.push_back(h_mulmod(hinv, c->pinfo[src_pid[s]].rmod, q));   // Montgomery form
@@ -289,6 +296,7 @@ static BConvTable make_bconv(Ctx *c, const std::vector<int> &src_pid, const std:
     bt.n_src = ns;
     bt.n_dst = nd;
     upload(c, bt.tab, t.data(), t.size() * 8);
+    upload(c, bt.iscale, isc.data(), isc.size() * sizeof(ulonglong2));
     return bt;
 }
 

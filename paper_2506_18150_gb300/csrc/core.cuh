@@ -186,7 +186,11 @@ struct Handle {
 // Device tables for one fast base conversion (src primes -> dst primes).
 struct BConvTable {
     int n_src = 0, n_dst = 0;
-    DevMem tab;   // see kernels.cu: bconv layout
+    DevMem tab;      // layout: context.cu, make_bconv
+    DevMem iscale;   // ulonglong2 [n_src]: N^-1 [(Q/q_s)^-1]_{q_s} and its Shoup quotient
+    // the Montgomery constants [Q/q_s]_{p_k} of destination k, stride n_dst
+    const u64 *hcol(int k) const { return tab.u() + 2 + 4 * n_src + 3 * n_dst + k; }
+    const ulonglong2 *scale(int s) const { return iscale.as<ulonglong2>() + s; }
 };
 
 struct Ctx : Handle {
@@ -420,6 +424,13 @@ void ntt_inv(Ctx *c, u64 *data, int n_limbs, LimbMap map);
 // the second works on dst.  With a forward transform and ea != nullptr, the
 // result is not stored in dst but as eo[i] = (ea[i] - NTT(y)[i]) * ep_scal[pid]
 // (+ eb[i] when eb != nullptr; eb may equal eo).
+//
+// Fused fast base conversion (Sec. 2.1's ModUp / ModDown): an inverse
+// transform may end with a scale of its own (scal: a Shoup pair replacing
+// N^-1, e.g. N^-1 [(Q/q_s)^-1]_{q_s}), and a forward transform may compute its
+// input on load as src[i] = sum_{s < fbc_n} src[s N + i] * fbc_h[s fbc_hs] mod
+// q (fbc_h in Montgomery form: the column of the conversion matrix for this
+// limb's prime), so the converted limbs are never written to memory.
 struct NttLimb {
     const u64 *src;
     u64 *dst;
@@ -427,6 +438,10 @@ struct NttLimb {
     const u64 *ea;
     u64 *eo;
     const u64 *eb;
+    const ulonglong2 *scal = nullptr;   // inverse: replaces N^-1 (device pointer; null: N^-1)
+    int fbc_n = 0;                      // forward: source limbs of the conversion (0: plain input)
+    const u64 *fbc_h = nullptr;         // forward: the conversion constants (device pointer)
+    int fbc_hs = 0;                     // their stride
 };
 void ntt_run(Ctx *c, const std::vector<NttLimb> &limbs, bool inverse, const u64 *ep_scal);
 // same as ntt_fwd / ntt_inv, with the launch list built on the stack (no heap use)
@@ -460,16 +475,6 @@ void sub_mul_scalar(Ctx *c, u64 *out, const u64 *a, const u64 *b, const u64 *d_s
                     int n_limbs, LimbMap map);
 // centred integers (int64 N) -> residues for n_limbs limbs
 void from_signed(Ctx *c, u64 *out, const i64 *in, int n_limbs, LimbMap map);
-void bconv(Ctx *c, const BConvTable &t, const u64 *in_base, u64 *out_base);
-// several conversions in one launch
-struct BConvCall {
-    const BConvTable *t;
-    const u64 *in;
-    u64 *out;
-};
-void bconv_multi(Ctx *c, const std::vector<BConvCall> &calls);
-// ModUp base conversion of every digit at `level` in one launch (digits: [dnum][level+1+K][N])
-void bconv_modup(Ctx *c, int level, const u64 *coef, u64 *digits);
 // d_out[l][i] = sum_j dig_j[l][perm(i)] * key_j(l)[i] for the level-ell QP basis, both
 // polys of the key; if c0 != null, out0 on Q limbs += P * c0[perm(i)]
 // bq (optional): a QP polynomial whose image phi(bq) is added to the first
@@ -524,6 +529,13 @@ void sigmoid(Ctx *c, double *d_p, const double *d_x, int n);
 // ------------------------------------------------------ scheme (scheme.cu)
 Ciphertext *new_ct(Ctx *c, int level, double scale);
 void ks_modup(Ctx *c, const u64 *poly_ntt, int level, u64 *digits_out);
+// the launch lists of a ModUp / one half of a ModDown with the base conversion
+// fused into the transforms (appended to inv and fwd; coef: (level+1) limbs of
+// scratch; pc: K limbs, y: level+1 limbs of scratch)
+void modup_limbs(Ctx *c, int level, const u64 *poly, u64 *coef, u64 *digits, std::vector<k::NttLimb> &inv,
+                 std::vector<k::NttLimb> &fwd);
+void moddown_limbs(Ctx *c, int level, const u64 *qp, u64 *pc, u64 *y, u64 *out, const u64 *add,
+                   std::vector<k::NttLimb> &inv, std::vector<k::NttLimb> &fwd);
 void ks_moddown(Ctx *c, const u64 *qp_ntt, int level, u64 *out_ntt);
 // out_h = ModDown(u_h) (+ add_h when add_h != nullptr; add_h may equal out_h)
 void ks_moddown2(Ctx *c, const u64 *u, int level, u64 *out0, u64 *out1, const u64 *add0 = nullptr,

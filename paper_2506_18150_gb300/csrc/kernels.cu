@@ -115,58 +115,6 @@ __global__ void k_from_signed(u64 *__restrict__ out, const i64 *__restrict__ in,
     }
 }
 
-// ------------------------------------------------------------ base conversion
-// Table layout (context.cu, make_bconv): [0] n_src, [1] n_dst; per source s
-// (q_s, q_s^-1 mod 2^64, [(Q/q_s)^-1]_{q_s} in Montgomery form, source limb);
-// per destination d (q_d, q_d^-1 mod 2^64, output limb); then the matrix
-// [Q/q_s]_{q_d} (Montgomery form), row s.
-//
-// One launch runs a list of jobs (a table, an input and an output base, a
-// range of destinations); blockIdx.y is the job and each thread one
-// coefficient, so every (coefficient, destination chunk) pair is its own
-// thread.  Table reads are warp-uniform (broadcast from L1).
-constexpr int BCONV_CHUNK = 4;
-constexpr int BCONV_MAX_JOBS = 96;
-struct BConvJob {
-    const u64 *in;
-    u64 *out;
-    const u64 *tab;
-    int d0, d1;
-};
-struct BConvJobs {
-    int n;
-    BConvJob j[BCONV_MAX_JOBS];
-};
-
-__global__ void __launch_bounds__(256) k_bconv_jobs(BConvJobs jobs, int logN)
-{
-    pdl_begin();
-    const BConvJob jb = jobs.j[blockIdx.y];
-    const u64 *__restrict__ tab = jb.tab;
-    const size_t N = (size_t)1 << logN;
-    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const int ns = (int)tab[0], nd = (int)tab[1];
-    const int db = 2 + 4 * ns, hb = db + 3 * nd;
-    u64 t[8];
-#pragma unroll
-    for (int s = 0; s < 8; s++) {
-        if (s >= ns) break;
-        const u64 *e = tab + 2 + 4 * s;
-        t[s] = mont_mul(jb.in[e[3] * N + i], e[2], e[0], e[1]);
-    }
-    for (int k2 = jb.d0; k2 < jb.d1; k2++) {
-        const u64 *e = tab + db + 3 * k2;
-        Acc128 acc;
-#pragma unroll
-        for (int s = 0; s < 8; s++) {
-            if (s >= ns) break;
-            acc.mac(t[s], tab[hb + s * nd + k2], e[0]);
-        }
-        jb.out[e[2] * N + i] = acc.reduce(e[0], e[1]);
-    }
-}
-
 // ------------------------------------------------- automorphism + key inner product
 // NTT-domain Galois map for the bit-reversed order: slot i holds a(psi^(2x+1)),
 // x = brv(i); X -> X^k sends it to the slot of exponent (2x+1)k.
@@ -610,43 +558,6 @@ void from_signed(Ctx *c, u64 *out, const i64 *in, int n_limbs, LimbMap map)
     launch(c, k_from_signed, grid_for(total), TPB, 0, out, in, c->logN, total, c->d_pinfo.as<PrimeInfo>(), map);
     LAUNCHED(c);
 }
-void bconv_multi(Ctx *c, const std::vector<BConvCall> &calls)
-{
-    BConvJobs jobs;
-    jobs.n = 0;
-    double bytes = 0;
-    auto flush = [&] {
-        if (!jobs.n) return;
-        launch(c, k_bconv_jobs, dim3((c->N + 255) / 256, jobs.n), 256, 0, jobs, c->logN);
-        LAUNCHED(c);
-        jobs.n = 0;
-    };
-    {
-        KTimer kt(c, "bconv", 0.0);
-        for (const BConvCall &x : calls) {
-            HCHECK(x.t->n_src <= 8, HELRM_E_PARAM, "base conversion supports at most 8 source primes");
-            bytes += 8.0 * c->N * (x.t->n_src + x.t->n_dst);   // sources read, destinations written, once
-            for (int d0 = 0; d0 < x.t->n_dst; d0 += BCONV_CHUNK) {
-                if (jobs.n == BCONV_MAX_JOBS) flush();
-                jobs.j[jobs.n++] = {x.in, x.out, x.t->tab.u(), d0, std::min(x.t->n_dst, d0 + BCONV_CHUNK)};
-            }
-        }
-        flush();
-        if (kt.idx != (size_t)-1) c->prof[kt.idx].bytes = bytes;
-    }
-}
-void bconv(Ctx *c, const BConvTable &t, const u64 *in_base, u64 *out_base)
-{
-    bconv_multi(c, {{&t, in_base, out_base}});
-}
-void bconv_modup(Ctx *c, int level, const u64 *coef, u64 *digits)
-{
-    const int dnum = c->dnum(level), nl = level + 1 + c->K;
-    std::vector<BConvCall> v;
-    for (int j = 0; j < dnum; j++) v.push_back({&c->modup_table(level, j), coef, digits + (size_t)j * nl * c->N});
-    bconv_multi(c, v);
-}
-
 void ks_inner_auto(Ctx *c, u64 *out, const u64 *digits, int dnum, const SwitchKey *key, int level, u64 galois,
                    const u64 *c0, const u64 *d_pmod_mont, const u64 *bq, bool accumulate)
 {

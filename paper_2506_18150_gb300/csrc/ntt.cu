@@ -42,6 +42,24 @@ struct LimbList {
     unsigned short pid[MAX_LIMBS];
 };
 
+// Per-limb extras of a column pass (NttLimb::scal / fbc_*), passed only to
+// the instances that use them so that plain launches keep a smaller argument
+// block.  A conversion has at most FBC_MAX source limbs (alpha and K are 3).
+constexpr int FBC_MAX = 4;
+struct XList {
+    const ulonglong2 *scal[MAX_LIMBS];   // inverse: final scale (null: N^-1)
+    const u64 *fh[MAX_LIMBS];            // forward: conversion constants, stride fhs
+    unsigned short fhs[MAX_LIMBS];
+    unsigned char fn[MAX_LIMBS];         // forward: source limbs (0: plain input)
+};
+template <bool XL>
+struct XArg {
+    XList x;
+};
+template <>
+struct XArg<false> {
+};
+
 __device__ __forceinline__ int pad(int e) { return e + (e >> 4); }
 
 // Shoup product without its final correction: a * w mod q in [0, 2q).
@@ -83,12 +101,17 @@ enum Mode { M_LAZY = 0, M_SCALE = 1, M_REDUCE = 2 };
 // both compile-time constants (the production sizes), so every shared- and
 // global-memory address is a per-thread base plus an immediate offset; 0: the
 // arguments logN / logG are used (every other size).
-template <int LOGP, bool COLS, bool INV, int FIXN = 0, int FIXG = 0>
+// XL (column passes only): the per-limb extras of XList apply -- a forward
+// first pass computes its input as a fast base conversion of fn source limbs
+// on load (the 128-bit multiply-accumulate and the one reduction of the
+// stand-alone conversion kernel, so the values are identical); an inverse
+// last pass scales by its own constant.
+template <int LOGP, bool COLS, bool INV, int FIXN = 0, int FIXG = 0, bool XL = false>
 __global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN_arg, int logG_arg, LimbList list,
                                                    const ulonglong2 *__restrict__ tw_all,
                                                    const ulonglong2 *__restrict__ ninv,
                                                    const PrimeInfo *__restrict__ pinfo, int mode,
-                                                   const u64 *__restrict__ ep_scal)
+                                                   const u64 *__restrict__ ep_scal, const XArg<XL> xa)
 {
     constexpr int P = 1 << LOGP;
     constexpr int TPS = P / 8;              // threads per sub-transform
@@ -130,6 +153,20 @@ __global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN_arg, int l
     // run) into L2.  The column pass's set is shared, so only its g = 0 lanes
     // fetch it.
     const PrimeInfo pi = pinfo[pid];
+    int fn = 0;                 // fused conversion: source limbs and their constants
+    u64 hk[FBC_MAX];
+    ulonglong2 xs = make_ulonglong2(0, 0);
+    if constexpr (XL) {
+        if (!INV) {
+            fn = xa.x.fn[y];
+            const u64 *fh = xa.x.fh[y];
+            const int hs = xa.x.fhs[y];
+#pragma unroll
+            for (int s = 0; s < FBC_MAX; s++) hk[s] = s < fn ? fh[s * hs] : 0;
+        } else if (xa.x.scal[y]) {
+            xs = *xa.x.scal[y];
+        }
+    }
     if (!COLS || g == 0) {
 #pragma unroll
         for (int s = 0; s < LOGP; s++)
@@ -170,10 +207,24 @@ __global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN_arg, int l
             return blk * (T * gs) + boff + k * T;
         };
         if (rr == 0) {
+            if (XL && !INV && fn) {
 #pragma unroll
-            for (int qg = 0; qg < ng; qg++)
+                for (int qg = 0; qg < ng; qg++)
 #pragma unroll
-                for (int k = 0; k < gs; k++) v[qg * gs + k] = in[gaddr(elem(qg, k))];
+                    for (int k = 0; k < gs; k++) {
+                        const size_t a = gaddr(elem(qg, k));
+                        Acc128 acc;
+#pragma unroll
+                        for (int s = 0; s < FBC_MAX; s++)
+                            if (s < fn) acc.mac(in[(size_t)s * N + a], hk[s], q);
+                        v[qg * gs + k] = acc.reduce(q, pi.qinv);
+                    }
+            } else {
+#pragma unroll
+                for (int qg = 0; qg < ng; qg++)
+#pragma unroll
+                    for (int k = 0; k < gs; k++) v[qg * gs + k] = in[gaddr(elem(qg, k))];
+            }
         } else {
             __syncthreads();
 #pragma unroll
@@ -217,7 +268,7 @@ __global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN_arg, int l
         } else {
             ulonglong2 ni = make_ulonglong2(0, 0);
             u64 ec = 0;
-            if (mode == M_SCALE) ni = ninv[pid];
+            if (mode == M_SCALE) ni = (XL && INV && xs.x) ? xs : ninv[pid];
             if (mode == M_REDUCE && ea) ec = ep_scal[pid];
 #pragma unroll
             for (int qg = 0; qg < ng; qg++)
@@ -243,17 +294,17 @@ __global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN_arg, int l
     }
 }
 
-template <int LOGP, bool COLS, bool INV, int FIXN, int FIXG>
+template <int LOGP, bool COLS, bool INV, int FIXN, int FIXG, bool XL>
 void launch_kernel(Ctx *c, dim3 grid, int threads, size_t smem, const LimbList &ll, int first, int logG, int mode,
-                   const u64 *ep_scal)
+                   const u64 *ep_scal, const XArg<XL> &xa)
 {
     const ulonglong2 *tw = INV ? c->d_tw_inv.as<ulonglong2>() : c->d_tw_fwd.as<ulonglong2>();
-    launch(c, k_ntt_pass<LOGP, COLS, INV, FIXN, FIXG>, grid, threads, smem, first, c->logN, logG, ll, tw,
-           c->d_ninv.as<ulonglong2>(), c->d_pinfo.as<PrimeInfo>(), mode, ep_scal);
+    launch(c, k_ntt_pass<LOGP, COLS, INV, FIXN, FIXG, XL>, grid, threads, smem, first, c->logN, logG, ll, tw,
+           c->d_ninv.as<ulonglong2>(), c->d_pinfo.as<PrimeInfo>(), mode, ep_scal, xa);
 }
 
-template <int LOGP, bool COLS, bool INV>
-void launch_pass(Ctx *c, const LimbList &ll, int n_sub, int first, int mode, const u64 *ep_scal)
+template <int LOGP, bool COLS, bool INV, bool XL>
+void launch_pass(Ctx *c, const LimbList &ll, int n_sub, int first, int mode, const u64 *ep_scal, const XArg<XL> &xa)
 {
     constexpr int P = 1 << LOGP;
     // sub-transforms per CTA: as many as fit the tuned tile, fewer when the
@@ -272,40 +323,49 @@ void launch_pass(Ctx *c, const LimbList &ll, int n_sub, int first, int mode, con
     if constexpr (LOGP == 8) {
         if (c->logN == 16) {
             switch (logG) {
-            case 0: launch_kernel<8, COLS, INV, 16, 0>(c, grid, threads, smem, ll, first, logG, mode, ep_scal); return;
-            case 1: launch_kernel<8, COLS, INV, 16, 1>(c, grid, threads, smem, ll, first, logG, mode, ep_scal); return;
-            case 2: launch_kernel<8, COLS, INV, 16, 2>(c, grid, threads, smem, ll, first, logG, mode, ep_scal); return;
-            case 3: launch_kernel<8, COLS, INV, 16, 3>(c, grid, threads, smem, ll, first, logG, mode, ep_scal); return;
+            case 0: launch_kernel<8, COLS, INV, 16, 0, XL>(c, grid, threads, smem, ll, first, logG, mode, ep_scal, xa); return;
+            case 1: launch_kernel<8, COLS, INV, 16, 1, XL>(c, grid, threads, smem, ll, first, logG, mode, ep_scal, xa); return;
+            case 2: launch_kernel<8, COLS, INV, 16, 2, XL>(c, grid, threads, smem, ll, first, logG, mode, ep_scal, xa); return;
+            case 3: launch_kernel<8, COLS, INV, 16, 3, XL>(c, grid, threads, smem, ll, first, logG, mode, ep_scal, xa); return;
             default: break;
             }
         }
     }
-    launch_kernel<LOGP, COLS, INV, 0, 0>(c, grid, threads, smem, ll, first, logG, mode, ep_scal);
+    launch_kernel<LOGP, COLS, INV, 0, 0, XL>(c, grid, threads, smem, ll, first, logG, mode, ep_scal, xa);
 }
 
-template <bool COLS, bool INV>
-void dispatch(Ctx *c, int logp, const LimbList &ll, int n_sub, int first, int mode, const u64 *ep_scal)
+template <bool COLS, bool INV, bool XL>
+void dispatch(Ctx *c, int logp, const LimbList &ll, int n_sub, int first, int mode, const u64 *ep_scal,
+              const XArg<XL> &xa)
 {
     switch (logp) {
-    case 5: launch_pass<5, COLS, INV>(c, ll, n_sub, first, mode, ep_scal); break;
-    case 6: launch_pass<6, COLS, INV>(c, ll, n_sub, first, mode, ep_scal); break;
-    case 7: launch_pass<7, COLS, INV>(c, ll, n_sub, first, mode, ep_scal); break;
-    case 8: launch_pass<8, COLS, INV>(c, ll, n_sub, first, mode, ep_scal); break;
+    case 5: launch_pass<5, COLS, INV, XL>(c, ll, n_sub, first, mode, ep_scal, xa); break;
+    case 6: launch_pass<6, COLS, INV, XL>(c, ll, n_sub, first, mode, ep_scal, xa); break;
+    case 7: launch_pass<7, COLS, INV, XL>(c, ll, n_sub, first, mode, ep_scal, xa); break;
+    case 8: launch_pass<8, COLS, INV, XL>(c, ll, n_sub, first, mode, ep_scal, xa); break;
     default: fail(HELRM_E_PARAM, "unsupported NTT size");
     }
 }
 
-// both passes of one launch list
-void run_list(Ctx *c, const LimbList &ll, bool inverse, const u64 *ep_scal)
+// both passes of one launch list; xl (may be null) holds the column pass's
+// per-limb extras: the forward transform's first pass, the inverse's last
+void run_list(Ctx *c, const LimbList &ll, bool inverse, const u64 *ep_scal, const XArg<true> *xl = nullptr)
 {
     const int logN = c->logN, logN1 = logN / 2, logN2 = logN - logN1;
     const int N1 = 1 << logN1, N2 = 1 << logN2;
+    const XArg<false> none;
     if (!inverse) {
-        dispatch<true, false>(c, logN1, ll, N2, 1, M_LAZY, nullptr);
-        dispatch<false, false>(c, logN2, ll, N1, 0, M_REDUCE, ep_scal);
+        if (xl)
+            dispatch<true, false, true>(c, logN1, ll, N2, 1, M_LAZY, nullptr, *xl);
+        else
+            dispatch<true, false, false>(c, logN1, ll, N2, 1, M_LAZY, nullptr, none);
+        dispatch<false, false, false>(c, logN2, ll, N1, 0, M_REDUCE, ep_scal, none);
     } else {
-        dispatch<false, true>(c, logN2, ll, N1, 1, M_LAZY, nullptr);
-        dispatch<true, true>(c, logN1, ll, N2, 0, M_SCALE, nullptr);
+        dispatch<false, true, false>(c, logN2, ll, N1, 1, M_LAZY, nullptr, none);
+        if (xl)
+            dispatch<true, true, true>(c, logN1, ll, N2, 0, M_SCALE, nullptr, *xl);
+        else
+            dispatch<true, true, false>(c, logN1, ll, N2, 0, M_SCALE, nullptr, none);
     }
     c->launches += 2;
     CUDA_CHECK(cudaGetLastError());
@@ -319,9 +379,11 @@ void ntt_run(Ctx *c, const std::vector<NttLimb> &limbs, bool inverse, const u64 
 {
     if (limbs.empty()) return;
     KTimer kt(c, "ntt", 16.0 * c->N * limbs.size());   // algorithmic: each limb read and written once
+    std::unique_ptr<XArg<true>> xl;
     for (size_t b = 0; b < limbs.size(); b += MAX_LIMBS) {
         LimbList ll;
         ll.n = (int)std::min<size_t>(MAX_LIMBS, limbs.size() - b);
+        bool extras = false;
         for (int i = 0; i < ll.n; i++) {
             const NttLimb &x = limbs[b + i];
             ll.src[i] = x.src;
@@ -330,8 +392,22 @@ void ntt_run(Ctx *c, const std::vector<NttLimb> &limbs, bool inverse, const u64 
             ll.eb[i] = x.eb;
             ll.eo[i] = x.eo;
             ll.pid[i] = (unsigned short)x.pid;
+            extras |= (inverse ? x.scal != nullptr : x.fbc_n > 0);
         }
-        run_list(c, ll, inverse, ep_scal);
+        if (extras) {
+            if (!xl) xl.reset(new XArg<true>());
+            for (int i = 0; i < ll.n; i++) {
+                const NttLimb &x = limbs[b + i];
+                HCHECK(x.fbc_n >= 0 && x.fbc_n <= FBC_MAX && x.fbc_hs >= 0 && x.fbc_hs < 65536, HELRM_E_PARAM,
+                       "fused base conversion: at most 4 source limbs");
+                HCHECK(!x.fbc_n || x.src != x.dst, HELRM_E_PARAM, "fused base conversion cannot run in place");
+                xl->x.scal[i] = inverse ? x.scal : nullptr;
+                xl->x.fn[i] = (unsigned char)(inverse ? 0 : x.fbc_n);
+                xl->x.fh[i] = x.fbc_h;
+                xl->x.fhs[i] = (unsigned short)x.fbc_hs;
+            }
+        }
+        run_list(c, ll, inverse, ep_scal, extras ? xl.get() : nullptr);
     }
 }
 

@@ -31,68 +31,96 @@ Ciphertext *new_ct(Ctx *c, int level, double scale)
 }
 
 // ---------------------------------------------------------------- ModUp / ModDown
+// The fast base conversion runs inside the two transforms around it: the
+// inverse NTT of a source limb ends with N^-1 [(Q_j/q_s)^-1]_{q_s} instead of
+// N^-1, and the forward NTT of each converted limb computes its input from
+// the digit's source limbs on load (NttLimb::scal / fbc_*).
+void modup_limbs(Ctx *c, int level, const u64 *poly, u64 *coef, u64 *digits, std::vector<k::NttLimb> &inv,
+                 std::vector<k::NttLimb> &fwd)
+{
+    const int N = c->N, nl = level + 1 + c->K;
+    const LimbMap m = c->qmap(level);
+    for (int j = 0; j < c->dnum(level); j++) {
+        const BConvTable &t = c->modup_table(level, j);
+        const int lo = c->digit_lo(j), hi = c->digit_hi(j, level);
+        for (int l = lo; l < hi; l++) {
+            k::NttLimb x{poly + (size_t)l * N, coef + (size_t)l * N, m.pid(l), nullptr, nullptr, nullptr};
+            x.scal = t.scale(l - lo);
+            inv.push_back(x);
+        }
+        int kd = 0;   // destinations in limb order: every limb outside the digit
+        for (int l = 0; l < nl; l++) {
+            if (l >= lo && l < hi) continue;
+            k::NttLimb x{coef + (size_t)lo * N, digits + ((size_t)j * nl + l) * N, m.pid(l), nullptr, nullptr, nullptr};
+            x.fbc_n = hi - lo;
+            x.fbc_h = t.hcol(kd++);
+            x.fbc_hs = t.n_dst;
+            fwd.push_back(x);
+        }
+    }
+}
+
 void ks_modup(Ctx *c, const u64 *poly, int level, u64 *digits)
 {
     const int N = c->N, nq = level + 1, nl = nq + c->K;
-    const LimbMap m = c->qmap(level);
     DevMem coef(c, (size_t)nq * N * 8);
-    std::vector<k::NttLimb> v;   // iNTT straight from the input into coef
-    for (int l = 0; l < nq; l++) v.push_back({poly + (size_t)l * N, coef.u() + (size_t)l * N, m.pid(l), nullptr, nullptr});
-    k::ntt_run(c, v, true, nullptr);
-    k::bconv_modup(c, level, coef.u(), digits);
-    std::vector<std::pair<u32, int>> targets;   // every converted limb of every digit
-    for (int j = 0; j < c->dnum(level); j++) {
-        u64 *d = digits + (size_t)j * nl * N;
+    std::vector<k::NttLimb> inv, fwd;
+    modup_limbs(c, level, poly, coef.u(), digits, inv, fwd);
+    k::ntt_run(c, inv, true, nullptr);
+    for (int j = 0; j < c->dnum(level); j++) {   // each digit keeps its own limbs as they are
         const int lo = c->digit_lo(j), hi = c->digit_hi(j, level);
-        k::copy(c, d + (size_t)lo * N, poly + (size_t)lo * N, (size_t)(hi - lo) * N);
-        for (int l = 0; l < nl; l++)
-            if (l < lo || l >= hi) targets.push_back({(u32)(j * nl + l), m.pid(l)});
+        k::copy(c, digits + ((size_t)j * nl + lo) * N, poly + (size_t)lo * N, (size_t)(hi - lo) * N);
     }
-    k::ntt_list(c, digits, targets, false);
+    k::ntt_run(c, fwd, false, nullptr);
 }
 
 // ModDown of both halves of a QP ciphertext u = [2][nl][N] into out0, out1.
 // The iNTT reads the P limbs of u in place of a copy; the forward NTT of the
 // converted limbs ends with out = (u - y) * P^-1 (+ add) fused into its last pass.
+// One half of a ModDown: the iNTT of the K P-limbs of qp (into pc, scaled by
+// N^-1 [(P/p_i)^-1]_{p_i}) and the forward NTT of each Q-limb l converted
+// from them on load (through y), ending with out = (qp_l - y) P^-1 (+ add).
+void moddown_limbs(Ctx *c, int level, const u64 *qp, u64 *pc, u64 *y, u64 *out, const u64 *add,
+                   std::vector<k::NttLimb> &inv, std::vector<k::NttLimb> &fwd)
+{
+    const int N = c->N, nq = level + 1, K = c->K;
+    const LimbMap m = c->qmap(level);
+    const BConvTable &t = c->moddown_table(level);
+    for (int i = 0; i < K; i++) {
+        k::NttLimb x{qp + (size_t)(nq + i) * N, pc + (size_t)i * N, m.pid(nq + i), nullptr, nullptr, nullptr};
+        x.scal = t.scale(i);
+        inv.push_back(x);
+    }
+    for (int l = 0; l < nq; l++) {
+        k::NttLimb x{pc, y + (size_t)l * N, m.pid(l), qp + (size_t)l * N, out + (size_t)l * N,
+                     add ? add + (size_t)l * N : nullptr};
+        x.fbc_n = K;
+        x.fbc_h = t.hcol(l);
+        x.fbc_hs = t.n_dst;
+        fwd.push_back(x);
+    }
+}
+
 void ks_moddown2(Ctx *c, const u64 *u, int level, u64 *out0, u64 *out1, const u64 *add0, const u64 *add1)
 {
     const int N = c->N, nq = level + 1, K = c->K, nl = nq + K;
-    const LimbMap m = c->qmap(level);
     DevMem pc(c, (size_t)2 * K * N * 8), y(c, (size_t)2 * nq * N * 8);
-    std::vector<k::NttLimb> v;
+    std::vector<k::NttLimb> inv, fwd;
     for (int h = 0; h < 2; h++)
-        for (int i = 0; i < K; i++)
-            v.push_back({u + (size_t)(h * nl + nq + i) * N, pc.u() + (size_t)(h * K + i) * N, m.pid(nq + i), nullptr, nullptr});
-    k::ntt_run(c, v, true, nullptr);
-    const BConvTable &md = c->moddown_table(level);
-    k::bconv_multi(c, {{&md, pc.u(), y.u()}, {&md, pc.u() + (size_t)K * N, y.u() + (size_t)nq * N}});
-    v.clear();
-    for (int h = 0; h < 2; h++)
-        for (int l = 0; l < nq; l++) {
-            u64 *yl = y.u() + (size_t)(h * nq + l) * N;
-            const u64 *ad = h ? add1 : add0;
-            v.push_back({yl, yl, m.pid(l), u + (size_t)(h * nl + l) * N, (h ? out1 : out0) + (size_t)l * N,
-                         ad ? ad + (size_t)l * N : nullptr});
-        }
-    k::ntt_run(c, v, false, c->d_pinv_mont.u());
+        moddown_limbs(c, level, u + (size_t)h * nl * N, pc.u() + (size_t)h * K * N, y.u() + (size_t)h * nq * N,
+                      h ? out1 : out0, h ? add1 : add0, inv, fwd);
+    k::ntt_run(c, inv, true, nullptr);
+    k::ntt_run(c, fwd, false, c->d_pinv_mont.u());
 }
 
 void ks_moddown(Ctx *c, const u64 *u, int level, u64 *out)
 {
     const int N = c->N, nq = level + 1, K = c->K;
-    const LimbMap m = c->qmap(level);
     DevMem pc(c, (size_t)K * N * 8), y(c, (size_t)nq * N * 8);
-    std::vector<k::NttLimb> v;
-    for (int i = 0; i < K; i++)
-        v.push_back({u + (size_t)(nq + i) * N, pc.u() + (size_t)i * N, m.pid(nq + i), nullptr, nullptr});
-    k::ntt_run(c, v, true, nullptr);
-    k::bconv(c, c->moddown_table(level), pc.u(), y.u());
-    v.clear();
-    for (int l = 0; l < nq; l++) {
-        u64 *yl = y.u() + (size_t)l * N;
-        v.push_back({yl, yl, m.pid(l), u + (size_t)l * N, out + (size_t)l * N});
-    }
-    k::ntt_run(c, v, false, c->d_pinv_mont.u());
+    std::vector<k::NttLimb> inv, fwd;
+    moddown_limbs(c, level, u, pc.u(), y.u(), out, nullptr, inv, fwd);
+    k::ntt_run(c, inv, true, nullptr);
+    k::ntt_run(c, fwd, false, c->d_pinv_mont.u());
 }
 
 const SwitchKey *rot_key(const EvalKey *evk, u64 galois, int level)

@@ -402,6 +402,63 @@ void moddown_b(Ctx *c, const std::vector<const u64 *> &u, int level, int halves,
     k::ntt_run(c, fwd, false, c->d_pinv_mont.u());
 }
 
+// A ModDown of both halves followed by a rescale, merged into one pair of
+// transforms: out = rescale((u - FBC([u]_P)) P^-1 + add) at level - 1 with
+// scale / q_level (NttRescale: the same residues as moddown_b + rescale_b).
+// u[q] = [2][level+1+K][N]; add0/add1 entries may be null.
+Owned moddown_rescale_b(Ctx *c, const std::vector<const u64 *> &u, int level, const std::vector<double> &scale,
+                        const std::vector<const u64 *> &add0, const std::vector<const u64 *> &add1)
+{
+    HCHECK(level >= 1, HELRM_E_LEVEL, "no level left to rescale");
+    const int N = c->N, nq = level + 1, K = c->K, nl = nq + K;
+    const size_t B = u.size();
+    const BConvTable &t = c->moddown_table(level);
+    const LimbMap m = c->qmap(level);
+    Owned o;
+    for (size_t q = 0; q < B; q++) o.v.emplace_back(new_ct(c, level - 1, scale[q] / (double)c->primes[level]));
+    // per half: K P-limbs (scaled for the conversion), the top Q-limb of u and of the addend (plain)
+    DevMem pc(c, B * 2 * K * N * 8), top(c, B * 2 * 2 * N * 8), y(c, B * 2 * level * N * 8);
+    std::vector<k::NttLimb> inv, fwd;
+    for (size_t q = 0; q < B; q++)
+        for (int h = 0; h < 2; h++) {
+            const size_t qh = q * 2 + h;
+            const u64 *uh = u[q] + (size_t)h * nl * N;
+            const u64 *ad = h ? add1[q] : add0[q];
+            u64 *pch = pc.u() + qh * K * N;
+            for (int i = 0; i < K; i++) {
+                k::NttLimb x{uh + (size_t)(nq + i) * N, pch + (size_t)i * N, m.pid(nq + i), nullptr, nullptr, nullptr};
+                x.scal = t.scale(i);
+                inv.push_back(x);
+            }
+            u64 *ut = top.u() + (qh * 2) * N, *at = top.u() + (qh * 2 + 1) * N;
+            inv.push_back({uh + (size_t)level * N, ut, level, nullptr, nullptr, nullptr});
+            if (ad) inv.push_back({ad + (size_t)level * N, at, level, nullptr, nullptr, nullptr});
+            u64 *oh = h ? o.v[q]->c1() : o.v[q]->c0();
+            for (int i = 0; i < level; i++) {
+                k::NttLimb x{pch, y.u() + (qh * level + i) * N, i, uh + (size_t)i * N, oh + (size_t)i * N,
+                             ad ? ad + (size_t)i * N : nullptr};
+                x.fbc_n = K;
+                x.fbc_h = t.hcol(i);
+                x.fbc_hs = t.n_dst;
+                x.rs_u = ut;
+                x.rs_add = ad ? at : nullptr;
+                fwd.push_back(x);
+            }
+        }
+    k::ntt_run(c, inv, true, nullptr);
+    k::NttRescale rs;
+    rs.hl = t.hcol(level);
+    rs.hls = t.n_dst;
+    rs.lp = level;
+    rs.pmod = c->d_pmod_mont.u();
+    rs.qlmod = c->rescale_table(level) + c->nP();
+    rs.pinv = c->d_pinv_mont.u();
+    rs.ep_scal = c->moddown_rescale_table(level);
+    rs.add_off = c->nP();
+    k::ntt_run_rescale(c, fwd, rs);
+    return o;
+}
+
 // rescale of every ciphertext (all at the same level), as ct_rescale
 Owned rescale_b(Ctx *c, const CCtVec &a)
 {
@@ -575,9 +632,10 @@ Owned rotate_b(Ctx *c, const std::vector<const EvalKey *> &evk, const CCtVec &a,
     return o;
 }
 
-// relinearisation of (d0, d1, d2) per query, as ct_relin
+// relinearisation of (d0, d1, d2) per query, as ct_relin; with rescale, the
+// result is also rescaled (the ModDown and the rescale merged)
 Owned relin_b(Ctx *c, const std::vector<const EvalKey *> &evk, const std::vector<const u64 *> &d012, int level,
-              double scale)
+              double scale, bool rescale = false)
 {
     Owned o;
     const int N = c->N, nq = level + 1, nl = nq + c->K, dnum = c->dnum(level);
@@ -595,14 +653,17 @@ Owned relin_b(Ctx *c, const std::vector<const EvalKey *> &evk, const std::vector
     for (size_t q = 0; q < B; q++) {
         u64 *uq = u.u() + q * uplane;
         jobs.push_back({uq, dg[q], relin_key(evk[q], level), 1, nullptr, nullptr});
-        o.v.emplace_back(new_ct(c, level, scale));
         uu.push_back(uq);
-        o0.push_back(o.v[q]->c0());
-        o1.push_back(o.v[q]->c1());
         a0.push_back(d012[q]);
         a1.push_back(d012[q] + plane);
     }
     ks_inner_b(c, jobs, level, false);
+    if (rescale) return moddown_rescale_b(c, uu, level, std::vector<double>(B, scale), a0, a1);
+    for (size_t q = 0; q < B; q++) {
+        o.v.emplace_back(new_ct(c, level, scale));
+        o0.push_back(o.v[q]->c0());
+        o1.push_back(o.v[q]->c1());
+    }
     moddown_b(c, uu, level, 2, o0, o1, a0, a1);   // (d0, d1) + ModDown(u)
     return o;
 }
@@ -645,8 +706,7 @@ Owned square_b(Ctx *c, const std::vector<const EvalKey *> &evk, const CCtVec &a)
         cd.push_back(d.u() + q * per);
     }
     tensor_b(c, dd, a, a, false);
-    Owned r = relin_b(c, evk, cd, l, a[0]->scale * a[0]->scale);
-    return rescale_b(c, r.craw());
+    return relin_b(c, evk, cd, l, a[0]->scale * a[0]->scale, true);
 }
 
 }  // namespace
@@ -789,17 +849,13 @@ static Owned matvec_b(Ctx *c, const Batch *bt, const PtMatrix *m, const CCtVec &
             ks_inner_b(c, jobs, l, true);
         }
     }
-    Owned o;
     std::vector<const u64 *> acc, none(B, nullptr);
-    std::vector<u64 *> o0, o1;
+    std::vector<double> sc;
     for (size_t q = 0; q < B; q++) {
-        o.v.emplace_back(new_ct(c, l, in[q]->scale * m->pt_scale));
         acc.push_back(inner.u() + q * iq);
-        o0.push_back(o.v[q]->c0());
-        o1.push_back(o.v[q]->c1());
+        sc.push_back(in[q]->scale * m->pt_scale);
     }
-    moddown_b(c, acc, l, 2, o0, o1, none, none);
-    Owned y = rescale_b(c, o.craw());
+    Owned y = moddown_rescale_b(c, acc, l, sc, none, none);   // the final ModDown and the rescale, merged
     for (auto &p : y.v) p->scale = m->out_scale;
     for (int f : m->folds) {
         Owned r = rotate_b(c, bt->evk, y.craw(), {f});
@@ -852,8 +908,7 @@ static Owned dot_interaction_b(Ctx *c, const Batch *bt, const Model *m, const CC
         }
         tensor_b(c, dd, as, rs, s > 1);
     }
-    Owned rl = relin_b(c, bt->evk, cd, lvl, c->delta * c->delta);
-    return rescale_b(c, rl.craw());
+    return relin_b(c, bt->evk, cd, lvl, c->delta * c->delta, true);
 }
 
 std::vector<Ciphertext *> model_infer_batch(Ctx *c, const Batch *bt, const CCtVec &ct_dense, const CCtVec &ct_sel)

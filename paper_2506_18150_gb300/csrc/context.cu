@@ -203,6 +203,7 @@ Ctx::~Ctx()
     modup_tab.clear();
     moddown_tab.clear();
     rescale_tab.clear();
+    mdrs_tab.clear();
     d_pinfo = DevMem();
     d_tw_fwd = DevMem();
     d_tw_inv = DevMem();
@@ -353,6 +354,27 @@ const u64 *Ctx::rescale_table(int level)
     DevMem m;
     upload(this, m, t.data(), t.size() * 8);
     return (rescale_tab[level] = std::move(m)).u();
+}
+
+// ModDown merged with the rescale at `level` (NttRescale::ep_scal): per prime
+// i < level, (P q_level)^-1 R mod q_i, then at nP + i, q_level^-1 R mod q_i.
+const u64 *Ctx::moddown_rescale_table(int level)
+{
+    auto it = mdrs_tab.find(level);
+    if (it != mdrs_tab.end()) return it->second.u();
+    std::vector<u64> t(2 * nP(), 0);
+    const u64 ql = primes[level];
+    for (int i = 0; i < level; i++) {
+        const u64 q = primes[i];
+        u64 P = 1;
+        for (int k2 = 0; k2 < K; k2++) P = h_mulmod(P, primes[L + 1 + k2] % q, q);
+        const u64 qlinv = h_inv_mod(ql % q, q);
+        t[i] = h_mulmod(h_mulmod(h_inv_mod(P, q), qlinv, q), pinfo[i].rmod, q);
+        t[nP() + i] = h_mulmod(qlinv, pinfo[i].rmod, q);
+    }
+    DevMem m;
+    upload(this, m, t.data(), t.size() * 8);
+    return (mdrs_tab[level] = std::move(m)).u();
 }
 
 // -------------------------------------------------------------- creation

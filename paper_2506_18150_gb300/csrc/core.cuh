@@ -216,6 +216,7 @@ struct Ctx : Handle {
     std::map<std::pair<int, int>, BConvTable> modup_tab;   // (level, digit)
     std::map<int, BConvTable> moddown_tab;                 // level
     std::map<int, DevMem> rescale_tab;                     // level -> constants
+    std::map<int, DevMem> mdrs_tab;                        // level -> merged ModDown + rescale constants
     u64 mem_in_use = 0, mem_cap = 0, mem_peak = 0;   // bytes held, cap, high-water mark
     // NTT launch shape per limb-count bucket (<= 4, <= 16, <= 64, more limbs per
     // launch): words per CTA tile and the CTA count (in multiples of the SM count)
@@ -266,6 +267,7 @@ struct Ctx : Handle {
     const BConvTable &modup_table(int level, int digit);
     const BConvTable &moddown_table(int level);
     const u64 *rescale_table(int level);
+    const u64 *moddown_rescale_table(int level);
     // synchronise; if a kernel flagged bad data since the last check, clear and raise
     void check_device_errors();
 };
@@ -442,7 +444,26 @@ struct NttLimb {
     int fbc_n = 0;                      // forward: source limbs of the conversion (0: plain input)
     const u64 *fbc_h = nullptr;         // forward: the conversion constants (device pointer)
     int fbc_hs = 0;                     // their stride
+    const u64 *rs_u = nullptr;          // merged rescale (ntt_run_rescale): top limb of u, coefficients
+    const u64 *rs_add = nullptr;        //   top limb of the addend, coefficients (null: none)
 };
+// A ModDown merged with the rescale that follows it (forward transform of the
+// Q-limbs below the dropped prime q_l): the input of limb i is
+// FBC_i + P r, where r is the centred coefficient of the ModDown result's top
+// limb, x = (u_l - FBC_l) P^-1 (+ add_l) mod q_l, recomputed on load from the
+// same sources; the epilogue is eo = (u_i - NTT) (P q_l)^-1 + add_i q_l^-1.
+// Every step is exact modular arithmetic, so the residues equal those of a
+// ModDown followed by a rescale.
+struct NttRescale {
+    const u64 *hl;          // conversion constants of q_l (device), stride hls
+    int hls, lp;            // ... and the prime id of q_l
+    const u64 *pmod;        // [pid]: P R mod q
+    const u64 *qlmod;       // [pid]: q_l mod q
+    const u64 *pinv;        // [pid]: P^-1 R mod q
+    const u64 *ep_scal;     // [pid]: (P q_l)^-1 R mod q, then at add_off + pid: q_l^-1 R mod q
+    int add_off;
+};
+void ntt_run_rescale(Ctx *c, const std::vector<NttLimb> &limbs, const NttRescale &rs);
 void ntt_run(Ctx *c, const std::vector<NttLimb> &limbs, bool inverse, const u64 *ep_scal);
 // same as ntt_fwd / ntt_inv, with the launch list built on the stack (no heap use)
 void ntt_map_noheap(Ctx *c, u64 *data, int n_limbs, LimbMap map, bool inverse);

@@ -49,8 +49,22 @@ constexpr int FBC_MAX = 4;
 struct XList {
     const ulonglong2 *scal[MAX_LIMBS];   // inverse: final scale (null: N^-1)
     const u64 *fh[MAX_LIMBS];            // forward: conversion constants, stride fhs
+    const u64 *rs_u[MAX_LIMBS];          // forward, merged rescale: top limb of the half (coefficients)
+    const u64 *rs_add[MAX_LIMBS];        //   and of its addend (null: none)
     unsigned short fhs[MAX_LIMBS];
     unsigned char fn[MAX_LIMBS];         // forward: source limbs (0: plain input)
+    // merged rescale, uniform over the launch: the conversion constants of the
+    // dropped prime q_l (stride hls), its prime id, and per prime id P R mod q
+    // and q_l mod q
+    const u64 *hl;
+    int hls, lp;
+    const u64 *pmod, *qlmod, *pinv;
+};
+// Epilogue constants of a forward transform's last pass: eo = (ea - NTT(y)) *
+// scal[pid] + eb, the addend scaled by scal[add_off + pid] when add_off > 0.
+struct Ep {
+    const u64 *scal = nullptr;
+    int add_off = 0;
 };
 template <bool XL>
 struct XArg {
@@ -110,8 +124,8 @@ template <int LOGP, bool COLS, bool INV, int FIXN = 0, int FIXG = 0, bool XL = f
 __global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN_arg, int logG_arg, LimbList list,
                                                    const ulonglong2 *__restrict__ tw_all,
                                                    const ulonglong2 *__restrict__ ninv,
-                                                   const PrimeInfo *__restrict__ pinfo, int mode,
-                                                   const u64 *__restrict__ ep_scal, const XArg<XL> xa)
+                                                   const PrimeInfo *__restrict__ pinfo, int mode, const Ep ep,
+                                                   const XArg<XL> xa)
 {
     constexpr int P = 1 << LOGP;
     constexpr int TPS = P / 8;              // threads per sub-transform
@@ -154,7 +168,10 @@ __global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN_arg, int l
     // fetch it.
     const PrimeInfo pi = pinfo[pid];
     int fn = 0;                 // fused conversion: source limbs and their constants
-    u64 hk[FBC_MAX];
+    u64 hk[FBC_MAX], hl[FBC_MAX];
+    const u64 *rs_u = nullptr, *rs_add = nullptr;
+    PrimeInfo pl;
+    u64 pl_pinv = 0, pmod_q = 0, qlmod_q = 0;
     ulonglong2 xs = make_ulonglong2(0, 0);
     if constexpr (XL) {
         if (!INV) {
@@ -163,6 +180,16 @@ __global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN_arg, int l
             const int hs = xa.x.fhs[y];
 #pragma unroll
             for (int s = 0; s < FBC_MAX; s++) hk[s] = s < fn ? fh[s * hs] : 0;
+            rs_u = xa.x.rs_u[y];
+            if (rs_u) {   // merged rescale: the dropped prime's constants
+                rs_add = xa.x.rs_add[y];
+#pragma unroll
+                for (int s = 0; s < FBC_MAX; s++) hl[s] = s < fn ? xa.x.hl[s * xa.x.hls] : 0;
+                pl = pinfo[xa.x.lp];
+                pl_pinv = xa.x.pinv[xa.x.lp];
+                pmod_q = xa.x.pmod[pid];
+                qlmod_q = xa.x.qlmod[pid];
+            }
         } else if (xa.x.scal[y]) {
             xs = *xa.x.scal[y];
         }
@@ -214,9 +241,26 @@ __global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN_arg, int l
                     for (int k = 0; k < gs; k++) {
                         const size_t a = gaddr(elem(qg, k));
                         Acc128 acc;
+                        u64 ts[FBC_MAX];
 #pragma unroll
                         for (int s = 0; s < FBC_MAX; s++)
-                            if (s < fn) acc.mac(in[(size_t)s * N + a], hk[s], q);
+                            if (s < fn) {
+                                ts[s] = in[(size_t)s * N + a];
+                                acc.mac(ts[s], hk[s], q);
+                            }
+                        if (rs_u) {
+                            // the ModDown result's top limb in coefficient form,
+                            // x = (u_l - FBC_l) P^-1 (+ add_l) mod q_l, centred and
+                            // taken mod q: P r joins the conversion before the REDC
+                            Acc128 al;
+#pragma unroll
+                            for (int s = 0; s < FBC_MAX; s++)
+                                if (s < fn) al.mac(ts[s], hl[s], pl.q);
+                            u64 x = mont_mul(sub_mod(rs_u[a], al.reduce(pl.q, pl.qinv), pl.q), pl_pinv, pl.q, pl.qinv);
+                            if (rs_add) x = add_mod(x, rs_add[a], pl.q);
+                            const u64 xm = x < q ? x : x % q;
+                            acc.mac(x <= ((pl.q - 1) >> 1) ? xm : sub_mod(xm, qlmod_q, q), pmod_q, q);
+                        }
                         v[qg * gs + k] = acc.reduce(q, pi.qinv);
                     }
             } else {
@@ -267,9 +311,12 @@ __global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN_arg, int l
                 for (int k = 0; k < gs; k++) sm[saddr(elem(qg, k))] = v[qg * gs + k];
         } else {
             ulonglong2 ni = make_ulonglong2(0, 0);
-            u64 ec = 0;
+            u64 ec = 0, ec2 = 0;
             if (mode == M_SCALE) ni = (XL && INV && xs.x) ? xs : ninv[pid];
-            if (mode == M_REDUCE && ea) ec = ep_scal[pid];
+            if (mode == M_REDUCE && ea) {
+                ec = ep.scal[pid];
+                if (ep.add_off) ec2 = ep.scal[ep.add_off + pid];
+            }
 #pragma unroll
             for (int qg = 0; qg < ng; qg++)
 #pragma unroll
@@ -282,7 +329,7 @@ __global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN_arg, int l
                         z = csub(csub(z, q2), q);
                         if (ea) {
                             u64 w = mont_mul(sub_mod(ea[a], z, q), ec, q, pi.qinv);
-                            if (eb) w = add_mod(w, eb[a], q);
+                            if (eb) w = add_mod(w, ep.add_off ? mont_mul(eb[a], ec2, q, pi.qinv) : eb[a], q);
                             eo[a] = w;
                         } else
                             out[a] = z;
@@ -296,7 +343,7 @@ __global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN_arg, int l
 
 template <int LOGP, bool COLS, bool INV, int FIXN, int FIXG, bool XL>
 void launch_kernel(Ctx *c, dim3 grid, int threads, size_t smem, const LimbList &ll, int first, int logG, int mode,
-                   const u64 *ep_scal, const XArg<XL> &xa)
+                   const Ep &ep_scal, const XArg<XL> &xa)
 {
     const ulonglong2 *tw = INV ? c->d_tw_inv.as<ulonglong2>() : c->d_tw_fwd.as<ulonglong2>();
     launch(c, k_ntt_pass<LOGP, COLS, INV, FIXN, FIXG, XL>, grid, threads, smem, first, c->logN, logG, ll, tw,
@@ -304,7 +351,7 @@ void launch_kernel(Ctx *c, dim3 grid, int threads, size_t smem, const LimbList &
 }
 
 template <int LOGP, bool COLS, bool INV, bool XL>
-void launch_pass(Ctx *c, const LimbList &ll, int n_sub, int first, int mode, const u64 *ep_scal, const XArg<XL> &xa)
+void launch_pass(Ctx *c, const LimbList &ll, int n_sub, int first, int mode, const Ep &ep_scal, const XArg<XL> &xa)
 {
     constexpr int P = 1 << LOGP;
     // sub-transforms per CTA: as many as fit the tuned tile, fewer when the
@@ -335,7 +382,7 @@ void launch_pass(Ctx *c, const LimbList &ll, int n_sub, int first, int mode, con
 }
 
 template <bool COLS, bool INV, bool XL>
-void dispatch(Ctx *c, int logp, const LimbList &ll, int n_sub, int first, int mode, const u64 *ep_scal,
+void dispatch(Ctx *c, int logp, const LimbList &ll, int n_sub, int first, int mode, const Ep &ep_scal,
               const XArg<XL> &xa)
 {
     switch (logp) {
@@ -349,23 +396,24 @@ void dispatch(Ctx *c, int logp, const LimbList &ll, int n_sub, int first, int mo
 
 // both passes of one launch list; xl (may be null) holds the column pass's
 // per-limb extras: the forward transform's first pass, the inverse's last
-void run_list(Ctx *c, const LimbList &ll, bool inverse, const u64 *ep_scal, const XArg<true> *xl = nullptr)
+void run_list(Ctx *c, const LimbList &ll, bool inverse, const Ep &ep_scal, const XArg<true> *xl = nullptr)
 {
     const int logN = c->logN, logN1 = logN / 2, logN2 = logN - logN1;
     const int N1 = 1 << logN1, N2 = 1 << logN2;
     const XArg<false> none;
+    const Ep no_ep;
     if (!inverse) {
         if (xl)
-            dispatch<true, false, true>(c, logN1, ll, N2, 1, M_LAZY, nullptr, *xl);
+            dispatch<true, false, true>(c, logN1, ll, N2, 1, M_LAZY, no_ep, *xl);
         else
-            dispatch<true, false, false>(c, logN1, ll, N2, 1, M_LAZY, nullptr, none);
+            dispatch<true, false, false>(c, logN1, ll, N2, 1, M_LAZY, no_ep, none);
         dispatch<false, false, false>(c, logN2, ll, N1, 0, M_REDUCE, ep_scal, none);
     } else {
-        dispatch<false, true, false>(c, logN2, ll, N1, 1, M_LAZY, nullptr, none);
+        dispatch<false, true, false>(c, logN2, ll, N1, 1, M_LAZY, no_ep, none);
         if (xl)
-            dispatch<true, true, true>(c, logN1, ll, N2, 0, M_SCALE, nullptr, *xl);
+            dispatch<true, true, true>(c, logN1, ll, N2, 0, M_SCALE, no_ep, *xl);
         else
-            dispatch<true, true, false>(c, logN1, ll, N2, 0, M_SCALE, nullptr, none);
+            dispatch<true, true, false>(c, logN1, ll, N2, 0, M_SCALE, no_ep, none);
     }
     c->launches += 2;
     CUDA_CHECK(cudaGetLastError());
@@ -375,7 +423,9 @@ void run_list(Ctx *c, const LimbList &ll, bool inverse, const u64 *ep_scal, cons
 
 namespace k {
 
-void ntt_run(Ctx *c, const std::vector<NttLimb> &limbs, bool inverse, const u64 *ep_scal)
+// rs (forward only, may be null): the launch is a merged ModDown + rescale
+static void ntt_run_impl(Ctx *c, const std::vector<NttLimb> &limbs, bool inverse, const Ep &ep,
+                         const NttRescale *rs)
 {
     if (limbs.empty()) return;
     KTimer kt(c, "ntt", 16.0 * c->N * limbs.size());   // algorithmic: each limb read and written once
@@ -383,7 +433,7 @@ void ntt_run(Ctx *c, const std::vector<NttLimb> &limbs, bool inverse, const u64 
     for (size_t b = 0; b < limbs.size(); b += MAX_LIMBS) {
         LimbList ll;
         ll.n = (int)std::min<size_t>(MAX_LIMBS, limbs.size() - b);
-        bool extras = false;
+        bool extras = rs != nullptr;
         for (int i = 0; i < ll.n; i++) {
             const NttLimb &x = limbs[b + i];
             ll.src[i] = x.src;
@@ -401,14 +451,40 @@ void ntt_run(Ctx *c, const std::vector<NttLimb> &limbs, bool inverse, const u64 
                 HCHECK(x.fbc_n >= 0 && x.fbc_n <= FBC_MAX && x.fbc_hs >= 0 && x.fbc_hs < 65536, HELRM_E_PARAM,
                        "fused base conversion: at most 4 source limbs");
                 HCHECK(!x.fbc_n || x.src != x.dst, HELRM_E_PARAM, "fused base conversion cannot run in place");
+                HCHECK(!x.rs_u || (rs && x.fbc_n), HELRM_E_PARAM, "a merged rescale needs a fused conversion");
                 xl->x.scal[i] = inverse ? x.scal : nullptr;
                 xl->x.fn[i] = (unsigned char)(inverse ? 0 : x.fbc_n);
                 xl->x.fh[i] = x.fbc_h;
                 xl->x.fhs[i] = (unsigned short)x.fbc_hs;
+                xl->x.rs_u[i] = inverse ? nullptr : x.rs_u;
+                xl->x.rs_add[i] = inverse ? nullptr : x.rs_add;
+            }
+            if (rs) {
+                xl->x.hl = rs->hl;
+                xl->x.hls = rs->hls;
+                xl->x.lp = rs->lp;
+                xl->x.pmod = rs->pmod;
+                xl->x.qlmod = rs->qlmod;
+                xl->x.pinv = rs->pinv;
             }
         }
-        run_list(c, ll, inverse, ep_scal, extras ? xl.get() : nullptr);
+        run_list(c, ll, inverse, ep, extras ? xl.get() : nullptr);
     }
+}
+
+void ntt_run(Ctx *c, const std::vector<NttLimb> &limbs, bool inverse, const u64 *ep_scal)
+{
+    Ep ep;
+    ep.scal = ep_scal;
+    ntt_run_impl(c, limbs, inverse, ep, nullptr);
+}
+
+void ntt_run_rescale(Ctx *c, const std::vector<NttLimb> &limbs, const NttRescale &rs)
+{
+    Ep ep;
+    ep.scal = rs.ep_scal;
+    ep.add_off = rs.add_off;
+    ntt_run_impl(c, limbs, false, ep, &rs);
 }
 
 // Contiguous limbs described by a LimbMap, in place; the launch list is built
@@ -428,7 +504,7 @@ void ntt_map_noheap(Ctx *c, u64 *data, int n_limbs, LimbMap map, bool inverse)
             ll.eo[i] = nullptr;
             ll.pid[i] = (unsigned short)map.pid(b + i);
         }
-        run_list(c, ll, inverse, nullptr);
+        run_list(c, ll, inverse, Ep());
     }
 }
 

@@ -223,7 +223,7 @@ helrm_status helrm_rotate_hoisted(helrm_ctx *ctx, const helrm_evk *evk, const he
 /* Encode the BSGS diagonals of the rows x cols row-major FP64 matrix W, padded
  * to out_pad x in_pad (powers of two, <= n): D = min(in_pad, out_pad) extended
  * diagonals diag_i[j] = W[j mod out_pad, (j+i) mod in_pad], split i = g n1 + b
- * (n1 = min(D, 64) baby steps, n2 = D / n1 giant steps), pre-rotated by -g n1 and
+ * (n1 = min(D, max(16, D / 8)) baby steps, n2 = D / n1 giant steps), pre-rotated by -g n1 and
  * encoded over the QP basis at `level` with scale q_level * target_scale /
  * ct_scale.  All-zero diagonals are skipped. */
 helrm_status helrm_ptmat_prepare(helrm_ctx *ctx, const double *W, uint32_t rows, uint32_t cols,

@@ -35,16 +35,17 @@ def pow2ceil(x: int) -> int:
     return 1 << (x - 1).bit_length()
 
 
-BABY_MAX = 64
+BABY_MIN, GIANT_MAX = 16, 8
 
 
 def bsgs_split(D: int):
-    """n1 = min(D, 64) baby steps, n2 = D / n1 giant steps.
+    """n1 = min(D, max(16, D / 8)) baby steps, n2 = D / n1 giant steps.
 
-    A hoisted baby step costs one key inner product; a giant step costs a
-    ModDown and a ModUp as well, so the split favours baby steps (the paper
-    fixes only that BSGS needs O(sqrt n) rotations, not the split)."""
-    n1 = min(D, BABY_MAX)
+    The paper fixes only that BSGS needs O(sqrt n) rotations, not the split.
+    A hoisted baby step costs one key inner product (a key read), a giant
+    step a ModDown and a ModUp as well; this split keeps at most 8 giant
+    steps and otherwise trades baby-step keys for giant steps."""
+    n1 = min(D, max(BABY_MIN, D // GIANT_MAX))
     return n1, D // n1
 
 

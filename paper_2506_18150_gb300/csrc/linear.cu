@@ -5,9 +5,9 @@
 // slots.  For W padded to out_pad x in_pad there are D = min(in_pad, out_pad)
 // extended diagonals diag_i[j] = W[j mod out_pad, (j + i) mod in_pad]; when the
 // matrix is wide, rotate-and-add folds by in_pad/2, ..., out_pad finish the
-// sum.  BSGS: n1 = min(D, 64), n2 = D / n1 (a giant step costs a ModDown and a
-// ModUp, a hoisted baby step only a key inner product, so baby steps win),
-// i = g n1 + b, diag'_{g,b} = rot(diag_i, -g n1), which reads
+// sum.  BSGS: n1 = min(D, max(16, D / 8)), n2 = D / n1 <= 8 (a hoisted baby
+// step costs a key inner product and a key read, a giant step a ModDown and a
+// ModUp as well), i = g n1 + b, diag'_{g,b} = rot(diag_i, -g n1), which reads
 // W[(j - g n1) mod out_pad, (j + b) mod in_pad].
 //
 // Double hoisting: one ModUp of c1; each baby step b is phi_{5^b} applied to
@@ -71,7 +71,7 @@ PtMatrix *ptmat_prepare(Ctx *c, const double *W, int rows, int cols, int in_pad,
     m->in_pad = in_pad;
     m->out_pad = out_pad;
     m->D = std::min(in_pad, out_pad);
-    m->n1 = std::min(m->D, 64);
+    m->n1 = std::min(m->D, std::max(16, m->D / 8));   // at most 8 giant steps
     m->n2 = m->D / m->n1;
     m->level = level;
     for (int s = in_pad / 2; s >= out_pad; s /= 2) m->folds.push_back(s);

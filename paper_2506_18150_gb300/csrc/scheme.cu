@@ -487,17 +487,20 @@ Ciphertext *encrypt_pt(Ctx *c, const EvalKey *evk, const Plaintext *pt, u64 seed
     const int l = pt->level, nq = l + 1, N = c->N, nqL = c->L + 1;
     std::unique_ptr<Ciphertext> ct(new_ct(c, l, pt->scale));
     LimbMap qm = c->qmap(l);
-    DevMem raw(c, (size_t)N * 8), v(c, (size_t)nq * N * 8), e(c, (size_t)nq * N * 8);
+    // v, e0 and e1 (each sampled from its own counter stream) are transformed
+    // by one NTT launch: vee = [v | e0 | e1], each nq limbs
+    DevMem raw(c, (size_t)3 * N * 8), vee(c, (size_t)3 * nq * N * 8);
     k::sample_ternary(c, raw.as<i64>(), seed, P_ENC_V, 0);
-    k::from_signed(c, v.u(), raw.as<i64>(), nq, qm);
-    k::ntt_fwd(c, v.u(), nq, qm);
+    k::sample_cbd21(c, raw.as<i64>() + N, seed, P_ENC_E0, 0);
+    k::sample_cbd21(c, raw.as<i64>() + 2 * (size_t)N, seed, P_ENC_E1, 0);
+    for (int p = 0; p < 3; p++)
+        k::from_signed(c, vee.u() + (size_t)p * nq * N, raw.as<i64>() + (size_t)p * N, nq, qm);
+    k::ntt_fwd(c, vee.u(), 3 * nq, c->qmap(l, 0, nq));
+    const u64 *v = vee.u();
     for (int p = 0; p < 2; p++) {
         u64 *dst = p ? ct->c1() : ct->c0();
-        k::sample_cbd21(c, raw.as<i64>(), seed, p ? P_ENC_E1 : P_ENC_E0, 0);
-        k::from_signed(c, e.u(), raw.as<i64>(), nq, qm);
-        k::ntt_fwd(c, e.u(), nq, qm);
-        k::mul_mont(c, dst, v.u(), evk->pk.u() + (size_t)p * nqL * N, nq, qm);
-        k::add(c, dst, dst, e.u(), nq, qm);
+        k::mul_mont(c, dst, v, evk->pk.u() + (size_t)p * nqL * N, nq, qm);
+        k::add(c, dst, dst, vee.u() + (size_t)(1 + p) * nq * N, nq, qm);
     }
     k::add(c, ct->c0(), ct->c0(), pt->data.u(), nq, qm);
     return ct.release();

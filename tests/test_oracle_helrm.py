@@ -81,9 +81,12 @@ def test_diagonal_count_for_416_outputs():
 
 
 def test_bsgs_split():
-    for D, n1, n2 in [(1, 1, 1), (2, 2, 1), (16, 16, 1), (32, 32, 1), (64, 64, 1), (256, 64, 4),
-                      (512, 64, 8), (1024, 64, 16)]:
+    for D, n1, n2 in [(1, 1, 1), (2, 2, 1), (16, 16, 1), (32, 16, 2), (64, 16, 4), (128, 16, 8),
+                      (256, 32, 8), (512, 64, 8), (1024, 128, 8)]:
         assert linear.bsgs_split(D) == (n1, n2)
+    for k in range(16):   # every power-of-two D: an exact split with at most 8 giant steps
+        n1, n2 = linear.bsgs_split(1 << k)
+        assert n1 * n2 == 1 << k and n2 <= 8
 
 
 @pytest.mark.parametrize("shape", [(16, 64), (64, 16), (32, 32), (1, 32), (10, 3), (5, 7)])

@@ -206,6 +206,18 @@ helrm_status helrm_mul_pt(helrm_ctx *ctx, const helrm_ct *a, const helrm_pt *pt,
  * "Multiplication ... followed by a rescaling procedure"). */
 helrm_status helrm_mul(helrm_ctx *ctx, const helrm_evk *evk, const helrm_ct *a, const helrm_ct *b,
                        helrm_ct **out);
+/* out = p(x) slot-wise for p(x) = sum_k coeffs[k] x^k, degree d = n_coeffs - 1
+ * >= 1 with coeffs[d] != 0 (the polynomial activations of Sec. 2.1.4 /
+ * Sec. 5.4).  The needed powers x^k = x^a x^(k-a) (a the largest power of
+ * two below k) are ct x ct products; each term a_k x^k is the power at the
+ * deepest power's level L_c times the integer round_half_away(a_k s_k),
+ * s_k = target_scale q_{L_c} / scale(x^k); the sum is rescaled once and a_0
+ * added as the integer round_half_away(a_0 scale) in every slot.  Consumes
+ * ceil(log2 d) + 1 levels; the output scale is target_scale up to FP64
+ * rounding.  Errors: HELRM_E_LEVEL if the input level is too low,
+ * HELRM_E_INVAL for a constant polynomial or a zero leading coefficient. */
+helrm_status helrm_poly_eval(helrm_ctx *ctx, const helrm_evk *evk, const helrm_ct *x, const double *coeffs,
+                             uint32_t n_coeffs, double target_scale, helrm_ct **out);
 /* Drop q_level: out = round(x / q_level) (centred remainder). */
 helrm_status helrm_rescale(helrm_ctx *ctx, const helrm_ct *a, helrm_ct **out);
 /* Keep limbs q_0..q_level (level <= current). */
@@ -303,10 +315,17 @@ typedef struct {
     const float *const *tables;      /* as for helrm_emb_prepare */
     int32_t interaction;             /* 0 = pairwise dot, 1 = concatenation */
     uint64_t threshold;              /* tables with more rows are digit-decomposed (0 = base_p) */
+    uint32_t act_degree;             /* 0: the activation is x^2; d >= 1: the polynomial below */
+    const double *act_coeffs;        /* a_0 .. a_d (powers of x, a_d != 0), see helrm_poly_eval */
 } helrm_model_desc;
 
 /* Compile the model: layouts, as-late-as-possible levels (the logit ends at
- * level 0), all diagonals, biases and masks encoded on the device.
+ * level 0), all diagonals, biases and masks encoded on the device.  Each
+ * activation (after every bottom layer and every top layer but the last)
+ * costs one level for x^2, or ceil(log2 d) + 1 for a degree-d polynomial: it
+ * is evaluated without a_0 (helrm_poly_eval's schedule), and a_0 is then added
+ * as a plaintext on the layer's real outputs only, so that the layout's zero
+ * padding stays zero.
  * Errors: HELRM_E_PARAM if the chain is too short or a layout exceeds n. */
 helrm_status helrm_model_create(helrm_ctx *ctx, const helrm_model_desc *desc, helrm_model **out);
 /* info_out[0..9] = level of ct_dense, level of ct_sel, level of z, level of
@@ -317,10 +336,10 @@ helrm_status helrm_model_create(helrm_ctx *ctx, const helrm_model_desc *desc, he
 helrm_status helrm_model_info(const helrm_model *m, uint32_t *info_out);
 helrm_status helrm_model_rotations(const helrm_model *m, int32_t *steps_out, uint32_t *n_out);
 /* Replace / read all encoded plaintexts (count x N signed coefficients) in
- * the canonical order: per bottom layer its diagonals then its bias; the
- * embedding diagonals (selector ciphertext by selector ciphertext); (dot) the
- * ones block and masks 0..S; per top layer its
- * diagonals then its bias. */
+ * the canonical order: per bottom layer its diagonals, its bias, then (a
+ * polynomial activation with a_0 != 0) its a_0 plaintext; the embedding
+ * diagonals (selector ciphertext by selector ciphertext); (dot) the ones
+ * block and masks 0..S; per top layer the same as per bottom layer. */
 helrm_status helrm_model_import_plaintexts(helrm_ctx *ctx, helrm_model *m, const int64_t *coeffs,
                                            uint32_t count);
 helrm_status helrm_model_export_plaintexts(helrm_ctx *ctx, const helrm_model *m, int64_t *coeffs,

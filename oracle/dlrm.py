@@ -22,7 +22,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import ckks, linear, ring
+from . import ckks, linear, poly, ring
 
 DIM = 16
 
@@ -119,14 +119,44 @@ def embedding_cleartext(cards, p, tables, indices, threshold=None):
     return out
 
 
+def activation(spec, v):
+    """x^2, or the model's activation polynomial (spec.act, powers of x)."""
+    act = getattr(spec, "act", None)
+    if act is None:
+        return v ** 2
+    return np.polynomial.polynomial.polyval(v, np.asarray(act, dtype=np.float64))
+
+
+def act_const(p: ckks.Params, spec, rows: int, out_pad: int, scale: float):
+    """The polynomial's a_0 as a plaintext on the layer's real outputs only
+    (rows of each period out_pad), at the activation's output scale: the
+    homomorphic polynomial is evaluated without a_0, so the zero padding of
+    the layout stays zero (x^2 keeps it zero by itself)."""
+    act = getattr(spec, "act", None)
+    if act is None or act[0] == 0:
+        return None
+    return ckks.encode_real(p, replicate(np.full(rows, float(act[0])), out_pad, p.n), scale)
+
+
+def act_linear(act):
+    """The activation polynomial without its constant term (evaluated on the ciphertext)."""
+    return (0.0,) + tuple(act[1:])
+
+
+def activation_levels(spec) -> int:
+    """Levels one activation consumes: 1 for x^2, poly.depth(d) for a polynomial."""
+    act = getattr(spec, "act", None)
+    return 1 if act is None else poly.depth(len(act) - 1)
+
+
 def dlrm_cleartext(spec, w, dense, indices):
-    """Bottom MLP (x^2 after every layer), embeddings, interaction
+    """Bottom MLP (the activation after every layer), embeddings, interaction
     ([b; e_1..e_T] for concat; [b; <z_a, z_c> for a < c] for dot, pairs in
-    lexicographic order), top MLP (x^2 after all but the last layer); returns
-    (logit, sigmoid(logit), top-MLP input)."""
+    lexicographic order), top MLP (the activation after all but the last
+    layer); returns (logit, sigmoid(logit), top-MLP input)."""
     h = np.asarray(dense, dtype=np.float64)
     for W, b in zip(w.bottom_W, w.bottom_b):
-        h = (W @ h + b) ** 2
+        h = activation(spec, W @ h + b)
     embs = embedding_cleartext(spec.cards, spec.base, w.tables, indices, spec.threshold)
     blocks = [h] + embs
     if spec.interaction == "dot":
@@ -139,7 +169,7 @@ def dlrm_cleartext(spec, w, dense, indices):
     for i, (W, b) in enumerate(zip(w.top_W, w.top_b)):
         y = W @ y + b
         if i + 1 < len(w.top_W):
-            y = y ** 2
+            y = activation(spec, y)
     logit = float(y[0])
     return logit, 1.0 / (1.0 + np.exp(-logit)), x
 
@@ -151,7 +181,8 @@ def dlrm_cleartext(spec, w, dense, indices):
 class Layer:
     pm: linear.PtMatrix
     bias: np.ndarray | None          # signed coefficients at (level - 1), scale = out_scale
-    square: bool
+    square: bool                     # an activation follows (x^2, or the model's polynomial)
+    act_const: np.ndarray | None = None   # polynomial activation: a_0 on the layer's real outputs
 
 
 @dataclass
@@ -197,18 +228,22 @@ class Compiled:
 
     def plaintexts(self):
         """Every plaintext of the model, in the canonical order: per bottom
-        layer its diagonals in (g, b) order then its bias; the embedding
-        diagonals; (dot) the ones block and the masks 0..S; per top layer its
-        diagonals then its bias."""
+        layer its diagonals in (g, b) order, its bias, then (polynomial
+        activation with a_0 != 0) its activation constant; the embedding
+        diagonals; (dot) the ones block and the masks 0..S; per top layer the
+        same as per bottom layer."""
+        def layer(lay):
+            return [lay.pm.pts[k] for k in lay.pm.ordered_keys()] + [lay.bias] + \
+                ([lay.act_const] if lay.act_const is not None else [])
         out = []
         for lay in self.bottom:
-            out += [lay.pm.pts[k] for k in lay.pm.ordered_keys()] + [lay.bias]
+            out += layer(lay)
         for pm in self.emb_pms():
             out += [pm.pts[k] for k in pm.ordered_keys()]
         if self.spec.interaction == "dot":
             out += [self.ones] + list(self.masks)
         for lay in self.top:
-            out += [lay.pm.pts[k] for k in lay.pm.ordered_keys()] + [lay.bias]
+            out += layer(lay)
         return out
 
 
@@ -238,15 +273,18 @@ def dot_top_matrix(W0: np.ndarray, B: int, Bp: int, S: int, W2: int, W_u: int) -
 
 def compile_model(p: ckks.Params, spec, w) -> Compiled:
     """Levels are assigned as late as possible so the logit ends at level 0:
-    each matvec and each x^2 consumes one level, the dot interaction two."""
+    each matvec consumes one level, each activation one (x^2) or poly.depth(d)
+    (a degree-d polynomial), the dot interaction two."""
     T = len(spec.cards)
     B = T + 1
     n_bot, n_top = len(w.bottom_W), len(w.top_W)
-    lvl_u = 2 * n_top - 1
+    act = getattr(spec, "act", None)
+    ad = activation_levels(spec)
+    lvl_u = (1 + ad) * (n_top - 1) + 1
     dot = spec.interaction == "dot"
     lvl_z = lvl_u + 2 if dot else lvl_u
     lvl_sel = lvl_z + 1
-    lvl_dense = lvl_z + 2 * n_bot
+    lvl_dense = lvl_z + (1 + ad) * n_bot
     if lvl_dense > p.L:
         raise ValueError(f"model needs {lvl_dense} levels, chain has {p.L}")
     Bp = B + 1 if dot else B
@@ -273,8 +311,12 @@ def compile_model(p: ckks.Params, spec, w) -> Compiled:
         bias = ckks.encode_real(p, replicate(b, out_pad, p.n), delta)
         c.bottom.append(Layer(pm, bias, True))
         lvl -= 1
-        scale = (delta * delta) / p.q[lvl]
-        lvl -= 1
+        if act is None:
+            scale = (delta * delta) / p.q[lvl]
+            lvl -= 1
+        else:
+            lvl, scale = poly.simulate(p.q, lvl, delta, act_linear(act), delta)
+            c.bottom[-1].act_const = act_const(p, spec, W.shape[0], out_pad, scale)
         in_pad = out_pad
     assert lvl == lvl_z
     scale_b = scale
@@ -316,8 +358,12 @@ def compile_model(p: ckks.Params, spec, w) -> Compiled:
         lvl -= 1
         scale = delta
         if not last:
-            scale = (delta * delta) / p.q[lvl]
-            lvl -= 1
+            if act is None:
+                scale = (delta * delta) / p.q[lvl]
+                lvl -= 1
+            else:
+                lvl, scale = poly.simulate(p.q, lvl, delta, act_linear(act), delta)
+                c.top[-1].act_const = act_const(p, spec, W.shape[0], out_pad, scale)
     assert lvl == 0
     return c
 
@@ -348,11 +394,16 @@ def encrypt_query(p, keys, c: Compiled, dense, indices, seed: int):
     return ct_d, ct_s
 
 
-def _dense_layer(p, keys, lay: Layer, x: ckks.Ct) -> ckks.Ct:
+def _dense_layer(p, keys, lay: Layer, x: ckks.Ct, act=None) -> ckks.Ct:
     y = linear.matvec(p, keys, lay.pm, x)
     y = ckks.add_pt(p, y, lay.bias, y.scale)
     if lay.square:
-        y = ckks.square(p, keys, y)
+        if act is None:
+            y = ckks.square(p, keys, y)
+        else:   # the polynomial without a_0, then a_0 on the real outputs only
+            y = poly.poly_eval(p, keys, y, act_linear(act), p.delta)
+            if lay.act_const is not None:
+                y = ckks.add_pt(p, y, lay.act_const, y.scale)
     return y
 
 
@@ -386,7 +437,7 @@ def infer(p, keys, c: Compiled, ct_dense: ckks.Ct, ct_sel) -> ckks.Ct:
     """ct_sel: one ciphertext, or the list of them for a selector wider than n slots."""
     h = ct_dense
     for lay in c.bottom:
-        h = _dense_layer(p, keys, lay, h)
+        h = _dense_layer(p, keys, lay, h, getattr(c.spec, "act", None))
     if c.emb is None:
         e = lookup_multi(p, keys, c.emb_chunks, ct_sel)
     else:
@@ -399,7 +450,7 @@ def infer(p, keys, c: Compiled, ct_dense: ckks.Ct, ct_sel) -> ckks.Ct:
         u = z
     y = u
     for lay in c.top:
-        y = _dense_layer(p, keys, lay, y)
+        y = _dense_layer(p, keys, lay, y, getattr(c.spec, "act", None))
     return y
 
 

@@ -9,6 +9,8 @@
 #include "core.cuh"
 
 namespace helrm {
+Ciphertext *ct_poly_eval(Ctx *c, const EvalKey *evk, const Ciphertext *x, const std::vector<double> &a,
+                         double target);
 Ctx *ctx_create(const helrm_params *p, int device, void *stream);
 struct Emb;
 struct Model;
@@ -459,6 +461,16 @@ helrm_status helrm_mul(helrm_ctx *ctx, const helrm_evk *evk, const helrm_ct *a, 
     CT_OP(ct_mul(c, EVK(evk), CT(a), CT(b)));
 }
 helrm_status helrm_rescale(helrm_ctx *ctx, const helrm_ct *a, helrm_ct **out) { CT_OP(ct_rescale(c, CT(a))); }
+helrm_status helrm_poly_eval(helrm_ctx *ctx, const helrm_evk *evk, const helrm_ct *x, const double *coeffs,
+                             uint32_t n_coeffs, double target_scale, helrm_ct **out)
+{
+    if (out) *out = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        HCHECK(out && coeffs, HELRM_E_INVAL, "NULL argument");
+        *out = (helrm_ct *)ct_poly_eval(C(ctx), EVK(evk), CT(x), std::vector<double>(coeffs, coeffs + n_coeffs),
+                                        target_scale);
+    });
+}
 helrm_status helrm_drop_level(helrm_ctx *ctx, const helrm_ct *a, int32_t level, helrm_ct **out)
 {
     CT_OP(ct_drop(c, CT(a), level));

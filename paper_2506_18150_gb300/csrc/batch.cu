@@ -709,7 +709,83 @@ Owned square_b(Ctx *c, const std::vector<const EvalKey *> &evk, const CCtVec &a)
     return relin_b(c, evk, cd, l, a[0]->scale * a[0]->scale, true);
 }
 
+// every ciphertext taken down to `level` (the first level + 1 limbs of each half)
+Owned drop_b(Ctx *c, const CCtVec &a, int level)
+{
+    Owned o;
+    std::vector<u64 *> out;
+    std::vector<const u64 *> in;
+    std::vector<u64> words;
+    for (auto *x : a) {
+        HCHECK(level >= 0 && level <= x->level, HELRM_E_LEVEL, "cannot raise the level");
+        o.v.emplace_back(new_ct(c, level, x->scale));
+        for (int h = 0; h < 2; h++) {
+            out.push_back(h ? o.v.back()->c1() : o.v.back()->c0());
+            in.push_back(h ? x->c1() : x->c0());
+            words.push_back((u64)(level + 1) * c->N);
+        }
+    }
+    copy_b(c, out, in, words);
+    return o;
+}
+
 }  // namespace
+
+// The polynomial of `plan` on every query's ciphertext (poly.cu gives the
+// schedule): the needed powers by merged ct x ct products, each term times its
+// integer constant at the common level, the sum, one rescale, then a_0.
+std::vector<Ciphertext *> poly_b(Ctx *c, const std::vector<const EvalKey *> &evk, const CCtVec &x,
+                                 const ActPlan &plan)
+{
+    const size_t B = x.size();
+    HCHECK(B >= 1 && evk.size() == B, HELRM_E_INVAL, "one key set per ciphertext");
+    for (auto *ct : x)
+        HCHECK(ct->level == plan.in_level && ct->scale == plan.in_scale, HELRM_E_SCALE,
+               "ciphertext level or scale differs from the polynomial plan's");
+    std::map<int, Owned> own;
+    std::map<int, CCtVec> pw;
+    pw[1] = x;
+    auto at_level = [&](const CCtVec &v, int l, Owned &keep) -> CCtVec {
+        if (v[0]->level == l) return v;
+        keep = drop_b(c, v, l);
+        return keep.craw();
+    };
+    for (const auto &t : plan.tree) {
+        const int lvl = std::min(pw[t[1]][0]->level, pw[t[2]][0]->level);
+        Owned ka, kb;
+        const CCtVec A = at_level(pw[t[1]], lvl, ka), Bv = at_level(pw[t[2]], lvl, kb);
+        const size_t per = (size_t)3 * (lvl + 1) * c->N;
+        DevMem d(c, B * per * 8);
+        std::vector<u64 *> dd;
+        std::vector<const u64 *> cd;
+        for (size_t q = 0; q < B; q++) {
+            dd.push_back(d.u() + q * per);
+            cd.push_back(d.u() + q * per);
+        }
+        tensor_b(c, dd, A, Bv, false);
+        own[t[0]] = relin_b(c, evk, cd, lvl, A[0]->scale * Bv[0]->scale, true);
+        pw[t[0]] = own[t[0]].craw();
+    }
+    const int lc = plan.level_c;
+    Owned acc;
+    for (const auto &term : plan.terms) {
+        Owned keep;
+        const CCtVec v = at_level(pw[term.k], lc, keep);
+        Owned m;
+        for (size_t q = 0; q < B; q++) {
+            m.v.emplace_back(new_ct(c, lc, term.scale));
+            k::mul_scalar_mont(c, m.v[q]->data.u(), v[q]->data.u(), term.mont.u(), 2 * (lc + 1),
+                               c->qmap(lc, 0, lc + 1));
+        }
+        acc = acc.v.empty() ? std::move(m) : add_b(c, acc.craw(), m.craw());
+    }
+    Owned y = rescale_b(c, acc.craw());
+    if (plan.a0.ptr)
+        for (auto &ct : y.v) k::add_scalar(c, ct->c0(), ct->c0(), plan.a0.u(), ct->level + 1, c->qmap(ct->level));
+    std::vector<Ciphertext *> out;
+    for (auto &p : y.v) out.push_back(p.release());
+    return out;
+}
 
 // ------------------------------------------------------------------ the batch
 struct Batch : Handle {
@@ -868,7 +944,12 @@ static Owned dense_layer_b(Ctx *c, const Batch *bt, const Layer &L, const CCtVec
 {
     Owned y = matvec_b(c, bt, L.pm.get(), x);
     y = add_pt_b(c, y.craw(), L.bias.get());
-    if (L.square) y = square_b(c, bt->evk, y.craw());
+    if (L.square && !L.act) y = square_b(c, bt->evk, y.craw());
+    if (L.square && L.act) {   // the polynomial without a_0, then a_0 on the real outputs
+        Owned p;
+        for (auto *ct : poly_b(c, bt->evk, y.craw(), *L.act)) p.v.emplace_back(ct);
+        y = L.act_const ? add_pt_b(c, p.craw(), L.act_const.get()) : std::move(p);
+    }
     return y;
 }
 

@@ -492,6 +492,8 @@ void tensor(Ctx *c, u64 *d, const u64 *a0, const u64 *a1, const u64 *b0, const u
 void mul_scalar_mont(Ctx *c, u64 *out, const u64 *a, const u64 *d_scal_by_prime, int n_limbs,
                      LimbMap map);
 // out = (a - b) * scal[pid]
+// out = a + d_scal_by_prime[pid] (plain residues) on every coefficient of n_limbs limbs
+void add_scalar(Ctx *c, u64 *out, const u64 *a, const u64 *d_scal_by_prime, int n_limbs, LimbMap map);
 void sub_mul_scalar(Ctx *c, u64 *out, const u64 *a, const u64 *b, const u64 *d_scal_by_prime,
                     int n_limbs, LimbMap map);
 // centred integers (int64 N) -> residues for n_limbs limbs

@@ -190,10 +190,20 @@ Model *model_create(Ctx *c, const helrm_model_desc *d)
     const int nb = (int)d->n_bottom, nt = (int)d->n_top;
     const u32 want_top = dot ? DIM + m->B * (m->B - 1) / 2 : DIM * m->B;
     HCHECK(d->top_widths[0] == want_top, HELRM_E_INVAL, "top MLP input width does not match the interaction");
-    m->lvl_u = 2 * nt - 1;
+    // the activation: x^2 (one level) or a polynomial (poly_depth(d) levels),
+    // evaluated without its a_0, which is added on the real outputs only
+    std::vector<double> act, act_lin;
+    if (d->act_degree) {
+        HCHECK(d->act_coeffs, HELRM_E_INVAL, "act_coeffs is NULL");
+        act.assign(d->act_coeffs, d->act_coeffs + d->act_degree + 1);
+        act_lin = act;
+        act_lin[0] = 0.0;
+    }
+    const int ad = act.empty() ? 1 : poly_depth((int)d->act_degree);
+    m->lvl_u = (1 + ad) * (nt - 1) + 1;
     m->lvl_z = dot ? m->lvl_u + 2 : m->lvl_u;
     m->lvl_sel = m->lvl_z + 1;
-    m->lvl_dense = m->lvl_z + 2 * nb;
+    m->lvl_dense = m->lvl_z + (1 + ad) * nb;
     HCHECK(m->lvl_dense <= c->L, HELRM_E_PARAM,
            "model needs " + std::to_string(m->lvl_dense) + " levels, chain has " + std::to_string(c->L));
     m->Bp = dot ? m->B + 1 : m->B;
@@ -214,6 +224,21 @@ Model *model_create(Ctx *c, const helrm_model_desc *d)
     HCHECK(std::max({m->W_u, m->W_z, m->p_dense}) <= c->n_slots, HELRM_E_PARAM, "layout wider than the slot count");
 
     const double delta = c->delta;
+    // after a layer's matvec (and bias) at level lvl: the activation's level and scale
+    auto activate = [&](Layer &L, int rows, int out_pad, int &lvl, double &scale) {
+        if (act.empty()) {
+            scale = (delta * delta) / (double)c->primes[lvl];
+            lvl -= 1;
+            return;
+        }
+        L.act.reset(act_plan(c, act_lin, lvl, delta, delta));
+        lvl = L.act->out_level;
+        scale = L.act->out_scale;
+        if (act[0] != 0.0) {
+            std::vector<double> a0(rows, act[0]);
+            L.act_const.reset(encode_vec(c, replicate_bias(a0.data(), rows, out_pad), lvl, scale, PT_PLAIN));
+        }
+    };
     int lvl = m->lvl_dense, in_pad = m->p_dense;
     double scale = delta;
     for (int i = 0; i < nb; i++) {
@@ -223,10 +248,9 @@ Model *model_create(Ctx *c, const helrm_model_desc *d)
         L.pm.reset(ptmat_prepare(c, d->bottom_W[i], rows, cols, in_pad, out_pad, lvl, scale, delta));
         L.bias.reset(encode_vec(c, replicate_bias(d->bottom_b[i], rows, out_pad), lvl - 1, delta, PT_PLAIN));
         L.square = true;
+        lvl -= 1;
+        activate(L, rows, out_pad, lvl, scale);
         m->bottom.push_back(std::move(L));
-        lvl -= 1;
-        scale = (delta * delta) / (double)c->primes[lvl];
-        lvl -= 1;
         in_pad = out_pad;
     }
     const double scale_b = scale;
@@ -285,15 +309,13 @@ Model *model_create(Ctx *c, const helrm_model_desc *d)
         }
         L.bias.reset(encode_vec(c, replicate_bias(d->top_b[i], rows, out_pad), lvl - 1, delta, PT_PLAIN));
         L.square = !last;
-        m->top.push_back(std::move(L));
         lvl -= 1;
         scale = delta;
-        if (!last) {
-            scale = (delta * delta) / (double)c->primes[lvl];
-            lvl -= 1;
-        }
+        if (!last) activate(L, rows, out_pad, lvl, scale);
+        m->top.push_back(std::move(L));
     }
     HCHECK(lvl == 0, HELRM_E_PARAM, "internal: level schedule does not end at 0");
+    m->act = act;
     c->check_device_errors();
     return m.release();
 }

@@ -101,6 +101,17 @@ __global__ void k_scalar(u64 *__restrict__ out, const u64 *__restrict__ a, const
     }
 }
 
+__global__ void k_add_scalar(u64 *__restrict__ out, const u64 *__restrict__ a, const u64 *__restrict__ scal,
+                             int logN, size_t total, const PrimeInfo *__restrict__ pinfo, LimbMap map)
+{
+    pdl_begin();
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int pid = map.pid((int)(idx >> logN));
+        out[idx] = add_mod(a[idx], scal[pid], pinfo[pid].q);
+    }
+}
+
 __global__ void k_from_signed(u64 *__restrict__ out, const i64 *__restrict__ in, int logN, size_t total,
                               const PrimeInfo *__restrict__ pinfo, LimbMap map)
 {
@@ -540,6 +551,14 @@ void mul_scalar_mont(Ctx *c, u64 *out, const u64 *a, const u64 *scal, int n_limb
     KTimer kt(c, "elementwise", 16.0 * total);
     launch(c, k_scalar, grid_for(total), TPB, 0, out, a, nullptr, scal, c->logN, total,
                                                      c->d_pinfo.as<PrimeInfo>(), map);
+    LAUNCHED(c);
+}
+void add_scalar(Ctx *c, u64 *out, const u64 *a, const u64 *scal, int n_limbs, LimbMap map)
+{
+    const size_t total = (size_t)n_limbs * c->N;
+    if (!total) return;
+    KTimer kt(c, "elementwise", 16.0 * total);
+    launch(c, k_add_scalar, grid_for(total), TPB, 0, out, a, scal, c->logN, total, c->d_pinfo.as<PrimeInfo>(), map);
     LAUNCHED(c);
 }
 void sub_mul_scalar(Ctx *c, u64 *out, const u64 *a, const u64 *b, const u64 *scal, int n_limbs, LimbMap map)

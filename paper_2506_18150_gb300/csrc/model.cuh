@@ -3,12 +3,40 @@
 #pragma once
 
 #include <algorithm>
+#include <array>
 
 #include "core.cuh"
 
 namespace helrm {
 
 constexpr int DIM = 16;
+
+// A polynomial evaluation fixed for an input level and scale (poly.cu): the
+// products that form the needed powers, the simulated scale of each power,
+// the integer constant of each term as per-prime Montgomery residues, and the
+// constant term as plain residues.
+struct ActPlan {
+    std::vector<double> a;                      // a_0 .. a_d
+    std::vector<std::array<int, 3>> tree;       // (k, a, b): x^k = x^a x^b, increasing k
+    std::map<int, double> pw_scale;             // scale of x^k
+    int in_level = 0, level_c = 0, out_level = 0;
+    double in_scale = 0, out_scale = 0;
+    struct Term {
+        int k;
+        double scale;                           // scale of a_k x^k before the rescale
+        DevMem mont;                            // [c_k]_q R mod q per prime id
+    };
+    std::vector<Term> terms;
+    DevMem a0;                                  // [round(a_0 out_scale)]_q per prime id (empty: a_0 = 0)
+};
+int poly_depth(int d);
+ActPlan *act_plan(Ctx *c, const std::vector<double> &a, int level, double scale, double target);
+// the plan's polynomial on every query's ciphertext (batch.cu); evk[q]: the
+// relinearisation key of query q
+std::vector<Ciphertext *> poly_b(Ctx *c, const std::vector<const EvalKey *> &evk,
+                                 const std::vector<const Ciphertext *> &x, const ActPlan &plan);
+Ciphertext *ct_poly_eval(Ctx *c, const EvalKey *evk, const Ciphertext *x, const std::vector<double> &a,
+                         double target);
 
 struct SelSeg {
     int t, j, off, width;
@@ -31,7 +59,9 @@ struct Emb : Handle {
 struct Layer {
     std::unique_ptr<PtMatrix> pm;
     std::unique_ptr<Plaintext> bias;
-    bool square = false;
+    bool square = false;                    // an activation follows: x^2, or act (a polynomial)
+    std::unique_ptr<ActPlan> act;           // the activation polynomial without a_0 (null: x^2)
+    std::unique_ptr<Plaintext> act_const;   // a_0 on the layer's real outputs (null: none)
 };
 
 struct Model : Handle {
@@ -43,6 +73,7 @@ struct Model : Handle {
     std::unique_ptr<Emb> emb;
     std::unique_ptr<Plaintext> ones;
     std::vector<std::unique_ptr<Plaintext>> masks;
+    std::vector<double> act;   // the activation polynomial a_0 .. a_d (empty: x^2)
     Model(Ctx *c) : Handle(KIND_MODEL), ctx(c) {}
 
     // the lookup's matrices: one, or one per ciphertext of a wide selector
@@ -57,20 +88,19 @@ struct Model : Handle {
     std::vector<std::unique_ptr<Plaintext> *> plaintexts()
     {
         std::vector<std::unique_ptr<Plaintext> *> out;
-        for (auto &l : bottom) {
+        auto layer = [&](Layer &l) {
             for (auto &p : l.pm->pts) out.push_back(&p);
             out.push_back(&l.bias);
-        }
+            if (l.act_const) out.push_back(&l.act_const);
+        };
+        for (auto &l : bottom) layer(l);
         for (PtMatrix *pm : emb_mats())
             for (auto &p : pm->pts) out.push_back(&p);
         if (interaction == 0) {
             out.push_back(&ones);
             for (auto &m : masks) out.push_back(&m);
         }
-        for (auto &l : top) {
-            for (auto &p : l.pm->pts) out.push_back(&p);
-            out.push_back(&l.bias);
-        }
+        for (auto &l : top) layer(l);
         return out;
     }
     std::vector<int> rotations() const

@@ -49,7 +49,8 @@ class ModelDesc(C.Structure):
                 ("top_W", C.POINTER(C.POINTER(C.c_double))), ("top_b", C.POINTER(C.POINTER(C.c_double))),
                 ("n_tables", C.c_uint32), ("cards", C.POINTER(C.c_uint64)), ("base_p", C.c_uint32),
                 ("dim", C.c_uint32), ("tables", C.POINTER(C.POINTER(C.c_float))),
-                ("interaction", C.c_int32), ("threshold", C.c_uint64)]
+                ("interaction", C.c_int32), ("threshold", C.c_uint64),
+                ("act_degree", C.c_uint32), ("act_coeffs", C.POINTER(C.c_double))]
 
 
 _lib = None
@@ -117,6 +118,7 @@ _SIGS = {
     "helrm_infer_e2e": [_vp, _vp, _vp, _vp, _dp, _u64p, C.c_uint32, C.c_uint64, _dp, _dp],
     "helrm_infer_e2e_device": [_vp, _vp, _vp, _vp, _vp, _vp, C.c_uint32, C.c_uint64, _vp, _vp],
     "helrm_rescale_noalloc": [_vp, _vp, _vp, C.c_int32, C.c_uint32],
+    "helrm_poly_eval": [_vp, _vp, _vp, _dp, C.c_uint32, C.c_double, _pp],
     "helrm_batch_create": [_vp, _vp, C.c_uint32, _pp, _pp],
     "helrm_infer_batch": [_vp, _vp, _pp, _pp, _pp],
     "helrm_batch_set_graph": [_vp, _vp, C.c_int],
@@ -414,6 +416,15 @@ def helrm_mul(ctx, evk, a, b):
     return _ct_op("helrm_mul", ctx, evk.ptr, a.ptr, b.ptr)
 
 
+def helrm_poly_eval(ctx, evk, x, coeffs, target_scale: float):
+    """sum_k coeffs[k] x^k slot-wise (coeffs: a_0 .. a_d)."""
+    cf = np.ascontiguousarray(coeffs, dtype=np.float64)
+    out = C.c_void_p()
+    _check(ctx, lib().helrm_poly_eval(ctx.ptr, evk.ptr, x.ptr, cf.ctypes.data_as(_dp), len(cf), target_scale,
+                                      C.byref(out)))
+    return Handle(out.value, ctx)
+
+
 def helrm_rescale(ctx, a):
     return _ct_op("helrm_rescale", ctx, a.ptr)
 
@@ -543,6 +554,12 @@ def helrm_model_create(ctx, spec, w):
                   len(w.top_W), tw, dptrs(w.top_W), dptrs(w.top_b), len(spec.cards),
                   cards.ctypes.data_as(_u64p), spec.base, spec.dim, tptrs,
                   0 if spec.interaction == "dot" else 1, getattr(spec, "threshold", 0) or 0)
+    act = getattr(spec, "act", None)
+    if act is not None:
+        acts = np.ascontiguousarray(act, dtype=np.float64)
+        keep.append(acts)
+        d.act_degree = len(acts) - 1
+        d.act_coeffs = acts.ctypes.data_as(_dp)
     out = C.c_void_p()
     _check(ctx, lib().helrm_model_create(ctx.ptr, C.byref(d), C.byref(out)))
     return Handle(out.value, ctx)

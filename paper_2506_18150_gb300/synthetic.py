@@ -52,6 +52,44 @@ class DLRMSpec:
     dim: int = 16
     interaction: str = "dot"    # "dot" (pairwise) or "concat" (the paper's choice)
     threshold: int | None = None    # tables with more rows are digit-decomposed (None: base)
+    act: tuple | None = None    # activation polynomial a_0..a_d (power basis); None: x^2
+
+
+def act_apply(spec: DLRMSpec, v):
+    """The model's activation on cleartext values: x^2, or its polynomial."""
+    if spec.act is None:
+        return v ** 2
+    return np.polynomial.polynomial.polyval(v, np.asarray(spec.act, dtype=np.float64))
+
+
+def _lsq_fit(f, degree: int, bound: float) -> tuple:
+    # least squares at 1024 Chebyshev points of [-bound, bound], in the
+    # Chebyshev basis of the scaled interval, then converted to powers of x
+    t = np.cos(np.pi * (np.arange(1024) + 0.5) / 1024)
+    cheb = np.polynomial.chebyshev.chebfit(t, f(bound * t), degree)
+    pw = np.polynomial.chebyshev.cheb2poly(cheb)
+    a = [float(pw[k] / bound ** k) for k in range(degree + 1)]
+    # terms that vanish by symmetry come out at rounding level: make them exact
+    # zeros (the evaluation then skips their powers), and drop trailing zeros
+    top = max(abs(v) for v in a)
+    a = [0.0 if abs(v) < 1e-12 * top else v for v in a]
+    while len(a) > 1 and a[-1] == 0.0:
+        a.pop()
+    return tuple(a)
+
+
+def silu_poly(degree: int = 7, bound: float = 6.0) -> tuple:
+    """Power-basis coefficients of a least-squares fit of SiLU(x) = x / (1 +
+    e^-x) on [-bound, bound] (the paper's SiLU activation, Sec. 5.4; its
+    coefficients are not printed, so this fit stands in for them)."""
+    return _lsq_fit(lambda x: x / (1.0 + np.exp(-x)), degree, bound)
+
+
+def relu_poly(degree: int = 8, bound: float = 6.0) -> tuple:
+    """Power-basis coefficients of a least-squares fit of max(x, 0) on
+    [-bound, bound] (a single low-degree stand-in for the paper's composite
+    ReLU polynomials, which need bootstrapping depth)."""
+    return _lsq_fit(lambda x: np.maximum(x, 0.0), degree, bound)
 
 
 def n_digits(k: int, p: int) -> int:
@@ -92,6 +130,16 @@ def uci_paper_spec() -> DLRMSpec:
     """The paper's UCI shape: 5 dense features and tables of [2,4,2,3,2,3,4,3] rows."""
     s = DLRMSpec("uci_paper", 5, [5, 16, 16], [0, 16, 1], [2, 4, 2, 3, 2, 3, 4, 3], 64, 16)
     s.top[0] = top_input_width(s)
+    return s
+
+
+def uci_silu_spec(seed: int = 0, degree: int = 7) -> DLRMSpec:
+    """The UCI-shaped model with a degree-7 SiLU polynomial instead of x^2:
+    three activations of depth 4 fit the 20-level chain without bootstrapping
+    (ct_dense at level 18)."""
+    s = uci_spec(seed)
+    s.name = "uci_silu"
+    s.act = silu_poly(degree)
     return s
 
 
@@ -157,13 +205,6 @@ class DLRMWeights:
     tables: list = field(default_factory=list)      # tables[t][j]: rows x dim float32
 
 
-def _calib_forward_bottom(Ws, bs, x):
-    h = x
-    for W, b in zip(Ws, bs):
-        h = (h @ W.T + b) ** 2
-    return h
-
-
 def _calib_top_input(spec, h, embs):
     blocks = [h] + embs
     if spec.interaction == "dot":
@@ -198,7 +239,7 @@ def make_weights(spec: DLRMSpec, seed: int = 0) -> DLRMWeights:
         c = 1.0 / np.sqrt(np.mean(pre ** 2))
         w.bottom_W[i] *= c
         w.bottom_b[i] *= c
-        h = (pre * c) ** 2
+        h = act_apply(spec, pre * c)
     embs = []
     for t, k in enumerate(spec.cards):
         rows = table_rows(k, spec.base, spec.threshold)
@@ -216,7 +257,7 @@ def make_weights(spec: DLRMSpec, seed: int = 0) -> DLRMWeights:
         w.top_b[i] *= c
         y = pre * c
         if i + 1 < len(w.top_W):
-            y = y ** 2
+            y = act_apply(spec, y)
     return w
 
 

@@ -261,3 +261,25 @@ def test_encrypted_dlrm_with_two_selector_ciphertexts(small_params):
         logit, _ = dlrm.decrypt_logit(p, sk, out)
         ref = dlrm.dlrm_cleartext(spec, w, dense[q], idx[q])[0]
         assert abs(logit - ref) < 1e-3, (q, logit, ref)
+
+
+def test_encrypted_dlrm_with_polynomial_silu():
+    """A tiny DLRM (bottom 4-16, tables of 3 and 5 rows, dot interaction, top
+    19-1) whose activation is the degree-6 SiLU polynomial: the activation
+    costs poly.depth(6) = 4 levels, so ct_dense sits at level 3 + 5 = 8, and
+    the encrypted logit matches the FP64 DLRM with the same polynomial."""
+    from oracle import poly
+    p = ckks.Params(10, [60] + [40] * 8, 3, 60, 3, 40.0)
+    spec = syn.DLRMSpec("tiny_silu", 4, [4, 16], [0, 1], [3, 5], 8, 16, "dot", act=syn.silu_poly(7))
+    spec.top[0] = syn.top_input_width(spec)
+    w = syn.make_weights(spec, 0)
+    c = dlrm.compile_model(p, spec, w)
+    assert dlrm.activation_levels(spec) == poly.depth(6) == 4
+    assert (c.lvl_dense, c.lvl_sel, c.lvl_z, c.lvl_u) == (8, 4, 3, 1)
+    sk, keys = ckks.keygen(p, 8, rot_steps=c.rotation_steps())
+    dense, idx = syn.make_queries(spec, 2, seed=3)
+    for q in range(2):
+        cd, cs = dlrm.encrypt_query(p, keys, c, dense[q], idx[q], 60 + 3 * q)
+        logit, _ = dlrm.decrypt_logit(p, sk, dlrm.infer(p, keys, c, cd, cs))
+        ref = dlrm.dlrm_cleartext(spec, w, dense[q], idx[q])[0]
+        assert abs(logit - ref) < 1e-3, (q, logit, ref)

@@ -20,6 +20,9 @@ through one lockstep batch (helrm_infer_batch_e2e_device), against the same
 16 queries one at a time.
 
 --workload criteo   the same line for the Criteo-shaped DLRM (one query/step).
+--workload uci_silu the UCI-shaped line with polynomial activations: every
+                    activation a degree-6 SiLU polynomial (depth 4, 18 of
+                    the 20 levels, no bootstrapping).
 --workload batched  64 concurrent queries per step, 32 UCI-shaped (16 clients)
                     and 32 Criteo-shaped (8 clients), each model's queries in
                     one lockstep batch; keys truncated to the levels each
@@ -56,7 +59,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="uci", choices=["uci", "criteo", "batched", "served"])
+    ap.add_argument("--workload", default="uci", choices=["uci", "criteo", "uci_silu", "batched", "served"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=1000, help="served: requests per arrival rate")
     ap.add_argument("--rates", default="1,5,10,20,50,100,200", help="served: arrival rates (requests/s)")
@@ -67,15 +70,17 @@ def parse():
 
 def workload_config(name):
     from paper_2506_18150_gb300 import synthetic as syn
-    spec = syn.uci_spec(0) if name == "uci" else syn.criteo_spec(0)
+    spec = {"uci": syn.uci_spec, "criteo": syn.criteo_spec, "uci_silu": syn.uci_silu_spec}[name](0)
     desc = {
         "uci": "UCI-health-shaped DLRM, 1 query/step: 10 dense, 8 tables (2..64 rows), dim 16, "
                "bottom 10-32-16, dot interaction, top 52-32-1, x^2",
         "criteo": "Criteo-shaped DLRM, 1 query/step: 13 dense, 26 tables (33.8M rows, base 64), dim 16, "
                   "bottom 13-512-256-64-16, dot interaction, top 367-512-256-1, x^2",
+        "uci_silu": "UCI-health-shaped DLRM, 1 query/step, as 'uci' but every activation is a degree-6 "
+                    "least-squares SiLU polynomial on [-6, 6] (depth 4, no bootstrapping; ct_dense at level 18)",
     }[name]
     cfg = {"workload": desc, "ckks": "N=2^16, q0 60-bit + 20x40-bit, K=3x60-bit special, alpha=3, Delta=2^40",
-           "tables": spec.cards if name == "uci" else f"{len(spec.cards)} tables, {sum(spec.cards)} rows",
+           "tables": spec.cards if name != "criteo" else f"{len(spec.cards)} tables, {sum(spec.cards)} rows",
            "l2": "no flush: each step streams ~GBs of keys and diagonals (>> 129 MB L2)"}
     return spec, cfg
 
@@ -208,7 +213,7 @@ def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    if args.workload not in ("uci", "criteo"):
+    if args.workload not in ("uci", "criteo", "uci_silu"):
         print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the one-query workloads "
                           "(uci, criteo); it has no batched or served mode"}), flush=True)
         return

@@ -44,11 +44,12 @@ def polymul_ratio(log_full: int, log_sample: int, limbs: int = 8, reps: int = 3)
 
 def run(workload: str = "uci", steps: int = 3, warmup: int = 1):
     from paper_2506_18150_gb300 import synthetic as syn
-    spec = syn.uci_spec(0) if workload == "uci" else syn.criteo_spec(0)
+    spec = {"uci": syn.uci_spec, "criteo": syn.criteo_spec, "uci_silu": syn.uci_silu_spec}[workload](0)
     w = syn.make_weights(spec, 0)
-    log_sample = 13 if workload == "uci" else 15
+    log_sample = 15 if workload == "criteo" else 13
     n_bot, n_top = len(w.bottom_W), len(w.top_W)
-    levels = 2 * n_top - 1 + 2 + 2 * n_bot            # dot interaction
+    ad = dlrm.activation_levels(spec)
+    levels = (1 + ad) * (n_top - 1) + 1 + 2 + (1 + ad) * n_bot     # dot interaction
     p = _params(log_sample, levels)
     t0 = time.perf_counter()
     c = dlrm.compile_model(p, spec, w)

@@ -11,7 +11,9 @@ bottom 10-32-16, top 52-32-1) at N = 2^16 with a 60-bit base prime, 20
 levels of 40-bit primes and three 60-bit special primes, synthetic seeded
 inputs.
 
-  value  inferences/s with the query's inputs already in HBM (device pointers);
+  value  inferences/s with the query's inputs already in HBM (device pointers),
+         the server path of a batch of one replayed as a CUDA graph
+         (value_eager: the same with every kernel launched on the stream);
   e2e    the same through helrm_infer_e2e from pinned host buffers, the
          host->device copy of the query and the device->host read of the
          logit inside the timed region.
@@ -536,6 +538,16 @@ def run_ours(args):
         H.helrm_infer_e2e_device(ctx, sk, evk, model, d_dense[q].data_ptr(), d_idx[q].data_ptr(), 1,
                                  7 + 2 * q, d_logit[q:q + 1].data_ptr())
 
+    # the same query through a batch of one whose server path is replayed as a
+    # CUDA graph (helrm_batch_set_graph; bit-identical to the eager path): the
+    # client's packing and encryption and the decryption stay eager
+    bt1 = H.helrm_batch_create(ctx, model, [evk])
+    H.helrm_batch_set_graph(ctx, bt1, True)
+
+    def step_graph(q):
+        H.helrm_infer_batch_e2e_device(ctx, bt1, [sk], d_dense[q].data_ptr(), d_idx[q].data_ptr(), 7 + 2 * q,
+                                       d_logit[q:q + 1].data_ptr())
+
     def barrier():
         torch.cuda.synchronize()
         if world > 1:
@@ -543,12 +555,25 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- value: inputs resident in HBM
+    # ---- value_eager: inputs resident in HBM, every kernel launched on the stream
     for q in range(W):
         step_dev(q)
     barrier()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
     l0 = H.helrm_ctx_launch_count(ctx)
+    ee = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ee[0].record(stream)
+    for s in range(K):
+        step_dev(W + s)
+    ee[1].record(stream)
+    barrier()
+    launches_per_step = (H.helrm_ctx_launch_count(ctx) - l0) / K   # the graph replays the same kernels
+    value_eager, _ = job_throughput(K, ee[0].elapsed_time(ee[1]), world)
+
+    # ---- value: the same steps with the server path replayed as a graph
+    for q in range(W):
+        step_graph(q)
+    barrier()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
     clocks = ClockSampler(local)
     clocks.start()
     ncu_range = os.environ.get("HELRM_PROFILE_RANGE") == "1"   # lets `ncu --profile-from-start off` see only these steps
@@ -556,14 +581,14 @@ def run_ours(args):
         torch.cuda.profiler.start()
     ev[0].record(stream)
     for s in range(K):
-        step_dev(W + s)
+        step_graph(W + s)
         ev[s + 1].record(stream)
     torch.cuda.synchronize()
     if ncu_range:
         torch.cuda.profiler.stop()
     clk = clocks.stop()
     barrier()
-    launches = H.helrm_ctx_launch_count(ctx) - l0
+    launches = launches_per_step * K
     per = [ev[i].elapsed_time(ev[i + 1]) for i in range(K)]
     value, total_ms = job_throughput(K, ev[0].elapsed_time(ev[K]), world)
     logits = d_logit.cpu().numpy()
@@ -576,7 +601,16 @@ def run_ours(args):
     dp = ctypes.POINTER(ctypes.c_double)
     up = ctypes.POINTER(ctypes.c_uint64)
 
-    def step_host(q):
+    sks = (ctypes.c_void_p * 1)(sk.ptr.value)
+
+    def step_host(q):   # helrm_infer_batch_e2e: the graph-replayed batch of one, host buffers
+        st = L.helrm_infer_batch_e2e(ctx.ptr, bt1.ptr, sks, ctypes.c_void_p(h_dense.data_ptr() + 8 * nd * q),
+                                     ctypes.c_void_p(h_idx.data_ptr() + 8 * nt * q), 7 + 2 * q,
+                                     ctypes.c_void_p(h_out.data_ptr() + 8 * q))
+        if st != 0:
+            raise H.HelrmError(st, L.helrm_last_error(ctx.ptr).decode())
+
+    def step_host_eager(q):   # helrm_infer_e2e: every kernel launched on the stream, host buffers
         st = L.helrm_infer_e2e(ctx.ptr, sk.ptr, evk.ptr, model.ptr,
                                ctypes.cast(h_dense.data_ptr() + 8 * nd * q, dp),
                                ctypes.cast(h_idx.data_ptr() + 8 * nt * q, up), 1, 7 + 2 * q,
@@ -584,16 +618,20 @@ def run_ours(args):
         if st != 0:
             raise H.HelrmError(st, L.helrm_last_error(ctx.ptr).decode())
 
-    for q in range(W):
-        step_host(q)
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for s in range(K):
-        step_host(W + s)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_value, e2e_ms = job_throughput(K, e0.elapsed_time(e1), world)
+    def timed_host(fn):
+        for q in range(W):
+            fn(q)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s in range(K):
+            fn(W + s)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return job_throughput(K, e0.elapsed_time(e1), world)[0]
+
+    e2e_eager = timed_host(step_host_eager)
+    e2e_value = timed_host(step_host)
     same = bool(np.allclose(h_out.numpy()[W:], logits[W:], atol=1e-9))
 
     # ---- kernel roofline: per-kernel CUDA events on the launch stream
@@ -621,8 +659,14 @@ def run_ours(args):
                                "p99": per_sorted[min(len(per) - 1, int(round(0.99 * (len(per) - 1))))],
                                "min": per_sorted[0], "max": per_sorted[-1]},
                 "clocks": clk, "gpu_launches": int(launches),
+                "value_eager": value_eager,
+                "value_note": "value: the server path of a batch of one replayed as a CUDA graph "
+                              "(helrm_infer_batch_e2e_device); value_eager: every kernel launched on the "
+                              "stream (helrm_infer_e2e_device); both bit-identical",
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * (nd + nt),
-                        "d2h_bytes_per_step": 8, "same_logits_as_value_path": same},
+                        "d2h_bytes_per_step": 8, "same_logits_as_value_path": same,
+                        "api": "helrm_infer_batch_e2e (graph-replayed batch of one, host buffers)",
+                        "eager": e2e_eager},
                 "roofline": roof}
         if batched:
             line["batched"] = batched

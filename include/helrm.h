@@ -422,6 +422,14 @@ helrm_status helrm_infer_batch(helrm_ctx *ctx, const helrm_batch *b, const helrm
 helrm_status helrm_infer_batch_e2e_device(helrm_ctx *ctx, const helrm_batch *b, const helrm_sk *const *sks,
                                          const double *d_dense, const uint64_t *d_indices, uint64_t seed,
                                          double *d_logits);
+/* The same protocol for the batch from host buffers (dense: n x n_dense FP64,
+ * indices: n x n_tables u64, logits_out: n FP64): the inputs are copied to
+ * the device, the batch runs as helrm_infer_batch_e2e_device (as a CUDA graph
+ * when enabled), the logits are copied back, and the call synchronises.  As
+ * with the device variant, an index outside its table sets no selector slot. */
+helrm_status helrm_infer_batch_e2e(helrm_ctx *ctx, const helrm_batch *b, const helrm_sk *const *sks,
+                                   const double *dense, const uint64_t *indices, uint64_t seed,
+                                   double *logits_out);
 
 /* --------------------------------------------------- serving (a2-a13, batched) */
 /* A request loop over lockstep batches.  Clients register their model and

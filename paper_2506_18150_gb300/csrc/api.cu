@@ -842,14 +842,44 @@ helrm_status helrm_infer_batch(helrm_ctx *ctx, const helrm_batch *b, const helrm
     });
 }
 
+namespace {
+void batch_e2e_device(Ctx *c, Batch *bt, const helrm_sk *const *sks, const double *d_dense, const uint64_t *d_indices,
+                      uint64_t seed, double *d_logits);
+}
+
+helrm_status helrm_infer_batch_e2e(helrm_ctx *ctx, const helrm_batch *b, const helrm_sk *const *sks,
+                                   const double *dense, const uint64_t *indices, uint64_t seed, double *logits_out)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        Batch *bt = BAT(b);
+        HCHECK(sks && dense && indices && logits_out, HELRM_E_INVAL, "NULL argument");
+        const Model *mm = batch_model(bt);
+        const size_t n = batch_size(bt), nd = model_n_dense((Model *)mm), nt = model_n_tables((Model *)mm);
+        DevMem dd(c, n * nd * 8), di(c, n * nt * 8), dl(c, n * 8);
+        CUDA_CHECK(cudaMemcpyAsync(dd.ptr, dense, n * nd * 8, cudaMemcpyHostToDevice, c->stream));
+        CUDA_CHECK(cudaMemcpyAsync(di.ptr, indices, n * nt * 8, cudaMemcpyHostToDevice, c->stream));
+        batch_e2e_device(c, bt, sks, dd.as<double>(), di.u(), seed, dl.as<double>());
+        CUDA_CHECK(cudaMemcpyAsync(logits_out, dl.ptr, n * 8, cudaMemcpyDeviceToHost, c->stream));
+        c->check_device_errors();
+    });
+}
+
 helrm_status helrm_infer_batch_e2e_device(helrm_ctx *ctx, const helrm_batch *b, const helrm_sk *const *sks,
                                          const double *d_dense, const uint64_t *d_indices, uint64_t seed,
                                          double *d_logits)
 {
     return guard(ctx_or_null(ctx), [&] {
-        Ctx *c = C(ctx);
-        Batch *bt = BAT(b);
         HCHECK(sks && d_dense && d_indices && d_logits, HELRM_E_INVAL, "NULL argument");
+        batch_e2e_device(C(ctx), BAT(b), sks, d_dense, d_indices, seed, d_logits);
+    });
+}
+
+namespace {
+void batch_e2e_device(Ctx *c, Batch *bt, const helrm_sk *const *sks, const double *d_dense, const uint64_t *d_indices,
+                      uint64_t seed, double *d_logits)
+{
+    {
         const Model *mm = batch_model(bt);
         const size_t n = batch_size(bt), nd = model_n_dense((Model *)mm), nt = model_n_tables((Model *)mm);
         std::vector<const SecretKey *> sk;
@@ -868,8 +898,9 @@ helrm_status helrm_infer_batch_e2e_device(helrm_ctx *ctx, const helrm_batch *b, 
         std::vector<std::unique_ptr<Ciphertext>> yo;
         for (auto *p : y) yo.emplace_back(p);
         for (size_t q = 0; q < n; q++) decrypt_slots_device(c, sk[q], yo[q].get(), d_logits + q, 1);
-    });
+    }
 }
+}  // namespace
 
 // ------------------------------------------------------------------ serving
 helrm_status helrm_server_create(helrm_ctx *ctx, uint32_t n_slots, uint32_t max_batch, uint64_t mem_budget,

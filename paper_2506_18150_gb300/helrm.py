@@ -123,6 +123,7 @@ _SIGS = {
     "helrm_infer_batch": [_vp, _vp, _pp, _pp, _pp],
     "helrm_batch_set_graph": [_vp, _vp, C.c_int],
     "helrm_infer_batch_e2e_device": [_vp, _vp, _pp, _vp, _vp, C.c_uint64, _vp],
+    "helrm_infer_batch_e2e": [_vp, _vp, _pp, _vp, _vp, C.c_uint64, _vp],
     "helrm_server_create": [_vp, C.c_uint32, C.c_uint32, C.c_uint64, _pp],
     "helrm_server_add_client": [_vp, _vp, _vp, _vp, _u32p],
     "helrm_server_run": [_vp, _vp, C.c_uint32, _dp, _u32p, _pp, _pp, _pp, _dp, C.c_void_p],
@@ -654,6 +655,16 @@ def helrm_infer_batch_e2e_device(ctx, batch, sks, d_dense: int, d_indices: int, 
     """Device pointers (ints): d_dense n x n_dense f64, d_indices n x n_tables u64, d_logits n f64."""
     _check(ctx, lib().helrm_infer_batch_e2e_device(ctx.ptr, batch.ptr, _ptrs(sks), C.c_void_p(d_dense),
                                                    C.c_void_p(d_indices), seed, C.c_void_p(d_logits)))
+
+
+def helrm_infer_batch_e2e(ctx, batch, sks, dense, indices, seed: int):
+    """Host arrays: dense n x n_dense, indices n x n_tables; returns the n logits."""
+    d = np.ascontiguousarray(dense, dtype=np.float64)
+    i = np.ascontiguousarray(np.asarray(indices).astype(np.uint64))
+    out = np.zeros(d.shape[0])
+    _check(ctx, lib().helrm_infer_batch_e2e(ctx.ptr, batch.ptr, _ptrs(sks), C.c_void_p(d.ctypes.data),
+                                            C.c_void_p(i.ctypes.data), seed, C.c_void_p(out.ctypes.data)))
+    return out
 
 
 def helrm_server_create(ctx, n_slots: int, max_batch: int, mem_budget: int = 0):

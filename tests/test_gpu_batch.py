@@ -178,3 +178,23 @@ def test_batch_graph_replay_matches_eager():
         b = H.helrm_infer_batch(ctx, graph, [c[0] for c in cts], [c[1] for c in cts])
         for q in range(3):
             _same_ct(ctx, a[q], b[q])
+
+
+def test_batch_e2e_host_buffers_with_graph():
+    """helrm_infer_batch_e2e from host buffers, the batch's server path
+    replayed as a CUDA graph: the logits equal helrm_infer_e2e's for the same
+    queries and seeds (twice: the capture, then a replay)."""
+    from paper_2506_18150_gb300 import helrm as H
+    from paper_2506_18150_gb300 import synthetic as syn
+    pr = syn.reduced_params(13, 9)
+    spec = syn.uci_spec(0)
+    ctx = gpu_ctx(pr)
+    model = H.helrm_model_create(ctx, spec, syn.make_weights(spec, 0))
+    sk, evk = H.helrm_model_keygen(ctx, model, 90)
+    batch = H.helrm_batch_create(ctx, model, [evk, evk])
+    H.helrm_batch_set_graph(ctx, batch, True)
+    for call in range(2):
+        dense, idx = syn.make_queries(spec, 2, seed=95 + call)
+        want, _ = H.helrm_infer_e2e(ctx, sk, evk, model, dense, idx, 300 + call)
+        got = H.helrm_infer_batch_e2e(ctx, batch, [sk, sk], dense, idx, 300 + call)
+        assert list(got) == list(want)

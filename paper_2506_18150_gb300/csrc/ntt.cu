@@ -115,13 +115,20 @@ enum Mode { M_LAZY = 0, M_SCALE = 1, M_REDUCE = 2 };
 // both compile-time constants (the production sizes), so every shared- and
 // global-memory address is a per-thread base plus an immediate offset; 0: the
 // arguments logN / logG are used (every other size).
+// Register budget of the fixed-size instances with tiles of 4 or 8
+// sub-transforms (128, 256 threads): 48 registers, i.e. 40 resident warps per
+// SM instead of 32, without spills; every other instance is left to the
+// compiler under the 512-thread bound (it settles at 56-64 registers).
+#define NTT_MAX_THREADS(FIXN, FIXG) ((FIXN) && (FIXG) >= 2 ? (32 << (FIXG)) : 512)
+#define NTT_MIN_BLOCKS(FIXN, FIXG) ((FIXN) && (FIXG) >= 2 ? 65536 / ((32 << (FIXG)) * 48) : 0)
+
 // XL (column passes only): the per-limb extras of XList apply -- a forward
 // first pass computes its input as a fast base conversion of fn source limbs
 // on load (the 128-bit multiply-accumulate and the one reduction of the
 // stand-alone conversion kernel, so the values are identical); an inverse
 // last pass scales by its own constant.
 template <int LOGP, bool COLS, bool INV, int FIXN = 0, int FIXG = 0, bool XL = false>
-__global__ void __launch_bounds__(512) k_ntt_pass(int first, int logN_arg, int logG_arg, LimbList list,
+__global__ void __launch_bounds__(NTT_MAX_THREADS(FIXN, FIXG), NTT_MIN_BLOCKS(FIXN, FIXG)) k_ntt_pass(int first, int logN_arg, int logG_arg, LimbList list,
                                                    const ulonglong2 *__restrict__ tw_all,
                                                    const ulonglong2 *__restrict__ ninv,
                                                    const PrimeInfo *__restrict__ pinfo, int mode, const Ep ep,

@@ -352,20 +352,62 @@ __global__ void k_cbd21(i64 *out, u64 seed, u32 purpose, u64 index, int N)
 }
 
 // ------------------------------------------------------------- FP64 FFT
-// Stockham radix-2 pass: l = N / 2^(s+1), m = 2^s; twiddle e^(-+2 pi i j m / N).
-__global__ void k_fft_pass(const double2 *__restrict__ x, double2 *__restrict__ y, int logN, int s,
-                           const double2 *__restrict__ tw, int inverse)
+// The N-point DFT X_k = sum_n x_n e^{-+2 pi i n k / N} (- forward, + inverse)
+// as a four-step FFT in two launches: N = R C, n = C n1 + n2, k = k1 + R k2.
+// Column pass (COLS): for each n2 the R-point DFT over n1, times e^{-+2 pi i
+// n2 k1 / N}, stored at k1 C + n2; row pass: for each k1 the C-point DFT over
+// n2, stored at k1 + R k2.  A CTA takes G sub-transforms of P points (P = R or
+// C), loads them coalesced, runs the log2 P radix-2 Stockham stages in shared
+// memory (one butterfly per thread per stage) and stores them coalesced.
+// tw[t] = e^{-2 pi i t / N}, t < N/2.
+template <bool COLS>
+__global__ void k_fft4(const double2 *__restrict__ x, double2 *__restrict__ y, int logN, int logR, int logP,
+                       const double2 *__restrict__ tw, int inverse)
 {
     pdl_begin();
-    const int N = 1 << logN, m = 1 << s, l = N >> (s + 1);
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N / 2; idx += gridDim.x * blockDim.x) {
+    extern __shared__ double2 fsm[];
+    const int N = 1 << logN, R = 1 << logR, C = N >> logR, P = 1 << logP;
+    const int G = (2 * blockDim.x) >> logP;          // sub-transforms per CTA
+    double2 *b0 = fsm, *b1 = fsm + G * P;
+    const int base = blockIdx.x * G;                 // first column (COLS) or row
+    for (int e = threadIdx.x; e < G * P; e += blockDim.x) {
+        if (COLS) {
+            const int g = e % G, n1 = e / G;
+            b0[g * P + n1] = x[(size_t)n1 * C + base + g];
+        } else {
+            const int g = e >> logP, n2 = e & (P - 1);
+            b0[e] = x[(size_t)(base + g) * C + n2];
+        }
+    }
+    __syncthreads();
+    const int half = P / 2, g = threadIdx.x / half, idx = threadIdx.x % half;
+    double2 *in = b0, *out = b1;
+    for (int s = 0; s < logP; s++) {
+        const int m = 1 << s, l = P >> (s + 1);
         const int j = idx >> s, kk = idx & (m - 1);
-        double2 w = tw[j * m];
+        double2 w = tw[(size_t)j * m << (logN - logP)];
         if (inverse) w.y = -w.y;
-        const double2 c0 = x[kk + j * m], c1 = x[kk + j * m + l * m];
+        const double2 c0 = in[g * P + kk + j * m], c1 = in[g * P + kk + j * m + l * m];
         const double2 d = make_double2(c0.x - c1.x, c0.y - c1.y);
-        y[kk + 2 * j * m] = make_double2(c0.x + c1.x, c0.y + c1.y);
-        y[kk + 2 * j * m + m] = make_double2(w.x * d.x - w.y * d.y, w.x * d.y + w.y * d.x);
+        out[g * P + kk + 2 * j * m] = make_double2(c0.x + c1.x, c0.y + c1.y);
+        out[g * P + kk + 2 * j * m + m] = make_double2(w.x * d.x - w.y * d.y, w.x * d.y + w.y * d.x);
+        __syncthreads();
+        double2 *t = in;
+        in = out;
+        out = t;
+    }
+    for (int e = threadIdx.x; e < G * P; e += blockDim.x) {
+        const int gg = e % G, k = e / G;
+        double2 v = in[gg * P + k];
+        if (COLS) {   // k = k1, column n2 = base + gg: times e^{-+2 pi i n2 k1 / N}
+            const int n2 = base + gg;
+            const int t = (int)(((long long)n2 * k) & (N - 1));
+            double2 w = t < N / 2 ? tw[t] : make_double2(-tw[t - N / 2].x, -tw[t - N / 2].y);
+            if (inverse) w.y = -w.y;
+            y[(size_t)k * C + n2] = make_double2(w.x * v.x - w.y * v.y, w.x * v.y + w.y * v.x);
+        } else {      // k = k2, row k1 = base + gg
+            y[(size_t)(base + gg) + (size_t)R * k] = v;
+        }
     }
 }
 
@@ -655,16 +697,20 @@ void sample_cbd21(Ctx *c, i64 *out, u64 seed, u32 purpose, u64 index)
     LAUNCHED(c);
 }
 
+// N-point DFT of buf_a (four-step, k_fft4): the result lands in buf_a again
+// (the column pass writes buf_b, the row pass buf_a)
 static void fft(Ctx *c, double2 *buf_a, double2 *buf_b, bool inverse, double2 **result)
 {
-    double2 *x = buf_a, *y = buf_b;
-    for (int s = 0; s < c->logN; s++) {
-        launch(c, k_fft_pass, grid_for(c->N / 2), TPB, 0, x, y, c->logN, s, c->d_fft_tw.as<double2>(),
-                                                              inverse ? 1 : 0);
-        LAUNCHED(c);
-        std::swap(x, y);
-    }
-    *result = x;
+    const int logN = c->logN, logR = logN / 2, logC = logN - logR;
+    constexpr int G = 4;   // sub-transforms per CTA
+    const double2 *tw = c->d_fft_tw.as<double2>();
+    launch(c, k_fft4<true>, (1 << logC) / G, G << (logR - 1), (size_t)2 * G * (8 << logR) * 2, buf_a, buf_b, logN,
+           logR, logR, tw, inverse ? 1 : 0);
+    LAUNCHED(c);
+    launch(c, k_fft4<false>, (1 << logR) / G, G << (logC - 1), (size_t)2 * G * (8 << logC) * 2, buf_b, buf_a, logN,
+           logR, logC, tw, inverse ? 1 : 0);
+    LAUNCHED(c);
+    *result = buf_a;
 }
 
 void encode_slots(Ctx *c, u64 *out, const double *d_slots, int n_valid, int period, double scale, int n_limbs,

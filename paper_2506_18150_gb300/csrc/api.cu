@@ -769,7 +769,7 @@ helrm_status helrm_infer_e2e(helrm_ctx *ctx, const helrm_sk *sk, const helrm_evk
     return guard(ctx_or_null(ctx), [&] {
         Ctx *c = C(ctx);
         Model *mm = MOD(m);
-        HCHECK(dense && indices && logits_out, HELRM_E_INVAL, "NULL argument");
+        HCHECK((dense && indices && logits_out) || n_queries == 0, HELRM_E_INVAL, "NULL argument");
         const size_t nd = model_n_dense(mm), nt = model_n_tables(mm);
         const u64 stride = 1 + (u64)model_n_sel(mm);
         for (u32 q = 0; q < n_queries; q++) {
@@ -790,7 +790,7 @@ helrm_status helrm_infer_e2e_device(helrm_ctx *ctx, const helrm_sk *sk, const he
     return guard(ctx_or_null(ctx), [&] {
         Ctx *c = C(ctx);
         Model *mm = MOD(m);
-        HCHECK(d_dense && d_indices && d_logits, HELRM_E_INVAL, "NULL argument");
+        HCHECK((d_dense && d_indices && d_logits) || n_queries == 0, HELRM_E_INVAL, "NULL argument");
         const size_t nd = model_n_dense(mm), nt = model_n_tables(mm);
         const u64 stride = 1 + (u64)model_n_sel(mm);
         for (u32 q = 0; q < n_queries; q++) {
@@ -798,7 +798,7 @@ helrm_status helrm_infer_e2e_device(helrm_ctx *ctx, const helrm_sk *sk, const he
             std::unique_ptr<Ciphertext> y(model_infer(c, EVK(evk), mm, x.dense.get(), x.sel_ptrs()));
             decrypt_slots_device(c, SK(sk), y.get(), d_logits + q, 1);
         }
-        if (d_probs) k::sigmoid(c, d_probs, d_logits, (int)n_queries);
+        if (d_probs && n_queries) k::sigmoid(c, d_probs, d_logits, (int)n_queries);
     });
 }
 

@@ -241,7 +241,8 @@ helrm_status helrm_rotate_hoisted(helrm_ctx *ctx, const helrm_evk *evk, const he
 helrm_status helrm_ptmat_prepare(helrm_ctx *ctx, const double *W, uint32_t rows, uint32_t cols,
                                  uint32_t in_pad, uint32_t out_pad, int32_t level, double ct_scale,
                                  double target_scale, helrm_ptmat **out);
-/* info_out[0..5] = D, n1, n2, number of non-zero diagonals, number of folds, level. */
+/* info_out[0..5] = D, n1, n2, number of non-zero diagonals, number of fold
+ * levels, level. */
 helrm_status helrm_ptmat_info(const helrm_ptmat *m, uint32_t *info_out);
 /* Rotation steps the matvec needs; steps_out may be NULL to query the count. */
 helrm_status helrm_ptmat_rotations(const helrm_ptmat *m, int32_t *steps_out, uint32_t *n_out);
@@ -250,9 +251,11 @@ helrm_status helrm_ptmat_rotations(const helrm_ptmat *m, int32_t *steps_out, uin
 helrm_status helrm_ptmat_import(helrm_ctx *ctx, helrm_ptmat *m, const int64_t *coeffs, uint32_t count);
 /* y = W x: double-hoisted BSGS (one ModUp of c1 shared by the baby steps, the
  * diagonal products accumulated over QP, giant steps rotated in QP, one final
- * ModDown), rescale, then the rotate-and-add folds for wide matrices.  The
- * output is W x replicated with period out_pad, one level lower, at
- * target_scale.  n_in must be 1. */
+ * ModDown), rescale, then for a wide matrix the folds: the sum of
+ * rot(y, j out_pad) over j < in_pad / out_pad, in levels of up to 8 hoisted
+ * rotations (strides out_pad, 8 out_pad, 64 out_pad, ...).  The output is
+ * W x replicated with period out_pad, one level lower, at target_scale.
+ * n_in must be 1. */
 helrm_status helrm_ptct_matvec(helrm_ctx *ctx, const helrm_evk *evk, const helrm_ptmat *m,
                                const helrm_ct *in, uint32_t n_in, helrm_ct **out);
 

@@ -15,7 +15,8 @@ D = min(in_pad, out_pad) extended diagonals
 
     diag_i[j] = W[j mod out_pad, (j + i) mod in_pad],   j < n,  i < D,
 
-and, when in_pad > out_pad, rotate-and-add folds by in_pad/2, ..., out_pad.
+and, when in_pad > out_pad, the folds: sum_j rot(y, j out_pad) over j <
+in_pad / out_pad, in levels of up to 8 hoisted rotations (fold_plan).
 The result is W x replicated with period out_pad.  BSGS split: n1 =
 min(D, 64), n2 = D / n1 (see bsgs_split); i = g*n1 + b and
 diag'_{g,b} = rot(diag_{g n1 + b}, -g n1).  All-zero diagonals are skipped,
@@ -58,12 +59,26 @@ def extended_diagonals(W: np.ndarray, in_pad: int, out_pad: int, n: int) -> np.n
     return np.stack([Wp[j % out_pad, (j + i) % in_pad] for i in range(D)])
 
 
-def fold_shifts(in_pad: int, out_pad: int):
-    out, s = [], in_pad // 2
-    while s >= out_pad:
-        out.append(s)
-        s //= 2
+FOLD_RADIX_BITS = 3
+
+
+def fold_plan(in_pad: int, out_pad: int):
+    """The folds of a wide matrix as levels [(stride, radix)], from the
+    smallest stride: level t adds rot(y, d * stride_t) for d = 1..radix_t - 1
+    (hoisted rotations of the same ciphertext), radix 8 except the last, so
+    that together they sum rot(y, j * out_pad) over j < in_pad / out_pad."""
+    bits = (in_pad // out_pad).bit_length() - 1
+    out, stride = [], out_pad
+    while bits > 0:
+        r = min(FOLD_RADIX_BITS, bits)
+        out.append((stride, 1 << r))
+        stride <<= r
+        bits -= r
     return out
+
+
+def fold_steps(folds):
+    return [d * s for s, r in folds for d in range(1, r)]
 
 
 @dataclass
@@ -79,7 +94,7 @@ class Layout:
     def make(in_pad: int, out_pad: int) -> "Layout":
         D = min(in_pad, out_pad)
         n1, n2 = bsgs_split(D)
-        return Layout(in_pad, out_pad, D, n1, n2, fold_shifts(in_pad, out_pad))
+        return Layout(in_pad, out_pad, D, n1, n2, fold_plan(in_pad, out_pad))
 
 
 @dataclass
@@ -122,7 +137,7 @@ def rotation_steps(pm: PtMatrix):
     lay = pm.layout
     babies = {b for (_, b) in pm.pts}
     giants = {g for (g, _) in pm.pts}
-    return sorted({b for b in babies if b} | {g * lay.n1 for g in giants if g} | set(lay.folds))
+    return sorted({b for b in babies if b} | {g * lay.n1 for g in giants if g} | set(fold_steps(lay.folds)))
 
 
 def matvec(p: ckks.Params, keys: ckks.Keys, pm: PtMatrix, ct: ckks.Ct) -> ckks.Ct:
@@ -180,8 +195,13 @@ def matvec(p: ckks.Params, keys: ckks.Keys, pm: PtMatrix, ct: ckks.Ct) -> ckks.C
                   ct.scale * pm.pt_scale)
     out = ckks.rescale(p, out)
     out.scale = pm.out_scale
-    for sh in lay.folds:
-        out = ckks.add(p, out, ckks.rotate(p, keys, out, sh))
+    for stride, radix in lay.folds:
+        steps = [d * stride for d in range(1, radix)]
+        rots = ckks.rotate_hoisted(p, keys, out, steps)
+        acc = out
+        for st in steps:
+            acc = ckks.add(p, acc, rots[st])
+        out = acc
     return out
 
 

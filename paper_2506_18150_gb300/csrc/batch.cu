@@ -933,9 +933,15 @@ static Owned matvec_b(Ctx *c, const Batch *bt, const PtMatrix *m, const CCtVec &
     }
     Owned y = moddown_rescale_b(c, acc, l, sc, none, none);   // the final ModDown and the rescale, merged
     for (auto &p : y.v) p->scale = m->out_scale;
-    for (int f : m->folds) {
-        Owned r = rotate_b(c, bt->evk, y.craw(), {f});
-        y = add_b(c, y.craw(), r.craw());
+    for (auto &f : m->folds) {   // one level: the radix - 1 rotations hoisted, then added
+        std::vector<int> steps;
+        for (int d = 1; d < f.second; d++) steps.push_back(d * f.first);
+        Owned r = rotate_b(c, bt->evk, y.craw(), steps);   // [q][step]
+        for (size_t s = 0; s < steps.size(); s++) {
+            CCtVec rs;
+            for (size_t q = 0; q < B; q++) rs.push_back(r.v[q * steps.size() + s].get());
+            y = add_b(c, y.craw(), rs);
+        }
     }
     return y;
 }

@@ -600,7 +600,7 @@ struct PtMatrix : Handle {
     Ctx *ctx;
     int in_pad = 0, out_pad = 0, D = 0, n1 = 0, n2 = 0, level = 0;
     double pt_scale = 0, out_scale = 0;
-    std::vector<int> folds;
+    std::vector<std::pair<int, int>> folds;   // fold levels (stride, radix), smallest stride first
     std::vector<std::pair<int, int>> gb;      // non-zero diagonals, (g, b) order
     std::vector<std::unique_ptr<Plaintext>> pts;
     DevMem d_ptrs;                             // device array of diagonal pointers

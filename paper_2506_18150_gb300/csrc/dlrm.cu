@@ -439,7 +439,8 @@ std::vector<std::pair<int, int>> model_key_levels(const Model *m, int *relin_lev
             if (gb.second) use(gb.second, pm->level);
             if (gb.first) use(gb.first * pm->n1, pm->level);
         }
-        for (int f : pm->folds) use(f, pm->level - 1);
+        for (auto &f : pm->folds)
+            for (int dd = 1; dd < f.second; dd++) use(dd * f.first, pm->level - 1);
     };
     int rl = -1;
     for (auto &L : m->bottom) {

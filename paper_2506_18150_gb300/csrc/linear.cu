@@ -5,7 +5,8 @@
 // slots.  For W padded to out_pad x in_pad there are D = min(in_pad, out_pad)
 // extended diagonals diag_i[j] = W[j mod out_pad, (j + i) mod in_pad]; when the
 // matrix is wide, rotate-and-add folds by in_pad/2, ..., out_pad finish the
-// sum.  BSGS: n1 = min(D, max(16, D / 8)), n2 = D / n1 <= 8 (a hoisted baby
+// sum (levels of up to 8 hoisted rotations: rot(y, d stride) for d < radix,
+// stride out_pad, 8 out_pad, 64 out_pad, ...).  BSGS: n1 = min(D, max(16, D / 8)), n2 = D / n1 <= 8 (a hoisted baby
 // step costs a key inner product and a key read, a giant step a ModDown and a
 // ModUp as well), i = g n1 + b, diag'_{g,b} = rot(diag_i, -g n1), which reads
 // W[(j - g n1) mod out_pad, (j + b) mod in_pad].
@@ -37,7 +38,8 @@ std::vector<int> PtMatrix::rotations() const
         if (gb2.second) st.push_back(gb2.second);
         if (gb2.first) st.push_back(gb2.first * n1);
     }
-    for (int f : folds) st.push_back(f);
+    for (auto &f : folds)
+        for (int d = 1; d < f.second; d++) st.push_back(d * f.first);
     std::sort(st.begin(), st.end());
     st.erase(std::unique(st.begin(), st.end()), st.end());
     return st;
@@ -74,7 +76,15 @@ PtMatrix *ptmat_prepare(Ctx *c, const double *W, int rows, int cols, int in_pad,
     m->n1 = std::min(m->D, std::max(16, m->D / 8));   // at most 8 giant steps
     m->n2 = m->D / m->n1;
     m->level = level;
-    for (int s = in_pad / 2; s >= out_pad; s /= 2) m->folds.push_back(s);
+    // folds: levels of up to 8 hoisted rotations, from the smallest stride,
+    // together summing rot(y, j out_pad) over j < in_pad / out_pad
+    const int fold = in_pad > out_pad ? in_pad / out_pad : 1;   // a tall matrix has no folds
+    for (int bits = 31 - __builtin_clz((unsigned)fold), stride = out_pad; bits > 0;) {
+        const int r = std::min(3, bits);
+        m->folds.push_back({stride, 1 << r});
+        stride <<= r;
+        bits -= r;
+    }
     m->pt_scale = (double)c->primes[level] * target_scale / ct_scale;
     m->out_scale = target_scale;
     auto Wp = [&](int r, int col) -> double { return (r < rows && col < cols) ? W[(size_t)r * cols + col] : 0.0; };
@@ -164,9 +174,16 @@ Ciphertext *matvec(Ctx *c, const EvalKey *evk, const PtMatrix *m, const Cipherte
     ks_moddown2(c, acc, l, o->c0(), o->c1());
     std::unique_ptr<Ciphertext> y(ct_rescale(c, o.get()));
     y->scale = m->out_scale;
-    for (int f : m->folds) {
-        std::unique_ptr<Ciphertext> r(ct_rotate(c, evk, y.get(), f));
-        y.reset(ct_add(c, y.get(), r.get()));
+    for (auto &f : m->folds) {
+        std::vector<int> steps;
+        for (int d = 1; d < f.second; d++) steps.push_back(d * f.first);
+        std::vector<Ciphertext *> rs;
+        ct_rotate_hoisted(c, evk, y.get(), steps, rs);
+        std::vector<std::unique_ptr<Ciphertext>> own;
+        for (auto *r : rs) own.emplace_back(r);
+        std::unique_ptr<Ciphertext> acc(ct_add(c, y.get(), own[0].get()));
+        for (size_t i = 1; i < own.size(); i++) acc.reset(ct_add(c, acc.get(), own[i].get()));
+        y = std::move(acc);
     }
     return y.release();
 }

@@ -252,8 +252,8 @@ helrm_status helrm_ptmat_import(helrm_ctx *ctx, helrm_ptmat *m, const int64_t *c
 /* y = W x: double-hoisted BSGS (one ModUp of c1 shared by the baby steps, the
  * diagonal products accumulated over QP, giant steps rotated in QP, one final
  * ModDown), rescale, then for a wide matrix the folds: the sum of
- * rot(y, j out_pad) over j < in_pad / out_pad, in levels of up to 8 hoisted
- * rotations (strides out_pad, 8 out_pad, 64 out_pad, ...).  The output is
+ * rot(y, j out_pad) over j < in_pad / out_pad, in levels of up to 3 hoisted
+ * rotations (strides out_pad, 4 out_pad, 16 out_pad, ...).  The output is
  * W x replicated with period out_pad, one level lower, at target_scale.
  * n_in must be 1. */
 helrm_status helrm_ptct_matvec(helrm_ctx *ctx, const helrm_evk *evk, const helrm_ptmat *m,

@@ -16,7 +16,7 @@ D = min(in_pad, out_pad) extended diagonals
     diag_i[j] = W[j mod out_pad, (j + i) mod in_pad],   j < n,  i < D,
 
 and, when in_pad > out_pad, the folds: sum_j rot(y, j out_pad) over j <
-in_pad / out_pad, in levels of up to 8 hoisted rotations (fold_plan).
+in_pad / out_pad, in levels of up to 3 hoisted rotations (fold_plan).
 The result is W x replicated with period out_pad.  BSGS split: n1 =
 min(D, 64), n2 = D / n1 (see bsgs_split); i = g*n1 + b and
 diag'_{g,b} = rot(diag_{g n1 + b}, -g n1).  All-zero diagonals are skipped,
@@ -59,13 +59,13 @@ def extended_diagonals(W: np.ndarray, in_pad: int, out_pad: int, n: int) -> np.n
     return np.stack([Wp[j % out_pad, (j + i) % in_pad] for i in range(D)])
 
 
-FOLD_RADIX_BITS = 3
+FOLD_RADIX_BITS = 2
 
 
 def fold_plan(in_pad: int, out_pad: int):
     """The folds of a wide matrix as levels [(stride, radix)], from the
     smallest stride: level t adds rot(y, d * stride_t) for d = 1..radix_t - 1
-    (hoisted rotations of the same ciphertext), radix 8 except the last, so
+    (hoisted rotations of the same ciphertext), radix 4 except the last, so
     that together they sum rot(y, j * out_pad) over j < in_pad / out_pad."""
     bits = (in_pad // out_pad).bit_length() - 1
     out, stride = [], out_pad

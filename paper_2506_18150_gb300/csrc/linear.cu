@@ -5,8 +5,8 @@
 // slots.  For W padded to out_pad x in_pad there are D = min(in_pad, out_pad)
 // extended diagonals diag_i[j] = W[j mod out_pad, (j + i) mod in_pad]; when the
 // matrix is wide, rotate-and-add folds by in_pad/2, ..., out_pad finish the
-// sum (levels of up to 8 hoisted rotations: rot(y, d stride) for d < radix,
-// stride out_pad, 8 out_pad, 64 out_pad, ...).  BSGS: n1 = min(D, max(16, D / 8)), n2 = D / n1 <= 8 (a hoisted baby
+// sum (levels of up to 3 hoisted rotations: rot(y, d stride) for d < 4,
+// stride out_pad, 4 out_pad, 16 out_pad, ...).  BSGS: n1 = min(D, max(16, D / 8)), n2 = D / n1 <= 8 (a hoisted baby
 // step costs a key inner product and a key read, a giant step a ModDown and a
 // ModUp as well), i = g n1 + b, diag'_{g,b} = rot(diag_i, -g n1), which reads
 // W[(j - g n1) mod out_pad, (j + b) mod in_pad].
@@ -76,11 +76,11 @@ PtMatrix *ptmat_prepare(Ctx *c, const double *W, int rows, int cols, int in_pad,
     m->n1 = std::min(m->D, std::max(16, m->D / 8));   // at most 8 giant steps
     m->n2 = m->D / m->n1;
     m->level = level;
-    // folds: levels of up to 8 hoisted rotations, from the smallest stride,
+    // folds: levels of up to 3 hoisted rotations (radix 4), from the smallest stride,
     // together summing rot(y, j out_pad) over j < in_pad / out_pad
     const int fold = in_pad > out_pad ? in_pad / out_pad : 1;   // a tall matrix has no folds
     for (int bits = 31 - __builtin_clz((unsigned)fold), stride = out_pad; bits > 0;) {
-        const int r = std::min(3, bits);
+        const int r = std::min(2, bits);
         m->folds.push_back({stride, 1 << r});
         stride <<= r;
         bits -= r;

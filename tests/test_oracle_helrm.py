@@ -76,7 +76,7 @@ def test_selector_ciphertext_counts_and_compression_table():
 def test_diagonal_count_for_416_outputs():
     """26 tables x 16 = 416 outputs, padded to 512: 512 diagonals (Sec. 5.4)."""
     lay = linear.Layout.make(in_pad=8192, out_pad=linear.pow2ceil(416))
-    assert lay.D == 512 and lay.n1 * lay.n2 == 512 and lay.folds == [(512, 8), (4096, 2)]
+    assert lay.D == 512 and lay.n1 * lay.n2 == 512 and lay.folds == [(512, 4), (2048, 4)]
     assert linear.Layout.make(in_pad=512, out_pad=512).D == 512
 
 
@@ -89,7 +89,7 @@ def test_fold_plan_covers_every_offset_once():
         for b in range(0, 13):
             in_pad = out_pad << b
             plan = linear.fold_plan(in_pad, out_pad)
-            assert all(r <= 8 for _, r in plan) and len(plan) == (b + 2) // 3
+            assert all(r <= 4 for _, r in plan) and len(plan) == (b + 1) // 2
             offs = [sum(d * s for d, (s, _) in zip(ds, plan))
                     for ds in itertools.product(*[range(r) for _, r in plan])]
             assert sorted(offs) == list(range(0, in_pad, out_pad))

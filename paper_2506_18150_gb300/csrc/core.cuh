@@ -497,7 +497,13 @@ void add_scalar(Ctx *c, u64 *out, const u64 *a, const u64 *d_scal_by_prime, int 
 void sub_mul_scalar(Ctx *c, u64 *out, const u64 *a, const u64 *b, const u64 *d_scal_by_prime,
                     int n_limbs, LimbMap map);
 // centred integers (int64 N) -> residues for n_limbs limbs
-void from_signed(Ctx *c, u64 *out, const i64 *in, int n_limbs, LimbMap map);
+// n_polys polynomials (in: [n_polys][N], out: [n_polys][n_limbs][N]) in one launch
+void from_signed(Ctx *c, u64 *out, const i64 *in, int n_limbs, LimbMap map, int n_polys = 1);
+// an encryption's v (ternary), e0, e1 (CBD(21)) into out3[3][N], one launch
+void sample_enc_noise(Ctx *c, i64 *out3, u64 seed, u32 pv, u32 pe0, u32 pe1);
+// c0 = v pk0 + e0 + m, c1 = v pk1 + e1 over n_limbs limbs, one launch
+void enc_combine(Ctx *c, u64 *c0, u64 *c1, const u64 *v, const u64 *e0, const u64 *e1, const u64 *m, const u64 *pk0,
+                 const u64 *pk1, int n_limbs, LimbMap map);
 // d_out[l][i] = sum_j dig_j[l][perm(i)] * key_j(l)[i] for the level-ell QP basis, both
 // polys of the key; if c0 != null, out0 on Q limbs += P * c0[perm(i)]
 // bq (optional): a QP polynomial whose image phi(bq) is added to the first

@@ -112,11 +112,14 @@ __global__ void k_add_scalar(u64 *__restrict__ out, const u64 *__restrict__ a, c
     }
 }
 
+// blockIdx.y = polynomial p: out + p total <- in + p N (one launch for several)
 __global__ void k_from_signed(u64 *__restrict__ out, const i64 *__restrict__ in, int logN, size_t total,
                               const PrimeInfo *__restrict__ pinfo, LimbMap map)
 {
     pdl_begin();
     const size_t N = (size_t)1 << logN;
+    out += blockIdx.y * total;
+    in += blockIdx.y * N;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
         const u64 q = pinfo[map.pid((int)(idx >> logN))].q;
@@ -348,6 +351,51 @@ __global__ void k_cbd21(i64 *out, u64 seed, u32 purpose, u64 index, int N)
             const u64 m = (1ull << 21) - 1;
             out[8 * b + c] = (i64)__popcll(x & m) - (i64)__popcll((x >> 21) & m);
         }
+    }
+}
+
+// An encryption's three noise polynomials in one launch (blockIdx.y): v
+// ternary from stream pv into out[0..N), e0 and e1 CBD(21) from streams pe0,
+// pe1 into out[N..2N) and out[2N..3N); the same words as k_ternary / k_cbd21.
+__global__ void k_enc_noise(i64 *out, u64 seed, u32 pv, u32 pe0, u32 pe1, int N)
+{
+    pdl_begin();
+    const int y = blockIdx.y;
+    i64 *o = out + (size_t)y * N;
+    if (y == 0) {
+        for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < N / 16; b += gridDim.x * blockDim.x) {
+            u32 w[16];
+            chacha_block(seed, pv, 0, (u32)b, w);
+            for (int k2 = 0; k2 < 16; k2++) o[16 * b + k2] = (i64)(w[k2] & 1) - (i64)((w[k2] >> 1) & 1);
+        }
+        return;
+    }
+    const u32 purpose = y == 1 ? pe0 : pe1;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < N / 8; b += gridDim.x * blockDim.x) {
+        u32 w[16];
+        chacha_block(seed, purpose, 0, (u32)b, w);
+        for (int c = 0; c < 8; c++) {
+            u64 x = (u64)w[2 * c] | ((u64)w[2 * c + 1] << 32);
+            const u64 m = (1ull << 21) - 1;
+            o[8 * b + c] = (i64)__popcll(x & m) - (i64)__popcll((x >> 21) & m);
+        }
+    }
+}
+
+// c0 = v pk0 + e0 + m, c1 = v pk1 + e1 (v, pk Montgomery products; the adds in
+// this order), over the n limbs of `total` words
+__global__ void k_enc_combine(u64 *__restrict__ c0, u64 *__restrict__ c1, const u64 *__restrict__ v,
+                              const u64 *__restrict__ e0, const u64 *__restrict__ e1, const u64 *__restrict__ m,
+                              const u64 *__restrict__ pk0, const u64 *__restrict__ pk1, int logN, size_t total,
+                              const PrimeInfo *__restrict__ pinfo, LimbMap map)
+{
+    pdl_begin();
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const PrimeInfo pi = pinfo[map.pid((int)(idx >> logN))];
+        const u64 x = v[idx];
+        c0[idx] = add_mod(add_mod(mont_mul(x, pk0[idx], pi.q, pi.qinv), e0[idx], pi.q), m[idx], pi.q);
+        c1[idx] = add_mod(mont_mul(x, pk1[idx], pi.q, pi.qinv), e1[idx], pi.q);
     }
 }
 
@@ -612,11 +660,26 @@ void sub_mul_scalar(Ctx *c, u64 *out, const u64 *a, const u64 *b, const u64 *sca
                                                      c->d_pinfo.as<PrimeInfo>(), map);
     LAUNCHED(c);
 }
-void from_signed(Ctx *c, u64 *out, const i64 *in, int n_limbs, LimbMap map)
+void from_signed(Ctx *c, u64 *out, const i64 *in, int n_limbs, LimbMap map, int n_polys)
+{
+    size_t total = (size_t)n_limbs * c->N;
+    if (!total || n_polys < 1) return;
+    launch(c, k_from_signed, dim3(grid_for(total), n_polys), TPB, 0, out, in, c->logN, total,
+           c->d_pinfo.as<PrimeInfo>(), map);
+    LAUNCHED(c);
+}
+void sample_enc_noise(Ctx *c, i64 *out3, u64 seed, u32 pv, u32 pe0, u32 pe1)
+{
+    launch(c, k_enc_noise, dim3(grid_for(c->N / 8), 3), TPB, 0, out3, seed, pv, pe0, pe1, c->N);
+    LAUNCHED(c);
+}
+void enc_combine(Ctx *c, u64 *c0, u64 *c1, const u64 *v, const u64 *e0, const u64 *e1, const u64 *m, const u64 *pk0,
+                 const u64 *pk1, int n_limbs, LimbMap map)
 {
     size_t total = (size_t)n_limbs * c->N;
     if (!total) return;
-    launch(c, k_from_signed, grid_for(total), TPB, 0, out, in, c->logN, total, c->d_pinfo.as<PrimeInfo>(), map);
+    launch(c, k_enc_combine, grid_for(total), TPB, 0, c0, c1, v, e0, e1, m, pk0, pk1, c->logN, total,
+           c->d_pinfo.as<PrimeInfo>(), map);
     LAUNCHED(c);
 }
 void ks_inner_auto(Ctx *c, u64 *out, const u64 *digits, int dnum, const SwitchKey *key, int level, u64 galois,

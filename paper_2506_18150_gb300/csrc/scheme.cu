@@ -490,19 +490,12 @@ Ciphertext *encrypt_pt(Ctx *c, const EvalKey *evk, const Plaintext *pt, u64 seed
     // v, e0 and e1 (each sampled from its own counter stream) are transformed
     // by one NTT launch: vee = [v | e0 | e1], each nq limbs
     DevMem raw(c, (size_t)3 * N * 8), vee(c, (size_t)3 * nq * N * 8);
-    k::sample_ternary(c, raw.as<i64>(), seed, P_ENC_V, 0);
-    k::sample_cbd21(c, raw.as<i64>() + N, seed, P_ENC_E0, 0);
-    k::sample_cbd21(c, raw.as<i64>() + 2 * (size_t)N, seed, P_ENC_E1, 0);
-    for (int p = 0; p < 3; p++)
-        k::from_signed(c, vee.u() + (size_t)p * nq * N, raw.as<i64>() + (size_t)p * N, nq, qm);
+    k::sample_enc_noise(c, raw.as<i64>(), seed, P_ENC_V, P_ENC_E0, P_ENC_E1);
+    k::from_signed(c, vee.u(), raw.as<i64>(), nq, qm, 3);
     k::ntt_fwd(c, vee.u(), 3 * nq, c->qmap(l, 0, nq));
-    const u64 *v = vee.u();
-    for (int p = 0; p < 2; p++) {
-        u64 *dst = p ? ct->c1() : ct->c0();
-        k::mul_mont(c, dst, v, evk->pk.u() + (size_t)p * nqL * N, nq, qm);
-        k::add(c, dst, dst, vee.u() + (size_t)(1 + p) * nq * N, nq, qm);
-    }
-    k::add(c, ct->c0(), ct->c0(), pt->data.u(), nq, qm);
+    const size_t pl = (size_t)nq * N;
+    k::enc_combine(c, ct->c0(), ct->c1(), vee.u(), vee.u() + pl, vee.u() + 2 * pl, pt->data.u(), evk->pk.u(),
+                   evk->pk.u() + (size_t)nqL * N, nq, qm);
     return ct.release();
 }
 

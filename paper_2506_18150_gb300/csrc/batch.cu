@@ -346,12 +346,6 @@ using CCtVec = std::vector<const Ciphertext *>;
 
 struct Owned {   // owns the ciphertexts of one batched value
     std::vector<std::unique_ptr<Ciphertext>> v;
-    CtVec raw() const
-    {
-        CtVec r;
-        for (auto &p : v) r.push_back(p.get());
-        return r;
-    }
     CCtVec craw() const
     {
         CCtVec r;

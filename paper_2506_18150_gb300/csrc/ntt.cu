@@ -74,8 +74,6 @@ template <>
 struct XArg<false> {
 };
 
-__device__ __forceinline__ int pad(int e) { return e + (e >> 4); }
-
 // Shoup product without its final correction: a * w mod q in [0, 2q).
 __device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 wp, u64 q) { return a * w - mulhi64(a, wp) * q; }
 // x >= m ? x - m : x, as one 64-bit min (x - m wraps above x when x < m)

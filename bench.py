@@ -58,7 +58,8 @@ UNIT = "inferences/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 100 for the one-query workloads, 20 for batched and --impl reference)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="uci", choices=["uci", "criteo", "uci_silu", "batched", "served"])
@@ -67,7 +68,10 @@ def parse():
     ap.add_argument("--rates", default="1,5,10,20,50,100,200", help="served: arrival rates (requests/s)")
     ap.add_argument("--slots", type=int, default=2, help="served: batch slots (CUDA streams) of the batching server")
     ap.add_argument("--max-batch", type=int, default=8, help="served: requests per batch of the batching server")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 100 if args.impl == "ours" and args.workload in ("uci", "criteo", "uci_silu") else 20
+    return args
 
 
 def workload_config(name):
@@ -88,7 +92,9 @@ def workload_config(name):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms; start()
+    returns once the first sample is in (at most 5 s), so the sampling is
+    live when the timed region begins."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -102,12 +108,16 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(self.idx)],
+                                          "-lms", "100", "-i", str(self.idx)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except (OSError, ValueError):
             self.proc = None
+            return
+        t0 = time.time()
+        while not self.lines and self.proc.poll() is None and time.time() - t0 < 5.0:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:

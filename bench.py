@@ -170,7 +170,31 @@ NTT_INSTR_PER_BUTTERFLY = 23
 ALU_LANES = 152 * 4 * 32
 
 
-def roofline(rep, n_steps, log_n, sm_mhz, peak_hbm, peak_src):
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per NTT launch
+# (one transform, both passes) over the one-query UCI-shaped step, from one
+# ncu capture with its default cold caches (profiles/ntt_traffic_uci_dlrm_n16.md).
+# It holds for the sources it was taken on: reported while their SHA-256
+# still matches, null otherwise.
+NTT_TRAFFIC = {"workload": "uci", "bytes_per_launch": 19.83e6,
+               "sha256": {"ntt.cu": "381430a43604fce2ae84e91c42d1e8e831cb84c3b8bb2854fe410d1d0b4a0642",
+                          "core.cuh": "b07128795e4ff0ab3e8bb30502566ed472f561f9e424ae75a00afd43277c7013"}}
+
+
+def ntt_traffic(workload):
+    import hashlib
+    if workload != NTT_TRAFFIC["workload"]:
+        return None
+    for name, digest in NTT_TRAFFIC["sha256"].items():
+        try:
+            with open(os.path.join(ROOT, "paper_2506_18150_gb300", "csrc", name), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != digest:
+                    return None
+        except OSError:
+            return None
+    return NTT_TRAFFIC["bytes_per_launch"]
+
+
+def roofline(rep, n_steps, log_n, sm_mhz, peak_hbm, peak_src, workload=None):
     """Dominant kernel (by time) with its bound: the NTT against the issue
     ceiling (butterflies/s), everything else against measured HBM bandwidth."""
     total = sum(v[1] for v in rep.values())
@@ -192,7 +216,11 @@ def roofline(rep, n_steps, log_n, sm_mhz, peak_hbm, peak_src):
         achieved = byts / (ms / 1000.0) / 1e9
         out = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
                "frac": achieved / peak_hbm, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
-    out.update({"traffic": None, "launches_per_step": n / n_steps, "ms_per_step": ms / n_steps,
+    traffic = ntt_traffic(workload) if dom == "ntt" else None
+    if traffic is not None:
+        out["traffic_note"] = ("DRAM bytes per transform under ncu (cold caches), against "
+                               f"{byts / n:.4g} algorithmic bytes per transform")
+    out.update({"traffic": traffic, "launches_per_step": n / n_steps, "ms_per_step": ms / n_steps,
                 "share_of_kernel_time": ms / total, "kernels": kernels})
     return out
 
@@ -652,7 +680,7 @@ def run_ours(args):
     rep = H.helrm_ctx_profile_report(ctx)
     H.helrm_ctx_profile(ctx, False)
     peak, peak_src = peaks()
-    roof = roofline(rep, n_prof, pr["log_n"], clk.get("sm_mhz") or 2070.0, peak, peak_src)
+    roof = roofline(rep, n_prof, pr["log_n"], clk.get("sm_mhz") or 2070.0, peak, peak_src, args.workload)
 
     # ---- batched: 16 queries of 8 clients in one lockstep batch vs one at a time
     batched = None

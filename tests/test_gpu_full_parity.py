@@ -10,7 +10,17 @@ embedding lookup's level and at level 1; hoisted rotations; a relinearised
 product and a square; a degree-3 polynomial (products with the rescale
 merged into the ModDown); and two BSGS matvecs at the lookup's level (a
 square one with two giant steps, a wide one with a radix-4 fold level).
-The oracle generates 18 keys at N = 2^16 (about a minute of host time)."""
+The oracle generates 18 keys at N = 2^16 (about a minute of host time).
+
+Last, one UCI-shaped inference end to end at this size, through the path the
+benchmark times (the server path of a batch of one, captured as a CUDA graph
+and replayed): its logit ciphertext against the oracle's, word for word.  Its
+47 oracle keys are made by the oracle's own key functions in a spawn-started
+process pool, one key per task."""
+import multiprocessing as mp
+import os
+from concurrent.futures import ProcessPoolExecutor
+
 import numpy as np
 import pytest
 
@@ -111,3 +121,69 @@ def test_full_matvec(full, which):
     assert_ct_equal(ctx, out, linear.matvec(p, keys_o, pm_o, ct_o))
     want = linear.matvec_cleartext(W, x, ip, op, p.n)
     assert np.max(np.abs(H.helrm_decrypt(ctx, sk, out, 256) - want[:256])) < 1e-3
+
+
+def _switch_key_task(job):
+    """One oracle switching key, composed as the oracle's keygen composes it:
+    key id 0 = relinearisation (s' = s^2), else the Galois element k (s' = s(X^k))."""
+    from oracle import ckks, ring
+    pr, seed, k = job
+    p = oracle_params(pr)
+    sk = ckks.secret_key(p, seed)
+    mods = p.qp_mods(p.L)
+    if k == 0:
+        s_mod = ring.from_signed(sk.s, mods)
+        target = ckks.polymul(p, s_mod, s_mod, mods)
+    else:
+        target = ring.from_signed(ckks.automorphism_signed(p, sk.s, k), mods)
+    return k, ckks.switch_key(p, seed, sk, target, k)
+
+
+def _oracle_keys(pr, seed, steps):
+    from oracle import ckks
+    p = oracle_params(pr)
+    sk = ckks.secret_key(p, seed)
+    keys = ckks.Keys(seed, *ckks.public_key(p, seed, sk))
+    gal = sorted({p.galois(st) for st in {int(r) % p.n for r in steps} - {0}})
+    jobs = [(pr, seed, 0)] + [(pr, seed, k) for k in gal]
+    workers = max(1, min(16, os.cpu_count() or 1, len(jobs)))
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as pool:   # a lost worker raises
+        for k, sw in pool.map(_switch_key_task, jobs):
+            if k == 0:
+                keys.relin = sw
+            else:
+                keys.rot[k] = sw
+    return sk, keys
+
+
+def test_full_uci_inference_graph_bit_exact():
+    from oracle import ckks, dlrm
+    from paper_2506_18150_gb300 import helrm as H
+    from paper_2506_18150_gb300 import synthetic as syn
+    pr = syn.PARAMS["full"]
+    p = oracle_params(pr)
+    spec = syn.uci_spec(0)
+    w = syn.make_weights(spec, 0)
+    c = dlrm.compile_model(p, spec, w)
+    steps = c.rotation_steps()
+    _, keys_o = _oracle_keys(pr, 77, steps)           # the pool starts before this test's first GPU call
+    ctx = gpu_ctx(pr)
+    model = H.helrm_model_create(ctx, spec, w)
+    assert H.helrm_model_rotations(ctx, model) == steps
+    H.helrm_model_import_plaintexts(ctx, model, np.stack([np.asarray(x, dtype=np.int64) for x in c.plaintexts()]))
+    sk, evk = H.helrm_keygen(ctx, 77, steps)
+    batch = H.helrm_batch_create(ctx, model, [evk])
+    H.helrm_batch_set_graph(ctx, batch, True)
+    dense, idx = syn.make_queries(spec, 2, seed=33)
+    for q in range(2):                                # the capture, then a replay
+        xd, xs = dlrm.query_slots(p, c, dense[q], idx[q])
+        md, ms = ckks.encode_real(p, xd, p.delta), ckks.encode_real(p, xs, p.delta)
+        cd = H.helrm_encrypt(ctx, evk, H.helrm_pt_import(ctx, md, c.lvl_dense, p.delta), 40 + 2 * q)
+        cs = H.helrm_encrypt(ctx, evk, H.helrm_pt_import(ctx, ms, c.lvl_sel, p.delta), 41 + 2 * q)
+        y = H.helrm_infer_batch(ctx, batch, [cd], [cs])[0]
+        if q == 1:
+            y_o = dlrm.infer(p, keys_o, c, ckks.encrypt(p, keys_o, md, c.lvl_dense, p.delta, 40 + 2 * q),
+                             ckks.encrypt(p, keys_o, ms, c.lvl_sel, p.delta, 41 + 2 * q))
+            assert_ct_equal(ctx, y, y_o)
+            lg = H.helrm_decrypt_logit(ctx, sk, y)[0]
+            assert abs(lg - dlrm.dlrm_cleartext(spec, w, dense[q], idx[q])[0]) < 1e-3

@@ -123,6 +123,10 @@ def test_full_matvec(full, which):
     assert np.max(np.abs(H.helrm_decrypt(ctx, sk, out, 256) - want[:256])) < 1e-3
 
 
+def _worker_init(threads):
+    os.environ["OMP_NUM_THREADS"] = str(threads)   # before the oracle's OpenMP library loads here
+
+
 def _switch_key_task(job):
     """One oracle switching key, composed as the oracle's keygen composes it:
     key id 0 = relinearisation (s' = s^2), else the Galois element k (s' = s(X^k))."""
@@ -146,8 +150,10 @@ def _oracle_keys(pr, seed, steps):
     keys = ckks.Keys(seed, *ckks.public_key(p, seed, sk))
     gal = sorted({p.galois(st) for st in {int(r) % p.n for r in steps} - {0}})
     jobs = [(pr, seed, 0)] + [(pr, seed, k) for k in gal]
-    workers = max(1, min(16, os.cpu_count() or 1, len(jobs)))
-    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as pool:   # a lost worker raises
+    cpus = os.cpu_count() or 1
+    workers = max(1, min(16, cpus, len(jobs)))
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn"),            # a lost worker raises
+                             initializer=_worker_init, initargs=(max(1, cpus // workers),)) as pool:
         for k, sw in pool.map(_switch_key_task, jobs):
             if k == 0:
                 keys.relin = sw

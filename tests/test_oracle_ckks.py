@@ -173,6 +173,29 @@ def test_moddown_is_division_by_P_within_K(small_params):
         assert any((v % Q) == ov for v in range(lo, hi + 1))
 
 
+def test_moddown_rounding_error_has_the_uncorrected_conversions_mean(small_params):
+    """Without an overflow correction, ModDown returns floor(u/P) - v with v
+    the conversion's overflow (v in [0, K), of mean 1 for K = 3: the floor of
+    a sum of three uniforms), so its error against round(u/P) has mean
+    -1/2 - 1 = -3/2.  A corrected conversion would give -1/2, an exact
+    rounding 0; 1024 random coefficients tell them apart (standard error 0.03)."""
+    p = small_params
+    lvl = 2
+    qp = p.qp_mods(lvl)
+    rng = np.random.default_rng(6)
+    u = np.stack([rng.integers(0, q, p.N, dtype=np.uint64) for q in qp])
+    out = ckks.moddown(p, u, lvl)
+    U = big(p, u, qp)
+    O = big(p, out, p.q_mods(lvl))
+    Q = math.prod(p.q_mods(lvl))
+    err = []
+    for uv, ov in zip(U, O):
+        e = (ov - (2 * uv + p.P) // (2 * p.P)) % Q       # against round(u / P)
+        err.append(e - Q if e > Q // 2 else e)
+    assert set(err) <= {0, -1, -2, -3}
+    assert abs(np.mean(err) + 1.5) < 0.15
+
+
 # ---------------------------------------------------------------- rotation / key switching
 @pytest.mark.parametrize("step", [1, 3, -1, 100, -7])
 def test_rotation_is_cyclic_shift(small_params, small_keys, step):

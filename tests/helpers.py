@@ -1,5 +1,11 @@
 """Shared helpers for the GPU parity tests: build matching library/oracle
-contexts and move data between them.  Nothing here computes the method."""
+contexts, move data between them, and make the oracle's keys in a process
+pool.  Nothing here computes the method: the key helper only calls the
+oracle's own key functions."""
+import multiprocessing as mp
+import os
+from concurrent.futures import ProcessPoolExecutor
+
 import numpy as np
 
 
@@ -42,3 +48,45 @@ def import_ct(ctx, ct_or):
 
 def as_signed(m):
     return np.array([int(x) for x in m], dtype=np.int64)
+
+
+def _worker_init(threads):
+    os.environ["OMP_NUM_THREADS"] = str(threads)   # before the oracle's OpenMP library loads here
+
+
+def _switch_key_task(job):
+    """One oracle switching key, composed as the oracle's keygen composes it:
+    key id 0 = relinearisation (s' = s^2), else the Galois element k (s' = s(X^k))."""
+    from oracle import ckks, ring
+    pr, seed, k = job
+    p = oracle_params(pr)
+    sk = ckks.secret_key(p, seed)
+    mods = p.qp_mods(p.L)
+    if k == 0:
+        s_mod = ring.from_signed(sk.s, mods)
+        target = ckks.polymul(p, s_mod, s_mod, mods)
+    else:
+        target = ring.from_signed(ckks.automorphism_signed(p, sk.s, k), mods)
+    return k, ckks.switch_key(p, seed, sk, target, k)
+
+
+def oracle_keys_pool(pr, seed, steps):
+    """The oracle's keys (public, relinearisation, one per rotation step),
+    each switching key made by the oracle's own key functions in a
+    spawn-started process pool, one key per task; equal to ckks.keygen's."""
+    from oracle import ckks
+    p = oracle_params(pr)
+    sk = ckks.secret_key(p, seed)
+    keys = ckks.Keys(seed, *ckks.public_key(p, seed, sk))
+    gal = sorted({p.galois(st) for st in {int(r) % p.n for r in steps} - {0}})
+    jobs = [(pr, seed, 0)] + [(pr, seed, k) for k in gal]
+    cpus = os.cpu_count() or 1
+    workers = max(1, min(16, cpus, len(jobs)))
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn"),            # a lost worker raises
+                             initializer=_worker_init, initargs=(max(1, cpus // workers),)) as pool:
+        for k, sw in pool.map(_switch_key_task, jobs):
+            if k == 0:
+                keys.relin = sw
+            else:
+                keys.rot[k] = sw
+    return sk, keys

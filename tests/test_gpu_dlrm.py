@@ -6,7 +6,7 @@ and at the full UCI-shaped configuration (N=2^16, 20 levels)."""
 import numpy as np
 import pytest
 
-from helpers import assert_ct_equal, gpu_ctx, oracle_params
+from helpers import assert_ct_equal, gpu_ctx, oracle_keys_pool, oracle_params
 
 pytestmark = pytest.mark.gpu
 
@@ -148,3 +148,43 @@ def test_wrong_query_level_is_rejected():
     with pytest.raises(H.HelrmError) as ex:
         H.helrm_encrypt_query(e["ctx"], e["evk"], e["model"], dense[0], bad, 3)
     assert ex.value.name == "HELRM_E_INVAL"
+
+
+def test_criteo_shaped_logit_bit_exact():
+    """The Criteo model's structure at a smaller size: 13 dense features, 26
+    tables (2..399 rows, base 64), bottom 13-64-16, dot interaction of 27
+    blocks (367 = 16 + C(27, 2) top inputs, padded to 512), top 367-64-1.  The
+    interaction's layout needs 13 x 1024 slots, so N = 2^15.  With the
+    oracle's plaintexts, keys and encryption randomness the logit ciphertext
+    is bit-exact; the logit is the FP64 model's within 1e-3."""
+    from oracle import ckks, dlrm
+    from paper_2506_18150_gb300 import helrm as H
+    from paper_2506_18150_gb300 import synthetic as syn
+    rng = np.random.default_rng(5)
+    spec = syn.DLRMSpec("criteo_small", 13, [13, 64, 16], [0, 64, 1], [int(x) for x in rng.integers(2, 400, 26)],
+                        64, 16, "dot")
+    spec.top[0] = syn.top_input_width(spec)
+    assert spec.top[0] == 367
+    pr = syn.reduced_params(15, 9)
+    p = oracle_params(pr)
+    w = syn.make_weights(spec, 0)
+    c = dlrm.compile_model(p, spec, w)
+    steps = c.rotation_steps()
+    _, keys_o = oracle_keys_pool(pr, 3, steps)          # the pool starts before this test's first GPU call
+    ctx = gpu_ctx(pr)
+    model = H.helrm_model_create(ctx, spec, w)
+    info = H.helrm_model_info(ctx, model)
+    assert (info["lvl_dense"], info["lvl_sel"], info["lvl_z"], info["lvl_u"]) == (c.lvl_dense, c.lvl_sel, c.lvl_z, c.lvl_u)
+    assert H.helrm_model_rotations(ctx, model) == steps
+    H.helrm_model_import_plaintexts(ctx, model, np.stack([np.asarray(x, dtype=np.int64) for x in c.plaintexts()]))
+    sk, evk = H.helrm_keygen(ctx, 3, steps)
+    dense, idx = syn.make_queries(spec, 1, seed=4)
+    xd, xs = dlrm.query_slots(p, c, dense[0], idx[0])
+    md, ms = ckks.encode_real(p, xd, p.delta), ckks.encode_real(p, xs, p.delta)
+    cd = H.helrm_encrypt(ctx, evk, H.helrm_pt_import(ctx, md, c.lvl_dense, p.delta), 20)
+    cs = H.helrm_encrypt(ctx, evk, H.helrm_pt_import(ctx, ms, c.lvl_sel, p.delta), 21)
+    y = H.helrm_infer(ctx, evk, model, cd, cs)
+    y_o = dlrm.infer(p, keys_o, c, ckks.encrypt(p, keys_o, md, c.lvl_dense, p.delta, 20),
+                     ckks.encrypt(p, keys_o, ms, c.lvl_sel, p.delta, 21))
+    assert_ct_equal(ctx, y, y_o)
+    assert abs(H.helrm_decrypt_logit(ctx, sk, y)[0] - dlrm.dlrm_cleartext(spec, w, dense[0], idx[0])[0]) < 1e-3

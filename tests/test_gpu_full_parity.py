@@ -17,14 +17,10 @@ benchmark times (the server path of a batch of one, captured as a CUDA graph
 and replayed): its logit ciphertext against the oracle's, word for word.  Its
 47 oracle keys are made by the oracle's own key functions in a spawn-started
 process pool, one key per task."""
-import multiprocessing as mp
-import os
-from concurrent.futures import ProcessPoolExecutor
-
 import numpy as np
 import pytest
 
-from helpers import assert_ct_equal, gpu_ctx, oracle_params
+from helpers import assert_ct_equal, gpu_ctx, oracle_keys_pool, oracle_params
 
 pytestmark = pytest.mark.gpu
 
@@ -123,45 +119,6 @@ def test_full_matvec(full, which):
     assert np.max(np.abs(H.helrm_decrypt(ctx, sk, out, 256) - want[:256])) < 1e-3
 
 
-def _worker_init(threads):
-    os.environ["OMP_NUM_THREADS"] = str(threads)   # before the oracle's OpenMP library loads here
-
-
-def _switch_key_task(job):
-    """One oracle switching key, composed as the oracle's keygen composes it:
-    key id 0 = relinearisation (s' = s^2), else the Galois element k (s' = s(X^k))."""
-    from oracle import ckks, ring
-    pr, seed, k = job
-    p = oracle_params(pr)
-    sk = ckks.secret_key(p, seed)
-    mods = p.qp_mods(p.L)
-    if k == 0:
-        s_mod = ring.from_signed(sk.s, mods)
-        target = ckks.polymul(p, s_mod, s_mod, mods)
-    else:
-        target = ring.from_signed(ckks.automorphism_signed(p, sk.s, k), mods)
-    return k, ckks.switch_key(p, seed, sk, target, k)
-
-
-def _oracle_keys(pr, seed, steps):
-    from oracle import ckks
-    p = oracle_params(pr)
-    sk = ckks.secret_key(p, seed)
-    keys = ckks.Keys(seed, *ckks.public_key(p, seed, sk))
-    gal = sorted({p.galois(st) for st in {int(r) % p.n for r in steps} - {0}})
-    jobs = [(pr, seed, 0)] + [(pr, seed, k) for k in gal]
-    cpus = os.cpu_count() or 1
-    workers = max(1, min(16, cpus, len(jobs)))
-    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn"),            # a lost worker raises
-                             initializer=_worker_init, initargs=(max(1, cpus // workers),)) as pool:
-        for k, sw in pool.map(_switch_key_task, jobs):
-            if k == 0:
-                keys.relin = sw
-            else:
-                keys.rot[k] = sw
-    return sk, keys
-
-
 def test_full_uci_inference_graph_bit_exact():
     from oracle import ckks, dlrm
     from paper_2506_18150_gb300 import helrm as H
@@ -172,7 +129,7 @@ def test_full_uci_inference_graph_bit_exact():
     w = syn.make_weights(spec, 0)
     c = dlrm.compile_model(p, spec, w)
     steps = c.rotation_steps()
-    _, keys_o = _oracle_keys(pr, 77, steps)           # the pool starts before this test's first GPU call
+    _, keys_o = oracle_keys_pool(pr, 77, steps)           # the pool starts before this test's first GPU call
     ctx = gpu_ctx(pr)
     model = H.helrm_model_create(ctx, spec, w)
     assert H.helrm_model_rotations(ctx, model) == steps

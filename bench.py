@@ -6,43 +6,49 @@ client packing of the dense features and the digit one-hot selectors,
 encoding and encryption (two ciphertexts), the server's bottom MLP, packed
 embedding lookup, dot interaction and top MLP (double-hoisted BSGS matvecs,
 x^2 activations), and decryption of the logit.  Default workload: the
-UCI-health-shaped DLRM (10 dense features, 8 tables of 2..64 rows, dim 16,
-bottom 10-32-16, top 52-32-1) at N = 2^16 with a 60-bit base prime, 20
-levels of 40-bit primes and three 60-bit special primes, synthetic seeded
-inputs.
+Criteo-shaped DLRM (13 dense features, 26 tables with 33.8M rows in base 64,
+dim 16, bottom 13-512-256-64-16, top 367-512-256-1), the largest one-query
+configuration, at N = 2^16 with a 60-bit base prime, 20 levels of 40-bit
+primes and three 60-bit special primes, synthetic seeded inputs.
 
   value  inferences/s with the query's inputs already in HBM (device pointers),
          the server path of a batch of one replayed as a CUDA graph
          (value_eager: the same with every kernel launched on the stream);
-  e2e    the same through helrm_infer_e2e from pinned host buffers, the
-         host->device copy of the query and the device->host read of the
-         logit inside the timed region.
-The default line also carries "batched": 16 UCI-shaped queries of 8 clients
-through one lockstep batch (helrm_infer_batch_e2e_device), against the same
-16 queries one at a time.
+  e2e    the same through helrm_infer_batch_e2e from pinned host buffers: the
+         host->device copy of the query's features and the device->host read
+         of the logit inside the timed region (the client encrypts on the same
+         GPU); e2e.server: the server's side of the protocol alone, the two
+         query ciphertexts imported from host memory (helrm_ct_import), the
+         inference, the logit ciphertext exported to host memory.
+The default line also carries, each timed on the same GPU in the same run:
+  uci      the same measurements for the UCI-shaped DLRM (10 dense, 8 tables
+           of 2..64 rows, bottom 10-32-16, top 52-32-1);
+  batched  16 UCI-shaped queries of 8 clients in one lockstep batch against
+           the same 16 one at a time;
+  config4  64 concurrent queries per step, 32 UCI-shaped (16 clients) and 32
+           Criteo-shaped (8 clients), each model's queries one lockstep batch,
+           against the same queries one at a time;
+  served   the request loop (helrm_server_run) on Poisson traces at two
+           arrival rates, 80% UCI / 20% Criteo over config4's clients, with
+           p50/p99 latency, for the continuous-batching server and the plain
+           one-request-at-a-time path.
 
---workload criteo   the same line for the Criteo-shaped DLRM (one query/step).
---workload uci_silu the UCI-shaped line with polynomial activations: every
-                    activation a degree-6 SiLU polynomial (depth 4, 18 of
-                    the 20 levels, no bootstrapping).
---workload batched  64 concurrent queries per step, 32 UCI-shaped (16 clients)
-                    and 32 Criteo-shaped (8 clients), each model's queries in
-                    one lockstep batch; keys truncated to the levels each
-                    model uses them at (helrm_model_keygen).
---workload served   the request loop (helrm_server_run) on Poisson traces,
-                    80% UCI / 20% Criteo, 32 + 8 clients with resident keys:
-                    p50/p99 latency and inferences/s per arrival rate, for
-                    the continuous-batching server and for the plain
-                    one-request-at-a-time path.
+--workload uci / uci_silu   the one-query line for the UCI-shaped model
+                    (uci_silu: every activation a degree-6 SiLU polynomial).
+--workload batched  config4 alone, with more steps.
+--workload served   the request loop at every rate of --rates, 32 + 8 clients.
 Multi-GPU: replicas (each rank its own clients and queries, no collective);
-value = all ranks' inferences / the slowest rank's time.
+value = all ranks' inferences / the slowest rank's time.  Without torchrun,
+--gpus N > 1 starts N ranks itself.
 --impl reference times the CPU oracle instead (rank 0 only).
 """
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
+import socket
 import subprocess
 import sys
 import threading
@@ -53,46 +59,53 @@ sys.path.insert(0, ROOT)
 
 METRIC = "encrypted DLRM inferences/s"
 UNIT = "inferences/s"
+ONE_QUERY = ("criteo", "uci", "uci_silu")
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
-                    help="timed steps (default: 100 for the one-query workloads, 20 for batched and --impl reference)")
+                    help="timed steps (default: 100 for the one-query workloads, 20 for --impl reference "
+                         "and batched)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="uci", choices=["uci", "criteo", "uci_silu", "batched", "served"])
+    ap.add_argument("--workload", default="criteo", choices=["criteo", "uci", "uci_silu", "batched", "served"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="one-query line only (no uci/batched/config4/served keys)")
     ap.add_argument("--requests", type=int, default=1000, help="served: requests per arrival rate")
     ap.add_argument("--rates", default="1,5,10,20,50,100,200", help="served: arrival rates (requests/s)")
     ap.add_argument("--slots", type=int, default=2, help="served: batch slots (CUDA streams) of the batching server")
     ap.add_argument("--max-batch", type=int, default=8, help="served: requests per batch of the batching server")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
     if args.steps is None:
-        args.steps = 100 if args.impl == "ours" and args.workload in ("uci", "criteo", "uci_silu") else 20
+        args.steps = 100 if args.impl == "ours" and args.workload in ONE_QUERY else 20
     return args
 
 
-def workload_config(name):
+DESC = {
+    "uci": "UCI-health-shaped DLRM, 1 query/step: 10 dense, 8 tables (2..64 rows), dim 16, "
+           "bottom 10-32-16, dot interaction, top 52-32-1, x^2",
+    "criteo": "Criteo-shaped DLRM, 1 query/step: 13 dense, 26 tables (33.8M rows, base 64), dim 16, "
+              "bottom 13-512-256-64-16, dot interaction, top 367-512-256-1, x^2",
+    "uci_silu": "UCI-health-shaped DLRM, 1 query/step, as 'uci' but every activation is a degree-6 "
+                "least-squares SiLU polynomial on [-6, 6] (depth 4, no bootstrapping; ct_dense at level 18)",
+}
+CKKS = "N=2^16, q0 60-bit + 20x40-bit, K=3x60-bit special, alpha=3, Delta=2^40"
+
+
+def workload_config(name, world=1):
     from paper_2506_18150_gb300 import synthetic as syn
     spec = {"uci": syn.uci_spec, "criteo": syn.criteo_spec, "uci_silu": syn.uci_silu_spec}[name](0)
-    desc = {
-        "uci": "UCI-health-shaped DLRM, 1 query/step: 10 dense, 8 tables (2..64 rows), dim 16, "
-               "bottom 10-32-16, dot interaction, top 52-32-1, x^2",
-        "criteo": "Criteo-shaped DLRM, 1 query/step: 13 dense, 26 tables (33.8M rows, base 64), dim 16, "
-                  "bottom 13-512-256-64-16, dot interaction, top 367-512-256-1, x^2",
-        "uci_silu": "UCI-health-shaped DLRM, 1 query/step, as 'uci' but every activation is a degree-6 "
-                    "least-squares SiLU polynomial on [-6, 6] (depth 4, no bootstrapping; ct_dense at level 18)",
-    }[name]
-    cfg = {"workload": desc, "ckks": "N=2^16, q0 60-bit + 20x40-bit, K=3x60-bit special, alpha=3, Delta=2^40",
+    cfg = {"workload": DESC[name], "ckks": CKKS,
            "tables": spec.cards if name != "criteo" else f"{len(spec.cards)} tables, {sum(spec.cards)} rows",
-           "l2": "no flush: each step streams ~GBs of keys and diagonals (>> 129 MB L2)"}
+           "l2": "no flush: each step streams GBs of keys and diagonals (>> 129 MB L2)",
+           "parallelism": f"replicas x{world}"}
     return spec, cfg
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 100 ms; start()
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms; start()
     returns once the first sample is in (at most 5 s), so the sampling is
     live when the timed region begins."""
 
@@ -108,7 +121,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-lms", "100", "-i", str(self.idx)],
+                                          "-lms", "50", "-i", str(self.idx)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -153,7 +166,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def peaks():
+def hbm_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
@@ -162,84 +175,66 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# Issue-bound ceiling of the NTT: 152 SMs x 4 schedulers x 32 lanes issue at
-# most 19,456 integer instructions per SM clock, and a lazy Shoup butterfly on
-# 64-bit words needs at least 23 of them (three 64-bit products as 32-bit
-# multiply-adds, the lazy corrections and the sum/difference).
-NTT_INSTR_PER_BUTTERFLY = 23
-ALU_LANES = 152 * 4 * 32
+def alu_peaks(H, ctx):
+    """The integer ceilings, measured on this GPU by helrm_alu_peak: the
+    register-resident rate (no memory traffic) of the NTT's forward and
+    inverse lazy butterflies and of the inner products' 128-bit
+    multiply-accumulates, best of 2..8 CTAs of 256 threads per SM."""
+    out = {}
+    for name, kind in (("fwd_butterfly", 0), ("inv_butterfly", 1), ("mac128", 2)):
+        out[name] = max(H.helrm_alu_peak(ctx, kind, bps, 4096) for bps in (2, 4, 8)) / 1e9
+    # the NTT runs as many forward as inverse butterflies: their mean time per butterfly
+    out["ntt_butterfly"] = 2.0 / (1.0 / out["fwd_butterfly"] + 1.0 / out["inv_butterfly"])
+    return out
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per NTT launch
-# (one transform, both passes) over the one-query UCI-shaped step, from one
-# ncu capture with its default cold caches (profiles/ntt_traffic_uci_dlrm_n16.md).
-# It holds for the sources it was taken on: reported while their SHA-256
-# still matches, null otherwise.
-NTT_TRAFFIC = {"workload": "uci", "bytes_per_launch": 19.83e6,
-               "sha256": {"ntt.cu": "381430a43604fce2ae84e91c42d1e8e831cb84c3b8bb2854fe410d1d0b4a0642",
-                          "core.cuh": "b07128795e4ff0ab3e8bb30502566ed472f561f9e424ae75a00afd43277c7013"}}
-
-
-def ntt_traffic(workload):
-    import hashlib
-    if workload != NTT_TRAFFIC["workload"]:
-        return None
-    for name, digest in NTT_TRAFFIC["sha256"].items():
-        try:
-            with open(os.path.join(ROOT, "paper_2506_18150_gb300", "csrc", name), "rb") as f:
-                if hashlib.sha256(f.read()).hexdigest() != digest:
-                    return None
-        except OSError:
-            return None
-    return NTT_TRAFFIC["bytes_per_launch"]
-
-
-def roofline(rep, n_steps, log_n, sm_mhz, peak_hbm, peak_src, workload=None):
-    """Dominant kernel (by time) with its bound: the NTT against the issue
-    ceiling (butterflies/s), everything else against measured HBM bandwidth."""
+def roofline(rep, n_steps, log_n, peak_hbm, hbm_src, alu=None):
+    """Dominant kernel (by time) with its bound: the NTT against the measured
+    butterfly rate (integer issue, G butterflies/s), every other kernel
+    against the measured HBM copy bandwidth."""
     total = sum(v[1] for v in rep.values())
     dom = max(rep, key=lambda k: rep[k][1])
     n, ms, byts = rep[dom]
     kernels = {k: {"launches_per_step": v[0] / n_steps, "ms_per_step": v[1] / n_steps,
-                   "GBps": (v[2] / (v[1] / 1000.0) / 1e9) if v[1] else None}
+                   "GBps": (v[2] / (v[1] / 1000.0) / 1e9) if v[1] else None,
+                   "hbm_frac": (v[2] / (v[1] / 1000.0) / 1e9 / peak_hbm) if v[1] else None}
                for k, v in sorted(rep.items(), key=lambda kv: -kv[1][1])}
     if dom == "ntt":
         bfly = byts * log_n / 32.0                      # 16 N bytes per limb <-> (N/2) log2 N butterflies
         achieved = bfly / (ms / 1000.0) / 1e9
-        peak = ALU_LANES * sm_mhz * 1e6 / NTT_INSTR_PER_BUTTERFLY / 1e9
+        if alu:
+            peak, src = alu["ntt_butterfly"], ("measured: helrm_alu_peak, register-resident lazy Shoup butterflies "
+                                               "(the NTT passes' code), mean of forward and inverse")
+        else:
+            peak, src = None, "not measured"
         out = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Gbutterfly/s",
-               "frac": achieved / peak,
-               "peak_source": f"derived: {ALU_LANES} lanes x {sm_mhz:.0f} MHz / {NTT_INSTR_PER_BUTTERFLY} "
-                              f"instructions per butterfly",
+               "frac": achieved / peak if peak else None, "peak_source": src,
                "hbm_GBps": byts / (ms / 1000.0) / 1e9, "hbm_frac": byts / (ms / 1000.0) / 1e9 / peak_hbm}
     else:
         achieved = byts / (ms / 1000.0) / 1e9
         out = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
-               "frac": achieved / peak_hbm, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
-    traffic = ntt_traffic(workload) if dom == "ntt" else None
-    if traffic is not None:
-        out["traffic_note"] = ("DRAM bytes per transform under ncu (cold caches), against "
-                               f"{byts / n:.4g} algorithmic bytes per transform")
-    out.update({"traffic": traffic, "launches_per_step": n / n_steps, "ms_per_step": ms / n_steps,
+               "frac": achieved / peak_hbm, "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}
+    out.update({"traffic": None, "launches_per_step": n / n_steps, "ms_per_step": ms / n_steps,
                 "share_of_kernel_time": ms / total, "kernels": kernels})
+    if alu:
+        out["alu_peaks_G_per_s"] = alu
     return out
 
 
 def cpu_baseline(workload: str):
-    """The oracle, as it stands, on this host's cores (subprocess: no CUDA in it)."""
+    """The oracle, as it stands, on this host's cores (subprocess: no CUDA in
+    it), on a bounded sample (oracle.bench_sample --budget)."""
     env = dict(os.environ)
     env.pop("CUDA_VISIBLE_DEVICES", None)
     try:
         r = subprocess.run([sys.executable, "-m", "oracle.bench_sample", "--workload", workload,
-                            "--steps", "2", "--warmup", "0"], cwd=ROOT, capture_output=True, text=True,
-                           timeout=900, env=env)
+                            "--budget"], cwd=ROOT, capture_output=True, text=True,
+                           timeout=1200, env=env)
         d = json.loads(r.stdout.strip().splitlines()[-1])
     except Exception as e:  # noqa: BLE001
         return {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {e}"}
     return {"value": 1.0 / d["est_full_s_per_query"], "unit": UNIT, "cores": d["cores"], "kind": "oracle",
-            "sample": (f"2 queries of the same model at N=2^{d['sample_log_n']} (same levels, keys, limbs per op), "
-                       f"median {d['sample_s_per_query']:.2f} s, scaled x{d['ratio_to_full']:.2f} "
-                       f"(measured oracle ring-product time ratio N=2^16 : N=2^{d['sample_log_n']})")}
+            "sample": d["sample"]}
 
 
 def dist_env():
@@ -249,27 +244,45 @@ def dist_env():
     return world, rank, local
 
 
+def free_port() -> int:
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def spawn_replicas(n: int, script: str, argv, env=None, stdout=None) -> int:
+    """Start n ranks of `script` on this node (torch.distributed.run, one
+    process per GPU, rendezvous on 127.0.0.1); rank 0 prints the JSON line.
+    Returns the launcher's exit status."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(free_port()), script] + list(argv)
+    return subprocess.run(cmd, cwd=ROOT, env=env, stdout=stdout).returncode
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    if args.workload not in ("uci", "criteo", "uci_silu"):
+    if args.workload not in ONE_QUERY:
         print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the one-query workloads "
-                          "(uci, criteo); it has no batched or served mode"}), flush=True)
+                          "(criteo, uci, uci_silu); it has no batched or served mode"}), flush=True)
         return
     from oracle import bench_sample
-    spec, cfg = workload_config(args.workload)
+    spec, cfg = workload_config(args.workload, world)
     d = bench_sample.run(args.workload, args.steps, args.warmup)
-    per = [t * d["ratio_to_full"] for t in d["sample_times_s"]]
-    total = sum(per)
-    value = len(per) / total
+    units = d["steps_in_queries"]                 # the part of a query the timed stages cover
+    value = units / (d["wall_s"] * d["ratio_to_full"])
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(per),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * d["wall_s"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic", "config": cfg,
+            "value_note": (f"each step one stage of a query (of {d['n_stages']}) on the CPU oracle at "
+                           f"N=2^{d['sample_log_n']}; the {args.steps} timed stages cover {units:.3f} queries "
+                           f"(each stage weighted by its measured share of a query) in {d['wall_s']:.1f} s, "
+                           f"scaled x{d['ratio_to_full']:.2f} to N=2^16 (the oracle's ring-product time ratio "
+                           "measured on this host)"),
             "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": d["cores"],
-                             "sample": f"each step one query at N=2^{d['sample_log_n']} scaled x"
-                                       f"{d['ratio_to_full']:.2f} to N=2^16"},
+                             "sample": d["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -299,10 +312,224 @@ def _timed(fn, reps=1):
     return e0.elapsed_time(e1) / reps
 
 
-def batched_probe(H, syn, ctx, model, spec, pr, n_clients=8, n_queries=16):
-    """n_queries queries of n_clients clients: one lockstep batch vs one at a time."""
+class Env:
+    """The context and process state one run of the bench shares."""
+
+    def __init__(self):
+        import torch
+
+        from paper_2506_18150_gb300 import helrm as H
+        from paper_2506_18150_gb300 import synthetic as syn
+        self.torch, self.H, self.syn = torch, H, syn
+        self.world, self.rank, self.local = dist_env()
+        torch.cuda.set_device(self.local)
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+        self.stream = torch.cuda.current_stream()
+        self.pr = syn.PARAMS["full"]
+        pr = self.pr
+        self.ctx = H.helrm_ctx_create(pr["log_n"], pr["q_bits"], pr["n_p"], pr["p_bits"], pr["alpha"],
+                                      pr["log2_scale"], device=self.local, stream=self.stream.cuda_stream)
+        self.models = {}
+
+    def model(self, name):
+        if name not in self.models:
+            spec = {"uci": self.syn.uci_spec, "criteo": self.syn.criteo_spec,
+                    "uci_silu": self.syn.uci_silu_spec}[name](0)
+            self.models[name] = (spec, self.H.helrm_model_create(self.ctx, spec, self.syn.make_weights(spec, 0)))
+        return self.models[name]
+
+    def barrier(self):
+        self.torch.cuda.synchronize()
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        self.torch.cuda.synchronize()
+
+    def close(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+def one_query(E, wl, K, W, hbm, alu, seed=1000):
+    """The one-query measurements of workload wl: value (graph-replayed batch
+    of one, inputs in HBM), value_eager, e2e from host features, e2e of the
+    server side from host ciphertexts, per-query latency, the kernel
+    roofline."""
+    import ctypes
+
     import numpy as np
-    import torch
+    torch, H, syn, ctx, stream = E.torch, E.H, E.syn, E.ctx, E.stream
+    spec, model = E.model(wl)
+    sk, evk = H.helrm_model_keygen(ctx, model, seed + E.rank)
+    dense, idx = syn.make_queries(spec, K + W, seed=500 + E.rank)
+    d_dense = torch.tensor(dense, dtype=torch.float64, device="cuda")
+    d_idx = torch.tensor(idx.astype(np.int64), dtype=torch.int64, device="cuda")
+    d_logit = torch.zeros(K + W, dtype=torch.float64, device="cuda")
+    nd, nt = dense.shape[1], idx.shape[1]
+
+    def step_dev(q):
+        H.helrm_infer_e2e_device(ctx, sk, evk, model, d_dense[q].data_ptr(), d_idx[q].data_ptr(), 1,
+                                 7 + 2 * q, d_logit[q:q + 1].data_ptr())
+
+    # the same query through a batch of one whose server path is replayed as a
+    # CUDA graph (helrm_batch_set_graph; bit-identical to the eager path): the
+    # client's packing and encryption and the decryption stay eager
+    bt1 = H.helrm_batch_create(ctx, model, [evk])
+    H.helrm_batch_set_graph(ctx, bt1, True)
+
+    def step_graph(q):
+        H.helrm_infer_batch_e2e_device(ctx, bt1, [sk], d_dense[q].data_ptr(), d_idx[q].data_ptr(), 7 + 2 * q,
+                                       d_logit[q:q + 1].data_ptr())
+
+    # ---- value_eager: inputs resident in HBM, every kernel launched on the stream
+    for q in range(W):
+        step_dev(q)
+    E.barrier()
+    l0 = H.helrm_ctx_launch_count(ctx)
+    ee = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ee[0].record(stream)
+    for s in range(K):
+        step_dev(W + s)
+    ee[1].record(stream)
+    E.barrier()
+    launches_per_step = (H.helrm_ctx_launch_count(ctx) - l0) / K   # the graph replays the same kernels
+    value_eager, _ = job_throughput(K, ee[0].elapsed_time(ee[1]), E.world)
+
+    # ---- value: the same steps with the server path replayed as a graph
+    for q in range(W):
+        step_graph(q)
+    E.barrier()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    ncu_range = os.environ.get("HELRM_PROFILE_RANGE") == "1"   # lets `ncu --profile-from-start off` see only these steps
+    if ncu_range:
+        torch.cuda.profiler.start()
+    ev[0].record(stream)
+    for s in range(K):
+        step_graph(W + s)
+        ev[s + 1].record(stream)
+    torch.cuda.synchronize()
+    if ncu_range:
+        torch.cuda.profiler.stop()
+    E.barrier()
+    per = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(K))
+    value, total_ms = job_throughput(K, ev[0].elapsed_time(ev[K]), E.world)
+    logits = d_logit.cpu().numpy()
+
+    # ---- e2e: pinned host buffers through helrm_infer_batch_e2e
+    h_dense = torch.from_numpy(np.ascontiguousarray(dense)).pin_memory()
+    h_idx = torch.from_numpy(np.ascontiguousarray(idx.astype(np.uint64)).view(np.int64)).pin_memory()
+    h_out = torch.zeros(K + W, dtype=torch.float64).pin_memory()
+    L = H.lib()
+    dp = ctypes.POINTER(ctypes.c_double)
+    up = ctypes.POINTER(ctypes.c_uint64)
+    sks = (ctypes.c_void_p * 1)(sk.ptr.value)
+
+    def call(st):
+        if st != 0:
+            raise H.HelrmError(st, L.helrm_last_error(ctx.ptr).decode())
+
+    def step_host(q):   # helrm_infer_batch_e2e: the graph-replayed batch of one, host buffers
+        call(L.helrm_infer_batch_e2e(ctx.ptr, bt1.ptr, sks, ctypes.c_void_p(h_dense.data_ptr() + 8 * nd * q),
+                                     ctypes.c_void_p(h_idx.data_ptr() + 8 * nt * q), 7 + 2 * q,
+                                     ctypes.c_void_p(h_out.data_ptr() + 8 * q)))
+
+    def step_host_eager(q):   # helrm_infer_e2e: every kernel launched on the stream, host buffers
+        call(L.helrm_infer_e2e(ctx.ptr, sk.ptr, evk.ptr, model.ptr,
+                               ctypes.cast(h_dense.data_ptr() + 8 * nd * q, dp),
+                               ctypes.cast(h_idx.data_ptr() + 8 * nt * q, up), 1, 7 + 2 * q,
+                               ctypes.cast(h_out.data_ptr() + 8 * q, dp), None))
+
+    def timed_host(fn):
+        for q in range(W):
+            fn(q)
+        E.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s in range(K):
+            fn(W + s)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return job_throughput(K, e0.elapsed_time(e1), E.world)[0]
+
+    e2e_eager = timed_host(step_host_eager)
+    e2e_value = timed_host(step_host)
+    same = bool(np.allclose(h_out.numpy()[W:], logits[W:], atol=1e-9))
+
+    # ---- e2e of the server side: ciphertexts in from host memory, logit ciphertext out
+    n_srv = min(K, 20)
+    q_cts = [H.helrm_encrypt_query(ctx, evk, model, dense[q], idx[q], 7 + 2 * q) for q in range(W + n_srv)]
+    if isinstance(q_cts[0][1], list):
+        raise RuntimeError("server e2e expects a one-ciphertext selector")
+    host_cts = []
+    for cd, cs in q_cts:
+        pair = []
+        for ct in (cd, cs):
+            coeffs, lv, sc = H.helrm_ct_export(ctx, ct)
+            pair.append((torch.from_numpy(coeffs.reshape(-1).view(np.int64)).pin_memory(), lv, sc))
+        host_cts.append(pair)
+    del q_cts
+    h2d_srv = sum(8 * t.numel() for t, _, _ in host_cts[0])
+    h_logct = None
+
+    def step_server(q):
+        ins = []
+        for t, lv, sc in host_cts[q]:
+            o = ctypes.c_void_p()
+            call(L.helrm_ct_import(ctx.ptr, ctypes.cast(t.data_ptr(), up), lv, ctypes.c_double(sc), ctypes.byref(o)))
+            ins.append(H.Handle(o.value, ctx))
+        y = H.helrm_infer_batch(ctx, bt1, [ins[0]], [ins[1]])[0]
+        nonlocal h_logct
+        if h_logct is None:   # sized once, at the first (untimed) call, for the logit's level
+            h_logct = torch.zeros(2 * (H.helrm_ct_info(ctx, y)[0] + 1) << E.pr["log_n"], dtype=torch.int64)
+            h_logct = h_logct.pin_memory()
+        call(L.helrm_ct_export(ctx.ptr, y.ptr, ctypes.cast(h_logct.data_ptr(), up), None, None))
+
+    for q in range(W):
+        step_server(q)
+    E.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(n_srv):
+        step_server(W + s)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    srv_value = job_throughput(n_srv, e0.elapsed_time(e1), E.world)[0]
+
+    # ---- kernel roofline: per-kernel CUDA events on the launch stream
+    H.helrm_ctx_profile(ctx, True)
+    n_prof = min(K, 5)
+    for s in range(n_prof):
+        step_dev(W + s)
+    rep = H.helrm_ctx_profile_report(ctx)
+    H.helrm_ctx_profile(ctx, False)
+    roof = roofline(rep, n_prof, E.pr["log_n"], hbm[0], hbm[1], alu)
+    out = {"value": value, "ms_per_step": total_ms / K, "value_eager": value_eager,
+           "latency_ms": {"p50": per[len(per) // 2], "p99": per[min(len(per) - 1, int(round(0.99 * (len(per) - 1))))],
+                          "min": per[0], "max": per[-1]},
+           "launches_per_step": launches_per_step,
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * (nd + nt),
+                   "d2h_bytes_per_step": 8, "same_logits_as_value_path": same,
+                   "api": "helrm_infer_batch_e2e (graph-replayed batch of one, host buffers)",
+                   "eager": e2e_eager,
+                   "server": {"value": srv_value, "unit": UNIT, "steps": n_srv, "h2d_bytes_per_step": h2d_srv,
+                              "d2h_bytes_per_step": 8 * h_logct.numel(),
+                              "api": "helrm_ct_import x2 (query ciphertexts, coefficient domain, from pinned "
+                                     "host memory) + helrm_infer_batch (graph-replayed batch of one) + "
+                                     "helrm_ct_export (logit ciphertext to pinned host memory)"}},
+           "roofline": roof}
+    del bt1, sk, evk, host_cts
+    gc.collect()
+    return out
+
+
+def batched_probe(E, n_clients=8, n_queries=16):
+    """n_queries UCI-shaped queries of n_clients clients: one lockstep batch vs one at a time."""
+    import numpy as np
+    torch, H, syn, ctx = E.torch, E.H, E.syn, E.ctx
+    spec, model = E.model("uci")
     keys = [H.helrm_model_keygen(ctx, model, 4000 + c) for c in range(n_clients)]
     owner = [q % n_clients for q in range(n_queries)]
     batch = H.helrm_batch_create(ctx, model, [keys[o][1] for o in owner])
@@ -326,65 +553,56 @@ def batched_probe(H, syn, ctx, model, spec, pr, n_clients=8, n_queries=16):
     torch.cuda.synchronize()
     t1 = _timed(one_at_a_time, 2)
     tb = _timed(lockstep, 2)
-    return {"queries": n_queries, "clients": n_clients, "keys": "helrm_model_keygen (truncated per level)",
-            "value": n_queries / (tb / 1000.0), "one_at_a_time": n_queries / (t1 / 1000.0),
-            "speedup": t1 / tb, "same_logits": bool(torch.equal(lb, ls)), "unit": UNIT}
+    out = {"queries": n_queries, "clients": n_clients, "keys": "helrm_model_keygen (truncated per level)",
+           "value": n_queries / (tb / 1000.0), "one_at_a_time": n_queries / (t1 / 1000.0),
+           "speedup": t1 / tb, "same_logits": bool(torch.equal(lb, ls)), "unit": UNIT}
+    del batch, keys
+    gc.collect()
+    return out
 
 
-def run_batched(args):
-    """Config 4: 64 concurrent queries per step (32 UCI-shaped of 16 clients,
-    32 Criteo-shaped of 8 clients), each model's queries one lockstep batch."""
+def make_clients(E, n_uci, n_crit, seed_base):
+    """Per-client keys (truncated per level) for n_uci UCI-shaped and n_crit
+    Criteo-shaped clients: [(model name, sk, evk)]."""
+    H, ctx = E.H, E.ctx
+    out = []
+    for c in range(n_uci + n_crit):
+        name = "uci" if c < n_uci else "criteo"
+        sk, evk = H.helrm_model_keygen(ctx, E.model(name)[1], seed_base + c)
+        out.append((name, sk, evk))
+    return out
+
+
+def config4(E, clients, K, W, hbm, alu):
+    """64 concurrent queries per step: 32 UCI-shaped (16 clients) and 32
+    Criteo-shaped (8 clients), each model's queries one lockstep batch; the
+    same queries one at a time."""
     import numpy as np
-    import torch
-
-    from paper_2506_18150_gb300 import helrm as H
-    from paper_2506_18150_gb300 import synthetic as syn
-
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    stream = torch.cuda.current_stream()
-    pr = syn.PARAMS["full"]
-    ctx = H.helrm_ctx_create(pr["log_n"], pr["q_bits"], pr["n_p"], pr["p_bits"], pr["alpha"], pr["log2_scale"],
-                             device=local, stream=stream.cuda_stream)
+    torch, H, syn, ctx, stream = E.torch, E.H, E.syn, E.ctx, E.stream
     groups = []
-    for name, spec_fn, n_cl, n_q in [("uci", syn.uci_spec, 16, 32), ("criteo", syn.criteo_spec, 8, 32)]:
-        spec = spec_fn(0)
-        model = H.helrm_model_create(ctx, spec, syn.make_weights(spec, 0))
-        keys = [H.helrm_model_keygen(ctx, model, 10_000 * (rank + 1) + 100 * len(groups) + c) for c in range(n_cl)]
-        owner = [q % n_cl for q in range(n_q)]
-        batch = H.helrm_batch_create(ctx, model, [keys[o][1] for o in owner])
-        K, W = args.steps, args.warmup
-        dense, idx = syn.make_queries(spec, n_q * (K + W), seed=600 + rank * 10 + len(groups))
-        groups.append(dict(name=name, spec=spec, model=model, keys=keys, owner=owner, batch=batch, n_q=n_q,
-                           dense=dense, idx=idx, nd=dense.shape[1], nt=idx.shape[1],
+    for name, n_q in (("uci", 32), ("criteo", 32)):
+        spec, model = E.model(name)
+        mine = [c for c in clients if c[0] == name]
+        owner = [mine[q % len(mine)] for q in range(n_q)]
+        batch = H.helrm_batch_create(ctx, model, [o[2] for o in owner])
+        dense, idx = syn.make_queries(spec, n_q * (K + W), seed=600 + E.rank * 10 + len(groups))
+        groups.append(dict(name=name, model=model, owner=owner, batch=batch, n_q=n_q, dense=dense, idx=idx,
+                           nd=dense.shape[1], nt=idx.shape[1],
                            d_dense=torch.tensor(dense, dtype=torch.float64, device="cuda"),
                            d_idx=torch.tensor(idx.astype(np.int64), dtype=torch.int64, device="cuda"),
                            d_lg=torch.zeros(n_q * (K + W), dtype=torch.float64, device="cuda")))
-    K, W = args.steps, args.warmup
     n_step = sum(g["n_q"] for g in groups)
 
     def step(s):
         for g in groups:
             o = s * g["n_q"]
-            H.helrm_infer_batch_e2e_device(ctx, g["batch"], [g["keys"][x][0] for x in g["owner"]],
+            H.helrm_infer_batch_e2e_device(ctx, g["batch"], [x[1] for x in g["owner"]],
                                            g["d_dense"][o].data_ptr(), g["d_idx"][o].data_ptr(), 21 + 2 * o,
                                            g["d_lg"][o:].data_ptr())
 
-    def barrier():
-        torch.cuda.synchronize()
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize()
-
     for s in range(W):
         step(s)
-    barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
+    E.barrier()
     l0 = H.helrm_ctx_launch_count(ctx)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
     ev[0].record(stream)
@@ -392,11 +610,10 @@ def run_batched(args):
         step(W + s)
         ev[s + 1].record(stream)
     torch.cuda.synchronize()
-    clk = clocks.stop()
-    barrier()
+    E.barrier()
     launches = H.helrm_ctx_launch_count(ctx) - l0
     per = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(K))
-    value, total_ms = job_throughput(n_step * K, ev[0].elapsed_time(ev[K]), world)
+    value, total_ms = job_throughput(n_step * K, ev[0].elapsed_time(ev[K]), E.world)
 
     # e2e: each step's inputs copied from pinned host memory, logits read back
     host = [(torch.from_numpy(np.ascontiguousarray(g["dense"])).pin_memory(),
@@ -412,8 +629,8 @@ def run_batched(args):
         for g, (hd, hi, hl) in zip(groups, host):
             o = s * g["n_q"]
             hl[o:o + g["n_q"]].copy_(g["d_lg"][o:o + g["n_q"]], non_blocking=True)
-    barrier()
-    e2e_value, e2e_ms = job_throughput(n_step, _timed(lambda: [step_e2e(W + s) for s in range(K)]) / K, world)
+    E.barrier()
+    e2e_value, _ = job_throughput(n_step, _timed(lambda: [step_e2e(W + s) for s in range(K)]) / K, E.world)
     same = all(torch.equal(hl[W * g["n_q"]:], g["d_lg"][W * g["n_q"]:].cpu()) for g, (_, _, hl) in zip(groups, host))
 
     # the plain one-request-at-a-time path on the same 64 queries
@@ -421,7 +638,7 @@ def run_batched(args):
         for g in groups:
             for q in range(g["n_q"]):
                 o = s * g["n_q"] + q
-                sk, evk = g["keys"][g["owner"][q]]
+                _, sk, evk = g["owner"][q]
                 H.helrm_infer_e2e_device(ctx, sk, evk, g["model"], g["d_dense"][o].data_ptr(),
                                          g["d_idx"][o].data_ptr(), 1, 21 + 2 * o, g["d_lg"][o:o + 1].data_ptr())
     plain_ms = _timed(lambda: plain(W))
@@ -433,79 +650,52 @@ def run_batched(args):
     step(W)
     rep = H.helrm_ctx_profile_report(ctx)
     H.helrm_ctx_profile(ctx, False)
-    peak, peak_src = peaks()
-    roof = roofline(rep, 1, pr["log_n"], clk.get("sm_mhz") or 2070.0, peak, peak_src)
-    mem = H.helrm_ctx_memory_in_use(ctx)
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
-                "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "u64", "data": "synthetic (seeded; shapes of the paper's UCI/Criteo workloads)",
-                "config": {"workload": "batched: 64 concurrent encrypted queries per step, 32 UCI-shaped "
-                                       "(16 clients) + 32 Criteo-shaped (8 clients), one lockstep batch per model",
-                           "ckks": "N=2^16, q0 60-bit + 20x40-bit, K=3x60-bit special, alpha=3, Delta=2^40",
-                           "keys": "per client, each key truncated to the levels its model uses it at",
-                           "device_bytes_held": mem, "parallelism": f"replicas x{world}",
-                           "l2": "no flush: each step streams tens of GB of keys (>> 129 MB L2)"},
-                "latency_ms": {"p50_step": per[len(per) // 2], "max_step": per[-1]},
-                "clocks": clk, "gpu_launches": int(launches),
-                "e2e": {"value": e2e_value, "unit": UNIT,
-                        "h2d_bytes_per_step": sum(8 * g["n_q"] * (g["nd"] + g["nt"]) for g in groups),
-                        "d2h_bytes_per_step": 8 * n_step, "same_logits_as_value_path": bool(same)},
-                "one_at_a_time": {"value": plain_value, "unit": UNIT, "same_logits": bool(plain_same),
-                                  "speedup_of_batched": value / plain_value},
-                "roofline": roof}
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    out = {"value": value, "unit": UNIT, "queries_per_step": n_step, "steps": K, "warmup": W,
+           "ms_per_step": total_ms / K,
+           "workload": "64 concurrent encrypted queries per step, 32 UCI-shaped (16 clients) + 32 Criteo-shaped "
+                       "(8 clients), one lockstep batch per model",
+           "latency_ms": {"p50_step": per[len(per) // 2], "max_step": per[-1]},
+           "gpu_launches": int(launches), "device_bytes_held": H.helrm_ctx_memory_in_use(ctx),
+           "e2e": {"value": e2e_value, "unit": UNIT,
+                   "h2d_bytes_per_step": sum(8 * g["n_q"] * (g["nd"] + g["nt"]) for g in groups),
+                   "d2h_bytes_per_step": 8 * n_step, "same_logits_as_value_path": bool(same)},
+           "one_at_a_time": {"value": plain_value, "unit": UNIT, "same_logits": bool(plain_same),
+                             "speedup_of_batched": value / plain_value},
+           "roofline": roofline(rep, 1, E.pr["log_n"], hbm[0], hbm[1], alu)}
+    for g in groups:
+        g.clear()
+    gc.collect()
+    return out
 
 
-def run_served(args):
-    """Config 5: Poisson arrivals, 80% UCI / 20% Criteo, 32 + 8 clients with
-    resident keys; the continuous-batching server vs the plain path."""
+def served(E, clients, rates, n_requests, slots, max_batch, frac_uci=0.8):
+    """The request loop on Poisson traces: per rate, p50/p99 latency and
+    inferences/s of the continuous-batching server and of the plain path."""
     import numpy as np
-    import torch
-
-    from paper_2506_18150_gb300 import helrm as H
-    from paper_2506_18150_gb300 import synthetic as syn
-
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    pr = syn.PARAMS["full"]
-    ctx = H.helrm_ctx_create(pr["log_n"], pr["q_bits"], pr["n_p"], pr["p_bits"], pr["alpha"], pr["log2_scale"],
-                             device=local, stream=torch.cuda.current_stream().cuda_stream)
-    specs = [syn.uci_spec(0), syn.criteo_spec(0)]
-    models = [H.helrm_model_create(ctx, s, syn.make_weights(s, 0)) for s in specs]
-    n_uci, n_crit = 32, 8
-    cmodel = [0] * n_uci + [1] * n_crit
-    keys = [H.helrm_model_keygen(ctx, models[m], 20_000 * (rank + 1) + c) for c, m in enumerate(cmodel)]
-    key_bytes = sum(H.helrm_evk_bytes(ctx, k[1]) for k in keys)
-    servers = {"batched": H.helrm_server_create(ctx, args.slots, args.max_batch, 0),
+    H, syn, ctx = E.H, E.syn, E.ctx
+    n_uci = sum(1 for c in clients if c[0] == "uci")
+    n_crit = len(clients) - n_uci
+    servers = {"batched": H.helrm_server_create(ctx, slots, max_batch, 0),
                "one_at_a_time": H.helrm_server_create(ctx, 1, 1, 0)}
     for srv in servers.values():
-        for c, m in enumerate(cmodel):
-            H.helrm_server_add_client(ctx, srv, models[m], keys[c][1])
-    rates = [float(x) for x in args.rates.split(",")]
+        for name, _, evk in clients:
+            H.helrm_server_add_client(ctx, srv, E.model(name)[1], evk)
     results = []
-    clocks = ClockSampler(local)
-    clocks.start()
     l0 = H.helrm_ctx_launch_count(ctx)
     for rate in rates:
-        arrival, client = syn.serving_trace(rate, args.requests, n_uci, n_crit, 0.8, seed=int(rate * 10) + rank)
-        pools = [syn.make_queries(specs[m], int(np.sum(np.array([cmodel[c] for c in client]) == m)) or 1,
-                                  seed=700 + m + int(rate)) for m in range(2)]
-        used = [0, 0]
+        arrival, client = syn.serving_trace(rate, n_requests, n_uci, n_crit, frac_uci, seed=int(rate * 10) + E.rank)
+        cmodel = [c[0] for c in clients]
+        pools = {m: syn.make_queries(E.model(m)[0], int(sum(1 for c in client if cmodel[c] == m)) or 1,
+                                     seed=700 + (m == "criteo") + int(rate)) for m in ("uci", "criteo")}
+        used = {"uci": 0, "criteo": 0}
         cts = []
         for r in range(len(arrival)):
             c = int(client[r])
             m = cmodel[c]
             dense, idx = pools[m][0][used[m]], pools[m][1][used[m]]
             used[m] += 1
-            cts.append(H.helrm_encrypt_query(ctx, keys[c][1], models[m], dense, idx, 3 * r + 1))
-        torch.cuda.synchronize()
+            cts.append(H.helrm_encrypt_query(ctx, clients[c][2], E.model(m)[1], dense, idx, 3 * r + 1))
+        E.torch.cuda.synchronize()
         row = {"rate_per_s": rate, "requests": len(arrival)}
         firsts = {}
         for name, srv in servers.items():
@@ -520,204 +710,113 @@ def run_served(args):
                                                                              firsts["one_at_a_time"]))
         del cts
         results.append(row)
-    clk = clocks.stop()
     launches = H.helrm_ctx_launch_count(ctx) - l0
-    top = results[-1]
-    if rank == 0:
-        line = {"metric": METRIC, "value": top["batched"]["inferences_per_s"], "unit": UNIT, "n_gpus": world,
-                "steps": len(rates), "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "u64",
-                "data": "synthetic (seeded Poisson traces; shapes of the paper's UCI/Criteo workloads)",
-                "config": {"workload": f"served: Poisson arrivals at {args.rates} requests/s, {args.requests} "
-                                       "requests per rate, 80% UCI-shaped / 20% Criteo-shaped, 32 + 8 clients",
-                           "server": f"{args.slots} batch slots (CUDA streams), up to {args.max_batch} requests "
-                                     "of one model per batch",
-                           "baseline_server": "1 slot, 1 request per batch (the plain path)",
-                           "resident_key_bytes": key_bytes, "parallelism": f"replicas x{world}"},
-                "value_note": "inferences/s of the batching server at the highest arrival rate",
-                "latency_ms": {"p50": top["batched"]["p50_ms"], "p99": top["batched"]["p99_ms"]},
-                "clocks": clk, "gpu_launches": int(launches), "rates": results}
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    del servers
+    gc.collect()
+    return {"rates": results, "gpu_launches": int(launches), "clients": f"{n_uci} UCI-shaped + {n_crit} Criteo-shaped",
+            "server": f"{slots} batch slots (CUDA streams), up to {max_batch} requests of one model per batch",
+            "baseline_server": "1 slot, 1 request per batch (the plain path)",
+            "resident_key_bytes": sum(H.helrm_evk_bytes(ctx, c[2]) for c in clients)}
+
+
+def base_line(E, args, cfg):
+    return {"metric": METRIC, "unit": UNIT, "n_gpus": E.world, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic (seeded; shapes of the paper's UCI/Criteo workloads)", "config": cfg}
 
 
 def run_ours(args):
-    import ctypes
-
-    import numpy as np
-    import torch
-
-    from paper_2506_18150_gb300 import helrm as H
-    from paper_2506_18150_gb300 import synthetic as syn
-
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    stream = torch.cuda.current_stream()
-    pr = syn.PARAMS["full"]
-    ctx = H.helrm_ctx_create(pr["log_n"], pr["q_bits"], pr["n_p"], pr["p_bits"], pr["alpha"], pr["log2_scale"],
-                             device=local, stream=stream.cuda_stream)
-    spec, cfg = workload_config(args.workload)
-    w = syn.make_weights(spec, 0)
-    model = H.helrm_model_create(ctx, spec, w)
-    sk, evk = H.helrm_keygen(ctx, 1000 + rank, H.helrm_model_rotations(ctx, model))
+    E = Env()
     K, W = args.steps, args.warmup
-    dense, idx = syn.make_queries(spec, K + W, seed=500 + rank)
-    d_dense = torch.tensor(dense, dtype=torch.float64, device="cuda")
-    d_idx = torch.tensor(idx.astype(np.int64), dtype=torch.int64, device="cuda")
-    d_logit = torch.zeros(K + W, dtype=torch.float64, device="cuda")
-    nd, nt = dense.shape[1], idx.shape[1]
-
-    def step_dev(q):
-        H.helrm_infer_e2e_device(ctx, sk, evk, model, d_dense[q].data_ptr(), d_idx[q].data_ptr(), 1,
-                                 7 + 2 * q, d_logit[q:q + 1].data_ptr())
-
-    # the same query through a batch of one whose server path is replayed as a
-    # CUDA graph (helrm_batch_set_graph; bit-identical to the eager path): the
-    # client's packing and encryption and the decryption stay eager
-    bt1 = H.helrm_batch_create(ctx, model, [evk])
-    H.helrm_batch_set_graph(ctx, bt1, True)
-
-    def step_graph(q):
-        H.helrm_infer_batch_e2e_device(ctx, bt1, [sk], d_dense[q].data_ptr(), d_idx[q].data_ptr(), 7 + 2 * q,
-                                       d_logit[q:q + 1].data_ptr())
-
-    def barrier():
-        torch.cuda.synchronize()
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    # ---- value_eager: inputs resident in HBM, every kernel launched on the stream
-    for q in range(W):
-        step_dev(q)
-    barrier()
-    l0 = H.helrm_ctx_launch_count(ctx)
-    ee = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    ee[0].record(stream)
-    for s in range(K):
-        step_dev(W + s)
-    ee[1].record(stream)
-    barrier()
-    launches_per_step = (H.helrm_ctx_launch_count(ctx) - l0) / K   # the graph replays the same kernels
-    value_eager, _ = job_throughput(K, ee[0].elapsed_time(ee[1]), world)
-
-    # ---- value: the same steps with the server path replayed as a graph
-    for q in range(W):
-        step_graph(q)
-    barrier()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
-    clocks = ClockSampler(local)
+    hbm = hbm_peak()
+    alu = alu_peaks(E.H, E.ctx)
+    spec, cfg = workload_config(args.workload, E.world)
+    clocks = ClockSampler(E.local)
     clocks.start()
-    ncu_range = os.environ.get("HELRM_PROFILE_RANGE") == "1"   # lets `ncu --profile-from-start off` see only these steps
-    if ncu_range:
-        torch.cuda.profiler.start()
-    ev[0].record(stream)
-    for s in range(K):
-        step_graph(W + s)
-        ev[s + 1].record(stream)
-    torch.cuda.synchronize()
-    if ncu_range:
-        torch.cuda.profiler.stop()
+    main = one_query(E, args.workload, K, W, hbm, alu)
+    extras = {}
+    if args.workload == "criteo" and not args.no_extras:
+        u = one_query(E, "uci", K, W, hbm, alu)
+        u["config"] = workload_config("uci", E.world)[1]
+        extras["uci"] = u
+        if E.world == 1:
+            extras["batched"] = batched_probe(E)
+        clients = make_clients(E, 16, 8, 10_000 * (E.rank + 1))
+        extras["config4"] = config4(E, clients, min(K, 10), min(W, 3), hbm, alu)
+        extras["served"] = served(E, clients, [100.0, 200.0], 300, args.slots, args.max_batch)
+        del clients
+        gc.collect()
     clk = clocks.stop()
-    barrier()
-    launches = launches_per_step * K
-    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(K)]
-    value, total_ms = job_throughput(K, ev[0].elapsed_time(ev[K]), world)
-    logits = d_logit.cpu().numpy()
-
-    # ---- e2e: pinned host buffers through helrm_infer_e2e
-    h_dense = torch.from_numpy(np.ascontiguousarray(dense)).pin_memory()
-    h_idx = torch.from_numpy(np.ascontiguousarray(idx.astype(np.uint64)).view(np.int64)).pin_memory()
-    h_out = torch.zeros(K + W, dtype=torch.float64).pin_memory()
-    L = H.lib()
-    dp = ctypes.POINTER(ctypes.c_double)
-    up = ctypes.POINTER(ctypes.c_uint64)
-
-    sks = (ctypes.c_void_p * 1)(sk.ptr.value)
-
-    def step_host(q):   # helrm_infer_batch_e2e: the graph-replayed batch of one, host buffers
-        st = L.helrm_infer_batch_e2e(ctx.ptr, bt1.ptr, sks, ctypes.c_void_p(h_dense.data_ptr() + 8 * nd * q),
-                                     ctypes.c_void_p(h_idx.data_ptr() + 8 * nt * q), 7 + 2 * q,
-                                     ctypes.c_void_p(h_out.data_ptr() + 8 * q))
-        if st != 0:
-            raise H.HelrmError(st, L.helrm_last_error(ctx.ptr).decode())
-
-    def step_host_eager(q):   # helrm_infer_e2e: every kernel launched on the stream, host buffers
-        st = L.helrm_infer_e2e(ctx.ptr, sk.ptr, evk.ptr, model.ptr,
-                               ctypes.cast(h_dense.data_ptr() + 8 * nd * q, dp),
-                               ctypes.cast(h_idx.data_ptr() + 8 * nt * q, up), 1, 7 + 2 * q,
-                               ctypes.cast(h_out.data_ptr() + 8 * q, dp), None)
-        if st != 0:
-            raise H.HelrmError(st, L.helrm_last_error(ctx.ptr).decode())
-
-    def timed_host(fn):
-        for q in range(W):
-            fn(q)
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for s in range(K):
-            fn(W + s)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return job_throughput(K, e0.elapsed_time(e1), world)[0]
-
-    e2e_eager = timed_host(step_host_eager)
-    e2e_value = timed_host(step_host)
-    same = bool(np.allclose(h_out.numpy()[W:], logits[W:], atol=1e-9))
-
-    # ---- kernel roofline: per-kernel CUDA events on the launch stream
-    H.helrm_ctx_profile(ctx, True)
-    n_prof = min(K, 5)
-    for s in range(n_prof):
-        step_dev(W + s)
-    rep = H.helrm_ctx_profile_report(ctx)
-    H.helrm_ctx_profile(ctx, False)
-    peak, peak_src = peaks()
-    roof = roofline(rep, n_prof, pr["log_n"], clk.get("sm_mhz") or 2070.0, peak, peak_src, args.workload)
-
-    # ---- batched: 16 queries of 8 clients in one lockstep batch vs one at a time
-    batched = None
-    if args.workload == "uci" and world == 1:
-        batched = batched_probe(H, syn, ctx, model, spec, pr)
-
-    if rank == 0:
-        per_sorted = sorted(per)
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
-                "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "u64", "data": "synthetic (seeded; shapes of the paper's UCI/Criteo workloads)",
-                "config": dict(cfg, parallelism=f"replicas x{world}"),
-                "latency_ms": {"p50": per_sorted[len(per) // 2],
-                               "p99": per_sorted[min(len(per) - 1, int(round(0.99 * (len(per) - 1))))],
-                               "min": per_sorted[0], "max": per_sorted[-1]},
-                "clocks": clk, "gpu_launches": int(launches),
-                "value_eager": value_eager,
-                "value_note": "value: the server path of a batch of one replayed as a CUDA graph "
-                              "(helrm_infer_batch_e2e_device); value_eager: every kernel launched on the "
-                              "stream (helrm_infer_e2e_device); both bit-identical",
-                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * (nd + nt),
-                        "d2h_bytes_per_step": 8, "same_logits_as_value_path": same,
-                        "api": "helrm_infer_batch_e2e (graph-replayed batch of one, host buffers)",
-                        "eager": e2e_eager},
-                "roofline": roof}
-        if batched:
-            line["batched"] = batched
-        if world == 1 and not args.no_cpu_baseline:
+    if E.rank == 0:
+        line = base_line(E, args, cfg)
+        line.update({"value": main["value"], "ms_per_step": main["ms_per_step"], "latency_ms": main["latency_ms"],
+                     "clocks": clk, "gpu_launches": int(main["launches_per_step"] * K),
+                     "value_eager": main["value_eager"],
+                     "value_note": "value: the server path of a batch of one replayed as a CUDA graph "
+                                   "(helrm_infer_batch_e2e_device); value_eager: every kernel launched on the "
+                                   "stream (helrm_infer_e2e_device); both bit-identical",
+                     "e2e": main["e2e"], "roofline": main["roofline"]})
+        line.update(extras)
+        if E.world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    E.close()
+
+
+def run_batched(args):
+    E = Env()
+    K, W = args.steps, args.warmup
+    hbm = hbm_peak()
+    alu = alu_peaks(E.H, E.ctx)
+    clients = make_clients(E, 16, 8, 10_000 * (E.rank + 1))
+    clocks = ClockSampler(E.local)
+    clocks.start()
+    r = config4(E, clients, K, W, hbm, alu)
+    clk = clocks.stop()
+    if E.rank == 0:
+        line = base_line(E, args, {"workload": "batched: " + r.pop("workload"), "ckks": CKKS,
+                                   "keys": "per client, each key truncated to the levels its model uses it at",
+                                   "parallelism": f"replicas x{E.world}",
+                                   "l2": "no flush: each step streams tens of GB of keys (>> 129 MB L2)"})
+        line.update({"value": r.pop("value"), "ms_per_step": r.pop("ms_per_step"), "clocks": clk,
+                     "gpu_launches": r.pop("gpu_launches"), "e2e": r.pop("e2e"), "roofline": r.pop("roofline")})
+        line.update(r)
+        print(json.dumps(line), flush=True)
+    E.close()
+
+
+def run_served(args):
+    E = Env()
+    clients = make_clients(E, 32, 8, 20_000 * (E.rank + 1))
+    rates = [float(x) for x in args.rates.split(",")]
+    clocks = ClockSampler(E.local)
+    clocks.start()
+    r = served(E, clients, rates, args.requests, args.slots, args.max_batch)
+    clk = clocks.stop()
+    top = r["rates"][-1]
+    if E.rank == 0:
+        line = base_line(E, args, {"workload": f"served: Poisson arrivals at {args.rates} requests/s, "
+                                               f"{args.requests} requests per rate, 80% UCI-shaped / 20% "
+                                               "Criteo-shaped, 32 + 8 clients",
+                                   "server": r["server"], "baseline_server": r["baseline_server"],
+                                   "resident_key_bytes": r["resident_key_bytes"],
+                                   "parallelism": f"replicas x{E.world}"})
+        line.update({"value": top["batched"]["inferences_per_s"], "steps": len(rates), "warmup": 0,
+                     "ms_per_step": None, "value_note": "inferences/s of the batching server at the highest "
+                                                        "arrival rate",
+                     "latency_ms": {"p50": top["batched"]["p50_ms"], "p99": top["batched"]["p99_ms"]},
+                     "clocks": clk, "gpu_launches": r["gpu_launches"], "rates": r["rates"]})
+        print(json.dumps(line), flush=True)
+    E.close()
 
 
 def main():
     args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "0"))
+    if args.gpus > 1 and not world:
+        sys.exit(spawn_replicas(args.gpus, os.path.abspath(__file__), sys.argv[1:]))
+    if world and args.gpus != world:
+        sys.exit(f"--gpus {args.gpus} does not match WORLD_SIZE {world}")
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":

@@ -131,6 +131,9 @@ helrm_status helrm_ctx_profile(helrm_ctx *ctx, int enable);
  * "name launches total_ms algorithmic_bytes\n", into buf (len bytes, always
  * NUL-terminated); *needed (optional) receives the full length + 1. */
 helrm_status helrm_ctx_profile_report(helrm_ctx *ctx, char *buf, uint64_t len, uint64_t *needed);
+/* The same records one per line in launch order, "name ms algorithmic_bytes\n"
+ * (an NTT record's bytes are 16 N per limb, so they give its limb count). */
+helrm_status helrm_ctx_profile_records(helrm_ctx *ctx, char *buf, uint64_t len, uint64_t *needed);
 
 /* ------------------------------------------------------------- raw NTT (a2) */
 /* In-place negacyclic NTT of n_limbs contiguous limbs of N u64 at d_data;
@@ -140,6 +143,19 @@ helrm_status helrm_ctx_profile_report(helrm_ctx *ctx, char *buf, uint64_t len, u
  * The buffer is owned by the caller. */
 helrm_status helrm_ntt(helrm_ctx *ctx, uint64_t *d_data, uint32_t n_limbs, uint32_t first_prime,
                        int inverse);
+
+/* Integer ceiling of the transform (measurement only; the paper has no
+ * counterpart): the register-resident rate of the arithmetic the NTT and the
+ * inner products run, with no memory traffic, on blocks_per_sm x (SM count)
+ * CTAs of 256 threads, each thread repeating `iters` times: kind 0 a radix-8
+ * round of 12 lazy forward butterflies, 1 the same for the inverse
+ * butterflies, 2 eight 64 x 64 -> 128-bit multiply-accumulates, 3 eight
+ * Shoup modular products.  *ops_per_s receives butterflies (0, 1),
+ * multiply-accumulates (2) or products (3) per second, timed with CUDA events
+ * on the context's stream (synchronous).  HELRM_E_INVAL for an unknown kind
+ * or blocks_per_sm outside [1, 32]. */
+helrm_status helrm_alu_peak(helrm_ctx *ctx, int32_t kind, uint32_t blocks_per_sm, uint32_t iters,
+                            double *ops_per_s);
 
 /* ---------------------------------------------------------------- keys (a1) */
 /* Key generation from a 64-bit seed (ChaCha20 streams, as for the oracle):
@@ -484,15 +500,20 @@ helrm_status helrm_server_run(helrm_ctx *ctx, helrm_server *s, uint32_t n, const
  * cudaMalloc, cudaFree or other allocating routine.
  *   d_in    device, n_polys x (level+1) x N u64, NTT domain (the layout of the
  *           library's ciphertexts: c0 limbs then c1 limbs for n_polys = 2);
- *   d_out   device, n_polys x level x N u64, NTT domain; must not overlap d_in.
+ *   d_out   device, n_polys x level x N u64, NTT domain; must not overlap d_in
+ *           (HELRM_E_INVAL if it does).
  * Its one scratch buffer is a static device array of 2 x 65536 u64 words
- * (1 MiB) that every GPU loading the library holds until the process exits;
- * n_polys x N above that limit is rejected with HELRM_E_INVAL.  The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress), so
- * make that first call before any stream capture.  All calls share the array:
- * calls that overlap on the GPU (different streams or contexts on the same
- * device) race on it.  Work is ordered on the context's stream; the call does
- * not synchronise. */
+ * (1 MiB); n_polys x N above that limit is rejected with HELRM_E_INVAL.
+ * helrm_ctx_create does the set-up, where allocating is allowed: it looks up
+ * the array's device address (cudaGetSymbolAddress) and loads its module and
+ * kernels, so every GPU on which a context is created holds the array from
+ * then until the process exits, and this call itself loads nothing.  All
+ * calls share the array and it keeps the last call's contents (each call
+ * overwrites what it reads): calls that overlap on the GPU (different streams
+ * or contexts on the same device) race on it.  Work is ordered on the
+ * context's stream; the call does not synchronise.  Errors: HELRM_E_INVAL
+ * (NULL, overlapping or oversized buffers), HELRM_E_LEVEL (level outside
+ * [1, L]), HELRM_E_CUDA (a failed launch or copy). */
 helrm_status helrm_rescale_noalloc(helrm_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int32_t level,
                                    uint32_t n_polys);
 

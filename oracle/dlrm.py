@@ -433,25 +433,42 @@ def dot_interaction(p, keys, c: Compiled, z: ckks.Ct) -> ckks.Ct:
     return ckks.rescale(p, ckks.relinearize(p, keys, acc, lvl, p.delta * p.delta))
 
 
+def infer_stages(p, keys, c: Compiled, ct_dense: ckks.Ct, ct_sel):
+    """The steps of infer(), in order, as callables that each run one stage
+    (a bottom layer; the lookup and z = h + e; the interaction; a top layer)
+    on a shared state; after the last one state["y"] is the logit
+    ciphertext.  ct_sel: one ciphertext, or the list of them for a selector
+    wider than n slots."""
+    st = {"h": ct_dense}
+    act = getattr(c.spec, "act", None)
+
+    def bottom(lay):
+        st["h"] = _dense_layer(p, keys, lay, st["h"], act)
+
+    def lookup():
+        e = lookup_multi(p, keys, c.emb_chunks, ct_sel) if c.emb is None else linear.matvec(p, keys, c.emb, ct_sel)
+        st["y"] = ckks.add(p, st["h"], e)
+
+    def interaction():
+        z = st["y"]
+        if c.spec.interaction == "dot":
+            z = ckks.add_pt(p, z, c.ones, z.scale)
+            st["y"] = dot_interaction(p, keys, c, z)
+
+    def top(lay):
+        st["y"] = _dense_layer(p, keys, lay, st["y"], act)
+
+    stages = [lambda lay=lay: bottom(lay) for lay in c.bottom] + [lookup, interaction] + \
+        [lambda lay=lay: top(lay) for lay in c.top]
+    return stages, st
+
+
 def infer(p, keys, c: Compiled, ct_dense: ckks.Ct, ct_sel) -> ckks.Ct:
     """ct_sel: one ciphertext, or the list of them for a selector wider than n slots."""
-    h = ct_dense
-    for lay in c.bottom:
-        h = _dense_layer(p, keys, lay, h, getattr(c.spec, "act", None))
-    if c.emb is None:
-        e = lookup_multi(p, keys, c.emb_chunks, ct_sel)
-    else:
-        e = linear.matvec(p, keys, c.emb, ct_sel)
-    z = ckks.add(p, h, e)
-    if c.spec.interaction == "dot":
-        z = ckks.add_pt(p, z, c.ones, z.scale)
-        u = dot_interaction(p, keys, c, z)
-    else:
-        u = z
-    y = u
-    for lay in c.top:
-        y = _dense_layer(p, keys, lay, y, getattr(c.spec, "act", None))
-    return y
+    stages, st = infer_stages(p, keys, c, ct_dense, ct_sel)
+    for f in stages:
+        f()
+    return st["y"]
 
 
 def decrypt_logit(p, sk, ct: ckks.Ct):

@@ -18,7 +18,7 @@ D = min(in_pad, out_pad) extended diagonals
 and, when in_pad > out_pad, the folds: sum_j rot(y, j out_pad) over j <
 in_pad / out_pad, in levels of up to 3 hoisted rotations (fold_plan).
 The result is W x replicated with period out_pad.  BSGS split: n1 =
-min(D, 64), n2 = D / n1 (see bsgs_split); i = g*n1 + b and
+min(D, max(16, D / 8)), n2 = D / n1 (see bsgs_split); i = g*n1 + b and
 diag'_{g,b} = rot(diag_{g n1 + b}, -g n1).  All-zero diagonals are skipped,
 which changes no result (their products are exactly zero).
 """

@@ -86,27 +86,6 @@ Ctx *ctx_or_null(const void *h)
     return hh->kind == KIND_CTX ? (Ctx *)h : nullptr;
 }
 
-template <class F>
-helrm_status guard(Ctx *ctx, F &&f)
-{
-    try {
-        f();
-        return HELRM_OK;
-    } catch (const Error &e) {
-        if (ctx) ctx->last_error = e.msg;
-        if (e.code == HELRM_E_CUDA || e.code == HELRM_E_NOMEM) cudaGetLastError();
-        return e.code;
-    } catch (const std::bad_alloc &) {
-        if (ctx) ctx->last_error = "host allocation failed";
-        return HELRM_E_NOMEM;
-    } catch (const std::exception &e) {
-        if (ctx) ctx->last_error = e.what();
-        return HELRM_E_INVAL;
-    } catch (...) {
-        if (ctx) ctx->last_error = "unknown error";
-        return HELRM_E_INVAL;
-    }
-}
 
 template <class T>
 void set_out(T **out, T *v)
@@ -217,6 +196,28 @@ helrm_status helrm_ctx_profile(helrm_ctx *ctx, int enable)
     });
 }
 
+helrm_status helrm_ctx_profile_records(helrm_ctx *ctx, char *buf, uint64_t len, uint64_t *needed)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        CUDA_CHECK(cudaStreamSynchronize(c->stream));
+        std::string s;
+        char line[256];
+        for (auto &r : c->prof) {
+            float ms = 0;
+            CUDA_CHECK(cudaEventElapsedTime(&ms, r.start, r.stop));
+            snprintf(line, sizeof line, "%s %.6f %.0f\n", r.name, ms, r.bytes);
+            s += line;
+        }
+        if (needed) *needed = s.size() + 1;
+        if (buf && len) {
+            size_t n = std::min<size_t>(len - 1, s.size());
+            std::memcpy(buf, s.data(), n);
+            buf[n] = 0;
+        }
+    });
+}
+
 helrm_status helrm_ctx_profile_report(helrm_ctx *ctx, char *buf, uint64_t len, uint64_t *needed)
 {
     return guard(ctx_or_null(ctx), [&] {
@@ -248,6 +249,16 @@ helrm_status helrm_ctx_profile_report(helrm_ctx *ctx, char *buf, uint64_t len, u
             std::memcpy(buf, s.data(), n);
             buf[n] = 0;
         }
+    });
+}
+
+helrm_status helrm_alu_peak(helrm_ctx *ctx, int32_t kind, uint32_t blocks_per_sm, uint32_t iters,
+                            double *ops_per_s)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        HCHECK(ops_per_s, HELRM_E_INVAL, "ops_per_s is NULL");
+        *ops_per_s = k::alu_peak(c, kind, (int)blocks_per_sm, (int)iters);
     });
 }
 

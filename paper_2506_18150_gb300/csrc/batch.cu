@@ -16,7 +16,8 @@
 //    instead of once per query (the weight diagonals are the same for every
 //    client; the keys are not);
 //  * the per-query key tables of every matrix are built once, when the batch
-//    is created, so a batch can be replayed as a CUDA graph (graph.cu).
+//    is created, so a batch can be replayed as a CUDA graph
+//    (model_infer_batch_graph, below).
 #include <cmath>
 
 #include "model.cuh"

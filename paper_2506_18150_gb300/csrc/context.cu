@@ -488,6 +488,7 @@ Ctx *ctx_create(const helrm_params *p, int device, void *stream)
     u64 zero = 0;
     upload(c.get(), c->d_err, &zero, 8);
     k::ntt_autotune(c.get());   // launch shapes for this ring degree and GPU
+    noalloc_setup(c.get());
     return c.release();
 }
 

@@ -13,8 +13,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <exception>
 #include <map>
 #include <memory>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -272,6 +274,38 @@ struct Ctx : Handle {
     void check_device_errors();
 };
 
+// Runs f, turning every exception into a status (and the context's last
+// error message); after a CUDA or out-of-memory error the runtime's pending
+// error is cleared so that the next call does not report it again.  Every
+// entry point of the ABI is wrapped in it.
+template <class F>
+helrm_status guard(Ctx *ctx, F &&f)
+{
+    try {
+        f();
+        return HELRM_OK;
+    } catch (const Error &e) {
+        if (ctx) ctx->last_error = e.msg;
+        if (e.code == HELRM_E_CUDA || e.code == HELRM_E_NOMEM) cudaGetLastError();
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        if (ctx) ctx->last_error = "host allocation failed";
+        return HELRM_E_NOMEM;
+    } catch (const std::exception &e) {
+        if (ctx) ctx->last_error = e.what();
+        return HELRM_E_INVAL;
+    } catch (...) {
+        if (ctx) ctx->last_error = "unknown error";
+        return HELRM_E_INVAL;
+    }
+}
+
+// The allocation-free rescale's set-up for the context's device (noalloc.cu):
+// looks up the device address of its static scratch array and loads its
+// kernels, so that the call itself never loads a module.  Called once per
+// context at creation.
+void noalloc_setup(Ctx *c);
+
 // Fork / join of an independent branch of work.  The constructor records a
 // fork point on the context's stream; run(f) enqueues f's work on the side
 // stream of that stream (after the fork point, allocating from the side
@@ -470,6 +504,10 @@ void ntt_map_noheap(Ctx *c, u64 *data, int n_limbs, LimbMap map, bool inverse);
 // time every candidate NTT launch shape per limb-count bucket on scratch limbs
 // and keep the fastest (ntt.cu); the arithmetic is the same for every shape
 void ntt_autotune(Ctx *c);
+// register-resident throughput of the NTT's and the inner products' arithmetic
+// (kind 0: forward butterflies, 1: inverse butterflies, 2: 128-bit
+// multiply-accumulates, 3: Shoup products), in operations per second
+double alu_peak(Ctx *c, int kind, int blocks_per_sm, int iters);
 // transform an arbitrary list of limbs (offset in limbs from base, prime id) in one launch pair
 void ntt_list(Ctx *c, u64 *base, const std::vector<std::pair<u32, int>> &limbs, bool inverse);
 void copy(Ctx *c, u64 *dst, const u64 *src, size_t n_words);

@@ -7,8 +7,8 @@
 // buffers it was handed.  helrm_rescale_noalloc serves them: the caller passes
 // the input and output buffers, and the one scratch buffer the operation
 // needs (the inverse-NTT copy of the dropped limb of each polynomial) is the
-// file-scope device array below, loaded once with the library and held by
-// every GPU that loads it until the process exits.
+// file-scope device array below.  Creating a context on a device loads it
+// there (noalloc_setup); the device then holds it until the process exits.
 //
 // The arithmetic is that of helrm_rescale: out_i = (x_i - r) * q_l^-1 mod q_i
 // with r the centred remainder of the dropped limb, which is round(x / q_l).
@@ -70,24 +70,17 @@ __global__ void k_na_finish(u64 *__restrict__ out, const u64 *__restrict__ in, i
 }
 
 // Per-device address of the scratch array.  Host code cannot use the array's
-// name as a device address, so the first call on each device looks it up.
+// name as a device address; noalloc_setup looks it up when a context is
+// created on the device (where allocating is allowed: under lazy module
+// loading the lookup is what loads this file's module, and with it the
+// array), and the entry point only reads the table.
 std::mutex g_mu;
 u64 *g_scratch_ptr[64] = {nullptr};
 
-u64 *scratch_for(int device)
+u64 *scratch_of(int device)
 {
-    HCHECK(device >= 0 && device < 64, HELRM_E_INVAL, "device index out of range");
+    if (device < 0 || device >= 64) return nullptr;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[device]) {
-        int prev = 0;
-        CUDA_CHECK(cudaGetDevice(&prev));
-        CUDA_CHECK(cudaSetDevice(device));
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        cudaSetDevice(prev);
-        if (e != cudaSuccess) fail(HELRM_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_scratch_ptr[device] = (u64 *)p;
-    }
     return g_scratch_ptr[device];
 }
 
@@ -104,6 +97,26 @@ u64 h_powmod(u64 b, u64 e, u64 m)
 }
 
 }  // namespace
+
+void noalloc_setup(Ctx *c)
+{
+    HCHECK(c->device >= 0 && c->device < 64, HELRM_E_INVAL, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_scratch_ptr[c->device]) return;
+    int prev = 0;
+    CUDA_CHECK(cudaGetDevice(&prev));
+    CUDA_CHECK(cudaSetDevice(c->device));
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    // load the two kernels too, so that their first launch loads nothing
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_na_spread);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_na_finish);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) fail(HELRM_E_CUDA, std::string("noalloc set-up: ") + cudaGetErrorString(e));
+    g_scratch_ptr[c->device] = (u64 *)p;
+}
+
 }  // namespace helrm
 
 using namespace helrm;
@@ -113,18 +126,28 @@ extern "C" helrm_status helrm_rescale_noalloc(helrm_ctx *ctx, const uint64_t *d_
 {
     Ctx *c = (ctx && ((const Handle *)ctx)->kind == KIND_CTX) ? (Ctx *)ctx : nullptr;
     if (!c) return HELRM_E_INVAL;
-    const bool prof = c->prof_on;
-    c->prof_on = false;   // event bookkeeping would create driver objects
-    helrm_status st = HELRM_OK;
-    try {
+    // per-kernel timing records events, which creates driver objects: off for this call
+    struct ProfOff {
+        Ctx *c;
+        bool was;
+        explicit ProfOff(Ctx *cc) : c(cc), was(cc->prof_on) { c->prof_on = false; }
+        ~ProfOff() { c->prof_on = was; }
+    } prof_off(c);
+    return guard(c, [&] {
         HCHECK(d_in && d_out, HELRM_E_INVAL, "NULL buffer");
         HCHECK(level >= 1 && level <= c->L, HELRM_E_LEVEL, "level must be in [1, L]");
         HCHECK(n_polys >= 1, HELRM_E_INVAL, "n_polys must be at least 1");
         HCHECK((size_t)n_polys * c->N <= NOALLOC_SCRATCH_WORDS, HELRM_E_INVAL,
                "n_polys * N exceeds the static scratch of 2 * 65536 words");
         HCHECK(level <= MAXQ, HELRM_E_PARAM, "too many primes");
-        u64 *scratch = scratch_for(c->device);
         const int N = c->N, l = level;
+        {   // the kernels take both buffers as __restrict__: they must not overlap
+            const uintptr_t a0 = (uintptr_t)d_in, a1 = a0 + (uintptr_t)n_polys * (l + 1) * N * 8;
+            const uintptr_t b0 = (uintptr_t)d_out, b1 = b0 + (uintptr_t)n_polys * l * N * 8;
+            HCHECK(a1 <= b0 || b1 <= a0, HELRM_E_INVAL, "d_in and d_out overlap");
+        }
+        u64 *scratch = scratch_of(c->device);
+        HCHECK(scratch, HELRM_E_CUDA, "the scratch array of this device was not set up");
         RescaleConsts rc;
         rc.ql = c->primes[l];
         for (int i = 0; i < l; i++) {
@@ -146,13 +169,5 @@ extern "C" helrm_status helrm_rescale_noalloc(helrm_ctx *ctx, const uint64_t *d_
         launch(c, k_na_finish, grid, 256, 0, d_out, d_in, l, c->logN, (int)n_polys, rc);
         CUDA_CHECK(cudaGetLastError());
         c->launches += 2;
-    } catch (const Error &e) {
-        c->last_error = e.msg;
-        st = e.code;
-    } catch (...) {
-        c->last_error = "unknown error";
-        st = HELRM_E_INVAL;
-    }
-    c->prof_on = prof;
-    return st;
+    });
 }

@@ -424,9 +424,110 @@ void run_list(Ctx *c, const LimbList &ll, bool inverse, const Ep &ep_scal, const
     CUDA_CHECK(cudaGetLastError());
 }
 
+// Register-resident throughput of the transform's arithmetic (the integer
+// ceiling the NTT is measured against).  Every thread keeps 8 residues and 7
+// twiddles in registers and repeats, `iters` times, one of:
+//  PEAK_CT    a forward radix-8 round: 12 lazy Cooley-Tukey butterflies
+//             (bfly_ct, the code the forward passes run);
+//  PEAK_GS    an inverse radix-8 round: 12 Gentleman-Sande butterflies (bfly_gs);
+//  PEAK_MAC   8 carry-chained 64 x 64 -> 128-bit multiply-accumulates
+//             (Acc128::mac, the key and diagonal inner products);
+//  PEAK_SHOUP 8 fully reduced Shoup products (shoup_mul).
+// Nothing is loaded or stored inside the loop; the result is written once so
+// the work cannot be dropped.
+enum PeakKind { PEAK_CT = 0, PEAK_GS = 1, PEAK_MAC = 2, PEAK_SHOUP = 3 };
+template <int KIND>
+__global__ void __launch_bounds__(256) k_alu_peak(u64 *__restrict__ out, const PrimeInfo *__restrict__ pinfo,
+                                                  const ulonglong2 *__restrict__ tw, int pid, int logN, int iters)
+{
+    const u64 q = pinfo[pid].q, q2 = 2 * q;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const ulonglong2 *twp = tw + ((size_t)pid << logN);
+    u64 v[8];
+    ulonglong2 w[7];
+#pragma unroll
+    for (int j = 0; j < 7; j++) w[j] = twp[1 + ((t * 7 + j) & 255)];
+#pragma unroll
+    for (int k = 0; k < 8; k++) v[k] = w[k % 7].x ^ (u64)(t * 8 + k);
+#pragma unroll
+    for (int k = 0; k < 8; k++) v[k] = v[k] >= q ? v[k] - q : v[k];
+    if (KIND == PEAK_MAC) {
+        Acc128 acc[8];
+        for (int it = 0; it < iters; it++) {
+#pragma unroll
+            for (int k = 0; k < 8; k++) acc[k].mac(v[k], w[k % 7].x, q);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = acc[k].lo ^ acc[k].hi;
+    } else {
+        for (int it = 0; it < iters; it++) {
+            if (KIND == PEAK_CT) {
+#pragma unroll
+                for (int k = 0; k < 4; k++) bfly_ct(v[k], v[k + 4], w[0].x, w[0].y, q, q2);
+#pragma unroll
+                for (int k = 0; k < 8; k += 4) {
+                    bfly_ct(v[k], v[k + 2], w[1 + k / 4].x, w[1 + k / 4].y, q, q2);
+                    bfly_ct(v[k + 1], v[k + 3], w[1 + k / 4].x, w[1 + k / 4].y, q, q2);
+                }
+#pragma unroll
+                for (int k = 0; k < 8; k += 2) bfly_ct(v[k], v[k + 1], w[3 + k / 2].x, w[3 + k / 2].y, q, q2);
+            } else if (KIND == PEAK_GS) {
+#pragma unroll
+                for (int k = 0; k < 8; k += 2) bfly_gs(v[k], v[k + 1], w[3 + k / 2].x, w[3 + k / 2].y, q, q2);
+#pragma unroll
+                for (int k = 0; k < 8; k += 4) {
+                    bfly_gs(v[k], v[k + 2], w[1 + k / 4].x, w[1 + k / 4].y, q, q2);
+                    bfly_gs(v[k + 1], v[k + 3], w[1 + k / 4].x, w[1 + k / 4].y, q, q2);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k++) bfly_gs(v[k], v[k + 4], w[0].x, w[0].y, q, q2);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; k++) v[k] = shoup_mul(v[k], w[k % 7].x, w[k % 7].y, q);
+            }
+        }
+    }
+    u64 r = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) r ^= v[k];
+    out[t] = r;
+}
+
 }  // namespace
 
 namespace k {
+
+double alu_peak(Ctx *c, int kind, int blocks_per_sm, int iters)
+{
+    HCHECK(kind >= PEAK_CT && kind <= PEAK_SHOUP, HELRM_E_INVAL, "unknown peak kind");
+    HCHECK(blocks_per_sm >= 1 && blocks_per_sm <= 32 && iters >= 1, HELRM_E_INVAL, "bad peak launch shape");
+    const int blocks = c->n_sms * blocks_per_sm, threads = 256;
+    DevMem out(c, (size_t)blocks * threads * 8);
+    const int pid = c->nP() > 1 ? 1 : 0;
+    const ulonglong2 *tw = c->d_tw_fwd.as<ulonglong2>();
+    auto run = [&](int n) {
+        void (*kern)(u64 *, const PrimeInfo *, const ulonglong2 *, int, int, int) =
+            kind == PEAK_CT ? k_alu_peak<PEAK_CT> : kind == PEAK_GS ? k_alu_peak<PEAK_GS>
+                                                  : kind == PEAK_MAC ? k_alu_peak<PEAK_MAC> : k_alu_peak<PEAK_SHOUP>;
+        kern<<<blocks, threads, 0, c->stream>>>(out.u(), c->d_pinfo.as<PrimeInfo>(), tw, pid, c->logN, n);
+        CUDA_CHECK(cudaGetLastError());
+    };
+    run(std::max(1, iters / 8));   // warm-up (clocks, instruction cache)
+    cudaEvent_t e0, e1;
+    CUDA_CHECK(cudaEventCreate(&e0));
+    CUDA_CHECK(cudaEventCreate(&e1));
+    CUDA_CHECK(cudaEventRecord(e0, c->stream));
+    run(iters);
+    CUDA_CHECK(cudaEventRecord(e1, c->stream));
+    CUDA_CHECK(cudaEventSynchronize(e1));
+    float ms = 0;
+    CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->launches += 2;
+    const double per_iter = (kind == PEAK_CT || kind == PEAK_GS) ? 12.0 : 8.0;
+    return (double)blocks * threads * iters * per_iter / (ms / 1000.0);
+}
 
 // rs (forward only, may be null): the launch is a merged ModDown + rescale
 static void ntt_run_impl(Ctx *c, const std::vector<NttLimb> &limbs, bool inverse, const Ep &ep,

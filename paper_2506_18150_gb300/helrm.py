@@ -71,6 +71,7 @@ _SIGS = {
     "helrm_ctx_synchronize": [_vp],
     "helrm_ctx_launch_count": [_vp, _u64p],
     "helrm_ntt": [_vp, _vp, C.c_uint32, C.c_uint32, C.c_int],
+    "helrm_alu_peak": [_vp, C.c_int32, C.c_uint32, C.c_uint32, _dp],
     "helrm_keygen": [_vp, C.c_uint64, _i32p, C.c_uint32, _pp, _pp],
     "helrm_evk_add_rotations": [_vp, _vp, _vp, _i32p, C.c_uint32],
     "helrm_model_keygen": [_vp, _vp, C.c_uint64, _pp, _pp],
@@ -131,6 +132,7 @@ _SIGS = {
     "helrm_ctx_ntt_tuning": [_vp, _u32p],
     "helrm_ctx_wait_selftest": [_vp, C.c_uint32],
     "helrm_ctx_profile_report": [_vp, C.c_char_p, C.c_uint64, _u64p],
+    "helrm_ctx_profile_records": [_vp, C.c_char_p, C.c_uint64, _u64p],
 }
 
 
@@ -308,6 +310,12 @@ def helrm_ctx_launch_count(ctx) -> int:
 
 def helrm_ntt(ctx, d_ptr: int, n_limbs: int, first_prime: int, inverse: bool):
     _check(ctx, lib().helrm_ntt(ctx.ptr, C.c_void_p(d_ptr), n_limbs, first_prime, int(inverse)))
+
+
+def helrm_alu_peak(ctx, kind: int, blocks_per_sm: int = 4, iters: int = 4096) -> float:
+    out = C.c_double()
+    _check(ctx, lib().helrm_alu_peak(ctx.ptr, kind, blocks_per_sm, iters, C.byref(out)))
+    return out.value
 
 
 # ------------------------------------------------------------------ keys / pts / cts
@@ -726,6 +734,19 @@ def helrm_ctx_profile_report(ctx):
     for line in buf.value.decode().splitlines():
         name, n, ms, b = line.split()
         out[name] = (int(n), float(ms), float(b))
+    return out
+
+
+def helrm_ctx_profile_records(ctx):
+    """[(kernel name, ms, algorithmic_bytes)] per recorded launch, in order"""
+    need = C.c_uint64(0)
+    _check(ctx, lib().helrm_ctx_profile_records(ctx.ptr, None, 0, C.byref(need)))
+    buf = C.create_string_buffer(need.value + 1)
+    _check(ctx, lib().helrm_ctx_profile_records(ctx.ptr, buf, need.value + 1, None))
+    out = []
+    for line in buf.value.decode().splitlines():
+        name, ms, b = line.split()
+        out.append((name, float(ms), float(b)))
     return out
 
 

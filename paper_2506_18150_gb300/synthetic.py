@@ -313,3 +313,33 @@ def serving_trace(rate: float, count: int, n_uci_clients: int, n_criteo_clients:
     client = np.where(uci, rng.integers(0, n_uci_clients, count),
                       n_uci_clients + rng.integers(0, n_criteo_clients, count))
     return arrival, client.astype(np.uint32)
+
+
+# --------------------------------------------------------------------------
+# Platform-independent integer inputs (full-size parity fixtures)
+# --------------------------------------------------------------------------
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+
+
+def _splitmix64(x: np.ndarray) -> np.ndarray:
+    """The SplitMix64 output function (Steele, Lea, Flood 2014) on uint64
+    arrays, wrapping arithmetic."""
+    with np.errstate(over="ignore"):
+        z = x.copy()
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def int_poly(seed: int, index: int, n: int, bound: int = 1 << 20) -> np.ndarray:
+    """n signed integers in [-bound, bound], a pure function of (seed, index):
+    SplitMix64 of the counters (seed, index, j), reduced mod 2 bound + 1.
+    Integer-only, so it gives the same values on every machine and numpy
+    version (the FP64 encoder does not: its last-bit rounding can differ)."""
+    with np.errstate(over="ignore"):
+        base = _splitmix64(np.array([(seed & (2**64 - 1)) ^ 0x5DEECE66D], dtype=np.uint64))[0]
+        base = _splitmix64(np.array([base ^ np.uint64(index & (2**64 - 1))], dtype=np.uint64))[0]
+        ctr = base + (np.arange(1, n + 1, dtype=np.uint64) * _GOLDEN)
+    z = _splitmix64(ctr)
+    m = np.uint64(2 * bound + 1)
+    return (z % m).astype(np.int64) - bound

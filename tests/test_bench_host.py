@@ -1,8 +1,7 @@
 """Host logic of bench.py, on CPU: the roofline arithmetic (the NTT against
-its integer-issue ceiling, any other kernel against the HBM peak), the guard
-that reports the measured NTT traffic only while the sources it was measured
-on are unchanged, and the parsing of nvidia-smi clock samples with their
-throttle reasons."""
+its measured integer ceiling, any other kernel against the HBM peak), the
+parsing of nvidia-smi clock samples with their throttle reasons, and the
+oracle arm's accounting of stage samples."""
 import os
 import sys
 
@@ -12,35 +11,30 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 
-def test_roofline_ntt_against_issue_ceiling():
+def test_roofline_ntt_against_measured_ceiling():
     # 89 transforms moving 1190 MB (algorithmic) in 2.29 ms, per step
     rep = {"ntt": (89, 2.29, 1190e6), "bsgs_fused": (5, 1.27, 3.8e9)}
-    r = bench.roofline(rep, 1, 16, 2070.0, 6787.6, "measured", "criteo")
+    alu = {"fwd_butterfly": 800.0, "inv_butterfly": 800.0, "mac128": 3600.0, "ntt_butterfly": 800.0}
+    r = bench.roofline(rep, 1, 16, 6787.6, "measured", alu)
     assert r["bound"] == "alu" and r["kernel"] == "ntt" and r["unit"] == "Gbutterfly/s"
     # 16 N bytes per limb <-> (N/2) log2 N butterflies: bytes * 16 / 32 butterflies
     assert abs(r["achieved"] - 1190e6 * 16 / 32 / 2.29e-3 / 1e9) < 1e-9
-    assert abs(r["peak"] - 152 * 4 * 32 * 2070e6 / 23 / 1e9) < 1e-9
-    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
-    assert r["traffic"] is None                       # measured for the UCI step only
+    assert r["peak"] == 800.0 and abs(r["frac"] - r["achieved"] / 800.0) < 1e-12
+    assert r["peak_source"].startswith("measured")
+    assert abs(r["hbm_frac"] - 1190e6 / 2.29e-3 / 1e9 / 6787.6) < 1e-12
     assert r["launches_per_step"] == 89 and abs(r["share_of_kernel_time"] - 2.29 / 3.56) < 1e-12
+    # without a measured ceiling there is no fraction
+    r = bench.roofline(rep, 1, 16, 6787.6, "measured", None)
+    assert r["peak"] is None and r["frac"] is None
 
 
 def test_roofline_hbm_bound_kernel():
     rep = {"ntt": (10, 0.5, 100e6), "bsgs_fused": (5, 1.0, 3.4e9)}
-    r = bench.roofline(rep, 2, 16, 2070.0, 6800.0, "fallback", "uci")
+    r = bench.roofline(rep, 2, 16, 6800.0, "fallback")
     assert r["bound"] == "hbm" and r["kernel"] == "bsgs_fused" and r["unit"] == "GB/s"
     assert abs(r["achieved"] - 3.4e9 / 1e-3 / 1e9) < 1e-6 and abs(r["frac"] - 3400.0 / 6800.0) < 1e-12
     assert r["traffic"] is None and r["launches_per_step"] == 2.5
-
-
-def test_ntt_traffic_follows_the_measured_sources(monkeypatch):
-    assert bench.ntt_traffic("uci") == bench.NTT_TRAFFIC["bytes_per_launch"]
-    assert bench.ntt_traffic("criteo") is None
-    changed = dict(bench.NTT_TRAFFIC, sha256=dict(bench.NTT_TRAFFIC["sha256"], **{"ntt.cu": "0" * 64}))
-    monkeypatch.setattr(bench, "NTT_TRAFFIC", changed)
-    assert bench.ntt_traffic("uci") is None           # the kernel changed since the capture
-    r = bench.roofline({"ntt": (89, 2.29, 1190e6)}, 1, 16, 2070.0, 6787.6, "measured", "uci")
-    assert r["traffic"] is None
+    assert abs(r["kernels"]["ntt"]["hbm_frac"] - 100e6 / 0.5e-3 / 1e9 / 6800.0) < 1e-12
 
 
 def test_clock_samples_and_reasons():
@@ -57,3 +51,18 @@ def test_clock_samples_and_reasons():
     assert s.stop()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     s.lines = []
     assert s.stop()["samples"] == 0
+
+
+def test_stage_records_give_query_time():
+    from oracle import bench_sample
+    recs = [(0, 0, 1.0), (0, 1, 3.0), (0, 2, 2.0), (1, 0, 1.2), (1, 1, 2.8)]
+    assert abs(bench_sample.query_time(recs, 3) - (1.1 + 2.9 + 2.0)) < 1e-12
+    for k, v in bench_sample.STAGE_SHARES.items():
+        assert abs(sum(v) - 1.0) < 2e-3, k
+
+
+def test_parse_defaults():
+    a = bench.parse([])
+    assert a.workload == "criteo" and a.gpus == 1 and a.steps == 100 and a.warmup == 3
+    a = bench.parse(["--impl", "reference", "--steps", "20", "--warmup", "5"])
+    assert a.steps == 20 and a.warmup == 5

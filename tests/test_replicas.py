@@ -69,3 +69,29 @@ def test_serving_trace_is_poisson_with_the_stated_mix():
     assert len(np.unique(cl[uci])) == 32 and len(np.unique(cl[~uci])) == 8
     a2, c2 = syn.serving_trace(50.0, 20_000, 32, 8, 0.8, seed=3)
     assert np.array_equal(arr, a2) and np.array_equal(cl, c2)      # seeded
+
+
+def test_spawned_replicas_report_the_whole_job(tmp_path):
+    """bench.py --gpus N without torchrun starts N ranks itself
+    (bench.spawn_replicas); here two gloo ranks of a stub step on CPU."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    out = tmp_path / "out.txt"
+    with open(out, "w") as f:
+        rc = bench.spawn_replicas(2, os.path.join(ROOT, "tests", "replica_stub.py"), ["--gpus", "2"],
+                                  env=dict(os.environ, OMP_NUM_THREADS="1"), stdout=f)
+    assert rc == 0
+    lines = [ln for ln in open(out).read().splitlines() if ln.startswith("{")]
+    assert len(lines) == 1                       # rank 0 alone prints
+    d = json.loads(lines[0])
+    assert d["n_gpus"] == 2 and d["ms"] == 250.0 and d["value"] == pytest.approx(2 * 40 / 0.250)
+    assert d["argv"] == ["--gpus", "2"]
+
+
+def test_bench_rejects_a_mismatched_world():
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2"], cwd=ROOT,
+                       env=dict(os.environ, WORLD_SIZE="4", RANK="0", LOCAL_RANK="0"), capture_output=True,
+                       text=True, timeout=120)
+    assert r.returncode != 0 and "does not match WORLD_SIZE" in r.stderr

@@ -463,8 +463,8 @@ helrm_status helrm_infer_batch_e2e(helrm_ctx *ctx, const helrm_batch *b, const h
 helrm_status helrm_server_create(helrm_ctx *ctx, uint32_t n_slots, uint32_t max_batch, uint64_t mem_budget,
                                  helrm_server **out);
 /* Register a client: the model its queries use and its evaluation keys
- * (both must outlive the server).  *client_id receives its index.  The
- * model's selector must fit one ciphertext (n_sel = 1), else HELRM_E_INVAL. */
+ * (both must outlive the server).  *client_id receives its index.  Any model
+ * is accepted, including one whose selector spans several ciphertexts. */
 helrm_status helrm_server_add_client(helrm_ctx *ctx, helrm_server *s, const helrm_model *m, const helrm_evk *evk,
                                      uint32_t *client_id);
 typedef struct {
@@ -475,8 +475,11 @@ typedef struct {
     double mean_batch;
 } helrm_serve_stats;
 /* Replay n timed requests through the loop.  Request r arrives at
- * arrival_s[r] seconds (sorted ascending) from client[r] with its two query
- * ciphertexts (helrm_encrypt_query, already on the device).  Each pass of
+ * arrival_s[r] seconds (sorted ascending) from client[r] with its query
+ * ciphertexts (helrm_encrypt_query, already on the device): ct_dense[r], and
+ * in ct_sel the n_sel selector ciphertexts of the client's model (one unless
+ * the selector is wider than the slots), request after request, so ct_sel
+ * holds the sum of the requests' n_sel.  Each pass of
  * the loop admits the requests that have arrived, launches a batch on every
  * free slot that the memory budget allows (oldest pending request first,
  * with more pending requests of the same model), and polls the slots for

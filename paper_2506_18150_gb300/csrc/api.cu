@@ -52,6 +52,7 @@ bool batch_uses_graph(const Batch *b);
 struct Server;
 Server *server_create(Ctx *c, int n_slots, int max_batch, u64 budget);
 u32 server_add_client(Server *s, const Model *m, const EvalKey *evk);
+u32 server_sel_count(const Server *s, u32 n, const u32 *client);
 void server_run(Server *s, u32 n, const double *arrival, const u32 *client, const Ciphertext *const *ct_dense,
                 const Ciphertext *const *ct_sel, Ciphertext **out, double *latency_ms, helrm_serve_stats *st);
 }  // namespace helrm
@@ -944,11 +945,10 @@ helrm_status helrm_server_run(helrm_ctx *ctx, helrm_server *s, uint32_t n, const
         C(ctx);
         HCHECK(arrival_s && client && ct_dense && ct_sel && logits_out && latency_ms_out, HELRM_E_INVAL,
                "NULL argument");
-        std::vector<const Ciphertext *> d(n), sl(n);
-        for (u32 r = 0; r < n; r++) {
-            d[r] = CT(ct_dense[r]);
-            sl[r] = CT(ct_sel[r]);
-        }
+        const u32 n_sel = server_sel_count(SRV(s), n, client);
+        std::vector<const Ciphertext *> d(n), sl(n_sel);
+        for (u32 r = 0; r < n; r++) d[r] = CT(ct_dense[r]);
+        for (u32 k = 0; k < n_sel; k++) sl[k] = CT(ct_sel[k]);
         server_run(SRV(s), n, arrival_s, client, d.data(), sl.data(), (Ciphertext **)logits_out, latency_ms_out,
                    stats);
     });

@@ -15,6 +15,8 @@
 //    back its encrypted logit.
 // A batch of one request runs the one-query path (helrm_infer), so a server
 // with one slot and max_batch = 1 is the plain one-request-at-a-time path.
+// A model whose selector is wider than the slots brings n_sel selector
+// ciphertexts per request; its batches carry them query by query.
 //
 // Time is the host's steady clock.  When nothing is pending or in flight the
 // loop skips ahead to the next arrival instead of sleeping (the idle GPU has
@@ -81,9 +83,22 @@ Server *server_create(Ctx *c, int n_slots, int max_batch, u64 budget)
 
 u32 server_add_client(Server *s, const Model *m, const EvalKey *evk)
 {
-    HCHECK(m->n_sel() == 1, HELRM_E_INVAL, "the server takes models whose selector fits one ciphertext");
     s->clients.push_back({m, evk});
     return (u32)s->clients.size() - 1;
+}
+
+// Selector ciphertexts of a trace: request r brings the n_sel of its
+// client's model (one unless the selector is wider than the slots), request
+// after request.  Checks the client ids; returns the total.
+u32 server_sel_count(const Server *s, u32 n, const u32 *client)
+{
+    u64 total = 0;
+    for (u32 r = 0; r < n; r++) {
+        HCHECK(client[r] < s->clients.size(), HELRM_E_INVAL, "request names an unknown client");
+        total += (u64)s->clients[client[r]].m->n_sel();
+    }
+    HCHECK(total < (1ull << 31), HELRM_E_INVAL, "too many selector ciphertexts");
+    return (u32)total;
 }
 
 namespace {
@@ -107,10 +122,15 @@ void server_run(Server *s, u32 n, const double *arrival, const u32 *client, cons
                 const Ciphertext *const *ct_sel, Ciphertext **out, double *latency_ms, helrm_serve_stats *st)
 {
     Ctx *c = s->ctx;
+    server_sel_count(s, n, client);
+    std::vector<u32> sel_off(n + 1, 0);   // request r's selectors: ct_sel[sel_off[r] .. sel_off[r + 1])
     for (u32 r = 0; r < n; r++) {
-        HCHECK(client[r] < s->clients.size(), HELRM_E_INVAL, "request names an unknown client");
         HCHECK(r == 0 || arrival[r] >= arrival[r - 1], HELRM_E_INVAL, "arrivals must be sorted");
+        sel_off[r + 1] = sel_off[r] + (u32)s->clients[client[r]].m->n_sel();
     }
+    auto sels = [&](u32 r) {
+        return std::vector<const Ciphertext *>(ct_sel + sel_off[r], ct_sel + sel_off[r + 1]);
+    };
     CUDA_CHECK(cudaStreamSynchronize(c->stream));   // the requests' ciphertexts are ready
     const cudaStream_t home = c->stream;
     std::deque<u32> pending;
@@ -189,14 +209,14 @@ void server_run(Server *s, u32 n, const double *arrival, const u32 *client, cons
                 busy[k] = 1;   // from here on the slot owns whatever was launched
                 if (take.size() == 1) {
                     const Server::Client &cl = s->clients[client[take[0]]];
-                    f.out.push_back(model_infer(c, cl.evk, m, ct_dense[take[0]], {ct_sel[take[0]]}));
+                    f.out.push_back(model_infer(c, cl.evk, m, ct_dense[take[0]], sels(take[0])));
                 } else {
                     std::vector<const EvalKey *> ev;
                     std::vector<const Ciphertext *> d, sl;
                     for (u32 r : take) {
                         ev.push_back(s->clients[client[r]].evk);
                         d.push_back(ct_dense[r]);
-                        sl.push_back(ct_sel[r]);
+                        for (const Ciphertext *x : sels(r)) sl.push_back(x);
                     }
                     f.batch = batch_create(c, m, ev);
                     f.out = model_infer_batch(c, f.batch, d, sl);

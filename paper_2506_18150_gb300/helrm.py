@@ -689,8 +689,11 @@ def helrm_server_add_client(ctx, server, m, evk) -> int:
 
 
 def helrm_server_run(ctx, server, arrival_s, clients, cts_dense, cts_sel):
-    """Replay a trace; returns (logit ciphertexts, latencies in ms, stats dict)."""
+    """Replay a trace; returns (logit ciphertexts, latencies in ms, stats dict).
+    cts_sel[r]: request r's selector handle, or the list of them when its
+    model's selector spans several ciphertexts (flattened request by request)."""
     n = len(arrival_s)
+    cts_sel = [x for s in cts_sel for x in (s if isinstance(s, (list, tuple)) else [s])]
     arr, ap = _f64(arrival_s)
     cl = np.ascontiguousarray(clients, dtype=np.uint32)
     outs = (C.c_void_p * n)()

@@ -104,9 +104,6 @@ def test_wide_dlrm_with_two_selector_ciphertexts():
     with pytest.raises(H.HelrmError) as e:      # one selector ciphertext is not the whole query
         H.helrm_infer(ctx, evk, model, cts[0][0], cts[0][1][0])
     assert e.value.name == "HELRM_E_INVAL"
-    srv = H.helrm_server_create(ctx, 1, 1, 0)
-    with pytest.raises(H.HelrmError):
-        H.helrm_server_add_client(ctx, srv, model, evk)
 
     # the oracle's integer plaintexts and the same seeds: bit-exact
     H.helrm_model_import_plaintexts(ctx, model, np.stack([np.asarray(x, dtype=np.int64) for x in c.plaintexts()]))

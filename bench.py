@@ -37,6 +37,8 @@ The default line also carries, each timed on the same GPU in the same run:
                     (uci_silu: every activation a degree-6 SiLU polynomial).
 --workload batched  config4 alone, with more steps.
 --workload served   the request loop at every rate of --rates, 32 + 8 clients.
+--workload tiny     config 1: one 1024 x 16 table in base 32 at N = 2^13, one
+                    encrypted lookup per step (lookups/s).
 Multi-GPU: replicas (each rank its own clients and queries, no collective);
 value = all ranks' inferences / the slowest rank's time.  Without torchrun,
 --gpus N > 1 starts N ranks itself.
@@ -70,7 +72,8 @@ def parse(argv=None):
                          "and batched)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="criteo", choices=["criteo", "uci", "uci_silu", "batched", "served"])
+    ap.add_argument("--workload", default="criteo",
+                    choices=["criteo", "uci", "uci_silu", "batched", "served", "tiny"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="one-query line only (no uci/batched/config4/served keys)")
     ap.add_argument("--requests", type=int, default=1000, help="served: requests per arrival rate")
@@ -79,7 +82,8 @@ def parse(argv=None):
     ap.add_argument("--max-batch", type=int, default=8, help="served: requests per batch of the batching server")
     args = ap.parse_args(argv)
     if args.steps is None:
-        args.steps = 100 if args.impl == "ours" and args.workload in ONE_QUERY else 20
+        args.steps = {"tiny": 1000}.get(args.workload, 100) if args.impl == "ours" and \
+            args.workload in ONE_QUERY + ("tiny",) else 20
     return args
 
 
@@ -188,7 +192,32 @@ def alu_peaks(H, ctx):
     return out
 
 
-def roofline(rep, n_steps, log_n, peak_hbm, hbm_src, alu=None):
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per NTT launch (one
+# transform, both passes) over the one-query Criteo-shaped step, from one ncu
+# capture of every NTT pass of a step with warm caches (--cache-control none,
+# profiles/ntt_traffic_criteo_dlrm_n16.md), against 29.77 MB of algorithmic
+# bytes per transform.  It holds for the sources it was taken on: reported
+# while their SHA-256 still matches, null otherwise.
+NTT_TRAFFIC = {"workload": "criteo", "bytes_per_launch": 32.98e6, "algorithmic_per_launch": 29.77e6,
+               "sha256": {"ntt.cu": "ac1d8a5ff6399370faf43c4939b22c9bdfa8e14065ce3c4cc2d3c13099735ae4",
+                          "core.cuh": "5e59949639329632222f328193d56a3269e2316f01cc4fc002d8043ecb3a2cb7"}}
+
+
+def ntt_traffic(workload):
+    import hashlib
+    if workload != NTT_TRAFFIC["workload"]:
+        return None
+    for name, digest in NTT_TRAFFIC["sha256"].items():
+        try:
+            with open(os.path.join(ROOT, "paper_2506_18150_gb300", "csrc", name), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != digest:
+                    return None
+        except OSError:
+            return None
+    return NTT_TRAFFIC["bytes_per_launch"]
+
+
+def roofline(rep, n_steps, log_n, peak_hbm, hbm_src, alu=None, workload=None):
     """Dominant kernel (by time) with its bound: the NTT against the measured
     butterfly rate (integer issue, G butterflies/s), every other kernel
     against the measured HBM copy bandwidth."""
@@ -214,7 +243,12 @@ def roofline(rep, n_steps, log_n, peak_hbm, hbm_src, alu=None):
         achieved = byts / (ms / 1000.0) / 1e9
         out = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
                "frac": achieved / peak_hbm, "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}
-    out.update({"traffic": None, "launches_per_step": n / n_steps, "ms_per_step": ms / n_steps,
+    traffic = ntt_traffic(workload) if dom == "ntt" else None
+    if traffic is not None:
+        out["traffic_note"] = ("DRAM bytes per transform (both passes) under ncu with warm caches, against "
+                               f"{NTT_TRAFFIC['algorithmic_per_launch'] / 1e6:.2f} MB algorithmic per transform "
+                               f"in the same capture ({byts / n / 1e6:.2f} MB in this run)")
+    out.update({"traffic": traffic, "launches_per_step": n / n_steps, "ms_per_step": ms / n_steps,
                 "share_of_kernel_time": ms / total, "kernels": kernels})
     if alu:
         out["alu_peaks_G_per_s"] = alu
@@ -505,7 +539,7 @@ def one_query(E, wl, K, W, hbm, alu, seed=1000):
         step_dev(W + s)
     rep = H.helrm_ctx_profile_report(ctx)
     H.helrm_ctx_profile(ctx, False)
-    roof = roofline(rep, n_prof, E.pr["log_n"], hbm[0], hbm[1], alu)
+    roof = roofline(rep, n_prof, E.pr["log_n"], hbm[0], hbm[1], alu, wl)
     out = {"value": value, "ms_per_step": total_ms / K, "value_eager": value_eager,
            "latency_ms": {"p50": per[len(per) // 2], "p99": per[min(len(per) - 1, int(round(0.99 * (len(per) - 1))))],
                           "min": per[0], "max": per[-1]},
@@ -810,6 +844,115 @@ def run_served(args):
     E.close()
 
 
+def run_tiny(args):
+    """Config 1: the 1024 x 16 table in base 32 at N = 2^13 (three 50-bit
+    primes, one special prime), one encrypted lookup per step.  value:
+    lookups/s of the server's lookup on selector ciphertexts already on the
+    device; e2e: the client's selector (helrm_query_pack), encoding and
+    encryption, the lookup and the decryption of the 16 outputs, from a host
+    index to host floats, one query per step."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    from paper_2506_18150_gb300 import helrm as H
+    from paper_2506_18150_gb300 import synthetic as syn
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    pr = syn.PARAMS["tiny"]
+    ctx = H.helrm_ctx_create(pr["log_n"], pr["q_bits"], pr["n_p"], pr["p_bits"], pr["alpha"], pr["log2_scale"],
+                             device=local, stream=stream.cuda_stream)
+    delta = 2.0 ** pr["log2_scale"]
+    n = 1 << (pr["log_n"] - 1)
+    C = syn.tiny_table(0)
+    emb = H.helrm_emb_prepare(ctx, [1024], 32, 0, 16, [C], 0, 16, 1, delta, delta)
+    sk, evk = H.helrm_keygen(ctx, 0, H.helrm_ptmat_rotations(ctx, H.helrm_emb_matrix(ctx, emb, 0)))
+    K, W = args.steps, args.warmup
+    idx = [int(np.random.default_rng(1000 * rank + q).integers(0, 1024)) for q in range(K + W)]
+    cts = [H.helrm_encrypt(ctx, evk, H.helrm_encode(ctx, H.helrm_query_pack(ctx, emb, [i], n), 1, delta), 42 + q)
+           for q, i in enumerate(idx)]
+    outs = [None] * (K + W)
+
+    def step(q):
+        outs[q] = H.helrm_embedding_lookup(ctx, evk, emb, cts[q])
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+    for q in range(W):
+        step(q)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = H.helrm_ctx_launch_count(ctx)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    ev[0].record(stream)
+    for s in range(K):
+        step(W + s)
+        ev[s + 1].record(stream)
+    torch.cuda.synchronize()
+    launches = H.helrm_ctx_launch_count(ctx) - l0
+    per = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(K))
+    value, total_ms = job_throughput(K, ev[0].elapsed_time(ev[K]), world)
+    err = max(float(np.max(np.abs(H.helrm_decrypt(ctx, sk, outs[q], 16)
+                                  - (C[0][idx[q] % 32].astype(np.float64) + C[1][idx[q] // 32]))))
+              for q in range(W, W + K))
+
+    # e2e: host index in, host floats out, through the C ABI
+    L = H.lib()
+    out16 = np.zeros(16)
+
+    def step_e2e(q):
+        sel = H.helrm_query_pack(ctx, emb, [idx[q]], n)
+        ct = H.helrm_encrypt(ctx, evk, H.helrm_encode(ctx, sel, 1, delta), 42 + q)
+        y = H.helrm_embedding_lookup(ctx, evk, emb, ct)
+        st = L.helrm_decrypt(ctx.ptr, sk.ptr, y.ptr, out16.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 16)
+        if st != 0:
+            raise H.HelrmError(st, L.helrm_last_error(ctx.ptr).decode())
+    for q in range(W):
+        step_e2e(q)
+    barrier()
+    e2e_value, _ = job_throughput(K, _timed(lambda: [step_e2e(W + s) for s in range(K)]), world)
+    clk = clocks.stop()
+    if rank == 0:
+        line = {"metric": "encrypted embedding lookups/s", "value": value, "unit": "lookups/s", "n_gpus": world,
+                "steps": K, "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded; the paper's tiny-table shape)",
+                "config": {"workload": "tiny: one 1024 x 16 table in base 32 (2 digit one-hots of 32 slots in one "
+                                       "ciphertext), one lookup per step", "ckks": "N=2^13, q 3x50-bit, P 1x50-bit, "
+                                       "alpha=1, Delta=2^40", "parallelism": f"replicas x{world}",
+                           "l2": "no flush: a step reads keys and diagonals once (a few MB, L2-resident)"},
+                "latency_ms": {"p50": per[len(per) // 2], "max": per[-1]}, "max_abs_err": err,
+                "clocks": clk, "gpu_launches": int(launches),
+                "e2e": {"value": e2e_value, "unit": "lookups/s", "h2d_bytes_per_step": 8 * n,
+                        "d2h_bytes_per_step": 8 * 16,
+                        "api": "helrm_query_pack + helrm_encode + helrm_encrypt + helrm_embedding_lookup + "
+                               "helrm_decrypt"}}
+        if world == 1 and not args.no_cpu_baseline:
+            env = dict(os.environ)
+            env.pop("CUDA_VISIBLE_DEVICES", None)
+            try:
+                r = subprocess.run([sys.executable, "-m", "oracle.bench_sample", "--workload", "tiny", "--steps",
+                                    "3"], cwd=ROOT, capture_output=True, text=True, timeout=600, env=env)
+                d = json.loads(r.stdout.strip().splitlines()[-1])
+                line["cpu_baseline"] = {"value": 1.0 / d["s_per_lookup"], "unit": "lookups/s", "cores": d["cores"],
+                                        "kind": "oracle", "sample": d["sample"]}
+            except Exception as e:  # noqa: BLE001
+                line["cpu_baseline"] = {"value": None, "unit": "lookups/s", "kind": "oracle", "sample": f"failed: {e}"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "0"))
@@ -823,6 +966,8 @@ def main():
         run_batched(args)
     elif args.workload == "served":
         run_served(args)
+    elif args.workload == "tiny":
+        run_tiny(args)
     else:
         run_ours(args)
 

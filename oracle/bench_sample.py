@@ -40,6 +40,7 @@ import time
 import numpy as np
 
 SAMPLE_LOG_N = {"uci": 13, "uci_silu": 13, "criteo": 15}
+# The tiny lookup (--workload tiny) runs at its own N = 2^13: run_tiny.
 # Each stage's share of a whole query's time, measured on the development host
 # (python -m oracle.bench_sample --workload criteo: 149.6 s per query at N =
 # 2^15 on 8 cores; --workload uci --steps 21: 7.37 s at N = 2^13).
@@ -180,6 +181,43 @@ def run(workload: str = "uci", steps: int = 0, warmup: int = 0):
             "steps_in_queries": units, "setup_s": cyc.setup_s, "cores": cores(), "sample": sample}
 
 
+def run_tiny(steps: int = 3, exact: bool = False):
+    """The tiny lookup (one 1024 x 16 table in base 32 at N = 2^13, three
+    50-bit primes and one special prime): per step one query's selector
+    (index uniform on 0..1023, seeded), its encoding and encryption, the
+    lookup (one BSGS matvec with its folds) and the decryption of the 16
+    outputs.  exact: every ring product of the lookup by the schoolbook
+    convolution (ckks.EXACT); the keys are made before, the same either way.
+    Returns the median time per lookup (no ring-degree scaling: N is the
+    workload's own)."""
+    from paper_2506_18150_gb300 import synthetic as syn
+
+    from . import ckks, dlrm, linear
+    pr = syn.PARAMS["tiny"]
+    p = ckks.Params(pr["log_n"], pr["q_bits"], pr["n_p"], pr["p_bits"], pr["alpha"], pr["log2_scale"])
+    C = syn.tiny_table(0)
+    pm = linear.prepare(p, dlrm.lookup_matrix(C, 32, 1024), 64, 16, 1, p.delta, p.delta)
+    sk, keys = ckks.keygen(p, 0, rot_steps=linear.rotation_steps(pm))
+    times, err = [], 0.0
+    for q in range(steps):
+        i = int(np.random.default_rng(q).integers(0, 1024))
+        t0 = time.perf_counter()
+        ckks.EXACT = exact
+        try:
+            sel = dlrm.replicate(dlrm.selector_vector([1024], 32, [i]), 64, p.n)
+            ct = ckks.encrypt(p, keys, ckks.encode_real(p, sel, p.delta), 1, p.delta, 42 + q)
+            y = ckks.decrypt(p, sk, linear.matvec(p, keys, pm, ct), 16)
+        finally:
+            ckks.EXACT = False
+        times.append(time.perf_counter() - t0)
+        err = max(err, float(np.max(np.abs(y - (C[0][i % 32].astype(np.float64) + C[1][i // 32])))))
+    med = float(np.median(times))
+    kind = "oracle-exact (schoolbook products)" if exact else "oracle (textbook-NTT products)"
+    return {"workload": "tiny", "exact": exact, "times_s": times, "s_per_lookup": med, "max_abs_err": err,
+            "cores": cores(), "sample": f"{steps} lookups at N=2^13 (the workload's own size), {kind}, "
+                                        f"median {med:.3f} s"}
+
+
 def run_budget(workload: str, reps: int = 3):
     """The bounded sample of bench.py's cpu_baseline: the median of `reps`
     whole queries (UCI-shaped), or of `reps` runs of the first two stages
@@ -220,7 +258,11 @@ if __name__ == "__main__":
     ap.add_argument("--warmup", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0, help="OMP_NUM_THREADS for the oracle (0: all cores)")
     ap.add_argument("--budget", action="store_true", help="the bounded sample of bench.py's cpu_baseline")
+    ap.add_argument("--exact", action="store_true", help="tiny: schoolbook products (oracle-exact)")
     a = ap.parse_args()
     if a.threads:
         os.environ["OMP_NUM_THREADS"] = str(a.threads)
-    print(json.dumps(run_budget(a.workload) if a.budget else run(a.workload, a.steps, a.warmup)))
+    if a.workload == "tiny":
+        print(json.dumps(run_tiny(a.steps or 3, a.exact)))
+    else:
+        print(json.dumps(run_budget(a.workload) if a.budget else run(a.workload, a.steps, a.warmup)))

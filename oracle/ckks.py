@@ -16,6 +16,7 @@ at level l decrypts as c0 + c1*s mod Q_l.
 from __future__ import annotations
 
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -70,7 +71,25 @@ class Params:
         return pow(5, step % self.n, 2 * self.N)
 
 
+# EXACT = True: every ring product is the O(N^2) schoolbook negacyclic
+# convolution (the product's definition, X^N = -1) instead of the textbook NTT;
+# both are exact, so every result is the same, only slower (the "oracle-exact"
+# timing of the tiny lookup).  Limbs run on a thread pool (the C core releases
+# the GIL), which changes no result.
+EXACT = False
+
+
+def _schoolbook_limbs(a, b, mods):
+    from concurrent.futures import ThreadPoolExecutor
+    a2, b2 = np.atleast_2d(a), np.atleast_2d(b)
+    with ThreadPoolExecutor(max_workers=max(1, min(len(mods), os.cpu_count() or 1))) as ex:
+        rows = list(ex.map(lambda i: ring.schoolbook(a2[i], b2[i], int(mods[i])), range(len(mods))))
+    return np.stack(rows)
+
+
 def polymul(p: Params, a, b, mods):
+    if EXACT:
+        return _schoolbook_limbs(a, b, mods)
     return ring.polymul(a, b, mods, p.psis(mods))
 
 

@@ -162,8 +162,10 @@ def matvec(p: ckks.Params, keys: ckks.Keys, pm: PtMatrix, ct: ckks.Ct) -> ckks.C
         u0 = ring.add(u0, ckks.lift_times_P(p, ckks.automorphism(p, ct.c0, k, qm), lvl), qp)
         baby[b] = (u0, u1)
     # Products are sums of ring products; evaluate them in the oracle's own
-    # NTT domain (an exact ring isomorphism) to save transforms.
-    baby_hat = {b: (ring.ntt(u0, qp, psis), ring.ntt(u1, qp, psis)) for b, (u0, u1) in baby.items()}
+    # NTT domain (an exact ring isomorphism) to save transforms, or, with
+    # ckks.EXACT, each one by the schoolbook convolution.
+    baby_hat = {} if ckks.EXACT else \
+        {b: (ring.ntt(u0, qp, psis), ring.ntt(u1, qp, psis)) for b, (u0, u1) in baby.items()}
 
     acc0 = np.zeros((len(qp), p.N), dtype=np.uint64)
     acc1 = np.zeros_like(acc0)
@@ -174,11 +176,19 @@ def matvec(p: ckks.Params, keys: ckks.Keys, pm: PtMatrix, ct: ckks.Ct) -> ckks.C
         s0 = np.zeros((len(qp), p.N), dtype=np.uint64)
         s1 = np.zeros_like(s0)
         for b in bs:
+            if ckks.EXACT:
+                d = ring.from_signed(pm.pts[(g, b)], qp)
+                s0 = ring.add(s0, ckks.polymul(p, d, baby[b][0], qp), qp)
+                s1 = ring.add(s1, ckks.polymul(p, d, baby[b][1], qp), qp)
+                continue
             dh = ring.ntt(ring.from_signed(pm.pts[(g, b)], qp), qp, psis)
             s0 = ring.add(s0, ring.mul(dh, baby_hat[b][0], qp), qp)
             s1 = ring.add(s1, ring.mul(dh, baby_hat[b][1], qp), qp)
-        in0 = ring.ntt(s0, qp, psis, inverse=True)
-        in1 = ring.ntt(s1, qp, psis, inverse=True)
+        if ckks.EXACT:
+            in0, in1 = s0, s1
+        else:
+            in0 = ring.ntt(s0, qp, psis, inverse=True)
+            in1 = ring.ntt(s1, qp, psis, inverse=True)
         if g == 0:
             acc0, acc1 = ring.add(acc0, in0, qp), ring.add(acc1, in1, qp)
             continue

@@ -66,3 +66,13 @@ def test_parse_defaults():
     assert a.workload == "criteo" and a.gpus == 1 and a.steps == 100 and a.warmup == 3
     a = bench.parse(["--impl", "reference", "--steps", "20", "--warmup", "5"])
     assert a.steps == 20 and a.warmup == 5
+
+
+def test_ntt_traffic_follows_the_measured_sources(monkeypatch):
+    assert bench.ntt_traffic("criteo") == bench.NTT_TRAFFIC["bytes_per_launch"]
+    assert bench.ntt_traffic("uci") is None                 # measured on the Criteo-shaped step only
+    changed = dict(bench.NTT_TRAFFIC, sha256=dict(bench.NTT_TRAFFIC["sha256"], **{"ntt.cu": "0" * 64}))
+    monkeypatch.setattr(bench, "NTT_TRAFFIC", changed)
+    assert bench.ntt_traffic("criteo") is None              # the kernel changed since the capture
+    r = bench.roofline({"ntt": (145, 6.35, 4.5e9)}, 1, 16, 6787.6, "measured", None, "criteo")
+    assert r["traffic"] is None

@@ -163,3 +163,26 @@ def test_reduce128_and_scalar_ops():
     c = 123456789123456789
     got = ring.mul_scalar(hi, [c], [q])[0]
     assert [int(x) for x in got] == [int(h) * (c % q) % q for h in hi]
+
+
+def test_exact_mode_gives_the_same_products_and_matvec():
+    """ckks.EXACT (every ring product by the O(N^2) schoolbook convolution)
+    changes no result: a product and a whole BSGS matvec with folds agree
+    word for word with the NTT path."""
+    from oracle import ckks, linear
+    p = ckks.Params(8, [60, 40, 40], 3, 60, 3, 40.0)
+    rng = np.random.default_rng(5)
+    a = np.stack([rng.integers(0, q, p.N, dtype=np.uint64) for q in p.q])
+    b = np.stack([rng.integers(0, q, p.N, dtype=np.uint64) for q in p.q])
+    W = rng.normal(0, 0.3, (4, 16))
+    pm = linear.prepare(p, W, 16, 4, 2, p.delta, p.delta)
+    sk, keys = ckks.keygen(p, 3, rot_steps=linear.rotation_steps(pm))
+    ct = ckks.encrypt(p, keys, ckks.encode_real(p, rng.uniform(-1, 1, p.n), p.delta), 2, p.delta, 9)
+    fast_prod, fast_mv = ckks.polymul(p, a, b, p.q), linear.matvec(p, keys, pm, ct)
+    try:
+        ckks.EXACT = True
+        exact_prod, exact_mv = ckks.polymul(p, a, b, p.q), linear.matvec(p, keys, pm, ct)
+    finally:
+        ckks.EXACT = False
+    assert np.array_equal(fast_prod, exact_prod)
+    assert np.array_equal(fast_mv.c0, exact_mv.c0) and np.array_equal(fast_mv.c1, exact_mv.c1)

@@ -117,11 +117,14 @@ helrm_status helrm_ctx_launch_count(const helrm_ctx *ctx, uint64_t *count);
  * HELRM_E_TIMEOUT with the context still usable afterwards. */
 helrm_status helrm_ctx_wait_selftest(helrm_ctx *ctx, uint32_t polls);
 /* The NTT launch shapes the context chose when it was created: for limb
- * counts per launch <= 4, <= 16, <= 64 and above (out[2b], out[2b+1]), the
- * words per CTA tile and the CTA count, in multiples of the SM count, below
- * which tiles are split.  Creation times every candidate shape on scratch
- * limbs and keeps the fastest (set HELRM_NTT_AUTOTUNE=0 in the environment
- * to keep the defaults 1024 / 2); every shape computes the same result. */
+ * counts per launch <= 4, <= 16, <= 64 and above (out[3b], out[3b+1],
+ * out[3b+2]; out holds 12 words), the words per CTA tile, the CTA count, in
+ * multiples of the SM count, below which tiles are split, and the elements
+ * per thread (8: radix-8 rounds; 4: radix-4 rounds, N = 2^16 only).
+ * Creation times every candidate shape on scratch limbs and keeps the
+ * fastest (set HELRM_NTT_AUTOTUNE=0 in the environment to keep the defaults
+ * 1024 / 2 / 8, HELRM_NTT_EPT=4 or 8 to try one width only); every shape
+ * computes the same result. */
 helrm_status helrm_ctx_ntt_tuning(const helrm_ctx *ctx, uint32_t *out);
 /* Kernel timing: enable != 0 clears previous records and brackets every
  * library kernel (each NTT counts as one, both passes) with CUDA events on

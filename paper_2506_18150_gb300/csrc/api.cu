@@ -175,8 +175,9 @@ helrm_status helrm_ctx_ntt_tuning(const helrm_ctx *ctx, uint32_t *out)
         const Ctx *c = C(ctx);
         HCHECK(out, HELRM_E_INVAL, "out is NULL");
         for (int b = 0; b < 4; b++) {
-            out[2 * b] = (uint32_t)c->ntt_tune[b].tile;
-            out[2 * b + 1] = (uint32_t)c->ntt_tune[b].mult;
+            out[3 * b] = (uint32_t)c->ntt_tune[b].tile;
+            out[3 * b + 1] = (uint32_t)c->ntt_tune[b].mult;
+            out[3 * b + 2] = (uint32_t)c->ntt_tune[b].ept;
         }
     });
 }

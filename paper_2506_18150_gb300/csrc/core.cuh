@@ -226,6 +226,7 @@ struct Ctx : Handle {
     struct NttTune {
         int tile = 1024;
         int mult = 2;
+        int ept = 8;     // elements per thread (4: N = 2^16 instances only)
     };
     NttTune ntt_tune[4];
     u64 launches = 0;

@@ -117,23 +117,28 @@ enum Mode { M_LAZY = 0, M_SCALE = 1, M_REDUCE = 2 };
 // sub-transforms (128, 256 threads): 48 registers, i.e. 40 resident warps per
 // SM instead of 32, without spills; every other instance is left to the
 // compiler under the 512-thread bound (it settles at 56-64 registers).
-#define NTT_MAX_THREADS(FIXN, FIXG) ((FIXN) && (FIXG) >= 2 ? (32 << (FIXG)) : 512)
-#define NTT_MIN_BLOCKS(FIXN, FIXG) ((FIXN) && (FIXG) >= 2 ? 65536 / ((32 << (FIXG)) * 48) : 0)
+// EPT = 4 elements per thread (fixed-size instances only): radix-4 rounds,
+// twice the threads per sub-transform and half the serial work per thread,
+// which shortens launches that carry few limbs; up to 64 registers.
+#define NTT_MAX_THREADS(FIXN, FIXG, EPT) ((FIXN) && (FIXG) >= 2 ? ((256 / (EPT)) << (FIXG)) : 512)
+#define NTT_MIN_BLOCKS(FIXN, FIXG, EPT) \
+    ((FIXN) && (FIXG) >= 2 ? 65536 / (((256 / (EPT)) << (FIXG)) * ((EPT) == 8 ? 48 : 64)) : 0)
 
 // XL (column passes only): the per-limb extras of XList apply -- a forward
 // first pass computes its input as a fast base conversion of fn source limbs
 // on load (the 128-bit multiply-accumulate and the one reduction of the
 // stand-alone conversion kernel, so the values are identical); an inverse
 // last pass scales by its own constant.
-template <int LOGP, bool COLS, bool INV, int FIXN = 0, int FIXG = 0, bool XL = false>
-__global__ void __launch_bounds__(NTT_MAX_THREADS(FIXN, FIXG), NTT_MIN_BLOCKS(FIXN, FIXG)) k_ntt_pass(int first, int logN_arg, int logG_arg, LimbList list,
+template <int LOGP, bool COLS, bool INV, int FIXN = 0, int FIXG = 0, bool XL = false, int EPT = 8>
+__global__ void __launch_bounds__(NTT_MAX_THREADS(FIXN, FIXG, EPT), NTT_MIN_BLOCKS(FIXN, FIXG, EPT)) k_ntt_pass(int first, int logN_arg, int logG_arg, LimbList list,
                                                    const ulonglong2 *__restrict__ tw_all,
                                                    const ulonglong2 *__restrict__ ninv,
                                                    const PrimeInfo *__restrict__ pinfo, int mode, const Ep ep,
                                                    const XArg<XL> xa)
 {
     constexpr int P = 1 << LOGP;
-    constexpr int TPS = P / 8;              // threads per sub-transform
+    constexpr int TPS = P / EPT;            // threads per sub-transform (EPT elements each)
+    constexpr int RB = EPT >= 8 ? 3 : 2;    // stages per round
     extern __shared__ u64 sm[];
     const int logN = FIXN ? FIXN : logN_arg;
     const int logG = FIXN ? FIXG : logG_arg;
@@ -202,8 +207,8 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS(FIXN, FIXG), NTT_MIN_BLOCKS(FI
     if (!COLS || g == 0) {
 #pragma unroll
         for (int s = 0; s < LOGP; s++)
-            if (tt * 8 < (1 << s)) {
-                const ulonglong2 *line = tw + ((size_t)(bm + seg) << s) + tt * 8;
+            for (int e = tt * 8; e < (1 << s); e += TPS * 8) {
+                const ulonglong2 *line = tw + ((size_t)(bm + seg) << s) + e;
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(line));
             }
     }
@@ -221,17 +226,17 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS(FIXN, FIXG), NTT_MIN_BLOCKS(FI
     const int sbase = COLS ? (G <= 16 ? g : g + (g >> 4)) : (g * P + ((g * P) >> 4));
     auto saddr = [&](int e) -> int { return COLS ? e * G + ((e * G) >> 4) + sbase : e + (e >> 4) + sbase; };
 
-    u64 v[8];
-    // rounds of up to three stages; forward goes first-to-last, inverse last-to-first
-    constexpr int NR = (LOGP + 2) / 3;
+    u64 v[EPT];
+    // rounds of up to RB stages; forward goes first-to-last, inverse last-to-first
+    constexpr int NR = (LOGP + RB - 1) / RB;
 #pragma unroll
     for (int rr = 0; rr < NR; rr++) {
         const int rho = INV ? NR - 1 - rr : rr;
-        const int s0 = 3 * rho;
-        const int r = (s0 + 3 <= LOGP) ? 3 : LOGP - s0;
+        const int s0 = RB * rho;
+        const int r = (s0 + RB <= LOGP) ? RB : LOGP - s0;
         const int T = P >> (s0 + r);        // spacing of a group's members
         const int gs = 1 << r;              // group size
-        const int ng = 8 / gs;              // groups per thread
+        const int ng = EPT / gs;            // groups per thread
         // element index of member k of this thread's group qg
         auto elem = [&](int qg, int k) {
             const int gam = tt + qg * TPS;  // group index
@@ -346,12 +351,12 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS(FIXN, FIXG), NTT_MIN_BLOCKS(FI
     }
 }
 
-template <int LOGP, bool COLS, bool INV, int FIXN, int FIXG, bool XL>
+template <int LOGP, bool COLS, bool INV, int FIXN, int FIXG, bool XL, int EPT = 8>
 void launch_kernel(Ctx *c, dim3 grid, int threads, size_t smem, const LimbList &ll, int first, int logG, int mode,
                    const Ep &ep_scal, const XArg<XL> &xa)
 {
     const ulonglong2 *tw = INV ? c->d_tw_inv.as<ulonglong2>() : c->d_tw_fwd.as<ulonglong2>();
-    launch(c, k_ntt_pass<LOGP, COLS, INV, FIXN, FIXG, XL>, grid, threads, smem, first, c->logN, logG, ll, tw,
+    launch(c, k_ntt_pass<LOGP, COLS, INV, FIXN, FIXG, XL, EPT>, grid, threads, smem, first, c->logN, logG, ll, tw,
            c->d_ninv.as<ulonglong2>(), c->d_pinfo.as<PrimeInfo>(), mode, ep_scal, xa);
 }
 
@@ -368,10 +373,23 @@ void launch_pass(Ctx *c, const LimbList &ll, int n_sub, int first, int mode, con
     while (G > gmin && (long)(n_sub / G) * ll.n < (long)tu.mult * c->n_sms) G /= 2;
     int logG = 0;
     while ((1 << logG) < G) logG++;
-    const int threads = G * P / 8;
     const size_t smem = (size_t)(G * P + (G * P >> 4) + 1) * 8;
     dim3 grid(n_sub / G, ll.n);
-    // N = 2^16 (both passes 256-point): instances with the tile width fixed
+    // N = 2^16 (both passes 256-point): instances with the tile width fixed,
+    // with 8 or 4 elements per thread
+    if constexpr (LOGP == 8) {
+        if (c->logN == 16 && tu.ept == 4) {
+            const int t4 = G * P / 4;
+            switch (logG) {
+            case 0: launch_kernel<8, COLS, INV, 16, 0, XL, 4>(c, grid, t4, smem, ll, first, logG, mode, ep_scal, xa); return;
+            case 1: launch_kernel<8, COLS, INV, 16, 1, XL, 4>(c, grid, t4, smem, ll, first, logG, mode, ep_scal, xa); return;
+            case 2: launch_kernel<8, COLS, INV, 16, 2, XL, 4>(c, grid, t4, smem, ll, first, logG, mode, ep_scal, xa); return;
+            case 3: launch_kernel<8, COLS, INV, 16, 3, XL, 4>(c, grid, t4, smem, ll, first, logG, mode, ep_scal, xa); return;
+            default: break;
+            }
+        }
+    }
+    const int threads = G * P / 8;
     if constexpr (LOGP == 8) {
         if (c->logN == 16) {
             switch (logG) {
@@ -621,6 +639,9 @@ void ntt_autotune(Ctx *c)
     const int N = c->N, n_max = 128;
     const int tiles[] = {512, 1024, 2048};
     const int mults[] = {1, 2, 4, 8};
+    const char *ept_env = getenv("HELRM_NTT_EPT");   // 4 or 8: tune with that width only
+    std::vector<int> epts = {8, 4};
+    if (ept_env && (atoi(ept_env) == 8 || atoi(ept_env) == 4)) epts = {atoi(ept_env)};
     const int sizes[4] = {2, 8, 32, 128};   // a representative launch of each bucket
     DevMem buf(c, (size_t)n_max * N * 8);
     CUDA_CHECK(cudaMemsetAsync(buf.ptr, 0, (size_t)n_max * N * 8, c->stream));
@@ -638,9 +659,11 @@ void ntt_autotune(Ctx *c)
         }
         float best = 1e30f;
         Ctx::NttTune win = c->ntt_tune[bk];
+        for (int e : epts)
         for (int t : tiles)
             for (int m : mults) {
-                c->ntt_tune[bk] = {t, m};
+                if (e != 8 && N != 65536) continue;   // 4 per thread: the N = 2^16 instances only
+                c->ntt_tune[bk] = {t, m, e};
                 ntt_run(c, v, false, nullptr);   // warm-up
                 ntt_run(c, v, true, nullptr);
                 CUDA_CHECK(cudaEventRecord(e0, c->stream));
@@ -654,7 +677,7 @@ void ntt_autotune(Ctx *c)
                 CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
                 if (ms < best * 0.98f) {   // prefer the earlier (smaller) shape unless clearly faster
                     best = ms;
-                    win = {t, m};
+                    win = {t, m, e};
                 }
             }
         c->ntt_tune[bk] = win;

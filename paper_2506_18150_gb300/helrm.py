@@ -717,10 +717,10 @@ def helrm_ctx_wait_selftest(ctx, polls: int):
 
 
 def helrm_ctx_ntt_tuning(ctx):
-    """{limb bucket: (tile words, CTA multiple of the SM count)} chosen at context creation."""
-    out = (C.c_uint32 * 8)()
+    """{limb bucket: (tile words, CTA multiple of the SM count, elements per thread)} chosen at context creation."""
+    out = (C.c_uint32 * 12)()
     _check(ctx, lib().helrm_ctx_ntt_tuning(ctx.ptr, out))
-    return {b: (out[2 * i], out[2 * i + 1]) for i, b in enumerate(["<=4", "<=16", "<=64", ">64"])}
+    return {b: (out[3 * i], out[3 * i + 1], out[3 * i + 2]) for i, b in enumerate(["<=4", "<=16", "<=64", ">64"])}
 
 
 def helrm_ctx_profile(ctx, enable: bool):

@@ -85,6 +85,39 @@ def test_ntt_matches_oracle_evaluation(env, which):
     assert np.array_equal(dev.cpu().numpy().view(np.uint64), a)
 
 
+@pytest.mark.parametrize("ept", ["4", "8"])
+def test_ntt_both_thread_widths_full(ept, monkeypatch):
+    """The N = 2^16 transform with 4 and with 8 elements per thread (the
+    autotuner's radix-4 and radix-8 rounds; HELRM_NTT_EPT keeps one of them),
+    at 1, 3 and 21 limbs per launch, against the oracle's evaluation."""
+    import torch
+
+    from oracle import ring
+    from paper_2506_18150_gb300 import helrm as H
+    from paper_2506_18150_gb300 import synthetic as syn
+    monkeypatch.setenv("HELRM_NTT_EPT", ept)
+    pr = syn.PARAMS["full"]
+    ctx = gpu_ctx(pr)
+    primes, psis = H.helrm_ctx_primes(ctx)
+    tun = H.helrm_ctx_ntt_tuning(ctx)
+    assert all(v[2] == int(ept) for v in tun.values())
+    n = 1 << pr["log_n"]
+    brv = bitrev_perm(pr["log_n"])
+    rng = np.random.default_rng(11)
+    for cnt in (1, 3, 21):
+        a = np.stack([rng.integers(0, primes[1 + i], n, dtype=np.uint64) for i in range(cnt)])
+        dev = torch.from_numpy(a.view(np.int64).copy()).cuda()
+        H.helrm_ntt(ctx, dev.data_ptr(), cnt, 1, False)
+        H.helrm_ctx_synchronize(ctx)
+        fwd = dev.cpu().numpy().view(np.uint64)
+        for l in sorted({0, cnt - 1}):
+            want = ring.ntt(a[l], [primes[1 + l]], [psis[1 + l]])[0]
+            assert np.array_equal(fwd[l], want[brv]), (cnt, l)
+        H.helrm_ntt(ctx, dev.data_ptr(), cnt, 1, True)
+        H.helrm_ctx_synchronize(ctx)
+        assert np.array_equal(dev.cpu().numpy().view(np.uint64), a), cnt
+
+
 def test_encryption_bit_exact(env):
     for level in [0, 2, 4]:
         ct, ct_o, _ = fresh(env, level, 1000 + level)

@@ -101,3 +101,19 @@ def test_criteo_inference_full(full):
         _check(coeffs, lvl, case)
     coeffs, lvl, _ = H.helrm_ct_export(ctx, H.helrm_infer(ctx, evk, model, cd, cs))
     _check(coeffs, lvl, case)
+
+
+def test_criteo_products_with_radix4_transforms(monkeypatch):
+    """Two of the products again on a context whose transforms all run with
+    4 elements per thread (radix-4 rounds, HELRM_NTT_EPT=4), fused base
+    conversions and merged rescales included: the same words."""
+    from paper_2506_18150_gb300 import helrm as H
+    from paper_2506_18150_gb300 import synthetic as syn
+    monkeypatch.setenv("HELRM_NTT_EPT", "4")
+    pr = syn.PARAMS["full"]
+    ctx = gpu_ctx(pr)
+    spec = syn.criteo_spec(0)
+    model = H.helrm_model_create(ctx, spec, syn.make_weights(spec, 0))
+    _, evk = H.helrm_keygen(ctx, R["key_seed"], H.helrm_model_rotations(ctx, model))
+    for name in ("matvec_13_512x256", "matvec_1_256x1"):
+        test_criteo_matvec_full((ctx, model, evk, 1 << pr["log_n"], 2.0 ** pr["log2_scale"]), name)

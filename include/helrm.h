@@ -152,11 +152,14 @@ helrm_status helrm_ntt(helrm_ctx *ctx, uint64_t *d_data, uint32_t n_limbs, uint3
  * inner products run, with no memory traffic, on blocks_per_sm x (SM count)
  * CTAs of 256 threads, each thread repeating `iters` times: kind 0 a radix-8
  * round of 12 lazy forward butterflies, 1 the same for the inverse
- * butterflies, 2 eight 64 x 64 -> 128-bit multiply-accumulates, 3 eight
- * Shoup modular products.  *ops_per_s receives butterflies (0, 1),
- * multiply-accumulates (2) or products (3) per second, timed with CUDA events
- * on the context's stream (synchronous).  HELRM_E_INVAL for an unknown kind
- * or blocks_per_sm outside [1, 32]. */
+ * butterflies, 2 eight 64 x 64 -> 128-bit multiply-accumulates (the
+ * library's carry-chained form), 3 eight Shoup modular products, 4 the same
+ * sums as 2 from four 32 x 32 -> 64-bit products with explicit carries, 5
+ * the same sums for operands below 2^40 as three carry-free 64-bit column
+ * sums of 20 x 20-bit products.  *ops_per_s receives butterflies (0, 1),
+ * multiply-accumulates (2, 4, 5) or products (3) per second, timed with CUDA
+ * events on the context's stream (synchronous).  HELRM_E_INVAL for an
+ * unknown kind or blocks_per_sm outside [1, 32]. */
 helrm_status helrm_alu_peak(helrm_ctx *ctx, int32_t kind, uint32_t blocks_per_sm, uint32_t iters,
                             double *ops_per_s);
 

@@ -511,10 +511,27 @@ def chunk_slots(sel: np.ndarray, n: int):
     return [replicate(sel[c0:c0 + w], linear.pow2ceil(w), n) for c0, w in selector_chunks(len(sel), n)]
 
 
+def lookup_groups(pms):
+    """The chunks' matrices grouped by shape (linear.same_shape), in order of
+    first appearance: [[chunk indices], ...].  All but the last chunk hold n
+    columns, so there are at most two groups."""
+    groups = []
+    for k, pm in enumerate(pms):
+        for grp in groups:
+            if linear.same_shape(pms[grp[0]], pm):
+                grp.append(k)
+                break
+        else:
+            groups.append([k])
+    return groups
+
+
 def lookup_multi(p: ckks.Params, keys: ckks.Keys, pms, cts):
-    """y = M s = sum_c M_c s_c: the per-ciphertext products, added."""
+    """y = M s = sum_c M_c s_c.  The chunks of one shape share their giant
+    steps, ModDown, rescale and folds (linear.matvec_sum, reading R31); the
+    groups' results are added in order."""
     out = None
-    for pm, ct in zip(pms, cts):
-        y = linear.matvec(p, keys, pm, ct)
+    for grp in lookup_groups(pms):
+        y = linear.matvec_sum(p, keys, [pms[k] for k in grp], [cts[k] for k in grp])
         out = y if out is None else ckks.add(p, out, y)
     return out

@@ -140,8 +140,11 @@ def rotation_steps(pm: PtMatrix):
     return sorted({b for b in babies if b} | {g * lay.n1 for g in giants if g} | set(fold_steps(lay.folds)))
 
 
-def matvec(p: ckks.Params, keys: ckks.Keys, pm: PtMatrix, ct: ckks.Ct) -> ckks.Ct:
-    """Double-hoisted BSGS y = W x, then rescale, then the folds."""
+def baby_products(p: ckks.Params, keys: ckks.Keys, pm: PtMatrix, ct: ckks.Ct) -> dict:
+    """The first half of the double-hoisted BSGS product: the baby steps in QP
+    (one ModUp of c1, no ModDown) and, for every giant step g with diagonals,
+    inner_g = sum_b diag'_{g,b} (x) baby_b over the level's QP limbs, as a pair
+    of coefficient-domain polynomials.  Returns {g: (inner_g0, inner_g1)}."""
     lay, lvl = pm.layout, ct.level
     if lvl != pm.level:
         raise ValueError("ciphertext level does not match the prepared matrix")
@@ -167,8 +170,7 @@ def matvec(p: ckks.Params, keys: ckks.Keys, pm: PtMatrix, ct: ckks.Ct) -> ckks.C
     baby_hat = {} if ckks.EXACT else \
         {b: (ring.ntt(u0, qp, psis), ring.ntt(u1, qp, psis)) for b, (u0, u1) in baby.items()}
 
-    acc0 = np.zeros((len(qp), p.N), dtype=np.uint64)
-    acc1 = np.zeros_like(acc0)
+    inner = {}
     for g in range(lay.n2):
         bs = [b for (gg, b) in pm.pts if gg == g]
         if not bs:
@@ -185,15 +187,26 @@ def matvec(p: ckks.Params, keys: ckks.Keys, pm: PtMatrix, ct: ckks.Ct) -> ckks.C
             s0 = ring.add(s0, ring.mul(dh, baby_hat[b][0], qp), qp)
             s1 = ring.add(s1, ring.mul(dh, baby_hat[b][1], qp), qp)
         if ckks.EXACT:
-            in0, in1 = s0, s1
+            inner[g] = (s0, s1)
         else:
-            in0 = ring.ntt(s0, qp, psis, inverse=True)
-            in1 = ring.ntt(s1, qp, psis, inverse=True)
+            inner[g] = (ring.ntt(s0, qp, psis, inverse=True), ring.ntt(s1, qp, psis, inverse=True))
+    return inner
+
+
+def giant_steps(p: ckks.Params, keys: ckks.Keys, pm: PtMatrix, inner: dict, lvl: int, scale: float) -> ckks.Ct:
+    """The second half: the giant steps on the QP inner products (for g > 0:
+    ModDown the a-part, ModUp, phi, key inner product; the b-part is already
+    in QP and only gets phi), one ModDown of the sum, the rescale, then the
+    folds.  scale: the product's scale before the rescale."""
+    lay = pm.layout
+    qp = p.qp_mods(lvl)
+    acc0 = np.zeros((len(qp), p.N), dtype=np.uint64)
+    acc1 = np.zeros_like(acc0)
+    for g in sorted(inner):
+        in0, in1 = inner[g]
         if g == 0:
             acc0, acc1 = ring.add(acc0, in0, qp), ring.add(acc1, in1, qp)
             continue
-        # Giant step on a QP ciphertext: ModDown the a-part, ModUp, phi, key
-        # inner product; the b-part is already in QP and only gets phi.
         k = p.galois(g * lay.n1)
         c1q = ckks.moddown(p, in1, lvl)
         dr = [ckks.automorphism(p, d, k, qp) for d in ckks.modup(p, c1q, lvl)]
@@ -201,8 +214,7 @@ def matvec(p: ckks.Params, keys: ckks.Keys, pm: PtMatrix, ct: ckks.Ct) -> ckks.C
         acc0 = ring.add(acc0, ring.add(ckks.automorphism(p, in0, k, qp), k0, qp), qp)
         acc1 = ring.add(acc1, k1, qp)
 
-    out = ckks.Ct(ckks.moddown(p, acc0, lvl), ckks.moddown(p, acc1, lvl), lvl,
-                  ct.scale * pm.pt_scale)
+    out = ckks.Ct(ckks.moddown(p, acc0, lvl), ckks.moddown(p, acc1, lvl), lvl, scale)
     out = ckks.rescale(p, out)
     out.scale = pm.out_scale
     for stride, radix in lay.folds:
@@ -213,6 +225,40 @@ def matvec(p: ckks.Params, keys: ckks.Keys, pm: PtMatrix, ct: ckks.Ct) -> ckks.C
             acc = ckks.add(p, acc, rots[st])
         out = acc
     return out
+
+
+def matvec(p: ckks.Params, keys: ckks.Keys, pm: PtMatrix, ct: ckks.Ct) -> ckks.Ct:
+    """Double-hoisted BSGS y = W x, then rescale, then the folds."""
+    return giant_steps(p, keys, pm, baby_products(p, keys, pm, ct), ct.level, ct.scale * pm.pt_scale)
+
+
+def same_shape(a: PtMatrix, b: PtMatrix) -> bool:
+    """Matrices whose products can share their giant steps: the same layout
+    (pads, BSGS split, folds), level and scales."""
+    return (a.layout == b.layout and a.level == b.level and a.pt_scale == b.pt_scale
+            and a.out_scale == b.out_scale)
+
+
+def matvec_sum(p: ckks.Params, keys: ckks.Keys, pms, cts) -> ckks.Ct:
+    """sum_k W_k x_k for matrices of the same shape: the baby-step products
+    of every (W_k, x_k) are added in QP, giant step by giant step, and the
+    sum goes through one set of giant steps, one ModDown, one rescale and one
+    set of folds (reading R31).  All x_k share level and scale."""
+    if not pms or len(pms) != len(cts):
+        raise ValueError("matvec_sum takes one ciphertext per matrix")
+    lvl, scale = cts[0].level, cts[0].scale
+    for pm, ct in zip(pms, cts):
+        if not same_shape(pm, pms[0]) or ct.level != lvl or ct.scale != scale:
+            raise ValueError("matvec_sum: matrices and ciphertexts must share shape, level and scale")
+    qp = p.qp_mods(lvl)
+    total = {}
+    for pm, ct in zip(pms, cts):
+        for g, (i0, i1) in baby_products(p, keys, pm, ct).items():
+            if g in total:
+                total[g] = (ring.add(total[g][0], i0, qp), ring.add(total[g][1], i1, qp))
+            else:
+                total[g] = (i0, i1)
+    return giant_steps(p, keys, pms[0], total, lvl, scale * pms[0].pt_scale)
 
 
 def matvec_cleartext(W: np.ndarray, x: np.ndarray, in_pad: int, out_pad: int, n: int) -> np.ndarray:

@@ -843,27 +843,23 @@ Batch *batch_create(Ctx *c, const Model *m, const std::vector<const EvalKey *> &
 }
 
 // y = W x for every query (double-hoisted BSGS, rescale, folds), as matvec
-static Owned matvec_b(Ctx *c, const Batch *bt, const PtMatrix *m, const CCtVec &in)
+// The baby-step half of the batch's products by matrix m (the fused kernel's
+// shapes): one ModUp per query, then the hoisted baby steps and the BSGS MAC
+// into inner[q][g][2][plane]; need_g[g] is set for the giant steps with
+// diagonals.
+static void baby_products_b(Ctx *c, const Batch *bt, const PtMatrix *m, const CCtVec &in, u64 *inner,
+                            std::vector<char> &need_g)
 {
     const size_t B = in.size();
-    const int l = in[0]->level, N = c->N, nq = l + 1, nl = nq + c->K, dnum = c->dnum(l);
-    for (auto *x : in) HCHECK(x->level == m->level, HELRM_E_LEVEL, "ciphertext level does not match the prepared matrix");
+    const int l = in[0]->level, N = c->N, nl = l + 1 + c->K, dnum = c->dnum(l);
     auto kt = bt->keytab.find(m);
-    if (kt == bt->keytab.end()) {   // shapes outside the fused kernel: the one-query path, query by query
-        Owned o;
-        for (size_t q = 0; q < B; q++) o.v.emplace_back(matvec(c, bt->evk[q], m, in[q]));
-        return o;
-    }
     const size_t plane = (size_t)nl * N, dplane = (size_t)dnum * plane;
-    std::vector<char> need_b(m->n1, 0), need_g(m->n2, 0);
+    std::vector<char> need_b(m->n1, 0);
+    need_g.assign(m->n2, 0);
     for (auto &gb : m->gb) {
         need_b[gb.second] = 1;
         need_g[gb.first] = 1;
     }
-    std::vector<const SwitchKey *> gkey(B * m->n2, nullptr);
-    for (size_t q = 0; q < B; q++)
-        for (int g = 1; g < m->n2; g++)
-            if (need_g[g]) gkey[q * m->n2 + g] = rot_key(bt->evk[q], c->galois(g * m->n1), l);
     bool any_baby = false;
     int n_keys = 0;
     for (int b = 1; b < m->n1; b++) {
@@ -879,16 +875,67 @@ static Owned matvec_b(Ctx *c, const Batch *bt, const PtMatrix *m, const CCtVec &
     }
     if (any_baby) modup_b(c, c1s, l, dg);
     const size_t iq = (size_t)m->n2 * 2 * plane;   // inner products of one query
-    DevMem inner(c, B * iq * 8);
     std::vector<u64> gals(m->n1, 1);
     for (int b = 1; b < m->n1; b++)
         if (need_b[b]) gals[b] = c->galois(b);
     std::vector<k::BsgsQuery> qs;
-    for (size_t q = 0; q < B; q++) qs.push_back({inner.u() + q * iq, dg[q], in[q]->c0(), in[q]->c1()});
+    for (size_t q = 0; q < B; q++) qs.push_back({inner + q * iq, dg[q], in[q]->c0(), in[q]->c1()});
     k::bsgs_tma_batch(c, qs, kt->second.as<const u64 *const>(),
                       (const int *)((const char *)kt->second.ptr + B * 64 * sizeof(u64 *)), gals.data(),
                       m->d_ptrs.as<const u64 *const>(),
                       m->d_gb_index.as<int>(), (int)m->gb.size(), n_keys, m->n1, m->n2, l);
+}
+
+// sum_k W_k x_k for every query of the batch, the matrices of one shape
+// (reading R31: the baby-step products are added over QP and the sum takes
+// one set of giant steps, one ModDown + rescale and one set of folds); with
+// one matrix, the batch's product by it.  in[k] holds the B ciphertexts
+// multiplied by ms[k].
+static Owned matvec_sum_b(Ctx *c, const Batch *bt, const std::vector<const PtMatrix *> &ms,
+                          const std::vector<CCtVec> &in)
+{
+    const PtMatrix *m = ms[0];
+    const size_t B = in[0].size();
+    const int l = in[0][0]->level, N = c->N, nq = l + 1, nl = nq + c->K, dnum = c->dnum(l);
+    for (size_t k2 = 0; k2 < ms.size(); k2++) {
+        HCHECK(same_shape(ms[k2], m) && in[k2].size() == B, HELRM_E_PARAM, "batched product sum: shapes differ");
+        for (size_t q = 0; q < B; q++)
+            HCHECK(in[k2][q]->level == m->level && in[k2][q]->scale == in[0][q]->scale, HELRM_E_LEVEL,
+                   "ciphertext level or scale does not match the prepared matrix");
+    }
+    bool fused = true;
+    for (auto *mk : ms) fused &= bt->keytab.count(mk) != 0;
+    if (!fused) {   // shapes outside the fused kernel: the one-query path, query by query
+        Owned o;
+        for (size_t q = 0; q < B; q++) {
+            std::vector<const Ciphertext *> xs;
+            for (auto &v : in) xs.push_back(v[q]);
+            o.v.emplace_back(matvec_sum(c, bt->evk[q], ms, xs));
+        }
+        return o;
+    }
+    const size_t plane = (size_t)nl * N, dplane = (size_t)dnum * plane;
+    const size_t iq = (size_t)m->n2 * 2 * plane;   // inner products of one query
+    DevMem inner(c, B * iq * 8);
+    std::vector<char> need_g;
+    if (ms.size() == 1) {
+        baby_products_b(c, bt, m, in[0], inner.u(), need_g);
+    } else {
+        DevMem part(c, B * iq * 8);
+        k::zero(c, inner.u(), B * iq);
+        need_g.assign(m->n2, 0);
+        std::vector<char> ng;
+        for (size_t k2 = 0; k2 < ms.size(); k2++) {
+            k::zero(c, part.u(), B * iq);
+            baby_products_b(c, bt, ms[k2], in[k2], part.u(), ng);
+            for (int g = 0; g < m->n2; g++) need_g[g] |= ng[g];
+            k::add(c, inner.u(), inner.u(), part.u(), (int)(B * m->n2 * 2 * nl), c->qmap(l, 0, nl));
+        }
+    }
+    std::vector<const SwitchKey *> gkey(B * m->n2, nullptr);
+    for (size_t q = 0; q < B; q++)
+        for (int g = 1; g < m->n2; g++)
+            if (need_g[g]) gkey[q * m->n2 + g] = rot_key(bt->evk[q], c->galois(g * m->n1), l);
     // giant steps: ModDown the a-part of every (query, g > 0), ModUp them all,
     // then one key product per g adds phi(inner_g) into inner_0 of each query
     std::vector<int> gs;
@@ -924,7 +971,7 @@ static Owned matvec_b(Ctx *c, const Batch *bt, const PtMatrix *m, const CCtVec &
     std::vector<double> sc;
     for (size_t q = 0; q < B; q++) {
         acc.push_back(inner.u() + q * iq);
-        sc.push_back(in[q]->scale * m->pt_scale);
+        sc.push_back(in[0][q]->scale * m->pt_scale);
     }
     Owned y = moddown_rescale_b(c, acc, l, sc, none, none);   // the final ModDown and the rescale, merged
     for (auto &p : y.v) p->scale = m->out_scale;
@@ -939,6 +986,11 @@ static Owned matvec_b(Ctx *c, const Batch *bt, const PtMatrix *m, const CCtVec &
         }
     }
     return y;
+}
+
+static Owned matvec_b(Ctx *c, const Batch *bt, const PtMatrix *m, const CCtVec &in)
+{
+    return matvec_sum_b(c, bt, {m}, {in});
 }
 
 static Owned dense_layer_b(Ctx *c, const Batch *bt, const Layer &L, const CCtVec &x)
@@ -1010,12 +1062,33 @@ std::vector<Ciphertext *> model_infer_batch(Ctx *c, const Batch *bt, const CCtVe
     Owned e, h;
     Fork branch(c);
     branch.run([&] {
-        // one product per selector ciphertext, added (ct_sel is query-major)
+        // one product per selector ciphertext (ct_sel is query-major); the
+        // chunks of one shape share their giant steps (matvec_sum_b), and the
+        // groups, in order of first appearance, are added in order
+        std::vector<std::vector<size_t>> groups;
         for (size_t k2 = 0; k2 < ns; k2++) {
-            CCtVec sk2;
-            for (size_t q = 0; q < B; q++) sk2.push_back(ct_sel[q * ns + k2]);
-            Owned t = matvec_b(c, bt, mats[k2], sk2);
-            e = k2 == 0 ? std::move(t) : add_b(c, e.craw(), t.craw());
+            bool placed = false;
+            for (auto &grp : groups)
+                if (same_shape(mats[grp[0]], mats[k2])) {
+                    grp.push_back(k2);
+                    placed = true;
+                    break;
+                }
+            if (!placed) groups.push_back({k2});
+        }
+        bool first = true;
+        for (auto &grp : groups) {
+            std::vector<const PtMatrix *> ms;
+            std::vector<CCtVec> xs;
+            for (size_t k2 : grp) {
+                ms.push_back(mats[k2]);
+                CCtVec sk2;
+                for (size_t q = 0; q < B; q++) sk2.push_back(ct_sel[q * ns + k2]);
+                xs.push_back(sk2);
+            }
+            Owned t = matvec_sum_b(c, bt, ms, xs);
+            e = first ? std::move(t) : add_b(c, e.craw(), t.craw());
+            first = false;
         }
     });
     CCtVec x = ct_dense;

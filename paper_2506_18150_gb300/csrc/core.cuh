@@ -657,6 +657,10 @@ struct PtMatrix : Handle {
 PtMatrix *ptmat_prepare(Ctx *c, const double *W, int rows, int cols, int in_pad, int out_pad,
                         int level, double ct_scale, double target_scale);
 Ciphertext *matvec(Ctx *c, const EvalKey *evk, const PtMatrix *m, const Ciphertext *in);
+// products of matrices of one shape share their giant steps (linear.cu)
+bool same_shape(const PtMatrix *a, const PtMatrix *b);
+Ciphertext *matvec_sum(Ctx *c, const EvalKey *evk, const std::vector<const PtMatrix *> &ms,
+                       const std::vector<const Ciphertext *> &in);
 int pow2ceil(int x);
 
 }  // namespace helrm

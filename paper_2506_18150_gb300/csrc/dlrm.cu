@@ -472,9 +472,28 @@ Ciphertext *emb_lookup_multi(Ctx *c, const EvalKey *evk, const Emb *e, const std
     const int n = emb_n_chunks(e);
     HCHECK((int)sel.size() == n, HELRM_E_INVAL,
            "the selector spans " + std::to_string(n) + " ciphertexts, got " + std::to_string(sel.size()));
-    std::unique_ptr<Ciphertext> y;
+    // chunks of one shape share their giant steps (matvec_sum); the groups, in
+    // order of first appearance, are added in order
+    std::vector<std::vector<int>> groups;
     for (int k = 0; k < n; k++) {
-        std::unique_ptr<Ciphertext> t(matvec(c, evk, emb_chunk(e, k), sel[k]));
+        bool placed = false;
+        for (auto &grp : groups)
+            if (same_shape(emb_chunk(e, grp[0]), emb_chunk(e, k))) {
+                grp.push_back(k);
+                placed = true;
+                break;
+            }
+        if (!placed) groups.push_back({k});
+    }
+    std::unique_ptr<Ciphertext> y;
+    for (auto &grp : groups) {
+        std::vector<const PtMatrix *> ms;
+        std::vector<const Ciphertext *> xs;
+        for (int k : grp) {
+            ms.push_back(emb_chunk(e, k));
+            xs.push_back(sel[k]);
+        }
+        std::unique_ptr<Ciphertext> t(matvec_sum(c, evk, ms, xs));
         y.reset(y ? ct_add(c, y.get(), t.get()) : t.release());
     }
     return y.release();

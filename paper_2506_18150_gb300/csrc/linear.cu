@@ -107,34 +107,38 @@ PtMatrix *ptmat_prepare(Ctx *c, const double *W, int rows, int cols, int in_pad,
     return m.release();
 }
 
-Ciphertext *matvec(Ctx *c, const EvalKey *evk, const PtMatrix *m, const Ciphertext *in)
+// The baby-step half of a product (one ModUp of c1, the hoisted baby steps
+// and the BSGS MAC over QP): inner[g][2][plane] for every giant step g with
+// diagonals (need_g[g] set).
+static void baby_products(Ctx *c, const EvalKey *evk, const PtMatrix *m, const Ciphertext *in, u64 *inner,
+                          std::vector<char> &need_g)
 {
     const int l = in->level, N = c->N, nq = l + 1, nl = nq + c->K, dnum = c->dnum(l);
     HCHECK(l == m->level, HELRM_E_LEVEL, "ciphertext level does not match the prepared matrix");
     const size_t plane = (size_t)nl * N;
-    std::vector<char> need_b(m->n1, 0), need_g(m->n2, 0);
+    std::vector<char> need_b(m->n1, 0);
+    need_g.assign(m->n2, 0);
     for (auto &gb : m->gb) {
         need_b[gb.second] = 1;
         need_g[gb.first] = 1;
     }
     // keys first, so a missing key fails before any work
-    std::vector<const SwitchKey *> bkey(m->n1, nullptr), gkey(m->n2, nullptr);
+    std::vector<const SwitchKey *> bkey(m->n1, nullptr);
     for (int b = 1; b < m->n1; b++)
         if (need_b[b]) bkey[b] = rot_key(evk, c->galois(b), l);
     for (int g = 1; g < m->n2; g++)
-        if (need_g[g]) gkey[g] = rot_key(evk, c->galois(g * m->n1), l);
+        if (need_g[g]) rot_key(evk, c->galois(g * m->n1), l);
 
     DevMem digits(c, (size_t)dnum * plane * 8);
     bool any_baby = false;
     for (int b = 1; b < m->n1; b++) any_baby |= need_b[b] != 0;
     if (any_baby) ks_modup(c, in->c1(), l, digits.u());   // hoisted: one ModUp for all baby steps
-    DevMem inner(c, (size_t)m->n2 * 2 * plane * 8);
     if (m->n1 <= 64 && m->n2 <= 8) {
         // baby steps formed in registers inside the MAC (no baby buffer)
         std::vector<u64> gals(m->n1, 1);
         for (int b = 1; b < m->n1; b++)
             if (need_b[b]) gals[b] = c->galois(b);
-        k::bsgs_tma(c, inner.u(), digits.u(), in->c0(), in->c1(), bkey.data(), gals.data(),
+        k::bsgs_tma(c, inner, digits.u(), in->c0(), in->c1(), bkey.data(), gals.data(),
                     m->d_ptrs.as<const u64 *>(), m->d_gb_index.as<int>(), (int)m->gb.size(), m->n1, m->n2, l);
     } else {
         // wide baby-step sets: baby steps materialised over QP, then the tiled MAC
@@ -153,16 +157,30 @@ Ciphertext *matvec(Ctx *c, const EvalKey *evk, const PtMatrix *m, const Cipherte
                                  c->d_pmod_mont.u());
             }
         }
-        k::bsgs_mac(c, inner.u(), baby.u(), (int)m->gb.size(), m->d_ptrs.as<const u64 *>(), m->d_gb_index.as<int>(),
+        k::bsgs_mac(c, inner, baby.u(), (int)m->gb.size(), m->d_ptrs.as<const u64 *>(), m->d_gb_index.as<int>(),
                     m->n2, m->n1, nl, c->qmap(l));
     }
+}
+
+// The giant-step half: the giant steps on the QP inner products, one ModDown
+// of their sum, the rescale (scale: the product's scale before it) and the
+// folds of a wide matrix.
+static Ciphertext *giant_steps(Ctx *c, const EvalKey *evk, const PtMatrix *m, u64 *inner,
+                               const std::vector<char> &need_g, int l, double scale)
+{
+    const int N = c->N, nq = l + 1, nl = nq + c->K, dnum = c->dnum(l);
+    const size_t plane = (size_t)nl * N;
+    std::vector<const SwitchKey *> gkey(m->n2, nullptr);
+    for (int g = 1; g < m->n2; g++)
+        if (need_g[g]) gkey[g] = rot_key(evk, c->galois(g * m->n1), l);
+    DevMem digits(c, (size_t)dnum * plane * 8);
     // the giant steps accumulate into inner_0
-    u64 *acc = inner.u();
+    u64 *acc = inner;
     DevMem c1q(c, (size_t)nq * N * 8);
     if (!need_g[0]) k::zero(c, acc, 2 * plane);
     for (int g = 1; g < m->n2; g++) {
         if (!need_g[g]) continue;
-        const u64 *ig = inner.u() + (size_t)g * 2 * plane;
+        const u64 *ig = inner + (size_t)g * 2 * plane;
         // giant step on a QP ciphertext: ModDown the a-part, ModUp, then one kernel
         // adds the key inner product and phi of the b-part (already over QP) to acc
         const u64 gal = c->galois(g * m->n1);
@@ -170,7 +188,7 @@ Ciphertext *matvec(Ctx *c, const EvalKey *evk, const PtMatrix *m, const Cipherte
         ks_modup(c, c1q.u(), l, digits.u());
         k::ks_inner_auto(c, acc, digits.u(), dnum, gkey[g], l, gal, nullptr, nullptr, ig, true);
     }
-    std::unique_ptr<Ciphertext> o(new_ct(c, l, in->scale * m->pt_scale));
+    std::unique_ptr<Ciphertext> o(new_ct(c, l, scale));
     ks_moddown2(c, acc, l, o->c0(), o->c1());
     std::unique_ptr<Ciphertext> y(ct_rescale(c, o.get()));
     y->scale = m->out_scale;
@@ -181,11 +199,57 @@ Ciphertext *matvec(Ctx *c, const EvalKey *evk, const PtMatrix *m, const Cipherte
         ct_rotate_hoisted(c, evk, y.get(), steps, rs);
         std::vector<std::unique_ptr<Ciphertext>> own;
         for (auto *r : rs) own.emplace_back(r);
-        std::unique_ptr<Ciphertext> acc(ct_add(c, y.get(), own[0].get()));
-        for (size_t i = 1; i < own.size(); i++) acc.reset(ct_add(c, acc.get(), own[i].get()));
-        y = std::move(acc);
+        std::unique_ptr<Ciphertext> acc2(ct_add(c, y.get(), own[0].get()));
+        for (size_t i = 1; i < own.size(); i++) acc2.reset(ct_add(c, acc2.get(), own[i].get()));
+        y = std::move(acc2);
     }
     return y.release();
+}
+
+Ciphertext *matvec(Ctx *c, const EvalKey *evk, const PtMatrix *m, const Ciphertext *in)
+{
+    const int l = in->level;
+    const size_t plane = (size_t)(l + 1 + c->K) * c->N;
+    DevMem inner(c, (size_t)m->n2 * 2 * plane * 8);
+    std::vector<char> need_g;
+    baby_products(c, evk, m, in, inner.u(), need_g);
+    return giant_steps(c, evk, m, inner.u(), need_g, l, in->scale * m->pt_scale);
+}
+
+bool same_shape(const PtMatrix *a, const PtMatrix *b)
+{
+    return a->in_pad == b->in_pad && a->out_pad == b->out_pad && a->D == b->D && a->n1 == b->n1 &&
+           a->n2 == b->n2 && a->level == b->level && a->folds == b->folds && a->pt_scale == b->pt_scale &&
+           a->out_scale == b->out_scale;
+}
+
+// sum_k W_k x_k for matrices of one shape (reading R31): the baby-step
+// products are added over QP, giant step by giant step, and the sum takes one
+// set of giant steps, one ModDown, one rescale and one set of folds.
+Ciphertext *matvec_sum(Ctx *c, const EvalKey *evk, const std::vector<const PtMatrix *> &ms,
+                       const std::vector<const Ciphertext *> &in)
+{
+    HCHECK(!ms.empty() && ms.size() == in.size(), HELRM_E_INVAL, "matvec_sum takes one ciphertext per matrix");
+    if (ms.size() == 1) return matvec(c, evk, ms[0], in[0]);
+    const int l = in[0]->level;
+    for (size_t k2 = 0; k2 < ms.size(); k2++) {
+        HCHECK(same_shape(ms[k2], ms[0]), HELRM_E_PARAM, "matvec_sum: the matrices differ in shape");
+        HCHECK(in[k2]->level == l && in[k2]->scale == in[0]->scale, HELRM_E_SCALE,
+               "matvec_sum: the ciphertexts differ in level or scale");
+    }
+    const PtMatrix *m = ms[0];
+    const int nl = l + 1 + c->K;
+    const size_t plane = (size_t)nl * c->N, words = (size_t)m->n2 * 2 * plane;
+    DevMem total(c, words * 8), part(c, words * 8);
+    k::zero(c, total.u(), words);
+    std::vector<char> need_all(m->n2, 0), need_g;
+    for (size_t k2 = 0; k2 < ms.size(); k2++) {
+        k::zero(c, part.u(), words);
+        baby_products(c, evk, ms[k2], in[k2], part.u(), need_g);
+        for (int g = 0; g < m->n2; g++) need_all[g] |= need_g[g];
+        k::add(c, total.u(), total.u(), part.u(), m->n2 * 2 * nl, c->qmap(l, 0, nl));
+    }
+    return giant_steps(c, evk, m, total.u(), need_all, l, in[0]->scale * m->pt_scale);
 }
 
 }  // namespace helrm

@@ -155,6 +155,15 @@ def wide_spec(interaction: str = "dot") -> DLRMSpec:
     return s
 
 
+def wider_spec(interaction: str = "dot") -> DLRMSpec:
+    """As wide_spec with a 1100-row table in place of the 700-row one: 1127
+    selector slots, three ciphertexts at N = 2^10 (512 + 512 + 103 columns),
+    the first two of one shape."""
+    s = DLRMSpec("wider", 4, [4, 16], [0, 1], [1100, 2000, 3], 4, 16, interaction, threshold=1200)
+    s.top[0] = top_input_width(s)
+    return s
+
+
 def criteo_cards(seed: int = 0, total: float = 33.8e6) -> list:
     """26 log-uniform cardinalities on [3, 1e7]; every k > 1e5 is multiplied by
     one common factor (clamped at 1e7), found by bisection, so the total is
@@ -343,3 +352,18 @@ def int_poly(seed: int, index: int, n: int, bound: int = 1 << 20) -> np.ndarray:
     z = _splitmix64(ctr)
     m = np.uint64(2 * bound + 1)
     return (z % m).astype(np.int64) - bound
+
+
+def dyadic(coeffs, bits: int = 20) -> tuple:
+    """Coefficients rounded to multiples of 2^-bits: exact binary fractions,
+    so a model built from them is the same on every machine (a least-squares
+    fit's last bits depend on the linear-algebra library)."""
+    return tuple(float(np.round(float(a) * 2.0**bits)) / 2.0**bits for a in coeffs)
+
+
+def uci_silu_fixed_spec(seed: int = 0) -> DLRMSpec:
+    """uci_silu_spec with its SiLU coefficients rounded to multiples of 2^-20
+    (dyadic), for the full-size parity fixtures."""
+    s = uci_silu_spec(seed)
+    s.act = dyadic(s.act)
+    return s

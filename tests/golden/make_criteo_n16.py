@@ -1,7 +1,11 @@
 """Writes tests/golden/criteo_n16.json: what the oracle computes for the
 Criteo-shaped DLRM at the full parameter set (N = 2^16, q_0 60-bit + 20 x
 40-bit, K = 3 x 60-bit special primes, alpha = 3), for the full-size GPU
-parity tests (tests/test_gpu_criteo_full.py).
+parity tests (tests/test_gpu_criteo_full.py).  With --model uci_silu it
+writes tests/golden/uci_silu_n16.json, the inference case alone, for the
+UCI-shaped model whose activations are the degree-6 SiLU polynomial (its
+coefficients rounded to multiples of 2^-20, synthetic.uci_silu_fixed_spec, so
+that the model does not depend on the machine's least-squares fit).
 
 Only oracle/ and the seeded input generators run here.  Every input is an
 integer, so the stored results do not depend on the machine: the keys come
@@ -28,7 +32,8 @@ Cases:
       order, on ct_dense = Enc(int_poly(SEED_QUERY, 0)) at lvl_dense (seed
       40) and ct_sel = Enc(int_poly(SEED_QUERY, 1)) at lvl_sel (seed 41).
 
-Usage: python tests/golden/make_criteo_n16.py   (about 13 minutes on 8 cores)
+Usage: python tests/golden/make_criteo_n16.py [--model uci_silu]
+(about 13 minutes on 8 cores for the Criteo-shaped model)
 """
 from __future__ import annotations
 
@@ -45,7 +50,7 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 sys.path.insert(0, os.path.dirname(HERE))
 
-OUT = os.path.join(HERE, "criteo_n16.json")
+OUT = os.path.join(HERE, "{model}_n16.json")
 KEY_SEED = 77
 SEED_MODEL, SEED_QUERY, SEED_MV = 901, 902, 1000
 BOUND = 1 << 20
@@ -74,7 +79,7 @@ def matvec_shapes(c):
     return out
 
 
-def main():
+def main(model: str = "criteo"):
     from helpers import oracle_keys_pool, oracle_params
     from oracle import ckks, dlrm, linear
     from paper_2506_18150_gb300 import synthetic as syn
@@ -82,7 +87,7 @@ def main():
     t0 = time.time()
     pr = syn.PARAMS["full"]
     p = oracle_params(pr)
-    spec = syn.criteo_spec(0)
+    spec = {"criteo": syn.criteo_spec, "uci_silu": syn.uci_silu_fixed_spec}[model](0)
     c = dlrm.compile_model(p, spec, syn.make_weights(spec, 0))
     steps = c.rotation_steps()
     _, keys = oracle_keys_pool(pr, KEY_SEED, steps)
@@ -92,7 +97,7 @@ def main():
                       "lvl_dense": c.lvl_dense, "lvl_sel": c.lvl_sel},
            "cases": {}}
 
-    for k, (name, level, rows, cols, ip, op) in enumerate(matvec_shapes(c)):
+    for k, (name, level, rows, cols, ip, op) in enumerate(matvec_shapes(c) if model == "criteo" else []):
         t1 = time.time()
         pm = linear.prepare(p, np.ones((rows, cols)), ip, op, level, p.delta, p.delta)
         for j, key in enumerate(pm.ordered_keys()):
@@ -139,10 +144,14 @@ def main():
     d.update({"level": y.level, "n_plaintexts": len(pts)})
     res["cases"]["inference"] = d
     print(f"inference in {time.time() - t1:.0f} s", flush=True)
-    with open(OUT, "w") as f:
+    out = OUT.format(model=model)
+    with open(out, "w") as f:
         json.dump(res, f, indent=1)
-    print(f"wrote {OUT} in {time.time() - t0:.0f} s")
+    print(f"wrote {out} in {time.time() - t0:.0f} s")
 
 
 if __name__ == "__main__":
-    main()
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--model", default="criteo", choices=["criteo", "uci_silu"])
+    main(ap.parse_args().model)

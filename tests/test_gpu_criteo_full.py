@@ -117,3 +117,29 @@ def test_criteo_products_with_radix4_transforms(monkeypatch):
     _, evk = H.helrm_keygen(ctx, R["key_seed"], H.helrm_model_rotations(ctx, model))
     for name in ("matvec_13_512x256", "matvec_1_256x1"):
         test_criteo_matvec_full((ctx, model, evk, 1 << pr["log_n"], 2.0 ** pr["log2_scale"]), name)
+
+
+def test_criteo_batched_and_served_full(full):
+    """The lockstep batch path and the serving loop at full size: a batch of
+    two queries (the stored query twice, one key set) and a served trace of
+    two requests give the stored oracle words for every query."""
+    from paper_2506_18150_gb300 import helrm as H
+    from paper_2506_18150_gb300 import synthetic as syn
+    ctx, model, evk, n, delta = full
+    case = GOLD["cases"]["inference"]
+    H.helrm_model_import_plaintexts(ctx, model, np.stack([syn.int_poly(R["seed_model"], k, n, R["bound"])
+                                                          for k in range(case["n_plaintexts"])]))
+    md, ms = (syn.int_poly(R["seed_query"], j, n, R["bound"]) for j in range(2))
+    cd = H.helrm_encrypt(ctx, evk, H.helrm_pt_import(ctx, md, R["lvl_dense"], delta), 40)
+    cs = H.helrm_encrypt(ctx, evk, H.helrm_pt_import(ctx, ms, R["lvl_sel"], delta), 41)
+    batch = H.helrm_batch_create(ctx, model, [evk, evk])
+    for y in H.helrm_infer_batch(ctx, batch, [cd, cd], [cs, cs]):
+        coeffs, lvl, _ = H.helrm_ct_export(ctx, y)
+        _check(coeffs, lvl, case)
+    srv = H.helrm_server_create(ctx, 2, 2, 0)
+    H.helrm_server_add_client(ctx, srv, model, evk)
+    outs, lat, st = H.helrm_server_run(ctx, srv, [0.0, 0.0, 0.0], [0, 0, 0], [cd, cd, cd], [cs, cs, cs])
+    assert st["max_batch"] == 2                      # the first request alone, then a batch of two
+    for y in outs:
+        coeffs, lvl, _ = H.helrm_ct_export(ctx, y)
+        _check(coeffs, lvl, case)

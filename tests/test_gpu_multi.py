@@ -117,3 +117,69 @@ def test_wide_dlrm_with_two_selector_ciphertexts():
     out_o = dlrm.infer(p, keys_o, c, ckks.encrypt(p, keys_o, md, c.lvl_dense, p.delta, 300),
                        [ckks.encrypt(p, keys_o, m, c.lvl_sel, p.delta, 301 + k) for k, m in enumerate(ms)])
     assert_ct_equal(ctx, H.helrm_infer_multi(ctx, evk, model, cd, cs), out_o)
+
+
+def test_three_ciphertext_lookup_and_dlrm_share_giant_steps():
+    """Three selector ciphertexts, the first two of one shape, so their
+    products share one set of giant steps, ModDown, rescale and folds
+    (reading R31).  The lookup at N = 2^12 (tables of 3000 and 1500 rows:
+    2048 + 2048 + 404 columns) and the wider DLRM at N = 2^10 (1127 slots:
+    512 + 512 + 103), one query and a lockstep batch of two, bit-exact
+    against the oracle with its integer plaintexts."""
+    from oracle import ckks, dlrm, linear
+    from paper_2506_18150_gb300 import helrm as H
+    from paper_2506_18150_gb300 import synthetic as syn
+    pr = syn.reduced_params(12, 3)
+    p = oracle_params(pr)
+    cards, base = [3000, 1500], 4096
+    rng = np.random.default_rng(32)
+    tables = [[rng.uniform(-0.05, 0.05, (k, 16)).astype(np.float32)] for k in cards]
+    ctx = gpu_ctx(pr)
+    emb = H.helrm_emb_prepare(ctx, cards, base, 0, 16, tables, 0, 32, 2, p.delta, p.delta)
+    assert H.helrm_emb_chunks(ctx, emb) == 3
+    M = dlrm.embedding_matrix(cards, base, tables, 0, 32)
+    pms = dlrm.prepare_multi(p, M, 32, 2, p.delta, p.delta)
+    assert dlrm.lookup_groups(pms) == [[0, 1], [2]]
+    mats = [H.helrm_emb_matrix(ctx, emb, c) for c in range(3)]
+    steps = sorted(set().union(*[set(H.helrm_ptmat_rotations(ctx, m)) for m in mats]))
+    sk, evk = H.helrm_keygen(ctx, 18, steps)
+    _, keys_o = ckks.keygen(p, 18, rot_steps=steps, relin=False)
+    for c in range(3):
+        H.helrm_ptmat_import(ctx, mats[c], np.stack([pms[c].pts[k] for k in pms[c].ordered_keys()]).astype(np.int64))
+    sel = dlrm.selector_vector(cards, base, (2999, 1499))
+    ms = [ckks.encode_real(p, xi, p.delta) for xi in dlrm.chunk_slots(sel, p.n)]
+    cts = [H.helrm_encrypt(ctx, evk, H.helrm_pt_import(ctx, m, 2, p.delta), 70 + c) for c, m in enumerate(ms)]
+    cts_o = [ckks.encrypt(p, keys_o, m, 2, p.delta, 70 + c) for c, m in enumerate(ms)]
+    y = H.helrm_embedding_lookup_multi(ctx, evk, emb, cts)
+    assert_ct_equal(ctx, y, dlrm.lookup_multi(p, keys_o, pms, cts_o))
+    want = np.concatenate(dlrm.embedding_cleartext(cards, base, tables, (2999, 1499)))
+    assert np.max(np.abs(H.helrm_decrypt(ctx, sk, y, 32) - want)) < 1e-3
+
+    pr = syn.reduced_params(10, 5)
+    p = oracle_params(pr)
+    spec = syn.wider_spec()
+    w = syn.make_weights(spec, 0)
+    ctx = gpu_ctx(pr)
+    model = H.helrm_model_create(ctx, spec, w)
+    c = dlrm.compile_model(p, spec, w)
+    assert H.helrm_model_info(ctx, model)["n_sel"] == c.n_sel() == 3
+    assert dlrm.lookup_groups(c.emb_chunks) == [[0, 1], [2]]
+    H.helrm_model_import_plaintexts(ctx, model, np.stack([np.asarray(x, dtype=np.int64) for x in c.plaintexts()]))
+    steps = H.helrm_model_rotations(ctx, model)
+    assert steps == c.rotation_steps()
+    sk, evk = H.helrm_keygen(ctx, 3, steps)
+    _, keys_o = ckks.keygen(p, 3, rot_steps=steps)
+    dense, idx = syn.make_queries(spec, 1, seed=8)
+    xd, xs = dlrm.query_slots(p, c, dense[0], idx[0])
+    md = ckks.encode_real(p, xd, p.delta)
+    msel = [ckks.encode_real(p, x, p.delta) for x in xs]
+    cd = H.helrm_encrypt(ctx, evk, H.helrm_pt_import(ctx, md, c.lvl_dense, p.delta), 400)
+    cs = [H.helrm_encrypt(ctx, evk, H.helrm_pt_import(ctx, m, c.lvl_sel, p.delta), 401 + k) for k, m in enumerate(msel)]
+    out_o = dlrm.infer(p, keys_o, c, ckks.encrypt(p, keys_o, md, c.lvl_dense, p.delta, 400),
+                       [ckks.encrypt(p, keys_o, m, c.lvl_sel, p.delta, 401 + k) for k, m in enumerate(msel)])
+    assert_ct_equal(ctx, H.helrm_infer_multi(ctx, evk, model, cd, cs), out_o)
+    batch = H.helrm_batch_create(ctx, model, [evk, evk])
+    for yb in H.helrm_infer_batch(ctx, batch, [cd, cd], [cs, cs]):
+        assert_ct_equal(ctx, yb, out_o)
+    lg, _ = H.helrm_infer_e2e(ctx, sk, evk, model, dense, idx, 9)
+    assert abs(lg[0] - dlrm.dlrm_cleartext(spec, w, dense[0], idx[0])[0]) < 1e-3

@@ -231,6 +231,41 @@ def test_multi_ciphertext_lookup_matches_gather(small_params):
         assert np.max(np.abs(got - want)) < 1e-4, idx
 
 
+def test_multi_ciphertext_lookup_shares_giant_steps(small_params):
+    """Three selector ciphertexts (plain tables of 600 and 500 rows at n = 512
+    slots: 512 + 512 + 76 columns): the two full chunks have the same shape
+    and share one set of giant steps, ModDown, rescale and folds
+    (linear.matvec_sum, reading R31).  The lookup decrypts to the gathered
+    rows; a one-matrix matvec_sum is matvec word for word; and the shared
+    tail decrypts to the sum of the two separate products."""
+    p = small_params
+    cards, base = [600, 500], 1024
+    rng = np.random.default_rng(13)
+    tables = [[rng.uniform(-0.05, 0.05, (k, dlrm.DIM)).astype(np.float32)] for k in cards]
+    M = dlrm.embedding_matrix(cards, base, tables, 0, 2 * dlrm.DIM)
+    pms = dlrm.prepare_multi(p, M, 2 * dlrm.DIM, 3, p.delta, p.delta)
+    assert [pm.layout.in_pad for pm in pms] == [512, 512, 128]
+    assert dlrm.lookup_groups(pms) == [[0, 1], [2]]
+    steps = sorted(set().union(*[linear.rotation_steps(pm) for pm in pms]))
+    sk, keys = ckks.keygen(p, 22, rot_steps=steps, relin=False)
+    idx = (599, 3)
+    sel = dlrm.selector_vector(cards, base, idx)
+    cts = [ckks.encrypt(p, keys, ckks.encode_real(p, xi, p.delta), 3, p.delta, 50 + c)
+           for c, xi in enumerate(dlrm.chunk_slots(sel, p.n))]
+    y = dlrm.lookup_multi(p, keys, pms, cts)
+    got = ckks.decrypt(p, sk, y)[: 2 * dlrm.DIM]
+    want = np.concatenate(dlrm.embedding_cleartext(cards, base, tables, idx))
+    assert np.max(np.abs(got - want)) < 1e-4
+    one, alone = linear.matvec_sum(p, keys, [pms[2]], [cts[2]]), linear.matvec(p, keys, pms[2], cts[2])
+    assert np.array_equal(one.c0, alone.c0) and np.array_equal(one.c1, alone.c1)
+    both = linear.matvec_sum(p, keys, pms[:2], cts[:2])
+    sep = ckks.add(p, linear.matvec(p, keys, pms[0], cts[0]), linear.matvec(p, keys, pms[1], cts[1]))
+    assert not np.array_equal(both.c0, sep.c0)          # a different rounding path ...
+    assert np.max(np.abs(ckks.decrypt(p, sk, both) - ckks.decrypt(p, sk, sep))) < 1e-5   # ... to the same sum
+    with pytest.raises(ValueError):
+        linear.matvec_sum(p, keys, [pms[0], pms[2]], [cts[0], cts[2]])
+
+
 def test_threshold_policy_layout():
     """Sec. 5.2's policy: a table is digit-decomposed (base p) only if it has
     more rows than the threshold; with the threshold at p this is the plain

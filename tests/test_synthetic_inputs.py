@@ -25,3 +25,12 @@ def test_int_poly_range_determinism_and_independence():
     assert not np.array_equal(a, syn.int_poly(8, 3, 1 << 12, 1 << 20))
     assert np.array_equal(a[:100], syn.int_poly(7, 3, 100, 1 << 20))      # a prefix of the same stream
     assert abs(a.mean()) < 3 * (1 << 20) / np.sqrt(3 * len(a))           # centred
+
+
+def test_dyadic_coefficients_are_exact_binary_fractions():
+    a = syn.uci_silu_spec(0).act
+    b = syn.uci_silu_fixed_spec(0).act
+    assert len(a) == len(b)
+    for x, y in zip(a, b):
+        assert abs(x - y) <= 2.0**-21 and float(y * 2**20).is_integer()
+    assert syn.dyadic((0.5, -0.25, 1e-9)) == (0.5, -0.25, 0.0)

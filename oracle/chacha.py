@@ -20,6 +20,11 @@ Samplers (the reading of the paper's unspecified distributions):
   CBD(21)       : coefficient i takes words 2i, 2i+1 as x = w0 | w1 << 32 and
                   returns popcount(x & M) - popcount((x >> 21) & M),
                   M = 2^21 - 1 (standard deviation sqrt(10.5) ~ 3.24, |e| <= 21).
+  sparse ternary: exactly h non-zero coefficients (the secret of the
+                  bootstrapping key set).  Word i is the priority of
+                  coefficient i; the h coefficients with the smallest
+                  (priority, i) pairs are non-zero, and coefficient i is
+                  +1 if bit 0 of word n + i is 0, else -1.
 """
 from __future__ import annotations
 
@@ -29,6 +34,7 @@ from . import ring
 
 # Stream purposes (nonce word 0).
 SK, PK_A, PK_E, KSK_A, KSK_E, ENC_V, ENC_E0, ENC_E1 = 1, 2, 3, 4, 5, 6, 7, 8
+SK_SPARSE = 9
 
 _CONST = (0x61707865, 0x3320646E, 0x79622D32, 0x6B206574)   # "expand 32-byte k"
 
@@ -116,3 +122,15 @@ def cbd21(seed: int, purpose: int, index: int, n: int) -> np.ndarray:
     x = w[:, 0] | (w[:, 1] << np.uint64(32))
     m = np.uint64((1 << 21) - 1)
     return _popcount64(x & m) - _popcount64((x >> np.uint64(21)) & m)
+
+
+def sparse_ternary(seed: int, purpose: int, index: int, n: int, h: int) -> np.ndarray:
+    """h coefficients in {-1, +1} at the h smallest (priority, position) pairs, the rest 0."""
+    if not 0 < h <= n:
+        raise ValueError("need 0 < h <= n")
+    w = stream_words(seed, purpose, index, 2 * n).astype(np.int64)
+    order = np.lexsort((np.arange(n), w[:n]))          # by priority, then by position
+    s = np.zeros(n, dtype=np.int64)
+    pos = order[:h]
+    s[pos] = 1 - 2 * (w[n + pos] & 1)
+    return s

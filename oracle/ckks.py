@@ -70,6 +70,10 @@ class Params:
         """Rotation by `step` slots (left) is X -> X^(5^step mod 2N)."""
         return pow(5, step % self.n, 2 * self.N)
 
+    def conj_galois(self) -> int:
+        """Complex conjugation of every slot is X -> X^(2N-1) = X^(-1)."""
+        return 2 * self.N - 1
+
 
 # EXACT = True: every ring product is the O(N^2) schoolbook negacyclic
 # convolution (the product's definition, X^N = -1) instead of the textbook NTT;
@@ -128,6 +132,32 @@ def encode_real(p: Params, z, scale: float) -> np.ndarray:
     w[e] = v
     w[(2 * p.N - e) % (2 * p.N)] = np.conj(v)
     m = np.fft.fft(w)[: p.N].real / p.N
+    return round_half_away(scale * m)
+
+
+def encode_complex(p: Params, z, scale: float) -> np.ndarray:
+    """encode_real for complex slots: the same length-2N FFT of the vector
+    that holds z_j at 5^j and conj(z_j) at -5^j (mod 2N), whose real part is
+    sigma^-1(z) scaled by N."""
+    v = np.zeros(p.n, dtype=np.complex128)
+    z = np.asarray(z, dtype=np.complex128)
+    v[: z.shape[0]] = z
+    e = _slot_exponents(p)
+    w = np.zeros(2 * p.N, dtype=np.complex128)
+    w[e] = v
+    w[(2 * p.N - e) % (2 * p.N)] = np.conj(v)
+    m = np.fft.fft(w)[: p.N].real / p.N
+    return round_half_away(scale * m)
+
+
+def encode_complex_direct(p: Params, z, scale: float) -> np.ndarray:
+    """m_k = round(scale (1/N) sum_j 2 Re(z_j zeta^(-5^j k))), the definition (small N only)."""
+    zz = np.zeros(p.n, dtype=np.complex128)
+    z = np.asarray(z, dtype=np.complex128)
+    zz[: z.shape[0]] = z
+    e = _slot_exponents(p)
+    ang = np.pi * np.outer(e, np.arange(p.N)) / p.N
+    m = 2.0 * np.real(zz[:, None] * np.exp(-1j * ang)).sum(axis=0) / p.N
     return round_half_away(scale * m)
 
 
@@ -213,7 +243,12 @@ class Keys:
     rot: dict = field(default_factory=dict)       # galois element -> SwitchKey
 
 
-def secret_key(p: Params, seed: int) -> SecretKey:
+def secret_key(p: Params, seed: int, h: int = 0) -> SecretKey:
+    """Dense ternary CBD(1) secret (h = 0), or exactly h coefficients in
+    {-1, +1} (h > 0): the sparse secret a bootstrapping key set needs, so
+    that the multiple of q_0 that ModRaise adds stays small (|I| <= (h+1)/2)."""
+    if h:
+        return SecretKey(chacha.sparse_ternary(seed, chacha.SK_SPARSE, 0, p.N, h))
     return SecretKey(chacha.ternary(seed, chacha.SK, 0, p.N))
 
 
@@ -254,8 +289,10 @@ def switch_key(p: Params, seed: int, sk: SecretKey, s_prime_mod: np.ndarray, key
     return SwitchKey(bs, as_)
 
 
-def keygen(p: Params, seed: int, rot_steps=(), relin: bool = True):
-    sk = secret_key(p, seed)
+def keygen(p: Params, seed: int, rot_steps=(), relin: bool = True, h: int = 0, conj: bool = False):
+    """Secret, public, relinearisation and rotation keys; with conj the key of
+    the conjugation X -> X^(2N-1) as well (its key id is that element)."""
+    sk = secret_key(p, seed, h)
     pk_b, pk_a = public_key(p, seed, sk)
     keys = Keys(seed, pk_b, pk_a)
     mods = p.qp_mods(p.L)
@@ -269,6 +306,9 @@ def keygen(p: Params, seed: int, rot_steps=(), relin: bool = True):
             continue
         sk_rot = ring.from_signed(automorphism_signed(p, sk.s, k), mods)
         keys.rot[k] = switch_key(p, seed, sk, sk_rot, k)
+    if conj:
+        k = p.conj_galois()
+        keys.rot[k] = switch_key(p, seed, sk, ring.from_signed(automorphism_signed(p, sk.s, k), mods), k)
     return sk, keys
 
 
@@ -461,6 +501,24 @@ def rotate_hoisted(p: Params, keys: Keys, a: Ct, steps) -> dict:
 
 def rotate(p: Params, keys: Keys, a: Ct, step: int) -> Ct:
     return rotate_hoisted(p, keys, a, [step])[step]
+
+
+def apply_galois(p: Params, keys: Keys, a: Ct, k: int) -> Ct:
+    """X -> X^k with the key switch from phi_k(s) back to s, in the order of
+    a hoisted rotation: ModUp of c1, phi_k on the extended digits, the key
+    inner product, ModDown, plus phi_k(c0).  (ModUp and phi_k do not commute
+    word for word: the base conversion of a negated residue differs.)"""
+    digits = modup(p, a.c1, a.level)
+    qp = p.qp_mods(a.level)
+    mods = p.q_mods(a.level)
+    u0, u1 = ks_inner(p, [automorphism(p, d, k, qp) for d in digits], _key_for(keys, k), a.level)
+    c0 = ring.add(automorphism(p, a.c0, k, mods), moddown(p, u0, a.level), mods)
+    return Ct(c0, moddown(p, u1, a.level), a.level, a.scale)
+
+
+def conjugate(p: Params, keys: Keys, a: Ct) -> Ct:
+    """Every slot z_j -> conj(z_j)."""
+    return apply_galois(p, keys, a, p.conj_galois())
 
 
 def tensor(p: Params, a: Ct, b: Ct):

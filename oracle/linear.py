@@ -51,8 +51,8 @@ def bsgs_split(D: int):
 
 
 def extended_diagonals(W: np.ndarray, in_pad: int, out_pad: int, n: int) -> np.ndarray:
-    """[D, n] float64 array of diag_i[j] = Wpad[j mod out_pad, (j+i) mod in_pad]."""
-    Wp = np.zeros((out_pad, in_pad))
+    """[D, n] array of diag_i[j] = Wpad[j mod out_pad, (j+i) mod in_pad] (float64, or complex128 for a complex W)."""
+    Wp = np.zeros((out_pad, in_pad), dtype=np.result_type(W.dtype, np.float64))
     Wp[: W.shape[0], : W.shape[1]] = W
     D = min(in_pad, out_pad)
     j = np.arange(n)
@@ -118,17 +118,26 @@ def prepare(p: ckks.Params, W: np.ndarray, in_pad: int, out_pad: int, level: int
             ct_scale: float, target_scale: float) -> PtMatrix:
     """Encode the diagonals so the rescaled output has scale exactly target_scale:
     pt_scale = q_l * target / ct_scale."""
-    lay = Layout.make(in_pad, out_pad)
-    diags = extended_diagonals(np.asarray(W, dtype=np.float64), in_pad, out_pad, p.n)
     pt_scale = float(p.q[level]) * target_scale / ct_scale
-    pm = PtMatrix(lay, level, pt_scale, target_scale)
+    return prepare_scaled(p, np.asarray(W, dtype=np.float64), in_pad, out_pad, level, pt_scale, target_scale)
+
+
+def prepare_scaled(p: ckks.Params, W: np.ndarray, in_pad: int, out_pad: int, level: int,
+                   pt_scale: float, out_scale: float) -> PtMatrix:
+    """The diagonals of a real or complex W encoded at pt_scale; out_scale is
+    the scale the product declares after its rescale."""
+    lay = Layout.make(in_pad, out_pad)
+    W = np.asarray(W)
+    diags = extended_diagonals(W, in_pad, out_pad, p.n)
+    enc = ckks.encode_complex if np.iscomplexobj(W) else ckks.encode_real
+    pm = PtMatrix(lay, level, pt_scale, out_scale)
     for g in range(lay.n2):
         for b in range(lay.n1):
             dg = diags[g * lay.n1 + b]
             if not np.any(dg):
                 continue
             rot = np.roll(dg, g * lay.n1)            # rot(x, -s)[j] = x[j - s]
-            pm.pts[(g, b)] = ckks.encode_real(p, rot, pt_scale)
+            pm.pts[(g, b)] = enc(p, rot, pt_scale)
     return pm
 
 

@@ -1,0 +1,166 @@
+"""Pins of the oracle's bootstrapping (oracle/boot.py) and the pieces it adds
+to the scheme (complex encoding, the sparse secret, conjugation), each
+against what mathematics fixes: the encoding's definition, brute force,
+closed forms, the decrypted integers of every stage, and the message itself
+after a whole bootstrap.
+
+The chain is the bootstrappable shape at N = 2^10: q_0 60-bit, 4 x 40-bit
+compute primes, 13 x 60-bit primes for the bootstrapping levels, 3 x 60-bit
+special primes, a secret with h = 192 non-zero coefficients."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import boot, chacha, ckks, poly
+
+LOG_N, N_S, H = 10, 64, 192
+Q_BITS = [60] + [40] * 4 + [60] * 13
+
+
+@pytest.fixture(scope="module")
+def setup():
+    p = ckks.Params(LOG_N, Q_BITS, 3, 60, 3, 40.0)
+    b = boot.prepare(p, boot.BootParams(n_s=N_S))
+    sk, keys = ckks.keygen(p, 7, rot_steps=b.rotation_steps(), h=H, conj=True)
+    return p, b, sk, keys
+
+
+@pytest.fixture(scope="module")
+def booted(setup):
+    p, b, sk, keys = setup
+    z = np.random.default_rng(1).uniform(-1, 1, N_S)
+    zz = z[np.arange(p.n) % N_S]
+    ct = ckks.encrypt(p, keys, ckks.encode_real(p, zz, p.delta), 2, p.delta, 11)
+    st = {}
+    out = boot.bootstrap(p, keys, b, ct, st)
+    return zz, ct, st, out
+
+
+def test_encode_complex_is_its_definition():
+    p = ckks.Params(8, [60, 40], 1, 60, 1, 40.0)
+    rng = np.random.default_rng(3)
+    z = rng.normal(size=p.n) + 1j * rng.normal(size=p.n)
+    m = ckks.encode_complex(p, z, 2.0**30)
+    assert np.array_equal(m, ckks.encode_complex_direct(p, z, 2.0**30))
+    assert np.max(np.abs(ckks.decode(p, m, 2.0**30) - z)) < 1e-7
+    x = rng.normal(size=p.n)
+    assert np.array_equal(ckks.encode_complex(p, x, 2.0**30), ckks.encode_real(p, x, 2.0**30))
+
+
+def test_sparse_secret_brute_force():
+    n, h = 512, 37
+    s = chacha.sparse_ternary(9, chacha.SK_SPARSE, 0, n, h)
+    w = [int(v) for v in chacha.stream_words(9, chacha.SK_SPARSE, 0, 2 * n)]
+    chosen = sorted(range(n), key=lambda i: (w[i], i))[:h]
+    want = [0] * n
+    for i in chosen:
+        want[i] = 1 if w[n + i] % 2 == 0 else -1
+    assert s.tolist() == want
+    assert np.count_nonzero(s) == h
+    p = ckks.Params(LOG_N, [60, 40], 1, 60, 1, 40.0)
+    assert np.count_nonzero(ckks.secret_key(p, 4, h=H).s) == H
+    assert np.count_nonzero(ckks.secret_key(p, 4).s) > p.N // 3      # the dense default (about N/2) is unchanged
+
+
+def test_conjugation():
+    p = ckks.Params(LOG_N, [60, 40, 40], 3, 60, 3, 40.0)
+    sk, keys = ckks.keygen(p, 5, relin=False, conj=True)
+    rng = np.random.default_rng(4)
+    z = rng.uniform(-1, 1, p.n) + 1j * rng.uniform(-1, 1, p.n)
+    ct = ckks.encrypt(p, keys, ckks.encode_complex(p, z, p.delta), 2, p.delta, 6)
+    out = ckks.conjugate(p, keys, ct)
+    got = ckks.decode(p, ckks.decrypt_poly(p, sk, out), out.scale)          # complex slots
+    assert np.max(np.abs(got - np.conj(z))) < 1e-6
+
+
+def test_slot_matrix_closed_forms():
+    p = ckks.Params(LOG_N, [60, 40], 1, 60, 1, 40.0)
+    U = boot.slot_matrix(N_S)
+    # 2 Re(U^H U) = 2 n_s I, so t = (U^H w + U^T conj(w)) / (2 n_s) inverts w = U t for real t
+    assert np.max(np.abs(2 * (U.conj().T @ U).real - 2 * N_S * np.eye(2 * N_S))) < 1e-9
+    t = np.random.default_rng(5).integers(-1000, 1000, 2 * N_S)
+    w = U @ t
+    assert np.max(np.abs((U.conj().T @ w + U.T @ np.conj(w)) / (2 * N_S) - t)) < 1e-8
+    # the slots of sum_k t_k X^(g k) are U t (period n_s)
+    g = p.N // (2 * N_S)
+    m = np.zeros(p.N, dtype=np.int64)
+    m[::g] = t
+    assert np.max(np.abs(ckks.decode(p, m, 1.0) - w[np.arange(p.n) % N_S])) < 1e-6
+
+
+def test_cos_fit_and_double_angles():
+    bp = boot.BootParams(n_s=N_S)
+    c = boot.cos_fit(bp.K, bp.r, bp.degree)
+    assert all(c[k] == 0.0 for k in range(1, bp.degree + 1, 2)) and c[bp.degree] != 0.0
+    Y = (bp.K + 0.5) / 2.0**bp.r
+    y = np.linspace(-Y, Y, 100001)
+    assert np.max(np.abs(np.polynomial.polynomial.polyval(y, c) - np.cos(2 * np.pi * y))) < 1e-12
+    u = np.linspace(-bp.K - 0.01, bp.K + 0.01, 200001)
+    v = np.polynomial.polynomial.polyval((u - 0.25) / 2.0**bp.r, c)
+    for _ in range(bp.r):
+        v = 2 * v * v - 1
+    assert np.max(np.abs(v - np.sin(2 * np.pi * u))) < 1e-10
+    assert boot.levels_used(bp) == 1 + poly.depth(16) + 6 + 1 == 13
+
+
+def test_mod_raise_adds_a_small_multiple_of_q0(setup, booted):
+    p, b, sk, keys = setup
+    zz, ct, st, _ = booted
+    low = ckks.decrypt_poly(p, sk, boot.boost(p, ct, b.bp.log2_boost))
+    high = ckks.decrypt_poly(p, sk, st["raised"])
+    q0 = int(p.q[0])
+    diff = [int(hv) - int(lv) for hv, lv in zip(high, low)]
+    assert all(d % q0 == 0 for d in diff)
+    I = np.array([d // q0 for d in diff])
+    assert np.max(np.abs(I)) <= (H + 1) // 2 and np.max(np.abs(I)) >= 1
+    assert st["raised"].level == p.L
+
+
+def test_subsum_is_the_trace(setup, booted):
+    p, b, sk, _ = setup
+    _, _, st, _ = booted
+    g = p.N // (2 * N_S)
+    raised = np.array([float(v) for v in ckks.decrypt_poly(p, sk, st["raised"])])
+    ss = np.array([float(v) for v in ckks.decrypt_poly(p, sk, st["subsum"])])
+    keep = np.arange(p.N) % g == 0
+    q0 = float(p.q[0])
+    assert np.max(np.abs(ss[keep] - g * raised[keep])) / q0 < 1e-6
+    assert np.max(np.abs(ss[~keep])) / q0 < 1e-6
+
+
+def test_coeff_to_slot_and_eval_mod(setup, booted):
+    p, b, sk, _ = setup
+    _, _, st, _ = booted
+    g = p.N // (2 * N_S)
+    u = np.array([float(v) for v in ckks.decrypt_poly(p, sk, st["raised"])])[::g] / float(p.q[0])
+    per = np.arange(p.n) % (2 * N_S)
+    cts = ckks.decrypt(p, sk, st["cts"]).real
+    assert np.max(np.abs(cts - u[per] / 2.0**b.bp.r)) < 1e-10
+    em = ckks.decrypt(p, sk, st["evalmod"]).real
+    assert np.max(np.abs(em - np.sin(2 * np.pi * u[per]))) < 1e-8
+
+
+def test_bootstrap_refreshes_the_message(setup, booted):
+    p, b, sk, _ = setup
+    zz, ct, st, out = booted
+    assert out.level == p.L - boot.levels_used(b.bp) == 4
+    assert abs(math.log2(out.scale) - 40) < 1e-6
+    got = ckks.decrypt(p, sk, out)
+    assert np.max(np.abs(got.real - zz)) < 1e-6
+    assert np.max(np.abs(ckks.decrypt(p, sk, ct).real - zz)) < 1e-6    # the input still decrypts too
+
+
+def test_bootstrap_on_the_forty_bit_chain_runs_at_lower_precision():
+    """The all-40-bit chain of the non-bootstrapped models: CoeffToSlot takes
+    two rescales and EvalMod runs at 2^40, so the double angles amplify the
+    noise and about 4 bits of a unit message survive (the reason for the
+    bootstrappable chain)."""
+    p = ckks.Params(LOG_N, [60] + [40] * 20, 3, 60, 3, 40.0)
+    b = boot.prepare(p, boot.BootParams(n_s=N_S, cts_levels=2, eval_scale=2.0**40))
+    sk, keys = ckks.keygen(p, 7, rot_steps=b.rotation_steps(), h=H, conj=True)
+    z = np.random.default_rng(1).uniform(-1, 1, N_S)[np.arange(p.n) % N_S]
+    out = boot.bootstrap(p, keys, b, ckks.encrypt(p, keys, ckks.encode_real(p, z, p.delta), 1, p.delta, 3))
+    assert out.level == 20 - 14
+    err = np.max(np.abs(ckks.decrypt(p, sk, out).real - z))
+    assert 1e-4 < err < 0.2

@@ -39,6 +39,10 @@ The default line also carries, each timed on the same GPU in the same run:
 --workload served   the request loop at every rate of --rates, 32 + 8 clients.
 --workload tiny     config 1: one 1024 x 16 table in base 32 at N = 2^13, one
                     encrypted lookup per step (lookups/s).
+--workload boot     bootstrapping alone (bootstraps/s): one bootstrap of a
+                    ciphertext with 512-periodic slots per step at N = 2^16 on
+                    the bootstrappable chain; the default line carries the same
+                    measurement as its `boot` key.
 Multi-GPU: replicas (each rank its own clients and queries, no collective);
 value = all ranks' inferences / the slowest rank's time.  Without torchrun,
 --gpus N > 1 starts N ranks itself.
@@ -73,7 +77,7 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="criteo",
-                    choices=["criteo", "uci", "uci_silu", "batched", "served", "tiny"])
+                    choices=["criteo", "uci", "uci_silu", "batched", "served", "tiny", "boot"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="one-query line only (no uci/batched/config4/served keys)")
     ap.add_argument("--requests", type=int, default=1000, help="served: requests per arrival rate")
@@ -201,7 +205,7 @@ def alu_peaks(H, ctx):
 NTT_TRAFFIC = {"workload": "criteo", "bytes_per_launch": 32.53e6, "algorithmic_per_launch": 29.77e6,
                "sha256": {"ntt.cu": "3770ec2c28a75bf1784d58cd26d6dd7e72959c539994d9aa1e08ca1c465ef294",
                           "butterfly.cuh": "c18964e4e06f1b00915ec55936ad0b6bd0ad7a30966d19e64b31cc886fe0e95e",
-                          "core.cuh": "57bfcffaefa942bb2e83815d690472bd4ffe2d270c946ee6bb0a4c318b77cf94"}}
+                          "core.cuh": "9850591e1add3f99728e66f9a632545c7fecc69f2304fcd9fdc62a510748f42b"}}
 
 
 def ntt_traffic(workload):
@@ -754,6 +758,121 @@ def served(E, clients, rates, n_requests, slots, max_batch, frac_uci=0.8):
             "resident_key_bytes": sum(H.helrm_evk_bytes(ctx, c[2]) for c in clients)}
 
 
+BOOT_NS = 512
+
+
+def boot_measure(local, world, K, W, hbm, alu, n_s=BOOT_NS):
+    """Bootstrapping (Sec. 2.1.4; the paper's Criteo models with polynomial
+    activations need 12 or 5 per inference, Sec. 5.4): one bootstrap per step
+    of a ciphertext whose slots repeat with period n_s (512: the widest layer
+    of the Criteo-shaped model), N = 2^16 on the bootstrappable chain (q_0,
+    13 x 40-bit compute primes, 13 x 60-bit bootstrapping primes, 3 special
+    primes), a secret with 192 non-zero coefficients.  value: bootstraps/s
+    with the input ciphertexts resident in HBM; e2e: the input ciphertext
+    imported from pinned host memory, the bootstrap, the output ciphertext
+    exported to pinned host memory."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    from paper_2506_18150_gb300 import helrm as H
+    from paper_2506_18150_gb300 import synthetic as syn
+    stream = torch.cuda.current_stream()
+    pr = syn.boot_params()
+    ctx = H.helrm_ctx_create(pr["log_n"], pr["q_bits"], pr["n_p"], pr["p_bits"], pr["alpha"], pr["log2_scale"],
+                             device=local, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    bt = H.helrm_boot_create(ctx, n_s)
+    info = H.helrm_boot_info(ctx, bt)
+    sk, evk = H.helrm_keygen_ex(ctx, 5, 192, H.helrm_boot_rotations(ctx, bt), conj=True)
+    setup_s = time.perf_counter() - t0
+    n = 1 << (pr["log_n"] - 1)
+    rng = np.random.default_rng(77)
+    zs = [rng.uniform(-1, 1, n_s) for _ in range(K + W)]
+    cts = [H.helrm_encrypt(ctx, evk, H.helrm_encode(ctx, z[np.arange(n) % n_s], 0, 2.0**40), 3 + q)
+           for q, z in enumerate(zs)]
+    outs = [None] * (K + W)
+
+    def step(q):
+        outs[q] = H.helrm_bootstrap(ctx, evk, bt, cts[q])
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+    for q in range(W):
+        step(q)
+    barrier()
+    l0 = H.helrm_ctx_launch_count(ctx)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    ev[0].record(stream)
+    for s in range(K):
+        step(W + s)
+        ev[s + 1].record(stream)
+    torch.cuda.synchronize()
+    launches = (H.helrm_ctx_launch_count(ctx) - l0) / K
+    per = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(K))
+    value, total_ms = job_throughput(K, ev[0].elapsed_time(ev[K]), world)
+    err = max(float(np.max(np.abs(H.helrm_decrypt(ctx, sk, outs[q], n_s) - zs[q]))) for q in range(W, W + K))
+    for q in range(K + W):
+        outs[q] = None
+
+    # e2e: the input ciphertext from pinned host memory, the output back to it
+    L = H.lib()
+    up = ctypes.POINTER(ctypes.c_uint64)
+    host = []
+    for ct in cts:
+        coeffs, lv, sc = H.helrm_ct_export(ctx, ct)
+        host.append((torch.from_numpy(coeffs.reshape(-1).view(np.int64)).pin_memory(), lv, sc))
+    h_out = torch.zeros(2 * (info["level_out"] + 1) << pr["log_n"], dtype=torch.int64).pin_memory()
+
+    def call(st):
+        if st != 0:
+            raise H.HelrmError(st, L.helrm_last_error(ctx.ptr).decode())
+
+    def step_e2e(q):
+        t, lv, sc = host[q]
+        o = ctypes.c_void_p()
+        call(L.helrm_ct_import(ctx.ptr, ctypes.cast(t.data_ptr(), up), lv, ctypes.c_double(sc), ctypes.byref(o)))
+        y = H.helrm_bootstrap(ctx, evk, bt, H.Handle(o.value, ctx))
+        call(L.helrm_ct_export(ctx.ptr, y.ptr, ctypes.cast(h_out.data_ptr(), up), None, None))
+    for q in range(W):
+        step_e2e(q)
+    barrier()
+    e2e_value, _ = job_throughput(K, _timed(lambda: [step_e2e(W + s) for s in range(K)]), world)
+
+    H.helrm_ctx_profile(ctx, True)
+    n_prof = min(K, 3)
+    for s in range(n_prof):
+        step(W + s)
+    rep = H.helrm_ctx_profile_report(ctx)
+    H.helrm_ctx_profile(ctx, False)
+    roof = roofline(rep, n_prof, pr["log_n"], hbm[0], hbm[1], alu, "boot")
+    out = {"value": value, "unit": "bootstraps/s", "ms_per_step": total_ms / K,
+           "latency_ms": {"p50": per[len(per) // 2], "min": per[0], "max": per[-1]},
+           "launches_per_step": launches, "max_abs_err": err, "setup_s": setup_s,
+           "levels": {"in": 0, "top": info["level_top"], "out": info["level_out"]},
+           "e2e": {"value": e2e_value, "unit": "bootstraps/s", "h2d_bytes_per_step": 8 * host[0][0].numel(),
+                   "d2h_bytes_per_step": 8 * h_out.numel(),
+                   "api": "helrm_ct_import (level-0 ciphertext, pinned host memory) + helrm_bootstrap + "
+                          "helrm_ct_export (refreshed ciphertext to pinned host memory)"},
+           "config": {"workload": f"bootstrapping of n_s={n_s} periodic real slots, one per step (ModRaise, SubSum, "
+                                  f"CoeffToSlot on the ciphertext and its conjugate, EvalMod: degree-16 cosine and "
+                                  f"6 double angles, SlotToCoeff)",
+                      "ckks": "N=2^16, q0 60-bit + 13x40-bit + 13x60-bit, K=3x60-bit special, alpha=3, "
+                              "secret h=192, Delta=2^40",
+                      "l2": "no flush: each step streams GBs of keys and diagonals (>> 129 MB L2)"},
+           "roofline": roof}
+    del bt, sk, evk, cts, host
+    gc.collect()
+    del ctx
+    gc.collect()
+    return out
+
+
 def base_line(E, args, cfg):
     return {"metric": METRIC, "unit": UNIT, "n_gpus": E.world, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
@@ -781,6 +900,7 @@ def run_ours(args):
         extras["served"] = served(E, clients, [100.0, 200.0], 300, args.slots, args.max_batch)
         del clients
         gc.collect()
+        extras["boot"] = boot_measure(E.local, E.world, min(K, 10), min(W, 3), hbm, alu)
     clk = clocks.stop()
     if E.rank == 0:
         line = base_line(E, args, cfg)
@@ -843,6 +963,54 @@ def run_served(args):
                      "clocks": clk, "gpu_launches": r["gpu_launches"], "rates": r["rates"]})
         print(json.dumps(line), flush=True)
     E.close()
+
+
+def run_boot(args):
+    """--workload boot: bootstrapping alone (boot_measure), with the oracle's
+    bounded CPU sample beside it."""
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2506_18150_gb300 import helrm as H
+    from paper_2506_18150_gb300 import synthetic as syn
+    hbm = hbm_peak()
+    pr = syn.PARAMS["full"]
+    actx = H.helrm_ctx_create(pr["log_n"], pr["q_bits"], pr["n_p"], pr["p_bits"], pr["alpha"], pr["log2_scale"],
+                              device=local, stream=torch.cuda.current_stream().cuda_stream)
+    alu = alu_peaks(H, actx)
+    del actx
+    clocks = ClockSampler(local)
+    clocks.start()
+    r = boot_measure(local, world, args.steps, args.warmup, hbm, alu)
+    clk = clocks.stop()
+    if rank == 0:
+        line = {"metric": "bootstraps/s", "value": r["value"], "unit": "bootstraps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+                "data": "synthetic (seeded uniform slots in [-1, 1])", "config": dict(r["config"]),
+                "latency_ms": r["latency_ms"], "max_abs_err": r["max_abs_err"], "levels": r["levels"],
+                "clocks": clk, "gpu_launches": int(r["launches_per_step"] * args.steps), "e2e": r["e2e"],
+                "roofline": r["roofline"]}
+        line["config"]["parallelism"] = f"replicas x{world}"
+        if world == 1 and not args.no_cpu_baseline:
+            env = dict(os.environ)
+            env.pop("CUDA_VISIBLE_DEVICES", None)
+            try:
+                p = subprocess.run([sys.executable, "-m", "oracle.bench_sample", "--workload", "boot"], cwd=ROOT,
+                                   capture_output=True, text=True, timeout=900, env=env)
+                d = json.loads(p.stdout.strip().splitlines()[-1])
+                line["cpu_baseline"] = {"value": 1.0 / d["est_full_s_per_boot"], "unit": "bootstraps/s",
+                                        "cores": d["cores"], "kind": "oracle", "sample": d["sample"]}
+            except Exception as e:  # noqa: BLE001
+                line["cpu_baseline"] = {"value": None, "unit": "bootstraps/s", "kind": "oracle",
+                                        "sample": f"failed: {e}"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 def run_tiny(args):
@@ -969,6 +1137,8 @@ def main():
         run_served(args)
     elif args.workload == "tiny":
         run_tiny(args)
+    elif args.workload == "boot":
+        run_boot(args)
     else:
         run_ours(args)
 

@@ -526,6 +526,77 @@ helrm_status helrm_server_run(helrm_ctx *ctx, helrm_server *s, uint32_t n, const
 helrm_status helrm_rescale_noalloc(helrm_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int32_t level,
                                    uint32_t n_polys);
 
+/* ----------------------------------------------------- bootstrapping (Sec. 2.1.4) */
+/* The paper refreshes levels by bootstrapping (Sec. 2.1.4; 12 or 5 bootstraps
+ * in its Criteo models, Sec. 5.4) without giving the steps; the library runs
+ * the standard pipeline for a ciphertext whose real slots are periodic with
+ * period n_s (2 n_s <= N/2):
+ *   boost (x 2^log2_boost at level 0), ModRaise (the level-0 residues,
+ *   centred, as residues of q_0..q_L), SubSum (ct += rot(ct, n_s 2^i) up to
+ *   N/2: the trace onto X^(N/(2 n_s))), CoeffToSlot (two BSGS products of
+ *   the n_s x 2 n_s slot matrix U[i][k] = exp(i pi (5^i k mod 4 n_s) /
+ *   (2 n_s)): U^H on the ciphertext and U^T on its conjugate, giant steps
+ *   shared; the slots, period 2 n_s, then hold the coefficients over q_0 and
+ *   2^r), EvalMod (minus 1/(4 2^r), an even polynomial fit of cos(2 pi y) on
+ *   |y| <= (K + 1/2)/2^r, r double angles 2c^2 - 1: sin(2 pi u)) and
+ *   SlotToCoeff (U times q_0 / (2 pi 2^log2_boost s_ref), one fold).
+ * It consumes cts_levels + depth(degree) + r + 1 levels from the top
+ * (depth as for helrm_poly_eval).  Precision needs EvalMod at about 2^60:
+ * the bootstrappable chain puts 60-bit primes at the top (cts_levels = 1,
+ * eval_scale = 2^60); on an all-40-bit chain (cts_levels = 2, eval_scale =
+ * 2^40) about 4 bits of a unit message survive.  The keys must come from a
+ * sparse secret (helrm_keygen_ex, h about 192 for K = 24) with the rotations
+ * of helrm_boot_rotations and the conjugation key. */
+typedef struct helrm_boot helrm_boot;
+typedef struct {
+    uint32_t n_s;          /* slot period (power of two, 2 n_s <= N/2) */
+    uint32_t K;            /* |I| the sine covers (about 6 sqrt(h/12)) */
+    uint32_t r;            /* double angles */
+    uint32_t degree;       /* even degree of the cosine fit */
+    uint32_t log2_boost;   /* the message is multiplied by 2^log2_boost at level 0 */
+    uint32_t cts_levels;   /* 1 or 2 rescales after CoeffToSlot */
+    double s_ref;          /* input scale the SlotToCoeff constant assumes */
+    double eval_scale;     /* scale EvalMod runs at */
+    const double *coeffs;  /* degree + 1 power-basis coefficients in y, or NULL: the library's
+                              interpolant at the degree + 1 Chebyshev points of the interval */
+} helrm_boot_desc;
+/* Encodes the three matrices (CoeffToSlot A and B at level L, SlotToCoeff at
+ * the level EvalMod ends on) on the device.  HELRM_E_PARAM if the chain is
+ * too short, HELRM_E_INVAL for other bad parameters. */
+helrm_status helrm_boot_create(helrm_ctx *ctx, const helrm_boot_desc *desc, helrm_boot **out);
+/* info_out[6]: n_s, top level, SlotToCoeff level, output level, number of
+ * encoded diagonals (A, then B, then S), degree. */
+helrm_status helrm_boot_info(const helrm_boot *b, uint32_t *info_out);
+/* The slot rotations the keys must cover (SubSum, the BSGS steps, the fold). */
+helrm_status helrm_boot_rotations(const helrm_boot *b, int32_t *steps_out, uint32_t *n_out);
+/* The cosine polynomial in use (degree + 1 values). */
+helrm_status helrm_boot_coeffs(const helrm_boot *b, double *coeffs_out, uint32_t n);
+/* Borrowed matrix handles (0: CoeffToSlot on the ciphertext, 1: on its
+ * conjugate, 2: SlotToCoeff), valid while b lives; for
+ * helrm_ptmat_import / helrm_ptmat_export. */
+helrm_status helrm_boot_matrix(const helrm_boot *b, uint32_t which, helrm_ptmat **out);
+/* out = the refreshed ciphertext at the output level, scale about Delta
+ * (times in->scale / s_ref), slots decoding to the input's.  The input may
+ * be at any level (it is dropped to level 0); it is not modified.  stages
+ * (optional, NULL or 5 entries) receives copies of the intermediate
+ * ciphertexts: after ModRaise, SubSum, CoeffToSlot, EvalMod, and the output;
+ * the caller frees them.  HELRM_E_NOKEY without the rotation or conjugation
+ * keys. */
+helrm_status helrm_bootstrap(helrm_ctx *ctx, const helrm_evk *evk, const helrm_boot *b, const helrm_ct *in,
+                             helrm_ct **out, helrm_ct **stages);
+/* helrm_keygen with a choice of secret: hamming_weight = 0 is the dense
+ * ternary secret of helrm_keygen (the same keys); h > 0 gives exactly h
+ * coefficients in {-1, +1} (ChaCha20 stream words 0..N-1 rank the positions,
+ * the h smallest (word, position) pairs are non-zero, bit 0 of word N + i is
+ * the sign of position i).  conj != 0 adds the key of X -> X^(2N-1). */
+helrm_status helrm_keygen_ex(helrm_ctx *ctx, uint64_t seed, uint32_t hamming_weight, const int32_t *rot_steps,
+                             uint32_t n_rot, int conj, helrm_sk **sk_out, helrm_evk **evk_out);
+/* X -> X^(2N-1) with the key switch: every slot conjugated. */
+helrm_status helrm_conjugate(helrm_ctx *ctx, const helrm_evk *evk, const helrm_ct *a, helrm_ct **out);
+/* The diagonals of a prepared matrix as centred coefficients (limb 0,
+ * count x N int64, the order of helrm_ptmat_import). */
+helrm_status helrm_ptmat_export(helrm_ctx *ctx, const helrm_ptmat *m, int64_t *coeffs, uint32_t count);
+
 /* --------------------------------------------------------------- misc */
 /* Release any handle (context last; handles must not outlive their context). */
 void helrm_free(void *handle);

@@ -218,6 +218,55 @@ def run_tiny(steps: int = 3, exact: bool = False):
                                         f"median {med:.3f} s"}
 
 
+def run_boot(log_n: int = 12, n_s: int = 512, reps: int = 1):
+    """One bootstrap (oracle/boot.py) on the bootstrappable chain (q_0, 13 x
+    40-bit, 13 x 60-bit, 3 special primes: the same limbs per operation as at
+    N = 2^16) at N = 2^log_n, n_s slots, keys made before the timing.  Each
+    stage is timed; SubSum takes log2(N / (2 n_s)) rotations, so its time is
+    scaled to the full size's count before the ring-product ratio is applied."""
+    from paper_2506_18150_gb300 import synthetic as syn
+
+    from . import boot, ckks
+    pr = syn.boot_params(log_n)
+    p = ckks.Params(pr["log_n"], pr["q_bits"], pr["n_p"], pr["p_bits"], pr["alpha"], pr["log2_scale"])
+    t0 = time.perf_counter()
+    b = boot.prepare(p, boot.BootParams(n_s=n_s))
+    sk, keys = ckks.keygen(p, 7, rot_steps=b.rotation_steps(), h=192, conj=True)
+    setup = time.perf_counter() - t0
+    z = np.random.default_rng(1).uniform(-1, 1, n_s)[np.arange(p.n) % n_s]
+    ct = ckks.encrypt(p, keys, ckks.encode_real(p, z, p.delta), 0, p.delta, 11)
+    runs, err = [], 0.0
+    for _ in range(reps):
+        st = {}
+        tt = {}
+        x = ct
+        t = time.perf_counter()
+        x = boot.mod_raise(p, boot.boost(p, x, b.bp.log2_boost))
+        tt["raise"] = time.perf_counter() - t
+        t = time.perf_counter()
+        x = boot.subsum(p, keys, x, b.subsum_steps)
+        tt["subsum"] = time.perf_counter() - t
+        t = time.perf_counter()
+        y = boot.eval_mod(p, keys, b, boot.coeff_to_slot(p, keys, b, x))
+        tt["cts_evalmod"] = time.perf_counter() - t
+        t = time.perf_counter()
+        out = boot.slot_to_coeff(p, keys, b, y, ct.scale)
+        tt["stc"] = time.perf_counter() - t
+        runs.append(tt)
+        err = max(err, float(np.max(np.abs(ckks.decrypt(p, sk, out) - z))))
+    full_steps = (1 << 15).bit_length() - 1 - (n_s.bit_length() - 1)      # log2(2^15 / n_s)
+    k = full_steps / max(1, len(b.subsum_steps))
+    tot = [r["raise"] + k * r["subsum"] + r["cts_evalmod"] + r["stc"] for r in runs]
+    med = float(np.median(tot))
+    ratio = polymul_ratio(16, log_n)
+    return {"workload": "boot", "sample_log_n": log_n, "n_s": n_s, "stage_times_s": runs, "max_abs_err": err,
+            "sample_s_per_boot": med, "ratio_to_full": ratio, "est_full_s_per_boot": med * ratio,
+            "setup_s": setup, "cores": cores(),
+            "sample": (f"{reps} bootstrap(s) of n_s={n_s} slots at N=2^{log_n} on the bootstrappable chain "
+                       f"({med:.2f} s, SubSum's {len(b.subsum_steps)} rotations scaled to the {full_steps} of "
+                       f"N=2^16), scaled x{ratio:.2f} to N=2^16 (the oracle's measured ring-product time ratio)")}
+
+
 def run_budget(workload: str, reps: int = 3):
     """The bounded sample of bench.py's cpu_baseline: the median of `reps`
     whole queries (UCI-shaped), or of `reps` runs of the first two stages
@@ -264,5 +313,7 @@ if __name__ == "__main__":
         os.environ["OMP_NUM_THREADS"] = str(a.threads)
     if a.workload == "tiny":
         print(json.dumps(run_tiny(a.steps or 3, a.exact)))
+    elif a.workload == "boot":
+        print(json.dumps(run_boot(reps=a.steps or 1)))
     else:
         print(json.dumps(run_budget(a.workload) if a.budget else run(a.workload, a.steps, a.warmup)))

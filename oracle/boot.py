@@ -21,9 +21,11 @@ period n_s (2 n_s <= n = N/2), under a secret with h non-zero coefficients:
      xi = exp(i pi / (2 n_s)), so t = (U^H w + U^T conj(w)) / (2 n_s).  Both
      products, one on the ciphertext and one on its conjugate, are BSGS
      matvecs of one shape that share their giant steps (reading R31); the
-     slots (period 2 n_s) then hold u_k / 2^r, u_k = m_k / q_0 + I_k, read at
-     the scale q_0.  A second rescale follows (the diagonals are encoded at
-     about 2^60 so that their rounding stays below the noise);
+     slots (period 2 n_s) then hold u_k / 2^r, u_k = m_k / q_0 + I_k, at
+     about eval_scale.  The diagonals are encoded at eval_scale times the
+     primes the product is rescaled by, over q_0: one rescale when the top
+     primes are 60-bit (the bootstrappable chain), two on an all-40-bit
+     chain, so that their rounding stays below the noise;
   5. EvalMod: y = u / 2^r - 1 / (4 2^r) (a constant), c = p(y), p a
      polynomial fit of cos(2 pi y) on |y| <= (K + 1/2) / 2^r (even degree),
      then r double angles c <- 2 c^2 - 1, so c = cos(2 pi (u - 1/4)) =
@@ -31,8 +33,11 @@ period n_s (2 n_s <= n = N/2), under a secret with h non-zero coefficients:
   6. SlotToCoeff: z = U (q_0 / (2 pi 2^b s_ref)) c, a BSGS matvec from
      period 2 n_s to period n_s (one fold): the slots hold the message again.
 
-The output sits 3 + depth(p) + r levels below L (poly.depth), at a scale
-about Delta.  Every step is an exact integer operation of ckks / linear /
+EvalMod runs at eval_scale (about its primes: 2^60 on the bootstrappable
+chain, whose top 13 primes are 60-bit, so its noise stays far below the
+message after the r double angles multiply it).  The output sits
+cts_levels + depth(p) + r + 1 levels below L (poly.depth), at a scale about
+Delta.  Every step is an exact integer operation of ckks / linear /
 poly; only the constants (diagonals, polynomial, the scales) come from FP64.
 """
 from __future__ import annotations
@@ -129,6 +134,26 @@ def prepare(p: ckks.Params, bp: BootParams) -> Boot:
     coeffs = list(bp.coeffs) if bp.coeffs is not None else cos_fit(bp.K, bp.r, bp.degree)
     steps = [n_s << i for i in range((p.n // n_s).bit_length() - 1)]
     return Boot(bp, g, L, [A, B], stc, coeffs, steps)
+
+
+def scales(p: ckks.Params, boot: Boot):
+    """(CoeffToSlot output scale, EvalMod output scale): the scales the run
+    declares, from the same FP64 steps (they do not depend on the input)."""
+    s, lv = boot.cts[0].out_scale, boot.level_top - 1
+    for _ in range(boot.bp.cts_levels - 1):
+        s = s / float(p.q[lv])
+        lv -= 1
+    lv2, s2 = poly.simulate(p.q, lv, s, boot.coeffs, boot.bp.eval_scale)
+    for _ in range(boot.bp.r):
+        s2 = (s2 * s2) / float(p.q[lv2])
+        lv2 -= 1
+    return s, s2
+
+
+def out_scale(p: ckks.Params, boot: Boot, in_scale: float) -> float:
+    """The declared scale of the output for an input of scale in_scale."""
+    s2 = scales(p, boot)[1]
+    return (s2 * boot.stc.pt_scale) / float(p.q[boot.stc.level]) * (in_scale / boot.bp.s_ref)
 
 
 def mod_raise(p: ckks.Params, ct: ckks.Ct) -> ckks.Ct:

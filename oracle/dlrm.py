@@ -207,6 +207,8 @@ class Compiled:
     masks: list = field(default_factory=list)       # dot: mask_0 .. mask_S
     mask_scale: float = 0.0
     top: list = field(default_factory=list)
+    lvl_h: int = 0                   # level of z = h + e (lvl_z unless z is bootstrapped)
+    boots: dict = field(default_factory=dict)       # boot point ("b<i>", "z", "t<i>") -> (boot.Boot, level after)
 
     def rotation_steps(self):
         st = set()
@@ -217,6 +219,8 @@ class Compiled:
         if self.spec.interaction == "dot":
             st.add(-DIM * self.Bp)
             st |= {DIM * s for s in range(1, self.S + 1)}
+        for b, _ in self.boots.values():
+            st |= set(b.rotation_steps())
         return sorted(st)
 
     def emb_pms(self):
@@ -244,6 +248,10 @@ class Compiled:
             out += [self.ones] + list(self.masks)
         for lay in self.top:
             out += layer(lay)
+        for name in boot_order(self):
+            b = self.boots[name][0]
+            for pm in b.cts + [b.stc]:
+                out += [pm.pts[k] for k in pm.ordered_keys()]
         return out
 
 
@@ -271,27 +279,85 @@ def dot_top_matrix(W0: np.ndarray, B: int, Bp: int, S: int, W2: int, W_u: int) -
     return M
 
 
+BOOT_POINT_ORDER = "bzt"   # bootstraps run in model order: before bottom layers, on z, before top layers
+
+
+def boot_order(c) -> list:
+    """The model's bootstrap points in the order the inference meets them."""
+    def key(name):
+        return (BOOT_POINT_ORDER.index(name[0]), int(name[1:]) if name[1:] else 0)
+    return sorted(c.boots, key=key)
+
+
+BOOT_LOG2_BOOST = 8    # activations reach |z| ~ 6: the message is 2^-12 |z| of q_0 in EvalMod
+
+
+def level_plan(n_bot: int, n_top: int, ad: int, dot: bool, points):
+    """Levels as late as possible in every segment between bootstraps (each
+    segment ends at level 0, where the next bootstrap or the logit takes it):
+    returns {stage: level its input sits at} for the stages "b<i>" (bottom
+    layer i), "I" (the interaction on z), "t<i>" (top layer i), and "h" (the
+    level of z = h + e).  A bootstrap point "b<i>" (1 <= i < n_bot) runs
+    before bottom layer i, "z" before the interaction, "t<i>" (1 <= i < n_top)
+    before top layer i.  Costs: a layer 1 + ad (the last top layer 1), the
+    dot interaction 2."""
+    seq = [(f"b{i}", 1 + ad) for i in range(n_bot)] + [("I", 2 if dot else 0)] + \
+        [(f"t{i}", 1 + ad if i + 1 < n_top else 1) for i in range(n_top)]
+    cut = {f"b{i}" for i in range(1, n_bot) if f"b{i}" in points} | \
+        ({"I"} if "z" in points else set()) | {f"t{i}" for i in range(1, n_top) if f"t{i}" in points}
+    bad = set(points) - {f"b{i}" for i in range(1, n_bot)} - {"z"} - {f"t{i}" for i in range(1, n_top)}
+    if bad:
+        raise ValueError(f"unknown bootstrap points {sorted(bad)}")
+    lv, out = 0, {}
+    for name, cost in reversed(seq):
+        lv += cost
+        out[name] = lv
+        if name in cut:
+            lv = 0
+    out["h"] = out["I"] if "z" not in points else 0
+    return out
+
+
 def compile_model(p: ckks.Params, spec, w) -> Compiled:
     """Levels are assigned as late as possible so the logit ends at level 0:
     each matvec consumes one level, each activation one (x^2) or poly.depth(d)
-    (a degree-d polynomial), the dot interaction two."""
+    (a degree-d polynomial), the dot interaction two.  With bootstrap points
+    (spec.boot) every segment between them is planned the same way and ends
+    at level 0, and a bootstrap (boot.bootstrap, 512 or fewer periodic slots)
+    lifts the ciphertext to the next segment's first level."""
     T = len(spec.cards)
     B = T + 1
     n_bot, n_top = len(w.bottom_W), len(w.top_W)
     act = getattr(spec, "act", None)
     ad = activation_levels(spec)
-    lvl_u = (1 + ad) * (n_top - 1) + 1
     dot = spec.interaction == "dot"
-    lvl_z = lvl_u + 2 if dot else lvl_u
-    lvl_sel = lvl_z + 1
-    lvl_dense = lvl_z + (1 + ad) * n_bot
-    if lvl_dense > p.L:
-        raise ValueError(f"model needs {lvl_dense} levels, chain has {p.L}")
+    points = tuple(getattr(spec, "boot", ()) or ())
+    plan = level_plan(n_bot, n_top, ad, dot, points)
+    lvl_u = plan["t0"]
+    lvl_z = plan["I"]
+    lvl_h = plan["h"]
+    lvl_sel = lvl_h + 1
+    lvl_dense = plan["b0"]
+    cap = p.L
+    if points:
+        from . import boot as _boot
+        cap = p.L - _boot.levels_used(_boot.BootParams(n_s=1))
+    need = max(v for k, v in plan.items() if k != "h")
+    if need > cap or lvl_sel > cap:
+        raise ValueError(f"model needs {max(need, lvl_sel)} levels, chain has {cap}")
     Bp = B + 1 if dot else B
     W_z = linear.pow2ceil(DIM * Bp)
     lay_sel, sel_w = selector_layout(spec.cards, spec.base, spec.threshold)
     c = Compiled(spec, lvl_dense, lvl_sel, lvl_z, lvl_u, linear.pow2ceil(spec.n_dense),
-                 min(linear.pow2ceil(sel_w), p.n), W_z, Bp=Bp)
+                 min(linear.pow2ceil(sel_w), p.n), W_z, Bp=Bp, lvl_h=lvl_h)
+
+    def bootstrap_point(name, period, lvl_now, scale_now, lvl_next):
+        """A bootstrap at `name` of a ciphertext at level 0 with `period`-periodic slots."""
+        from . import boot as _boot
+        assert lvl_now == 0
+        bt = _boot.prepare(p, _boot.BootParams(n_s=period, log2_boost=BOOT_LOG2_BOOST, s_ref=scale_now))
+        c.boots[name] = (bt, lvl_next)
+        return lvl_next, _boot.out_scale(p, bt, scale_now)
     if dot:
         c.W2 = linear.pow2ceil(2 * DIM * Bp)
         c.S = Bp // 2
@@ -306,6 +372,8 @@ def compile_model(p: ckks.Params, spec, w) -> Compiled:
     lvl, scale, in_pad = lvl_dense, delta, c.p_dense
     for i, (W, b) in enumerate(zip(w.bottom_W, w.bottom_b)):
         last = i + 1 == n_bot
+        if f"b{i}" in points and i > 0:
+            lvl, scale = bootstrap_point(f"b{i}", in_pad, lvl, scale, plan[f"b{i}"])
         out_pad = W_z if last else linear.pow2ceil(W.shape[0])
         pm = linear.prepare(p, W, in_pad, out_pad, lvl, scale, delta)
         bias = ckks.encode_real(p, replicate(b, out_pad, p.n), delta)
@@ -318,7 +386,7 @@ def compile_model(p: ckks.Params, spec, w) -> Compiled:
             lvl, scale = poly.simulate(p.q, lvl, delta, act_linear(act), delta)
             c.bottom[-1].act_const = act_const(p, spec, W.shape[0], out_pad, scale)
         in_pad = out_pad
-    assert lvl == lvl_z
+    assert lvl == lvl_h
     scale_b = scale
     # Embedding lookup (block-diagonal, rows [16, 16 (T+1)) of the z layout)
     M = embedding_matrix(spec.cards, spec.base, w.tables, DIM, DIM * B, threshold=spec.threshold)
@@ -326,11 +394,14 @@ def compile_model(p: ckks.Params, spec, w) -> Compiled:
         c.emb = linear.prepare(p, M, c.p_sel, W_z, lvl_sel, delta, scale_b)
     else:
         c.emb_chunks = prepare_multi(p, M, W_z, lvl_sel, delta, scale_b)
+    scale_z = scale_b
+    if "z" in points:
+        _, scale_z = bootstrap_point("z", W_z, lvl_h, scale_b, lvl_z)
     if dot:
         ones = np.zeros(W_z)
         ones[DIM * B: DIM * B + DIM] = 1.0
         c.ones = ckks.encode_real(p, replicate(ones, W_z, p.n), scale_b)
-        c.mask_scale = float(p.q[lvl_z]) * delta / scale_b
+        c.mask_scale = float(p.q[lvl_z]) * delta / scale_z
         j = np.arange(p.n)
         c.masks.append(ckks.encode_real(p, ((j % c.W2) < DIM * Bp).astype(float), c.mask_scale))
         for s in range(1, c.S + 1):
@@ -340,11 +411,14 @@ def compile_model(p: ckks.Params, spec, w) -> Compiled:
             c.masks.append(ckks.encode_real(p, m, c.mask_scale))
         u_scale = (delta * delta) / p.q[lvl_z - 1]
     else:
-        u_scale = scale_b
+        u_scale = scale_z
     # Top MLP
     lvl, scale = lvl_u, u_scale
     for i, (W, b) in enumerate(zip(w.top_W, w.top_b)):
         last = i + 1 == n_top
+        if f"t{i}" in points and i > 0:
+            lvl, scale = bootstrap_point(f"t{i}", linear.pow2ceil(w.top_W[i - 1].shape[0]), lvl, scale,
+                                         plan[f"t{i}"])
         if i == 0:
             in_pad = c.W_u
             Wm = dot_top_matrix(W, B, Bp, c.S, c.W2, c.W_u) if dot else W
@@ -442,8 +516,15 @@ def infer_stages(p, keys, c: Compiled, ct_dense: ckks.Ct, ct_sel):
     st = {"h": ct_dense}
     act = getattr(c.spec, "act", None)
 
-    def bottom(lay):
-        st["h"] = _dense_layer(p, keys, lay, st["h"], act)
+    def boot_at(name, x):
+        if name not in c.boots:
+            return x
+        from . import boot as _boot
+        bt, lvl_next = c.boots[name]
+        return ckks.drop_level(p, _boot.bootstrap(p, keys, bt, x), lvl_next)
+
+    def bottom(i, lay):
+        st["h"] = _dense_layer(p, keys, lay, boot_at(f"b{i}", st["h"]), act)
 
     def lookup():
         e = lookup_multi(p, keys, c.emb_chunks, ct_sel) if c.emb is None else linear.matvec(p, keys, c.emb, ct_sel)
@@ -453,13 +534,15 @@ def infer_stages(p, keys, c: Compiled, ct_dense: ckks.Ct, ct_sel):
         z = st["y"]
         if c.spec.interaction == "dot":
             z = ckks.add_pt(p, z, c.ones, z.scale)
-            st["y"] = dot_interaction(p, keys, c, z)
+            st["y"] = dot_interaction(p, keys, c, boot_at("z", z))
+        else:
+            st["y"] = boot_at("z", z)
 
-    def top(lay):
-        st["y"] = _dense_layer(p, keys, lay, st["y"], act)
+    def top(i, lay):
+        st["y"] = _dense_layer(p, keys, lay, boot_at(f"t{i}", st["y"]), act)
 
-    stages = [lambda lay=lay: bottom(lay) for lay in c.bottom] + [lookup, interaction] + \
-        [lambda lay=lay: top(lay) for lay in c.top]
+    stages = [lambda i=i, lay=lay: bottom(i, lay) for i, lay in enumerate(c.bottom)] + [lookup, interaction] + \
+        [lambda i=i, lay=lay: top(i, lay) for i, lay in enumerate(c.top)]
     return stages, st
 
 

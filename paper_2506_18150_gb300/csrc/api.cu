@@ -6,7 +6,7 @@
 #include <cstring>
 #include <new>
 
-#include "core.cuh"
+#include "model.cuh"
 
 namespace helrm {
 Ciphertext *ct_poly_eval(Ctx *c, const EvalKey *evk, const Ciphertext *x, const std::vector<double> &a,
@@ -79,6 +79,7 @@ Emb *EMB(const helrm_emb *p) { return as<Emb>(p, KIND_EMB, "embedding"); }
 Model *MOD(const helrm_model *p) { return as<Model>(p, KIND_MODEL, "model"); }
 Batch *BAT(const helrm_batch *p) { return as<Batch>(p, KIND_BATCH, "batch"); }
 Server *SRV(const helrm_server *p) { return as<Server>(p, KIND_SERVER, "server"); }
+Boot *BT(const helrm_boot *p) { return as<Boot>(p, KIND_BOOT, "bootstrapping"); }
 
 Ctx *ctx_or_null(const void *h)
 {
@@ -956,11 +957,125 @@ helrm_status helrm_server_run(helrm_ctx *ctx, helrm_server *s, uint32_t n, const
 }
 
 // ------------------------------------------------------------------ misc
+helrm_status helrm_keygen_ex(helrm_ctx *ctx, uint64_t seed, uint32_t hamming_weight, const int32_t *rot_steps,
+                             uint32_t n_rot, int conj, helrm_sk **sk_out, helrm_evk **evk_out)
+{
+    if (sk_out) *sk_out = nullptr;
+    if (evk_out) *evk_out = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        HCHECK(sk_out && evk_out, HELRM_E_INVAL, "output pointers are NULL");
+        HCHECK(rot_steps || n_rot == 0, HELRM_E_INVAL, "rot_steps is NULL");
+        HCHECK(hamming_weight <= (u32)c->N, HELRM_E_INVAL, "hamming_weight above N");
+        std::unique_ptr<SecretKey> sk(keygen_sk(c, seed, (int)hamming_weight));
+        std::unique_ptr<EvalKey> evk(keygen_evk(c, sk.get(), seed));
+        keygen_rot(c, sk.get(), evk.get(), std::vector<int>(rot_steps, rot_steps + n_rot));
+        if (conj) keygen_galois(c, sk.get(), evk.get(), {2ull * c->N - 1});
+        CUDA_CHECK(cudaStreamSynchronize(c->stream));
+        *sk_out = (helrm_sk *)sk.release();
+        *evk_out = (helrm_evk *)evk.release();
+    });
+}
+
+helrm_status helrm_conjugate(helrm_ctx *ctx, const helrm_evk *evk, const helrm_ct *a, helrm_ct **out)
+{
+    if (out) *out = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        HCHECK(out, HELRM_E_INVAL, "out is NULL");
+        *out = (helrm_ct *)ct_apply_galois(C(ctx), EVK(evk), CT(a), 2ull * C(ctx)->N - 1);
+    });
+}
+
+helrm_status helrm_ptmat_export(helrm_ctx *ctx, const helrm_ptmat *m, int64_t *coeffs, uint32_t count)
+{
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        const PtMatrix *p = PM(m);
+        HCHECK(coeffs, HELRM_E_INVAL, "coeffs is NULL");
+        HCHECK(count == p->pts.size(), HELRM_E_INVAL, "diagonal count mismatch");
+        for (u32 i = 0; i < count; i++) pt_export_signed(c, p->pts[i].get(), coeffs + (size_t)i * c->N);
+    });
+}
+
+helrm_status helrm_boot_create(helrm_ctx *ctx, const helrm_boot_desc *desc, helrm_boot **out)
+{
+    if (out) *out = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        Ctx *c = C(ctx);
+        HCHECK(desc && out, HELRM_E_INVAL, "NULL argument");
+        BootDesc d{(int)desc->n_s, (int)desc->K, (int)desc->r, (int)desc->degree, (int)desc->log2_boost,
+                   (int)desc->cts_levels, desc->s_ref, desc->eval_scale, {}};
+        if (desc->coeffs) d.coeffs.assign(desc->coeffs, desc->coeffs + desc->degree + 1);
+        std::unique_ptr<Boot> b(boot_create(c, d));
+        c->check_device_errors();
+        *out = (helrm_boot *)b.release();
+    });
+}
+
+helrm_status helrm_boot_info(const helrm_boot *bh, uint32_t *info_out)
+{
+    return guard(nullptr, [&] {
+        const Boot *b = BT(bh);
+        HCHECK(info_out, HELRM_E_INVAL, "info_out is NULL");
+        size_t nd = 0;
+        for (PtMatrix *m : b->matrices()) nd += m->pts.size();
+        info_out[0] = (u32)b->n_s;
+        info_out[1] = (u32)b->level_top;
+        info_out[2] = (u32)b->level_stc;
+        info_out[3] = (u32)b->level_out;
+        info_out[4] = (u32)nd;
+        info_out[5] = (u32)b->degree;
+    });
+}
+
+helrm_status helrm_boot_rotations(const helrm_boot *b, int32_t *steps_out, uint32_t *n_out)
+{
+    return guard(nullptr, [&] { copy_steps(BT(b)->rotations(), steps_out, n_out); });
+}
+
+helrm_status helrm_boot_coeffs(const helrm_boot *bh, double *coeffs_out, uint32_t n)
+{
+    return guard(nullptr, [&] {
+        const Boot *b = BT(bh);
+        HCHECK(coeffs_out && n == b->coeffs.size(), HELRM_E_INVAL, "coeffs_out must hold degree + 1 values");
+        for (u32 i = 0; i < n; i++) coeffs_out[i] = b->coeffs[i];
+    });
+}
+
+helrm_status helrm_boot_matrix(const helrm_boot *bh, uint32_t which, helrm_ptmat **out)
+{
+    return guard(nullptr, [&] {
+        HCHECK(out && which < 3, HELRM_E_INVAL, "which must be 0, 1 or 2");
+        *out = (helrm_ptmat *)BT(bh)->matrices()[which];
+    });
+}
+
+helrm_status helrm_bootstrap(helrm_ctx *ctx, const helrm_evk *evk, const helrm_boot *b, const helrm_ct *in,
+                             helrm_ct **out, helrm_ct **stages)
+{
+    if (out) *out = nullptr;
+    if (stages)
+        for (int i = 0; i < 5; i++) stages[i] = nullptr;
+    return guard(ctx_or_null(ctx), [&] {
+        HCHECK(out, HELRM_E_INVAL, "out is NULL");
+        std::vector<Ciphertext *> st;
+        std::unique_ptr<Ciphertext> y;
+        try {
+            y.reset(bootstrap(C(ctx), EVK(evk), BT(b), CT(in), stages ? &st : nullptr));
+        } catch (...) {
+            for (auto *p : st) delete p;
+            throw;
+        }
+        for (size_t i = 0; i < st.size() && stages; i++) stages[i] = (helrm_ct *)st[i];
+        *out = (helrm_ct *)y.release();
+    });
+}
+
 void helrm_free(void *handle)
 {
     if (!handle) return;
     Handle *h = (Handle *)handle;
-    if (h->kind < KIND_CTX || h->kind > KIND_SERVER) return;
+    if (h->kind < KIND_CTX || h->kind > KIND_BOOT) return;
     delete h;
 }
 

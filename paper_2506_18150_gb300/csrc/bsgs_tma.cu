@@ -378,7 +378,7 @@ void bsgs_tma_batch(Ctx *c, const std::vector<BsgsQuery> &qv, const u64 *const *
 {
     const int dnum = c->dnum(level);
     HCHECK(n1 <= 64 && (n2 == 1 || n2 == 2 || n2 == 4 || n2 == 8), HELRM_E_PARAM, "BSGS tile supports n1 <= 64, n2 <= 8");
-    HCHECK(dnum >= 1 && dnum <= 7 && c->N >= T, HELRM_E_PARAM, "BSGS tile supports 1..7 digits");
+    HCHECK(dnum >= 1 && dnum <= 9 && c->N >= T, HELRM_E_PARAM, "BSGS tile supports 1..9 digits");
     TmaGals bk;
     for (int b = 0; b < 64; b++) bk.gal[b] = b < n1 ? gals[b] : 1;
     const size_t plane = (size_t)(level + 1 + c->K) * c->N;
@@ -405,7 +405,9 @@ void bsgs_tma_batch(Ctx *c, const std::vector<BsgsQuery> &qv, const u64 *const *
     case 4: HELRM_TMA(NN, 4); break; \
     case 5: HELRM_TMA(NN, 5); break; \
     case 6: HELRM_TMA(NN, 6); break; \
-    default: HELRM_TMA(NN, 7); break; \
+    case 7: HELRM_TMA(NN, 7); break; \
+    case 8: HELRM_TMA(NN, 8); break; \
+    default: HELRM_TMA(NN, 9); break; \
     }
         switch (n2) {
         case 1: HELRM_TMA_D(1); break;

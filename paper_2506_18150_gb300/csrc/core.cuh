@@ -177,6 +177,7 @@ enum Kind : u32 {
     KIND_MODEL,
     KIND_BATCH,
     KIND_SERVER,
+    KIND_BOOT,
 };
 
 struct Handle {
@@ -584,9 +585,15 @@ void sample_uniform(Ctx *c, u64 *out, u64 seed, u32 purpose, u64 index, int n_li
                     const int *d_limb_pid, const int *d_limb_gid);
 void sample_ternary(Ctx *c, i64 *out, u64 seed, u32 purpose, u64 index);
 void sample_cbd21(Ctx *c, i64 *out, u64 seed, u32 purpose, u64 index);
+// exactly h coefficients in {-1, +1} at the h smallest (priority, position) pairs (one CTA)
+void sample_sparse_ternary(Ctx *c, i64 *out, u64 seed, u32 purpose, int h);
+// ModRaise: n_polys level-0 polynomials (limb 0, coefficient domain, in_stride words
+// apart) centred mod q_0 and written as residues of n_limbs limbs ([n_polys][n_limbs][N])
+void mod_raise(Ctx *c, u64 *out, const u64 *in0_coef, size_t in_stride, int n_polys, int n_limbs, LimbMap map);
 // FFT encode / decode
+// (d_slots_im != null: complex slots, real parts d_slots)
 void encode_slots(Ctx *c, u64 *out_residues, const double *d_slots, int n_valid, int period,
-                  double scale, int n_limbs, LimbMap map, i64 *d_coeffs_out);
+                  double scale, int n_limbs, LimbMap map, i64 *d_coeffs_out, const double *d_slots_im = nullptr);
 void decode_limb0(Ctx *c, double *d_slots_out, const u64 *m_coef_limb0, double scale, int n_slots);
 void check_range(Ctx *c, const u64 *data, int n_limbs, LimbMap map, int *d_flag);
 // selector one-hots of one query: d_tab [T][3] = (rows, offset, digits)
@@ -616,21 +623,28 @@ Ciphertext *ct_drop(Ctx *c, const Ciphertext *a, int level);
 void ct_rotate_hoisted(Ctx *c, const EvalKey *evk, const Ciphertext *a, const std::vector<int> &steps,
                        std::vector<Ciphertext *> &outs);
 Ciphertext *ct_rotate(Ctx *c, const EvalKey *evk, const Ciphertext *a, int step);
+// X -> X^g and the key switch back to s (g = 2N - 1: complex conjugation of every slot)
+Ciphertext *ct_apply_galois(Ctx *c, const EvalKey *evk, const Ciphertext *a, u64 g);
 void ct_tensor_acc(Ctx *c, u64 *d012, const Ciphertext *a, const Ciphertext *b, bool accumulate);
 Ciphertext *ct_relin(Ctx *c, const EvalKey *evk, const u64 *d012, int level, double scale);
 Ciphertext *ct_mul(Ctx *c, const EvalKey *evk, const Ciphertext *a, const Ciphertext *b);
+// h_slots_im != null: complex slots (h_slots the real parts)
 Plaintext *pt_encode(Ctx *c, const double *h_slots, int n_slots, int period, int level, bool qp,
-                     double scale, int form);
+                     double scale, int form, const double *h_slots_im = nullptr);
 Plaintext *pt_encode_dev(Ctx *c, const double *d_slots, int n_valid, int period, int level, double scale);
 Plaintext *pt_from_signed(Ctx *c, const i64 *h_coeffs, int level, bool qp, double scale, int form);
 void pt_export_signed(Ctx *c, const Plaintext *pt, i64 *h_out);
-SecretKey *keygen_sk(Ctx *c, u64 seed);
+// h = 0: dense ternary CBD(1) secret; h > 0: exactly h coefficients in {-1, +1}
+SecretKey *keygen_sk(Ctx *c, u64 seed, int h = 0);
 // relin_level < 0: the relinearisation key at the top level
 EvalKey *keygen_evk(Ctx *c, const SecretKey *sk, u64 seed, int relin_level = -1);
 // one key per step, generated up to levels[i] (empty: the top level); a key
 // already present at a level >= the requested one is kept
 void keygen_rot(Ctx *c, const SecretKey *sk, EvalKey *evk, const std::vector<int> &steps,
                 const std::vector<int> &levels = {});
+// the same for Galois elements (X -> X^g, g odd, < 2N; the key id is g)
+void keygen_galois(Ctx *c, const SecretKey *sk, EvalKey *evk, const std::vector<u64> &gals,
+                   const std::vector<int> &levels = {});
 Ciphertext *encrypt_pt(Ctx *c, const EvalKey *evk, const Plaintext *pt, u64 seed);
 void decrypt_slots(Ctx *c, const SecretKey *sk, const Ciphertext *ct, double *h_out, int n_slots);
 // decrypt into a device buffer, stream-ordered, no synchronisation
@@ -656,6 +670,10 @@ struct PtMatrix : Handle {
 };
 PtMatrix *ptmat_prepare(Ctx *c, const double *W, int rows, int cols, int in_pad, int out_pad,
                         int level, double ct_scale, double target_scale);
+// the diagonals of W (+ i W_im when W_im != null) encoded at pt_scale; the
+// product declares out_scale after its rescale
+PtMatrix *ptmat_prepare_scaled(Ctx *c, const double *W, const double *W_im, int rows, int cols, int in_pad,
+                               int out_pad, int level, double pt_scale, double out_scale);
 Ciphertext *matvec(Ctx *c, const EvalKey *evk, const PtMatrix *m, const Ciphertext *in);
 // products of matrices of one shape share their giant steps (linear.cu)
 bool same_shape(const PtMatrix *a, const PtMatrix *b);

@@ -354,6 +354,68 @@ __global__ void k_cbd21(i64 *out, u64 seed, u32 purpose, u64 index, int N)
     }
 }
 
+// Sparse ternary secret: exactly h coefficients in {-1, +1}.  Stream word i
+// (i < N) is the priority of coefficient i, word N + i its sign (bit 0: 0 ->
+// +1, 1 -> -1); the h coefficients with the smallest (priority, i) pairs are
+// non-zero.  One CTA of SPARSE_T threads: the 2N words go to `words` (global
+// scratch), a bisection over the 32-bit values finds the h-th smallest
+// priority T, every coefficient below T is taken and, of those equal to T,
+// the ones with the smallest positions (a block-wide prefix over contiguous
+// chunks of SPARSE_T-th of the positions each).
+constexpr int SPARSE_T = 1024;
+__device__ int block_sum_int(int v, int *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
+    return s;
+}
+__global__ void __launch_bounds__(SPARSE_T) k_sparse_ternary(i64 *out, u32 *words, u64 seed, u32 purpose, int N,
+                                                             int h)
+{
+    pdl_begin();
+    __shared__ int red[32];
+    __shared__ int pre[SPARSE_T];
+    const int t = threadIdx.x, T = blockDim.x, per = N / T;
+    for (int b = t; b < 2 * N / 16; b += T) {
+        u32 w[16];
+        chacha_block(seed, purpose, 0, (u32)b, w);
+        for (int k2 = 0; k2 < 16; k2++) words[16 * b + k2] = w[k2];
+    }
+    __syncthreads();
+    const u32 *pr = words + (size_t)t * per;
+    // smallest v with #{priority <= v} >= h
+    u32 lo = 0, hi = 0xffffffffu;
+    while (lo < hi) {
+        const u32 mid = lo + ((hi - lo) >> 1);
+        int cnt = 0;
+        for (int i = 0; i < per; i++) cnt += pr[i] <= mid;
+        if (block_sum_int(cnt, red) >= h)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    int lt = 0, eq = 0;
+    for (int i = 0; i < per; i++) {
+        lt += pr[i] < lo;
+        eq += pr[i] == lo;
+    }
+    const int need = h - block_sum_int(lt, red);   // how many of the ties are taken, by position
+    pre[t] = eq;
+    __syncthreads();
+    int rank = 0;
+    for (int w = 0; w < t; w++) rank += pre[w];
+    for (int i = 0; i < per; i++) {
+        const int pos = t * per + i;
+        bool take = pr[i] < lo;
+        if (pr[i] == lo) take = rank++ < need;
+        out[pos] = take ? ((words[N + pos] & 1u) ? -1 : 1) : 0;
+    }
+}
+
 // An encryption's three noise polynomials in one launch (blockIdx.y): v
 // ternary from stream pv into out[0..N), e0 and e1 CBD(21) from streams pe0,
 // pe1 into out[N..2N) and out[2N..3N); the same words as k_ternary / k_cbd21.
@@ -467,6 +529,42 @@ __global__ void k_enc_gather(double2 *x, const double *__restrict__ slots, const
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < N; u += gridDim.x * blockDim.x) {
         const int j = slot_of[u] % period;
         x[u] = make_double2(j < n_valid ? slots[j] : 0.0, 0.0);
+    }
+}
+
+// complex slots: x[u] = z_j at the position of exponent 5^j (u_of_slot[j]),
+// conj(z_j) at the position of -5^j
+__global__ void k_enc_gather_c(double2 *x, const double *__restrict__ re, const double *__restrict__ im,
+                               const int *__restrict__ slot_of, const int *__restrict__ u_of_slot, int n_valid,
+                               int period, int N)
+{
+    pdl_begin();
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < N; u += gridDim.x * blockDim.x) {
+        const int s = slot_of[u], j = s % period;
+        const double a = j < n_valid ? re[j] : 0.0, b = j < n_valid ? im[j] : 0.0;
+        x[u] = make_double2(a, u_of_slot[s] == u ? b : -b);
+    }
+}
+
+// ModRaise: limb 0 of a coefficient-domain polynomial (mod q0), centred in
+// (-q0/2, q0/2], as residues of n_limbs limbs; blockIdx.y = polynomial
+__global__ void k_mod_raise(u64 *__restrict__ out, const u64 *__restrict__ in0, int logN, size_t total, u64 q0,
+                            size_t in_stride, const PrimeInfo *__restrict__ pinfo, LimbMap map)
+{
+    pdl_begin();
+    const size_t N = (size_t)1 << logN;
+    out += blockIdx.y * total;
+    in0 += blockIdx.y * in_stride;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const u64 q = pinfo[map.pid((int)(idx >> logN))].q;
+        const u64 v = in0[idx & (N - 1)];
+        if (v > (q0 - 1) / 2) {   // negative: v - q0
+            const u64 m = (q0 - v) % q;
+            out[idx] = m ? q - m : 0;
+        } else {
+            out[idx] = v % q;
+        }
     }
 }
 
@@ -754,6 +852,22 @@ void sample_ternary(Ctx *c, i64 *out, u64 seed, u32 purpose, u64 index)
     launch(c, k_ternary, grid_for(c->N / 16), TPB, 0, out, seed, purpose, index, c->N);
     LAUNCHED(c);
 }
+void sample_sparse_ternary(Ctx *c, i64 *out, u64 seed, u32 purpose, int h)
+{
+    HCHECK(h > 0 && h <= c->N, HELRM_E_INVAL, "the secret's Hamming weight must be in [1, N]");
+    DevMem words(c, (size_t)2 * c->N * 4);
+    const int T = std::min(SPARSE_T, c->N);
+    launch(c, k_sparse_ternary, 1, T, 0, out, words.as<u32>(), seed, purpose, c->N, h);
+    LAUNCHED(c);
+    CUDA_CHECK(cudaStreamSynchronize(c->stream));   // the scratch words are freed on return
+}
+void mod_raise(Ctx *c, u64 *out, const u64 *in0_coef, size_t in_stride, int n_polys, int n_limbs, LimbMap map)
+{
+    size_t total = (size_t)n_limbs * c->N;
+    launch(c, k_mod_raise, dim3(grid_for(total), n_polys), TPB, 0, out, in0_coef, c->logN, total, c->primes[0],
+           in_stride, c->d_pinfo.as<PrimeInfo>(), map);
+    LAUNCHED(c);
+}
 void sample_cbd21(Ctx *c, i64 *out, u64 seed, u32 purpose, u64 index)
 {
     launch(c, k_cbd21, grid_for(c->N / 8), TPB, 0, out, seed, purpose, index, c->N);
@@ -777,12 +891,16 @@ static void fft(Ctx *c, double2 *buf_a, double2 *buf_b, bool inverse, double2 **
 }
 
 void encode_slots(Ctx *c, u64 *out, const double *d_slots, int n_valid, int period, double scale, int n_limbs,
-                  LimbMap map, i64 *d_coeffs_out)
+                  LimbMap map, i64 *d_coeffs_out, const double *d_slots_im)
 {
     DevMem a(c, (size_t)c->N * sizeof(double2)), b(c, (size_t)c->N * sizeof(double2));
     KTimer kt(c, "encode_fft", 8.0 * c->N * n_limbs);
-    launch(c, k_enc_gather, grid_for(c->N), TPB, 0, a.as<double2>(), d_slots, c->d_slot_of.as<int>(), n_valid,
-                                                        period, c->N);
+    if (d_slots_im)
+        launch(c, k_enc_gather_c, grid_for(c->N), TPB, 0, a.as<double2>(), d_slots, d_slots_im,
+               c->d_slot_of.as<int>(), c->d_u_of_slot.as<int>(), n_valid, period, c->N);
+    else
+        launch(c, k_enc_gather, grid_for(c->N), TPB, 0, a.as<double2>(), d_slots, c->d_slot_of.as<int>(), n_valid,
+               period, c->N);
     LAUNCHED(c);
     double2 *X;
     fft(c, a.as<double2>(), b.as<double2>(), false, &X);

@@ -64,6 +64,14 @@ void PtMatrix::upload_index()
 PtMatrix *ptmat_prepare(Ctx *c, const double *W, int rows, int cols, int in_pad, int out_pad, int level,
                         double ct_scale, double target_scale)
 {
+    HCHECK(level >= 1 && level <= c->L, HELRM_E_LEVEL, "matvec level must be in [1, L]");
+    return ptmat_prepare_scaled(c, W, nullptr, rows, cols, in_pad, out_pad, level,
+                                (double)c->primes[level] * target_scale / ct_scale, target_scale);
+}
+
+PtMatrix *ptmat_prepare_scaled(Ctx *c, const double *W, const double *W_im, int rows, int cols, int in_pad,
+                               int out_pad, int level, double pt_scale, double out_scale)
+{
     HCHECK(W && rows >= 1 && cols >= 1, HELRM_E_INVAL, "empty matrix");
     HCHECK(in_pad == pow2ceil(in_pad) && out_pad == pow2ceil(out_pad), HELRM_E_INVAL, "pads must be powers of two");
     HCHECK(rows <= out_pad && cols <= in_pad, HELRM_E_INVAL, "matrix larger than its padding");
@@ -85,22 +93,29 @@ PtMatrix *ptmat_prepare(Ctx *c, const double *W, int rows, int cols, int in_pad,
         stride <<= r;
         bits -= r;
     }
-    m->pt_scale = (double)c->primes[level] * target_scale / ct_scale;
-    m->out_scale = target_scale;
-    auto Wp = [&](int r, int col) -> double { return (r < rows && col < cols) ? W[(size_t)r * cols + col] : 0.0; };
+    m->pt_scale = pt_scale;
+    m->out_scale = out_scale;
+    auto Wp = [&](const double *A, int r, int col) -> double {
+        return (r < rows && col < cols) ? A[(size_t)r * cols + col] : 0.0;
+    };
     const int P = std::max(in_pad, out_pad);
-    std::vector<double> v(P);
+    std::vector<double> v(P), vi(W_im ? P : 0);
     for (int g = 0; g < m->n2; g++)
         for (int b = 0; b < m->n1; b++) {
             bool nz = false;
             for (int j = 0; j < P; j++) {
                 int r = ((j - g * m->n1) % out_pad + out_pad) % out_pad;
-                v[j] = Wp(r, (j + b) % in_pad);
+                v[j] = Wp(W, r, (j + b) % in_pad);
                 nz |= v[j] != 0.0;
+                if (W_im) {
+                    vi[j] = Wp(W_im, r, (j + b) % in_pad);
+                    nz |= vi[j] != 0.0;
+                }
             }
             if (!nz) continue;
             m->gb.push_back({g, b});
-            m->pts.emplace_back(pt_encode(c, v.data(), P, P, level, true, m->pt_scale, PT_MONT));
+            m->pts.emplace_back(pt_encode(c, v.data(), P, P, level, true, m->pt_scale, PT_MONT,
+                                          W_im ? vi.data() : nullptr));
         }
     c->check_device_errors();
     m->upload_index();

@@ -30,6 +30,11 @@ struct ActPlan {
     DevMem a0;                                  // [round(a_0 out_scale)]_q per prime id (empty: a_0 = 0)
 };
 int poly_depth(int d);
+// per-prime residues of an integer (Montgomery form when mont), as a device table indexed by prime id
+DevMem int_table(Ctx *c, i64 v, bool mont);
+// the same for an integer-valued double of any finite size (the exact integer it holds)
+DevMem int_table_f(Ctx *c, double v, bool mont);
+double round_half_away(double v);
 ActPlan *act_plan(Ctx *c, const std::vector<double> &a, int level, double scale, double target);
 // the plan's polynomial on every query's ciphertext (batch.cu); evk[q]: the
 // relinearisation key of query q
@@ -123,5 +128,44 @@ struct Model : Handle {
 // ct_sel: the model's n_sel() selector ciphertexts
 Ciphertext *model_infer(Ctx *c, const EvalKey *evk, const Model *m, const Ciphertext *ct_dense,
                         const std::vector<const Ciphertext *> &ct_sel);
+
+// Bootstrapping of a ciphertext whose real slots are periodic with period n_s
+// (boot.cu): ModRaise, SubSum, CoeffToSlot (the ciphertext and its
+// conjugate, giant steps shared), EvalMod (cosine fit, r double angles),
+// SlotToCoeff.
+struct Boot : Handle {
+    Ctx *ctx;
+    int n_s = 0, K = 0, r = 0, degree = 0, log2_boost = 0, cts_levels = 1;
+    int level_top = 0, level_stc = 0, level_out = 0;
+    double s_ref = 0, eval_scale = 0;
+    std::vector<double> coeffs;                 // the cosine polynomial, power basis in y
+    std::unique_ptr<PtMatrix> cts_a, cts_b;     // CoeffToSlot on ct and on conj(ct), at level_top
+    std::unique_ptr<PtMatrix> stc;              // SlotToCoeff at level_stc
+    std::vector<int> subsum_steps;
+    DevMem boost_mont;                          // 2^b per prime id, Montgomery form
+    // fixed at creation (no host synchronisation while bootstrapping, so a
+    // bootstrap can be captured in a CUDA graph): the CoeffToSlot output scale,
+    // the EvalMod constants and polynomial plan, the SlotToCoeff scale factor
+    double s_cts = 0, s_eval = 0, c_out = 0;
+    DevMem c_shift;                             // round(-s_cts / (4 2^r)), plain residues per prime id
+    std::unique_ptr<ActPlan> plan;              // the cosine polynomial at (L - cts_levels, s_cts)
+    std::vector<DevMem> c_double;               // round(-scale) after each double angle's product
+    Boot(Ctx *c) : Handle(KIND_BOOT), ctx(c) {}
+    // the declared scale of the output for an input of scale in_scale
+    double out_scale(double in_scale) const { return c_out * (in_scale / s_ref); }
+    std::vector<int> rotations() const;
+    std::vector<PtMatrix *> matrices() const { return {cts_a.get(), cts_b.get(), stc.get()}; }
+};
+struct BootDesc {
+    int n_s, K, r, degree, log2_boost, cts_levels;
+    double s_ref, eval_scale;
+    std::vector<double> coeffs;   // empty: the library's Chebyshev fit
+};
+Boot *boot_create(Ctx *c, const BootDesc &d);
+std::vector<double> boot_cos_fit(int K, int r, int degree);
+// stages (optional, 5 entries): raised, subsum, CoeffToSlot, EvalMod, output
+// (the caller owns them; the output is also returned)
+Ciphertext *bootstrap(Ctx *c, const EvalKey *evk, const Boot *b, const Ciphertext *in,
+                      std::vector<Ciphertext *> *stages = nullptr);
 
 }  // namespace helrm

@@ -34,6 +34,8 @@ u64 mod_signed(i64 v, u64 q)
 
 u64 mulmod_host(u64 a, u64 b, u64 q) { return (u64)(((unsigned __int128)a * b) % q); }
 
+}  // namespace
+
 // per-prime residues of an integer (plain, or times R for Montgomery products)
 DevMem int_table(Ctx *c, i64 v, bool mont)
 {
@@ -50,7 +52,31 @@ DevMem int_table(Ctx *c, i64 v, bool mont)
 
 double round_half_away(double v) { return std::copysign(std::floor(std::fabs(v) + 0.5), v); }
 
-}  // namespace
+// the same for an integer-valued double of any finite size: v = m 2^e with an
+// integer mantissa m (|m| < 2^53), so v mod q = m (2^e mod q) mod q, exactly
+DevMem int_table_f(Ctx *c, double v, bool mont)
+{
+    HCHECK(std::isfinite(v) && v == std::floor(v), HELRM_E_INVAL, "internal: constant is not an integer");
+    if (std::fabs(v) < 9.2e18) return int_table(c, (i64)v, mont);
+    int e = 0;
+    const double f = std::frexp(std::fabs(v), &e);   // |v| = f 2^e, f in [0.5, 1)
+    const u64 m = (u64)std::ldexp(f, 53);
+    e -= 53;                                         // |v| = m 2^e, e > 0 here
+    std::vector<u64> t(c->nP());
+    for (int i = 0; i < c->nP(); i++) {
+        const u64 q = c->primes[i];
+        u64 p2 = 1, b = 2 % q;
+        for (int k = e; k; k >>= 1, b = mulmod_host(b, b, q))
+            if (k & 1) p2 = mulmod_host(p2, b, q);
+        u64 r = mulmod_host(m % q, p2, q);
+        if (v < 0 && r) r = q - r;
+        t[i] = mont ? mulmod_host(r, c->pinfo[i].rmod, q) : r;
+    }
+    DevMem d(c, t.size() * 8);
+    CUDA_CHECK(cudaMemcpyAsync(d.ptr, t.data(), t.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    return d;
+}
 
 int poly_power_depth(int k) { return k <= 1 ? 0 : 32 - __builtin_clz((unsigned)(k - 1)); }
 int poly_depth(int d) { return d <= 0 ? 0 : poly_power_depth(d) + 1; }
@@ -96,11 +122,11 @@ ActPlan *act_plan(Ctx *c, const std::vector<double> &a, int level, double scale,
         if (a[k] == 0.0) continue;
         const double s = (target * qc) / p->pw_scale[k];
         const double v = round_half_away(a[k] * s);
-        HCHECK(std::fabs(v) < 9.2e18, HELRM_E_PARAM, "polynomial coefficient too large for the scale");
+        HCHECK(std::isfinite(v), HELRM_E_PARAM, "polynomial coefficient too large for the scale");
         ActPlan::Term t;
         t.k = k;
         t.scale = p->pw_scale[k] * s;
-        t.mont = int_table(c, (i64)v, true);
+        t.mont = int_table_f(c, v, true);
         p->terms.push_back(std::move(t));
     }
     HCHECK(!p->terms.empty(), HELRM_E_INVAL, "need a non-constant polynomial");
@@ -108,8 +134,8 @@ ActPlan *act_plan(Ctx *c, const std::vector<double> &a, int level, double scale,
     p->out_scale = p->terms[0].scale / qc;
     if (a[0] != 0.0) {
         const double v = round_half_away(a[0] * p->out_scale);
-        HCHECK(std::fabs(v) < 9.2e18, HELRM_E_PARAM, "constant term too large for the scale");
-        p->a0 = int_table(c, (i64)v, false);
+        HCHECK(std::isfinite(v), HELRM_E_PARAM, "constant term too large for the scale");
+        p->a0 = int_table_f(c, v, false);
     }
     return p.release();
 }

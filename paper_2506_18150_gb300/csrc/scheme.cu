@@ -19,7 +19,7 @@
 
 namespace helrm {
 
-enum Purpose : u32 { P_SK = 1, P_PK_A, P_PK_E, P_KSK_A, P_KSK_E, P_ENC_V, P_ENC_E0, P_ENC_E1 };
+enum Purpose : u32 { P_SK = 1, P_PK_A, P_PK_E, P_KSK_A, P_KSK_E, P_ENC_V, P_ENC_E0, P_ENC_E1, P_SK_SPARSE };
 
 Ciphertext *new_ct(Ctx *c, int level, double scale)
 {
@@ -243,6 +243,21 @@ void ct_rotate_hoisted(Ctx *c, const EvalKey *evk, const Ciphertext *a, const st
     for (auto &r : res) outs.push_back(r.release());
 }
 
+// X -> X^g with the key switch, in a hoisted rotation's order (ModUp of c1,
+// then phi_g on the extended digits inside the key inner product)
+Ciphertext *ct_apply_galois(Ctx *c, const EvalKey *evk, const Ciphertext *a, u64 g)
+{
+    const int l = a->level, N = c->N, nq = l + 1, nl = nq + c->K, dnum = c->dnum(l);
+    const SwitchKey *key = rot_key(evk, g, l);
+    DevMem digits(c, (size_t)dnum * nl * N * 8), u(c, (size_t)2 * nl * N * 8);
+    ks_modup(c, a->c1(), l, digits.u());
+    std::unique_ptr<Ciphertext> o(new_ct(c, l, a->scale));
+    k::ks_inner_auto(c, u.u(), digits.u(), dnum, key, l, g, nullptr, nullptr);
+    k::automorphism(c, o->c0(), a->c0(), nq, g);
+    ks_moddown2(c, u.u(), l, o->c0(), o->c1(), o->c0());
+    return o.release();
+}
+
 Ciphertext *ct_rotate(Ctx *c, const EvalKey *evk, const Ciphertext *a, int step)
 {
     std::vector<Ciphertext *> outs;
@@ -282,7 +297,7 @@ Ciphertext *ct_mul(Ctx *c, const EvalKey *evk, const Ciphertext *a, const Cipher
 
 // ---------------------------------------------------------------- plaintexts
 Plaintext *pt_encode(Ctx *c, const double *h_slots, int n_slots, int period, int level, bool qp, double scale,
-                     int form)
+                     int form, const double *h_slots_im)
 {
     HCHECK(level >= 0 && level <= c->L, HELRM_E_LEVEL, "level out of range");
     HCHECK(period >= 1 && period <= c->n_slots && (c->n_slots % period) == 0 && n_slots <= period,
@@ -294,9 +309,13 @@ Plaintext *pt_encode(Ctx *c, const double *h_slots, int n_slots, int period, int
     pt->scale = scale;
     const int nl = pt->limbs();
     pt->data = DevMem(c, (size_t)nl * c->N * 8);
-    DevMem ds(c, (size_t)std::max(n_slots, 1) * 8);
+    DevMem ds(c, (size_t)std::max(n_slots, 1) * 8 * (h_slots_im ? 2 : 1));
     if (n_slots) CUDA_CHECK(cudaMemcpyAsync(ds.ptr, h_slots, (size_t)n_slots * 8, cudaMemcpyHostToDevice, c->stream));
-    k::encode_slots(c, pt->data.u(), ds.as<double>(), n_slots, period, scale, nl, c->qmap(level), nullptr);
+    if (n_slots && h_slots_im)
+        CUDA_CHECK(cudaMemcpyAsync(ds.as<double>() + n_slots, h_slots_im, (size_t)n_slots * 8,
+                                   cudaMemcpyHostToDevice, c->stream));
+    k::encode_slots(c, pt->data.u(), ds.as<double>(), n_slots, period, scale, nl, c->qmap(level), nullptr,
+                    h_slots_im ? ds.as<double>() + n_slots : nullptr);
     k::ntt_fwd(c, pt->data.u(), nl, c->qmap(level));
     if (form == PT_MONT) k::to_mont(c, pt->data.u(), pt->data.u(), nl, c->qmap(level));
     return pt.release();
@@ -374,13 +393,16 @@ static LimbIds full_limbs(Ctx *c, int n)
     return level_limbs(c, c->L);
 }
 
-SecretKey *keygen_sk(Ctx *c, u64 seed)
+SecretKey *keygen_sk(Ctx *c, u64 seed, int h)
 {
     std::unique_ptr<SecretKey> sk(new SecretKey(c));
     const int nP = c->nP(), N = c->N;
     LimbMap all = c->qmap(c->L);
     DevMem s(c, (size_t)N * 8);
-    k::sample_ternary(c, s.as<i64>(), seed, P_SK, 0);
+    if (h > 0)
+        k::sample_sparse_ternary(c, s.as<i64>(), seed, P_SK_SPARSE, h);
+    else
+        k::sample_ternary(c, s.as<i64>(), seed, P_SK, 0);
     sk->s_ntt = DevMem(c, (size_t)nP * N * 8);
     sk->s_mont = DevMem(c, (size_t)nP * N * 8);
     k::from_signed(c, sk->s_ntt.u(), s.as<i64>(), nP, all);
@@ -464,11 +486,20 @@ EvalKey *keygen_evk(Ctx *c, const SecretKey *sk, u64 seed, int relin_level)
 void keygen_rot(Ctx *c, const SecretKey *sk, EvalKey *evk, const std::vector<int> &steps,
                 const std::vector<int> &levels)
 {
+    std::vector<u64> gals;
+    for (int st : steps) gals.push_back(c->galois(st));
+    keygen_galois(c, sk, evk, gals, levels);
+}
+
+void keygen_galois(Ctx *c, const SecretKey *sk, EvalKey *evk, const std::vector<u64> &gals,
+                   const std::vector<int> &levels)
+{
     const int nP = c->nP(), N = c->N;
     std::map<int, LimbIds> ids;
     DevMem sp(c, (size_t)nP * N * 8);
-    for (size_t i = 0; i < steps.size(); i++) {
-        const u64 g = c->galois(steps[i]);
+    for (size_t i = 0; i < gals.size(); i++) {
+        const u64 g = gals[i];
+        HCHECK((g & 1) && g < 2ull * N, HELRM_E_INVAL, "a Galois element is odd and below 2N");
         const int kl = levels.empty() ? c->L : levels[i];
         HCHECK(kl >= 0 && kl <= c->L, HELRM_E_LEVEL, "key level outside the chain");
         if (g == 1) continue;

@@ -35,6 +35,12 @@ class Params(C.Structure):
                 ("log2_scale", C.c_double)]
 
 
+class BootDesc(C.Structure):
+    _fields_ = [("n_s", C.c_uint32), ("K", C.c_uint32), ("r", C.c_uint32), ("degree", C.c_uint32),
+                ("log2_boost", C.c_uint32), ("cts_levels", C.c_uint32), ("s_ref", C.c_double),
+                ("eval_scale", C.c_double), ("coeffs", C.POINTER(C.c_double))]
+
+
 class ServeStats(C.Structure):
     _fields_ = [("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("max_ms", C.c_double),
                 ("makespan_s", C.c_double), ("throughput", C.c_double), ("n_batches", C.c_uint32),
@@ -133,6 +139,15 @@ _SIGS = {
     "helrm_ctx_wait_selftest": [_vp, C.c_uint32],
     "helrm_ctx_profile_report": [_vp, C.c_char_p, C.c_uint64, _u64p],
     "helrm_ctx_profile_records": [_vp, C.c_char_p, C.c_uint64, _u64p],
+    "helrm_keygen_ex": [_vp, C.c_uint64, C.c_uint32, _i32p, C.c_uint32, C.c_int, _pp, _pp],
+    "helrm_conjugate": [_vp, _vp, _vp, _pp],
+    "helrm_ptmat_export": [_vp, _vp, _i64p, C.c_uint32],
+    "helrm_boot_create": [_vp, C.POINTER(BootDesc), _pp],
+    "helrm_boot_info": [_vp, _u32p],
+    "helrm_boot_rotations": [_vp, _i32p, _u32p],
+    "helrm_boot_coeffs": [_vp, _dp, C.c_uint32],
+    "helrm_boot_matrix": [_vp, C.c_uint32, _pp],
+    "helrm_bootstrap": [_vp, _vp, _vp, _vp, _pp, _pp],
 }
 
 
@@ -762,3 +777,68 @@ def helrm_infer_e2e(ctx, sk, evk, m, dense, indices, seed: int):
     _check(ctx, lib().helrm_infer_e2e(ctx.ptr, sk.ptr, evk.ptr, m.ptr, dp, ip, nq, seed,
                                       lg.ctypes.data_as(_dp), pr.ctypes.data_as(_dp)))
     return lg, pr
+
+
+# ------------------------------------------------------------------ bootstrapping
+def helrm_keygen_ex(ctx, seed: int, hamming_weight: int = 0, rot_steps=(), conj: bool = False):
+    """(sk, evk): hamming_weight 0 is helrm_keygen's dense secret, h > 0 a sparse one;
+    conj adds the key of X -> X^(2N-1)."""
+    st_arr, st_p = _i32(list(rot_steps) or [0])
+    sk, evk = C.c_void_p(), C.c_void_p()
+    _check(ctx, lib().helrm_keygen_ex(ctx.ptr, seed, hamming_weight, st_p, len(rot_steps), 1 if conj else 0,
+                                      C.byref(sk), C.byref(evk)))
+    return Handle(sk.value, ctx), Handle(evk.value, ctx)
+
+
+def helrm_conjugate(ctx, evk, a):
+    return _ct_op("helrm_conjugate", ctx, evk.ptr, a.ptr)
+
+
+def helrm_ptmat_export(ctx, m, count: int, n: int):
+    out = np.zeros((count, n), dtype=np.int64)
+    _check(ctx, lib().helrm_ptmat_export(ctx.ptr, m.ptr, out.ctypes.data_as(_i64p), count))
+    return out
+
+
+def helrm_boot_create(ctx, n_s: int, K: int = 24, r: int = 6, degree: int = 16, log2_boost: int = 10,
+                      cts_levels: int = 1, s_ref: float = 2.0**40, eval_scale: float = 2.0**60, coeffs=None):
+    cf = None if coeffs is None else np.ascontiguousarray(coeffs, dtype=np.float64)
+    d = BootDesc(n_s, K, r, degree, log2_boost, cts_levels, s_ref, eval_scale,
+                 cf.ctypes.data_as(_dp) if cf is not None else None)
+    out = C.c_void_p()
+    _check(ctx, lib().helrm_boot_create(ctx.ptr, C.byref(d), C.byref(out)))
+    return Handle(out.value, ctx)
+
+
+def helrm_boot_info(ctx, b):
+    o = (C.c_uint32 * 6)()
+    _check(ctx, lib().helrm_boot_info(b.ptr, o))
+    return dict(zip(["n_s", "level_top", "level_stc", "level_out", "n_plaintexts", "degree"], list(o)))
+
+
+def helrm_boot_rotations(ctx, b):
+    return _steps(lib().helrm_boot_rotations, ctx, b)
+
+
+def helrm_boot_coeffs(ctx, b):
+    n = helrm_boot_info(ctx, b)["degree"] + 1
+    out = (C.c_double * n)()
+    _check(ctx, lib().helrm_boot_coeffs(b.ptr, out, n))
+    return list(out)
+
+
+def helrm_boot_matrix(ctx, b, which: int):
+    """0: CoeffToSlot on the ciphertext, 1: on its conjugate, 2: SlotToCoeff (not freed by this handle)."""
+    out = C.c_void_p()
+    _check(ctx, lib().helrm_boot_matrix(b.ptr, which, C.byref(out)))
+    return Borrowed(out.value, b)
+
+
+def helrm_bootstrap(ctx, evk, b, ct, stages: bool = False):
+    """The refreshed ciphertext; with stages, (out, [raised, subsum, cts, evalmod, out copy])."""
+    out = C.c_void_p()
+    st = (C.c_void_p * 5)() if stages else None
+    _check(ctx, lib().helrm_bootstrap(ctx.ptr, evk.ptr, b.ptr, ct.ptr, C.byref(out), st))
+    if stages:
+        return Handle(out.value, ctx), [Handle(v, ctx) for v in st]
+    return Handle(out.value, ctx)

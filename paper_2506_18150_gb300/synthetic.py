@@ -32,6 +32,15 @@ PARAMS = {
 }
 
 
+def boot_params(log_n: int = 16, n_compute: int = 13) -> dict:
+    """The bootstrappable chain: q_0 60-bit, n_compute x 40-bit primes for the
+    model's levels, 13 x 60-bit primes for bootstrapping (CoeffToSlot 1,
+    the degree-16 cosine 5, 6 double angles, SlotToCoeff 1), 3 x 60-bit
+    special primes; at N = 2^16 with 13 compute primes log2(QP) = 1540."""
+    return dict(log_n=log_n, q_bits=[60] + [40] * n_compute + [60] * 13, n_p=3, p_bits=60, alpha=3,
+                log2_scale=40.0)
+
+
 def reduced_params(log_n: int, n_levels: int) -> dict:
     """The 'full' chain shape at a smaller ring degree and depth (tests)."""
     return dict(log_n=log_n, q_bits=[60] + [40] * n_levels, n_p=3, p_bits=60, alpha=3,
@@ -53,6 +62,7 @@ class DLRMSpec:
     interaction: str = "dot"    # "dot" (pairwise) or "concat" (the paper's choice)
     threshold: int | None = None    # tables with more rows are digit-decomposed (None: base)
     act: tuple | None = None    # activation polynomial a_0..a_d (power basis); None: x^2
+    boot: tuple = ()            # bootstrap points: "b<i>" before bottom layer i, "z" on z, "t<i>" before top layer i
 
 
 def act_apply(spec: DLRMSpec, v):

@@ -146,6 +146,8 @@ def test_bootstrap_refreshes_the_message(setup, booted):
     zz, ct, st, out = booted
     assert out.level == p.L - boot.levels_used(b.bp) == 4
     assert abs(math.log2(out.scale) - 40) < 1e-6
+    assert out.scale == boot.out_scale(p, b, ct.scale)                  # the scale is known before the run
+    assert st["cts"].scale == boot.scales(p, b)[0] and st["evalmod"].scale == boot.scales(p, b)[1]
     got = ckks.decrypt(p, sk, out)
     assert np.max(np.abs(got.real - zz)) < 1e-6
     assert np.max(np.abs(ckks.decrypt(p, sk, ct).real - zz)) < 1e-6    # the input still decrypts too

@@ -65,7 +65,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "encrypted DLRM inferences/s"
 UNIT = "inferences/s"
-ONE_QUERY = ("criteo", "uci", "uci_silu")
+ONE_QUERY = ("criteo", "uci", "uci_silu", "criteo_silu_boot")
 
 
 def parse(argv=None):
@@ -77,7 +77,7 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="criteo",
-                    choices=["criteo", "uci", "uci_silu", "batched", "served", "tiny", "boot"])
+                    choices=["criteo", "uci", "uci_silu", "criteo_silu_boot", "batched", "served", "tiny", "boot"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="one-query line only (no uci/batched/config4/served keys)")
     ap.add_argument("--requests", type=int, default=1000, help="served: requests per arrival rate")
@@ -98,15 +98,22 @@ DESC = {
               "bottom 13-512-256-64-16, dot interaction, top 367-512-256-1, x^2",
     "uci_silu": "UCI-health-shaped DLRM, 1 query/step, as 'uci' but every activation is a degree-6 "
                 "least-squares SiLU polynomial on [-6, 6] (depth 4, no bootstrapping; ct_dense at level 18)",
+    "criteo_silu_boot": "Criteo-shaped DLRM, 1 query/step, as 'criteo' but every activation is the degree-6 "
+                        "SiLU polynomial (34 levels in all), with 2 bootstraps per query (before bottom layer 2, "
+                        "256 slots; on z before the interaction, 512 slots)",
 }
 CKKS = "N=2^16, q0 60-bit + 20x40-bit, K=3x60-bit special, alpha=3, Delta=2^40"
+CKKS_BOOT = "N=2^16, q0 60-bit + 13x40-bit + 13x60-bit, K=3x60-bit special, alpha=3, secret h=192, Delta=2^40"
+SPECS = {"uci": "uci_spec", "criteo": "criteo_spec", "uci_silu": "uci_silu_spec",
+         "criteo_silu_boot": "criteo_silu_boot_spec"}
 
 
 def workload_config(name, world=1):
     from paper_2506_18150_gb300 import synthetic as syn
-    spec = {"uci": syn.uci_spec, "criteo": syn.criteo_spec, "uci_silu": syn.uci_silu_spec}[name](0)
-    cfg = {"workload": DESC[name], "ckks": CKKS,
-           "tables": spec.cards if name != "criteo" else f"{len(spec.cards)} tables, {sum(spec.cards)} rows",
+    spec = getattr(syn, SPECS[name])(0)
+    cfg = {"workload": DESC[name], "ckks": CKKS_BOOT if spec.boot else CKKS,
+           "tables": spec.cards if not name.startswith("criteo") else
+           f"{len(spec.cards)} tables, {sum(spec.cards)} rows",
            "l2": "no flush: each step streams GBs of keys and diagonals (>> 129 MB L2)",
            "parallelism": f"replicas x{world}"}
     return spec, cfg
@@ -354,7 +361,9 @@ def _timed(fn, reps=1):
 class Env:
     """The context and process state one run of the bench shares."""
 
-    def __init__(self):
+    def __init__(self, boot_chain: bool = False):
+        """boot_chain: the context on the bootstrappable chain (models with
+        bootstraps), else on the 20-level chain of the other models."""
         import torch
 
         from paper_2506_18150_gb300 import helrm as H
@@ -362,11 +371,11 @@ class Env:
         self.torch, self.H, self.syn = torch, H, syn
         self.world, self.rank, self.local = dist_env()
         torch.cuda.set_device(self.local)
-        if self.world > 1:
-            import torch.distributed as dist
+        import torch.distributed as dist
+        if self.world > 1 and not dist.is_initialized():
             dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
         self.stream = torch.cuda.current_stream()
-        self.pr = syn.PARAMS["full"]
+        self.pr = syn.boot_params() if boot_chain else syn.PARAMS["full"]
         pr = self.pr
         self.ctx = H.helrm_ctx_create(pr["log_n"], pr["q_bits"], pr["n_p"], pr["p_bits"], pr["alpha"],
                                       pr["log2_scale"], device=self.local, stream=self.stream.cuda_stream)
@@ -374,8 +383,7 @@ class Env:
 
     def model(self, name):
         if name not in self.models:
-            spec = {"uci": self.syn.uci_spec, "criteo": self.syn.criteo_spec,
-                    "uci_silu": self.syn.uci_silu_spec}[name](0)
+            spec = getattr(self.syn, SPECS[name])(0)
             self.models[name] = (spec, self.H.helrm_model_create(self.ctx, spec, self.syn.make_weights(spec, 0)))
         return self.models[name]
 
@@ -417,7 +425,8 @@ def one_query(E, wl, K, W, hbm, alu, seed=1000):
     # CUDA graph (helrm_batch_set_graph; bit-identical to the eager path): the
     # client's packing and encryption and the decryption stay eager
     bt1 = H.helrm_batch_create(ctx, model, [evk])
-    H.helrm_batch_set_graph(ctx, bt1, True)
+    graph = not spec.boot          # a model with bootstraps runs eagerly
+    H.helrm_batch_set_graph(ctx, bt1, graph)
 
     def step_graph(q):
         H.helrm_infer_batch_e2e_device(ctx, bt1, [sk], d_dense[q].data_ptr(), d_idx[q].data_ptr(), 7 + 2 * q,
@@ -880,7 +889,7 @@ def base_line(E, args, cfg):
 
 
 def run_ours(args):
-    E = Env()
+    E = Env(boot_chain=args.workload == "criteo_silu_boot")
     K, W = args.steps, args.warmup
     hbm = hbm_peak()
     alu = alu_peaks(E.H, E.ctx)
@@ -901,18 +910,27 @@ def run_ours(args):
         del clients
         gc.collect()
         extras["boot"] = boot_measure(E.local, E.world, min(K, 10), min(W, 3), hbm, alu)
+        E2 = Env(boot_chain=True)
+        b = one_query(E2, "criteo_silu_boot", min(K, 10), min(W, 3), hbm, alu)
+        b["config"] = workload_config("criteo_silu_boot", E.world)[1]
+        extras["criteo_silu_boot"] = b
+        del E2
+        gc.collect()
     clk = clocks.stop()
     if E.rank == 0:
         line = base_line(E, args, cfg)
         line.update({"value": main["value"], "ms_per_step": main["ms_per_step"], "latency_ms": main["latency_ms"],
                      "clocks": clk, "gpu_launches": int(main["launches_per_step"] * K),
                      "value_eager": main["value_eager"],
-                     "value_note": "value: the server path of a batch of one replayed as a CUDA graph "
-                                   "(helrm_infer_batch_e2e_device); value_eager: every kernel launched on the "
-                                   "stream (helrm_infer_e2e_device); both bit-identical",
+                     "value_note": ("value: the server path of a batch of one replayed as a CUDA graph "
+                                    "(helrm_infer_batch_e2e_device); value_eager: every kernel launched on the "
+                                    "stream (helrm_infer_e2e_device); both bit-identical")
+                     if args.workload != "criteo_silu_boot" else
+                     ("value: the batch of one launched on the stream (a model with bootstraps runs without "
+                      "a CUDA graph); value_eager: helrm_infer_e2e_device, the same launches"),
                      "e2e": main["e2e"], "roofline": main["roofline"]})
         line.update(extras)
-        if E.world == 1 and not args.no_cpu_baseline:
+        if E.world == 1 and not args.no_cpu_baseline and args.workload != "criteo_silu_boot":
             line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)
     E.close()

@@ -342,6 +342,11 @@ typedef struct {
     uint64_t threshold;              /* tables with more rows are digit-decomposed (0 = base_p) */
     uint32_t act_degree;             /* 0: the activation is x^2; d >= 1: the polynomial below */
     const double *act_coeffs;        /* a_0 .. a_d (powers of x, a_d != 0), see helrm_poly_eval */
+    uint32_t boot_bottom;            /* bit i (1 <= i < n_bottom): bootstrap before bottom layer i */
+    uint32_t boot_z;                 /* != 0: bootstrap z = h + e (+ ones) before the interaction */
+    uint32_t boot_top;               /* bit i (1 <= i < n_top): bootstrap before top layer i */
+    const double *boot_coeffs;       /* 17 values: the bootstraps' cosine polynomial (power basis, see
+                                        helrm_boot_desc), or NULL: the library's interpolant */
 } helrm_model_desc;
 
 /* Compile the model: layouts, as-late-as-possible levels (the logit ends at
@@ -351,6 +356,19 @@ typedef struct {
  * is evaluated without a_0 (helrm_poly_eval's schedule), and a_0 is then added
  * as a plaintext on the layer's real outputs only, so that the layout's zero
  * padding stays zero.
+ * Bootstrap points (boot_bottom, boot_z, boot_top; the paper's Criteo models
+ * with polynomial activations bootstrap between layers, Sec. 5.4) split the
+ * network into segments, each planned as late as possible so that it ends at
+ * level 0; there a bootstrap (helrm_bootstrap's pipeline with n_s the
+ * ciphertext's slot period, K = 24, r = 6, degree 16, 2^8 boost, on the
+ * bootstrappable chain: 60-bit primes above the compute levels) lifts the
+ * ciphertext, and it is dropped to the first level of the next segment.
+ * Every segment must fit in the compute levels (L minus the 13 a bootstrap
+ * uses).  The plaintexts of the bootstraps (CoeffToSlot, then SlotToCoeff
+ * diagonals per point, in model order) follow the model's in the canonical
+ * order.  helrm_model_keygen then draws a sparse secret (h = 192) and adds
+ * the bootstraps' rotation keys, the conjugation key and a full-level
+ * relinearisation key; a model with bootstraps runs eagerly (no CUDA graph).
  * Errors: HELRM_E_PARAM if the chain is too short or a layout exceeds n. */
 helrm_status helrm_model_create(helrm_ctx *ctx, const helrm_model_desc *desc, helrm_model **out);
 /* info_out[0..9] = level of ct_dense, level of ct_sel, level of z, level of
@@ -533,11 +551,10 @@ helrm_status helrm_rescale_noalloc(helrm_ctx *ctx, const uint64_t *d_in, uint64_
  * period n_s (2 n_s <= N/2):
  *   boost (x 2^log2_boost at level 0), ModRaise (the level-0 residues,
  *   centred, as residues of q_0..q_L), SubSum (ct += rot(ct, n_s 2^i) up to
- *   N/2: the trace onto X^(N/(2 n_s))), CoeffToSlot (two BSGS products of
- *   the n_s x 2 n_s slot matrix U[i][k] = exp(i pi (5^i k mod 4 n_s) /
- *   (2 n_s)): U^H on the ciphertext and U^T on its conjugate, giant steps
- *   shared; the slots, period 2 n_s, then hold the coefficients over q_0 and
- *   2^r), EvalMod (minus 1/(4 2^r), an even polynomial fit of cos(2 pi y) on
+ *   N/2: the trace onto X^(N/(2 n_s))), CoeffToSlot (a BSGS product C of
+ *   U^H / (2 n_s), U[i][k] = exp(i pi (5^i k mod 4 n_s) / (2 n_s)) the
+ *   n_s x 2 n_s slot matrix, then C + conj(C): the slots, period 2 n_s,
+ *   hold the coefficients over q_0 and 2^r), EvalMod (minus 1/(4 2^r), an even polynomial fit of cos(2 pi y) on
  *   |y| <= (K + 1/2)/2^r, r double angles 2c^2 - 1: sin(2 pi u)) and
  *   SlotToCoeff (U times q_0 / (2 pi 2^log2_boost s_ref), one fold).
  * It consumes cts_levels + depth(degree) + r + 1 levels from the top
@@ -560,20 +577,19 @@ typedef struct {
     const double *coeffs;  /* degree + 1 power-basis coefficients in y, or NULL: the library's
                               interpolant at the degree + 1 Chebyshev points of the interval */
 } helrm_boot_desc;
-/* Encodes the three matrices (CoeffToSlot A and B at level L, SlotToCoeff at
- * the level EvalMod ends on) on the device.  HELRM_E_PARAM if the chain is
+/* Encodes the two matrices (CoeffToSlot at level L, SlotToCoeff at the level
+ * EvalMod ends on) on the device.  HELRM_E_PARAM if the chain is
  * too short, HELRM_E_INVAL for other bad parameters. */
 helrm_status helrm_boot_create(helrm_ctx *ctx, const helrm_boot_desc *desc, helrm_boot **out);
 /* info_out[6]: n_s, top level, SlotToCoeff level, output level, number of
- * encoded diagonals (A, then B, then S), degree. */
+ * encoded diagonals (CoeffToSlot's, then SlotToCoeff's), degree. */
 helrm_status helrm_boot_info(const helrm_boot *b, uint32_t *info_out);
 /* The slot rotations the keys must cover (SubSum, the BSGS steps, the fold). */
 helrm_status helrm_boot_rotations(const helrm_boot *b, int32_t *steps_out, uint32_t *n_out);
 /* The cosine polynomial in use (degree + 1 values). */
 helrm_status helrm_boot_coeffs(const helrm_boot *b, double *coeffs_out, uint32_t n);
-/* Borrowed matrix handles (0: CoeffToSlot on the ciphertext, 1: on its
- * conjugate, 2: SlotToCoeff), valid while b lives; for
- * helrm_ptmat_import / helrm_ptmat_export. */
+/* Borrowed matrix handles (0: CoeffToSlot, 1: SlotToCoeff), valid while b
+ * lives; for helrm_ptmat_import / helrm_ptmat_export. */
 helrm_status helrm_boot_matrix(const helrm_boot *b, uint32_t which, helrm_ptmat **out);
 /* out = the refreshed ciphertext at the output level, scale about Delta
  * (times in->scale / s_ref), slots decoding to the input's.  The input may

@@ -18,11 +18,11 @@ period n_s (2 n_s <= n = N/2), under a secret with h non-zero coefficients:
      coefficients at multiples of g and cancels the others;
   4. CoeffToSlot: the 2 n_s coefficients t_k of the polynomial in Y and its
      n_s slot values w_i are tied by w = U t, U[i, k] = xi^(k 5^i),
-     xi = exp(i pi / (2 n_s)), so t = (U^H w + U^T conj(w)) / (2 n_s).  Both
-     products, one on the ciphertext and one on its conjugate, are BSGS
-     matvecs of one shape that share their giant steps (reading R31); the
-     slots (period 2 n_s) then hold u_k / 2^r, u_k = m_k / q_0 + I_k, at
-     about eval_scale.  The diagonals are encoded at eval_scale times the
+     xi = exp(i pi / (2 n_s)), so t = (U^H w + U^T conj(w)) / (2 n_s).  The
+     second term is the conjugate of the first (U^T conj(w) = conj(U^H w)),
+     so one BSGS matvec C = U^H w / (2 n_s) and the conjugate of its output
+     give t = C + conj(C); the slots (period 2 n_s) then hold u_k / 2^r,
+     u_k = m_k / q_0 + I_k, at about eval_scale.  The diagonals are encoded at eval_scale times the
      primes the product is rescaled by, over q_0: one rescale when the top
      primes are 60-bit (the bootstrappable chain), two on an all-40-bit
      chain, so that their rounding stays below the noise;
@@ -96,7 +96,7 @@ class Boot:
     bp: BootParams
     g: int                       # N / (2 n_s)
     level_top: int
-    cts: list                    # [A, B]: PtMatrix on ct and on conj(ct), at level L
+    cts: list                    # [A]: the CoeffToSlot PtMatrix, at level L
     stc: linear.PtMatrix
     coeffs: list
     subsum_steps: list = field(default_factory=list)
@@ -126,14 +126,13 @@ def prepare(p: ckks.Params, bp: BootParams) -> Boot:
     pt_cts /= float(p.q[0])
     out_cts = float(p.q[0]) * pt_cts / float(p.q[L])
     A = linear.prepare_scaled(p, f * U.conj().T, n_s, 2 * n_s, L, pt_cts, out_cts)
-    B = linear.prepare_scaled(p, f * U.T, n_s, 2 * n_s, L, pt_cts, out_cts)
     # SlotToCoeff at the level EvalMod ends on: from about eval_scale to Delta
     ls = L - levels_used(bp) + 1
     S = (float(p.q[0]) / (2 * math.pi * 2.0**bp.log2_boost * bp.s_ref)) * U
     stc = linear.prepare_scaled(p, S, 2 * n_s, n_s, ls, float(p.q[ls]) * p.delta / bp.eval_scale, p.delta)
     coeffs = list(bp.coeffs) if bp.coeffs is not None else cos_fit(bp.K, bp.r, bp.degree)
     steps = [n_s << i for i in range((p.n // n_s).bit_length() - 1)]
-    return Boot(bp, g, L, [A, B], stc, coeffs, steps)
+    return Boot(bp, g, L, [A], stc, coeffs, steps)
 
 
 def scales(p: ckks.Params, boot: Boot):
@@ -179,7 +178,8 @@ def subsum(p: ckks.Params, keys: ckks.Keys, ct: ckks.Ct, steps) -> ckks.Ct:
 
 
 def coeff_to_slot(p: ckks.Params, keys: ckks.Keys, boot: Boot, ct: ckks.Ct) -> ckks.Ct:
-    y = linear.matvec_sum(p, keys, boot.cts, [ct, ckks.conjugate(p, keys, ct)])
+    y = linear.matvec(p, keys, boot.cts[0], ct)
+    y = ckks.add(p, y, ckks.conjugate(p, keys, y))
     for _ in range(boot.bp.cts_levels - 1):
         y = ckks.rescale(p, y)
     return y

@@ -355,7 +355,8 @@ def compile_model(p: ckks.Params, spec, w) -> Compiled:
         """A bootstrap at `name` of a ciphertext at level 0 with `period`-periodic slots."""
         from . import boot as _boot
         assert lvl_now == 0
-        bt = _boot.prepare(p, _boot.BootParams(n_s=period, log2_boost=BOOT_LOG2_BOOST, s_ref=scale_now))
+        bt = _boot.prepare(p, _boot.BootParams(n_s=period, log2_boost=BOOT_LOG2_BOOST, s_ref=scale_now,
+                                               coeffs=getattr(spec, "boot_coeffs", None)))
         c.boots[name] = (bt, lvl_next)
         return lvl_next, _boot.out_scale(p, bt, scale_now)
     if dot:

@@ -313,9 +313,12 @@ helrm_status helrm_model_keygen(helrm_ctx *ctx, const helrm_model *m, uint64_t s
             steps.push_back(x.first);
             levels.push_back(x.second);
         }
-        std::unique_ptr<SecretKey> sk(keygen_sk(c, seed));
+        // a model with bootstraps needs a sparse secret (the sine covers |I| <= 24)
+        const bool boots = MOD(m)->has_boot();
+        std::unique_ptr<SecretKey> sk(keygen_sk(c, seed, boots ? 192 : 0));
         std::unique_ptr<EvalKey> evk(keygen_evk(c, sk.get(), seed, rl));
         keygen_rot(c, sk.get(), evk.get(), steps, levels);
+        if (boots) keygen_galois(c, sk.get(), evk.get(), {2ull * c->N - 1});
         CUDA_CHECK(cudaStreamSynchronize(c->stream));
         *sk_out = (helrm_sk *)sk.release();
         *evk_out = (helrm_evk *)evk.release();
@@ -1045,7 +1048,7 @@ helrm_status helrm_boot_coeffs(const helrm_boot *bh, double *coeffs_out, uint32_
 helrm_status helrm_boot_matrix(const helrm_boot *bh, uint32_t which, helrm_ptmat **out)
 {
     return guard(nullptr, [&] {
-        HCHECK(out && which < 3, HELRM_E_INVAL, "which must be 0, 1 or 2");
+        HCHECK(out && which < 2, HELRM_E_INVAL, "which must be 0 or 1");
         *out = (helrm_ptmat *)BT(bh)->matrices()[which];
     });
 }

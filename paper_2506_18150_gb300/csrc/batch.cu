@@ -1045,6 +1045,19 @@ static Owned dot_interaction_b(Ctx *c, const Batch *bt, const Model *m, const CC
     return relin_b(c, bt->evk, cd, lvl, c->delta * c->delta, true);
 }
 
+// every query's ciphertext bootstrapped (one query after another: a
+// bootstrap's launches already carry the whole ring) and dropped to the first
+// level of the next segment
+static Owned boot_all(Ctx *c, const Batch *bt, const Model::BootPoint &bp, const CCtVec &x)
+{
+    Owned o;
+    for (size_t q = 0; q < x.size(); q++) {
+        std::unique_ptr<Ciphertext> y(bootstrap(c, bt->evk[q], bp.b.get(), x[q]));
+        o.v.emplace_back(ct_drop(c, y.get(), bp.lvl_next));
+    }
+    return o;
+}
+
 std::vector<Ciphertext *> model_infer_batch(Ctx *c, const Batch *bt, const CCtVec &ct_dense, const CCtVec &ct_sel)
 {
     const Model *m = bt->model;
@@ -1092,10 +1105,16 @@ std::vector<Ciphertext *> model_infer_batch(Ctx *c, const Batch *bt, const CCtVe
         }
     });
     CCtVec x = ct_dense;
-    for (auto &L : m->bottom) {
-        h = dense_layer_b(c, bt, L, x);
+    Owned hb;
+    for (size_t i = 0; i < m->bottom.size(); i++) {
+        if (m->boot_b[i].b) {
+            hb = boot_all(c, bt, m->boot_b[i], x);
+            x = hb.craw();
+        }
+        h = dense_layer_b(c, bt, m->bottom[i], x);
         x = h.craw();
     }
+    hb = Owned();
     branch.join();
     Owned z = add_b(c, h.craw(), e.craw());
     h = Owned();
@@ -1103,11 +1122,16 @@ std::vector<Ciphertext *> model_infer_batch(Ctx *c, const Batch *bt, const CCtVe
     Owned y;
     if (m->interaction == 0) {
         z = add_pt_b(c, z.craw(), m->ones.get());
+        if (m->boot_z.b) z = boot_all(c, bt, m->boot_z, z.craw());
         y = dot_interaction_b(c, bt, m, z.craw());
     } else {
         y = std::move(z);
+        if (m->boot_z.b) y = boot_all(c, bt, m->boot_z, y.craw());
     }
-    for (auto &L : m->top) y = dense_layer_b(c, bt, L, y.craw());
+    for (size_t i = 0; i < m->top.size(); i++) {
+        if (m->boot_t[i].b) y = boot_all(c, bt, m->boot_t[i], y.craw());
+        y = dense_layer_b(c, bt, m->top[i], y.craw());
+    }
     std::vector<Ciphertext *> out;
     for (auto &p : y.v) out.push_back(p.release());
     return out;
@@ -1127,6 +1151,7 @@ std::vector<Ciphertext *> model_infer_batch_graph(Ctx *c, Batch *bt, const CCtVe
     const size_t S = B * (size_t)m->n_sel();   // ct_sel is query-major, n_sel per query
     HCHECK(ct_dense.size() == B && ct_sel.size() == S, HELRM_E_INVAL, "batch size mismatch");
     HCHECK(!c->prof_on, HELRM_E_INVAL, "kernel profiling cannot be recorded inside a graph");
+    HCHECK(!m->has_boot(), HELRM_E_PARAM, "a model with bootstraps runs eagerly (no CUDA graph)");
     for (size_t q = 0; q < B; q++)
         HCHECK(ct_dense[q]->level == m->lvl_dense, HELRM_E_LEVEL, "ct_dense is not at the model's dense level");
     for (size_t r = 0; r < S; r++)

@@ -14,9 +14,9 @@
 //      Z[Y], Y = X^g, g = N / (2 n_s);
 //   4. CoeffToSlot: with U[i][k] = xi^(k 5^i), xi = exp(i pi / (2 n_s)), the
 //      2 n_s coefficients t of the polynomial in Y are (U^H w + U^T conj(w)) /
-//      (2 n_s) for its n_s slot values w; the two BSGS products (on the
-//      ciphertext and on its conjugate, X -> X^(2N-1)) share their giant
-//      steps, ModDown and rescale (linear.cu, matvec_sum), and the slots
+//      (2 n_s) for its n_s slot values w; the second term is the conjugate
+//      of the first, so one BSGS product C = U^H w / (2 n_s) and its
+//      conjugate (X -> X^(2N-1)) give t = C + conj(C), and the slots
 //      (period 2 n_s) hold u_k / 2^r, u_k = m_k / q_0 + I_k, at about
 //      eval_scale after cts_levels rescales;
 //   5. EvalMod: y - 1 / (4 2^r) (a constant), a polynomial fit of
@@ -143,23 +143,19 @@ Boot *boot_create(Ctx *c, const BootDesc &d)
     const int g = c->N / (2 * n_s);
     std::vector<double> ure, uim;
     slot_matrix(n_s, ure, uim);
-    // CoeffToSlot: A = f U^H, B = f U^T (2 n_s x n_s), f = 1 / (2 n_s g 2^r)
+    // CoeffToSlot: A = f U^H (2 n_s x n_s), f = 1 / (2 n_s g 2^r)
     const double f = 1.0 / (2.0 * n_s * g * std::ldexp(1.0, d.r));
     double pt_cts = d.eval_scale;
     for (int i = 0; i < d.cts_levels; i++) pt_cts *= (double)c->primes[L - i];
     pt_cts /= (double)c->primes[0];
     const double out_cts = (double)c->primes[0] * pt_cts / (double)c->primes[L];
-    std::vector<double> are((size_t)2 * n_s * n_s), aim(are.size()), bre(are.size()), bim(are.size());
+    std::vector<double> are((size_t)2 * n_s * n_s), aim(are.size());
     for (int k = 0; k < 2 * n_s; k++)
         for (int i = 0; i < n_s; i++) {
-            const double x = ure[(size_t)i * 2 * n_s + k], y = uim[(size_t)i * 2 * n_s + k];
-            are[(size_t)k * n_s + i] = f * x;
-            aim[(size_t)k * n_s + i] = f * -y;
-            bre[(size_t)k * n_s + i] = f * x;
-            bim[(size_t)k * n_s + i] = f * y;
+            are[(size_t)k * n_s + i] = f * ure[(size_t)i * 2 * n_s + k];
+            aim[(size_t)k * n_s + i] = f * -uim[(size_t)i * 2 * n_s + k];
         }
     b->cts_a.reset(ptmat_prepare_scaled(c, are.data(), aim.data(), 2 * n_s, n_s, n_s, 2 * n_s, L, pt_cts, out_cts));
-    b->cts_b.reset(ptmat_prepare_scaled(c, bre.data(), bim.data(), 2 * n_s, n_s, n_s, 2 * n_s, L, pt_cts, out_cts));
     // SlotToCoeff: S = (q_0 / (2 pi 2^b s_ref)) U (n_s x 2 n_s), from about eval_scale to Delta
     const int ls = b->level_stc;
     const double fs = (double)c->primes[0] / (2.0 * M_PI * std::ldexp(1.0, d.log2_boost) * d.s_ref);
@@ -233,9 +229,12 @@ Ciphertext *bootstrap(Ctx *c, const EvalKey *evk, const Boot *b, const Ciphertex
         x.reset(ct_add(c, x.get(), r.get()));
     }
     stage(x);
-    // 4. CoeffToSlot: the ciphertext and its conjugate, giant steps shared
-    P xc(ct_apply_galois(c, evk, x.get(), 2ull * N - 1));
-    P y(matvec_sum(c, evk, {b->cts_a.get(), b->cts_b.get()}, {x.get(), xc.get()}));
+    // 4. CoeffToSlot: C = A w, then C + conj(C)
+    P y(matvec(c, evk, b->cts_a.get(), x.get()));
+    {
+        P yc(ct_apply_galois(c, evk, y.get(), 2ull * N - 1));
+        y.reset(ct_add(c, y.get(), yc.get()));
+    }
     for (int i = 1; i < b->cts_levels; i++) y.reset(ct_rescale(c, y.get()));
     stage(y);
     // 5. EvalMod

@@ -200,12 +200,57 @@ Model *model_create(Ctx *c, const helrm_model_desc *d)
         act_lin[0] = 0.0;
     }
     const int ad = act.empty() ? 1 : poly_depth((int)d->act_degree);
-    m->lvl_u = (1 + ad) * (nt - 1) + 1;
-    m->lvl_z = dot ? m->lvl_u + 2 : m->lvl_u;
-    m->lvl_sel = m->lvl_z + 1;
-    m->lvl_dense = m->lvl_z + (1 + ad) * nb;
-    HCHECK(m->lvl_dense <= c->L, HELRM_E_PARAM,
-           "model needs " + std::to_string(m->lvl_dense) + " levels, chain has " + std::to_string(c->L));
+    // Bootstrap points split the network into segments; every segment is
+    // planned as late as possible and ends at level 0 (costs: a layer 1 + ad,
+    // the last top layer 1, the dot interaction 2).
+    HCHECK((d->boot_bottom & 1u) == 0 && (d->boot_top & 1u) == 0 && (nb >= 32 || (d->boot_bottom >> nb) == 0) &&
+               (nt >= 32 || (d->boot_top >> nt) == 0),
+           HELRM_E_INVAL, "bootstrap points must lie before bottom / top layers 1 .. n-1");
+    std::vector<char> pb(nb, 0), pt(nt, 0);
+    for (int i = 1; i < nb; i++) pb[i] = (d->boot_bottom >> i) & 1u;
+    for (int i = 1; i < nt; i++) pt[i] = (d->boot_top >> i) & 1u;
+    const bool pz = d->boot_z != 0;
+    std::vector<int> lv_b(nb), lv_t(nt);
+    int lv = 0;
+    for (int i = nt - 1; i >= 0; i--) {
+        lv += (i + 1 < nt) ? 1 + ad : 1;
+        lv_t[i] = lv;
+        if (pt[i]) lv = 0;
+    }
+    lv += dot ? 2 : 0;
+    const int lv_I = lv;
+    if (pz) lv = 0;
+    for (int i = nb - 1; i >= 0; i--) {
+        lv += 1 + ad;
+        lv_b[i] = lv;
+        if (pb[i]) lv = 0;
+    }
+    const bool boots = pz || std::count(pb.begin(), pb.end(), 1) || std::count(pt.begin(), pt.end(), 1);
+    const int boot_levels = 1 + poly_depth(16) + 6 + 1;   // the bootstraps' CoeffToSlot, cosine, double angles, SlotToCoeff
+    const int cap = boots ? c->L - boot_levels : c->L;
+    m->lvl_u = lv_t[0];
+    m->lvl_z = lv_I;
+    m->lvl_h = pz ? 0 : lv_I;
+    m->lvl_sel = m->lvl_h + 1;
+    m->lvl_dense = lv_b[0];
+    int need = std::max({*std::max_element(lv_b.begin(), lv_b.end()), *std::max_element(lv_t.begin(), lv_t.end()),
+                         lv_I, m->lvl_sel});
+    HCHECK(need <= cap, HELRM_E_PARAM,
+           "model needs " + std::to_string(need) + " levels, chain has " + std::to_string(cap) +
+               (boots ? " below its bootstrapping levels" : ""));
+    m->boot_b.resize(nb);
+    m->boot_t.resize(nt);
+    std::vector<double> boot_coeffs;
+    if (d->boot_coeffs) boot_coeffs.assign(d->boot_coeffs, d->boot_coeffs + 17);
+    // a bootstrap of the level-0 ciphertext with period-n_s slots and scale `scale`
+    auto boot_point = [&](Model::BootPoint &bp, int n_s, int &lvl, double &scale, int lvl_next) {
+        HCHECK(lvl == 0, HELRM_E_PARAM, "internal: a segment does not end at level 0");
+        BootDesc bd{n_s, 24, 6, 16, 8, 1, scale, std::ldexp(1.0, 60), boot_coeffs};
+        bp.b.reset(boot_create(c, bd));
+        bp.lvl_next = lvl_next;
+        scale = bp.b->out_scale(scale);
+        lvl = lvl_next;
+    };
     m->Bp = dot ? m->B + 1 : m->B;
     m->W_z = pow2ceil(DIM * m->Bp);
     m->p_dense = pow2ceil(m->n_dense);
@@ -244,6 +289,7 @@ Model *model_create(Ctx *c, const helrm_model_desc *d)
     for (int i = 0; i < nb; i++) {
         const int rows = (int)d->bottom_widths[i + 1], cols = (int)d->bottom_widths[i];
         const int out_pad = (i + 1 == nb) ? m->W_z : pow2ceil(rows);
+        if (pb[i]) boot_point(m->boot_b[i], in_pad, lvl, scale, lv_b[i]);
         Layer L;
         L.pm.reset(ptmat_prepare(c, d->bottom_W[i], rows, cols, in_pad, out_pad, lvl, scale, delta));
         L.bias.reset(encode_vec(c, replicate_bias(d->bottom_b[i], rows, out_pad), lvl - 1, delta, PT_PLAIN));
@@ -253,14 +299,17 @@ Model *model_create(Ctx *c, const helrm_model_desc *d)
         m->bottom.push_back(std::move(L));
         in_pad = out_pad;
     }
+    HCHECK(lvl == m->lvl_h, HELRM_E_PARAM, "internal: the bottom MLP does not end at the lookup's level");
     const double scale_b = scale;
     m->emb.reset(emb_prepare(c, cards, (int)d->base_p, thr, DIM, d->tables, DIM, m->W_z, m->lvl_sel, delta, scale_b));
-    double u_scale = scale_b;
+    double scale_z = scale_b;
+    if (pz) boot_point(m->boot_z, m->W_z, lvl, scale_z, lv_I);
+    double u_scale = scale_z;
     if (dot) {
         std::vector<double> ones(m->W_z, 0.0);
         for (int kk = 0; kk < DIM; kk++) ones[DIM * m->B + kk] = 1.0;
-        m->ones.reset(encode_vec(c, ones, m->lvl_z, scale_b, PT_PLAIN));
-        m->mask_scale = (double)c->primes[m->lvl_z] * delta / scale_b;
+        m->ones.reset(encode_vec(c, ones, m->lvl_h, scale_b, PT_PLAIN));
+        m->mask_scale = (double)c->primes[m->lvl_z] * delta / scale_z;
         std::vector<double> m0(m->W2, 0.0);
         for (int j = 0; j < DIM * m->Bp; j++) m0[j] = 1.0;
         m->masks.emplace_back(encode_vec(c, m0, m->lvl_z, m->mask_scale, PT_MONT));
@@ -278,6 +327,7 @@ Model *model_create(Ctx *c, const helrm_model_desc *d)
         const bool last = i + 1 == nt;
         const int rows = (int)d->top_widths[i + 1], cols = (int)d->top_widths[i];
         const int out_pad = pow2ceil(rows);
+        if (pt[i]) boot_point(m->boot_t[i], pow2ceil(cols), lvl, scale, lv_t[i]);
         Layer L;
         if (i == 0 && dot) {
             // first top layer over the interaction layout
@@ -333,6 +383,8 @@ void model_import(Ctx *c, Model *m, const i64 *coeffs, u32 count)
     if (m->emb->pm) m->emb->pm->upload_index();
     for (auto &ch : m->emb->chunks) ch->upload_index();
     for (auto &l : m->top) l.pm->upload_index();
+    for (const Model::BootPoint *bp : m->boot_points())
+        for (PtMatrix *pm : bp->b->matrices()) pm->upload_index();
 }
 
 void model_export(Ctx *c, Model *m, i64 *coeffs, u32 count)
@@ -457,6 +509,11 @@ std::vector<std::pair<int, int>> model_key_levels(const Model *m, int *relin_lev
     for (auto &L : m->top) {
         mat(L.pm.get());
         if (L.square) rl = std::max(rl, L.pm->level - 1);
+    }
+    // a bootstrap works at the top of the chain (its keys at full level)
+    for (const Model::BootPoint *bp : m->boot_points()) {
+        for (int st : bp->b->rotations()) use(st, m->ctx->L);
+        rl = m->ctx->L;
     }
     *relin_level = std::max(rl, 0);
     return std::vector<std::pair<int, int>>(lv.begin(), lv.end());

@@ -43,6 +43,44 @@ std::vector<Ciphertext *> poly_b(Ctx *c, const std::vector<const EvalKey *> &evk
 Ciphertext *ct_poly_eval(Ctx *c, const EvalKey *evk, const Ciphertext *x, const std::vector<double> &a,
                          double target);
 
+// Bootstrapping of a ciphertext whose real slots are periodic with period n_s
+// (boot.cu): ModRaise, SubSum, CoeffToSlot (one product and the conjugate
+// of its output), EvalMod (cosine fit, r double angles), SlotToCoeff.
+struct Boot : Handle {
+    Ctx *ctx;
+    int n_s = 0, K = 0, r = 0, degree = 0, log2_boost = 0, cts_levels = 1;
+    int level_top = 0, level_stc = 0, level_out = 0;
+    double s_ref = 0, eval_scale = 0;
+    std::vector<double> coeffs;                 // the cosine polynomial, power basis in y
+    std::unique_ptr<PtMatrix> cts_a;            // CoeffToSlot, at level_top
+    std::unique_ptr<PtMatrix> stc;              // SlotToCoeff at level_stc
+    std::vector<int> subsum_steps;
+    DevMem boost_mont;                          // 2^b per prime id, Montgomery form
+    // fixed at creation (no host synchronisation while bootstrapping, so a
+    // bootstrap can be captured in a CUDA graph): the CoeffToSlot output scale,
+    // the EvalMod constants and polynomial plan, the SlotToCoeff scale factor
+    double s_cts = 0, s_eval = 0, c_out = 0;
+    DevMem c_shift;                             // round(-s_cts / (4 2^r)), plain residues per prime id
+    std::unique_ptr<ActPlan> plan;              // the cosine polynomial at (L - cts_levels, s_cts)
+    std::vector<DevMem> c_double;               // round(-scale) after each double angle's product
+    Boot(Ctx *c) : Handle(KIND_BOOT), ctx(c) {}
+    // the declared scale of the output for an input of scale in_scale
+    double out_scale(double in_scale) const { return c_out * (in_scale / s_ref); }
+    std::vector<int> rotations() const;
+    std::vector<PtMatrix *> matrices() const { return {cts_a.get(), stc.get()}; }
+};
+struct BootDesc {
+    int n_s, K, r, degree, log2_boost, cts_levels;
+    double s_ref, eval_scale;
+    std::vector<double> coeffs;   // empty: the library's Chebyshev fit
+};
+Boot *boot_create(Ctx *c, const BootDesc &d);
+std::vector<double> boot_cos_fit(int K, int r, int degree);
+// stages (optional, 5 entries): raised, subsum, CoeffToSlot, EvalMod, output
+// (the caller owns them; the output is also returned)
+Ciphertext *bootstrap(Ctx *c, const EvalKey *evk, const Boot *b, const Ciphertext *in,
+                      std::vector<Ciphertext *> *stages = nullptr);
+
 struct SelSeg {
     int t, j, off, width;
 };
@@ -79,7 +117,29 @@ struct Model : Handle {
     std::unique_ptr<Plaintext> ones;
     std::vector<std::unique_ptr<Plaintext>> masks;
     std::vector<double> act;   // the activation polynomial a_0 .. a_d (empty: x^2)
+    // bootstraps: before bottom layer i (boot_b[i], i >= 1), on z before the
+    // interaction (boot_z), before top layer i (boot_t[i], i >= 1); each lifts
+    // its input (level 0, the end of a segment) and drops it to lvl_next
+    struct BootPoint {
+        std::unique_ptr<Boot> b;
+        int lvl_next = 0;
+    };
+    std::vector<BootPoint> boot_b, boot_t;
+    BootPoint boot_z;
+    int lvl_h = 0;   // level of z = h + e (lvl_z unless z is bootstrapped)
     Model(Ctx *c) : Handle(KIND_MODEL), ctx(c) {}
+    // the bootstrap points in the order the inference meets them
+    std::vector<const BootPoint *> boot_points() const
+    {
+        std::vector<const BootPoint *> v;
+        for (auto &x : boot_b)
+            if (x.b) v.push_back(&x);
+        if (boot_z.b) v.push_back(&boot_z);
+        for (auto &x : boot_t)
+            if (x.b) v.push_back(&x);
+        return v;
+    }
+    bool has_boot() const { return !boot_points().empty(); }
 
     // the lookup's matrices: one, or one per ciphertext of a wide selector
     std::vector<PtMatrix *> emb_mats() const
@@ -106,6 +166,9 @@ struct Model : Handle {
             for (auto &m : masks) out.push_back(&m);
         }
         for (auto &l : top) layer(l);
+        for (const BootPoint *bp : boot_points())
+            for (PtMatrix *pm : bp->b->matrices())
+                for (auto &p : pm->pts) out.push_back(&p);
         return out;
     }
     std::vector<int> rotations() const
@@ -119,6 +182,7 @@ struct Model : Handle {
             for (int s = 1; s <= S; s++) st.push_back(DIM * s);
         }
         for (auto &l : top) addv(l.pm->rotations());
+        for (const BootPoint *bp : boot_points()) addv(bp->b->rotations());
         std::sort(st.begin(), st.end());
         st.erase(std::unique(st.begin(), st.end()), st.end());
         return st;
@@ -129,43 +193,5 @@ struct Model : Handle {
 Ciphertext *model_infer(Ctx *c, const EvalKey *evk, const Model *m, const Ciphertext *ct_dense,
                         const std::vector<const Ciphertext *> &ct_sel);
 
-// Bootstrapping of a ciphertext whose real slots are periodic with period n_s
-// (boot.cu): ModRaise, SubSum, CoeffToSlot (the ciphertext and its
-// conjugate, giant steps shared), EvalMod (cosine fit, r double angles),
-// SlotToCoeff.
-struct Boot : Handle {
-    Ctx *ctx;
-    int n_s = 0, K = 0, r = 0, degree = 0, log2_boost = 0, cts_levels = 1;
-    int level_top = 0, level_stc = 0, level_out = 0;
-    double s_ref = 0, eval_scale = 0;
-    std::vector<double> coeffs;                 // the cosine polynomial, power basis in y
-    std::unique_ptr<PtMatrix> cts_a, cts_b;     // CoeffToSlot on ct and on conj(ct), at level_top
-    std::unique_ptr<PtMatrix> stc;              // SlotToCoeff at level_stc
-    std::vector<int> subsum_steps;
-    DevMem boost_mont;                          // 2^b per prime id, Montgomery form
-    // fixed at creation (no host synchronisation while bootstrapping, so a
-    // bootstrap can be captured in a CUDA graph): the CoeffToSlot output scale,
-    // the EvalMod constants and polynomial plan, the SlotToCoeff scale factor
-    double s_cts = 0, s_eval = 0, c_out = 0;
-    DevMem c_shift;                             // round(-s_cts / (4 2^r)), plain residues per prime id
-    std::unique_ptr<ActPlan> plan;              // the cosine polynomial at (L - cts_levels, s_cts)
-    std::vector<DevMem> c_double;               // round(-scale) after each double angle's product
-    Boot(Ctx *c) : Handle(KIND_BOOT), ctx(c) {}
-    // the declared scale of the output for an input of scale in_scale
-    double out_scale(double in_scale) const { return c_out * (in_scale / s_ref); }
-    std::vector<int> rotations() const;
-    std::vector<PtMatrix *> matrices() const { return {cts_a.get(), cts_b.get(), stc.get()}; }
-};
-struct BootDesc {
-    int n_s, K, r, degree, log2_boost, cts_levels;
-    double s_ref, eval_scale;
-    std::vector<double> coeffs;   // empty: the library's Chebyshev fit
-};
-Boot *boot_create(Ctx *c, const BootDesc &d);
-std::vector<double> boot_cos_fit(int K, int r, int degree);
-// stages (optional, 5 entries): raised, subsum, CoeffToSlot, EvalMod, output
-// (the caller owns them; the output is also returned)
-Ciphertext *bootstrap(Ctx *c, const EvalKey *evk, const Boot *b, const Ciphertext *in,
-                      std::vector<Ciphertext *> *stages = nullptr);
 
 }  // namespace helrm

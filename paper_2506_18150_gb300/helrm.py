@@ -56,7 +56,9 @@ class ModelDesc(C.Structure):
                 ("n_tables", C.c_uint32), ("cards", C.POINTER(C.c_uint64)), ("base_p", C.c_uint32),
                 ("dim", C.c_uint32), ("tables", C.POINTER(C.POINTER(C.c_float))),
                 ("interaction", C.c_int32), ("threshold", C.c_uint64),
-                ("act_degree", C.c_uint32), ("act_coeffs", C.POINTER(C.c_double))]
+                ("act_degree", C.c_uint32), ("act_coeffs", C.POINTER(C.c_double)),
+                ("boot_bottom", C.c_uint32), ("boot_z", C.c_uint32), ("boot_top", C.c_uint32),
+                ("boot_coeffs", C.POINTER(C.c_double))]
 
 
 _lib = None
@@ -584,6 +586,20 @@ def helrm_model_create(ctx, spec, w):
         keep.append(acts)
         d.act_degree = len(acts) - 1
         d.act_coeffs = acts.ctypes.data_as(_dp)
+    for pt in getattr(spec, "boot", ()) or ():
+        if pt == "z":
+            d.boot_z = 1
+        elif pt[0] == "b":
+            d.boot_bottom |= 1 << int(pt[1:])
+        elif pt[0] == "t":
+            d.boot_top |= 1 << int(pt[1:])
+        else:
+            raise ValueError(f"unknown bootstrap point {pt}")
+    bc = getattr(spec, "boot_coeffs", None)
+    if bc is not None:
+        bca = np.ascontiguousarray(bc, dtype=np.float64)
+        keep.append(bca)
+        d.boot_coeffs = bca.ctypes.data_as(_dp)
     out = C.c_void_p()
     _check(ctx, lib().helrm_model_create(ctx.ptr, C.byref(d), C.byref(out)))
     return Handle(out.value, ctx)
@@ -828,7 +844,7 @@ def helrm_boot_coeffs(ctx, b):
 
 
 def helrm_boot_matrix(ctx, b, which: int):
-    """0: CoeffToSlot on the ciphertext, 1: on its conjugate, 2: SlotToCoeff (not freed by this handle)."""
+    """0: CoeffToSlot, 1: SlotToCoeff (not freed by this handle)."""
     out = C.c_void_p()
     _check(ctx, lib().helrm_boot_matrix(b.ptr, which, C.byref(out)))
     return Borrowed(out.value, b)

@@ -63,6 +63,7 @@ class DLRMSpec:
     threshold: int | None = None    # tables with more rows are digit-decomposed (None: base)
     act: tuple | None = None    # activation polynomial a_0..a_d (power basis); None: x^2
     boot: tuple = ()            # bootstrap points: "b<i>" before bottom layer i, "z" on z, "t<i>" before top layer i
+    boot_coeffs: tuple | None = None    # the bootstraps' cosine polynomial (None: each side's own fit)
 
 
 def act_apply(spec: DLRMSpec, v):
@@ -203,6 +204,32 @@ def criteo_spec(seed: int = 0, interaction: str = "dot") -> DLRMSpec:
     s = DLRMSpec("criteo", 13, [13, 512, 256, 64, 16], [0, 512, 256, 1], criteo_cards(seed), 64, 16,
                  interaction)
     s.top[0] = top_input_width(s)
+    return s
+
+
+def criteo_silu_boot_spec(seed: int = 0) -> DLRMSpec:
+    """The Criteo-shaped model with the degree-7 SiLU fit as every activation
+    (depth 4: five levels per activated layer, 34 in all), as the paper runs
+    its Criteo models with polynomial activations between bootstraps (Sec.
+    5.4): on the bootstrappable chain (13 compute levels) it bootstraps twice,
+    before bottom layer 2 (256 slots) and on z before the interaction (512
+    slots)."""
+    s = criteo_spec(seed)
+    s.name = "criteo_silu_boot"
+    s.act = silu_poly(7)
+    s.boot = ("b2", "z")
+    return s
+
+
+def uci_silu_boot_spec(seed: int = 0, boot=("b1", "z")) -> DLRMSpec:
+    """A small model for the bootstrapped path: the UCI-shaped SiLU model with
+    the concatenation interaction (its layout fits n = 512 slots, N = 2^10),
+    bootstrapping before bottom layer 1 (32 slots) and on z (256 slots)."""
+    s = uci_silu_spec(seed)
+    s.name = "uci_silu_boot"
+    s.interaction = "concat"
+    s.top[0] = top_input_width(s)
+    s.boot = tuple(boot)
     return s
 
 

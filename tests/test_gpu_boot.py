@@ -26,7 +26,7 @@ def _gpu_boot(ctx, p, b_or):
     """The library's bootstrapping with the oracle's polynomial and diagonals imported."""
     from paper_2506_18150_gb300 import helrm as H
     bt = H.helrm_boot_create(ctx, b_or.bp.n_s, coeffs=b_or.coeffs)
-    mats = [b_or.cts[0], b_or.cts[1], b_or.stc]
+    mats = [b_or.cts[0], b_or.stc]
     info = H.helrm_boot_info(ctx, bt)
     assert info["n_plaintexts"] == sum(len(pm.pts) for pm in mats)
     for w, pm in enumerate(mats):
@@ -109,7 +109,7 @@ def test_library_constants_next_to_the_oracle():
     pv = np.polynomial.polynomial.polyval
     assert np.max(np.abs(pv(y, cf) - pv(y, want))) < 1e-12
     assert np.max(np.abs(pv(y, cf) - np.cos(2 * np.pi * y))) < 1e-12
-    for w, pm in enumerate([b_or.cts[0], b_or.cts[1], b_or.stc]):
+    for w, pm in enumerate([b_or.cts[0], b_or.stc]):
         got = H.helrm_ptmat_export(ctx, H.helrm_boot_matrix(ctx, bt, w), len(pm.pts), p.N)
         ref = np.stack([pm.pts[k] for k in pm.ordered_keys()])
         assert np.max(np.abs(got - ref)) <= 1, w
@@ -157,3 +157,71 @@ def test_bootstrap_full_size_refreshes_the_message():
     assert np.max(np.abs(got - z)) < 1e-4
     y2 = H.helrm_bootstrap(ctx, evk, bt, H.helrm_drop_level(ctx, y, 0))
     assert np.max(np.abs(H.helrm_decrypt(ctx, sk, y2, n_s) - z)) < 2e-4
+
+
+def test_bootstrapped_dlrm_bit_exact():
+    """The UCI-shaped SiLU model (concatenation) with bootstraps before bottom
+    layer 1 and on z, at N = 2^10 on the bootstrappable chain: with the
+    oracle's plaintexts (the bootstraps' diagonals included) and cosine
+    polynomial, the logit ciphertext of helrm_infer and of a batch of two
+    equals the oracle's word for word; the graph path refuses the model."""
+    from oracle import boot, ckks, dlrm
+    from paper_2506_18150_gb300 import helrm as H
+    from paper_2506_18150_gb300 import synthetic as syn
+    pr = syn.boot_params(10, 10)
+    p = oracle_params(pr)
+    spec = syn.uci_silu_boot_spec(0)
+    spec.boot_coeffs = tuple(boot.cos_fit(24, 6, 16))
+    w = syn.make_weights(spec, 0)
+    c = dlrm.compile_model(p, spec, w)
+    ctx = gpu_ctx(pr)
+    model = H.helrm_model_create(ctx, spec, w)
+    info = H.helrm_model_info(ctx, model)
+    assert (info["lvl_dense"], info["lvl_sel"]) == (c.lvl_dense, c.lvl_sel)
+    pts = c.plaintexts()
+    assert info["n_plaintexts"] == len(pts)
+    H.helrm_model_import_plaintexts(ctx, model, np.stack([np.asarray(x, dtype=np.int64) for x in pts]))
+    assert H.helrm_model_rotations(ctx, model) == c.rotation_steps()
+    sk, evk = H.helrm_model_keygen(ctx, model, 3)
+    _, keys = ckks.keygen(p, 3, rot_steps=c.rotation_steps(), h=H_SECRET, conj=True)
+    dense, idx = syn.make_queries(spec, 2, seed=5)
+    cts = [dlrm.encrypt_query(p, keys, c, dense[q], idx[q], 100 + 2 * q) for q in range(2)]
+    want = [dlrm.infer(p, keys, c, cd, cs) for cd, cs in cts]
+    for q, (cd, cs) in enumerate(cts):
+        assert_ct_equal(ctx, H.helrm_infer(ctx, evk, model, import_ct(ctx, cd), import_ct(ctx, cs)), want[q])
+    bt = H.helrm_batch_create(ctx, model, [evk, evk])
+    ys = H.helrm_infer_batch(ctx, bt, [import_ct(ctx, cd) for cd, _ in cts], [import_ct(ctx, cs) for _, cs in cts])
+    for q in range(2):
+        assert_ct_equal(ctx, ys[q], want[q])
+    H.helrm_batch_set_graph(ctx, bt, True)
+    with pytest.raises(H.HelrmError) as e:
+        H.helrm_infer_batch(ctx, bt, [import_ct(ctx, cts[0][0])] * 2, [import_ct(ctx, cts[0][1])] * 2)
+    assert e.value.name == "HELRM_E_PARAM"
+    logit = H.helrm_decrypt_logit(ctx, sk, ys[0])[0]
+    assert abs(logit - dlrm.dlrm_cleartext(spec, w, dense[0], idx[0])[0]) < 1e-4
+
+
+def test_criteo_silu_with_bootstraps_full_size():
+    """The Criteo-shaped model with SiLU activations at N = 2^16 on the
+    bootstrappable chain, bootstrapped before bottom layer 2 (256 slots) and
+    on z (512 slots): the library's own constants and keys, the client's
+    encryption and the decrypted logit against the FP64 model (3 queries)."""
+    from oracle import dlrm
+    from paper_2506_18150_gb300 import helrm as H
+    from paper_2506_18150_gb300 import synthetic as syn
+    pr = syn.boot_params()
+    ctx = gpu_ctx(pr)
+    spec = syn.criteo_silu_boot_spec(0)
+    w = syn.make_weights(spec, 0)
+    model = H.helrm_model_create(ctx, spec, w)
+    info = H.helrm_model_info(ctx, model)
+    assert (info["lvl_dense"], info["lvl_sel"]) == (10, 1)
+    sk, evk = H.helrm_model_keygen(ctx, model, 11)
+    dense, idx = syn.make_queries(spec, 3, seed=21)
+    for q in range(3):
+        cd, cs = H.helrm_encrypt_query(ctx, evk, model, dense[q], idx[q], 40 + 2 * q)
+        y = H.helrm_infer(ctx, evk, model, cd, cs)
+        assert H.helrm_ct_info(ctx, y)[0] == 0
+        got = H.helrm_decrypt_logit(ctx, sk, y)[0]
+        want = dlrm.dlrm_cleartext(spec, w, dense[q], idx[q])[0]
+        assert abs(got - want) < 1e-2, (q, got, want)

@@ -166,3 +166,42 @@ def test_bootstrap_on_the_forty_bit_chain_runs_at_lower_precision():
     assert out.level == 20 - 14
     err = np.max(np.abs(ckks.decrypt(p, sk, out).real - z))
     assert 1e-4 < err < 0.2
+
+
+def test_level_plan_segments():
+    """Segments between bootstrap points each end at level 0; without points
+    the plan is the single as-late-as-possible schedule."""
+    from oracle import dlrm
+    # Criteo-shaped with SiLU (depth 4): layers cost 5, the last top layer 1, the dot interaction 2
+    plan = dlrm.level_plan(4, 3, 4, True, ("b2", "z"))
+    assert plan == {"t2": 1, "t1": 6, "t0": 11, "I": 13, "b3": 5, "b2": 10, "b1": 5, "b0": 10, "h": 0}
+    plain = dlrm.level_plan(2, 2, 1, True, ())
+    lvl_u = (1 + 1) * (2 - 1) + 1
+    assert plain["t0"] == lvl_u and plain["I"] == lvl_u + 2 == plain["h"] and plain["b0"] == lvl_u + 2 + 2 * 2
+    with pytest.raises(ValueError):
+        dlrm.level_plan(2, 2, 1, True, ("b0",))          # before the first layer: not a point
+
+
+def test_bootstrapped_dlrm_matches_the_cleartext_model():
+    """The UCI-shaped SiLU model (concatenation) bootstrapped before bottom
+    layer 1 and on z, at N = 2^10 on the bootstrappable chain with 10 compute
+    levels: every segment ends at level 0 and the decrypted logit is the
+    FP64 model's."""
+    from oracle import dlrm
+    from paper_2506_18150_gb300 import synthetic as syn
+    pr = syn.boot_params(10, 10)
+    p = ckks.Params(pr["log_n"], pr["q_bits"], pr["n_p"], pr["p_bits"], pr["alpha"], pr["log2_scale"])
+    spec = syn.uci_silu_boot_spec(0)
+    w = syn.make_weights(spec, 0)
+    c = dlrm.compile_model(p, spec, w)
+    assert (c.lvl_dense, c.lvl_sel, c.lvl_h, c.lvl_z, c.lvl_u) == (5, 1, 0, 6, 6)
+    assert {k: (v[0].bp.n_s, v[1]) for k, v in c.boots.items()} == {"b1": (32, 5), "z": (256, 6)}
+    assert dlrm.boot_order(c) == ["b1", "z"]
+    sk, keys = ckks.keygen(p, 3, rot_steps=c.rotation_steps(), h=H, conj=True)
+    dense, idx = syn.make_queries(spec, 1, seed=5)
+    cd, cs = dlrm.encrypt_query(p, keys, c, dense[0], idx[0], 100)
+    y = dlrm.infer(p, keys, c, cd, cs)
+    assert y.level == 0
+    got = dlrm.decrypt_logit(p, sk, y)[0]
+    want = dlrm.dlrm_cleartext(spec, w, dense[0], idx[0])[0]
+    assert abs(got - want) < 1e-4

@@ -560,13 +560,15 @@ def one_query(E, wl, K, W, hbm, alu, seed=1000):
            "launches_per_step": launches_per_step,
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * (nd + nt),
                    "d2h_bytes_per_step": 8, "same_logits_as_value_path": same,
-                   "api": "helrm_infer_batch_e2e (graph-replayed batch of one, host buffers)",
+                   "api": "helrm_infer_batch_e2e (%s batch of one, host buffers)" % ("graph-replayed" if graph
+                                                                                     else "eager"),
                    "eager": e2e_eager,
                    "server": {"value": srv_value, "unit": UNIT, "steps": n_srv, "h2d_bytes_per_step": h2d_srv,
                               "d2h_bytes_per_step": 8 * h_logct.numel(),
                               "api": "helrm_ct_import x2 (query ciphertexts, coefficient domain, from pinned "
-                                     "host memory) + helrm_infer_batch (graph-replayed batch of one) + "
-                                     "helrm_ct_export (logit ciphertext to pinned host memory)"}},
+                                     "host memory) + helrm_infer_batch (%s batch of one) + "
+                                     "helrm_ct_export (logit ciphertext to pinned host memory)"
+                                     % ("graph-replayed" if graph else "eager")}},
            "roofline": roof}
     del bt1, sk, evk, host_cts
     gc.collect()

@@ -58,9 +58,9 @@ def _switch_key_task(job):
     """One oracle switching key, composed as the oracle's keygen composes it:
     key id 0 = relinearisation (s' = s^2), else the Galois element k (s' = s(X^k))."""
     from oracle import ckks, ring
-    pr, seed, k = job
+    pr, seed, k, h = job
     p = oracle_params(pr)
-    sk = ckks.secret_key(p, seed)
+    sk = ckks.secret_key(p, seed, h)
     mods = p.qp_mods(p.L)
     if k == 0:
         s_mod = ring.from_signed(sk.s, mods)
@@ -70,16 +70,19 @@ def _switch_key_task(job):
     return k, ckks.switch_key(p, seed, sk, target, k)
 
 
-def oracle_keys_pool(pr, seed, steps):
-    """The oracle's keys (public, relinearisation, one per rotation step),
+def oracle_keys_pool(pr, seed, steps, h=0, conj=False):
+    """The oracle's keys (public, relinearisation, one per rotation step and,
+    with conj, the conjugation key; a sparse secret of weight h if h > 0),
     each switching key made by the oracle's own key functions in a
     spawn-started process pool, one key per task; equal to ckks.keygen's."""
     from oracle import ckks
     p = oracle_params(pr)
-    sk = ckks.secret_key(p, seed)
+    sk = ckks.secret_key(p, seed, h)
     keys = ckks.Keys(seed, *ckks.public_key(p, seed, sk))
     gal = sorted({p.galois(st) for st in {int(r) % p.n for r in steps} - {0}})
-    jobs = [(pr, seed, 0)] + [(pr, seed, k) for k in gal]
+    if conj:
+        gal.append(p.conj_galois())
+    jobs = [(pr, seed, 0, h)] + [(pr, seed, k, h) for k in gal]
     cpus = os.cpu_count() or 1
     workers = max(1, min(16, cpus, len(jobs)))
     with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn"),            # a lost worker raises

@@ -819,11 +819,16 @@ def boot_measure(local, world, K, W, hbm, alu, n_s=BOOT_NS):
     barrier()
     l0 = H.helrm_ctx_launch_count(ctx)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    ncu_range = os.environ.get("HELRM_PROFILE_RANGE") == "1"   # lets `ncu --profile-from-start off` see only these steps
+    if ncu_range:
+        torch.cuda.profiler.start()
     ev[0].record(stream)
     for s in range(K):
         step(W + s)
         ev[s + 1].record(stream)
     torch.cuda.synchronize()
+    if ncu_range:
+        torch.cuda.profiler.stop()
     launches = (H.helrm_ctx_launch_count(ctx) - l0) / K
     per = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(K))
     value, total_ms = job_throughput(K, ev[0].elapsed_time(ev[K]), world)

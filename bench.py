@@ -876,7 +876,7 @@ def boot_measure(local, world, K, W, hbm, alu, n_s=BOOT_NS):
                    "api": "helrm_ct_import (level-0 ciphertext, pinned host memory) + helrm_bootstrap + "
                           "helrm_ct_export (refreshed ciphertext to pinned host memory)"},
            "config": {"workload": f"bootstrapping of n_s={n_s} periodic real slots, one per step (ModRaise, SubSum, "
-                                  f"CoeffToSlot on the ciphertext and its conjugate, EvalMod: degree-16 cosine and "
+                                  f"CoeffToSlot: one product and the conjugate of its output, EvalMod: degree-16 cosine and "
                                   f"6 double angles, SlotToCoeff)",
                       "ckks": "N=2^16, q0 60-bit + 13x40-bit + 13x60-bit, K=3x60-bit special, alpha=3, "
                               "secret h=192, Delta=2^40",

@@ -22,12 +22,16 @@ def libpath():
     return build.build()
 
 
-def test_header_declares_the_survey_boundary():
+def test_header_declares_the_boundary():
+    """The calls of the hot path's boundary: keys, encryption, the matvec and
+    the lookup, the inference, import/export, the client's packing, the NTT,
+    and bootstrapping."""
     names = declared()
     for must in ["helrm_keygen", "helrm_encrypt", "helrm_decrypt", "helrm_rotate", "helrm_ptct_matvec",
                  "helrm_embedding_lookup", "helrm_infer", "helrm_ct_export", "helrm_ct_import",
                  "helrm_query_pack", "helrm_emb_prepare", "helrm_ptmat_prepare", "helrm_free",
-                 "helrm_last_error", "helrm_ntt"]:
+                 "helrm_last_error", "helrm_ntt", "helrm_bootstrap", "helrm_boot_create", "helrm_keygen_ex",
+                 "helrm_conjugate"]:
         assert must in names
 
 

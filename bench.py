@@ -209,7 +209,7 @@ def alu_peaks(H, ctx):
 # profiles/ntt_traffic_criteo_dlrm_n16.md), against 29.77 MB of algorithmic
 # bytes per transform.  It holds for the sources it was taken on: reported
 # while their SHA-256 still matches, null otherwise.
-NTT_TRAFFIC = {"workload": "criteo", "bytes_per_launch": 32.53e6, "algorithmic_per_launch": 29.77e6,
+NTT_TRAFFIC = {"workload": "criteo", "bytes_per_launch": 32.80e6, "algorithmic_per_launch": 29.77e6,
                "sha256": {"ntt.cu": "3770ec2c28a75bf1784d58cd26d6dd7e72959c539994d9aa1e08ca1c465ef294",
                           "butterfly.cuh": "c18964e4e06f1b00915ec55936ad0b6bd0ad7a30966d19e64b31cc886fe0e95e",
                           "core.cuh": "9850591e1add3f99728e66f9a632545c7fecc69f2304fcd9fdc62a510748f42b"}}

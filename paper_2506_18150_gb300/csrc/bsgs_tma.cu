@@ -92,9 +92,16 @@ struct TmaGals {
 // 108 KB of stages per CTA): the consumers stall on stages still in flight
 // (the copies' latency under load exceeds two steps of arithmetic), so every
 // extra stage the shared memory holds is time the copies get to land.
+// With many digits (the 7- to 9-digit key switches at the top of the
+// bootstrappable chain) two stages of every row would not fit two CTAs per SM;
+// there the diagonal rows stay out of the stage (DD): the consumers read their
+// own diagonal words from global memory (coalesced, one word per thread and
+// giant step), issued before the key products they then wait behind, and
+// the stage keeps the digit and key rows only.
 template <int N2, int DN>
 struct Stage {
-    static constexpr int WORDS = (3 * DN + N2) * T;
+    static constexpr bool DD = 2 * (3 * DN + N2) * T * 8 > 108 * 1024;
+    static constexpr int WORDS = (3 * DN + (DD ? 0 : N2)) * T;
     static constexpr int S = (4 * WORDS * 8 <= 108 * 1024) ? 4 : (3 * WORDS * 8 <= 108 * 1024) ? 3 : 2;
 };
 
@@ -131,6 +138,7 @@ __global__ void __launch_bounds__(T + 32, 2) k_bsgs_tma(
     extern __shared__ __align__(128) u64 smem[];
     constexpr int SW = Stage<N2, DN>::WORDS;
     constexpr int S = Stage<N2, DN>::S;
+    constexpr bool DD = Stage<N2, DN>::DD;
     u64 *full = smem + S * SW;        // S mbarriers
     u64 *empty = full + S;            // S mbarriers
     __shared__ int sgb[64 * 8];
@@ -210,11 +218,11 @@ __global__ void __launch_bounds__(T + 32, 2) k_bsgs_tma(
                 st_gal[s] = (u32)bk.gal[b];
                 st_base[s] = src_base;
                 st_mask[s] = mask;
-                mbar_arrive_expect_tx(&full[s], (u32)(3 * DN + nd) * T * 8);
+                mbar_arrive_expect_tx(&full[s], (u32)(3 * DN + (DD ? 0 : nd)) * T * 8);
             }
             __syncwarp();
-            // rows: DN digit rows, 2 DN key rows, the present diagonal rows
-            for (int cidx = lane; cidx < 3 * DN + N2; cidx += 32) {
+            // rows: DN digit rows, 2 DN key rows, the present diagonal rows (not with DD)
+            for (int cidx = lane; cidx < 3 * DN + (DD ? 0 : N2); cidx += 32) {
                 const u64 *src = nullptr;
                 u64 *dst = nullptr;
                 if (cidx < DN) {
@@ -286,6 +294,15 @@ __global__ void __launch_bounds__(T + 32, 2) k_bsgs_tma(
         const u64 *st = smem + s * SW;
         const u32 mask = st_mask[s];
         const int src_loc = auto_src_x(xi, logN, st_gal[s]) - st_base[s];
+        u64 dd_g[DD ? N2 : 1];   // DD: this baby step's diagonal words, loaded before the key products
+        if constexpr (DD) {
+            const int b = blist[k];
+#pragma unroll
+            for (int g = 0; g < N2; g++) {
+                const int di = sgb[g * n1 + b];
+                dd_g[g] = di >= 0 ? __ldg(diag[di] + idx) : 0;
+            }
+        }
         Acc128 t0, t1;
 #pragma unroll
         for (int j = 0; j < DN; j++) {
@@ -297,7 +314,15 @@ __global__ void __launch_bounds__(T + 32, 2) k_bsgs_tma(
         if (qlimb) t0.mac(c0v, pm, pi.q);
         const u64 v0 = t0.reduce(pi.q, pi.qinv);
         const u64 v1 = t1.reduce(pi.q, pi.qinv);
-        if (N2 <= 4) {   // few diagonals: take them into registers and release the stage first
+        if constexpr (DD) {   // the stage holds no diagonals: release it, then the products
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+#pragma unroll
+            for (int g = 0; g < N2; g++) {
+                a0[g].mac(v0, dd_g[g], pi.q);
+                a1[g].mac(v1, dd_g[g], pi.q);
+            }
+        } else if (N2 <= 4) {   // few diagonals: take them into registers and release the stage first
             u64 dd[N2];
 #pragma unroll
             for (int g = 0; g < N2; g++) dd[g] = (mask >> g) & 1u ? st[(3 * DN + g) * T + tid] : 0;

@@ -221,6 +221,15 @@ def criteo_silu_boot_spec(seed: int = 0) -> DLRMSpec:
     return s
 
 
+def criteo_silu_boot_fixed_spec(seed: int = 0) -> DLRMSpec:
+    """criteo_silu_boot_spec with its SiLU coefficients rounded to multiples of
+    2^-20 (dyadic), for the full-size parity fixture (which also fixes the
+    bootstraps' cosine polynomial, spec.boot_coeffs, from its stored file)."""
+    s = criteo_silu_boot_spec(seed)
+    s.act = dyadic(s.act)
+    return s
+
+
 def uci_silu_boot_spec(seed: int = 0, boot=("b1", "z")) -> DLRMSpec:
     """A small model for the bootstrapped path: the UCI-shaped SiLU model with
     the concatenation interaction (its layout fits n = 512 slots, N = 2^10),

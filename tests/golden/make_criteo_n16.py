@@ -32,7 +32,15 @@ Cases:
       order, on ct_dense = Enc(int_poly(SEED_QUERY, 0)) at lvl_dense (seed
       40) and ct_sel = Enc(int_poly(SEED_QUERY, 1)) at lvl_sel (seed 41).
 
-Usage: python tests/golden/make_criteo_n16.py [--model uci_silu]
+With --model criteo_silu_boot it writes tests/golden/criteo_silu_boot_n16.json,
+the inference case alone, for the Criteo-shaped model with SiLU activations
+and two bootstraps on the bootstrappable chain (synthetic.boot_params(): 13
+compute and 13 bootstrapping primes, a secret with 192 non-zero
+coefficients): the SiLU and cosine coefficients rounded to multiples of 2^-20
+and 2^-44, and the bootstraps' diagonals int_poly integers like every other
+plaintext (they follow the model's in the canonical order).
+
+Usage: python tests/golden/make_criteo_n16.py [--model uci_silu | criteo_silu_boot]
 (about 13 minutes on 8 cores for the Criteo-shaped model)
 """
 from __future__ import annotations
@@ -85,17 +93,25 @@ def main(model: str = "criteo"):
     from paper_2506_18150_gb300 import synthetic as syn
 
     t0 = time.time()
-    pr = syn.PARAMS["full"]
+    boots = model == "criteo_silu_boot"
+    pr = syn.boot_params() if boots else syn.PARAMS["full"]
     p = oracle_params(pr)
-    spec = {"criteo": syn.criteo_spec, "uci_silu": syn.uci_silu_fixed_spec}[model](0)
+    spec = {"criteo": syn.criteo_spec, "uci_silu": syn.uci_silu_fixed_spec,
+            "criteo_silu_boot": syn.criteo_silu_boot_fixed_spec}[model](0)
+    if boots:   # the cosine polynomial of the bootstraps: the oracle's fit, rounded to multiples of 2^-44
+        from oracle import boot
+        spec.boot_coeffs = syn.dyadic(boot.cos_fit(24, 6, 16), bits=44)
     c = dlrm.compile_model(p, spec, syn.make_weights(spec, 0))
     steps = c.rotation_steps()
-    _, keys = oracle_keys_pool(pr, KEY_SEED, steps)
+    _, keys = oracle_keys_pool(pr, KEY_SEED, steps, h=192 if boots else 0, conj=boots)
     print(f"{len(steps)} rotation keys in {time.time() - t0:.0f} s", flush=True)
     res = {"recipe": {"params": pr, "key_seed": KEY_SEED, "seed_model": SEED_MODEL, "seed_query": SEED_QUERY,
                       "seed_matvec": SEED_MV, "bound": BOUND, "rotation_steps": steps,
                       "lvl_dense": c.lvl_dense, "lvl_sel": c.lvl_sel},
            "cases": {}}
+    if boots:
+        res["recipe"]["boot_coeffs"] = list(spec.boot_coeffs)
+        res["recipe"]["act"] = list(spec.act)
 
     for k, (name, level, rows, cols, ip, op) in enumerate(matvec_shapes(c) if model == "criteo" else []):
         t1 = time.time()
@@ -135,6 +151,11 @@ def main(model: str = "criteo"):
         lay.bias = next(it)
         if lay.act_const is not None:
             lay.act_const = next(it)
+    for name in dlrm.boot_order(c):
+        bt = c.boots[name][0]
+        for pm in bt.cts + [bt.stc]:
+            for key in pm.ordered_keys():
+                pm.pts[key] = next(it)
     assert next(it, None) is None
     assert all(np.array_equal(a, b) for a, b in zip(c.plaintexts(), ints))
     cd = ckks.encrypt(p, keys, syn.int_poly(SEED_QUERY, 0, p.N, BOUND), c.lvl_dense, p.delta, 40)
@@ -153,5 +174,5 @@ def main(model: str = "criteo"):
 if __name__ == "__main__":
     import argparse
     ap = argparse.ArgumentParser()
-    ap.add_argument("--model", default="criteo", choices=["criteo", "uci_silu"])
+    ap.add_argument("--model", default="criteo", choices=["criteo", "uci_silu", "criteo_silu_boot"])
     main(ap.parse_args().model)

@@ -148,9 +148,42 @@ def bench_multi(n_cts: int, level: int, reps: int):
             "ms_per_lookup": s0.elapsed_time(s1) / reps, "max_abs_err": float(np.max(np.abs(got - want)))}
 
 
+def bench_boot_matvec(log_n: int, n_s: int, reps: int):
+    """The CoeffToSlot product of a bootstrap (its BSGS matvec at the top of
+    the bootstrappable chain: 9 key-switching digits) on a ciphertext of
+    n_s-periodic slots at N = 2^log_n, with keys for its rotations only; the
+    first product is a warm-up.  Reports ms per product per kernel family."""
+    import torch
+
+    from . import helrm as H
+    from . import synthetic as syn
+    pr = syn.boot_params(log_n)
+    ctx = H.helrm_ctx_create(pr["log_n"], pr["q_bits"], pr["n_p"], pr["p_bits"], pr["alpha"], pr["log2_scale"],
+                             device=torch.cuda.current_device(), stream=torch.cuda.current_stream().cuda_stream)
+    bt = H.helrm_boot_create(ctx, n_s)
+    m = H.helrm_boot_matrix(ctx, bt, 0)
+    _, evk = H.helrm_keygen_ex(ctx, 5, 192, H.helrm_ptmat_rotations(ctx, m))
+    n = 1 << (log_n - 1)
+    z = np.random.default_rng(1).uniform(-1, 1, n_s)
+    top = len(pr["q_bits"]) - 1
+    ct = H.helrm_encrypt(ctx, evk, H.helrm_encode(ctx, z[np.arange(n) % n_s], top, 2.0**40), 4)
+    H.helrm_ptct_matvec(ctx, evk, m, ct)
+    torch.cuda.synchronize()
+    H.helrm_ctx_profile(ctx, True)
+    for _ in range(reps):
+        H.helrm_ptct_matvec(ctx, evk, m, ct)
+    rep = H.helrm_ctx_profile_report(ctx)
+    H.helrm_ctx_profile(ctx, False)
+    return {"log_n": log_n, "n_s": n_s, "level": top,
+            "kernels": {k: {"ms_per_product": v[1] / reps, "GBps": v[2] / (v[1] / 1000) / 1e9 if v[1] else None}
+                        for k, v in rep.items()}}
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["ntt", "rotate", "matvec", "multi"])
+    ap.add_argument("what", choices=["ntt", "rotate", "matvec", "multi", "boot_matvec"])
+    ap.add_argument("--log-n", type=int, default=14, help="boot_matvec: ring degree 2^log_n")
+    ap.add_argument("--ns", type=int, default=256, help="boot_matvec: slot period")
     ap.add_argument("--cts", type=int, default=18)
     ap.add_argument("--D", type=int, default=256)
     ap.add_argument("--limbs", type=int, default=192)
@@ -164,6 +197,8 @@ def main():
         r = bench_rotate(a.level, a.reps)
     elif a.what == "multi":
         r = bench_multi(a.cts, a.level, a.reps)
+    elif a.what == "boot_matvec":
+        r = bench_boot_matvec(a.log_n, a.ns, a.reps)
     else:
         r = bench_matvec(a.D, a.level, a.reps)
     print(json.dumps(r))

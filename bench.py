@@ -65,7 +65,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "encrypted DLRM inferences/s"
 UNIT = "inferences/s"
-ONE_QUERY = ("criteo", "uci", "uci_silu", "criteo_silu_boot")
+ONE_QUERY = ("criteo", "uci", "uci_silu", "criteo_silu_boot", "criteo_relu_boot")
 
 
 def parse(argv=None):
@@ -77,7 +77,8 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="criteo",
-                    choices=["criteo", "uci", "uci_silu", "criteo_silu_boot", "batched", "served", "tiny", "boot"])
+                    choices=["criteo", "uci", "uci_silu", "criteo_silu_boot", "criteo_relu_boot", "batched", "served",
+                             "tiny", "boot"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="one-query line only (no uci/batched/config4/served keys)")
     ap.add_argument("--requests", type=int, default=1000, help="served: requests per arrival rate")
@@ -101,11 +102,15 @@ DESC = {
     "criteo_silu_boot": "Criteo-shaped DLRM, 1 query/step, as 'criteo' but every activation is the degree-6 "
                         "SiLU polynomial (34 levels in all), with 2 bootstraps per query (before bottom layer 2, "
                         "256 slots; on z before the interaction, 512 slots)",
+    "criteo_relu_boot": "Criteo-shaped DLRM, 1 query/step, as 'criteo' but every activation is a degree-14 "
+                        "least-squares ReLU polynomial on [-6, 6] (44 levels in all), with 3 bootstraps per query "
+                        "(before bottom layer 2, 256 slots; on z, 512 slots; before top layer 1, 512 slots)",
 }
 CKKS = "N=2^16, q0 60-bit + 20x40-bit, K=3x60-bit special, alpha=3, Delta=2^40"
 CKKS_BOOT = "N=2^16, q0 60-bit + 13x40-bit + 13x60-bit, K=3x60-bit special, alpha=3, secret h=192, Delta=2^40"
 SPECS = {"uci": "uci_spec", "criteo": "criteo_spec", "uci_silu": "uci_silu_spec",
-         "criteo_silu_boot": "criteo_silu_boot_spec"}
+         "criteo_silu_boot": "criteo_silu_boot_spec", "criteo_relu_boot": "criteo_relu_boot_spec"}
+BOOT_WORKLOADS = ("criteo_silu_boot", "criteo_relu_boot")
 
 
 def workload_config(name, world=1):
@@ -898,7 +903,7 @@ def base_line(E, args, cfg):
 
 
 def run_ours(args):
-    E = Env(boot_chain=args.workload == "criteo_silu_boot")
+    E = Env(boot_chain=args.workload in BOOT_WORKLOADS)
     K, W = args.steps, args.warmup
     hbm = hbm_peak()
     alu = alu_peaks(E.H, E.ctx)
@@ -920,9 +925,10 @@ def run_ours(args):
         gc.collect()
         extras["boot"] = boot_measure(E.local, E.world, min(K, 10), min(W, 3), hbm, alu)
         E2 = Env(boot_chain=True)
-        b = one_query(E2, "criteo_silu_boot", min(K, 10), min(W, 3), hbm, alu)
-        b["config"] = workload_config("criteo_silu_boot", E.world)[1]
-        extras["criteo_silu_boot"] = b
+        for wl in BOOT_WORKLOADS:
+            b = one_query(E2, wl, min(K, 10), min(W, 3), hbm, alu)
+            b["config"] = workload_config(wl, E.world)[1]
+            extras[wl] = b
         del E2
         gc.collect()
     clk = clocks.stop()
@@ -934,12 +940,12 @@ def run_ours(args):
                      "value_note": ("value: the server path of a batch of one replayed as a CUDA graph "
                                     "(helrm_infer_batch_e2e_device); value_eager: every kernel launched on the "
                                     "stream (helrm_infer_e2e_device); both bit-identical")
-                     if args.workload != "criteo_silu_boot" else
+                     if args.workload not in BOOT_WORKLOADS else
                      ("value: the batch of one launched on the stream (a model with bootstraps runs without "
                       "a CUDA graph); value_eager: helrm_infer_e2e_device, the same launches"),
                      "e2e": main["e2e"], "roofline": main["roofline"]})
         line.update(extras)
-        if E.world == 1 and not args.no_cpu_baseline and args.workload != "criteo_silu_boot":
+        if E.world == 1 and not args.no_cpu_baseline and args.workload not in BOOT_WORKLOADS:
             line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)
     E.close()

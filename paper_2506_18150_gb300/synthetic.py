@@ -221,6 +221,21 @@ def criteo_silu_boot_spec(seed: int = 0) -> DLRMSpec:
     return s
 
 
+def criteo_relu_boot_spec(seed: int = 0) -> DLRMSpec:
+    """The Criteo-shaped model with a degree-14 least-squares ReLU stand-in as
+    every activation (relu_poly(15): powers {1, 2, 4, ..., 14}, depth 5: six
+    levels per activated layer, 44 in all), as the paper runs its Criteo
+    models with ReLU between bootstraps (Sec. 5.4, with composite
+    polynomials and 12 bootstraps): here three bootstraps, before bottom
+    layer 2 (256 slots), on z (512 slots) and before top layer 1 (512
+    slots)."""
+    s = criteo_spec(seed)
+    s.name = "criteo_relu_boot"
+    s.act = relu_poly(15)
+    s.boot = ("b2", "z", "t1")
+    return s
+
+
 def criteo_silu_boot_fixed_spec(seed: int = 0) -> DLRMSpec:
     """criteo_silu_boot_spec with its SiLU coefficients rounded to multiples of
     2^-20 (dyadic), for the full-size parity fixture (which also fixes the
@@ -330,12 +345,14 @@ def make_queries(spec: DLRMSpec, count: int, seed: int = 0):
     """(dense [count, n_dense] float64, indices [count, T] uint64).
 
     UCI-shaped dense features are N(0,1) with uniform indices; Criteo-shaped
-    dense features are LogNormal(0,1) with Zipf(1.1) ranks mapped to rows by a
-    seeded affine bijection r -> (a r + c) mod k, gcd(a, k) = 1."""
+    dense features are log(1 + x), x ~ LogNormal(0,1) (heavy-tailed counts
+    through the logarithm DLRM pipelines apply to Criteo's count features),
+    with Zipf(1.1) ranks mapped to rows by a seeded affine bijection
+    r -> (a r + c) mod k, gcd(a, k) = 1."""
     rng = np.random.default_rng([seed, 404])
     T = len(spec.cards)
     if spec.name.startswith("criteo"):
-        dense = rng.lognormal(0.0, 1.0, size=(count, spec.n_dense))
+        dense = np.log1p(rng.lognormal(0.0, 1.0, size=(count, spec.n_dense)))
         prm = np.random.default_rng([seed, 405])
         idx = np.zeros((count, T), dtype=np.uint64)
         for t, k in enumerate(spec.cards):

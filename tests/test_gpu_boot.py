@@ -201,21 +201,24 @@ def test_bootstrapped_dlrm_bit_exact():
     assert abs(logit - dlrm.dlrm_cleartext(spec, w, dense[0], idx[0])[0]) < 1e-4
 
 
-def test_criteo_silu_with_bootstraps_full_size():
-    """The Criteo-shaped model with SiLU activations at N = 2^16 on the
-    bootstrappable chain, bootstrapped before bottom layer 2 (256 slots) and
-    on z (512 slots): the library's own constants and keys, the client's
-    encryption and the decrypted logit against the FP64 model (3 queries)."""
+@pytest.mark.parametrize("name,levels", [("criteo_silu_boot_spec", (10, 1)), ("criteo_relu_boot_spec", (12, 1))])
+def test_criteo_with_bootstraps_full_size(name, levels):
+    """The Criteo-shaped model with polynomial activations at N = 2^16 on the
+    bootstrappable chain: SiLU (degree 6) bootstrapped before bottom layer 2
+    (256 slots) and on z (512 slots); the ReLU stand-in (degree 14)
+    bootstrapped there and before top layer 1 (512 slots).  The library's own
+    constants and keys, the client's encryption and the decrypted logit
+    against the FP64 model with the same polynomial (3 queries)."""
     from oracle import dlrm
     from paper_2506_18150_gb300 import helrm as H
     from paper_2506_18150_gb300 import synthetic as syn
     pr = syn.boot_params()
     ctx = gpu_ctx(pr)
-    spec = syn.criteo_silu_boot_spec(0)
+    spec = getattr(syn, name)(0)
     w = syn.make_weights(spec, 0)
     model = H.helrm_model_create(ctx, spec, w)
     info = H.helrm_model_info(ctx, model)
-    assert (info["lvl_dense"], info["lvl_sel"]) == (10, 1)
+    assert (info["lvl_dense"], info["lvl_sel"]) == levels
     sk, evk = H.helrm_model_keygen(ctx, model, 11)
     dense, idx = syn.make_queries(spec, 3, seed=21)
     for q in range(3):
@@ -224,4 +227,5 @@ def test_criteo_silu_with_bootstraps_full_size():
         assert H.helrm_ct_info(ctx, y)[0] == 0
         got = H.helrm_decrypt_logit(ctx, sk, y)[0]
         want = dlrm.dlrm_cleartext(spec, w, dense[q], idx[q])[0]
+        print(f"{name} query {q}: logit {got:.6f}, FP64 {want:.6f}, error {abs(got - want):.2e}")
         assert abs(got - want) < 1e-2, (q, got, want)

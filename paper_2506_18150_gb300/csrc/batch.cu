@@ -574,18 +574,20 @@ Owned mul_pt_b(Ctx *c, const CCtVec &a, const std::vector<const Plaintext *> &pt
 
 // rotations of every a[q] by every step (one ModUp per query, shared by its
 // steps): out[q * S + s], as ct_rotate_hoisted
-Owned rotate_b(Ctx *c, const std::vector<const EvalKey *> &evk, const CCtVec &a, const std::vector<int> &steps)
+// X -> X^g for every Galois element of gals on every query's ciphertext,
+// sharing one ModUp per query (hoisted), as ct_rotate_hoisted / ct_apply_galois
+Owned galois_b(Ctx *c, const std::vector<const EvalKey *> &evk, const CCtVec &a, const std::vector<u64> &gals)
 {
     Owned o;
     if (a.empty()) return o;
     const int l = a[0]->level, N = c->N, nq = l + 1, nl = nq + c->K, dnum = c->dnum(l);
-    const size_t B = a.size(), S = steps.size();
+    const size_t B = a.size(), S = gals.size();
     const size_t dplane = (size_t)dnum * nl * N, uplane = (size_t)2 * nl * N;
     for (auto *x : a) HCHECK(x->level == l, HELRM_E_LEVEL, "batched rotation needs one level");
     std::vector<const SwitchKey *> keys(B * S, nullptr);
     for (size_t q = 0; q < B; q++)
         for (size_t s = 0; s < S; s++)
-            if (c->galois(steps[s]) != 1) keys[q * S + s] = rot_key(evk[q], c->galois(steps[s]), l);
+            if (gals[s] != 1) keys[q * S + s] = rot_key(evk[q], gals[s], l);
     DevMem digits(c, B * dplane * 8), u(c, B * S * uplane * 8);
     std::vector<const u64 *> c1s;
     std::vector<u64 *> dg;
@@ -601,7 +603,7 @@ Owned rotate_b(Ctx *c, const std::vector<const EvalKey *> &evk, const CCtVec &a,
     std::vector<u64 *> o0, o1;
     for (size_t q = 0; q < B; q++)
         for (size_t s = 0; s < S; s++) {
-            const u64 g = c->galois(steps[s]);
+            const u64 g = gals[s];
             std::unique_ptr<Ciphertext> x(new_ct(c, l, a[q]->scale));
             if (g == 1) {
                 co.push_back(x->data.u());
@@ -625,6 +627,13 @@ Owned rotate_b(Ctx *c, const std::vector<const EvalKey *> &evk, const CCtVec &a,
     auto_b(c, ao, aa, ag, nq);
     moddown_b(c, uu, l, 2, o0, o1, add0, std::vector<const u64 *>(uu.size(), nullptr));   // phi(c0) + ModDown(u)
     return o;
+}
+
+Owned rotate_b(Ctx *c, const std::vector<const EvalKey *> &evk, const CCtVec &a, const std::vector<int> &steps)
+{
+    std::vector<u64> gals;
+    for (int st : steps) gals.push_back(c->galois(st));
+    return galois_b(c, evk, a, gals);
 }
 
 // relinearisation of (d0, d1, d2) per query, as ct_relin; with rescale, the
@@ -838,6 +847,8 @@ Batch *batch_create(Ctx *c, const Model *m, const std::vector<const EvalKey *> &
     for (auto &L : m->bottom) batch_keytab(b.get(), L.pm.get());
     for (PtMatrix *pm : m->emb_mats()) batch_keytab(b.get(), pm);
     for (auto &L : m->top) batch_keytab(b.get(), L.pm.get());
+    for (const Model::BootPoint *bp : m->boot_points())
+        for (PtMatrix *pm : bp->b->matrices()) batch_keytab(b.get(), pm);
     // (the host tables were staged by the copies themselves: nothing to wait for)
     return b.release();
 }
@@ -1045,15 +1056,74 @@ static Owned dot_interaction_b(Ctx *c, const Batch *bt, const Model *m, const CC
     return relin_b(c, bt->evk, cd, lvl, c->delta * c->delta, true);
 }
 
-// every query's ciphertext bootstrapped (one query after another: a
-// bootstrap's launches already carry the whole ring) and dropped to the first
-// level of the next segment
-static Owned boot_all(Ctx *c, const Batch *bt, const Model::BootPoint &bp, const CCtVec &x)
+// a + v on every slot of every query's ciphertext (v as residues per prime id)
+static Owned add_int_b(Ctx *c, const CCtVec &a, const DevMem &t)
 {
     Owned o;
-    for (size_t q = 0; q < x.size(); q++) {
-        std::unique_ptr<Ciphertext> y(bootstrap(c, bt->evk[q], bp.b.get(), x[q]));
-        o.v.emplace_back(ct_drop(c, y.get(), bp.lvl_next));
+    for (auto *x : a) {
+        o.v.emplace_back(new_ct(c, x->level, x->scale));
+        k::add_scalar(c, o.v.back()->c0(), x->c0(), t.u(), x->level + 1, c->qmap(x->level));
+        k::copy(c, o.v.back()->c1(), x->c1(), (size_t)(x->level + 1) * c->N);
+    }
+    return o;
+}
+
+// The bootstrap of boot.cu on every query's ciphertext, step by step for the
+// whole batch (the same operations: ModRaise per query, then SubSum,
+// CoeffToSlot and its conjugate, EvalMod and SlotToCoeff with the batched
+// rotations, products and matvecs, whose CTAs of all queries that work on the
+// same tile run together, so shared rows are read once); then dropped to the
+// first level of the next segment.
+static Owned boot_all(Ctx *c, const Batch *bt, const Model::BootPoint &bp, const CCtVec &x)
+{
+    const Boot *b = bp.b.get();
+    const size_t B = x.size();
+    const int N = c->N, L = b->level_top;
+    const std::vector<const EvalKey *> &evk = bt->evk;
+    Owned r;
+    for (size_t q = 0; q < B; q++) {   // boost and ModRaise
+        std::unique_ptr<Ciphertext> x0(ct_drop(c, x[q], 0));
+        k::mul_scalar_mont(c, x0->data.u(), x0->data.u(), b->boost_mont.u(), 2, c->qmap(0, 0, 1));
+        DevMem coef(c, (size_t)2 * N * 8);
+        std::vector<k::NttLimb> inv = {{x0->c0(), coef.u(), 0, nullptr, nullptr},
+                                       {x0->c1(), coef.u() + N, 0, nullptr, nullptr}};
+        k::ntt_run(c, inv, true, nullptr);
+        std::unique_ptr<Ciphertext> y(new_ct(c, L, (double)c->primes[0]));
+        k::mod_raise(c, y->data.u(), coef.u(), (size_t)N, 2, L + 1, c->qmap(L));
+        k::ntt_fwd(c, y->data.u(), 2 * (L + 1), c->qmap(L, 0, L + 1));
+        r.v.push_back(std::move(y));
+    }
+    for (int st : b->subsum_steps) {   // SubSum
+        Owned rr = rotate_b(c, evk, r.craw(), {st});
+        r = add_b(c, r.craw(), rr.craw());
+    }
+    Owned y = matvec_b(c, bt, b->cts_a.get(), r.craw());   // CoeffToSlot: C + conj(C)
+    r = Owned();
+    {
+        Owned yc = galois_b(c, evk, y.craw(), {2ull * N - 1});
+        y = add_b(c, y.craw(), yc.craw());
+    }
+    for (int i = 1; i < b->cts_levels; i++) y = rescale_b(c, y.craw());
+    for (auto &p : y.v)
+        HCHECK(p->scale == b->s_cts && p->level == b->plan->in_level, HELRM_E_SCALE,
+               "internal: CoeffToSlot ended on another scale or level");
+    y = add_int_b(c, y.craw(), b->c_shift);   // EvalMod
+    Owned cv;
+    for (Ciphertext *p : poly_b(c, evk, y.craw(), *b->plan)) cv.v.emplace_back(p);
+    y = Owned();
+    for (int i = 0; i < b->r; i++) {
+        cv = square_b(c, evk, cv.craw());
+        cv = add_b(c, cv.craw(), cv.craw());
+        cv = add_int_b(c, cv.craw(), b->c_double[i]);
+    }
+    for (auto &p : cv.v)
+        HCHECK(p->level == b->level_stc && p->scale == b->s_eval, HELRM_E_LEVEL,
+               "internal: EvalMod ended on another level or scale");
+    Owned z = matvec_b(c, bt, b->stc.get(), cv.craw());   // SlotToCoeff
+    Owned o;
+    for (size_t q = 0; q < B; q++) {
+        z.v[q]->scale = b->out_scale(x[q]->scale);
+        o.v.emplace_back(ct_drop(c, z.v[q].get(), bp.lvl_next));
     }
     return o;
 }

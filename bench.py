@@ -432,7 +432,7 @@ def one_query(E, wl, K, W, hbm, alu, seed=1000):
     # CUDA graph (helrm_batch_set_graph; bit-identical to the eager path): the
     # client's packing and encryption and the decryption stay eager
     bt1 = H.helrm_batch_create(ctx, model, [evk])
-    graph = not spec.boot          # a model with bootstraps runs eagerly
+    graph = True
     H.helrm_batch_set_graph(ctx, bt1, graph)
 
     def step_graph(q):
@@ -937,12 +937,9 @@ def run_ours(args):
         line.update({"value": main["value"], "ms_per_step": main["ms_per_step"], "latency_ms": main["latency_ms"],
                      "clocks": clk, "gpu_launches": int(main["launches_per_step"] * K),
                      "value_eager": main["value_eager"],
-                     "value_note": ("value: the server path of a batch of one replayed as a CUDA graph "
-                                    "(helrm_infer_batch_e2e_device); value_eager: every kernel launched on the "
-                                    "stream (helrm_infer_e2e_device); both bit-identical")
-                     if args.workload not in BOOT_WORKLOADS else
-                     ("value: the batch of one launched on the stream (a model with bootstraps runs without "
-                      "a CUDA graph); value_eager: helrm_infer_e2e_device, the same launches"),
+                     "value_note": "value: the server path of a batch of one replayed as a CUDA graph "
+                                   "(helrm_infer_batch_e2e_device); value_eager: every kernel launched on the "
+                                   "stream (helrm_infer_e2e_device); both bit-identical",
                      "e2e": main["e2e"], "roofline": main["roofline"]})
         line.update(extras)
         if E.world == 1 and not args.no_cpu_baseline and args.workload not in BOOT_WORKLOADS:

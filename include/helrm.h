@@ -368,7 +368,7 @@ typedef struct {
  * diagonals per point, in model order) follow the model's in the canonical
  * order.  helrm_model_keygen then draws a sparse secret (h = 192) and adds
  * the bootstraps' rotation keys, the conjugation key and a full-level
- * relinearisation key; a model with bootstraps runs eagerly (no CUDA graph).
+ * relinearisation key.
  * Errors: HELRM_E_PARAM if the chain is too short or a layout exceeds n. */
 helrm_status helrm_model_create(helrm_ctx *ctx, const helrm_model_desc *desc, helrm_model **out);
 /* info_out[0..9] = level of ct_dense, level of ct_sel, level of z, level of

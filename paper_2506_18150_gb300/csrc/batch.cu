@@ -1221,7 +1221,6 @@ std::vector<Ciphertext *> model_infer_batch_graph(Ctx *c, Batch *bt, const CCtVe
     const size_t S = B * (size_t)m->n_sel();   // ct_sel is query-major, n_sel per query
     HCHECK(ct_dense.size() == B && ct_sel.size() == S, HELRM_E_INVAL, "batch size mismatch");
     HCHECK(!c->prof_on, HELRM_E_INVAL, "kernel profiling cannot be recorded inside a graph");
-    HCHECK(!m->has_boot(), HELRM_E_PARAM, "a model with bootstraps runs eagerly (no CUDA graph)");
     for (size_t q = 0; q < B; q++)
         HCHECK(ct_dense[q]->level == m->lvl_dense, HELRM_E_LEVEL, "ct_dense is not at the model's dense level");
     for (size_t r = 0; r < S; r++)

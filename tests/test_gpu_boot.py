@@ -164,7 +164,7 @@ def test_bootstrapped_dlrm_bit_exact():
     layer 1 and on z, at N = 2^10 on the bootstrappable chain: with the
     oracle's plaintexts (the bootstraps' diagonals included) and cosine
     polynomial, the logit ciphertext of helrm_infer and of a batch of two
-    equals the oracle's word for word; the graph path refuses the model."""
+    equals the oracle's word for word, eagerly and replayed as a CUDA graph."""
     from oracle import boot, ckks, dlrm
     from paper_2506_18150_gb300 import helrm as H
     from paper_2506_18150_gb300 import synthetic as syn
@@ -194,9 +194,10 @@ def test_bootstrapped_dlrm_bit_exact():
     for q in range(2):
         assert_ct_equal(ctx, ys[q], want[q])
     H.helrm_batch_set_graph(ctx, bt, True)
-    with pytest.raises(H.HelrmError) as e:
-        H.helrm_infer_batch(ctx, bt, [import_ct(ctx, cts[0][0])] * 2, [import_ct(ctx, cts[0][1])] * 2)
-    assert e.value.name == "HELRM_E_PARAM"
+    for _ in range(2):                                  # the capture, then a replay
+        ys = H.helrm_infer_batch(ctx, bt, [import_ct(ctx, cd) for cd, _ in cts], [import_ct(ctx, cs) for _, cs in cts])
+        for q in range(2):
+            assert_ct_equal(ctx, ys[q], want[q])
     logit = H.helrm_decrypt_logit(ctx, sk, ys[0])[0]
     assert abs(logit - dlrm.dlrm_cleartext(spec, w, dense[0], idx[0])[0]) < 1e-4
 

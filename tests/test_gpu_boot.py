@@ -202,6 +202,39 @@ def test_bootstrapped_dlrm_bit_exact():
     assert abs(logit - dlrm.dlrm_cleartext(spec, w, dense[0], idx[0])[0]) < 1e-4
 
 
+def test_served_bootstrapped_dlrm_bit_exact():
+    """The bootstrapped UCI-shaped SiLU model (N = 2^10) through the serving
+    loop: a burst of three requests of one client batched together; every
+    served logit ciphertext equals the oracle's dlrm.infer word for word."""
+    from oracle import boot, ckks, dlrm
+    from paper_2506_18150_gb300 import helrm as H
+    from paper_2506_18150_gb300 import synthetic as syn
+    pr = syn.boot_params(10, 10)
+    p = oracle_params(pr)
+    spec = syn.uci_silu_boot_spec(0)
+    spec.boot_coeffs = tuple(boot.cos_fit(24, 6, 16))
+    w = syn.make_weights(spec, 0)
+    c = dlrm.compile_model(p, spec, w)
+    ctx = gpu_ctx(pr)
+    model = H.helrm_model_create(ctx, spec, w)
+    H.helrm_model_import_plaintexts(ctx, model, np.stack([np.asarray(x, dtype=np.int64) for x in c.plaintexts()]))
+    _, evk = H.helrm_model_keygen(ctx, model, 5)
+    _, keys = ckks.keygen(p, 5, rot_steps=c.rotation_steps(), h=H_SECRET, conj=True)
+    dense, idx = syn.make_queries(spec, 3, seed=8)
+    cts, want = [], []
+    for q in range(3):
+        cd, cs = dlrm.encrypt_query(p, keys, c, dense[q], idx[q], 300 + 2 * q)
+        cts.append((import_ct(ctx, cd), import_ct(ctx, cs)))
+        want.append(dlrm.infer(p, keys, c, cd, cs))
+    srv = H.helrm_server_create(ctx, 1, 4, 0)
+    H.helrm_server_add_client(ctx, srv, model, evk)
+    outs, _, st = H.helrm_server_run(ctx, srv, np.zeros(3), np.zeros(3, dtype=np.uint32), [x[0] for x in cts],
+                                     [x[1] for x in cts])
+    assert st["max_batch"] > 1, "the burst should have been batched"
+    for q in range(3):
+        assert_ct_equal(ctx, outs[q], want[q])
+
+
 @pytest.mark.parametrize("name,levels", [("criteo_silu_boot_spec", (10, 1)), ("criteo_relu_boot_spec", (12, 1))])
 def test_criteo_with_bootstraps_full_size(name, levels):
     """The Criteo-shaped model with polynomial activations at N = 2^16 on the

@@ -31,10 +31,17 @@ The default line also carries, each timed on the same GPU in the same run:
   served   the request loop (helrm_server_run) on Poisson traces at two
            arrival rates, 80% UCI / 20% Criteo over config4's clients, with
            p50/p99 latency, for the continuous-batching server and the plain
-           one-request-at-a-time path.
+           one-request-at-a-time path;
+  boot     bootstrapping alone (boot_measure: 512 periodic slots at N = 2^16
+           on the bootstrappable chain);
+  criteo_silu_boot / criteo_relu_boot   the one-query measurements of the
+           Criteo-shaped model with SiLU (two bootstraps per query) and with
+           a ReLU stand-in (three), on the bootstrappable chain.
 
 --workload uci / uci_silu   the one-query line for the UCI-shaped model
                     (uci_silu: every activation a degree-6 SiLU polynomial).
+--workload criteo_silu_boot / criteo_relu_boot   the one-query line for the
+                    bootstrapped Criteo-shaped models.
 --workload batched  config4 alone, with more steps.
 --workload served   the request loop at every rate of --rates, 32 + 8 clients.
 --workload tiny     config 1: one 1024 x 16 table in base 32 at N = 2^13, one

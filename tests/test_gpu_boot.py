@@ -34,7 +34,7 @@ def _gpu_boot(ctx, p, b_or):
     return bt
 
 
-@pytest.mark.parametrize("log_n,n_s", [(10, 64), (11, 256), (10, 4), (10, 1)])
+@pytest.mark.parametrize("log_n,n_s", [(10, 64), (11, 256), (10, 4), (10, 1), (10, 256)])
 def test_bootstrap_stages_bit_exact(log_n, n_s):
     from oracle import boot, ckks
     from paper_2506_18150_gb300 import helrm as H

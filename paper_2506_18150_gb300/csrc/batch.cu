@@ -146,10 +146,14 @@ struct KsJobs {
 // Fused automorphism + key inner product of k_ks_inner, one job per
 // (query, key): out_h[l][i] = sum_j dig_j[l][src(i)] key_j,h[pid(l)][i]
 // (+ P c0[l][src(i)] on the Q limbs, + bq[l][src(i)], + out when accumulating).
-__global__ void k_ks_inner_b(const KsJobs J, int dnum, int level, int L, int K, int logN, const u64 *__restrict__ pmod,
-                             int accumulate, const PrimeInfo *__restrict__ pinfo)
+// DN > 0: the digit count as a constant, so the 3 DN loads of a word are all
+// issued before its products; DN = 0 takes dnum_rt.
+template <int DN>
+__global__ void k_ks_inner_b(const KsJobs J, int dnum_rt, int level, int L, int K, int logN,
+                             const u64 *__restrict__ pmod, int accumulate, const PrimeInfo *__restrict__ pinfo)
 {
     pdl_begin();
+    const int dnum = DN > 0 ? DN : dnum_rt;
     const int jb = blockIdx.y;
     u64 *__restrict__ out = J.out[jb];
     const u64 *__restrict__ dig = J.dig[jb];
@@ -170,6 +174,7 @@ __global__ void k_ks_inner_b(const KsJobs J, int dnum, int level, int L, int K, 
         const PrimeInfo pi = pinfo[pid];
         const int src = galois == 1 ? i : auto_src_b(i, logN, galois);
         Acc128 a0, a1;
+#pragma unroll
         for (int j = 0; j < dnum; j++) {
             const u64 d = dig[((size_t)j * nl + l) * N + src];
             a0.mac(d, key[((size_t)(2 * j) * nK + kx) * N + i], pi.q);
@@ -290,6 +295,16 @@ struct KsJob {
     const u64 *bq;
 };
 
+using KsInnerB = void (*)(const KsJobs, int, int, int, int, int, const u64 *, int, const PrimeInfo *);
+
+KsInnerB ks_inner_kernel(int dnum)
+{
+    static const KsInnerB fns[] = {k_ks_inner_b<0>, k_ks_inner_b<1>, k_ks_inner_b<2>, k_ks_inner_b<3>,
+                                   k_ks_inner_b<4>, k_ks_inner_b<5>, k_ks_inner_b<6>, k_ks_inner_b<7>,
+                                   k_ks_inner_b<8>, k_ks_inner_b<9>};
+    return dnum >= 1 && dnum <= 9 ? fns[dnum] : fns[0];
+}
+
 void ks_inner_b(Ctx *c, const std::vector<KsJob> &jobs, int level, bool accumulate)
 {
     if (jobs.empty()) return;
@@ -314,7 +329,7 @@ void ks_inner_b(Ctx *c, const std::vector<KsJob> &jobs, int level, bool accumula
             J.bq[j] = x.bq;
             J.gal[j] = x.gal;
         }
-        launch(c, k_ks_inner_b, dim3(gx_for(total, J.n), J.n), TPB, 0, J, dnum, level, c->L, c->K, c->logN,
+        launch(c, ks_inner_kernel(dnum), dim3(gx_for(total, J.n), J.n), TPB, 0, J, dnum, level, c->L, c->K, c->logN,
                c->d_pmod_mont.u(), accumulate ? 1 : 0, c->d_pinfo.as<PrimeInfo>());
         c->launches++;
     }

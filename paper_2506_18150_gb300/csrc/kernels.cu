@@ -139,12 +139,16 @@ __device__ __forceinline__ int auto_src(int i, int logN, u64 galois)
     return (int)(__brev((u32)((e - 1) >> 1)) >> (32 - logN));
 }
 
-__global__ void k_ks_inner(u64 *__restrict__ out, const u64 *__restrict__ dig, int dnum,
+// DN > 0: the digit count as a constant (every load of a word issued before
+// its products); DN = 0 takes dnum_rt.
+template <int DN>
+__global__ void k_ks_inner(u64 *__restrict__ out, const u64 *__restrict__ dig, int dnum_rt,
                            const u64 *__restrict__ key, int kl, int level, int L, int K, int logN, u64 galois,
                            const u64 *__restrict__ c0, const u64 *__restrict__ pmod,
                            const u64 *__restrict__ bq, int accumulate, const PrimeInfo *__restrict__ pinfo)
 {
     pdl_begin();
+    const int dnum = DN > 0 ? DN : dnum_rt;
     const size_t N = (size_t)1 << logN;
     const int nl = level + 1 + K, nK = kl + 1 + K;
     const size_t total = (size_t)nl * N;
@@ -157,6 +161,7 @@ __global__ void k_ks_inner(u64 *__restrict__ out, const u64 *__restrict__ dig, i
         const PrimeInfo pi = pinfo[pid];
         const int src = galois == 1 ? i : auto_src(i, logN, galois);
         Acc128 a0, a1;
+#pragma unroll
         for (int j = 0; j < dnum; j++) {
             const u64 d = dig[((size_t)j * nl + l) * N + src];
             a0.mac(d, key[((size_t)(2 * j) * nK + kx) * N + i], pi.q);
@@ -789,7 +794,12 @@ void ks_inner_auto(Ctx *c, u64 *out, const u64 *digits, int dnum, const SwitchKe
     // written (and read, when accumulating)
     KTimer kt(c, "ks_inner_auto", 8.0 * (total * (3.0 * dnum + (accumulate ? 4 : 2) + (bq ? 1 : 0)) +
                                          (c0 ? (double)(level + 1) * c->N : 0.0)));
-    launch(c, k_ks_inner, grid_for(total), TPB, 0, out, digits, dnum, key->data.u(), key->level, level, c->L, c->K,
+    using Fn = void (*)(u64 *, const u64 *, int, const u64 *, int, int, int, int, int, u64, const u64 *, const u64 *,
+                        const u64 *, int, const PrimeInfo *);
+    static const Fn fns[] = {k_ks_inner<0>, k_ks_inner<1>, k_ks_inner<2>, k_ks_inner<3>, k_ks_inner<4>,
+                             k_ks_inner<5>, k_ks_inner<6>, k_ks_inner<7>, k_ks_inner<8>, k_ks_inner<9>};
+    launch(c, fns[dnum >= 1 && dnum <= 9 ? dnum : 0], grid_for(total), TPB, 0, out, digits, dnum, key->data.u(),
+           key->level, level, c->L, c->K,
            c->logN, galois, c0,
                                                  d_pmod_mont, bq, accumulate ? 1 : 0, c->d_pinfo.as<PrimeInfo>());
     LAUNCHED(c);

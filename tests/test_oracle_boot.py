@@ -205,3 +205,24 @@ def test_bootstrapped_dlrm_matches_the_cleartext_model():
     got = dlrm.decrypt_logit(p, sk, y)[0]
     want = dlrm.dlrm_cleartext(spec, w, dense[0], idx[0])[0]
     assert abs(got - want) < 1e-4
+
+
+def test_constant_message_follows_the_sine():
+    """With n_s = 1 a constant message z is the constant polynomial
+    m = round(Delta z), so EvalMod sees the single value u = 2^b m / q_0 and
+    the bootstrap returns sin(2 pi u) / (2 pi u) times z, not z: about
+    z (1 - (2 pi u)^2 / 6), 4.6e-6 below 0.9 at 2^b = 2^10 and a 60-bit q_0.
+    The output matches the sine to the bootstrap's noise (2e-8), which a
+    wrong boost, a dropped 2 pi or a wrong SlotToCoeff constant would miss by
+    far more."""
+    p = ckks.Params(LOG_N, Q_BITS, 3, 60, 3, 40.0)
+    b = boot.prepare(p, boot.BootParams(n_s=1))
+    assert len(b.subsum_steps) == LOG_N - 1
+    sk, keys = ckks.keygen(p, 7, rot_steps=b.rotation_steps(), h=H, conj=True)
+    for z0, seed in ((0.9, 11), (-0.5, 12)):
+        ct = ckks.encrypt(p, keys, ckks.encode_real(p, np.full(p.n, z0), p.delta), 2, p.delta, seed)
+        got = ckks.decrypt(p, sk, boot.bootstrap(p, keys, b, ct, {})).real
+        u = 2.0**b.bp.log2_boost * round(p.delta * z0) / float(p.q[0])
+        want = math.sin(2 * math.pi * u) / (2 * math.pi * u) * z0
+        assert abs(want - z0) > 5e-7                      # the sine's own departure from z
+        assert np.max(np.abs(got - want)) < 1e-7
